@@ -1,0 +1,427 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these compare the oracle with itself: they use closed-form band
+structures, dense diagonalisation, matrix exponentials, library Bessel
+functions, finite differences and the paper's stated spectra.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+from scipy.special import jv
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def facts():
+    with open(os.path.join(GOLDEN, "paper_facts.json")) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------- Dirac algebra
+def test_gamma_clifford_algebra():
+    G = O.gamma_matrices()
+    for a in range(1, 6):
+        assert np.allclose(G[a], G[a].conj().T)
+        for b in range(1, 6):
+            anti = G[a] @ G[b] + G[b] @ G[a]
+            assert np.allclose(anti, 2.0 * (a == b) * np.eye(4), atol=1e-15)
+    assert np.allclose(G[1], np.diag([1, -1, 1, -1]))
+    # Gamma^{ab} is Hermitian and anticommutes with Gamma^a
+    G15 = O.gamma_commutator(G, 1, 5)
+    assert np.allclose(G15, G15.conj().T)
+    assert np.allclose(G15 @ G[1] + G[1] @ G15, 0)
+
+
+# ---------------------------------------------------------------- TI Hamiltonian
+def ti_bloch_energies(dims, m, t):
+    """Closed-form bands E(k) = +-sqrt((m - t sum cos k_j)^2 + t^2 sum sin^2 k_j), each twice."""
+    ks = [2 * np.pi * np.arange(L) / L for L in dims]
+    KX, KY, KZ = np.meshgrid(*ks, indexing="ij")
+    c = np.cos(KX) + np.cos(KY) + np.cos(KZ)
+    s2 = np.sin(KX) ** 2 + np.sin(KY) ** 2 + np.sin(KZ) ** 2
+    E = np.sqrt((m - t * c) ** 2 + t ** 2 * s2).reshape(-1)
+    return np.sort(np.concatenate([E, E, -E, -E]))
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4), (3, 5, 4), (6, 2, 3)])
+@pytest.mark.parametrize("m", [0.5, 2.0, 3.5])
+def test_ti_periodic_bands_match_closed_form(dims, m):
+    n = int(np.prod(dims))
+    H = O.ti_hamiltonian(dims, (1, 1, 1), 1.0, m, np.zeros(n))
+    e = np.linalg.eigvalsh(H.toarray())
+    assert np.max(np.abs(e - ti_bloch_energies(dims, m, 1.0))) < 1e-12
+
+
+def test_ti_hopping_amplitude_t():
+    dims = (4, 3, 5)
+    n = int(np.prod(dims))
+    H = O.ti_hamiltonian(dims, (1, 1, 1), 0.7, 1.3, np.zeros(n))
+    e = np.linalg.eigvalsh(H.toarray())
+    assert np.max(np.abs(e - ti_bloch_energies(dims, 1.3, 0.7))) < 1e-12
+
+
+@pytest.mark.parametrize("dims,per", [((3, 4, 2), (1, 0, 1)), ((1, 2, 3), (1, 1, 0)),
+                                      ((2, 1, 1), (1, 1, 1)), ((5, 3, 4), (0, 0, 0))])
+def test_ti_hermitian_with_disorder(dims, per):
+    n = int(np.prod(dims))
+    V = W.disorder_potential(n, 2.0, 7)
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
+    assert abs(H - H.conj().T).max() == 0.0
+    assert np.allclose(H.diagonal().real.reshape(n, 4),
+                       V[:, None] + 2.0 * np.array([1, -1, 1, -1])[None, :] +
+                       _self_bond_diag(dims, per))
+
+
+def _self_bond_diag(dims, per):
+    # a periodic axis of length 1 bonds a site to itself: B + B^+ = -t Gamma^1
+    g1 = np.array([1, -1, 1, -1], dtype=float)
+    return sum(-g1 for L, p in zip(dims, per) if L == 1 and p)
+
+
+def test_ti_bulk_gap_and_phase_boundaries():
+    f = facts()
+    dims = (6, 6, 6)
+    n = 216
+    H = O.ti_hamiltonian(dims, (1, 1, 1), 1.0, f["ti_clean_bulk_gap"]["m"], np.zeros(n))
+    e = np.linalg.eigvalsh(H.toarray())
+    assert abs(np.min(np.abs(e)) - f["ti_clean_bulk_gap"]["gap_edge"]) < 1e-12
+    for m in f["ti_phase_boundaries"]["m_values"]:
+        H = O.ti_hamiltonian(dims, (1, 1, 1), 1.0, m, np.zeros(n))
+        assert np.min(np.abs(np.linalg.eigvalsh(H.toarray()))) < 1e-12
+    for m in (0.5, 2.0, 3.5):   # gapped inside each phase
+        H = O.ti_hamiltonian(dims, (1, 1, 1), 1.0, m, np.zeros(n))
+        assert np.min(np.abs(np.linalg.eigvalsh(H.toarray()))) > 0.4
+
+
+def test_ti_disordered_spectrum_in_paper_range():
+    f = facts()["ti_spectrum_range"]
+    dims = (6, 5, 6)
+    n = int(np.prod(dims))
+    V = W.disorder_potential(n, f["W"], 11)
+    H = O.ti_hamiltonian(dims, (1, 1, 1), 1.0, f["m"], V)
+    e = np.linalg.eigvalsh(H.toarray())
+    lo, hi = f["interval"]
+    assert e.min() >= lo and e.max() <= hi
+    # and it is not trivially inside: the clean band edges are at +-5
+    assert e.max() > 4.5 and e.min() < -4.5
+
+
+def test_ti_open_boundary_drops_bonds():
+    # a 1 x 1 x 2 open chain has exactly one bond along z
+    H = O.ti_hamiltonian((1, 1, 2), (0, 0, 0), 1.0, 0.0, np.zeros(2)).toarray()
+    G = O.gamma_matrices()
+    B = -(1.0 / 2.0) * (G[1] - 1j * G[4])
+    assert np.allclose(H[4:8, 0:4], B)
+    assert np.allclose(H[0:4, 4:8], B.conj().T)
+    assert np.allclose(H[0:4, 0:4], 0)
+
+
+# ---------------------------------------------------------------- graphene
+def graphene_paper_band(kx, ky):
+    """|eps(k)| from Eq. graphene_e_k (a = 1)."""
+    return np.sqrt(np.maximum(3 + 2 * np.cos(np.sqrt(3) * ky) +
+                              4 * np.cos(np.sqrt(3) * ky / 2) * np.cos(1.5 * kx), 0.0))
+
+
+@pytest.mark.parametrize("cells", [(6, 4), (5, 3), (4, 7)])
+def test_graphene_periodic_bands_match_paper_formula(cells):
+    Nx, Ny = cells
+    H = O.graphene_hamiltonian(cells, (1, 1), 1.0, np.zeros(4 * Nx * Ny))
+    assert abs(H - H.conj().T).max() == 0.0
+    e = np.linalg.eigvalsh(H.toarray())
+    ref = []
+    for p in range(Nx):
+        for q in range(Ny):
+            # cell axis x spans physical Y (period sqrt3), cell axis y spans physical X (period 3)
+            kX, kY = 2 * np.pi * q / (3 * Ny), 2 * np.pi * p / (np.sqrt(3) * Nx)
+            for kx in (kX, kX + 2 * np.pi / 3):   # the 4-site cell folds two primitive k's
+                E = graphene_paper_band(kx, kY)
+                ref += [E, -E]
+    assert np.max(np.abs(e - np.sort(ref))) < 1e-12
+
+
+def test_graphene_bonds_have_unit_length():
+    Nx, Ny = 5, 4
+    H = O.graphene_hamiltonian((Nx, Ny), (0, 0), 1.0, np.zeros(4 * Nx * Ny)).tocoo()
+    X, Y = W.graphene_positions(Nx, Ny)
+    off = H.row != H.col
+    d = np.hypot(X[H.row[off]] - X[H.col[off]], Y[H.row[off]] - Y[H.col[off]])
+    assert np.allclose(d, 1.0)
+    assert np.allclose(H.data[off], -1.0)
+    # every interior site has exactly three neighbours
+    deg = np.bincount(H.row[off], minlength=4 * Nx * Ny)
+    assert deg.max() == 3
+
+
+def _dsl_hamiltonian(Nx, Ny, periodic, V):
+    rows, cols, vals = [], [], []
+    path = os.path.join(GOLDEN, "graphene_dsl_couplings.txt")
+    entries = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    for x in range(Nx):
+        for y in range(Ny):
+            c = x + Nx * y
+            for dx, dy, r, col, val in entries:
+                xx, yy = x + int(dx), y + int(dy)
+                if periodic[0]:
+                    xx %= Nx
+                if periodic[1]:
+                    yy %= Ny
+                if not (0 <= xx < Nx and 0 <= yy < Ny):
+                    continue
+                cc = xx + Nx * yy
+                rows.append(4 * c + int(r))
+                cols.append(4 * cc + int(col))
+                vals.append(V[4 * c + int(r)] if val == "v" else float(val))
+    D = 4 * Nx * Ny
+    import scipy.sparse as sp
+    return sp.coo_matrix((vals, (rows, cols)), shape=(D, D)).tocsr()
+
+
+@pytest.mark.parametrize("periodic", [(1, 1), (0, 0), (1, 0)])
+def test_graphene_equation_equals_dsl_listing_up_to_mirror(periodic):
+    Nx, Ny = 5, 4
+    V = W.disorder_potential(4 * Nx * Ny, 1.0, 3)
+    Hd = _dsl_hamiltonian(Nx, Ny, periodic, V).toarray()
+    # mirror x -> Nx-1-x of the equation form (V mirrored along with it)
+    perm = np.array([4 * ((Nx - 1 - (c % Nx)) + Nx * (c // Nx)) + nu
+                     for c in range(Nx * Ny) for nu in range(4)])
+    He = O.graphene_hamiltonian((Nx, Ny), periodic, 1.0, V[perm]).toarray()
+    assert np.allclose(He[np.ix_(perm, perm)], Hd)
+    assert np.allclose(np.linalg.eigvalsh(He), np.linalg.eigvalsh(Hd))
+
+
+# ---------------------------------------------------------------- scaling
+def test_gershgorin_matches_row_sums_and_brackets_spectrum():
+    dims = (5, 4, 3)
+    n = 60
+    V = W.disorder_potential(n, 1.0, 1)
+    H = O.ti_hamiltonian(dims, (1, 1, 1), 1.0, 2.0, V)
+    emin, emax = O.gershgorin(H)
+    # every TI bond block has unit row abs-sum per unit t: radius 6 t in the bulk
+    assert abs(emin - (-2.0 - 6.0 + V.min())) < 1e-14 or abs(emin - (-2.0 - 6.0 + V[V < 0].min())) < 1e-14
+    assert abs(emax - (2.0 + 6.0 + V.max())) < 1e-14
+    e = np.linalg.eigvalsh(H.toarray())
+    assert emin <= e.min() and e.max() <= emax
+    a, b = O.cheb_scale(emin, emax)
+    et = (e - b) / a
+    assert et.min() > -1 and et.max() < 1
+    # graphene: radius 3 t
+    Hg = O.graphene_hamiltonian((4, 4), (1, 1), 1.0, np.full(64, 0.25))
+    assert O.gershgorin(Hg) == (0.25 - 3.0, 0.25 + 3.0)
+
+
+# ---------------------------------------------------------------- KPM
+def _dense_Tk(H, a, b, kmax):
+    e, U = np.linalg.eigh(H.toarray())
+    et = np.clip((e - b) / a, -1, 1)
+    return U, np.array([np.cos(k * np.arccos(et)) for k in range(kmax)])
+
+
+def test_kpm_mu0_is_one_for_random_phase():
+    dims = (3, 4, 5)
+    n = 60
+    H = O.ti_hamiltonian(dims, (1, 1, 0), 1.0, 2.0, W.disorder_potential(n, 1.0, 2))
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    r = W.random_phase_block(4 * n, 3, 9)
+    mu = O.kpm_moments(H, r, 16, a, b)
+    assert np.allclose(mu[:, 0], 1.0, atol=1e-14)
+    assert np.max(np.abs(mu.imag)) < 1e-13
+
+
+def test_kpm_eigenvector_start_gives_chebyshev_of_energy():
+    dims = (3, 3, 2)
+    n = 18
+    H = O.ti_hamiltonian(dims, (1, 1, 1), 1.0, 2.0, W.disorder_potential(n, 1.0, 4))
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    e, U = np.linalg.eigh(H.toarray())
+    l = [0, 17, 40]
+    mu = O.kpm_moments(H, U[:, l], 64, a, b)
+    ref = np.array([[math.cos(k * math.acos((e[j] - b) / a)) for k in range(64)] for j in l])
+    assert np.max(np.abs(mu - ref)) < 1e-12
+
+
+def test_kpm_exact_trace_equals_eigenvalue_sum():
+    dims = (2, 2, 2)
+    n = 8
+    H = O.ti_hamiltonian(dims, (1, 1, 1), 1.0, 2.0, W.disorder_potential(n, 1.0, 5))
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    D = 4 * n
+    mu = O.kpm_moments(H, np.eye(D), 40, a, b).real.mean(axis=0)
+    e = np.linalg.eigvalsh(H.toarray())
+    ref = np.array([np.mean(np.cos(k * np.arccos((e - b) / a))) for k in range(40)])
+    assert np.max(np.abs(mu - ref)) < 1e-12
+
+
+def test_kpm_matches_dense_polynomial_graphene():
+    H = O.graphene_hamiltonian((3, 4), (0, 1), 1.0, W.disorder_potential(48, 0.5, 6))
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    r = W.random_phase_block(48, 2, 1)
+    U, Tk = _dense_Tk(H, a, b, 30)
+    ref = np.array([[np.vdot(r[:, j], U @ (Tk[k] * (U.conj().T @ r[:, j]))) for k in range(30)]
+                    for j in range(2)])
+    assert np.max(np.abs(O.kpm_moments(H, r, 30, a, b) - ref)) < 1e-12
+
+
+def test_cheb_step_reproduces_recurrence_and_apply():
+    H = O.ti_hamiltonian((3, 2, 4), (1, 0, 1), 1.0, 2.0, W.disorder_potential(24, 1.0, 8))
+    x = W.gaussian_block(96, 2, 3)
+    y, _, dots = O.cheb_step(H, x, np.zeros_like(x), [1, 1], [0, 0], [0, 0])
+    e, U = np.linalg.eigh(H.toarray())
+    assert np.allclose(y, U @ (e[:, None] * (U.conj().T @ x)), atol=1e-12)
+    # <Hx|x> is the Rayleigh numerator, real for Hermitian H
+    ray = np.sum(e[:, None] * np.abs(U.conj().T @ x) ** 2, axis=0)
+    assert np.allclose(dots[:, 1], ray, atol=1e-12)
+    assert np.allclose(dots[:, 0].real, np.sum(np.abs(x) ** 2, axis=0))
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    w0 = x
+    w1, _, _ = O.cheb_step(H, w0, np.zeros_like(x), [1 / a] * 2, [b] * 2, [0, 0])
+    w2, z, _ = O.cheb_step(H, w1, w0, [2 / a] * 2, [b] * 2, [-1, -1], z=w0.copy(), delta=[0.5, 0.5])
+    _, Tk = _dense_Tk(H, a, b, 3)
+    assert np.allclose(w2, U @ (Tk[2][:, None] * (U.conj().T @ x)), atol=1e-12)
+    assert np.allclose(z, w0 + 0.5 * w2)
+
+
+# ---------------------------------------------------------------- propagation
+def test_bessel_against_library_and_sum_rules():
+    for x in (0.3, 3.05, 12.5):
+        J = O.bessel_j(x, 80)
+        assert np.max(np.abs(J - jv(np.arange(81), x))) < 2e-15
+        assert abs(J[0] + 2 * J[2::2].sum() - 1) < 1e-15
+        assert abs(J[0] ** 2 + 2 * np.sum(J[1:] ** 2) - 1) < 1e-14
+
+
+def test_bessel_asymptotic_decay_from_paper():
+    f = facts()["bessel_asymptotic"]
+    x = f["x"]
+    J = O.bessel_j(x, 60)
+    prev = 0
+    for k in f["k_values"]:
+        ratio = J[k] / ((math.e * x / (2 * k)) ** k / math.sqrt(2 * math.pi * k))
+        assert 0.85 < ratio < 1.0 and ratio > prev   # approaches 1 from below as k grows
+        prev = ratio
+
+
+def test_truncation_order_for_graphene_qd_workload():
+    # open graphene, V in [0, 0.1]: Gershgorin [-3, 3.1], a = 3.055, dt = 1 -> M = 19
+    a, b = O.cheb_scale(-3.0, 3.1)
+    c = O.propagation_coeffs(a, 1.0, 1e-14)
+    assert len(c) - 1 == 19
+    J = O.bessel_j(a, 30)
+    assert abs(J[19]) >= 1e-14 > abs(J[20])
+    assert np.allclose(np.abs(c), np.abs(J[:20]))
+    assert np.allclose(c[1], -1j * J[1]) and np.allclose(c[2], -J[2])
+
+
+def test_propagation_matches_matrix_exponential():
+    cells = (3, 4)
+    V = W.disorder_potential(48, 0.6, 2)
+    H = O.graphene_hamiltonian(cells, (0, 0), 1.0, V)
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    psi0 = W.gaussian_block(48, 1, 4)[:, 0]
+    psi0 /= np.linalg.norm(psi0)
+    psi = O.propagate(H, psi0, 1.0, 3, a, b)
+    U = sla.expm(-1j * H.toarray() * 1.0)
+    ref = U @ (U @ (U @ psi0))
+    assert np.linalg.norm(psi - ref) < 1e-12
+    assert abs(np.linalg.norm(psi) - 1) < 1e-13
+
+
+def test_propagation_eigenstate_picks_up_phase():
+    H = O.ti_hamiltonian((2, 3, 2), (1, 1, 0), 1.0, 2.0, W.disorder_potential(12, 1.0, 3))
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    e, U = np.linalg.eigh(H.toarray())
+    psi = O.propagate(H, U[:, 5], 0.7, 4, a, b)
+    assert np.linalg.norm(psi - np.exp(-1j * e[5] * 2.8) * U[:, 5]) < 1e-12
+
+
+def test_filter_series_matches_dense_polynomial():
+    H = O.ti_hamiltonian((2, 2, 3), (1, 1, 1), 1.0, 2.0, W.disorder_potential(12, 1.0, 1))
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    g = np.cos(np.arange(12) * 0.3) / (1 + np.arange(12))
+    x = W.gaussian_block(48, 2, 2)
+    U, Tk = _dense_Tk(H, a, b, 12)
+    ref = U @ ((g @ Tk)[:, None] * (U.conj().T @ x))
+    assert np.allclose(O.cheb_series(H, x, g, a, b), ref, atol=1e-12)
+
+
+# ---------------------------------------------------------------- adjoint
+def _loss(H0diag_free, V, cells, psi0, dt, nsteps, a, b, mask):
+    H = O.graphene_hamiltonian(cells, (0, 0), 1.0, V)
+    psi = O.propagate(H, psi0, dt, nsteps, a, b)
+    return O.detector_probability(psi, mask)
+
+
+def test_adjoint_gradient_matches_central_differences():
+    cells = (4, 3)
+    n = 48
+    V = W.disorder_potential(n, 0.4, 12)
+    H = O.graphene_hamiltonian(cells, (0, 0), 1.0, V)
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    psi0 = W.gaussian_block(n, 1, 3)[:, 0]
+    psi0 /= np.linalg.norm(psi0)
+    mask = np.zeros(n, dtype=bool)
+    mask[[3, 7, 8, 20, 33]] = True
+    dt, S = 0.8, 3
+    psiS = O.propagate(H, psi0, dt, S, a, b)
+    G = 2.0 * mask * psiS
+    grad, _ = O.propagate_adjoint(H, psi0, dt, S, a, b, G, O=1)
+    h = 1e-6
+    for site in (0, 3, 17, 30, 47):
+        Vp, Vm = V.copy(), V.copy()
+        Vp[site] += h
+        Vm[site] -= h
+        fd = (_loss(None, Vp, cells, psi0, dt, S, a, b, mask) -
+              _loss(None, Vm, cells, psi0, dt, S, a, b, mask)) / (2 * h)
+        assert abs(fd - grad[site]) < 1e-8 * max(1.0, abs(fd)) + 1e-9
+
+
+def test_adjoint_gradient_matches_daleckii_krein():
+    # one exact step psi1 = exp(-i H dt) psi0: dU/dV_n = U_ev [F o (U_ev^+ P_n U_ev)] U_ev^+
+    dims = (2, 2, 2)
+    n = 8
+    V = W.disorder_potential(n, 1.0, 21)
+    H = O.ti_hamiltonian(dims, (1, 1, 0), 1.0, 2.0, V)
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    dt = 0.9
+    psi0 = W.random_phase_block(32, 1, 5)[:, 0]
+    e, U = np.linalg.eigh(H.toarray())
+    ph = np.exp(-1j * e * dt)
+    de = e[:, None] - e[None, :]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        F = np.where(np.abs(de) > 1e-9, (ph[:, None] - ph[None, :]) / np.where(de == 0, 1, de),
+                     -1j * dt * ph[:, None])
+    psi1 = U @ (ph * (U.conj().T @ psi0))
+    mask_rows = np.zeros(32, dtype=bool)
+    mask_rows[4:12] = True
+    G = 2.0 * mask_rows * psi1
+    ref = np.zeros(n)
+    for site in range(n):
+        P = np.zeros(32)
+        P[4 * site:4 * site + 4] = 1.0
+        Pe = U.conj().T @ (P[:, None] * U)
+        dU = U @ (F * Pe) @ U.conj().T
+        ref[site] = np.real(np.vdot(G, dU @ psi0))
+    grad, G0 = O.propagate_adjoint(H, psi0, dt, 1, a, b, G, O=4)
+    assert np.max(np.abs(grad - ref)) < 1e-11
+    # and the adjoint state is U^+ G
+    Uf = U @ (ph[:, None] * U.conj().T)
+    assert np.allclose(G0[:, 0], Uf.conj().T @ G, atol=1e-12)
+
+
+# ---------------------------------------------------------------- inputs
+def test_counter_hash_known_values_and_disorder_range():
+    # SplitMix64 finaliser of 0 is 0 and of the golden gamma a published constant:
+    # splitmix64 with state 0 yields 0xE220A8397B1DCDAF as its first output
+    assert int(W.mix64(np.array([0], dtype=np.uint64))[0]) == 0
+    assert int(W.mix64(np.array([0x9E3779B97F4A7C15], dtype=np.uint64))[0]) == 0xE220A8397B1DCDAF
+    V = W.disorder_potential(100000, 4.0, 2)
+    assert V.min() >= -2.0 and V.max() < 2.0 and abs(V.mean()) < 0.02
+    r = W.random_phase_block(1000, 3, 3)
+    assert np.allclose(np.sum(np.abs(r) ** 2, axis=0), 1.0)
