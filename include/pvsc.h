@@ -1,0 +1,310 @@
+/*
+ * pvsc.h -- C ABI of the GB300 matrix-free Chebyshev stencil library.
+ *
+ * The library applies the tight-binding Hamiltonians of Pieper, Hager and
+ * Fehske (arXiv 1708.09689) to blocks of R complex vectors without storing a
+ * matrix, and fuses that stencil into the Chebyshev recurrences that call it
+ * (kernel polynomial method, Chebyshev filtering, Chebyshev time propagation).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Models.  PVSC_TI: Eq. TB_H_topi (Sec. 2.2), a cubic lattice with 4 orbitals
+ *   per site, on-site m Gamma^1 + V_n, hopping -(t/2)(Gamma^1 - i Gamma^{j+1})
+ *   from n to n + e_j plus its Hermitian conjugate (Delta_1 = Delta_2 = 0).
+ *   PVSC_GRAPHENE: Eq. graphene_model (Sec. 2.1), an Nx x Ny array of 4-site
+ *   cells with the 4x4 transfer matrices T_x, T_y, T_n (entries -t) and a
+ *   per-site potential v_{n,j}.
+ * Sites.  TI: n = x + Lx (y + Ly z).  Graphene: site = 4 c + nu, c = x + Nx y.
+ * Vectors.  A block of R vectors is stored site-major with the vector index
+ *   fastest (the interleaved layout of Sec. 3.1, Listing jacobi2d-r): element
+ *   (site, orbital nu, vector r) sits at complex offset ((site O + nu) R + r),
+ *   O = 4 (TI) or 1 (graphene site).  Complex numbers are (re, im) pairs:
+ *   16 bytes for PVSC_C128, 8 bytes for PVSC_C64.  D = O * n_sites.
+ * Precision.  PVSC_C128 stores and computes in fp64.  PVSC_C64 stores the
+ *   recurrence vectors as complex64 and computes the stencil in fp32, while
+ *   dot products, moments, the scaling (a, b), the Bessel coefficients and the
+ *   propagation accumulator stay fp64.  Vectors the caller passes as
+ *   "complex128" are complex128 in both precisions.
+ * R.  1, 2, 4, 8, 16, 32 or 64 vectors per block.
+ * Memory.  Every vector, work buffer and output pointer is a DEVICE pointer
+ *   owned by the caller, 16-byte aligned; the library owns only the lattice
+ *   handle (geometry, parameters and its copy of V).  Work buffers are sized
+ *   with pvsc_work_bytes.
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *   that launch kernels are asynchronous on that stream unless stated.
+ * Errors.  Every call returns PVSC_OK or a negative pvsc_status and leaves a
+ *   message for pvsc_last_error() (thread-local).  Invalid arguments are
+ *   reported before anything is launched; device-side waits are bounded and
+ *   report PVSC_ERR_TIMEOUT; nothing aborts the process or traps the device.
+ */
+#ifndef PVSC_H
+#define PVSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pvsc_lattice pvsc_lattice; /* opaque, library-owned */
+
+typedef enum {
+  PVSC_OK = 0,
+  PVSC_ERR_ARG = -1,         /* invalid argument (null, size, alignment, range) */
+  PVSC_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+  PVSC_ERR_OOM = -3,         /* a library-side allocation failed */
+  PVSC_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+  PVSC_ERR_UNSUPPORTED = -5  /* valid but not implemented combination */
+} pvsc_status;
+
+enum { PVSC_TI = 1, PVSC_GRAPHENE = 2 };
+enum { PVSC_C128 = 0, PVSC_C64 = 1 };
+
+/* Source of the on-site potential V (one fp64 value per site). */
+enum {
+  PVSC_V_ZERO = 0,       /* V = 0 */
+  PVSC_V_HOST = 1,       /* copied from desc.V, a host array of n_sites doubles */
+  PVSC_V_DEVICE = 2,     /* copied from desc.V, a device array of n_sites doubles */
+  PVSC_V_SEED = 3,       /* V_n = W (u_n - 1/2), u_n from the counter hash, stored */
+  PVSC_V_ON_THE_FLY = 4  /* same values, regenerated inside every stencil sweep */
+};
+
+/* Dot-product selection for pvsc_cheb_step. */
+enum { PVSC_DOT_XX = 1, PVSC_DOT_XY = 2, PVSC_DOT_YY = 4 };
+
+/* Operations for pvsc_work_bytes. */
+enum {
+  PVSC_OP_APPLY = 0,
+  PVSC_OP_CHEB_STEP = 1,
+  PVSC_OP_KPM = 2,
+  PVSC_OP_SERIES = 3,    /* pvsc_cheb_series, pvsc_cheb_filter, pvsc_cheb_propagate */
+  PVSC_OP_ADJOINT = 4,   /* pvsc_cheb_adjoint_step; M = number of series terms */
+  PVSC_OP_KPM_BATCHED = 5
+};
+
+/*
+ * Lattice description.  Defines H for one lattice: the model equation, the
+ * cuboid and its boundary conditions (Sec. 3.4: per-dimension periodic or
+ * open), the couplings and the on-site potential.  dims: TI (Lx, Ly, Lz)
+ * sites; graphene (Nx, Ny, 1) cells.  periodic[d] != 0 wraps axis d; an open
+ * axis drops the bonds that leave the cuboid.  Lengths 1 and 2 on a periodic
+ * axis make a site its own or its double neighbour; the terms then add.
+ * The counter hash is h = mix(mix(seed ^ (0 * 0x9E3779B97F4A7C15)) + n) with
+ * mix the SplitMix64 finaliser, u_n = (h >> 11) 2^-53; the paper draws the
+ * disorder from a box of width W (gamma), V_n in [-W/2, W/2) (Sec. 4.2).
+ */
+typedef struct {
+  int32_t model;        /* PVSC_TI or PVSC_GRAPHENE */
+  int32_t periodic[3];
+  int64_t dims[3];
+  double t;             /* transfer integral (the paper's unit of energy) */
+  double m;             /* TI mass parameter (ignored for graphene) */
+  double delta1;        /* TI Delta_1 Gamma^5: must be 0 (PVSC_ERR_UNSUPPORTED) */
+  double delta2;        /* TI Delta_2 Gamma^15: must be 0 (PVSC_ERR_UNSUPPORTED) */
+  int32_t v_source;     /* PVSC_V_* */
+  int32_t reserved;
+  const double* V;      /* for PVSC_V_HOST / PVSC_V_DEVICE, else ignored */
+  uint64_t seed;        /* for PVSC_V_SEED / PVSC_V_ON_THE_FLY */
+  double W;             /* disorder width for PVSC_V_SEED / PVSC_V_ON_THE_FLY */
+} pvsc_lattice_desc;
+
+/* Create a lattice handle.  Allocates the handle and its device copy of V,
+ * copies or generates V on `stream` and synchronises it.  *out is set only
+ * on success.  Errors: ARG (null, dims < 1, unknown model or v_source,
+ * t not finite), UNSUPPORTED (delta1/delta2 != 0), OOM, CUDA. */
+int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattice** out);
+
+/* Destroy a handle (NULL is accepted).  The caller must have synchronised
+ * every stream that still uses it. */
+int pvsc_lattice_destroy(pvsc_lattice* lat);
+
+/* Host query: number of sites and orbitals per site (4 TI, 1 graphene). */
+int pvsc_lattice_info(const pvsc_lattice* lat, int64_t* n_sites, int32_t* orbitals);
+
+/* Replace the stored on-site potential from a device array of n_sites
+ * doubles (for gradient loops over the gate potential).  Not allowed for
+ * PVSC_V_ON_THE_FLY lattices (ARG).  Asynchronous on stream. */
+int pvsc_set_potential(pvsc_lattice* lat, const double* V_dev, void* stream);
+
+/* Write the potential the stencil uses (stored or regenerated) to a device
+ * array of n_sites doubles.  Asynchronous on stream. */
+int pvsc_get_potential(const pvsc_lattice* lat, double* V_out_dev, void* stream);
+
+/* Exact Gershgorin interval over all rows of H (Sec. 4.1 needs the extreme
+ * eigenvalues; this bound contains them): emin = min_i (H_ii - sum_{j!=i}
+ * |H_ij|), emax = max_i (H_ii + sum_{j!=i}|H_ij|), evaluated on the device
+ * per row, coinciding neighbours combined first.  Then a = (emax - emin +
+ * eps)/2 and b = (emax + emin)/2, so that (H - b)/a has its spectrum inside
+ * [-1, 1].  Any output pointer may be NULL.  Synchronous (host results).
+ * `work` needs pvsc_work_bytes(lat, PVSC_OP_APPLY, 1, ...) bytes. */
+int pvsc_spectral_bounds(const pvsc_lattice* lat, double eps, double* emin, double* emax,
+                         double* a, double* b, void* work, size_t work_bytes, void* stream);
+
+/* y = H x for a block of R vectors in precision prec (x, y: D*R complex).
+ * x and y must not overlap.  No work buffer. */
+int pvsc_apply_H(const pvsc_lattice* lat, int R, int prec, const void* x, void* y, void* stream);
+
+/*
+ * Fused Chebyshev step, the generated-kernel contract of Listing graphenec
+ * (scale_h, shift_h, scale_z and the partial dot products xx, xy, yy):
+ *   per vector r:  y <- alpha_r (H - beta_r) x + gamma_r y
+ *   if z != NULL:  z <- z + delta_r y            (same precision as y)
+ *   dots (device, 4 x R doubles, written when dot_flags != 0):
+ *     dots[0 R + r] = <x|x>,   dots[1 R + r] = Re <y|x>,
+ *     dots[2 R + r] = Im <y|x>, dots[3 R + r] = <y|y>   (y the new y)
+ *   with <a|b> = sum_i conj(a_i) b_i accumulated in fp64 in a fixed order.
+ * alpha, beta, gamma, delta: HOST arrays of R doubles (delta only with z;
+ * gamma may be NULL for gamma = 0).  y is read (unless gamma is NULL) and
+ * written in place; x must not overlap y or z.  dot_flags is a mask of
+ * PVSC_DOT_*: unselected entries are left unspecified.
+ * work: device scratch of pvsc_work_bytes(lat, PVSC_OP_CHEB_STEP, R, prec, 0).
+ */
+int pvsc_cheb_step(const pvsc_lattice* lat, int R, int prec, const void* x, void* y, void* z,
+                   const double* alpha, const double* beta, const double* gamma,
+                   const double* delta, int dot_flags, double* dots, void* work,
+                   size_t work_bytes, void* stream);
+
+/*
+ * Kernel polynomial method moments (Sec. 2.2, Sec. 4): for each of the R
+ * start vectors r, mu_k = <r|T_k(H~)|r>, k = 0..M-1, H~ = (H - b)/a, through
+ * the recurrence w_0 = r, w_1 = H~ w_0, w_{k+1} = 2 H~ w_k - w_{k-1}, fused
+ * with the dot products of each step and the doubling identities
+ * mu_{2k} = 2<w_k|w_k> - mu_0, mu_{2k+1} = 2 Re<w_{k+1}|w_k> - mu_1
+ * (ceil(M/2) stencil sweeps).  r0: device block in precision prec, or NULL
+ * for random-phase vectors r_i = exp(2 pi i u)/sqrt(D) from the counter hash
+ * with stream 1 and idx = r D + i.  mu: device array [R][M] of doubles.
+ * M >= 1.  The step loop is captured once into a CUDA graph per argument set
+ * and replayed; the first call for a new argument set captures.
+ * work: pvsc_work_bytes(lat, PVSC_OP_KPM, R, prec, M).
+ */
+int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, uint64_t seed,
+                     int M, double a, double b, double* mu, void* work, size_t work_bytes,
+                     void* stream);
+
+/*
+ * Chebyshev series: y = phase * sum_{k=0}^{K-1} c_k T_k(H~) x, H~ = (H - b)/a,
+ * with the |w_k> from the three-term recurrence (Sec. 4.1) and the weighted
+ * sum accumulated in fp64.  x, y: device complex128 blocks (may be the same
+ * buffer).  coeffs: HOST array of K complex values (re, im pairs), used as
+ * given.  phase: HOST (re, im) or NULL for 1.  K >= 1.  The recurrence
+ * vectors are stored in precision prec.
+ * work: pvsc_work_bytes(lat, PVSC_OP_SERIES, R, prec, K).
+ */
+int pvsc_cheb_series(const pvsc_lattice* lat, int R, int prec, const void* x, void* y,
+                     const double* coeffs, int K, const double* phase, double a, double b,
+                     void* work, size_t work_bytes, void* stream);
+
+/*
+ * Chebyshev filter (the polynomial filter of ChebFD, Sec. 4.2):
+ * y = sum_{k=0}^{K-1} g_k T_k(H~) x with real HOST coefficients g (window and
+ * kernel factors already applied by the caller).  As pvsc_cheb_series.
+ */
+int pvsc_cheb_filter(const pvsc_lattice* lat, int R, int prec, const void* x, void* y,
+                     const double* g, int K, double a, double b, void* work,
+                     size_t work_bytes, void* stream);
+
+/*
+ * Chebyshev expansion coefficients of the time-evolution operator (Sec. 4.1,
+ * Eq. U_1): c_k(a dt) = (-i)^k J_k(a dt), J_k by Miller's backward
+ * recurrence normalised with J_0 + 2 sum J_2k = 1, truncated after the
+ * largest k with |J_k(a dt)| >= trunc.  Writes the series weights
+ * cw_0 = c_0, cw_k = 2 c_k (k >= 1) as (re, im) pairs to the HOST array
+ * coeffs (capacity max_terms) and the number of terms M+1 to *n_terms.
+ * Errors: ARG if max_terms is too small (*n_terms still set).  Host only.
+ */
+int pvsc_propagation_coeffs(double a_dt, double trunc, int max_terms, double* coeffs,
+                            int* n_terms);
+
+/*
+ * Chebyshev time propagation (Sec. 4.1, Eq. U_1): nsteps times
+ * psi <- e^{-i b dt} [c_0 w_0 + 2 sum_{k=1}^{M} c_k w_k],  w_k = T_k(H~) psi,
+ * with c_k from pvsc_propagation_coeffs(a dt, trunc).  psi: device complex128
+ * block (in/out).  Each time step is captured once into a CUDA graph and
+ * replayed.  work: pvsc_work_bytes(lat, PVSC_OP_SERIES, R, prec, M+1).
+ */
+int pvsc_cheb_propagate(const pvsc_lattice* lat, int R, int prec, void* psi, double dt,
+                        int nsteps, double a, double b, double trunc, void* work,
+                        size_t work_bytes, void* stream);
+
+/*
+ * One time step of the adjoint of pvsc_cheb_propagate with respect to the
+ * on-site potential (the paper has no adjoint; this is the reverse sweep of
+ * the recurrence of Eq. U_1 with a, b held fixed).  Given the state psi_s
+ * (device complex128, R vectors) and G = dL/dpsi_{s+1} in the convention
+ * dL = Re <G|dpsi_{s+1}>, it recomputes w_0..w_M from psi_s, runs
+ *   u_k = conj(cw_k) h + 2 H~ u_{k+1} - u_{k+2},  h = e^{+i b dt} G,
+ *   u_0 = conj(cw_0) h + H~ u_1 - u_2,
+ * adds (1/a) Re sum_k f_k sum_{orbitals, vectors} conj(u_{k+1}) w_k (f_0 = 1,
+ * f_k = 2) to dLdV[n] for every site n, and overwrites G with u_0 =
+ * dL/dpsi_s.  dLdV: device array of n_sites doubles (accumulated, not
+ * cleared).  prec must be PVSC_C128.
+ * work: pvsc_work_bytes(lat, PVSC_OP_ADJOINT, R, PVSC_C128, M+1).
+ */
+int pvsc_cheb_adjoint_step(const pvsc_lattice* lat, int R, int prec, const void* psi_s,
+                           void* G, double dt, double a, double b, double trunc,
+                           double* dLdV, void* work, size_t work_bytes, void* stream);
+
+/*
+ * Batched KPM: n independent TI lattices (uneven sizes allowed) x R
+ * random-phase vectors each, M moments, in one persistent cooperative launch
+ * that walks a device work list of (lattice, z-slab) units and advances each
+ * slab through the Chebyshev steps as soon as its neighbouring slabs of the
+ * same lattice have finished the previous step (bounded spin waits).
+ * a, b: HOST arrays of n doubles.  Start vectors: counter hash, stream 1,
+ * seed seeds[i] (HOST array of n).  mu: device [n][R][M] doubles.
+ * Returns PVSC_ERR_TIMEOUT if a wait exceeded pvsc_set_wait_limit (the
+ * kernel then stops cleanly; mu is undefined).
+ * work: pvsc_work_bytes(lats[0], PVSC_OP_KPM_BATCHED, R, prec, M) summed
+ * over the lattices plus 4096 bytes (use pvsc_batched_work_bytes).
+ */
+int pvsc_kpm_moments_batched(const pvsc_lattice* const* lats, int n, int R, int prec,
+                             const uint64_t* seeds, int M, const double* a, const double* b,
+                             double* mu, void* work, size_t work_bytes, void* stream);
+
+/* Work bytes for pvsc_kpm_moments_batched over the given lattices. */
+size_t pvsc_batched_work_bytes(const pvsc_lattice* const* lats, int n, int R, int prec, int M);
+
+/* Device scratch bytes an operation needs (0 if none); M is the moment count
+ * (KPM) or the number of series terms (series/adjoint).  0 on bad args. */
+size_t pvsc_work_bytes(const pvsc_lattice* lat, int op, int R, int prec, int M);
+
+/* Spin limit of every bounded device wait (persistent batched kernel); the
+ * default allows several seconds.  A wait that exceeds it sets an error
+ * word, the kernel returns, and the call reports PVSC_ERR_TIMEOUT. */
+int pvsc_set_wait_limit(uint64_t spins);
+
+/*
+ * Launch tuning.  A tuning entry fixes, for (lattice, op, R, prec), the
+ * threads per block, the blocks per SM of the persistent grid and the z-slab
+ * depth of the TI z-marching sweep (0 = automatic).  pvsc_autotune times the
+ * candidates on the device with CUDA events (synchronous; the vectors it
+ * sweeps are allocated inside and freed) and stores the winner in the
+ * handle; pvsc_get_tuning reads the entry in force.
+ */
+typedef struct {
+  int32_t threads;
+  int32_t blocks_per_sm;
+  int32_t zslab;
+  float time_ms; /* measured time of one sweep, 0 if not measured */
+} pvsc_tuning;
+int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tuning);
+int pvsc_get_tuning(const pvsc_lattice* lat, int R, int prec, pvsc_tuning* tuning);
+int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* best, void* stream);
+
+/* Neighbour table the stencil uses (debug/parity): for every site, 7 site
+ * indices (TI: self, -x, +x, -y, +y, -z, +z) or, for graphene, per cell
+ * (self, -x, +x, -y, +y) padded to 7 with -1, absent neighbours -1.
+ * Computed by a device kernel into nbr_dev (int64, n_sites*7 or n_cells*7). */
+int pvsc_debug_neighbours(const pvsc_lattice* lat, int64_t* nbr_dev, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* pvsc_last_error(void);
+
+/* Library version string. */
+const char* pvsc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PVSC_H */

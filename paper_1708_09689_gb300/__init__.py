@@ -1,0 +1,394 @@
+"""Python binding of libpvsc (matrix-free Chebyshev stencils for Dirac and
+topological materials on GB300).
+
+This module only marshals arguments: it turns torch CUDA tensors into device
+pointers, the current torch stream into a cudaStream_t and Python numbers into
+C values, and calls the C ABI declared in include/pvsc.h.  Every arithmetic
+step of the path runs in the library's CUDA kernels.  There is no CPU
+fallback: if libpvsc.so has not been built, importing the library raises.
+
+Vectors are torch tensors of shape (D, R) (or (D,) for R = 1) in the layout
+of the C ABI, D = orbitals * n_sites: complex128 selects PVSC_C128 and
+complex64 PVSC_C64.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import torch
+
+from .build import LIB_PATH
+
+PVSC_OK, PVSC_ERR_ARG, PVSC_ERR_CUDA, PVSC_ERR_OOM, PVSC_ERR_TIMEOUT, PVSC_ERR_UNSUPPORTED = \
+    0, -1, -2, -3, -4, -5
+TI, GRAPHENE = 1, 2
+C128, C64 = 0, 1
+V_ZERO, V_HOST, V_DEVICE, V_SEED, V_ON_THE_FLY = 0, 1, 2, 3, 4
+DOT_XX, DOT_XY, DOT_YY = 1, 2, 4
+OP_APPLY, OP_CHEB_STEP, OP_KPM, OP_SERIES, OP_ADJOINT, OP_KPM_BATCHED = 0, 1, 2, 3, 4, 5
+
+
+class PvscError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pvsc error {code}: {msg}")
+        self.code = code
+
+
+class LatticeDesc(ctypes.Structure):
+    _fields_ = [
+        ("model", ctypes.c_int32),
+        ("periodic", ctypes.c_int32 * 3),
+        ("dims", ctypes.c_int64 * 3),
+        ("t", ctypes.c_double),
+        ("m", ctypes.c_double),
+        ("delta1", ctypes.c_double),
+        ("delta2", ctypes.c_double),
+        ("v_source", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("V", ctypes.c_void_p),
+        ("seed", ctypes.c_uint64),
+        ("W", ctypes.c_double),
+    ]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("zslab", ctypes.c_int32), ("time_ms", ctypes.c_float)]
+
+
+_vp, _i, _sz, _d, _u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_double, ctypes.c_uint64
+_dp = ctypes.POINTER(ctypes.c_double)
+
+_SIGNATURES = {
+    "pvsc_lattice_create": (_i, [ctypes.POINTER(LatticeDesc), _vp, ctypes.POINTER(_vp)]),
+    "pvsc_lattice_destroy": (_i, [_vp]),
+    "pvsc_lattice_info": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
+    "pvsc_set_potential": (_i, [_vp, _vp, _vp]),
+    "pvsc_get_potential": (_i, [_vp, _vp, _vp]),
+    "pvsc_spectral_bounds": (_i, [_vp, _d, _dp, _dp, _dp, _dp, _vp, _sz, _vp]),
+    "pvsc_apply_H": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+    "pvsc_cheb_step": (_i, [_vp, _i, _i, _vp, _vp, _vp, _dp, _dp, _dp, _dp, _i, _vp, _vp, _sz, _vp]),
+    "pvsc_kpm_moments": (_i, [_vp, _i, _i, _vp, _u64, _i, _d, _d, _vp, _vp, _sz, _vp]),
+    "pvsc_cheb_series": (_i, [_vp, _i, _i, _vp, _vp, _dp, _i, _dp, _d, _d, _vp, _sz, _vp]),
+    "pvsc_cheb_filter": (_i, [_vp, _i, _i, _vp, _vp, _dp, _i, _d, _d, _vp, _sz, _vp]),
+    "pvsc_propagation_coeffs": (_i, [_d, _d, _i, _dp, ctypes.POINTER(ctypes.c_int)]),
+    "pvsc_cheb_propagate": (_i, [_vp, _i, _i, _vp, _d, _i, _d, _d, _d, _vp, _sz, _vp]),
+    "pvsc_cheb_adjoint_step": (_i, [_vp, _i, _i, _vp, _vp, _d, _d, _d, _d, _vp, _vp, _sz, _vp]),
+    "pvsc_kpm_moments_batched": (_i, [ctypes.POINTER(_vp), _i, _i, _i, ctypes.POINTER(_u64), _i,
+                                      _dp, _dp, _vp, _vp, _sz, _vp]),
+    "pvsc_batched_work_bytes": (_sz, [ctypes.POINTER(_vp), _i, _i, _i, _i]),
+    "pvsc_work_bytes": (_sz, [_vp, _i, _i, _i, _i]),
+    "pvsc_set_wait_limit": (_i, [_u64]),
+    "pvsc_set_tuning": (_i, [_vp, _i, _i, ctypes.POINTER(Tuning)]),
+    "pvsc_get_tuning": (_i, [_vp, _i, _i, ctypes.POINTER(Tuning)]),
+    "pvsc_autotune": (_i, [_vp, _i, _i, ctypes.POINTER(Tuning), _vp]),
+    "pvsc_debug_neighbours": (_i, [_vp, _vp, _vp]),
+    "pvsc_last_error": (ctypes.c_char_p, []),
+    "pvsc_version": (ctypes.c_char_p, []),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (or python -m "
+                          "paper_1708_09689_gb300.build) to compile the CUDA library")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(rc: int):
+    if rc != PVSC_OK:
+        raise PvscError(rc, _lib.pvsc_last_error().decode())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _darr(vals):
+    vals = [float(v) for v in vals]
+    return (ctypes.c_double * len(vals))(*vals)
+
+
+def prec_of(t: torch.Tensor) -> int:
+    if t.dtype == torch.complex128:
+        return C128
+    if t.dtype == torch.complex64:
+        return C64
+    raise ValueError(f"vectors must be complex128 or complex64, got {t.dtype}")
+
+
+def block_R(t: torch.Tensor) -> int:
+    return 1 if t.dim() == 1 else int(t.shape[1])
+
+
+def version() -> str:
+    return _lib.pvsc_version().decode()
+
+
+def work_buffer(nbytes: int, device=None) -> torch.Tensor:
+    """Caller-owned device scratch (16-byte aligned by the caching allocator)."""
+    return torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device or "cuda")
+
+
+# ---------------------------------------------------------------------------- lattice
+class Lattice:
+    """A TI (Eq. TB_H_topi) or graphene (Eq. graphene_model) lattice handle.
+
+    V: None (zero), a torch CUDA float64 tensor, or a numpy/CPU float64 array
+    (copied into the handle); or disorder=(W, seed) for box disorder from the
+    counter hash, stored (on_the_fly=False) or regenerated in every sweep.
+    """
+
+    def __init__(self, model: int, dims, periodic, t: float = 1.0, m: float = 0.0, V=None,
+                 disorder=None, on_the_fly: bool = False, stream=None):
+        d = LatticeDesc()
+        d.model = model
+        dims = list(dims) + [1] * (3 - len(dims))
+        per = list(periodic) + [0] * (3 - len(periodic))
+        for i in range(3):
+            d.dims[i] = int(dims[i])
+            d.periodic[i] = int(bool(per[i]))
+        d.t, d.m, d.delta1, d.delta2 = float(t), float(m), 0.0, 0.0
+        keep = None
+        if disorder is not None:
+            W, seed = disorder
+            d.v_source = V_ON_THE_FLY if on_the_fly else V_SEED
+            d.W, d.seed = float(W), int(seed)
+        elif V is None:
+            d.v_source = V_ZERO
+        elif isinstance(V, torch.Tensor) and V.is_cuda:
+            keep = V.to(torch.float64).contiguous()
+            d.v_source, d.V = V_DEVICE, keep.data_ptr()
+        else:
+            import numpy as np
+            keep = np.ascontiguousarray(np.asarray(V, dtype=np.float64))
+            d.v_source, d.V = V_HOST, keep.ctypes.data
+        h = ctypes.c_void_p()
+        _check(_lib.pvsc_lattice_create(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.model = model
+        self.dims = tuple(dims)
+        self.periodic = tuple(per)
+        self.t, self.m = float(t), float(m)
+        n = ctypes.c_int64()
+        o = ctypes.c_int32()
+        _check(_lib.pvsc_lattice_info(self._h, ctypes.byref(n), ctypes.byref(o)))
+        self.n_sites, self.orbitals = int(n.value), int(o.value)
+        self.D = self.n_sites * self.orbitals
+
+    @classmethod
+    def ti(cls, dims, periodic, t=1.0, m=2.0, **kw):
+        return cls(TI, dims, periodic, t=t, m=m, **kw)
+
+    @classmethod
+    def graphene(cls, cells, periodic, t=1.0, **kw):
+        return cls(GRAPHENE, list(cells) + [1], list(periodic) + [0], t=t, **kw)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pvsc_lattice_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def work_bytes(self, op: int, R: int, prec: int, M: int = 0) -> int:
+        return int(_lib.pvsc_work_bytes(self._h, op, R, prec, M))
+
+    def set_potential(self, V: torch.Tensor, stream=None):
+        V = V.to(torch.float64).contiguous()
+        _check(_lib.pvsc_set_potential(self._h, _ptr(V), _stream(stream)))
+
+    def potential(self, stream=None) -> torch.Tensor:
+        out = torch.empty(self.n_sites, dtype=torch.float64, device="cuda")
+        _check(_lib.pvsc_get_potential(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def spectral_bounds(self, eps: float = 0.01, stream=None):
+        """(emin, emax, a, b): exact Gershgorin interval and the Chebyshev scaling."""
+        w = work_buffer(self.work_bytes(OP_APPLY, 1, C128))
+        emin, emax, a, b = _d(), _d(), _d(), _d()
+        _check(_lib.pvsc_spectral_bounds(self._h, eps, ctypes.byref(emin), ctypes.byref(emax),
+                                         ctypes.byref(a), ctypes.byref(b), _ptr(w), w.numel(),
+                                         _stream(stream)))
+        return emin.value, emax.value, a.value, b.value
+
+    def neighbours(self, stream=None) -> torch.Tensor:
+        n = self.n_sites if self.model == TI else self.dims[0] * self.dims[1]
+        out = torch.empty((n, 7), dtype=torch.int64, device="cuda")
+        _check(_lib.pvsc_debug_neighbours(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def set_tuning(self, R: int, prec: int, threads: int = 256, blocks_per_sm: int = 0, zslab: int = 0):
+        t = Tuning(threads, blocks_per_sm, zslab, 0.0)
+        _check(_lib.pvsc_set_tuning(self._h, R, prec, ctypes.byref(t)))
+
+    def get_tuning(self, R: int, prec: int) -> dict:
+        t = Tuning()
+        _check(_lib.pvsc_get_tuning(self._h, R, prec, ctypes.byref(t)))
+        return {"threads": t.threads, "blocks_per_sm": t.blocks_per_sm, "zslab": t.zslab,
+                "time_ms": t.time_ms}
+
+    def autotune(self, R: int, prec: int, stream=None) -> dict:
+        t = Tuning()
+        _check(_lib.pvsc_autotune(self._h, R, prec, ctypes.byref(t), _stream(stream)))
+        return {"threads": t.threads, "blocks_per_sm": t.blocks_per_sm, "zslab": t.zslab,
+                "time_ms": t.time_ms}
+
+
+# ---------------------------------------------------------------------------- operations
+def apply_H(lat: Lattice, x: torch.Tensor, y: torch.Tensor | None = None, stream=None):
+    """y = H x."""
+    y = torch.empty_like(x) if y is None else y
+    _check(_lib.pvsc_apply_H(lat.handle, block_R(x), prec_of(x), _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def cheb_step(lat: Lattice, x, y, alpha, beta, gamma=None, z=None, delta=None, dots: int = 0,
+              work: torch.Tensor | None = None, stream=None):
+    """y <- alpha (H - beta) x + gamma y; z += delta y; returns the dots tensor [4, R] or None."""
+    R, prec = block_R(x), prec_of(x)
+    d = torch.zeros((4, R), dtype=torch.float64, device=x.device) if dots else None
+    if dots and work is None:
+        work = work_buffer(lat.work_bytes(OP_CHEB_STEP, R, prec))
+    _check(_lib.pvsc_cheb_step(
+        lat.handle, R, prec, _ptr(x), _ptr(y), _ptr(z), _darr(alpha), _darr(beta),
+        _darr(gamma) if gamma is not None else None, _darr(delta) if delta is not None else None,
+        int(dots), _ptr(d), _ptr(work), 0 if work is None else work.numel(), _stream(stream)))
+    return d
+
+
+def kpm_moments(lat: Lattice, M: int, a: float, b: float, R: int = 1, prec: int = C128,
+                r0: torch.Tensor | None = None, seed: int = 0, work=None, mu=None, stream=None):
+    """Per-vector KPM moments mu[r, k] = <r|T_k(H~)|r>, a float64 tensor (R, M)."""
+    if r0 is not None:
+        R, prec = block_R(r0), prec_of(r0)
+    mu = torch.empty((R, M), dtype=torch.float64, device="cuda") if mu is None else mu
+    if work is None:
+        work = work_buffer(lat.work_bytes(OP_KPM, R, prec, M))
+    _check(_lib.pvsc_kpm_moments(lat.handle, R, prec, _ptr(r0), int(seed), int(M), float(a),
+                                 float(b), _ptr(mu), _ptr(work), work.numel(), _stream(stream)))
+    return mu
+
+
+def _cplx_arr(coeffs):
+    flat = []
+    for c in coeffs:
+        c = complex(c)
+        flat += [c.real, c.imag]
+    return _darr(flat)
+
+
+def cheb_series(lat: Lattice, x, coeffs, a, b, phase=None, y=None, prec: int = C128, work=None,
+                stream=None):
+    """y = phase sum_k coeffs_k T_k(H~) x (x, y complex128)."""
+    R = block_R(x)
+    y = torch.empty_like(x) if y is None else y
+    K = len(coeffs)
+    if work is None:
+        work = work_buffer(lat.work_bytes(OP_SERIES, R, prec, K))
+    ph = None if phase is None else _darr([complex(phase).real, complex(phase).imag])
+    _check(_lib.pvsc_cheb_series(lat.handle, R, prec, _ptr(x), _ptr(y), _cplx_arr(coeffs), K, ph,
+                                 float(a), float(b), _ptr(work), work.numel(), _stream(stream)))
+    return y
+
+
+def cheb_filter(lat: Lattice, x, g, a, b, y=None, prec: int = C128, work=None, stream=None):
+    """y = sum_k g_k T_k(H~) x with real g (x, y complex128)."""
+    R = block_R(x)
+    y = torch.empty_like(x) if y is None else y
+    if work is None:
+        work = work_buffer(lat.work_bytes(OP_SERIES, R, prec, len(g)))
+    _check(_lib.pvsc_cheb_filter(lat.handle, R, prec, _ptr(x), _ptr(y), _darr(g), len(g), float(a),
+                                 float(b), _ptr(work), work.numel(), _stream(stream)))
+    return y
+
+
+def propagation_coeffs(a_dt: float, trunc: float = 1e-14):
+    """Series weights cw_0 = J_0, cw_k = 2 (-i)^k J_k(a dt) of Eq. U_1 (list of complex)."""
+    n = ctypes.c_int()
+    buf = (ctypes.c_double * 512)()
+    _check(_lib.pvsc_propagation_coeffs(float(a_dt), float(trunc), 256, buf, ctypes.byref(n)))
+    return [complex(buf[2 * k], buf[2 * k + 1]) for k in range(n.value)]
+
+
+def cheb_propagate(lat: Lattice, psi, dt, nsteps, a, b, trunc=1e-14, prec: int = C128, work=None,
+                   stream=None):
+    """psi <- U(dt)^nsteps psi in place (psi complex128)."""
+    R = block_R(psi)
+    if work is None:
+        K = len(propagation_coeffs(a * dt, trunc))
+        work = work_buffer(lat.work_bytes(OP_SERIES, R, prec, K))
+    _check(_lib.pvsc_cheb_propagate(lat.handle, R, prec, _ptr(psi), float(dt), int(nsteps), float(a),
+                                    float(b), float(trunc), _ptr(work), work.numel(), _stream(stream)))
+    return psi
+
+
+def cheb_adjoint_step(lat: Lattice, psi_s, G, dt, a, b, dLdV, trunc=1e-14, work=None, stream=None):
+    """G <- dL/dpsi_s and dLdV += the potential gradient of one propagation step."""
+    if work is None:
+        K = len(propagation_coeffs(a * dt, trunc))
+        work = work_buffer(lat.work_bytes(OP_ADJOINT, 1, C128, K))
+    _check(_lib.pvsc_cheb_adjoint_step(lat.handle, block_R(psi_s), C128, _ptr(psi_s), _ptr(G), float(dt),
+                                       float(a), float(b), float(trunc), _ptr(dLdV), _ptr(work),
+                                       work.numel(), _stream(stream)))
+    return G
+
+
+def kpm_moments_batched(lats, M, a, b, R=16, prec=C64, seeds=None, work=None, mu=None, stream=None):
+    """Batched KPM over several TI lattices in one persistent launch: mu (n, R, M)."""
+    n = len(lats)
+    hs = (ctypes.c_void_p * n)(*[l.handle.value for l in lats])
+    seeds = list(seeds) if seeds is not None else list(range(n))
+    sarr = (ctypes.c_uint64 * n)(*[int(s) for s in seeds])
+    mu = torch.empty((n, R, M), dtype=torch.float64, device="cuda") if mu is None else mu
+    if work is None:
+        work = work_buffer(int(_lib.pvsc_batched_work_bytes(hs, n, R, prec, M)))
+    _check(_lib.pvsc_kpm_moments_batched(hs, n, R, prec, sarr, int(M), _darr(a), _darr(b), _ptr(mu),
+                                         _ptr(work), work.numel(), _stream(stream)))
+    return mu
+
+
+def set_wait_limit(spins: int):
+    _check(_lib.pvsc_set_wait_limit(int(spins)))
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+from .autograd import ChebPropagate, propagate_with_grad  # noqa: E402,F401

@@ -1,0 +1,186 @@
+// Shared device/host definitions of the matrix-free Chebyshev stencil library.
+//
+// Everything here is written for sm_103a (GB300): 32-wide warps, 16-byte
+// vector loads, warp shuffles and a fixed-order block reduction.  The two
+// stencils are the topological-insulator Hamiltonian of Eq. TB_H_topi and the
+// graphene Hamiltonian of Eq. graphene_model (Sec. 2 of Pieper, Hager and
+// Fehske, arXiv 1708.09689).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pvsc {
+
+constexpr int kMaxR = 64;
+constexpr int kNumDots = 4;  // <x|x>, Re<y|x>, Im<y|x>, <y|y>
+
+// ---------------------------------------------------------------- geometry
+struct Geometry {
+  int model;            // 1 TI, 2 graphene
+  int per[3];           // periodic flags
+  int64_t L[3];         // TI: Lx, Ly, Lz sites; graphene: Nx, Ny cells, 1
+  int64_t n_sites;      // TI: Lx Ly Lz; graphene: 4 Nx Ny
+  double t, m;          // hopping, TI mass
+  const double* V;      // device [n_sites] when v_mode == 1
+  int v_mode;           // 0 zero, 1 stored, 2 regenerated from the hash
+  uint64_t vkey;        // mix(seed ^ stream*gamma) for stream 0
+  double W;             // disorder width for v_mode 2
+};
+
+// Neighbour index along one axis: idx -/+ stride, wrapped on a periodic axis,
+// -1 where an open axis ends.  A periodic axis of length 1 returns idx itself
+// (the site is its own neighbour and both bond terms act on it).
+__host__ __device__ __forceinline__ int64_t nbr_minus(int64_t idx, int64_t coord, int64_t L,
+                                                      int per, int64_t stride) {
+  return coord > 0 ? idx - stride : (per ? idx + (L - 1) * stride : -1);
+}
+__host__ __device__ __forceinline__ int64_t nbr_plus(int64_t idx, int64_t coord, int64_t L,
+                                                     int per, int64_t stride) {
+  return coord < L - 1 ? idx + stride : (per ? idx - (L - 1) * stride : -1);
+}
+
+// SplitMix64 output finaliser (Steele, Lea & Flood 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+constexpr uint64_t kGoldenGamma = 0x9E3779B97F4A7C15ull;
+__host__ __device__ __forceinline__ uint64_t hash_key(uint64_t seed, uint64_t stream) {
+  return mix64(seed ^ (stream * kGoldenGamma));
+}
+// Uniform double in [0, 1) from the top 53 bits: exact conversion.
+__host__ __device__ __forceinline__ double hash_uniform(uint64_t key, uint64_t idx) {
+  return (double)(mix64(key + idx) >> 11) * 0x1.0p-53;
+}
+
+__device__ __forceinline__ double site_potential(const Geometry& g, int64_t site) {
+  if (g.v_mode == 1) return __ldg(g.V + site);
+  if (g.v_mode == 2) return g.W * (hash_uniform(g.vkey, (uint64_t)site) - 0.5);
+  return 0.0;
+}
+
+// ---------------------------------------------------------------- complex
+template <typename T> struct CT;
+template <> struct CT<double> { using c = double2; using v = double2; };  // one complex per 16 B
+template <> struct CT<float>  { using c = float2;  using v = float4;  };  // two complex per 16 B
+
+template <typename T> struct cplx { T re, im; };
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return {a.re - b.re, a.im - b.im}; }
+
+// ---------------------------------------------------------------- sweep arguments
+// One fused stencil sweep (see the sweep kernels):
+//   y_new = alpha_r (H - beta_r) x + gamma_r y_in + sigma * src           (per vector r)
+//   z    += delta_r y_new
+//   acc   : init acc = cx x + cy y_new | add acc += cy y_new | final out = ph (acc + cy y_new)
+//   grad[site] += gscale Re sum_{orbitals} conj(y_new) wg
+//   dots  : <x|x>, Re/Im <y_new|x>, <y_new|y_new> per vector, fp64, fixed order
+struct Sweep {
+  Geometry g;
+  int R;
+  int C;                 // R / VPT vector chunks per site
+  const void* x;
+  const void* yin;       // may be null (gamma = 0)
+  void* yout;            // may be null (final series step)
+  void* z;               // may be null
+  double coef[4][kMaxR]; // alpha, beta, gamma, delta per vector
+  // series accumulation (complex128 accumulator)
+  int acc_mode;          // AccMode bits: start from cx x (INIT) or acc (ADD); FINAL writes ph (.) to acc_out
+  double2* acc;
+  double2* acc_out;      // final: written here
+  double cx_re, cx_im, cy_re, cy_im, ph_re, ph_im;
+  // adjoint source and gradient
+  const double2* src;    // y_new += sigma * src (complex128)
+  double sg_re, sg_im;
+  const void* wg;        // grad partner vector (same precision as x)
+  double* grad;          // [n_sites] fp64
+  double gscale;
+  // dot products
+  int dot_flags;         // bit0 xx, bit1 xy, bit2 yy
+  int dot_mode;          // 0 write dots[4][R]; 1 KPM first step; 2 KPM step k
+  double* partials;      // [gridDim][4][R]
+  unsigned* counter;     // zero before the first sweep; reset by the last block
+  double* dots;          // [4][R]
+  double* mu;            // [R][M]
+  int M;
+  int kpm_k;
+  int zslab;             // TI z-marching depth
+};
+
+enum AccMode { ACC_NONE = 0, ACC_INIT = 1, ACC_ADD = 2, ACC_FINAL = 4 };
+
+// ---------------------------------------------------------------- deterministic dot reduction
+// acc[d][v]: per-thread fp64 partial sums of dot d for vector rc*VPT+v.  Every
+// block reduces them in a fixed order (warp xor tree, then warps in index
+// order) to one value per (d, r), writes its row of `partials`, and the last
+// block to arrive sums the rows in block order and writes the outputs.  The
+// result is bitwise reproducible for a given launch configuration.
+constexpr int kMaxThreads = 256;
+template <int VPT>
+__device__ void reduce_dots(const Sweep& p, double (&acc)[kNumDots][VPT]) {
+  __shared__ double sm[kMaxThreads / 32][kNumDots][VPT][32];  // [warp][dot][v][lane]
+  __shared__ int s_last;
+  const int C = p.C;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int d = 0; d < kNumDots; ++d)
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      double s = acc[d][v];
+      for (int off = 16; off >= C; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if (lane < C) sm[warp][d][v][lane] = s;
+    }
+  __syncthreads();
+  double* row = p.partials + (size_t)blockIdx.x * kNumDots * p.R;
+  for (int t = threadIdx.x; t < C; t += blockDim.x) {
+    const int stride = C < 32 ? 1 : C / 32;  // warps that carry chunk t
+    const int w0 = C < 32 ? 0 : t / 32;
+    const int l = C < 32 ? t : t % 32;
+    for (int d = 0; d < kNumDots; ++d)
+      for (int v = 0; v < VPT; ++v) {
+        double s = 0.0;
+        for (int w = w0; w < nwarps; w += stride) s += sm[w][d][v][l];
+        row[d * p.R + t * VPT + v] = s;
+      }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(p.counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nb = gridDim.x;
+  for (int q = warp; q < kNumDots * p.R; q += nwarps) {
+    const int d = q / p.R, r = q % p.R;
+    if (!((p.dot_flags >> (d == 0 ? 0 : (d == 3 ? 2 : 1))) & 1)) continue;
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += __ldcg(p.partials + (size_t)b * kNumDots * p.R + q);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+      if (p.dot_mode == 0) {
+        p.dots[q] = s;
+      } else if (p.dot_mode == 1) {  // KPM step 0: mu_0 = <w0|w0>, mu_1 = Re<w1|w0>
+        if (d == 0) p.mu[(size_t)r * p.M + 0] = s;
+        if (d == 1 && p.M > 1) p.mu[(size_t)r * p.M + 1] = s;
+      } else {  // KPM step k: mu_2k = 2<wk|wk> - mu_0, mu_2k+1 = 2 Re<wk+1|wk> - mu_1
+        const int k = p.kpm_k;
+        if (d == 0 && 2 * k < p.M) p.mu[(size_t)r * p.M + 2 * k] = 2.0 * s - __ldcg(p.mu + (size_t)r * p.M);
+        if (d == 1 && 2 * k + 1 < p.M)
+          p.mu[(size_t)r * p.M + 2 * k + 1] = 2.0 * s - __ldcg(p.mu + (size_t)r * p.M + 1);
+      }
+    }
+  }
+  if (threadIdx.x == 0) *p.counter = 0u;
+}
+
+}  // namespace pvsc

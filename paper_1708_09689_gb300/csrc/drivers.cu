@@ -1,0 +1,622 @@
+// Host drivers of the C ABI: sweep launch shapes, the fused Chebyshev step,
+// KPM moments, Chebyshev series / filter / time propagation, the adjoint step
+// and the CUDA-graph cache that replays captured recurrence loops.
+#include <cmath>
+#include <complex>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "sweep.cuh"
+
+namespace pvsc {
+
+using cd = std::complex<double>;
+
+// ---------------------------------------------------------------- launch shapes
+static LaunchShape shape_for(const pvsc_lattice* lat, int R, int prec) {
+  LaunchShape sh;
+  auto it = lat->tuning.find({R, prec});
+  if (it != lat->tuning.end()) {
+    sh.threads = it->second.threads;
+    sh.blocks_per_sm = it->second.blocks_per_sm;
+    sh.zslab = it->second.zslab;
+  }
+  return sh;
+}
+
+void sweep_init(Sweep& p, const pvsc_lattice* lat, int R, int prec) {
+  std::memset(&p, 0, sizeof(Sweep));
+  p.g = lat->g;
+  p.R = R;
+  p.C = R / vpt_for(R, prec);
+  for (int r = 0; r < R; ++r) p.coef[0][r] = 1.0;
+  p.cx_re = 0; p.ph_re = 1.0;
+}
+
+int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStream_t st) {
+  const int vpt = vpt_for(p.R, prec);
+  p.C = p.R / vpt;
+  const LaunchShape sh = shape_for(lat, p.R, prec);
+  int threads = sh.threads;
+  if (threads < 32 || threads > kMaxThreads || threads % 32 != 0 || threads % p.C != 0) threads = 256;
+  int occ = 0;
+  const int model = lat->g.model;
+  int rc = prec == PVSC_C128 ? occupancy_c128(model, feat, threads, &occ)
+                             : occupancy_c64(model, vpt, feat, threads, &occ);
+  if (rc) return rc;
+  int bps = sh.blocks_per_sm;
+  if (bps <= 0 || bps > occ) bps = occ;
+  if (bps < 1) bps = 1;
+  if (bps > kMaxGridPerSM) bps = kMaxGridPerSM;
+  const int64_t grid_max = (int64_t)lat->sm_count * bps;
+  int64_t units;
+  if (model == PVSC_TI) {
+    const int64_t plane = lat->g.L[0] * lat->g.L[1], Lz = lat->g.L[2];
+    const int64_t nbx = (plane * p.C + threads - 1) / threads;
+    int64_t zs = sh.zslab;
+    if (zs <= 0) {
+      int64_t nz = (6 * grid_max + nbx - 1) / nbx;
+      if (nz < 1) nz = 1;
+      if (nz > Lz) nz = Lz;
+      zs = (Lz + nz - 1) / nz;
+    }
+    if (zs > Lz) zs = Lz;
+    p.zslab = (int)zs;
+    units = nbx * ((Lz + zs - 1) / zs);
+  } else {
+    const int64_t ncell = lat->g.L[0] * lat->g.L[1];
+    units = (ncell * p.C + threads - 1) / threads;
+  }
+  const int grid = (int)(units < grid_max ? units : grid_max);
+  return prec == PVSC_C128 ? launch_sweep_c128(model, feat, grid, threads, p, st)
+                           : launch_sweep_c64(model, vpt, feat, grid, threads, p, st);
+}
+
+// ---------------------------------------------------------------- CUDA graph cache
+static bool graphs_enabled() {
+  const char* e = std::getenv("PVSC_NO_GRAPH");
+  return !(e && e[0] && e[0] != '0');
+}
+
+template <class F>
+static int run_graph(const pvsc_lattice* clat, const std::vector<uint64_t>& key, cudaStream_t st,
+                     F&& body) {
+  if (!graphs_enabled()) return body(st);
+  pvsc_lattice* lat = const_cast<pvsc_lattice*>(clat);
+  std::lock_guard<std::mutex> lk(lat->mu);
+  auto it = lat->graphs.find(key);
+  if (it == lat->graphs.end()) {
+    if (lat->graphs.size() >= 32) {
+      for (auto& kv : lat->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaGraphDestroy(kv.second.graph);
+      }
+      lat->graphs.clear();
+    }
+    cudaStream_t cs;
+    PVSC_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cs);
+      return set_error(PVSC_ERR_CUDA, "graph capture failed to start: %s", cudaGetErrorString(e));
+    }
+    const int rc = body(cs);
+    Graph gr;
+    e = cudaStreamEndCapture(cs, &gr.graph);
+    cudaStreamDestroy(cs);
+    if (rc != PVSC_OK) {
+      if (gr.graph) cudaGraphDestroy(gr.graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return set_error(PVSC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&gr.exec, gr.graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(gr.graph);
+      return set_error(PVSC_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    it = lat->graphs.emplace(key, gr).first;
+  }
+  PVSC_CUDA_TRY(cudaGraphLaunch(it->second.exec, st));
+  return PVSC_OK;
+}
+
+static uint64_t bits(double d) {
+  uint64_t u;
+  std::memcpy(&u, &d, 8);
+  return u;
+}
+static uint64_t bits(const void* p) { return (uint64_t)reinterpret_cast<uintptr_t>(p); }
+
+// ---------------------------------------------------------------- argument checks
+static int check_common(const pvsc_lattice* lat, int R, int prec) {
+  if (int rc = check_lattice(lat)) return rc;
+  if (!valid_R(R)) return set_error(PVSC_ERR_ARG, "R = %d: must be 1, 2, 4, 8, 16, 32 or 64", R);
+  if (prec != PVSC_C128 && prec != PVSC_C64) return set_error(PVSC_ERR_ARG, "unknown precision %d", prec);
+  return PVSC_OK;
+}
+
+static int check_scaling(double a, double b) {
+  if (!(std::isfinite(a) && a > 0.0) || !std::isfinite(b))
+    return set_error(PVSC_ERR_ARG, "scaling needs a > 0 and finite b (a = %g, b = %g)", a, b);
+  return PVSC_OK;
+}
+
+static int check_work(void* work, size_t have, size_t need) {
+  if (need == 0) return PVSC_OK;
+  if (int rc = check_ptr(work, "work")) return rc;
+  if (have < need) return set_error(PVSC_ERR_ARG, "work buffer too small: %zu < %zu bytes", have, need);
+  return PVSC_OK;
+}
+
+static char* wptr(void* work, size_t off) { return static_cast<char*>(work) + off; }
+
+// ---------------------------------------------------------------- Bessel coefficients
+// J_0..J_n(x) by Miller's backward recurrence J_{k-1} = (2k/x) J_k - J_{k+1},
+// started far above max(n, x) and normalised with J_0 + 2 sum_k J_2k = 1
+// (Abramowitz & Stegun 9.12, Numerical Recipes 6.5).
+static std::vector<double> bessel_miller(double x, int n) {
+  std::vector<double> out(n + 1, 0.0);
+  if (x == 0.0) {
+    out[0] = 1.0;
+    return out;
+  }
+  const double big = std::fmax((double)n, std::fabs(x));
+  int start = (int)(big + 40.0 + 2.0 * std::sqrt(40.0 * big));
+  if (start % 2) ++start;
+  std::vector<double> j(start + 2, 0.0);
+  j[start] = 1e-300;
+  for (int k = start; k >= 1; --k) {
+    j[k - 1] = (2.0 * k / x) * j[k] - j[k + 1];
+    if (std::fabs(j[k - 1]) > 1e250)
+      for (int q = k - 1; q <= start; ++q) j[q] *= 1e-250;
+  }
+  double norm = j[0];
+  for (int k = 2; k <= start; k += 2) norm += 2.0 * j[k];
+  for (int k = 0; k <= n; ++k) out[k] = j[k] / norm;
+  return out;
+}
+
+static int propagation_weights(double adt, double trunc, std::vector<cd>& cw) {
+  if (!std::isfinite(adt) || !(trunc > 0.0))
+    return set_error(PVSC_ERR_ARG, "need finite a*dt and trunc > 0");
+  const int kmax = (int)(2.0 * std::fabs(adt) + 60.0);
+  std::vector<double> J = bessel_miller(adt, kmax);
+  int M = 0;
+  for (int k = 0; k <= kmax; ++k)
+    if (std::fabs(J[k]) >= trunc) M = k;
+  cw.assign(M + 1, cd(0, 0));
+  static const cd mi[4] = {cd(1, 0), cd(0, -1), cd(-1, 0), cd(0, 1)};  // (-i)^k
+  for (int k = 0; k <= M; ++k) cw[k] = (k == 0 ? 1.0 : 2.0) * mi[k % 4] * J[k];
+  return PVSC_OK;
+}
+
+// ---------------------------------------------------------------- Chebyshev series
+// y = phase * sum_k cw_k T_k(H~) x with the recurrence vectors in `prec`.
+struct SeriesLayout {
+  size_t hdr, wa, wb, acc, total;
+};
+static SeriesLayout series_layout(const pvsc_lattice* lat, int R, int prec) {
+  SeriesLayout L;
+  L.hdr = 0;
+  L.wa = kWorkHeader;
+  L.wb = L.wa + vec_bytes(lat, R, prec);
+  L.acc = L.wb + vec_bytes(lat, R, prec);
+  L.total = L.acc + vec_bytes(lat, R, PVSC_C128);
+  return L;
+}
+
+static int run_series(const pvsc_lattice* lat, int R, int prec, const void* x, void* y,
+                      const std::vector<cd>& cw, cd phase, double a, double b, void* work,
+                      cudaStream_t st) {
+  const SeriesLayout L = series_layout(lat, R, prec);
+  const int64_t n = lat->g.n_sites * (lat->g.model == PVSC_TI ? 4 : 1) * (int64_t)R;
+  void* wa = wptr(work, L.wa);
+  void* wb = wptr(work, L.wb);
+  double2* acc = reinterpret_cast<double2*>(wptr(work, L.acc));
+  const int K = (int)cw.size();
+  if (K == 1) {  // y = phase c_0 x (elementwise, safe when x and y alias)
+    const cd c = phase * cw[0];
+    return launch_scale_init(x, static_cast<double2*>(y), c.real(), c.imag(), n, st);
+  }
+  Sweep p;
+  sweep_init(p, lat, R, prec);
+  auto set_scal = [&](double alpha, double gamma) {
+    for (int r = 0; r < R; ++r) {
+      p.coef[0][r] = alpha;
+      p.coef[1][r] = b;
+      p.coef[2][r] = gamma;
+      p.coef[3][r] = 0.0;
+    }
+  };
+  const void* prev;  // w_{k-2}
+  void* cur;         // w_{k-1}
+  // k = 1
+  if (prec == PVSC_C128) {
+    set_scal(1.0 / a, 0.0);
+    p.x = x;
+    p.yin = nullptr;
+    p.yout = wa;
+    p.acc = acc;
+    p.acc_mode = ACC_INIT;
+    p.cx_re = cw[0].real(); p.cx_im = cw[0].imag();
+    p.cy_re = cw[1].real(); p.cy_im = cw[1].imag();
+    if (int rc = launch_sweep(lat, prec, F_ACC, p, st)) return rc;
+    prev = x;
+    cur = wa;
+    if (K == 2) return launch_scale_init(acc, static_cast<double2*>(y), phase.real(), phase.imag(), n, st);
+  } else {
+    if (int rc = launch_convert_c128_to_c64(x, wb, n, st)) return rc;
+    if (int rc = launch_scale_init(x, acc, cw[0].real(), cw[0].imag(), n, st)) return rc;
+    set_scal(1.0 / a, 0.0);
+    p.x = wb;
+    p.yin = nullptr;
+    p.yout = (K == 2) ? nullptr : wa;
+    p.acc = acc;
+    p.acc_out = static_cast<double2*>(y);
+    p.acc_mode = ACC_ADD | (K == 2 ? ACC_FINAL : 0);
+    p.cy_re = cw[1].real(); p.cy_im = cw[1].imag();
+    p.ph_re = phase.real(); p.ph_im = phase.imag();
+    if (int rc = launch_sweep(lat, prec, F_ACC, p, st)) return rc;
+    if (K == 2) return PVSC_OK;
+    prev = wb;
+    cur = wa;
+  }
+  for (int k = 2; k < K; ++k) {
+    const bool last = (k == K - 1);
+    void* out = (prev == x) ? wb : const_cast<void*>(prev);
+    set_scal(2.0 / a, -1.0);
+    p.x = cur;
+    p.yin = prev;
+    p.yout = last ? nullptr : out;
+    p.acc = acc;
+    p.acc_out = static_cast<double2*>(y);
+    p.acc_mode = ACC_ADD | (last ? ACC_FINAL : 0);
+    p.cy_re = cw[k].real(); p.cy_im = cw[k].imag();
+    p.ph_re = phase.real(); p.ph_im = phase.imag();
+    if (int rc = launch_sweep(lat, prec, F_ACC, p, st)) return rc;
+    prev = cur;
+    cur = out;
+  }
+  return PVSC_OK;
+}
+
+}  // namespace pvsc
+
+using namespace pvsc;
+
+extern "C" {
+
+size_t pvsc_work_bytes(const pvsc_lattice* lat, int op, int R, int prec, int M) {
+  if (!lat || !valid_R(R) || (prec != PVSC_C128 && prec != PVSC_C64)) return 0;
+  switch (op) {
+    case PVSC_OP_APPLY:
+      return kWorkHeader + sizeof(double) * 2 * 2 * (size_t)lat->sm_count;
+    case PVSC_OP_CHEB_STEP:
+      return dots_work_bytes(lat, R);
+    case PVSC_OP_KPM:
+      return ((dots_work_bytes(lat, R) + 255) & ~size_t(255)) + 2 * vec_bytes(lat, R, prec);
+    case PVSC_OP_SERIES:
+      return series_layout(lat, R, prec).total;
+    case PVSC_OP_ADJOINT: {
+      const int nvec = (M < 1 ? 1 : M) + 2;
+      return kWorkHeader + (size_t)nvec * vec_bytes(lat, R, PVSC_C128);
+    }
+    default:
+      return 0;
+  }
+}
+
+int pvsc_apply_H(const pvsc_lattice* lat, int R, int prec, const void* x, void* y, void* stream) {
+  if (int rc = check_common(lat, R, prec)) return rc;
+  if (int rc = check_ptr(x, "x")) return rc;
+  if (int rc = check_ptr(y, "y")) return rc;
+  if (x == y) return set_error(PVSC_ERR_ARG, "x and y must not overlap");
+  Sweep p;
+  sweep_init(p, lat, R, prec);
+  p.x = x;
+  p.yout = y;
+  return launch_sweep(lat, prec, 0, p, static_cast<cudaStream_t>(stream));
+}
+
+int pvsc_cheb_step(const pvsc_lattice* lat, int R, int prec, const void* x, void* y, void* z,
+                   const double* alpha, const double* beta, const double* gamma,
+                   const double* delta, int dot_flags, double* dots, void* work,
+                   size_t work_bytes, void* stream) {
+  if (int rc = check_common(lat, R, prec)) return rc;
+  if (int rc = check_ptr(x, "x")) return rc;
+  if (int rc = check_ptr(y, "y")) return rc;
+  if (!alpha || !beta) return set_error(PVSC_ERR_ARG, "alpha and beta must not be NULL");
+  if (x == y || x == z) return set_error(PVSC_ERR_ARG, "x must not overlap y or z");
+  if (z) {
+    if (int rc = check_ptr(z, "z")) return rc;
+    if (!delta) return set_error(PVSC_ERR_ARG, "z needs delta");
+    if (z == y) return set_error(PVSC_ERR_ARG, "z must not overlap y");
+  }
+  if (dot_flags & ~7) return set_error(PVSC_ERR_ARG, "unknown dot flags 0x%x", dot_flags);
+  if (dot_flags && !dots) return set_error(PVSC_ERR_ARG, "dot_flags set but dots is NULL");
+  for (int r = 0; r < R; ++r)
+    if (!std::isfinite(alpha[r]) || !std::isfinite(beta[r]) || (gamma && !std::isfinite(gamma[r])) ||
+        (z && !std::isfinite(delta[r])))
+      return set_error(PVSC_ERR_ARG, "coefficients of vector %d are not finite", r);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Sweep p;
+  sweep_init(p, lat, R, prec);
+  for (int r = 0; r < R; ++r) {
+    p.coef[0][r] = alpha[r];
+    p.coef[1][r] = beta[r];
+    p.coef[2][r] = gamma ? gamma[r] : 0.0;
+    p.coef[3][r] = z ? delta[r] : 0.0;
+  }
+  p.x = x;
+  p.yin = gamma ? y : nullptr;
+  p.yout = y;
+  p.z = z;
+  int feat = z ? F_Z : 0;
+  if (dot_flags) {
+    if (int rc = check_work(work, work_bytes, dots_work_bytes(lat, R))) return rc;
+    feat |= F_DOTS;
+    p.dot_flags = dot_flags;
+    p.dot_mode = 0;
+    p.dots = dots;
+    p.counter = reinterpret_cast<unsigned*>(work);
+    p.partials = reinterpret_cast<double*>(wptr(work, kWorkHeader));
+    PVSC_CUDA_TRY(cudaMemsetAsync(work, 0, kWorkHeader, st));
+  }
+  return launch_sweep(lat, prec, feat, p, st);
+}
+
+int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, uint64_t seed,
+                     int M, double a, double b, double* mu, void* work, size_t work_bytes,
+                     void* stream) {
+  if (int rc = check_common(lat, R, prec)) return rc;
+  if (int rc = check_scaling(a, b)) return rc;
+  if (M < 1) return set_error(PVSC_ERR_ARG, "M = %d < 1", M);
+  if (!mu) return set_error(PVSC_ERR_ARG, "mu is NULL");
+  if (r0)
+    if (int rc = check_ptr(r0, "r0")) return rc;
+  const size_t need = pvsc_work_bytes(lat, PVSC_OP_KPM, R, prec, M);
+  if (int rc = check_work(work, work_bytes, need)) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t voff = (dots_work_bytes(lat, R) + 255) & ~size_t(255);
+  void* wa = wptr(work, voff);
+  void* wb = wptr(work, voff + vec_bytes(lat, R, prec));
+  const int64_t D = lat->g.n_sites * (lat->g.model == PVSC_TI ? 4 : 1);
+  const std::vector<uint64_t> key = {1, (uint64_t)R, (uint64_t)prec, bits(r0), seed, (uint64_t)M,
+                                     bits(a), bits(b), bits(mu), bits(work)};
+  auto body = [&](cudaStream_t cs) -> int {
+    PVSC_CUDA_TRY(cudaMemsetAsync(work, 0, kWorkHeader, cs));
+    const void* x0 = r0;
+    if (!r0) {
+      if (int rc = launch_random_phase(wa, prec, D, R, seed, cs)) return rc;
+      x0 = wa;
+    }
+    Sweep p;
+    sweep_init(p, lat, R, prec);
+    p.counter = reinterpret_cast<unsigned*>(work);
+    p.partials = reinterpret_cast<double*>(wptr(work, kWorkHeader));
+    p.mu = mu;
+    p.M = M;
+    p.dot_flags = 3;
+    for (int r = 0; r < R; ++r) {
+      p.coef[0][r] = 1.0 / a;
+      p.coef[1][r] = b;
+      p.coef[2][r] = 0.0;
+    }
+    p.x = x0;
+    p.yin = nullptr;
+    p.yout = wb;
+    p.dot_mode = 1;
+    if (int rc = launch_sweep(lat, prec, F_DOTS, p, cs)) return rc;
+    const void* prev = x0;
+    void* cur = wb;
+    const int nsteps = (M + 1) / 2;
+    for (int r = 0; r < R; ++r) {
+      p.coef[0][r] = 2.0 / a;
+      p.coef[2][r] = -1.0;
+    }
+    p.dot_mode = 2;
+    for (int k = 1; k < nsteps; ++k) {
+      void* out = (r0 && prev == r0) ? wa : const_cast<void*>(prev);
+      p.x = cur;
+      p.yin = prev;
+      p.yout = out;
+      p.kpm_k = k;
+      if (int rc = launch_sweep(lat, prec, F_DOTS, p, cs)) return rc;
+      prev = cur;
+      cur = out;
+    }
+    return PVSC_OK;
+  };
+  return run_graph(lat, key, st, body);
+}
+
+int pvsc_cheb_series(const pvsc_lattice* lat, int R, int prec, const void* x, void* y,
+                     const double* coeffs, int K, const double* phase, double a, double b,
+                     void* work, size_t work_bytes, void* stream) {
+  if (int rc = check_common(lat, R, prec)) return rc;
+  if (int rc = check_scaling(a, b)) return rc;
+  if (int rc = check_ptr(x, "x")) return rc;
+  if (int rc = check_ptr(y, "y")) return rc;
+  if (K < 1 || !coeffs) return set_error(PVSC_ERR_ARG, "need K >= 1 coefficients");
+  if (int rc = check_work(work, work_bytes, pvsc_work_bytes(lat, PVSC_OP_SERIES, R, prec, K))) return rc;
+  std::vector<cd> cw(K);
+  for (int k = 0; k < K; ++k) {
+    cw[k] = cd(coeffs[2 * k], coeffs[2 * k + 1]);
+    if (!std::isfinite(cw[k].real()) || !std::isfinite(cw[k].imag()))
+      return set_error(PVSC_ERR_ARG, "coefficient %d is not finite", k);
+  }
+  const cd ph = phase ? cd(phase[0], phase[1]) : cd(1, 0);
+  return run_series(lat, R, prec, x, y, cw, ph, a, b, work, static_cast<cudaStream_t>(stream));
+}
+
+int pvsc_cheb_filter(const pvsc_lattice* lat, int R, int prec, const void* x, void* y,
+                     const double* g, int K, double a, double b, void* work,
+                     size_t work_bytes, void* stream) {
+  if (K < 1 || !g) return set_error(PVSC_ERR_ARG, "need K >= 1 coefficients");
+  std::vector<double> c(2 * (size_t)K, 0.0);
+  for (int k = 0; k < K; ++k) c[2 * k] = g[k];
+  return pvsc_cheb_series(lat, R, prec, x, y, c.data(), K, nullptr, a, b, work, work_bytes, stream);
+}
+
+int pvsc_propagation_coeffs(double a_dt, double trunc, int max_terms, double* coeffs,
+                            int* n_terms) {
+  std::vector<cd> cw;
+  if (int rc = propagation_weights(a_dt, trunc, cw)) return rc;
+  if (n_terms) *n_terms = (int)cw.size();
+  if (!coeffs || max_terms < (int)cw.size())
+    return set_error(PVSC_ERR_ARG, "coefficient buffer holds %d < %d terms", max_terms, (int)cw.size());
+  for (size_t k = 0; k < cw.size(); ++k) {
+    coeffs[2 * k] = cw[k].real();
+    coeffs[2 * k + 1] = cw[k].imag();
+  }
+  return PVSC_OK;
+}
+
+int pvsc_cheb_propagate(const pvsc_lattice* lat, int R, int prec, void* psi, double dt,
+                        int nsteps, double a, double b, double trunc, void* work,
+                        size_t work_bytes, void* stream) {
+  if (int rc = check_common(lat, R, prec)) return rc;
+  if (int rc = check_scaling(a, b)) return rc;
+  if (int rc = check_ptr(psi, "psi")) return rc;
+  if (nsteps < 0) return set_error(PVSC_ERR_ARG, "nsteps = %d < 0", nsteps);
+  if (!std::isfinite(dt)) return set_error(PVSC_ERR_ARG, "dt is not finite");
+  std::vector<cd> cw;
+  if (int rc = propagation_weights(a * dt, trunc, cw)) return rc;
+  if (int rc = check_work(work, work_bytes, pvsc_work_bytes(lat, PVSC_OP_SERIES, R, prec, (int)cw.size())))
+    return rc;
+  if (nsteps == 0) return PVSC_OK;
+  const cd ph = std::exp(cd(0, -b * dt));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const std::vector<uint64_t> key = {2, (uint64_t)R, (uint64_t)prec, bits(psi), bits(dt), bits(a),
+                                     bits(b), bits(trunc), bits(work)};
+  auto body = [&](cudaStream_t cs) -> int {
+    return run_series(lat, R, prec, psi, psi, cw, ph, a, b, work, cs);
+  };
+  for (int s = 0; s < nsteps; ++s)
+    if (int rc = run_graph(lat, key, st, body)) return rc;
+  return PVSC_OK;
+}
+
+int pvsc_cheb_adjoint_step(const pvsc_lattice* lat, int R, int prec, const void* psi_s,
+                           void* G, double dt, double a, double b, double trunc,
+                           double* dLdV, void* work, size_t work_bytes, void* stream) {
+  if (int rc = check_common(lat, R, prec)) return rc;
+  if (prec != PVSC_C128) return set_error(PVSC_ERR_UNSUPPORTED, "the adjoint runs in complex128 only");
+  if (R != 1) return set_error(PVSC_ERR_UNSUPPORTED, "the adjoint takes one vector (R = 1)");
+  if (int rc = check_scaling(a, b)) return rc;
+  if (int rc = check_ptr(psi_s, "psi_s")) return rc;
+  if (int rc = check_ptr(G, "G")) return rc;
+  if (!dLdV) return set_error(PVSC_ERR_ARG, "dLdV is NULL");
+  if (psi_s == G) return set_error(PVSC_ERR_ARG, "psi_s and G must not overlap");
+  std::vector<cd> cw;
+  if (int rc = propagation_weights(a * dt, trunc, cw)) return rc;
+  const int M = (int)cw.size() - 1;
+  if (int rc = check_work(work, work_bytes, pvsc_work_bytes(lat, PVSC_OP_ADJOINT, R, prec, M + 1)))
+    return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t vb = vec_bytes(lat, R, PVSC_C128);
+  // work: [hdr | W_1 .. W_{M-1} | uA | uB]
+  auto Wk = [&](int k) -> void* { return k == 0 ? const_cast<void*>(psi_s) : wptr(work, kWorkHeader + (k - 1) * vb); };
+  void* ubuf[2] = {wptr(work, kWorkHeader + (size_t)(M > 1 ? M - 1 : 0) * vb),
+                   wptr(work, kWorkHeader + (size_t)(M > 1 ? M : 1) * vb)};
+  const cd cphi = std::exp(cd(0, b * dt));  // conj(e^{-i b dt})
+  auto sigma = [&](int k) { return std::conj(cw[k]) * cphi; };
+  const int64_t n = lat->g.n_sites * (lat->g.model == PVSC_TI ? 4 : 1);
+  if (M == 0) {
+    const cd s0 = sigma(0);
+    return launch_scale_init(G, static_cast<double2*>(G), s0.real(), s0.imag(), n, st);
+  }
+  Sweep p;
+  sweep_init(p, lat, R, prec);
+  // forward: w_1 .. w_{M-1}
+  for (int k = 1; k < M; ++k) {
+    p.coef[0][0] = (k == 1 ? 1.0 : 2.0) / a;
+    p.coef[1][0] = b;
+    p.coef[2][0] = (k == 1 ? 0.0 : -1.0);
+    p.x = Wk(k - 1);
+    p.yin = k == 1 ? nullptr : Wk(k - 2);
+    p.yout = Wk(k);
+    if (int rc = launch_sweep(lat, prec, 0, p, st)) return rc;
+  }
+  // u_M = sigma_M G, grad += (f_{M-1}/a) Re conj(u_M) w_{M-1}
+  {
+    const cd s = sigma(M);
+    const double f = (M - 1 == 0) ? 1.0 : 2.0;
+    if (int rc = launch_adjoint_top(lat, R, static_cast<const double2*>(G), s.real(), s.imag(),
+                                    static_cast<double2*>(ubuf[0]), static_cast<const double2*>(Wk(M - 1)),
+                                    f / a, dLdV, st))
+      return rc;
+  }
+  // u_k for k = M-1 .. 1 (u_{k+1} in cur, u_{k+2} in prev)
+  void* cur = ubuf[0];
+  void* prev = nullptr;
+  for (int k = M - 1; k >= 1; --k) {
+    void* out = prev ? prev : ubuf[1];
+    const cd s = sigma(k);
+    p.coef[0][0] = 2.0 / a;
+    p.coef[1][0] = b;
+    p.coef[2][0] = prev ? -1.0 : 0.0;
+    p.x = cur;
+    p.yin = prev;
+    p.yout = out;
+    p.src = static_cast<const double2*>(G);
+    p.sg_re = s.real();
+    p.sg_im = s.imag();
+    p.wg = Wk(k - 1);
+    p.grad = dLdV;
+    p.gscale = ((k - 1 == 0) ? 1.0 : 2.0) / a;
+    if (int rc = launch_sweep(lat, prec, F_ADJ, p, st)) return rc;
+    prev = cur;
+    cur = out;
+  }
+  // u_0 = sigma_0 G + H~ u_1 - u_2, written over G
+  {
+    const cd s = sigma(0);
+    p.coef[0][0] = 1.0 / a;
+    p.coef[1][0] = b;
+    p.coef[2][0] = prev ? -1.0 : 0.0;
+    p.x = cur;
+    p.yin = prev;
+    p.yout = G;
+    p.src = static_cast<const double2*>(G);
+    p.sg_re = s.real();
+    p.sg_im = s.imag();
+    p.wg = nullptr;
+    p.grad = nullptr;
+    if (int rc = launch_sweep(lat, prec, F_ADJ, p, st)) return rc;
+  }
+  return PVSC_OK;
+}
+
+int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tuning) {
+  if (int rc = check_common(lat, R, prec)) return rc;
+  if (!tuning) {
+    lat->tuning.erase({R, prec});
+    return PVSC_OK;
+  }
+  const int C = R / vpt_for(R, prec);
+  if (tuning->threads < 32 || tuning->threads > kMaxThreads || tuning->threads % 32 || tuning->threads % C)
+    return set_error(PVSC_ERR_ARG, "threads must be a multiple of 32 and of R/VPT = %d, at most %d", C, kMaxThreads);
+  if (tuning->blocks_per_sm < 0 || tuning->zslab < 0) return set_error(PVSC_ERR_ARG, "negative tuning value");
+  lat->tuning[{R, prec}] = *tuning;
+  return PVSC_OK;
+}
+
+int pvsc_get_tuning(const pvsc_lattice* lat, int R, int prec, pvsc_tuning* tuning) {
+  if (int rc = check_common(lat, R, prec)) return rc;
+  if (!tuning) return set_error(PVSC_ERR_ARG, "tuning is NULL");
+  auto it = lat->tuning.find({R, prec});
+  if (it != lat->tuning.end()) {
+    *tuning = it->second;
+  } else {
+    tuning->threads = 256;
+    tuning->blocks_per_sm = 0;
+    tuning->zslab = 0;
+    tuning->time_ms = 0.f;
+  }
+  return PVSC_OK;
+}
+
+}  // extern "C"

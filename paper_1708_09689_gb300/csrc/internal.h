@@ -1,0 +1,95 @@
+// Host-side internals shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/pvsc.h"
+#include "common.cuh"
+
+namespace pvsc {
+
+int set_error(int code, const char* fmt, ...);
+inline int ok() { return PVSC_OK; }
+
+#define PVSC_CUDA_TRY(call)                                                                  \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return ::pvsc::set_error(PVSC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Launch shape of one sweep kind on one lattice.
+struct LaunchShape {
+  int threads = 256;
+  int blocks_per_sm = 0;  // 0: occupancy maximum
+  int zslab = 0;          // 0: automatic
+};
+
+struct Graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace pvsc
+
+struct pvsc_lattice {
+  pvsc::Geometry g{};
+  double* V_dev = nullptr;  // owned when v_mode == 1
+  int v_source = 0;
+  uint64_t seed = 0;
+  int device = 0;
+  int sm_count = 0;
+  std::map<std::pair<int, int>, pvsc_tuning> tuning;  // (R, prec) -> tuning
+  // cached CUDA graphs keyed by the full argument set of a captured loop
+  std::map<std::vector<uint64_t>, pvsc::Graph> graphs;
+  std::mutex mu;
+  ~pvsc_lattice();
+};
+
+namespace pvsc {
+
+constexpr int kMaxGridPerSM = 16;
+constexpr size_t kWorkHeader = 256;  // counters at the start of every work buffer
+
+int vpt_for(int R, int prec);
+bool valid_R(int R);
+int check_lattice(const pvsc_lattice* lat);
+int check_ptr(const void* p, const char* name);
+
+// Fill p.g / p.R / p.C from the lattice; the caller sets the rest.
+void sweep_init(Sweep& p, const pvsc_lattice* lat, int R, int prec);
+// Launch one fused sweep (feat: F_* mask).  Dot features need p.partials and
+// p.counter inside a work buffer of at least dots_work_bytes(lat, R) bytes.
+int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStream_t st);
+size_t dots_work_bytes(const pvsc_lattice* lat, int R);
+size_t vec_bytes(const pvsc_lattice* lat, int R, int prec);  // one D x R block
+
+// per-precision kernel launchers (sweep_c128.cu / sweep_c64.cu)
+int launch_sweep_c128(int model, int feat, int grid, int threads, const Sweep& p,
+                      cudaStream_t st);
+int launch_sweep_c64(int model, int vpt, int feat, int grid, int threads, const Sweep& p,
+                     cudaStream_t st);
+int occupancy_c128(int model, int feat, int threads, int* blocks);
+int occupancy_c64(int model, int vpt, int feat, int threads, int* blocks);
+
+// elementwise helpers (aux.cu)
+int launch_random_phase(void* out, int prec, int64_t D, int R, uint64_t seed, cudaStream_t st);
+int launch_convert_c128_to_c64(const void* in, void* out, int64_t n, cudaStream_t st);
+int launch_scale_init(const void* x128, double2* acc, double cr, double ci, int64_t n,
+                      cudaStream_t st);
+int launch_seed_potential(double* V, int64_t n, uint64_t seed, double W, cudaStream_t st);
+int launch_get_potential(const Geometry& g, double* out, cudaStream_t st);
+int launch_gershgorin(const Geometry& g, double* out, int grid, cudaStream_t st);
+int launch_neighbours(const Geometry& g, int64_t* nbr, cudaStream_t st);
+int launch_adjoint_top(const pvsc_lattice* lat, int R, const double2* G, double sr, double si,
+                       double2* uM, const double2* w, double gscale, double* grad,
+                       cudaStream_t st);
+
+}  // namespace pvsc

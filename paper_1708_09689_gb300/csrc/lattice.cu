@@ -1,0 +1,220 @@
+// Lattice handles, argument checking, error reporting and the geometry-side
+// entry points of the C ABI (create/destroy/info, potential, Gershgorin
+// bounds, neighbour-table export).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace pvsc {
+
+static thread_local std::string g_err;
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+bool valid_R(int R) {
+  return R == 1 || R == 2 || R == 4 || R == 8 || R == 16 || R == 32 || R == 64;
+}
+
+int vpt_for(int R, int prec) { return (prec == PVSC_C64 && R >= 2) ? 2 : 1; }
+
+int check_lattice(const pvsc_lattice* lat) {
+  if (!lat) return set_error(PVSC_ERR_ARG, "lattice handle is NULL");
+  return PVSC_OK;
+}
+
+int check_ptr(const void* p, const char* name) {
+  if (!p) return set_error(PVSC_ERR_ARG, "%s is NULL", name);
+  if (reinterpret_cast<uintptr_t>(p) % 16 != 0)
+    return set_error(PVSC_ERR_ARG, "%s is not 16-byte aligned", name);
+  return PVSC_OK;
+}
+
+size_t vec_bytes(const pvsc_lattice* lat, int R, int prec) {
+  const int64_t D = lat->g.n_sites * (lat->g.model == 1 ? 4 : 1);
+  const size_t b = (size_t)D * R * (prec == PVSC_C128 ? 16 : 8);
+  return (b + 255) & ~size_t(255);
+}
+
+size_t dots_work_bytes(const pvsc_lattice* lat, int R) {
+  return kWorkHeader + (size_t)lat->sm_count * kMaxGridPerSM * kNumDots * R * sizeof(double);
+}
+
+}  // namespace pvsc
+
+pvsc_lattice::~pvsc_lattice() {
+  for (auto& kv : graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  if (V_dev) cudaFree(V_dev);
+}
+
+using namespace pvsc;
+
+extern "C" {
+
+const char* pvsc_last_error(void) { return g_err.c_str(); }
+
+const char* pvsc_version(void) { return "pvsc-gb300 1.0 (sm_103a)"; }
+
+int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattice** out) {
+  if (!desc || !out) return set_error(PVSC_ERR_ARG, "desc and out must not be NULL");
+  if (desc->model != PVSC_TI && desc->model != PVSC_GRAPHENE)
+    return set_error(PVSC_ERR_ARG, "unknown model %d", desc->model);
+  for (int d = 0; d < 3; ++d)
+    if (desc->dims[d] < 1) return set_error(PVSC_ERR_ARG, "dims[%d] = %lld < 1", d, (long long)desc->dims[d]);
+  if (desc->model == PVSC_GRAPHENE && desc->dims[2] != 1)
+    return set_error(PVSC_ERR_ARG, "graphene lattices are 2D: dims[2] must be 1");
+  if (!std::isfinite(desc->t) || !std::isfinite(desc->m))
+    return set_error(PVSC_ERR_ARG, "t and m must be finite");
+  if (desc->delta1 != 0.0 || desc->delta2 != 0.0)
+    return set_error(PVSC_ERR_UNSUPPORTED, "Delta_1 / Delta_2 terms are not implemented");
+  if (desc->v_source < PVSC_V_ZERO || desc->v_source > PVSC_V_ON_THE_FLY)
+    return set_error(PVSC_ERR_ARG, "unknown v_source %d", desc->v_source);
+  if ((desc->v_source == PVSC_V_HOST || desc->v_source == PVSC_V_DEVICE) && !desc->V)
+    return set_error(PVSC_ERR_ARG, "v_source needs desc->V");
+  if ((desc->v_source == PVSC_V_SEED || desc->v_source == PVSC_V_ON_THE_FLY) && !std::isfinite(desc->W))
+    return set_error(PVSC_ERR_ARG, "W must be finite");
+  const double cells = (double)desc->dims[0] * (double)desc->dims[1] * (double)desc->dims[2];
+  if (cells * 4.0 * kMaxR > 4.0e18) return set_error(PVSC_ERR_ARG, "lattice too large");
+
+  pvsc_lattice* lat = new (std::nothrow) pvsc_lattice();
+  if (!lat) return set_error(PVSC_ERR_OOM, "out of host memory");
+  Geometry& g = lat->g;
+  g.model = desc->model;
+  for (int d = 0; d < 3; ++d) {
+    g.per[d] = desc->periodic[d] ? 1 : 0;
+    g.L[d] = desc->dims[d];
+  }
+  g.n_sites = desc->model == PVSC_TI ? desc->dims[0] * desc->dims[1] * desc->dims[2]
+                                     : 4 * desc->dims[0] * desc->dims[1];
+  g.t = desc->t;
+  g.m = desc->model == PVSC_TI ? desc->m : 0.0;
+  g.v_mode = 0;
+  g.W = desc->W;
+  g.vkey = hash_key(desc->seed, 0);
+  lat->v_source = desc->v_source;
+  lat->seed = desc->seed;
+  cudaError_t e = cudaGetDevice(&lat->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&lat->sm_count, cudaDevAttrMultiProcessorCount, lat->device);
+  if (e != cudaSuccess) {
+    delete lat;
+    return set_error(PVSC_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = PVSC_OK;
+  if (desc->v_source == PVSC_V_HOST || desc->v_source == PVSC_V_DEVICE || desc->v_source == PVSC_V_SEED) {
+    e = cudaMalloc(&lat->V_dev, sizeof(double) * g.n_sites);
+    if (e != cudaSuccess) {
+      delete lat;
+      return set_error(PVSC_ERR_OOM, "cudaMalloc of V failed: %s", cudaGetErrorString(e));
+    }
+    g.V = lat->V_dev;
+    g.v_mode = 1;
+    if (desc->v_source == PVSC_V_SEED) {
+      rc = launch_seed_potential(lat->V_dev, g.n_sites, desc->seed, desc->W, st);
+    } else {
+      e = cudaMemcpyAsync(lat->V_dev, desc->V, sizeof(double) * g.n_sites,
+                          desc->v_source == PVSC_V_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) rc = set_error(PVSC_ERR_CUDA, "copy of V failed: %s", cudaGetErrorString(e));
+    }
+  } else if (desc->v_source == PVSC_V_ON_THE_FLY) {
+    g.v_mode = 2;
+  }
+  if (rc == PVSC_OK) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = set_error(PVSC_ERR_CUDA, "lattice setup failed: %s", cudaGetErrorString(e));
+  }
+  if (rc != PVSC_OK) {
+    delete lat;
+    return rc;
+  }
+  *out = lat;
+  return PVSC_OK;
+}
+
+int pvsc_lattice_destroy(pvsc_lattice* lat) {
+  delete lat;
+  return PVSC_OK;
+}
+
+int pvsc_lattice_info(const pvsc_lattice* lat, int64_t* n_sites, int32_t* orbitals) {
+  if (int rc = check_lattice(lat)) return rc;
+  if (n_sites) *n_sites = lat->g.n_sites;
+  if (orbitals) *orbitals = lat->g.model == PVSC_TI ? 4 : 1;
+  return PVSC_OK;
+}
+
+int pvsc_set_potential(pvsc_lattice* lat, const double* V_dev, void* stream) {
+  if (int rc = check_lattice(lat)) return rc;
+  if (!V_dev) return set_error(PVSC_ERR_ARG, "V_dev is NULL");
+  if (lat->g.v_mode == 2) return set_error(PVSC_ERR_ARG, "the potential of this lattice is regenerated on the fly");
+  if (!lat->V_dev) {
+    cudaError_t e = cudaMalloc(&lat->V_dev, sizeof(double) * lat->g.n_sites);
+    if (e != cudaSuccess) return set_error(PVSC_ERR_OOM, "cudaMalloc of V failed: %s", cudaGetErrorString(e));
+    lat->g.V = lat->V_dev;
+    lat->g.v_mode = 1;
+    // cached graphs captured with V = 0 read no potential: drop them
+    std::lock_guard<std::mutex> lk(lat->mu);
+    for (auto& kv : lat->graphs) {
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+      if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    lat->graphs.clear();
+  }
+  PVSC_CUDA_TRY(cudaMemcpyAsync(lat->V_dev, V_dev, sizeof(double) * lat->g.n_sites,
+                                cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+  return PVSC_OK;
+}
+
+int pvsc_get_potential(const pvsc_lattice* lat, double* V_out_dev, void* stream) {
+  if (int rc = check_lattice(lat)) return rc;
+  if (!V_out_dev) return set_error(PVSC_ERR_ARG, "V_out_dev is NULL");
+  return launch_get_potential(lat->g, V_out_dev, static_cast<cudaStream_t>(stream));
+}
+
+int pvsc_spectral_bounds(const pvsc_lattice* lat, double eps, double* emin, double* emax,
+                         double* a, double* b, void* work, size_t work_bytes, void* stream) {
+  if (int rc = check_lattice(lat)) return rc;
+  if (int rc = check_ptr(work, "work")) return rc;
+  if (!std::isfinite(eps) || eps < 0) return set_error(PVSC_ERR_ARG, "eps must be finite and >= 0");
+  const int grid = 2 * lat->sm_count;
+  if (work_bytes < sizeof(double) * 2 * grid)
+    return set_error(PVSC_ERR_ARG, "work too small: %zu < %zu", work_bytes, sizeof(double) * 2 * grid);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (int rc = launch_gershgorin(lat->g, static_cast<double*>(work), grid, st)) return rc;
+  std::vector<double> h(2 * grid);
+  PVSC_CUDA_TRY(cudaMemcpyAsync(h.data(), work, sizeof(double) * 2 * grid, cudaMemcpyDeviceToHost, st));
+  PVSC_CUDA_TRY(cudaStreamSynchronize(st));
+  double lo = h[0], hi = h[1];
+  for (int i = 1; i < grid; ++i) {
+    lo = std::fmin(lo, h[2 * i]);
+    hi = std::fmax(hi, h[2 * i + 1]);
+  }
+  if (emin) *emin = lo;
+  if (emax) *emax = hi;
+  if (a) *a = (hi - lo + eps) / 2.0;
+  if (b) *b = (hi + lo) / 2.0;
+  return PVSC_OK;
+}
+
+int pvsc_debug_neighbours(const pvsc_lattice* lat, int64_t* nbr_dev, void* stream) {
+  if (int rc = check_lattice(lat)) return rc;
+  if (!nbr_dev) return set_error(PVSC_ERR_ARG, "nbr_dev is NULL");
+  return launch_neighbours(lat->g, nbr_dev, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,485 @@
+// Fused stencil sweeps: one pass of H over a block of R vectors, fused with
+// the Chebyshev-recurrence update, the series accumulation, the adjoint
+// source/gradient terms and the partial dot products (the loop fusion of
+// Listing graphenec, Sec. 3.2).
+//
+// Layout: element (site, orbital, r) at complex offset ((site*4 + orbital)*R + r)
+// (TI) or ((4*cell + nu)*R + r) (graphene).  A thread owns one site (TI) or
+// one 4-site cell (graphene) and VPT consecutive vectors of it, so every load
+// and store is a 16-byte vector access: complex128 one value, complex64 two
+// vectors of one orbital (or, for R = 1, two orbitals).
+//
+// TI sweeps march along z (2.5D blocking): a thread keeps planes z-1, z, z+1
+// of its own column in registers and reads the four in-plane neighbours,
+// which its neighbours in the block have just loaded, from L1/L2.  Each
+// vector element is then read from HBM once per sweep; the paper's layer
+// condition (Sec. 3.1) becomes "one plane of the block in L1/L2".
+#pragma once
+
+#include "common.cuh"
+
+namespace pvsc {
+
+enum Feat { F_DOTS = 1, F_Z = 2, F_ACC = 4, F_ADJ = 8 };
+
+template <typename T, int VPT>
+struct Blk {
+  cplx<T> v[4][VPT];
+};
+
+template <typename T, int VPT>
+__device__ __forceinline__ void zero_blk(Blk<T, VPT>& b) {
+#pragma unroll
+  for (int o = 0; o < 4; ++o)
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) b.v[o][v] = {T(0), T(0)};
+}
+
+// Load the 4 orbitals (TI site) or 4 sites (graphene cell) `s` of chunk rc.
+template <typename T, int VPT, bool RO>
+__device__ __forceinline__ void load_blk(const T* __restrict__ base, int64_t s, int R, int rc,
+                                         Blk<T, VPT>& b) {
+  const T* p = base + 2 * ((s * 4) * (int64_t)R + rc * VPT);
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const double2* q = reinterpret_cast<const double2*>(p + 2 * o * R);
+      double2 a = RO ? __ldg(q) : *q;
+      b.v[o][0] = {a.x, a.y};
+    }
+  } else if constexpr (VPT == 1) {  // complex64, R == 1: 32 contiguous bytes
+    const float4* q = reinterpret_cast<const float4*>(p);
+    float4 a = RO ? __ldg(q) : q[0];
+    float4 c = RO ? __ldg(q + 1) : q[1];
+    b.v[0][0] = {a.x, a.y};
+    b.v[1][0] = {a.z, a.w};
+    b.v[2][0] = {c.x, c.y};
+    b.v[3][0] = {c.z, c.w};
+  } else {  // complex64, two vectors per 16 bytes
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const float4* q = reinterpret_cast<const float4*>(p + 2 * o * R);
+      float4 a = RO ? __ldg(q) : *q;
+      b.v[o][0] = {a.x, a.y};
+      b.v[o][1] = {a.z, a.w};
+    }
+  }
+}
+
+template <typename T, int VPT>
+__device__ __forceinline__ void store_blk(T* __restrict__ base, int64_t s, int R, int rc,
+                                          const Blk<T, VPT>& b) {
+  T* p = base + 2 * ((s * 4) * (int64_t)R + rc * VPT);
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+      *reinterpret_cast<double2*>(p + 2 * o * R) = make_double2(b.v[o][0].re, b.v[o][0].im);
+  } else if constexpr (VPT == 1) {
+    float4* q = reinterpret_cast<float4*>(p);
+    q[0] = make_float4(b.v[0][0].re, b.v[0][0].im, b.v[1][0].re, b.v[1][0].im);
+    q[1] = make_float4(b.v[2][0].re, b.v[2][0].im, b.v[3][0].re, b.v[3][0].im);
+  } else {
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+      *reinterpret_cast<float4*>(p + 2 * o * R) =
+          make_float4(b.v[o][0].re, b.v[o][0].im, b.v[o][1].re, b.v[o][1].im);
+  }
+}
+
+// One value (all VPT vectors) of orbital/site o of block s.
+template <typename T, int VPT>
+__device__ __forceinline__ void load_one(const T* __restrict__ base, int64_t s, int o, int R,
+                                         int rc, cplx<T> (&out)[VPT]) {
+  const T* p = base + 2 * ((s * 4 + o) * (int64_t)R + rc * VPT);
+  if constexpr (sizeof(T) == 8) {
+    double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    out[0] = {a.x, a.y};
+  } else if constexpr (VPT == 1) {
+    float2 a = __ldg(reinterpret_cast<const float2*>(p));
+    out[0] = {a.x, a.y};
+  } else {
+    float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    out[0] = {a.x, a.y};
+    out[1] = {a.z, a.w};
+  }
+}
+
+// complex128 accumulator element of (block s, orbital o, vector r)
+__device__ __forceinline__ double2* acc_ptr(double2* base, int64_t s, int o, int R, int r) {
+  return base + ((s * 4 + o) * (int64_t)R + r);
+}
+
+// ---------------------------------------------------------------- per-thread constants
+template <typename T, int VPT>
+struct VecCoef {
+  T alpha[VPT], ab[VPT], am[VPT], kt[VPT], gamma[VPT], delta[VPT];
+};
+
+template <typename T, int VPT>
+__device__ __forceinline__ VecCoef<T, VPT> load_coef(const Sweep& p, int rc) {
+  VecCoef<T, VPT> c;
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    const int r = rc * VPT + v;
+    const double a = p.coef[0][r], b = p.coef[1][r];
+    c.alpha[v] = T(a);
+    c.ab[v] = T(a * b);
+    c.am[v] = T(a * p.g.m);
+    c.kt[v] = T(-0.5 * a * p.g.t);
+    c.gamma[v] = T(p.coef[2][r]);
+    c.delta[v] = T(p.coef[3][r]);
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------- the shared epilogue
+// Everything a sweep does after y_new of one block is known.
+template <typename T, int VPT, int FEAT>
+__device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, const Blk<T, VPT>& xc,
+                                         Blk<T, VPT>& yn, double (&dacc)[kNumDots][VPT],
+                                         const int64_t* site_of /* 4 sites of the block */) {
+  const int R = p.R;
+  if constexpr ((FEAT & F_ADJ) != 0) {
+    // y_new += sigma * src (complex128 source)
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        const double2 h = *acc_ptr(const_cast<double2*>(p.src), s, o, R, rc * VPT + v);
+        yn.v[o][v].re += T(p.sg_re * h.x - p.sg_im * h.y);
+        yn.v[o][v].im += T(p.sg_re * h.y + p.sg_im * h.x);
+      }
+  }
+  if (p.yout != nullptr) store_blk<T, VPT>(static_cast<T*>(p.yout), s, R, rc, yn);
+  if constexpr ((FEAT & F_Z) != 0) {
+    Blk<T, VPT> zb;
+    load_blk<T, VPT, false>(static_cast<const T*>(p.z), s, R, rc, zb);
+    const VecCoef<T, VPT> c = load_coef<T, VPT>(p, rc);
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        zb.v[o][v].re += c.delta[v] * yn.v[o][v].re;
+        zb.v[o][v].im += c.delta[v] * yn.v[o][v].im;
+      }
+    store_blk<T, VPT>(static_cast<T*>(p.z), s, R, rc, zb);
+  }
+  if constexpr ((FEAT & F_ACC) != 0) {
+    const double cr = p.cy_re, ci = p.cy_im;
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        const int r = rc * VPT + v;
+        const double yr = (double)yn.v[o][v].re, yi = (double)yn.v[o][v].im;
+        double ar, ai;
+        if (p.acc_mode & ACC_INIT) {
+          const double xr = (double)xc.v[o][v].re, xi = (double)xc.v[o][v].im;
+          ar = p.cx_re * xr - p.cx_im * xi;
+          ai = p.cx_re * xi + p.cx_im * xr;
+        } else {
+          const double2 a = *acc_ptr(p.acc, s, o, R, r);
+          ar = a.x;
+          ai = a.y;
+        }
+        // Bessel weights are alternately real and imaginary: skip the zero half.
+        if (ci == 0.0) {
+          ar = fma(cr, yr, ar);
+          ai = fma(cr, yi, ai);
+        } else if (cr == 0.0) {
+          ar = fma(-ci, yi, ar);
+          ai = fma(ci, yr, ai);
+        } else {
+          ar = fma(cr, yr, fma(-ci, yi, ar));
+          ai = fma(cr, yi, fma(ci, yr, ai));
+        }
+        if (p.acc_mode & ACC_FINAL) {
+          *acc_ptr(p.acc_out, s, o, R, r) =
+              make_double2(p.ph_re * ar - p.ph_im * ai, p.ph_re * ai + p.ph_im * ar);
+        } else {
+          *acc_ptr(p.acc, s, o, R, r) = make_double2(ar, ai);
+        }
+      }
+  }
+  if constexpr ((FEAT & F_ADJ) != 0) {
+    if (p.grad != nullptr) {
+      // gradient partner w: one value per orbital/site, summed per site over vectors
+      Blk<T, VPT> wb;
+      load_blk<T, VPT, false>(static_cast<const T*>(p.wg), s, R, rc, wb);
+      if (p.g.model == 1) {
+        double gsum = 0.0;
+#pragma unroll
+        for (int o = 0; o < 4; ++o)
+#pragma unroll
+          for (int v = 0; v < VPT; ++v)
+            gsum += (double)yn.v[o][v].re * (double)wb.v[o][v].re +
+                    (double)yn.v[o][v].im * (double)wb.v[o][v].im;
+        p.grad[site_of[0]] += p.gscale * gsum;
+      } else {
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          double gsum = 0.0;
+#pragma unroll
+          for (int v = 0; v < VPT; ++v)
+            gsum += (double)yn.v[o][v].re * (double)wb.v[o][v].re +
+                    (double)yn.v[o][v].im * (double)wb.v[o][v].im;
+          p.grad[site_of[o]] += p.gscale * gsum;
+        }
+      }
+    }
+  }
+  if constexpr ((FEAT & F_DOTS) != 0) {
+    // exact-enough per-block partials in T, accumulated in fp64
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      T xx = 0, xyr = 0, xyi = 0, yy = 0;
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const cplx<T> a = xc.v[o][v], b = yn.v[o][v];
+        xx = fma(a.re, a.re, fma(a.im, a.im, xx));
+        xyr = fma(b.re, a.re, fma(b.im, a.im, xyr));
+        if (p.dot_flags & 2) xyi = fma(b.re, a.im, fma(-b.im, a.re, xyi));
+        if (p.dot_flags & 4) yy = fma(b.re, b.re, fma(b.im, b.im, yy));
+      }
+      dacc[0][v] += (double)xx;
+      dacc[1][v] += (double)xyr;
+      dacc[2][v] += (double)xyi;
+      dacc[3][v] += (double)yy;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- TI sweep
+// y_new = alpha (H - beta) x + gamma y_in with H of Eq. TB_H_topi:
+//   (H x)_n = (m Gamma^1 + V_n) x_n + sum_j [A_j x_{n-e_j} + A_j^+ x_{n+e_j}],
+//   A_j = -(t/2)(Gamma^1 - i Gamma^{j+1}).
+// With s_j = x_{n-e_j} + x_{n+e_j} and d_j = x_{n-e_j} - x_{n+e_j}:
+//   sum_j [...] = -(t/2) [Gamma^1 S - i sum_j Gamma^{j+1} d_j],  S = sum_j s_j,
+// and -i Gamma^{j+1} d is a signed permutation of d's components:
+//   j=x: ( d3,  d2, -d1, -d0)   j=y: -i (d3, d2, d1, d0)   j=z: (d1, -d0, d3, -d2).
+// Gamma^1 = diag(1,-1,1,-1) is a sign flip, so no multiply is spent on it.
+template <typename T, int VPT, int FEAT>
+__global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p) {
+  const int64_t Lx = p.g.L[0], Ly = p.g.L[1], Lz = p.g.L[2];
+  const int64_t plane = Lx * Ly;
+  const int R = p.R, C = p.C;
+  const int rc = threadIdx.x % C;
+  const VecCoef<T, VPT> cf = load_coef<T, VPT>(p, rc);
+  const T* __restrict__ X = static_cast<const T*>(p.x);
+  double dacc[kNumDots][VPT];
+#pragma unroll
+  for (int d = 0; d < kNumDots; ++d)
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) dacc[d][v] = 0.0;
+
+  const int64_t ncolthr = plane * C;
+  const int64_t nbx = (ncolthr + blockDim.x - 1) / blockDim.x;
+  const int zs = p.zslab;
+  const int64_t nzs = (Lz + zs - 1) / zs;
+  const int64_t nunits = nbx * nzs;
+  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int64_t bz = u / nbx, bx = u - bz * nbx;
+    const int64_t tid = bx * blockDim.x + threadIdx.x;
+    if (tid >= ncolthr) continue;
+    const int64_t col = tid / C;
+    const int64_t x = col % Lx, y = col / Lx;
+    // in-plane neighbour columns (-1: absent)
+    const int64_t cxm = nbr_minus(col, x, Lx, p.g.per[0], 1);
+    const int64_t cxp = nbr_plus(col, x, Lx, p.g.per[0], 1);
+    const int64_t cym = nbr_minus(col, y, Ly, p.g.per[1], Lx);
+    const int64_t cyp = nbr_plus(col, y, Ly, p.g.per[1], Lx);
+    const int64_t z0 = bz * zs, z1 = min(z0 + (int64_t)zs, Lz);
+    Blk<T, VPT> xm, xc, xp;
+    load_blk<T, VPT, true>(X, col + plane * z0, R, rc, xc);
+    {
+      const int64_t zm = nbr_minus(z0, z0, Lz, p.g.per[2], 1);
+      if (zm >= 0) load_blk<T, VPT, true>(X, col + plane * zm, R, rc, xm);
+      else zero_blk(xm);
+    }
+    for (int64_t z = z0; z < z1; ++z) {
+      const int64_t s = col + plane * z;
+      const int64_t zp = nbr_plus(z, z, Lz, p.g.per[2], 1);
+      if (zp >= 0) load_blk<T, VPT, true>(X, col + plane * zp, R, rc, xp);
+      else zero_blk(xp);
+      Blk<T, VPT> yi;
+      if (p.yin != nullptr) load_blk<T, VPT, false>(static_cast<const T*>(p.yin), s, R, rc, yi);
+      const T Vs = T(site_potential(p.g, s));
+      Blk<T, VPT> S, D;
+      // z axis: s_z, d_z
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        cplx<T> d[4];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          S.v[o][v] = cadd(xm.v[o][v], xp.v[o][v]);
+          d[o] = csub(xm.v[o][v], xp.v[o][v]);
+        }
+        D.v[0][v] = d[1];
+        D.v[1][v] = {-d[0].re, -d[0].im};
+        D.v[2][v] = d[3];
+        D.v[3][v] = {-d[2].re, -d[2].im};
+      }
+      // x axis
+      {
+        Blk<T, VPT> a, b;
+        const int64_t zoff = plane * z;
+        if (cxm >= 0) load_blk<T, VPT, true>(X, cxm + zoff, R, rc, a); else zero_blk(a);
+        if (cxp >= 0) load_blk<T, VPT, true>(X, cxp + zoff, R, rc, b); else zero_blk(b);
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          cplx<T> d[4];
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            S.v[o][v] = cadd(S.v[o][v], cadd(a.v[o][v], b.v[o][v]));
+            d[o] = csub(a.v[o][v], b.v[o][v]);
+          }
+          D.v[0][v] = cadd(D.v[0][v], d[3]);
+          D.v[1][v] = cadd(D.v[1][v], d[2]);
+          D.v[2][v] = csub(D.v[2][v], d[1]);
+          D.v[3][v] = csub(D.v[3][v], d[0]);
+        }
+      }
+      // y axis: -i d = (d.im, -d.re)
+      {
+        Blk<T, VPT> a, b;
+        const int64_t zoff = plane * z;
+        if (cym >= 0) load_blk<T, VPT, true>(X, cym + zoff, R, rc, a); else zero_blk(a);
+        if (cyp >= 0) load_blk<T, VPT, true>(X, cyp + zoff, R, rc, b); else zero_blk(b);
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          cplx<T> d[4];
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            S.v[o][v] = cadd(S.v[o][v], cadd(a.v[o][v], b.v[o][v]));
+            d[o] = csub(a.v[o][v], b.v[o][v]);
+          }
+          D.v[0][v] = cadd(D.v[0][v], cplx<T>{d[3].im, -d[3].re});
+          D.v[1][v] = cadd(D.v[1][v], cplx<T>{d[2].im, -d[2].re});
+          D.v[2][v] = cadd(D.v[2][v], cplx<T>{d[1].im, -d[1].re});
+          D.v[3][v] = cadd(D.v[3][v], cplx<T>{d[0].im, -d[0].re});
+        }
+      }
+      // y_new = d_o x_o + kt (Gamma^1 S + D)_o + gamma y_in,  d_o = alpha (V - beta) +- alpha m
+      Blk<T, VPT> yn;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        const T e = fma(cf.alpha[v], Vs, -cf.ab[v]);
+        const T dp = e + cf.am[v], dm = e - cf.am[v];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const T dd = (o & 1) ? dm : dp;
+          const cplx<T> Tt = (o & 1) ? csub(D.v[o][v], S.v[o][v]) : cadd(D.v[o][v], S.v[o][v]);
+          T re = fma(cf.kt[v], Tt.re, dd * xc.v[o][v].re);
+          T im = fma(cf.kt[v], Tt.im, dd * xc.v[o][v].im);
+          if (p.yin != nullptr) {
+            re = fma(cf.gamma[v], yi.v[o][v].re, re);
+            im = fma(cf.gamma[v], yi.v[o][v].im, im);
+          }
+          yn.v[o][v] = {re, im};
+        }
+      }
+      const int64_t sites[4] = {s, s, s, s};
+      epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
+      xm = xc;
+      xc = xp;
+    }
+  }
+  if constexpr ((FEAT & F_DOTS) != 0) reduce_dots<VPT>(p, dacc);
+}
+
+// ---------------------------------------------------------------- graphene sweep
+// H of Eq. graphene_model per 4-site cell c (x + Nx y), hopping -t:
+//   (Hx)_{c,0} = v0 x_{c,0} - t (x_{c,1} + x_{c+x,1} + x_{c-y,3})
+//   (Hx)_{c,1} = v1 x_{c,1} - t (x_{c,0} + x_{c,2} + x_{c-x,0})
+//   (Hx)_{c,2} = v2 x_{c,2} - t (x_{c,1} + x_{c,3} + x_{c-x,3})
+//   (Hx)_{c,3} = v3 x_{c,3} - t (x_{c,2} + x_{c+x,2} + x_{c+y,0})
+// (T_x couples site 0 to site 1 of cell c + x and site 3 to site 2; T_y site 0
+// to site 3 of cell c - y; T_n is the chain 0-1-2-3.)
+template <typename T, int VPT, int FEAT>
+__global__ void __launch_bounds__(256) gr_sweep(const __grid_constant__ Sweep p) {
+  const int64_t Nx = p.g.L[0], Ny = p.g.L[1];
+  const int64_t ncell = Nx * Ny;
+  const int R = p.R, C = p.C;
+  const int rc = threadIdx.x % C;
+  const VecCoef<T, VPT> cf = load_coef<T, VPT>(p, rc);
+  const T* __restrict__ X = static_cast<const T*>(p.x);
+  const T tt = T(p.g.t);
+  double dacc[kNumDots][VPT];
+#pragma unroll
+  for (int d = 0; d < kNumDots; ++d)
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) dacc[d][v] = 0.0;
+  const int64_t nthr = ncell * C;
+  for (int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tid < nthr;
+       tid += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = tid / C;
+    const int64_t x = c % Nx, y = c / Nx;
+    const int64_t cxm = nbr_minus(c, x, Nx, p.g.per[0], 1);
+    const int64_t cxp = nbr_plus(c, x, Nx, p.g.per[0], 1);
+    const int64_t cym = nbr_minus(c, y, Ny, p.g.per[1], Nx);
+    const int64_t cyp = nbr_plus(c, y, Ny, p.g.per[1], Nx);
+    Blk<T, VPT> xc, yi;
+    load_blk<T, VPT, true>(X, c, R, rc, xc);
+    if (p.yin != nullptr) load_blk<T, VPT, false>(static_cast<const T*>(p.yin), c, R, rc, yi);
+    cplx<T> n0[VPT], n1[VPT], n2[VPT], n3[VPT];  // neighbour sums of sites 0..3
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      n0[v] = xc.v[1][v];
+      n1[v] = cadd(xc.v[0][v], xc.v[2][v]);
+      n2[v] = cadd(xc.v[1][v], xc.v[3][v]);
+      n3[v] = xc.v[2][v];
+    }
+    cplx<T> a[VPT];
+    if (cxp >= 0) {
+      load_one<T, VPT>(X, cxp, 1, R, rc, a);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) n0[v] = cadd(n0[v], a[v]);
+      load_one<T, VPT>(X, cxp, 2, R, rc, a);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) n3[v] = cadd(n3[v], a[v]);
+    }
+    if (cxm >= 0) {
+      load_one<T, VPT>(X, cxm, 0, R, rc, a);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) n1[v] = cadd(n1[v], a[v]);
+      load_one<T, VPT>(X, cxm, 3, R, rc, a);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) n2[v] = cadd(n2[v], a[v]);
+    }
+    if (cym >= 0) {
+      load_one<T, VPT>(X, cym, 3, R, rc, a);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) n0[v] = cadd(n0[v], a[v]);
+    }
+    if (cyp >= 0) {
+      load_one<T, VPT>(X, cyp, 0, R, rc, a);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) n3[v] = cadd(n3[v], a[v]);
+    }
+    T Vs[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) Vs[o] = T(site_potential(p.g, 4 * c + o));
+    Blk<T, VPT> yn;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const T kt = -cf.alpha[v] * tt;
+      const cplx<T>* ns[4] = {&n0[v], &n1[v], &n2[v], &n3[v]};
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const T dd = fma(cf.alpha[v], Vs[o], -cf.ab[v]);
+        T re = fma(kt, ns[o]->re, dd * xc.v[o][v].re);
+        T im = fma(kt, ns[o]->im, dd * xc.v[o][v].im);
+        if (p.yin != nullptr) {
+          re = fma(cf.gamma[v], yi.v[o][v].re, re);
+          im = fma(cf.gamma[v], yi.v[o][v].im, im);
+        }
+        yn.v[o][v] = {re, im};
+      }
+    }
+    const int64_t sites[4] = {4 * c, 4 * c + 1, 4 * c + 2, 4 * c + 3};
+    epilogue<T, VPT, FEAT>(p, c, rc, xc, yn, dacc, sites);
+  }
+  if constexpr ((FEAT & F_DOTS) != 0) reduce_dots<VPT>(p, dacc);
+}
+
+}  // namespace pvsc
