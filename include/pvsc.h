@@ -141,6 +141,14 @@ int pvsc_get_potential(const pvsc_lattice* lat, double* V_out_dev, void* stream)
 int pvsc_spectral_bounds(const pvsc_lattice* lat, double eps, double* emin, double* emax,
                          double* a, double* b, void* work, size_t work_bytes, void* stream);
 
+/* Random-phase start block (the stochastic trace vectors of the kernel
+ * polynomial method, Sec. 4): out[i R + r] = exp(2 pi i u)/sqrt(D) with u from
+ * the counter hash, stream 1, idx = r D + i, so <r|r> = 1.  The device-side
+ * counterpart of the paper's pvsc_vector_from_func initialisation with a
+ * random seed (Sec. 3.4).  out: device block of D*R complex in prec. */
+int pvsc_random_vectors(const pvsc_lattice* lat, int R, int prec, uint64_t seed, void* out,
+                        void* stream);
+
 /* y = H x for a block of R vectors in precision prec (x, y: D*R complex).
  * x and y must not overlap.  No work buffer. */
 int pvsc_apply_H(const pvsc_lattice* lat, int R, int prec, const void* x, void* y, void* stream);

@@ -68,6 +68,7 @@ _SIGNATURES = {
     "pvsc_set_potential": (_i, [_vp, _vp, _vp]),
     "pvsc_get_potential": (_i, [_vp, _vp, _vp]),
     "pvsc_spectral_bounds": (_i, [_vp, _d, _dp, _dp, _dp, _dp, _vp, _sz, _vp]),
+    "pvsc_random_vectors": (_i, [_vp, _i, _i, _u64, _vp, _vp]),
     "pvsc_apply_H": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
     "pvsc_cheb_step": (_i, [_vp, _i, _i, _vp, _vp, _vp, _dp, _dp, _dp, _dp, _i, _vp, _vp, _sz, _vp]),
     "pvsc_kpm_moments": (_i, [_vp, _i, _i, _vp, _u64, _i, _d, _d, _vp, _vp, _sz, _vp]),
@@ -271,6 +272,14 @@ class Lattice:
 
 
 # ---------------------------------------------------------------------------- operations
+def random_vectors(lat: Lattice, R: int, prec: int, seed: int, stream=None) -> torch.Tensor:
+    """Random-phase block exp(2 pi i u)/sqrt(D) from the counter hash, shape (D, R)."""
+    out = torch.empty((lat.D, R), dtype=torch.complex128 if prec == C128 else torch.complex64,
+                      device="cuda")
+    _check(_lib.pvsc_random_vectors(lat.handle, R, prec, int(seed), _ptr(out), _stream(stream)))
+    return out
+
+
 def apply_H(lat: Lattice, x: torch.Tensor, y: torch.Tensor | None = None, stream=None):
     """y = H x."""
     y = torch.empty_like(x) if y is None else y

@@ -308,6 +308,14 @@ size_t pvsc_work_bytes(const pvsc_lattice* lat, int op, int R, int prec, int M) 
   }
 }
 
+int pvsc_random_vectors(const pvsc_lattice* lat, int R, int prec, uint64_t seed, void* out,
+                        void* stream) {
+  if (int rc = check_common(lat, R, prec)) return rc;
+  if (int rc = check_ptr(out, "out")) return rc;
+  const int64_t D = lat->g.n_sites * (lat->g.model == PVSC_TI ? 4 : 1);
+  return launch_random_phase(out, prec, D, R, seed, static_cast<cudaStream_t>(stream));
+}
+
 int pvsc_apply_H(const pvsc_lattice* lat, int R, int prec, const void* x, void* y, void* stream) {
   if (int rc = check_common(lat, R, prec)) return rc;
   if (int rc = check_ptr(x, "x")) return rc;
