@@ -174,6 +174,25 @@ int pvsc_cheb_step(const pvsc_lattice* lat, int R, int prec, const void* x, void
                    size_t work_bytes, void* stream);
 
 /*
+ * pvsc_cheb_step without a work buffer, for callers that cannot allocate
+ * device memory (a fixed memory budget owned by another pool, callbacks that
+ * must not call cudaMalloc because it can synchronise the device, hosts that
+ * forbid allocation after start-up).  The paper has no counterpart: this is a
+ * deployment variant of the fused step above, with identical arguments and
+ * results except `work`.  Its dot-product scratch is a 2 MiB array inside the
+ * library image; nothing is allocated.  Sizes that need more scratch than
+ * that (on a 152-SM GB300: R >= 32 with dots) are rejected with PVSC_ERR_ARG.
+ * The first call on a device looks up the array's device address (make it
+ * before any stream capture) and the current device must be the lattice's.
+ * All calls on a device share the array: calls whose kernels overlap on the
+ * GPU race, so order them on one stream.  With dot_flags == 0 it needs no
+ * scratch at all.
+ */
+int pvsc_cheb_step_noalloc(const pvsc_lattice* lat, int R, int prec, const void* x, void* y,
+                           void* z, const double* alpha, const double* beta, const double* gamma,
+                           const double* delta, int dot_flags, double* dots, void* stream);
+
+/*
  * Kernel polynomial method moments (Sec. 2.2, Sec. 4): for each of the R
  * start vectors r, mu_k = <r|T_k(H~)|r>, k = 0..M-1, H~ = (H - b)/a, through
  * the recurrence w_0 = r, w_1 = H~ w_0, w_{k+1} = 2 H~ w_k - w_{k-1}, fused

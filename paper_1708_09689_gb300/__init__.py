@@ -71,6 +71,7 @@ _SIGNATURES = {
     "pvsc_random_vectors": (_i, [_vp, _i, _i, _u64, _vp, _vp]),
     "pvsc_apply_H": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
     "pvsc_cheb_step": (_i, [_vp, _i, _i, _vp, _vp, _vp, _dp, _dp, _dp, _dp, _i, _vp, _vp, _sz, _vp]),
+    "pvsc_cheb_step_noalloc": (_i, [_vp, _i, _i, _vp, _vp, _vp, _dp, _dp, _dp, _dp, _i, _vp, _vp]),
     "pvsc_kpm_moments": (_i, [_vp, _i, _i, _vp, _u64, _i, _d, _d, _vp, _vp, _sz, _vp]),
     "pvsc_cheb_series": (_i, [_vp, _i, _i, _vp, _vp, _dp, _i, _dp, _d, _d, _vp, _sz, _vp]),
     "pvsc_cheb_filter": (_i, [_vp, _i, _i, _vp, _vp, _dp, _i, _d, _d, _vp, _sz, _vp]),
@@ -299,6 +300,21 @@ def cheb_step(lat: Lattice, x, y, alpha, beta, gamma=None, z=None, delta=None, d
         _darr(gamma) if gamma is not None else None, _darr(delta) if delta is not None else None,
         int(dots), _ptr(d), _ptr(work), 0 if work is None else work.numel(), _stream(stream)))
     return d
+
+
+def cheb_step_noalloc(lat: Lattice, x, y, alpha, beta, gamma=None, z=None, delta=None,
+                      dots: int = 0, out_dots: torch.Tensor | None = None, stream=None):
+    """cheb_step for callers that cannot allocate: no work buffer, the library's
+    static scratch holds the dot partials.  out_dots (float64 [4, R] on the
+    device) may be passed in so that this call allocates nothing either."""
+    R, prec = block_R(x), prec_of(x)
+    if dots and out_dots is None:
+        out_dots = torch.zeros((4, R), dtype=torch.float64, device=x.device)
+    _check(_lib.pvsc_cheb_step_noalloc(
+        lat.handle, R, prec, _ptr(x), _ptr(y), _ptr(z), _darr(alpha), _darr(beta),
+        _darr(gamma) if gamma is not None else None, _darr(delta) if delta is not None else None,
+        int(dots), _ptr(out_dots) if dots else None, _stream(stream)))
+    return out_dots if dots else None
 
 
 def kpm_moments(lat: Lattice, M: int, a: float, b: float, R: int = 1, prec: int = C128,
