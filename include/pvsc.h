@@ -301,6 +301,13 @@ size_t pvsc_work_bytes(const pvsc_lattice* lat, int op, int R, int prec, int M);
  * word, the kernel returns, and the call reports PVSC_ERR_TIMEOUT. */
 int pvsc_set_wait_limit(uint64_t spins);
 
+/* Fault injection for tests of the bounded waits: while enabled, the first
+ * dependency wait of every block in pvsc_kpm_moments_batched targets a phase
+ * that is never published, so it runs out after the wait limit and the call
+ * returns PVSC_ERR_TIMEOUT with the device context intact.  Host-side switch;
+ * nothing faults, traps or hangs.  Off by default. */
+int pvsc_debug_inject_stall(int enable);
+
 /*
  * Launch tuning.  A tuning entry fixes, for (lattice, op, R, prec), the
  * threads per block, the blocks per SM of the persistent grid and the z-slab

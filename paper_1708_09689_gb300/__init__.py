@@ -83,6 +83,7 @@ _SIGNATURES = {
     "pvsc_batched_work_bytes": (_sz, [ctypes.POINTER(_vp), _i, _i, _i, _i]),
     "pvsc_work_bytes": (_sz, [_vp, _i, _i, _i, _i]),
     "pvsc_set_wait_limit": (_i, [_u64]),
+    "pvsc_debug_inject_stall": (_i, [_i]),
     "pvsc_set_tuning": (_i, [_vp, _i, _i, ctypes.POINTER(Tuning)]),
     "pvsc_get_tuning": (_i, [_vp, _i, _i, ctypes.POINTER(Tuning)]),
     "pvsc_autotune": (_i, [_vp, _i, _i, ctypes.POINTER(Tuning), _vp]),
@@ -410,6 +411,16 @@ def kpm_moments_batched(lats, M, a, b, R=16, prec=C64, seeds=None, work=None, mu
 
 def set_wait_limit(spins: int):
     _check(_lib.pvsc_set_wait_limit(int(spins)))
+
+
+def inject_stall(enable: bool):
+    """Fault injection: make the batched kernel's first wait target an unpublished phase."""
+    _check(_lib.pvsc_debug_inject_stall(int(bool(enable))))
+
+
+def batched_work_bytes(lats, R, prec, M) -> int:
+    hs = (ctypes.c_void_p * len(lats))(*[l.handle.value for l in lats])
+    return int(_lib.pvsc_batched_work_bytes(hs, len(lats), R, prec, M))
 
 
 def library_path() -> str:

@@ -1,0 +1,165 @@
+// Launch-shape autotuner for the fused sweeps.
+//
+// The paper derives its spatial blocking from machine properties (the layer
+// condition, Sec. 3.1); here the launch shape of the z-marching sweep is
+// chosen by measurement instead: threads per block, resident blocks per SM
+// and z-slab depth are swept with CUDA events on the caller's stream, timing
+// the KPM-type sweep (recurrence update + fp64 dot products) that dominates
+// every recurrence, and the fastest shape is stored in the lattice handle.
+// With PVSC_TUNE_CACHE=<file> results are kept on disk, keyed by model,
+// dimensions, boundary conditions, R, precision and device name.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "sweep.cuh"
+
+namespace pvsc {
+
+static std::string cache_key(const pvsc_lattice* lat, int R, int prec) {
+  cudaDeviceProp prop;
+  std::string dev = "gpu";
+  if (cudaGetDeviceProperties(&prop, lat->device) == cudaSuccess) dev = prop.name;
+  for (auto& c : dev)
+    if (c == ' ') c = '_';
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%d %lld %lld %lld %d%d%d %d %d %s", lat->g.model, (long long)lat->g.L[0],
+           (long long)lat->g.L[1], (long long)lat->g.L[2], lat->g.per[0], lat->g.per[1], lat->g.per[2], R,
+           prec, dev.c_str());
+  return buf;
+}
+
+static bool cache_lookup(const std::string& key, pvsc_tuning* t) {
+  const char* path = std::getenv("PVSC_TUNE_CACHE");
+  if (!path || !path[0]) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[1024];
+  bool found = false;
+  while (std::fgets(line, sizeof(line), f)) {
+    char* bar = std::strchr(line, '|');
+    if (!bar) continue;
+    *bar = 0;
+    if (key != line) continue;
+    pvsc_tuning c;
+    if (std::sscanf(bar + 1, "%d %d %d %f", &c.threads, &c.blocks_per_sm, &c.zslab, &c.time_ms) == 4) {
+      *t = c;
+      found = true;
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+static void cache_store(const std::string& key, const pvsc_tuning& t) {
+  const char* path = std::getenv("PVSC_TUNE_CACHE");
+  if (!path || !path[0]) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s|%d %d %d %.6f\n", key.c_str(), t.threads, t.blocks_per_sm, t.zslab, t.time_ms);
+  std::fclose(f);
+}
+
+}  // namespace pvsc
+
+using namespace pvsc;
+
+extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* best, void* stream) {
+  if (int rc = check_lattice(lat)) return rc;
+  if (!valid_R(R)) return set_error(PVSC_ERR_ARG, "R = %d: must be 1, 2, 4, 8, 16, 32 or 64", R);
+  if (prec != PVSC_C128 && prec != PVSC_C64) return set_error(PVSC_ERR_ARG, "unknown precision %d", prec);
+  const std::string key = cache_key(lat, R, prec);
+  pvsc_tuning cached;
+  if (cache_lookup(key, &cached)) {
+    lat->tuning[{R, prec}] = cached;
+    if (best) *best = cached;
+    return PVSC_OK;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t vb = vec_bytes(lat, R, prec), wb = dots_work_bytes(lat, R);
+  void *x = nullptr, *y = nullptr, *work = nullptr;
+  double* dots = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = PVSC_OK;
+  auto cleanup = [&]() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(y);
+    cudaFree(work);
+    cudaFree(dots);
+  };
+  if (cudaMalloc(&x, vb) != cudaSuccess || cudaMalloc(&y, vb) != cudaSuccess ||
+      cudaMalloc(&work, wb) != cudaSuccess || cudaMalloc(&dots, sizeof(double) * 4 * R) != cudaSuccess) {
+    cleanup();
+    return set_error(PVSC_ERR_OOM, "autotune could not allocate its sweep vectors");
+  }
+  cudaMemsetAsync(x, 0, vb, st);
+  cudaMemsetAsync(y, 0, vb, st);
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int C = R / vpt_for(R, prec);
+  std::vector<int> threads_c, zslab_c = {0};
+  for (int t : {64, 128, 256})
+    if (t % C == 0 && t >= C) threads_c.push_back(t);
+  if (lat->g.model == PVSC_TI)
+    for (int z : {4, 8, 16, 32, 64})
+      if (z < lat->g.L[2]) zslab_c.push_back(z);
+  const std::vector<int> bps_c = {0, 1, 2};
+  auto saved = lat->tuning.find({R, prec});
+  const bool had = saved != lat->tuning.end();
+  const pvsc_tuning old = had ? saved->second : pvsc_tuning{};
+  pvsc_tuning win{256, 0, 0, 1e30f};
+  // time one candidate shape: one warm sweep, then the mean of three
+  auto time_one = [&](int th, int bps, int zs, float* ms) -> int {
+    lat->tuning[{R, prec}] = pvsc_tuning{th, bps, zs, 0.f};
+    Sweep p;
+    sweep_init(p, lat, R, prec);
+    for (int r = 0; r < R; ++r) {
+      p.coef[0][r] = 0.2;
+      p.coef[1][r] = 0.0;
+      p.coef[2][r] = -1.0;
+    }
+    p.x = x;
+    p.yin = y;
+    p.yout = y;
+    p.dot_flags = 3;
+    p.dot_mode = 0;
+    p.dots = dots;
+    p.counter = static_cast<unsigned*>(work);
+    p.partials = reinterpret_cast<double*>(static_cast<char*>(work) + kWorkHeader);
+    PVSC_CUDA_TRY(cudaMemsetAsync(work, 0, kWorkHeader, st));
+    if (int r = launch_sweep(lat, prec, F_DOTS, p, st)) return r;
+    PVSC_CUDA_TRY(cudaEventRecord(e0, st));
+    for (int rep = 0; rep < 3; ++rep)
+      if (int r = launch_sweep(lat, prec, F_DOTS, p, st)) return r;
+    PVSC_CUDA_TRY(cudaEventRecord(e1, st));
+    PVSC_CUDA_TRY(cudaEventSynchronize(e1));
+    PVSC_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= 3.f;
+    return PVSC_OK;
+  };
+  for (int th : threads_c) {
+    for (int bps : bps_c) {
+      for (int zs : zslab_c) {
+        float ms = 0.f;
+        if ((rc = time_one(th, bps, zs, &ms)) != PVSC_OK) break;
+        if (ms < win.time_ms) win = pvsc_tuning{th, bps, zs, ms};
+      }
+      if (rc != PVSC_OK) break;
+    }
+    if (rc != PVSC_OK) break;
+  }
+  cleanup();
+  if (rc != PVSC_OK) {
+    if (had) lat->tuning[{R, prec}] = old; else lat->tuning.erase({R, prec});
+    return rc;
+  }
+  lat->tuning[{R, prec}] = win;
+  cache_store(key, win);
+  if (best) *best = win;
+  return PVSC_OK;
+}

@@ -74,54 +74,6 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
                            : launch_sweep_c64(model, vpt, feat, grid, threads, p, st);
 }
 
-// ---------------------------------------------------------------- CUDA graph cache
-static bool graphs_enabled() {
-  const char* e = std::getenv("PVSC_NO_GRAPH");
-  return !(e && e[0] && e[0] != '0');
-}
-
-template <class F>
-static int run_graph(const pvsc_lattice* clat, const std::vector<uint64_t>& key, cudaStream_t st,
-                     F&& body) {
-  if (!graphs_enabled()) return body(st);
-  pvsc_lattice* lat = const_cast<pvsc_lattice*>(clat);
-  std::lock_guard<std::mutex> lk(lat->mu);
-  auto it = lat->graphs.find(key);
-  if (it == lat->graphs.end()) {
-    if (lat->graphs.size() >= 32) {
-      for (auto& kv : lat->graphs) {
-        cudaGraphExecDestroy(kv.second.exec);
-        cudaGraphDestroy(kv.second.graph);
-      }
-      lat->graphs.clear();
-    }
-    cudaStream_t cs;
-    PVSC_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) {
-      cudaStreamDestroy(cs);
-      return set_error(PVSC_ERR_CUDA, "graph capture failed to start: %s", cudaGetErrorString(e));
-    }
-    const int rc = body(cs);
-    Graph gr;
-    e = cudaStreamEndCapture(cs, &gr.graph);
-    cudaStreamDestroy(cs);
-    if (rc != PVSC_OK) {
-      if (gr.graph) cudaGraphDestroy(gr.graph);
-      return rc;
-    }
-    if (e != cudaSuccess) return set_error(PVSC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&gr.exec, gr.graph, 0);
-    if (e != cudaSuccess) {
-      cudaGraphDestroy(gr.graph);
-      return set_error(PVSC_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
-    }
-    it = lat->graphs.emplace(key, gr).first;
-  }
-  PVSC_CUDA_TRY(cudaGraphLaunch(it->second.exec, st));
-  return PVSC_OK;
-}
-
 static uint64_t bits(double d) {
   uint64_t u;
   std::memcpy(&u, &d, 8);

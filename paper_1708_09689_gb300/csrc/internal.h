@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdlib>
+
 #include <map>
 #include <mutex>
 #include <string>
@@ -38,6 +40,12 @@ struct Graph {
 };
 
 }  // namespace pvsc
+
+struct pvsc_lattice;
+namespace pvsc {
+template <class F>
+int run_graph(const pvsc_lattice* clat, const std::vector<uint64_t>& key, cudaStream_t st, F&& body);
+}
 
 struct pvsc_lattice {
   pvsc::Geometry g{};
@@ -91,5 +99,50 @@ int launch_neighbours(const Geometry& g, int64_t* nbr, cudaStream_t st);
 int launch_adjoint_top(const pvsc_lattice* lat, int R, const double2* G, double sr, double si,
                        double2* uM, const double2* w, double gscale, double* grad,
                        cudaStream_t st);
+
+// ---------------------------------------------------------------- CUDA graph cache
+inline bool graphs_enabled() {
+  const char* e = std::getenv("PVSC_NO_GRAPH");
+  return !(e && e[0] && e[0] != '0');
+}
+
+template <class F>
+int run_graph(const pvsc_lattice* clat, const std::vector<uint64_t>& key, cudaStream_t st,
+                     F&& body) {
+  if (!graphs_enabled()) return body(st);
+  pvsc_lattice* lat = const_cast<pvsc_lattice*>(clat);
+  std::lock_guard<std::mutex> lk(lat->mu);
+  auto it = lat->graphs.find(key);
+  if (it == lat->graphs.end()) {
+    if (lat->graphs.size() >= 32) {
+      for (auto& kv : lat->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaGraphDestroy(kv.second.graph);
+      }
+      lat->graphs.clear();
+    }
+    cudaStream_t cs;
+    PVSC_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cs);
+      return set_error(PVSC_ERR_CUDA, "graph capture failed to start: %s", cudaGetErrorString(e));
+    }
+    const int rc = body(cs);
+    Graph gr;
+    e = cudaStreamEndCapture(cs, &gr.graph);
+    cudaStreamDestroy(cs);
+    if (rc == PVSC_OK && e == cudaSuccess) e = cudaGraphInstantiate(&gr.exec, gr.graph, 0);
+    if (rc != PVSC_OK || e != cudaSuccess) {
+      // a launch the capture did not accept: run the same launches directly
+      if (gr.graph) cudaGraphDestroy(gr.graph);
+      cudaGetLastError();
+      return body(st);
+    }
+    it = lat->graphs.emplace(key, gr).first;
+  }
+  PVSC_CUDA_TRY(cudaGraphLaunch(it->second.exec, st));
+  return PVSC_OK;
+}
 
 }  // namespace pvsc

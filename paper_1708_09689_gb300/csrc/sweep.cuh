@@ -258,14 +258,126 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
 // and -i Gamma^{j+1} d is a signed permutation of d's components:
 //   j=x: ( d3,  d2, -d1, -d0)   j=y: -i (d3, d2, d1, d0)   j=z: (d1, -d0, d3, -d2).
 // Gamma^1 = diag(1,-1,1,-1) is a sign flip, so no multiply is spent on it.
+//
+// ti_march runs this along one column (x, y) of the lattice for planes
+// z0 <= z < z1 and vector chunk rc, handing every updated site to emit(s, xc,
+// yn).  NC selects the read-only (non-coherent) load path for x, valid only
+// when x is not written anywhere during the kernel.
+template <typename T, int VPT, bool NC, class Emit>
+__device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict__ X,
+                                         const T* __restrict__ Yin, int R, int rc, int64_t col,
+                                         int64_t z0, int64_t z1, const VecCoef<T, VPT>& cf,
+                                         Emit&& emit) {
+  const int64_t Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
+  const int64_t plane = Lx * Ly;
+  const int64_t x = col % Lx, y = col / Lx;
+  // in-plane neighbour columns (-1: absent)
+  const int64_t cxm = nbr_minus(col, x, Lx, g.per[0], 1);
+  const int64_t cxp = nbr_plus(col, x, Lx, g.per[0], 1);
+  const int64_t cym = nbr_minus(col, y, Ly, g.per[1], Lx);
+  const int64_t cyp = nbr_plus(col, y, Ly, g.per[1], Lx);
+  Blk<T, VPT> xm, xc, xp;
+  load_blk<T, VPT, NC>(X, col + plane * z0, R, rc, xc);
+  {
+    const int64_t zm = nbr_minus(z0, z0, Lz, g.per[2], 1);
+    if (zm >= 0) load_blk<T, VPT, NC>(X, col + plane * zm, R, rc, xm);
+    else zero_blk(xm);
+  }
+  for (int64_t z = z0; z < z1; ++z) {
+    const int64_t s = col + plane * z;
+    const int64_t zp = nbr_plus(z, z, Lz, g.per[2], 1);
+    if (zp >= 0) load_blk<T, VPT, NC>(X, col + plane * zp, R, rc, xp);
+    else zero_blk(xp);
+    Blk<T, VPT> yi;
+    if (Yin != nullptr) load_blk<T, VPT, false>(Yin, s, R, rc, yi);
+    const T Vs = T(site_potential(g, s));
+    Blk<T, VPT> S, D;
+    // z axis: s_z, d_z
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      cplx<T> d[4];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        S.v[o][v] = cadd(xm.v[o][v], xp.v[o][v]);
+        d[o] = csub(xm.v[o][v], xp.v[o][v]);
+      }
+      D.v[0][v] = d[1];
+      D.v[1][v] = {-d[0].re, -d[0].im};
+      D.v[2][v] = d[3];
+      D.v[3][v] = {-d[2].re, -d[2].im};
+    }
+    const int64_t zoff = plane * z;
+    // x axis
+    {
+      Blk<T, VPT> a, b;
+      if (cxm >= 0) load_blk<T, VPT, NC>(X, cxm + zoff, R, rc, a); else zero_blk(a);
+      if (cxp >= 0) load_blk<T, VPT, NC>(X, cxp + zoff, R, rc, b); else zero_blk(b);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        cplx<T> d[4];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          S.v[o][v] = cadd(S.v[o][v], cadd(a.v[o][v], b.v[o][v]));
+          d[o] = csub(a.v[o][v], b.v[o][v]);
+        }
+        D.v[0][v] = cadd(D.v[0][v], d[3]);
+        D.v[1][v] = cadd(D.v[1][v], d[2]);
+        D.v[2][v] = csub(D.v[2][v], d[1]);
+        D.v[3][v] = csub(D.v[3][v], d[0]);
+      }
+    }
+    // y axis: -i d = (d.im, -d.re)
+    {
+      Blk<T, VPT> a, b;
+      if (cym >= 0) load_blk<T, VPT, NC>(X, cym + zoff, R, rc, a); else zero_blk(a);
+      if (cyp >= 0) load_blk<T, VPT, NC>(X, cyp + zoff, R, rc, b); else zero_blk(b);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        cplx<T> d[4];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          S.v[o][v] = cadd(S.v[o][v], cadd(a.v[o][v], b.v[o][v]));
+          d[o] = csub(a.v[o][v], b.v[o][v]);
+        }
+        D.v[0][v] = cadd(D.v[0][v], cplx<T>{d[3].im, -d[3].re});
+        D.v[1][v] = cadd(D.v[1][v], cplx<T>{d[2].im, -d[2].re});
+        D.v[2][v] = cadd(D.v[2][v], cplx<T>{d[1].im, -d[1].re});
+        D.v[3][v] = cadd(D.v[3][v], cplx<T>{d[0].im, -d[0].re});
+      }
+    }
+    // y_new = d_o x_o + kt (Gamma^1 S + D)_o + gamma y_in,  d_o = alpha (V - beta) +- alpha m
+    Blk<T, VPT> yn;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const T e = fma(cf.alpha[v], Vs, -cf.ab[v]);
+      const T dp = e + cf.am[v], dm = e - cf.am[v];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const T dd = (o & 1) ? dm : dp;
+        const cplx<T> Tt = (o & 1) ? csub(D.v[o][v], S.v[o][v]) : cadd(D.v[o][v], S.v[o][v]);
+        T re = fma(cf.kt[v], Tt.re, dd * xc.v[o][v].re);
+        T im = fma(cf.kt[v], Tt.im, dd * xc.v[o][v].im);
+        if (Yin != nullptr) {
+          re = fma(cf.gamma[v], yi.v[o][v].re, re);
+          im = fma(cf.gamma[v], yi.v[o][v].im, im);
+        }
+        yn.v[o][v] = {re, im};
+      }
+    }
+    emit(s, xc, yn);
+    xm = xc;
+    xc = xp;
+  }
+}
+
 template <typename T, int VPT, int FEAT>
 __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p) {
-  const int64_t Lx = p.g.L[0], Ly = p.g.L[1], Lz = p.g.L[2];
-  const int64_t plane = Lx * Ly;
+  const int64_t plane = p.g.L[0] * p.g.L[1], Lz = p.g.L[2];
   const int R = p.R, C = p.C;
   const int rc = threadIdx.x % C;
   const VecCoef<T, VPT> cf = load_coef<T, VPT>(p, rc);
   const T* __restrict__ X = static_cast<const T*>(p.x);
+  const T* __restrict__ Yin = static_cast<const T*>(p.yin);
   double dacc[kNumDots][VPT];
 #pragma unroll
   for (int d = 0; d < kNumDots; ++d)
@@ -281,108 +393,12 @@ __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p)
     const int64_t bz = u / nbx, bx = u - bz * nbx;
     const int64_t tid = bx * blockDim.x + threadIdx.x;
     if (tid >= ncolthr) continue;
-    const int64_t col = tid / C;
-    const int64_t x = col % Lx, y = col / Lx;
-    // in-plane neighbour columns (-1: absent)
-    const int64_t cxm = nbr_minus(col, x, Lx, p.g.per[0], 1);
-    const int64_t cxp = nbr_plus(col, x, Lx, p.g.per[0], 1);
-    const int64_t cym = nbr_minus(col, y, Ly, p.g.per[1], Lx);
-    const int64_t cyp = nbr_plus(col, y, Ly, p.g.per[1], Lx);
     const int64_t z0 = bz * zs, z1 = min(z0 + (int64_t)zs, Lz);
-    Blk<T, VPT> xm, xc, xp;
-    load_blk<T, VPT, true>(X, col + plane * z0, R, rc, xc);
-    {
-      const int64_t zm = nbr_minus(z0, z0, Lz, p.g.per[2], 1);
-      if (zm >= 0) load_blk<T, VPT, true>(X, col + plane * zm, R, rc, xm);
-      else zero_blk(xm);
-    }
-    for (int64_t z = z0; z < z1; ++z) {
-      const int64_t s = col + plane * z;
-      const int64_t zp = nbr_plus(z, z, Lz, p.g.per[2], 1);
-      if (zp >= 0) load_blk<T, VPT, true>(X, col + plane * zp, R, rc, xp);
-      else zero_blk(xp);
-      Blk<T, VPT> yi;
-      if (p.yin != nullptr) load_blk<T, VPT, false>(static_cast<const T*>(p.yin), s, R, rc, yi);
-      const T Vs = T(site_potential(p.g, s));
-      Blk<T, VPT> S, D;
-      // z axis: s_z, d_z
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        cplx<T> d[4];
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          S.v[o][v] = cadd(xm.v[o][v], xp.v[o][v]);
-          d[o] = csub(xm.v[o][v], xp.v[o][v]);
-        }
-        D.v[0][v] = d[1];
-        D.v[1][v] = {-d[0].re, -d[0].im};
-        D.v[2][v] = d[3];
-        D.v[3][v] = {-d[2].re, -d[2].im};
-      }
-      // x axis
-      {
-        Blk<T, VPT> a, b;
-        const int64_t zoff = plane * z;
-        if (cxm >= 0) load_blk<T, VPT, true>(X, cxm + zoff, R, rc, a); else zero_blk(a);
-        if (cxp >= 0) load_blk<T, VPT, true>(X, cxp + zoff, R, rc, b); else zero_blk(b);
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-          cplx<T> d[4];
-#pragma unroll
-          for (int o = 0; o < 4; ++o) {
-            S.v[o][v] = cadd(S.v[o][v], cadd(a.v[o][v], b.v[o][v]));
-            d[o] = csub(a.v[o][v], b.v[o][v]);
-          }
-          D.v[0][v] = cadd(D.v[0][v], d[3]);
-          D.v[1][v] = cadd(D.v[1][v], d[2]);
-          D.v[2][v] = csub(D.v[2][v], d[1]);
-          D.v[3][v] = csub(D.v[3][v], d[0]);
-        }
-      }
-      // y axis: -i d = (d.im, -d.re)
-      {
-        Blk<T, VPT> a, b;
-        const int64_t zoff = plane * z;
-        if (cym >= 0) load_blk<T, VPT, true>(X, cym + zoff, R, rc, a); else zero_blk(a);
-        if (cyp >= 0) load_blk<T, VPT, true>(X, cyp + zoff, R, rc, b); else zero_blk(b);
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-          cplx<T> d[4];
-#pragma unroll
-          for (int o = 0; o < 4; ++o) {
-            S.v[o][v] = cadd(S.v[o][v], cadd(a.v[o][v], b.v[o][v]));
-            d[o] = csub(a.v[o][v], b.v[o][v]);
-          }
-          D.v[0][v] = cadd(D.v[0][v], cplx<T>{d[3].im, -d[3].re});
-          D.v[1][v] = cadd(D.v[1][v], cplx<T>{d[2].im, -d[2].re});
-          D.v[2][v] = cadd(D.v[2][v], cplx<T>{d[1].im, -d[1].re});
-          D.v[3][v] = cadd(D.v[3][v], cplx<T>{d[0].im, -d[0].re});
-        }
-      }
-      // y_new = d_o x_o + kt (Gamma^1 S + D)_o + gamma y_in,  d_o = alpha (V - beta) +- alpha m
-      Blk<T, VPT> yn;
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        const T e = fma(cf.alpha[v], Vs, -cf.ab[v]);
-        const T dp = e + cf.am[v], dm = e - cf.am[v];
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          const T dd = (o & 1) ? dm : dp;
-          const cplx<T> Tt = (o & 1) ? csub(D.v[o][v], S.v[o][v]) : cadd(D.v[o][v], S.v[o][v]);
-          T re = fma(cf.kt[v], Tt.re, dd * xc.v[o][v].re);
-          T im = fma(cf.kt[v], Tt.im, dd * xc.v[o][v].im);
-          if (p.yin != nullptr) {
-            re = fma(cf.gamma[v], yi.v[o][v].re, re);
-            im = fma(cf.gamma[v], yi.v[o][v].im, im);
-          }
-          yn.v[o][v] = {re, im};
-        }
-      }
-      const int64_t sites[4] = {s, s, s, s};
-      epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
-      xm = xc;
-      xc = xp;
-    }
+    ti_march<T, VPT, true>(p.g, X, Yin, R, rc, tid / C, z0, z1, cf,
+                           [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
+                             const int64_t sites[4] = {s, s, s, s};
+                             epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
+                           });
   }
   if constexpr ((FEAT & F_DOTS) != 0) reduce_dots<VPT>(p, dacc);
 }
