@@ -321,7 +321,17 @@ typedef struct {
   int32_t blocks_per_sm;
   int32_t zslab;
   float time_ms; /* measured time of one sweep, 0 if not measured */
+  int32_t vpt;   /* vectors per thread: 1, or 2 (complex64 with R >= 2); 0 = automatic */
+  int32_t tile_x; /* TI only: > 0 selects the shared-memory staged sweep (bulk-copy */
+  int32_t tile_y; /* engine, 4-plane ring) with tiles of tile_x x tile_y columns */
+  int32_t kernel; /* TI only: 0 z-marching in registers (or staged if tile_x > 0), */
+                  /* 1 flat (one site per thread and pass, neighbours folded in turn) */
 } pvsc_tuning;
+
+/* Device error word of the shared-memory staged sweeps: *flag = 1 if a copy
+ * wait ran out since the last clear (the sweep then stopped early and its
+ * outputs are invalid).  Synchronises the device.  clear != 0 resets it. */
+int pvsc_device_error(int* flag, int clear);
 int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tuning);
 int pvsc_get_tuning(const pvsc_lattice* lat, int R, int prec, pvsc_tuning* tuning);
 int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* best, void* stream);

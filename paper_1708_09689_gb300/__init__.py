@@ -55,7 +55,13 @@ class LatticeDesc(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("zslab", ctypes.c_int32), ("time_ms", ctypes.c_float)]
+                ("zslab", ctypes.c_int32), ("time_ms", ctypes.c_float), ("vpt", ctypes.c_int32),
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"threads": self.threads, "blocks_per_sm": self.blocks_per_sm, "zslab": self.zslab,
+                "time_ms": self.time_ms, "vpt": self.vpt, "tile_x": self.tile_x,
+                "tile_y": self.tile_y, "kernel": self.kernel}
 
 
 _vp, _i, _sz, _d, _u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_double, ctypes.c_uint64
@@ -256,21 +262,21 @@ class Lattice:
         _check(_lib.pvsc_debug_neighbours(self._h, _ptr(out), _stream(stream)))
         return out
 
-    def set_tuning(self, R: int, prec: int, threads: int = 256, blocks_per_sm: int = 0, zslab: int = 0):
-        t = Tuning(threads, blocks_per_sm, zslab, 0.0)
+    def set_tuning(self, R: int, prec: int, threads: int = 256, blocks_per_sm: int = 0,
+                   zslab: int = 0, vpt: int = 0, tile_x: int = 0, tile_y: int = 0,
+                   kernel: int = 0):
+        t = Tuning(threads, blocks_per_sm, zslab, 0.0, vpt, tile_x, tile_y, kernel)
         _check(_lib.pvsc_set_tuning(self._h, R, prec, ctypes.byref(t)))
 
     def get_tuning(self, R: int, prec: int) -> dict:
         t = Tuning()
         _check(_lib.pvsc_get_tuning(self._h, R, prec, ctypes.byref(t)))
-        return {"threads": t.threads, "blocks_per_sm": t.blocks_per_sm, "zslab": t.zslab,
-                "time_ms": t.time_ms}
+        return t.as_dict()
 
     def autotune(self, R: int, prec: int, stream=None) -> dict:
         t = Tuning()
         _check(_lib.pvsc_autotune(self._h, R, prec, ctypes.byref(t), _stream(stream)))
-        return {"threads": t.threads, "blocks_per_sm": t.blocks_per_sm, "zslab": t.zslab,
-                "time_ms": t.time_ms}
+        return t.as_dict()
 
 
 # ---------------------------------------------------------------------------- operations

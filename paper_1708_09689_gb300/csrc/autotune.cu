@@ -45,7 +45,8 @@ static bool cache_lookup(const std::string& key, pvsc_tuning* t) {
     *bar = 0;
     if (key != line) continue;
     pvsc_tuning c;
-    if (std::sscanf(bar + 1, "%d %d %d %f", &c.threads, &c.blocks_per_sm, &c.zslab, &c.time_ms) == 4) {
+    if (std::sscanf(bar + 1, "%d %d %d %f %d %d %d %d", &c.threads, &c.blocks_per_sm, &c.zslab,
+                    &c.time_ms, &c.vpt, &c.tile_x, &c.tile_y, &c.kernel) == 8) {
       *t = c;
       found = true;
     }
@@ -59,7 +60,8 @@ static void cache_store(const std::string& key, const pvsc_tuning& t) {
   if (!path || !path[0]) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s|%d %d %d %.6f\n", key.c_str(), t.threads, t.blocks_per_sm, t.zslab, t.time_ms);
+  std::fprintf(f, "%s|%d %d %d %.6f %d %d %d %d\n", key.c_str(), t.threads, t.blocks_per_sm, t.zslab,
+               t.time_ms, t.vpt, t.tile_x, t.tile_y, t.kernel);
   std::fclose(f);
 }
 
@@ -101,10 +103,9 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
   cudaMemsetAsync(y, 0, vb, st);
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int C = R / vpt_for(R, prec);
-  std::vector<int> threads_c, zslab_c = {0};
-  for (int t : {64, 128, 256})
-    if (t % C == 0 && t >= C) threads_c.push_back(t);
+  std::vector<int> vpt_c = {1};
+  if (prec == PVSC_C64 && R >= 2) vpt_c.push_back(2);
+  std::vector<int> zslab_c = {0};
   if (lat->g.model == PVSC_TI)
     for (int z : {4, 8, 16, 32, 64})
       if (z < lat->g.L[2]) zslab_c.push_back(z);
@@ -112,10 +113,10 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
   auto saved = lat->tuning.find({R, prec});
   const bool had = saved != lat->tuning.end();
   const pvsc_tuning old = had ? saved->second : pvsc_tuning{};
-  pvsc_tuning win{256, 0, 0, 1e30f};
+  pvsc_tuning win{256, 0, 0, 1e30f, 0, 0, 0, 0};
   // time one candidate shape: one warm sweep, then the mean of three
-  auto time_one = [&](int th, int bps, int zs, float* ms) -> int {
-    lat->tuning[{R, prec}] = pvsc_tuning{th, bps, zs, 0.f};
+  auto time_one = [&](const pvsc_tuning& cand, float* ms) -> int {
+    lat->tuning[{R, prec}] = cand;
     Sweep p;
     sweep_init(p, lat, R, prec);
     for (int r = 0; r < R; ++r) {
@@ -142,16 +143,37 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
     *ms /= 3.f;
     return PVSC_OK;
   };
-  for (int th : threads_c) {
-    for (int bps : bps_c) {
-      for (int zs : zslab_c) {
-        float ms = 0.f;
-        if ((rc = time_one(th, bps, zs, &ms)) != PVSC_OK) break;
-        if (ms < win.time_ms) win = pvsc_tuning{th, bps, zs, ms};
+  // candidate list: z-marching (all shapes), and for TI the flat, prefetching
+  // and shared-memory staged sweeps in a few shapes each
+  std::vector<pvsc_tuning> cands;
+  for (int vpt : vpt_c) {
+    const int C = R / vpt;
+    for (int th : {64, 128, 256}) {
+      if (th % C != 0 || th < C) continue;
+      for (int bps : bps_c)
+        for (int zs : zslab_c) cands.push_back(pvsc_tuning{th, bps, zs, 0.f, vpt, 0, 0, 0});
+      if (lat->g.model == PVSC_TI) {
+        cands.push_back(pvsc_tuning{th, 0, 0, 0.f, vpt, 0, 0, 1});
+        if (!(prec == PVSC_C64 && vpt == 1 && R > 1))
+          for (int zs : {0, 16}) cands.push_back(pvsc_tuning{th, 0, zs, 0.f, vpt, 0, 0, 2});
       }
-      if (rc != PVSC_OK) break;
     }
-    if (rc != PVSC_OK) break;
+  }
+  if (lat->g.model == PVSC_TI)
+    for (int th : {128, 256}) {
+      if (th % R) continue;
+      const int tiles[][2] = {{32, 8}, {16, 8}, {16, 4}, {8, 8}, {8, 4}, {4, 4}};
+      for (const auto& t : tiles)
+        if (t[0] * t[1] <= 2 * th && bulk_smem_bytes(t[0], t[1], R, prec) <= 200 * 1024)
+          cands.push_back(pvsc_tuning{th, 0, 0, 0.f, 1, t[0], t[1], 0});
+    }
+  for (const pvsc_tuning& cand : cands) {
+    float ms = 0.f;
+    if ((rc = time_one(cand, &ms)) != PVSC_OK) break;
+    if (ms < win.time_ms) {
+      win = cand;
+      win.time_ms = ms;
+    }
   }
   cleanup();
   if (rc != PVSC_OK) {

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
         }
         if (active) {
           // x is written by this kernel in other phases: coherent loads only (NC = false)
-          ti_march<T, VPT, false>(L.g, X, Yin, R, rc, col, z0, z1, cf,
+          ti_march<T, VPT, false, 0>(L.g, X, Yin, R, rc, col, z0, z1, cf, nullptr,
                                   [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
                                     store_blk<T, VPT>(Yout, s, R, rc, yn);
 #pragma unroll

@@ -113,6 +113,7 @@ struct Sweep {
   int M;
   int kpm_k;
   int zslab;             // TI z-marching depth
+  int tile_x, tile_y;    // TI shared-memory staged sweep: tile of columns (0: register marching)
 };
 
 enum AccMode { ACC_NONE = 0, ACC_INIT = 1, ACC_ADD = 2, ACC_FINAL = 4 };

@@ -22,8 +22,72 @@ static LaunchShape shape_for(const pvsc_lattice* lat, int R, int prec) {
     sh.threads = it->second.threads;
     sh.blocks_per_sm = it->second.blocks_per_sm;
     sh.zslab = it->second.zslab;
+    sh.vpt = it->second.vpt;
+    sh.tile_x = it->second.tile_x;
+    sh.tile_y = it->second.tile_y;
+    sh.kernel = it->second.kernel;
   }
   return sh;
+}
+
+// 4 halo plane slots + 4 y_in tile slots + 2 potential slots + 4 mbarriers
+size_t bulk_smem_bytes(int TX, int TY, int R, int prec) {
+  const size_t SB = (size_t)4 * R * (prec == PVSC_C128 ? 16 : 8);
+  return 4 * (size_t)(TX + 2) * (TY + 2) * SB + 4 * (size_t)TX * TY * SB +
+         2 * (size_t)TX * TY * sizeof(double) + 64;
+}
+
+int launch_sweep_bulk(int prec, int feat, int grid, int threads, size_t smem, const Sweep& p,
+                      cudaStream_t st) {
+  return prec == PVSC_C128 ? launch_sweep_bulk_c128(feat, grid, threads, smem, p, st)
+                           : launch_sweep_bulk_c64(feat, grid, threads, smem, p, st);
+}
+
+int occupancy_bulk(int prec, int feat, int threads, size_t smem, int* blocks) {
+  return prec == PVSC_C128 ? occupancy_bulk_c128(feat, threads, smem, blocks)
+                           : occupancy_bulk_c64(feat, threads, smem, blocks);
+}
+
+int bulk_sweep_error(int prec, int clear, int* flag) {
+  return prec == PVSC_C128 ? bulk_error_c128(clear, flag) : bulk_error_c64(clear, flag);
+}
+
+// The shared-memory staged TI sweep: tiles of TX x TY columns, z-slabs, one
+// vector per thread.
+static int launch_sweep_staged(const pvsc_lattice* lat, int prec, int feat, Sweep& p,
+                               const LaunchShape& sh, cudaStream_t st) {
+  int threads = sh.threads;
+  if (threads < 32 || threads > kMaxThreads || threads % 32 != 0 || threads % p.R != 0) threads = 256;
+  if (sh.tile_x * sh.tile_y > 2 * threads)
+    return set_error(PVSC_ERR_ARG, "staged tile %dx%d exceeds two sites per thread (%d threads)",
+                     sh.tile_x, sh.tile_y, threads);
+  p.C = p.R;
+  p.tile_x = sh.tile_x;
+  p.tile_y = sh.tile_y;
+  const size_t smem = bulk_smem_bytes(sh.tile_x, sh.tile_y, p.R, prec);
+  int occ = 0;
+  if (int rc = occupancy_bulk(prec, feat, threads, smem, &occ)) return rc;
+  if (occ < 1)
+    return set_error(PVSC_ERR_ARG, "staged sweep tile %dx%d needs %zu bytes of shared memory: too large",
+                     sh.tile_x, sh.tile_y, smem);
+  int bps = sh.blocks_per_sm;
+  if (bps <= 0 || bps > occ) bps = occ;
+  if (bps > kMaxGridPerSM) bps = kMaxGridPerSM;
+  const int64_t grid_max = (int64_t)lat->sm_count * bps;
+  const int64_t Lx = lat->g.L[0], Ly = lat->g.L[1], Lz = lat->g.L[2];
+  const int64_t ntiles = ((Lx + sh.tile_x - 1) / sh.tile_x) * ((Ly + sh.tile_y - 1) / sh.tile_y);
+  int64_t zs = sh.zslab;
+  if (zs <= 0) {
+    int64_t nz = (6 * grid_max + ntiles - 1) / ntiles;
+    if (nz < 1) nz = 1;
+    if (nz > Lz) nz = Lz;
+    zs = (Lz + nz - 1) / nz;
+  }
+  if (zs > Lz) zs = Lz;
+  p.zslab = (int)zs;
+  const int64_t units = ntiles * ((Lz + zs - 1) / zs);
+  const int grid = (int)(units < grid_max ? units : grid_max);
+  return launch_sweep_bulk(prec, feat, grid, threads, smem, p, st);
 }
 
 void sweep_init(Sweep& p, const pvsc_lattice* lat, int R, int prec) {
@@ -36,13 +100,19 @@ void sweep_init(Sweep& p, const pvsc_lattice* lat, int R, int prec) {
 }
 
 int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStream_t st) {
-  const int vpt = vpt_for(p.R, prec);
-  p.C = p.R / vpt;
   const LaunchShape sh = shape_for(lat, p.R, prec);
+  if (lat->g.model == PVSC_TI && sh.tile_x > 0 && sh.tile_y > 0)
+    return launch_sweep_staged(lat, prec, feat, p, sh, st);
+  const int vpt = vpt_tuned(sh.vpt, p.R, prec);
+  p.C = p.R / vpt;
   int threads = sh.threads;
   if (threads < 32 || threads > kMaxThreads || threads % 32 != 0 || threads % p.C != 0) threads = 256;
   int occ = 0;
-  const int model = lat->g.model;
+  const bool flat = lat->g.model == PVSC_TI && sh.kernel == 1;
+  // the prefetch ring moves 16-byte granules: not for complex64 with one vector of R > 1
+  const bool async = lat->g.model == PVSC_TI && sh.kernel == 2 &&
+                     !(prec == PVSC_C64 && vpt == 1 && p.R > 1);
+  const int model = flat ? kModelTIFlat : (async ? kModelTIAsync : lat->g.model);
   int rc = prec == PVSC_C128 ? occupancy_c128(model, feat, threads, &occ)
                              : occupancy_c64(model, vpt, feat, threads, &occ);
   if (rc) return rc;
@@ -52,7 +122,9 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
   if (bps > kMaxGridPerSM) bps = kMaxGridPerSM;
   const int64_t grid_max = (int64_t)lat->sm_count * bps;
   int64_t units;
-  if (model == PVSC_TI) {
+  if (flat) {
+    units = (lat->g.n_sites * p.C + threads - 1) / threads;
+  } else if (lat->g.model == PVSC_TI) {
     const int64_t plane = lat->g.L[0] * lat->g.L[1], Lz = lat->g.L[2];
     const int64_t nbx = (plane * p.C + threads - 1) / threads;
     int64_t zs = sh.zslab;
@@ -550,16 +622,37 @@ int pvsc_cheb_adjoint_step(const pvsc_lattice* lat, int R, int prec, const void*
   return PVSC_OK;
 }
 
+int pvsc_device_error(int* flag, int clear) {
+  if (!flag) return set_error(PVSC_ERR_ARG, "flag is NULL");
+  PVSC_CUDA_TRY(cudaDeviceSynchronize());
+  int a = 0, b = 0;
+  if (int rc = bulk_sweep_error(PVSC_C128, clear, &a)) return rc;
+  if (int rc = bulk_sweep_error(PVSC_C64, clear, &b)) return rc;
+  *flag = (a || b) ? 1 : 0;
+  return PVSC_OK;
+}
+
 int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tuning) {
   if (int rc = check_common(lat, R, prec)) return rc;
   if (!tuning) {
     lat->tuning.erase({R, prec});
     return PVSC_OK;
   }
-  const int C = R / vpt_for(R, prec);
+  if (tuning->vpt < 0 || tuning->vpt > 2) return set_error(PVSC_ERR_ARG, "vpt must be 0, 1 or 2");
+  if (tuning->kernel < 0 || tuning->kernel > 2) return set_error(PVSC_ERR_ARG, "kernel must be 0, 1 or 2");
+  const int C = R / vpt_tuned(tuning->vpt, R, prec);
   if (tuning->threads < 32 || tuning->threads > kMaxThreads || tuning->threads % 32 || tuning->threads % C)
     return set_error(PVSC_ERR_ARG, "threads must be a multiple of 32 and of R/VPT = %d, at most %d", C, kMaxThreads);
-  if (tuning->blocks_per_sm < 0 || tuning->zslab < 0) return set_error(PVSC_ERR_ARG, "negative tuning value");
+  if (tuning->blocks_per_sm < 0 || tuning->zslab < 0 || tuning->tile_x < 0 || tuning->tile_y < 0)
+    return set_error(PVSC_ERR_ARG, "negative tuning value");
+  if (tuning->tile_x > 0 || tuning->tile_y > 0) {
+    if (lat->g.model != PVSC_TI || tuning->tile_x < 1 || tuning->tile_y < 1)
+      return set_error(PVSC_ERR_ARG, "a staged tile needs a TI lattice and tile_x, tile_y >= 1");
+    if (tuning->threads % R) return set_error(PVSC_ERR_ARG, "staged sweeps need threads %% R == 0");
+    if (bulk_smem_bytes(tuning->tile_x, tuning->tile_y, R, prec) > 200 * 1024)
+      return set_error(PVSC_ERR_ARG, "staged tile %dx%d does not fit in shared memory", tuning->tile_x,
+                       tuning->tile_y);
+  }
   lat->tuning[{R, prec}] = *tuning;
   return PVSC_OK;
 }
@@ -575,6 +668,10 @@ int pvsc_get_tuning(const pvsc_lattice* lat, int R, int prec, pvsc_tuning* tunin
     tuning->blocks_per_sm = 0;
     tuning->zslab = 0;
     tuning->time_ms = 0.f;
+    tuning->vpt = vpt_for(R, prec);
+    tuning->tile_x = 0;
+    tuning->tile_y = 0;
+    tuning->kernel = 0;
   }
   return PVSC_OK;
 }

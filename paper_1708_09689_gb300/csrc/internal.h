@@ -32,7 +32,37 @@ struct LaunchShape {
   int threads = 256;
   int blocks_per_sm = 0;  // 0: occupancy maximum
   int zslab = 0;          // 0: automatic
+  int vpt = 0;            // 0: automatic
+  int tile_x = 0;         // > 0: shared-memory staged TI sweep with this tile
+  int tile_y = 0;
+  int kernel = 0;         // TI: 0 z-marching / staged, 1 flat
 };
+
+// kernel-selector "model" values of the flat and the cp.async-prefetching TI
+// sweeps in the launch tables
+constexpr int kModelTIFlat = 3;
+constexpr int kModelTIAsync = 4;
+constexpr int kAsyncDepth = 2;  // planes in flight per thread in the prefetching sweep
+inline size_t async_ring_bytes(int threads) { return (size_t)(kAsyncDepth + 1) * 2 * 4 * threads * 16; }
+int allow_max_smem(void* fn);
+
+// shared-memory staged TI sweep (sweep_c128.cu / sweep_c64.cu)
+int launch_sweep_bulk(int prec, int feat, int grid, int threads, size_t smem, const Sweep& p,
+                      cudaStream_t st);
+int launch_sweep_bulk_c128(int feat, int grid, int threads, size_t smem, const Sweep& p,
+                           cudaStream_t st);
+int launch_sweep_bulk_c64(int feat, int grid, int threads, size_t smem, const Sweep& p,
+                          cudaStream_t st);
+int occupancy_bulk_c128(int feat, int threads, size_t smem, int* blocks);
+int occupancy_bulk_c64(int feat, int threads, size_t smem, int* blocks);
+int bulk_error_c128(int clear, int* flag);
+int bulk_error_c64(int clear, int* flag);
+int occupancy_bulk(int prec, int feat, int threads, size_t smem, int* blocks);
+int bulk_sweep_error(int prec, int clear, int* flag);
+size_t bulk_smem_bytes(int TX, int TY, int R, int prec);
+
+// Vectors per thread for (R, prec) under an optional tuned value.
+int vpt_tuned(int tuned, int R, int prec);
 
 struct Graph {
   cudaGraph_t graph = nullptr;

@@ -30,6 +30,12 @@ bool valid_R(int R) {
 
 int vpt_for(int R, int prec) { return (prec == PVSC_C64 && R >= 2) ? 2 : 1; }
 
+int vpt_tuned(int tuned, int R, int prec) {
+  if (tuned == 1) return 1;
+  if (tuned == 2 && prec == PVSC_C64 && R >= 2) return 2;
+  return vpt_for(R, prec);
+}
+
 int check_lattice(const pvsc_lattice* lat) {
   if (!lat) return set_error(PVSC_ERR_ARG, "lattice handle is NULL");
   return PVSC_OK;

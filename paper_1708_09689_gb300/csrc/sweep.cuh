@@ -47,14 +47,23 @@ __device__ __forceinline__ void load_blk(const T* __restrict__ base, int64_t s, 
       double2 a = RO ? __ldg(q) : *q;
       b.v[o][0] = {a.x, a.y};
     }
-  } else if constexpr (VPT == 1) {  // complex64, R == 1: 32 contiguous bytes
-    const float4* q = reinterpret_cast<const float4*>(p);
-    float4 a = RO ? __ldg(q) : q[0];
-    float4 c = RO ? __ldg(q + 1) : q[1];
-    b.v[0][0] = {a.x, a.y};
-    b.v[1][0] = {a.z, a.w};
-    b.v[2][0] = {c.x, c.y};
-    b.v[3][0] = {c.z, c.w};
+  } else if constexpr (VPT == 1) {
+    if (R == 1) {  // complex64, R == 1: 32 contiguous bytes
+      const float4* q = reinterpret_cast<const float4*>(p);
+      float4 a = RO ? __ldg(q) : q[0];
+      float4 c = RO ? __ldg(q + 1) : q[1];
+      b.v[0][0] = {a.x, a.y};
+      b.v[1][0] = {a.z, a.w};
+      b.v[2][0] = {c.x, c.y};
+      b.v[3][0] = {c.z, c.w};
+    } else {  // complex64, one vector per thread: 8 bytes per orbital, coalesced across r
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const float2* q = reinterpret_cast<const float2*>(p + 2 * o * R);
+        float2 a = RO ? __ldg(q) : *q;
+        b.v[o][0] = {a.x, a.y};
+      }
+    }
   } else {  // complex64, two vectors per 16 bytes
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
@@ -75,9 +84,15 @@ __device__ __forceinline__ void store_blk(T* __restrict__ base, int64_t s, int R
     for (int o = 0; o < 4; ++o)
       *reinterpret_cast<double2*>(p + 2 * o * R) = make_double2(b.v[o][0].re, b.v[o][0].im);
   } else if constexpr (VPT == 1) {
-    float4* q = reinterpret_cast<float4*>(p);
-    q[0] = make_float4(b.v[0][0].re, b.v[0][0].im, b.v[1][0].re, b.v[1][0].im);
-    q[1] = make_float4(b.v[2][0].re, b.v[2][0].im, b.v[3][0].re, b.v[3][0].im);
+    if (R == 1) {
+      float4* q = reinterpret_cast<float4*>(p);
+      q[0] = make_float4(b.v[0][0].re, b.v[0][0].im, b.v[1][0].re, b.v[1][0].im);
+      q[1] = make_float4(b.v[2][0].re, b.v[2][0].im, b.v[3][0].re, b.v[3][0].im);
+    } else {
+#pragma unroll
+      for (int o = 0; o < 4; ++o)
+        *reinterpret_cast<float2*>(p + 2 * o * R) = make_float2(b.v[o][0].re, b.v[o][0].im);
+    }
   } else {
 #pragma unroll
     for (int o = 0; o < 4; ++o)
@@ -263,11 +278,70 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
 // z0 <= z < z1 and vector chunk rc, handing every updated site to emit(s, xc,
 // yn).  NC selects the read-only (non-coherent) load path for x, valid only
 // when x is not written anywhere during the kernel.
-template <typename T, int VPT, bool NC, class Emit>
+//
+// With DEPTH > 0 the HBM stream of the column (plane z+1 of x and y_in of
+// plane z) is prefetched DEPTH planes ahead with cp.async into a per-thread
+// shared-memory ring of DEPTH+1 slots, so every thread keeps DEPTH planes of
+// loads in flight without holding them in registers.  Each thread only reads
+// the slots it filled itself, so the ring needs no block barrier.  Ring layout:
+// 16-byte granule k of slot q, buffer b (0 x, 1 y_in) of thread t at
+// ((((q * 2 + b) * 4 + k) * nthr) + t) * 16 bytes (conflict-free).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Issue the 16-byte granules of one block (4 orbitals x VPT vectors) of site s.
+template <typename T, int VPT>
+__device__ __forceinline__ void ring_issue(unsigned char* buf, int nthr, const T* base, int64_t s,
+                                           int R, int rc) {
+  const T* p = base + 2 * ((s * 4) * (int64_t)R + rc * VPT);
+  if constexpr (sizeof(T) == 4 && VPT == 1) {  // complex64, R == 1: 2 granules
+    cp_async16(buf, p);
+    cp_async16(buf + (size_t)nthr * 16, p + 4);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cp_async16(buf + (size_t)k * nthr * 16, p + 2 * k * R);
+  }
+}
+
+template <typename T, int VPT>
+__device__ __forceinline__ void ring_read(const unsigned char* buf, int nthr, Blk<T, VPT>& b) {
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const double2 a = *reinterpret_cast<const double2*>(buf + (size_t)o * nthr * 16);
+      b.v[o][0] = {a.x, a.y};
+    }
+  } else if constexpr (VPT == 2) {
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const float4 a = *reinterpret_cast<const float4*>(buf + (size_t)o * nthr * 16);
+      b.v[o][0] = {a.x, a.y};
+      b.v[o][1] = {a.z, a.w};
+    }
+  } else {
+    const float4 a = *reinterpret_cast<const float4*>(buf);
+    const float4 c = *reinterpret_cast<const float4*>(buf + (size_t)nthr * 16);
+    b.v[0][0] = {a.x, a.y};
+    b.v[1][0] = {a.z, a.w};
+    b.v[2][0] = {c.x, c.y};
+    b.v[3][0] = {c.z, c.w};
+  }
+}
+
+template <typename T, int VPT, bool NC, int DEPTH, class Emit>
 __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict__ X,
                                          const T* __restrict__ Yin, int R, int rc, int64_t col,
                                          int64_t z0, int64_t z1, const VecCoef<T, VPT>& cf,
-                                         Emit&& emit) {
+                                         unsigned char* ring, Emit&& emit) {
   const int64_t Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
   const int64_t plane = Lx * Ly;
   const int64_t x = col % Lx, y = col / Lx;
@@ -283,14 +357,47 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
     if (zm >= 0) load_blk<T, VPT, NC>(X, col + plane * zm, R, rc, xm);
     else zero_blk(xm);
   }
+  const int nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  // prefetch group i: x of plane z0+i+1 and y_in of plane z0+i into slot i % (DEPTH+1)
+  auto ring_group = [&](int64_t i) {
+    if constexpr (DEPTH > 0) {
+      if (z0 + i < z1) {
+        unsigned char* sl = ring + ((size_t)((i % (DEPTH + 1)) * 2) * 4 * nthr + tid) * 16;
+        const int64_t zq = nbr_plus(z0 + i, z0 + i, Lz, g.per[2], 1);
+        if (zq >= 0) ring_issue<T, VPT>(sl, nthr, X, col + plane * zq, R, rc);
+        if (Yin != nullptr) ring_issue<T, VPT>(sl + (size_t)4 * nthr * 16, nthr, Yin, col + plane * (z0 + i), R, rc);
+      }
+      cp_async_commit();
+    }
+  };
+  if constexpr (DEPTH > 0)
+    for (int i = 0; i < DEPTH; ++i) ring_group(i);
   for (int64_t z = z0; z < z1; ++z) {
     const int64_t s = col + plane * z;
     const int64_t zp = nbr_plus(z, z, Lz, g.per[2], 1);
-    if (zp >= 0) load_blk<T, VPT, NC>(X, col + plane * zp, R, rc, xp);
-    else zero_blk(xp);
     Blk<T, VPT> yi;
-    if (Yin != nullptr) load_blk<T, VPT, false>(Yin, s, R, rc, yi);
+    if constexpr (DEPTH > 0) {
+      const int64_t i = z - z0;
+      ring_group(i + DEPTH);
+      cp_async_wait<DEPTH>();  // group i has landed (own slots only: no barrier)
+      const unsigned char* sl = ring + ((size_t)((i % (DEPTH + 1)) * 2) * 4 * nthr + tid) * 16;
+      if (zp >= 0) ring_read<T, VPT>(sl, nthr, xp);
+      else zero_blk(xp);
+      if (Yin != nullptr) ring_read<T, VPT>(sl + (size_t)4 * nthr * 16, nthr, yi);
+    } else {
+      if (zp >= 0) load_blk<T, VPT, NC>(X, col + plane * zp, R, rc, xp);
+      else zero_blk(xp);
+      if (Yin != nullptr) load_blk<T, VPT, false>(Yin, s, R, rc, yi);
+    }
     const T Vs = T(site_potential(g, s));
+    // issue the four in-plane neighbour loads together (one L1/L2 round trip)
+    const int64_t zoff = plane * z;
+    Blk<T, VPT> ax, bx, ay, by;
+    if (cxm >= 0) load_blk<T, VPT, NC>(X, cxm + zoff, R, rc, ax); else zero_blk(ax);
+    if (cxp >= 0) load_blk<T, VPT, NC>(X, cxp + zoff, R, rc, bx); else zero_blk(bx);
+    if (cym >= 0) load_blk<T, VPT, NC>(X, cym + zoff, R, rc, ay); else zero_blk(ay);
+    if (cyp >= 0) load_blk<T, VPT, NC>(X, cyp + zoff, R, rc, by); else zero_blk(by);
     Blk<T, VPT> S, D;
     // z axis: s_z, d_z
 #pragma unroll
@@ -306,12 +413,10 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
       D.v[2][v] = d[3];
       D.v[3][v] = {-d[2].re, -d[2].im};
     }
-    const int64_t zoff = plane * z;
     // x axis
     {
-      Blk<T, VPT> a, b;
-      if (cxm >= 0) load_blk<T, VPT, NC>(X, cxm + zoff, R, rc, a); else zero_blk(a);
-      if (cxp >= 0) load_blk<T, VPT, NC>(X, cxp + zoff, R, rc, b); else zero_blk(b);
+      const Blk<T, VPT>& a = ax;
+      const Blk<T, VPT>& b = bx;
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
         cplx<T> d[4];
@@ -328,9 +433,8 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
     }
     // y axis: -i d = (d.im, -d.re)
     {
-      Blk<T, VPT> a, b;
-      if (cym >= 0) load_blk<T, VPT, NC>(X, cym + zoff, R, rc, a); else zero_blk(a);
-      if (cyp >= 0) load_blk<T, VPT, NC>(X, cyp + zoff, R, rc, b); else zero_blk(b);
+      const Blk<T, VPT>& a = ay;
+      const Blk<T, VPT>& b = by;
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
         cplx<T> d[4];
@@ -370,8 +474,9 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
   }
 }
 
-template <typename T, int VPT, int FEAT>
+template <typename T, int VPT, int FEAT, int DEPTH = 0>
 __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p) {
+  extern __shared__ __align__(16) unsigned char ring[];  // DEPTH > 0: cp.async prefetch ring
   const int64_t plane = p.g.L[0] * p.g.L[1], Lz = p.g.L[2];
   const int R = p.R, C = p.C;
   const int rc = threadIdx.x % C;
@@ -394,11 +499,100 @@ __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p)
     const int64_t tid = bx * blockDim.x + threadIdx.x;
     if (tid >= ncolthr) continue;
     const int64_t z0 = bz * zs, z1 = min(z0 + (int64_t)zs, Lz);
-    ti_march<T, VPT, true>(p.g, X, Yin, R, rc, tid / C, z0, z1, cf,
+    ti_march<T, VPT, true, DEPTH>(p.g, X, Yin, R, rc, tid / C, z0, z1, cf, ring,
                            [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
                              const int64_t sites[4] = {s, s, s, s};
                              epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
                            });
+  }
+  if constexpr ((FEAT & F_DOTS) != 0) reduce_dots<VPT>(p, dacc);
+}
+
+// Flat TI sweep: one (site, vector chunk) per thread and pass, no state
+// carried between planes.  The six neighbours are folded into S and D one at
+// a time (each load consumed at once), which keeps the register footprint
+// small enough for several blocks per SM; neighbour reuse comes from L1 (x)
+// and L2 (y, z).
+template <typename T, int VPT, int FEAT>
+__global__ void __launch_bounds__(256, 2) ti_sweep_flat(const __grid_constant__ Sweep p) {
+  const int64_t Lx = p.g.L[0], Ly = p.g.L[1], Lz = p.g.L[2];
+  const int64_t plane = Lx * Ly;
+  const int R = p.R, C = p.C;
+  const int rc = threadIdx.x % C;
+  const VecCoef<T, VPT> cf = load_coef<T, VPT>(p, rc);
+  const T* __restrict__ X = static_cast<const T*>(p.x);
+  const T* __restrict__ Yin = static_cast<const T*>(p.yin);
+  double dacc[kNumDots][VPT];
+#pragma unroll
+  for (int d = 0; d < kNumDots; ++d)
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) dacc[d][v] = 0.0;
+  const int64_t nthr = p.g.n_sites * C;
+  for (int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tid < nthr;
+       tid += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = tid / C;
+    const int64_t col = s % plane, z = s / plane, x = col % Lx, y = col / Lx;
+    Blk<T, VPT> xc, S, D, a;
+    load_blk<T, VPT, true>(X, s, R, rc, xc);
+    zero_blk(S);
+    zero_blk(D);
+    // fold one neighbour: S += a, D += sg * P_axis(a)
+    auto fold = [&](int axis, T sg) {
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+#pragma unroll
+        for (int o = 0; o < 4; ++o) S.v[o][v] = cadd(S.v[o][v], a.v[o][v]);
+        if (axis == 2) {  // z: (d1, -d0, d3, -d2)
+          D.v[0][v].re += sg * a.v[1][v].re; D.v[0][v].im += sg * a.v[1][v].im;
+          D.v[1][v].re -= sg * a.v[0][v].re; D.v[1][v].im -= sg * a.v[0][v].im;
+          D.v[2][v].re += sg * a.v[3][v].re; D.v[2][v].im += sg * a.v[3][v].im;
+          D.v[3][v].re -= sg * a.v[2][v].re; D.v[3][v].im -= sg * a.v[2][v].im;
+        } else if (axis == 0) {  // x: (d3, d2, -d1, -d0)
+          D.v[0][v].re += sg * a.v[3][v].re; D.v[0][v].im += sg * a.v[3][v].im;
+          D.v[1][v].re += sg * a.v[2][v].re; D.v[1][v].im += sg * a.v[2][v].im;
+          D.v[2][v].re -= sg * a.v[1][v].re; D.v[2][v].im -= sg * a.v[1][v].im;
+          D.v[3][v].re -= sg * a.v[0][v].re; D.v[3][v].im -= sg * a.v[0][v].im;
+        } else {  // y: -i (d3, d2, d1, d0), -i d = (d.im, -d.re)
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            D.v[o][v].re += sg * a.v[3 - o][v].im;
+            D.v[o][v].im -= sg * a.v[3 - o][v].re;
+          }
+        }
+      }
+    };
+    const int64_t nb[6] = {nbr_minus(s, z, Lz, p.g.per[2], plane), nbr_plus(s, z, Lz, p.g.per[2], plane),
+                           nbr_minus(s, x, Lx, p.g.per[0], 1),     nbr_plus(s, x, Lx, p.g.per[0], 1),
+                           nbr_minus(s, y, Ly, p.g.per[1], Lx),    nbr_plus(s, y, Ly, p.g.per[1], Lx)};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      if (nb[k] < 0) continue;
+      load_blk<T, VPT, true>(X, nb[k], R, rc, a);
+      fold(k < 2 ? 2 : (k < 4 ? 0 : 1), (k & 1) ? T(-1) : T(1));
+    }
+    Blk<T, VPT> yi;
+    if (Yin != nullptr) load_blk<T, VPT, false>(Yin, s, R, rc, yi);
+    const T Vs = T(site_potential(p.g, s));
+    Blk<T, VPT> yn;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const T e = fma(cf.alpha[v], Vs, -cf.ab[v]);
+      const T dp = e + cf.am[v], dm = e - cf.am[v];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const T dd = (o & 1) ? dm : dp;
+        const cplx<T> Tt = (o & 1) ? csub(D.v[o][v], S.v[o][v]) : cadd(D.v[o][v], S.v[o][v]);
+        T re = fma(cf.kt[v], Tt.re, dd * xc.v[o][v].re);
+        T im = fma(cf.kt[v], Tt.im, dd * xc.v[o][v].im);
+        if (Yin != nullptr) {
+          re = fma(cf.gamma[v], yi.v[o][v].re, re);
+          im = fma(cf.gamma[v], yi.v[o][v].im, im);
+        }
+        yn.v[o][v] = {re, im};
+      }
+    }
+    const int64_t sites[4] = {s, s, s, s};
+    epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
   }
   if constexpr ((FEAT & F_DOTS) != 0) reduce_dots<VPT>(p, dacc);
 }

@@ -1,12 +1,21 @@
-// complex128 storage, fp64 arithmetic: kernel instantiations and launchers.
+// complex128 storage, fp64 arithmetic: kernel instantiations and launchers
+// (register-marching, flat, cp.async-prefetching and shared-memory staged TI
+// sweeps; graphene sweep).
+#include <mutex>
+#include <set>
+
 #include "internal.h"
 #include "sweep.cuh"
+#include "sweep_bulk.cuh"
 
 namespace pvsc {
 
 template <int MODEL, int FEAT>
 static void* kernel_c128() {
   if constexpr (MODEL == 1) return reinterpret_cast<void*>(&ti_sweep<double, 1, FEAT>);
+  else if constexpr (MODEL == kModelTIFlat) return reinterpret_cast<void*>(&ti_sweep_flat<double, 1, FEAT>);
+  else if constexpr (MODEL == kModelTIAsync)
+    return reinterpret_cast<void*>(&ti_sweep<double, 1, FEAT, kAsyncDepth>);
   else return reinterpret_cast<void*>(&gr_sweep<double, 1, FEAT>);
 }
 
@@ -24,22 +33,92 @@ static void* pick_c128(int feat) {
 }
 
 static void* pick(int model, int feat) {
-  return model == 1 ? pick_c128<1>(feat) : pick_c128<2>(feat);
+  switch (model) {
+    case 1: return pick_c128<1>(feat);
+    case kModelTIFlat: return pick_c128<kModelTIFlat>(feat);
+    case kModelTIAsync: return pick_c128<kModelTIAsync>(feat);
+    default: return pick_c128<2>(feat);
+  }
+}
+
+// Opt a kernel into the device's full dynamic shared memory (once per kernel).
+int allow_max_smem(void* fn) {
+  static std::mutex mu;
+  static std::set<void*> done;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(fn)) return PVSC_OK;
+  int dev = 0, optin = 0;
+  PVSC_CUDA_TRY(cudaGetDevice(&dev));
+  PVSC_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  PVSC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+  PVSC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes));
+  done.insert(fn);
+  return PVSC_OK;
 }
 
 int launch_sweep_c128(int model, int feat, int grid, int threads, const Sweep& p,
                       cudaStream_t st) {
   void* fn = pick(model, feat);
   if (!fn) return set_error(PVSC_ERR_UNSUPPORTED, "no complex128 sweep for feature set %d", feat);
+  const size_t smem = model == kModelTIAsync ? async_ring_bytes(threads) : 0;
+  if (smem)
+    if (int rc = allow_max_smem(fn)) return rc;
   void* args[] = {const_cast<Sweep*>(&p)};
-  PVSC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, 0, st));
+  PVSC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, st));
   return PVSC_OK;
 }
 
 int occupancy_c128(int model, int feat, int threads, int* blocks) {
   void* fn = pick(model, feat);
   if (!fn) return set_error(PVSC_ERR_UNSUPPORTED, "no complex128 sweep for feature set %d", feat);
-  PVSC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, threads, 0));
+  const size_t smem = model == kModelTIAsync ? async_ring_bytes(threads) : 0;
+  if (smem)
+    if (int rc = allow_max_smem(fn)) return rc;
+  PVSC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, threads, smem));
+  return PVSC_OK;
+}
+
+// ---------------------------------------------------------------- shared-memory staged TI sweep
+static void* pick_bulk_c128(int feat) {
+  switch (feat) {
+    case 0: return reinterpret_cast<void*>(&ti_sweep_bulk<double, 0>);
+    case F_DOTS: return reinterpret_cast<void*>(&ti_sweep_bulk<double, F_DOTS>);
+    case F_Z: return reinterpret_cast<void*>(&ti_sweep_bulk<double, F_Z>);
+    case F_DOTS | F_Z: return reinterpret_cast<void*>(&ti_sweep_bulk<double, F_DOTS | F_Z>);
+    case F_ACC: return reinterpret_cast<void*>(&ti_sweep_bulk<double, F_ACC>);
+    case F_ADJ: return reinterpret_cast<void*>(&ti_sweep_bulk<double, F_ADJ>);
+    default: return nullptr;
+  }
+}
+
+int launch_sweep_bulk_c128(int feat, int grid, int threads, size_t smem, const Sweep& p,
+                           cudaStream_t st) {
+  void* fn = pick_bulk_c128(feat);
+  if (!fn) return set_error(PVSC_ERR_UNSUPPORTED, "no staged complex128 sweep for feature set %d", feat);
+  if (int rc = allow_max_smem(fn)) return rc;
+  void* args[] = {const_cast<Sweep*>(&p)};
+  PVSC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, st));
+  return PVSC_OK;
+}
+
+int occupancy_bulk_c128(int feat, int threads, size_t smem, int* blocks) {
+  void* fn = pick_bulk_c128(feat);
+  if (!fn) return set_error(PVSC_ERR_UNSUPPORTED, "no staged complex128 sweep for feature set %d", feat);
+  if (int rc = allow_max_smem(fn)) return rc;
+  PVSC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, threads, smem));
+  return PVSC_OK;
+}
+
+int bulk_error_c128(int clear, int* flag) {
+  int h = 0;
+  PVSC_CUDA_TRY(cudaMemcpyFromSymbol(&h, g_bulk_sweep_error, sizeof(int)));
+  if (clear) {
+    const int z = 0;
+    PVSC_CUDA_TRY(cudaMemcpyToSymbol(g_bulk_sweep_error, &z, sizeof(int)));
+  }
+  *flag = h;
   return PVSC_OK;
 }
 

@@ -88,6 +88,92 @@ def test_autotune_picks_a_valid_shape_and_results_do_not_change():
     assert np.max(np.abs(after - before)) < 1e-13
 
 
+STAGED_CASES = [((9, 11, 13), (0, 1, 1)), ((16, 8, 5), (1, 1, 0)), ((1, 2, 3), (1, 1, 1)),
+                ((5, 1, 4), (1, 1, 0)), ((2, 7, 2), (1, 0, 1))]
+
+
+@pytest.mark.parametrize("dims,per", STAGED_CASES)
+@pytest.mark.parametrize("R", [1, 2, 8, 16])
+@pytest.mark.parametrize("prec", [pv.C128, pv.C64])
+def test_staged_sweep_matches_oracle(dims, per, R, prec):
+    """The shared-memory staged sweep (bulk copies, halo tiles, ragged tiles,
+    wrapped periodic halos, open edges) against the oracle, with dots."""
+    n = int(np.prod(dims))
+    V = W.disorder_potential(n, 2.0, 9)
+    lat = pv.Lattice.ti(dims, per, disorder=(2.0, 9))
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
+    cdt = torch.complex128 if prec == pv.C128 else torch.complex64
+    tol = 1e-12 if prec == pv.C128 else 2e-6
+    x = torch.from_numpy(W.gaussian_block(lat.D, R, 1)).to("cuda", cdt)
+    y0 = torch.from_numpy(W.gaussian_block(lat.D, R, 2)).to("cuda", cdt)
+    xh = x.cpu().numpy().astype(np.complex128)
+    yh = y0.cpu().numpy().astype(np.complex128)
+    yr, _, dr = O.cheb_step(H, xh, yh, [0.3] * R, [0.1] * R, [-1.0] * R)
+    tried = 0
+    for tile in [(4, 2), (3, 5), (8, 4), (2, 2)]:
+        try:
+            lat.set_tuning(R, prec, threads=128 if R <= 8 else 256, zslab=2, tile_x=tile[0],
+                           tile_y=tile[1])
+        except pv.PvscError as e:
+            assert "shared memory" in str(e)  # tile too large for this R and precision
+            continue
+        tried += 1
+        y = y0.clone()
+        d = pv.cheb_step(lat, x, y, [0.3] * R, [0.1] * R, [-1.0] * R, dots=7).cpu().numpy()
+        yy = y.cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(yy - yr) / np.linalg.norm(yr) < tol, tile
+        assert np.max(np.abs(d[0] - dr[:, 0].real)) < 10 * tol * np.abs(dr).max()
+        assert np.max(np.abs(d[1] - dr[:, 1].real)) < 10 * tol * np.abs(dr).max()
+        ya = pv.apply_H(lat, x).cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(ya - H @ xh) / np.linalg.norm(H @ xh) < tol
+    assert tried >= 2
+    flag = pv.ctypes.c_int()
+    assert pv.lib().pvsc_device_error(pv.ctypes.byref(flag), 1) == 0 and flag.value == 0
+
+
+def test_staged_kpm_and_series_match_oracle():
+    dims, per = (12, 10, 9), (1, 1, 0)
+    n = int(np.prod(dims))
+    lat = pv.Lattice.ti(dims, per, disorder=(1.0, 4))
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, W.disorder_potential(n, 1.0, 4))
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    for prec, tol in ((pv.C128, 1e-12), (pv.C64, 1e-4)):
+        lat.set_tuning(8, prec, threads=256, zslab=3, tile_x=8, tile_y=4)
+        mu = pv.kpm_moments(lat, 32, a, b, R=8, prec=prec, seed=3).cpu().numpy()
+        ref = O.kpm_moments(H, W.random_phase_block(4 * n, 8, 3), 32, a, b).real
+        assert np.max(np.abs(mu - ref)) < tol
+        x = W.gaussian_block(4 * n, 8, 5)
+        g = np.cos(0.3 * np.arange(9))
+        y = pv.cheb_filter(lat, torch.from_numpy(x).cuda(), g, a, b, prec=prec).cpu().numpy()
+        ref_y = O.cheb_series(H, x, g, a, b)
+        assert np.linalg.norm(y - ref_y) / np.linalg.norm(ref_y) < (1e-12 if prec == pv.C128 else 1e-5)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("dims,per", STAGED_CASES)
+@pytest.mark.parametrize("R", [1, 2, 8, 64])
+@pytest.mark.parametrize("prec", [pv.C128, pv.C64])
+def test_flat_and_prefetching_sweeps_match_oracle(kernel, dims, per, R, prec):
+    n = int(np.prod(dims))
+    V = W.disorder_potential(n, 2.0, 9)
+    lat = pv.Lattice.ti(dims, per, disorder=(2.0, 9))
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
+    cdt = torch.complex128 if prec == pv.C128 else torch.complex64
+    tol = 1e-12 if prec == pv.C128 else 2e-6
+    x = torch.from_numpy(W.gaussian_block(lat.D, R, 1)).to("cuda", cdt)
+    y0 = torch.from_numpy(W.gaussian_block(lat.D, R, 2)).to("cuda", cdt)
+    xh = x.cpu().numpy().astype(np.complex128)
+    yr, _, dr = O.cheb_step(H, xh, y0.cpu().numpy().astype(np.complex128), [0.3] * R, [0.1] * R,
+                            [-1.0] * R)
+    for th, zs in ((128, 2), (256, 0)):
+        lat.set_tuning(R, prec, threads=th, zslab=zs, kernel=kernel)
+        y = y0.clone()
+        d = pv.cheb_step(lat, x, y, [0.3] * R, [0.1] * R, [-1.0] * R, dots=7).cpu().numpy()
+        yy = y.cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(yy - yr) / np.linalg.norm(yr) < tol
+        assert np.max(np.abs(d[1] - dr[:, 1].real)) < 10 * tol * np.abs(dr).max()
+
+
 def test_explicit_tuning_shapes_all_agree():
     lat = pv.Lattice.ti((9, 11, 13), (0, 1, 1), disorder=(1.0, 8))
     x = torch.from_numpy(W.gaussian_block(lat.D, 16, 1)).cuda().to(torch.complex64)
