@@ -39,6 +39,22 @@ import workloads as W  # noqa: E402
 METRIC = "stencil GLUP/s & %HBM roofline: FP32/batched vs plain FP64, same accuracy"
 UNIT = "GLUP/s"
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the benchmark
+# kernel at the benchmark size, from the ncu capture summarised in
+# profiles/ti_sweep_c64_R8_ncu.md (a half-depth slab, scaled by the number of sites).  It is
+# reported only while the kernel sources still hash to the captured version.
+TRAFFIC = {("ti_slab", 8): {"bytes_per_launch": 3.28e9, "source_sha256_16": "6d54dfb9db53f7ad"}}
+KERNEL_SOURCES = ("paper_1708_09689_gb300/csrc/sweep.cuh", "paper_1708_09689_gb300/csrc/common.cuh")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -57,6 +73,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default launch shape instead of the autotuned one")
+    ap.add_argument("--sweeps-only", type=int, default=0,
+                    help="profiling case: run this many complex64 KPM-type sweeps (stencil, "
+                         "recurrence, dots) on the lattice and exit without timing")
+    ap.add_argument("--launch", default=None,
+                    help="JSON launch shape (threads, blocks_per_sm, zslab, vpt, tile_x, tile_y, kernel) "
+                         "to use instead of autotuning, e.g. for profiling runs")
     return ap.parse_args()
 
 
@@ -211,8 +233,22 @@ def main():
 
     # ---- device-resident run (headline)
     stream = torch.cuda.current_stream()
-    # launch shape: autotuned once, outside the timed region
-    tuning = None if args.no_autotune else lat.autotune(R, pv.C64)
+    # launch shape: autotuned once, outside the timed region (or given)
+    if args.launch:
+        shape = {k: v for k, v in json.loads(args.launch).items() if k != "time_ms"}
+        lat.set_tuning(R, pv.C64, **shape)
+        tuning = lat.get_tuning(R, pv.C64)
+    else:
+        tuning = None if args.no_autotune else lat.autotune(R, pv.C64)
+    if args.sweeps_only:
+        x = pv.random_vectors(lat, R, pv.C64, seed)
+        y = pv.random_vectors(lat, R, pv.C64, seed + 1)
+        w = pv.work_buffer(lat.work_bytes(pv.OP_CHEB_STEP, R, pv.C64), dev)
+        for _ in range(args.sweeps_only):
+            pv.cheb_step(lat, x, y, [2.0 / a] * R, [b] * R, [-1.0] * R, dots=3, work=w)
+        torch.cuda.synchronize()
+        print(json.dumps({"sweeps": args.sweeps_only, "dims": list(dims), "R": R, "launch": tuning}))
+        return 0
     # start block: random-phase vectors from the counter hash, generated on the device
     r0 = pv.random_vectors(lat, R, pv.C64, seed)
     work = pv.work_buffer(lat.work_bytes(pv.OP_KPM, R, pv.C64, M), dev)
@@ -248,13 +284,10 @@ def main():
                 "kernel": "ti_sweep<float,2,F_DOTS> (complex64 KPM sweep)",
                 "bytes_per_lup": bytes_per_lup, "peak_kind": f"{peak_kind} hbm_gbs",
                 "launch_ms": round(sweep_ms, 4)}
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            tr = json.load(f).get(f"ti_slab_c64_R{R}")
-        if tr:
-            roofline["traffic"] = tr
-    except (OSError, ValueError):
-        pass
+    tr = TRAFFIC.get(("ti_slab", R)) if tuple(dims) == tuple(W.CONFIG_TI_SLAB.dims) else None
+    if tr and tr["source_sha256_16"] == kernel_source_hash():
+        roofline["traffic"] = tr["bytes_per_launch"]
+        roofline["traffic_over_algorithmic"] = round(tr["bytes_per_launch"] / (bytes_per_lup * n_sites * R), 3)
 
     # ---- complex128 / fp64 comparison (same lattice, same start block, fewer moments)
     compare = None

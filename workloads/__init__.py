@@ -139,19 +139,32 @@ def qdot_potential(Nx: int, Ny: int, ndots: int, R_dot: float, V0: float,
     Dots sit on a square grid of spacing D_dot = 4 R_dot (the paper's 10 nm
     radius : 40 nm spacing), centred in the sample.
     """
-    X, Y = graphene_positions(Nx, Ny)
     Xe, Ye = graphene_extent(Nx, Ny)
     Xc, Yc = Xe / 2.0, Ye / 2.0
     D_dot = 4.0 * R_dot
-    V = np.zeros_like(X)
+    # S is evaluated within R_dot + 20 w of each dot centre and taken as 0 beyond,
+    # where it is below exp(-40) V0 (about 4e-18 V0).
+    r_cut = R_dot + 20.0 * w
+    V = np.zeros((Ny, Nx, 4))
     for l in range(ndots):
         for k in range(ndots):
             Rx = Xc + (l - (ndots - 1) / 2.0) * D_dot
             Ry = Yc + (k - (ndots - 1) / 2.0) * D_dot
             Vk = V0 + dV * abs(k - ndots / 2.0)
+            cy0 = max(int(np.floor((Rx - r_cut - 2.0) / 3.0)), 0)
+            cy1 = min(int(np.ceil((Rx + r_cut) / 3.0)) + 1, Ny)
+            cx0 = max(int(np.floor((Ry - r_cut - SQRT3) / SQRT3)), 0)
+            cx1 = min(int(np.ceil((Ry + r_cut) / SQRT3)) + 1, Nx)
+            if cy0 >= cy1 or cx0 >= cx1:
+                continue
+            CY, CX = np.meshgrid(np.arange(cy0, cy1, dtype=np.float64),
+                                 np.arange(cx0, cx1, dtype=np.float64), indexing="ij")
+            X = 3.0 * CY[..., None] + _CELL_OFFSETS[None, None, :, 0]
+            Y = SQRT3 * CX[..., None] + _CELL_OFFSETS[None, None, :, 1]
             d = np.hypot(X - Rx, Y - Ry)
-            V += Vk * 0.5 * (1.0 + np.tanh((R_dot - d) / w))
-    return V
+            S = np.where(d < r_cut, 0.5 * (1.0 + np.tanh((R_dot - d) / w)), 0.0)
+            V[cy0:cy1, cx0:cx1, :] += Vk * S
+    return V.reshape(-1)
 
 
 def dirac_point() -> tuple[float, float]:
