@@ -73,6 +73,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default launch shape instead of the autotuned one")
+    ap.add_argument("--workload", default="ti_slab",
+                    choices=["ti_slab", "ti_cube", "graphene_qd", "batched", "adjoint"],
+                    help="ti_slab (default): the benchmark line; the others measure the remaining "
+                         "workloads (16^3 cube KPM, graphene QD-array propagation, batched KPM over "
+                         "64 lattices, adjoint gradient) and print one JSON line each")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="profiling case: run this many complex64 KPM-type sweeps (stencil, "
                          "recurrence, dots) on the lattice and exit without timing")
@@ -203,6 +208,189 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------------- other workloads
+def _timed(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _hbm_roof(bytes_per_lup, lups, ms, kernel):
+    peak, kind = measured_peaks()
+    achieved = bytes_per_lup * lups / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "kernel": kernel,
+            "bytes_per_lup": bytes_per_lup, "peak_kind": f"{kind} hbm_gbs"}
+
+
+def run_workload(args, pv, dev, rank, world):
+    """The remaining workloads, one JSON line each (single GPU; rank 0 prints)."""
+    import torch
+    from paper_1708_09689_gb300.sharding import max_over_ranks
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(dev.index or 0)
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    if args.workload == "ti_cube":
+        cfg = W.CONFIG_TI_CUBE
+        lat = pv.Lattice.ti(cfg.dims, cfg.periodic, t=cfg.t, m=cfg.m, disorder=(cfg.W, cfg.seed_V))
+        emin, emax, a, b = lat.spectral_bounds()
+        lat.autotune(1, pv.C128)
+        v = torch.from_numpy(W.gaussian_block(cfg.D, 1, 1)).to(dev)
+        y = torch.empty_like(v)
+        work = pv.work_buffer(lat.work_bytes(pv.OP_KPM, 1, pv.C128, cfg.M), dev)
+        mu = torch.empty((1, cfg.M), dtype=torch.float64, device=dev)
+
+        def step():
+            pv.apply_H(lat, v, y)
+            pv.kpm_moments(lat, cfg.M, a, b, R=1, prec=pv.C128, seed=cfg.seed_r, work=work, mu=mu)
+        for _ in range(args.warmup):
+            step()
+        clocks.start()
+        ms = max_over_ranks(_timed(step, args.steps, stream), dev)
+        clk = clocks.stop()
+        lups = cfg.n_sites * (1 + cfg.M // 2)
+        line.update({"workload": "ti_cube", "value": round(world * lups / (ms * 1e-3) / 1e9, 3),
+                     "ms_per_step": round(ms, 4), "dtype": "c128",
+                     "config": {"workload": "TI 16^3 periodic, W=1: one H.v + 256 KPM moments (R=1)",
+                                "l2": "whole state L2-resident (< 1 MiB): a latency workload, no % roof"},
+                     "roofline": None, "clocks": clk, "gpu_launches": args.steps * (2 + cfg.M // 2),
+                     "mu_0": float(mu[0, 0].item())})
+    elif args.workload == "graphene_qd":
+        cfg = W.CONFIG_GRAPHENE_QD
+        lat = pv.Lattice.graphene(cfg.cells, (0, 0), t=cfg.t, V=cfg.potential())
+        emin, emax, a, b = lat.spectral_bounds()
+        nterms = len(pv.propagation_coeffs(a * cfg.dt, cfg.trunc))
+        psi0 = torch.from_numpy(cfg.packet()).to(dev)
+        nsteps = args.steps if args.steps > 5 else cfg.nsteps
+        res = {}
+        for prec, name in ((pv.C64, "c64"), (pv.C128, "c128")):
+            lat.autotune(1, prec)
+            work = pv.work_buffer(lat.work_bytes(pv.OP_SERIES, 1, prec, nterms), dev)
+            psi = psi0.clone()
+            pv.cheb_propagate(lat, psi, cfg.dt, 1, a, b, cfg.trunc, prec=prec, work=work)  # warm
+            psi = psi0.clone()
+            n = nsteps if prec == pv.C64 else max(nsteps // 5, 1)
+            if prec == pv.C64:
+                clocks.start()
+            ms = _timed(lambda: pv.cheb_propagate(lat, psi, cfg.dt, n, a, b, cfg.trunc, prec=prec,
+                                                  work=work), 1, stream)
+            if prec == pv.C64:
+                clk = clocks.stop()
+            ms = max_over_ranks(ms, dev)
+            res[name] = (psi, n, ms)
+        psi64, n64, ms64 = res["c64"]
+        psi128, n128, ms128 = res["c128"]
+        lups = cfg.n_sites * (nterms - 1)
+        v64 = lups * n64 / (ms64 * 1e-3) / 1e9
+        v128 = lups * n128 / (ms128 * 1e-3) / 1e9
+        # same number of steps in both precisions for the state error
+        p64 = psi0.clone()
+        pv.cheb_propagate(lat, p64, cfg.dt, n128, a, b, cfg.trunc, prec=pv.C64)
+        line.update({"workload": "graphene_qd", "value": round(world * v64, 3),
+                     "ms_per_step": round(ms64 / n64, 4), "steps": n64, "dtype": "c64",
+                     "config": {"workload": "graphene 4096x2048 four-site cells (2^25 sites), open, 8x8 "
+                                            "QD array V0=0.1 R=40 w=5, Gaussian packet, dt=1, trunc 1e-14",
+                                "sweeps_per_time_step": nterms - 1},
+                     "roofline": _hbm_roof(64.0, lups, ms64 / n64,
+                                           "gr_sweep<float,1,F_ACC> (complex64 w, complex128 accumulator)"),
+                     "compare_fp64": {"c128_glups": round(v128, 3), "c64_over_c128": round(v64 / v128, 2),
+                                      "c128_steps": n128,
+                                      "norm_drift_c64": abs(torch.linalg.vector_norm(psi64).item() - 1),
+                                      "norm_drift_c128": abs(torch.linalg.vector_norm(psi128).item() - 1),
+                                      "c64_vs_c128_state_err": torch.linalg.vector_norm(p64 - psi128).item()},
+                     "clocks": clk, "gpu_launches": (nterms) * n64})
+    elif args.workload == "batched":
+        specs = W.batched_lattices()
+        lats = [pv.Lattice.ti((L, L, L), (1, 1, 1), disorder=(Wd, s)) for L, Wd, s in specs]
+        ab = [lat.spectral_bounds()[2:] for lat in lats]
+        R, M = 16, 1024
+        seeds = [vector_seed_for(i, rank) for i in range(len(lats))]
+        work = pv.work_buffer(pv.batched_work_bytes(lats, R, pv.C64, M), dev)
+        mu = torch.empty((len(lats), R, M), dtype=torch.float64, device=dev)
+        run = lambda: pv.kpm_moments_batched(lats, M, [x[0] for x in ab], [x[1] for x in ab], R=R,
+                                             prec=pv.C64, seeds=seeds, work=work, mu=mu)
+        for _ in range(args.warmup):
+            run()
+        clocks.start()
+        ms = max_over_ranks(_timed(run, args.steps, stream), dev)
+        clk = clocks.stop()
+        sites = sum(L ** 3 for L, _, _ in specs)
+        lups = sites * R * (M // 2)
+        line.update({"workload": "batched", "value": round(world * lups / (ms * 1e-3) / 1e9, 3),
+                     "ms_per_step": round(ms, 3), "steps": args.steps, "dtype": "c64",
+                     "config": {"workload": "64 periodic TI cubes, L from {24,32,48,64,96}, W~U[0,5), R=16, "
+                                            "1024 moments, one persistent cooperative launch in a CUDA graph",
+                                "sites": sites, "mu0_min": float(mu[:, :, 0].min().item())},
+                     "roofline": _hbm_roof(96.0 + 8.0 / R, lups, ms, "kpm_batched_kernel<float,2>"),
+                     "clocks": clk, "gpu_launches": args.steps})
+    elif args.workload == "adjoint":
+        cfg = W.CONFIG_GRAPHENE_ADJ
+        V = cfg.potential()
+        lat = pv.Lattice.graphene(cfg.cells, (0, 0), V=V)
+        emin, emax, a, b = lat.spectral_bounds()
+        lat.autotune(1, pv.C128)
+        psi0 = torch.from_numpy(cfg.packet()).to(dev)
+        mask = torch.from_numpy(cfg.detector()).to(dev)
+        Vt = torch.tensor(V, dtype=torch.float64, device=dev, requires_grad=True)
+
+        def fwd_bwd():
+            Vt.grad = None
+            psi = pv.propagate_with_grad(Vt, psi0, lat, cfg.dt, cfg.nsteps, a, b,
+                                         every=W.ADJ_CHECKPOINT_EVERY)
+            loss = (psi.abs() ** 2 * mask).sum()
+            loss.backward()
+            return loss
+        loss = fwd_bwd()
+        clocks.start()
+        t0 = time.perf_counter()
+        loss = fwd_bwd()
+        torch.cuda.synchronize()
+        secs = max_over_ranks(time.perf_counter() - t0, dev)
+        clk = clocks.stop()
+        g = Vt.grad.cpu().numpy()
+        # central differences at 32 seeded sites, h = 1e-6
+        rng = np.random.default_rng(W.ADJ_FD_SEED)
+        sites = rng.choice(len(V), W.ADJ_FD_SITES, replace=False)
+        work = pv.work_buffer(lat.work_bytes(pv.OP_SERIES, 1, pv.C128, 32), dev)
+
+        def L(Vv):
+            lat.set_potential(torch.from_numpy(Vv).to(dev))
+            p = psi0.clone()
+            pv.cheb_propagate(lat, p, cfg.dt, cfg.nsteps, a, b, prec=pv.C128, work=work)
+            return float((p.abs() ** 2 * mask).sum().item())
+        errs = []
+        for s in sites:
+            Vp, Vm = V.copy(), V.copy()
+            Vp[s] += W.ADJ_FD_H
+            Vm[s] -= W.ADJ_FD_H
+            fd = (L(Vp) - L(Vm)) / (2 * W.ADJ_FD_H)
+            errs.append(abs(fd - g[s]) / max(abs(g).max(), 1e-300))
+        nterms = len(pv.propagation_coeffs(a * cfg.dt, cfg.trunc))
+        lups = cfg.n_sites * (nterms - 1) * cfg.nsteps * 4  # forward, recompute, reverse (~2 sweeps)
+        line.update({"workload": "adjoint", "value": round(lups / secs / 1e9, 3),
+                     "ms_per_step": round(1000 * secs, 1), "dtype": "c128",
+                     "config": {"workload": "graphene 1024x512 cells (2^21 sites), 4x4 QD R=30 V0=0.1, 200 steps, "
+                                            "checkpoints every 20, loss = detector probability"},
+                     "loss": float(loss.item()), "fd_sites": len(sites),
+                     "fd_max_err_rel_to_max_grad": float(max(errs)),
+                     "seconds_fwd_bwd": round(secs, 3), "roofline": None, "clocks": clk})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def vector_seed_for(unit, rank):
+    from paper_1708_09689_gb300.sharding import vector_seed
+    return vector_seed(100 + 1000 * rank, unit)
+
+
 # --------------------------------------------------------------------------- native
 def main():
     args = parse()
@@ -216,13 +404,17 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     import paper_1708_09689_gb300 as pv
+    from paper_1708_09689_gb300.sharding import max_over_ranks, vector_seed
+
+    if args.workload != "ti_slab":
+        return run_workload(args, pv, dev, rank, world)
 
     dims, R, M, Wd = tuple(args.dims), args.R, args.M, args.W
     n_sites = dims[0] * dims[1] * dims[2]
     D = 4 * n_sites
     lat = pv.Lattice.ti(dims, (1, 1, 0), t=1.0, m=2.0, disorder=(Wd, 2))
     emin, emax, a, b = lat.spectral_bounds(0.01)
-    seed = 3 + 1000 * rank
+    seed = vector_seed(3, rank)  # each rank owns its own block of random vectors
     sweeps = (M + 1) // 2
     lups_per_step = n_sites * R * sweeps
 
@@ -267,10 +459,7 @@ def main():
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     value = world * lups_per_step / (ms * 1e-3) / 1e9
     mu64 = mu.clone()
 
@@ -326,11 +515,7 @@ def main():
             pv.kpm_moments(lat, M, a, b, r0=r0_dev, work=work, mu=mu)
             mu_host.copy_(mu, non_blocking=True)
         barrier()
-        te = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks((time.perf_counter() - t0) / args.steps, dev)
         e2e = {"value": round(world * lups_per_step / te / 1e9, 3), "unit": UNIT,
                "h2d_bytes_per_step": r0.numel() * 8, "d2h_bytes_per_step": R * M * 8}
 
