@@ -101,6 +101,45 @@ __device__ __forceinline__ void store_blk(T* __restrict__ base, int64_t s, int R
   }
 }
 
+// As load_blk, from a precomputed pointer to the block's first element
+// (p = base + 2 ((s * 4) R + rc VPT)); orbital o sits 2 o R reals further.
+template <typename T, int VPT, bool RO>
+__device__ __forceinline__ void load_at(const T* __restrict__ p, int R, Blk<T, VPT>& b) {
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const double2* q = reinterpret_cast<const double2*>(p + 2 * o * R);
+      double2 a = RO ? __ldg(q) : *q;
+      b.v[o][0] = {a.x, a.y};
+    }
+  } else if constexpr (VPT == 1) {
+    if (R == 1) {
+      const float4* q = reinterpret_cast<const float4*>(p);
+      float4 a = RO ? __ldg(q) : q[0];
+      float4 c = RO ? __ldg(q + 1) : q[1];
+      b.v[0][0] = {a.x, a.y};
+      b.v[1][0] = {a.z, a.w};
+      b.v[2][0] = {c.x, c.y};
+      b.v[3][0] = {c.z, c.w};
+    } else {
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const float2* q = reinterpret_cast<const float2*>(p + 2 * o * R);
+        float2 a = RO ? __ldg(q) : *q;
+        b.v[o][0] = {a.x, a.y};
+      }
+    }
+  } else {
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const float4* q = reinterpret_cast<const float4*>(p + 2 * o * R);
+      float4 a = RO ? __ldg(q) : *q;
+      b.v[o][0] = {a.x, a.y};
+      b.v[o][1] = {a.z, a.w};
+    }
+  }
+}
+
 // One value (all VPT vectors) of orbital/site o of block s.
 template <typename T, int VPT>
 __device__ __forceinline__ void load_one(const T* __restrict__ base, int64_t s, int o, int R,
@@ -350,11 +389,22 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
   const int64_t cxp = nbr_plus(col, x, Lx, g.per[0], 1);
   const int64_t cym = nbr_minus(col, y, Ly, g.per[1], Lx);
   const int64_t cyp = nbr_plus(col, y, Ly, g.per[1], Lx);
+  // column base pointers (plane 0) and the plane stride, in reals: the loop
+  // then steps pointers instead of recomputing 64-bit element offsets
+  const int64_t SS = (int64_t)8 * R;  // reals per site: 4 orbitals x R complex
+  const int64_t PS = plane * SS;      // reals per plane
+  const int64_t cofs = 2 * rc * VPT;
+  const T* Pc = X + col * SS + cofs;
+  const T* Pxm = X + (cxm >= 0 ? cxm : 0) * SS + cofs;
+  const T* Pxp = X + (cxp >= 0 ? cxp : 0) * SS + cofs;
+  const T* Pym = X + (cym >= 0 ? cym : 0) * SS + cofs;
+  const T* Pyp = X + (cyp >= 0 ? cyp : 0) * SS + cofs;
+  const T* Py = Yin != nullptr ? Yin + col * SS + cofs : nullptr;
   Blk<T, VPT> xm, xc, xp;
-  load_blk<T, VPT, NC>(X, col + plane * z0, R, rc, xc);
+  load_at<T, VPT, NC>(Pc + z0 * PS, R, xc);
   {
     const int64_t zm = nbr_minus(z0, z0, Lz, g.per[2], 1);
-    if (zm >= 0) load_blk<T, VPT, NC>(X, col + plane * zm, R, rc, xm);
+    if (zm >= 0) load_at<T, VPT, NC>(Pc + zm * PS, R, xm);
     else zero_blk(xm);
   }
   const int nthr = blockDim.x;
@@ -386,18 +436,18 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
       else zero_blk(xp);
       if (Yin != nullptr) ring_read<T, VPT>(sl + (size_t)4 * nthr * 16, nthr, yi);
     } else {
-      if (zp >= 0) load_blk<T, VPT, NC>(X, col + plane * zp, R, rc, xp);
+      if (zp >= 0) load_at<T, VPT, NC>(Pc + zp * PS, R, xp);
       else zero_blk(xp);
-      if (Yin != nullptr) load_blk<T, VPT, false>(Yin, s, R, rc, yi);
+      if (Yin != nullptr) load_at<T, VPT, false>(Py + z * PS, R, yi);
     }
     const T Vs = T(site_potential(g, s));
     // issue the four in-plane neighbour loads together (one L1/L2 round trip)
-    const int64_t zoff = plane * z;
+    const int64_t zoff = z * PS;
     Blk<T, VPT> ax, bx, ay, by;
-    if (cxm >= 0) load_blk<T, VPT, NC>(X, cxm + zoff, R, rc, ax); else zero_blk(ax);
-    if (cxp >= 0) load_blk<T, VPT, NC>(X, cxp + zoff, R, rc, bx); else zero_blk(bx);
-    if (cym >= 0) load_blk<T, VPT, NC>(X, cym + zoff, R, rc, ay); else zero_blk(ay);
-    if (cyp >= 0) load_blk<T, VPT, NC>(X, cyp + zoff, R, rc, by); else zero_blk(by);
+    if (cxm >= 0) load_at<T, VPT, NC>(Pxm + zoff, R, ax); else zero_blk(ax);
+    if (cxp >= 0) load_at<T, VPT, NC>(Pxp + zoff, R, bx); else zero_blk(bx);
+    if (cym >= 0) load_at<T, VPT, NC>(Pym + zoff, R, ay); else zero_blk(ay);
+    if (cyp >= 0) load_at<T, VPT, NC>(Pyp + zoff, R, by); else zero_blk(by);
     Blk<T, VPT> S, D;
     // z axis: s_z, d_z
 #pragma unroll
