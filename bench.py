@@ -184,6 +184,15 @@ def cpu_baseline(dims, R, Wd, budget_s=15.0):
                       f"{steps} spMVM steps in {dt:.1f} s"}
 
 
+def slab_config(args) -> dict:
+    """The benchmark workload's description, identical in both arms."""
+    return {"workload": "TI slab KPM: 256x256x64 sites (PBC x,y; open z), t=1, m=2, W=2, "
+                        "R random-phase vectors, 2048 moments",
+            "dims": list(args.dims), "R": args.R, "moments": args.M, "W": args.W,
+            "sweeps_per_step": (args.M + 1) // 2,
+            "l2": "vectors (1 GiB each) exceed L2; no flush"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -201,7 +210,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * elapsed / args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic",
-            "config": {"workload": "TI slab KPM (sample)", "dims": args.dims, "R": args.R, "W": args.W},
+            "config": slab_config(args),
             "cpu_baseline": {**cb, "value": value},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -528,11 +537,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
                 "data": "synthetic",
-                "config": {"workload": "TI slab KPM: 256x256x64 sites (PBC x,y; open z), t=1, m=2, "
-                                       "W=2, R random-phase vectors, 2048 moments",
-                           "dims": list(dims), "R": R, "moments": M, "W": Wd, "sweeps_per_step": sweeps,
-                           "l2": "vectors (1 GiB each) exceed L2; no flush",
-                           "launch": tuning},
+                "config": {**slab_config(args), "launch": tuning},
                 "roofline": roofline, "compare_fp64": compare, "e2e": e2e,
                 "gpu_launches": sweeps * args.steps, "clocks": clk, "cpu_baseline": cpu,
                 "spectral": {"emin": emin, "emax": emax, "a": a, "b": b}}
