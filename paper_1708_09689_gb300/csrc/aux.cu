@@ -73,6 +73,12 @@ __global__ void seed_potential_kernel(double* V, int64_t n, uint64_t key, double
     V[s] = W * (hash_uniform(key, (uint64_t)s) - 0.5);
 }
 
+__global__ void potential_f32_kernel(const double* __restrict__ V, float* __restrict__ V32, int64_t n) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x)
+    V32[s] = (float)V[s];
+}
+
 __global__ void get_potential_kernel(Geometry g, double* out) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.n_sites;
        s += (int64_t)gridDim.x * blockDim.x) {
@@ -228,6 +234,12 @@ int launch_adjoint_top(const pvsc_lattice* lat, int R, const double2* G, double 
 
 int launch_seed_potential(double* V, int64_t n, uint64_t seed, double W, cudaStream_t st) {
   seed_potential_kernel<<<grid_for(n, 256), 256, 0, st>>>(V, n, hash_key(seed, 0), W);
+  PVSC_CUDA_TRY(cudaGetLastError());
+  return PVSC_OK;
+}
+
+int launch_potential_f32(const double* V, float* V32, int64_t n, cudaStream_t st) {
+  potential_f32_kernel<<<grid_for(n, 256), 256, 0, st>>>(V, V32, n);
   PVSC_CUDA_TRY(cudaGetLastError());
   return PVSC_OK;
 }

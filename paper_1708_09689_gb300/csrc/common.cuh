@@ -23,6 +23,7 @@ struct Geometry {
   int64_t n_sites;      // TI: Lx Ly Lz; graphene: 4 Nx Ny
   double t, m;          // hopping, TI mass
   const double* V;      // device [n_sites] when v_mode == 1
+  const float* V32;     // the same potential rounded to fp32, for complex64 sweeps
   int v_mode;           // 0 zero, 1 stored, 2 regenerated from the hash
   uint64_t vkey;        // mix(seed ^ stream*gamma) for stream 0
   double W;             // disorder width for v_mode 2
@@ -62,6 +63,17 @@ __device__ __forceinline__ double site_potential(const Geometry& g, int64_t site
   if (g.v_mode == 1) return __ldg(g.V + site);
   if (g.v_mode == 2) return g.W * (hash_uniform(g.vkey, (uint64_t)site) - 0.5);
   return 0.0;
+}
+
+// The potential in the sweep's arithmetic type: complex64 sweeps read the fp32
+// copy (the same rounding as converting the fp64 value, without a per-site
+// conversion on GB300's narrow fp64 pipe and with half the bytes).
+template <typename T>
+__device__ __forceinline__ T site_potential_t(const Geometry& g, int64_t site) {
+  if constexpr (sizeof(T) == 4) {
+    if (g.v_mode == 1) return __ldg(g.V32 + site);
+  }
+  return T(site_potential(g, site));
 }
 
 // ---------------------------------------------------------------- complex

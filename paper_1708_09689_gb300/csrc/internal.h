@@ -42,8 +42,9 @@ struct LaunchShape {
 // sweeps in the launch tables
 constexpr int kModelTIFlat = 3;
 constexpr int kModelTIAsync = 4;
-constexpr int kAsyncDepth = 2;  // planes in flight per thread in the prefetching sweep
-inline size_t async_ring_bytes(int threads) { return (size_t)(kAsyncDepth + 1) * 2 * 4 * threads * 16; }
+constexpr int kAsyncDepth = 1;  // planes in flight per thread in the prefetching sweep
+// ring: (depth + 1) slots x 6 buffers x 4 granules of 16 bytes per thread
+inline size_t async_ring_bytes(int threads) { return (size_t)(kAsyncDepth + 1) * 6 * 4 * threads * 16; }
 int allow_max_smem(void* fn);
 
 // shared-memory staged TI sweep (sweep_c128.cu / sweep_c64.cu)
@@ -80,6 +81,7 @@ int run_graph(const pvsc_lattice* clat, const std::vector<uint64_t>& key, cudaSt
 struct pvsc_lattice {
   pvsc::Geometry g{};
   double* V_dev = nullptr;  // owned when v_mode == 1
+  float* V32_dev = nullptr; // fp32 copy of V_dev for complex64 sweeps
   int v_source = 0;
   uint64_t seed = 0;
   int device = 0;
@@ -124,6 +126,7 @@ int launch_scale_init(const void* x128, double2* acc, double cr, double ci, int6
                       cudaStream_t st);
 int launch_seed_potential(double* V, int64_t n, uint64_t seed, double W, cudaStream_t st);
 int launch_get_potential(const Geometry& g, double* out, cudaStream_t st);
+int launch_potential_f32(const double* V, float* V32, int64_t n, cudaStream_t st);
 int launch_gershgorin(const Geometry& g, double* out, int grid, cudaStream_t st);
 int launch_neighbours(const Geometry& g, int64_t* nbr, cudaStream_t st);
 int launch_adjoint_top(const pvsc_lattice* lat, int R, const double2* G, double sr, double si,

@@ -66,6 +66,7 @@ pvsc_lattice::~pvsc_lattice() {
     if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
   }
   if (V_dev) cudaFree(V_dev);
+  if (V32_dev) cudaFree(V32_dev);
 }
 
 using namespace pvsc;
@@ -124,11 +125,13 @@ int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattic
   int rc = PVSC_OK;
   if (desc->v_source == PVSC_V_HOST || desc->v_source == PVSC_V_DEVICE || desc->v_source == PVSC_V_SEED) {
     e = cudaMalloc(&lat->V_dev, sizeof(double) * g.n_sites);
+    if (e == cudaSuccess) e = cudaMalloc(&lat->V32_dev, sizeof(float) * g.n_sites);
     if (e != cudaSuccess) {
       delete lat;
       return set_error(PVSC_ERR_OOM, "cudaMalloc of V failed: %s", cudaGetErrorString(e));
     }
     g.V = lat->V_dev;
+    g.V32 = lat->V32_dev;
     g.v_mode = 1;
     if (desc->v_source == PVSC_V_SEED) {
       rc = launch_seed_potential(lat->V_dev, g.n_sites, desc->seed, desc->W, st);
@@ -137,6 +140,7 @@ int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattic
                           desc->v_source == PVSC_V_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
       if (e != cudaSuccess) rc = set_error(PVSC_ERR_CUDA, "copy of V failed: %s", cudaGetErrorString(e));
     }
+    if (rc == PVSC_OK) rc = launch_potential_f32(lat->V_dev, lat->V32_dev, g.n_sites, st);
   } else if (desc->v_source == PVSC_V_ON_THE_FLY) {
     g.v_mode = 2;
   }
@@ -170,8 +174,10 @@ int pvsc_set_potential(pvsc_lattice* lat, const double* V_dev, void* stream) {
   if (lat->g.v_mode == 2) return set_error(PVSC_ERR_ARG, "the potential of this lattice is regenerated on the fly");
   if (!lat->V_dev) {
     cudaError_t e = cudaMalloc(&lat->V_dev, sizeof(double) * lat->g.n_sites);
+    if (e == cudaSuccess) e = cudaMalloc(&lat->V32_dev, sizeof(float) * lat->g.n_sites);
     if (e != cudaSuccess) return set_error(PVSC_ERR_OOM, "cudaMalloc of V failed: %s", cudaGetErrorString(e));
     lat->g.V = lat->V_dev;
+    lat->g.V32 = lat->V32_dev;
     lat->g.v_mode = 1;
     // cached graphs captured with V = 0 read no potential: drop them
     std::lock_guard<std::mutex> lk(lat->mu);
@@ -183,7 +189,7 @@ int pvsc_set_potential(pvsc_lattice* lat, const double* V_dev, void* stream) {
   }
   PVSC_CUDA_TRY(cudaMemcpyAsync(lat->V_dev, V_dev, sizeof(double) * lat->g.n_sites,
                                 cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
-  return PVSC_OK;
+  return launch_potential_f32(lat->V_dev, lat->V32_dev, lat->g.n_sites, static_cast<cudaStream_t>(stream));
 }
 
 int pvsc_get_potential(const pvsc_lattice* lat, double* V_out_dev, void* stream) {

@@ -186,11 +186,56 @@ __device__ __forceinline__ VecCoef<T, VPT> load_coef(const Sweep& p, int rc) {
   return c;
 }
 
+// ---------------------------------------------------------------- dot-product accumulators
+// Per-thread partial sums of the fused dot products.  fp64 storage adds the
+// per-site fp64 products straight into fp64.  complex64 storage forms each
+// site's products in fp32 and accumulates them in a compensated fp32 pair
+// (Knuth's TwoSum keeps the exact rounding error of every addition), flushed
+// into fp64 once per column segment: the fp64 pipe, 1/64 of the fp32 rate on
+// GB300, is then not touched per site.
+template <typename T, int VPT>
+struct DotAcc {
+  double d[kNumDots][VPT];
+  T s[kNumDots][VPT], c[kNumDots][VPT];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int k = 0; k < kNumDots; ++k)
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        d[k][v] = 0.0;
+        s[k][v] = T(0);
+        c[k][v] = T(0);
+      }
+  }
+  __device__ __forceinline__ void add(int k, int v, T x) {
+    if constexpr (sizeof(T) == 8) {
+      d[k][v] += x;
+    } else {
+      const T t = s[k][v] + x;
+      const T bp = t - s[k][v];
+      c[k][v] += (s[k][v] - (t - bp)) + (x - bp);
+      s[k][v] = t;
+    }
+  }
+  __device__ __forceinline__ void flush() {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int k = 0; k < kNumDots; ++k)
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          d[k][v] += (double)s[k][v] + (double)c[k][v];
+          s[k][v] = T(0);
+          c[k][v] = T(0);
+        }
+    }
+  }
+};
+
 // ---------------------------------------------------------------- the shared epilogue
 // Everything a sweep does after y_new of one block is known.
 template <typename T, int VPT, int FEAT>
 __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, const Blk<T, VPT>& xc,
-                                         Blk<T, VPT>& yn, double (&dacc)[kNumDots][VPT],
+                                         Blk<T, VPT>& yn, DotAcc<T, VPT>& dacc,
                                          const int64_t* site_of /* 4 sites of the block */) {
   const int R = p.R;
   if constexpr ((FEAT & F_ADJ) != 0) {
@@ -283,7 +328,7 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
     }
   }
   if constexpr ((FEAT & F_DOTS) != 0) {
-    // exact-enough per-block partials in T, accumulated in fp64
+    // per-site products in T, accumulated per thread (compensated for fp32)
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
       T xx = 0, xyr = 0, xyi = 0, yy = 0;
@@ -295,10 +340,10 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
         if (p.dot_flags & 2) xyi = fma(b.re, a.im, fma(-b.im, a.re, xyi));
         if (p.dot_flags & 4) yy = fma(b.re, b.re, fma(b.im, b.im, yy));
       }
-      dacc[0][v] += (double)xx;
-      dacc[1][v] += (double)xyr;
-      dacc[2][v] += (double)xyi;
-      dacc[3][v] += (double)yy;
+      dacc.add(0, v, xx);
+      dacc.add(1, v, xyr);
+      if (p.dot_flags & 2) dacc.add(2, v, xyi);
+      if (p.dot_flags & 4) dacc.add(3, v, yy);
     }
   }
 }
@@ -337,11 +382,12 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Issue the 16-byte granules of one block (4 orbitals x VPT vectors) of site s.
+constexpr int kRingBuffers = 6;  // per ring slot: x(z+1), y_in(z), four in-plane neighbours
+
+// Issue the 16-byte granules of one block (4 orbitals x VPT vectors) whose
+// first element is at p (p as for load_at).
 template <typename T, int VPT>
-__device__ __forceinline__ void ring_issue(unsigned char* buf, int nthr, const T* base, int64_t s,
-                                           int R, int rc) {
-  const T* p = base + 2 * ((s * 4) * (int64_t)R + rc * VPT);
+__device__ __forceinline__ void ring_issue(unsigned char* buf, int nthr, const T* p, int R) {
   if constexpr (sizeof(T) == 4 && VPT == 1) {  // complex64, R == 1: 2 granules
     cp_async16(buf, p);
     cp_async16(buf + (size_t)nthr * 16, p + 4);
@@ -409,14 +455,24 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
   }
   const int nthr = blockDim.x;
   const int tid = threadIdx.x;
-  // prefetch group i: x of plane z0+i+1 and y_in of plane z0+i into slot i % (DEPTH+1)
+  // prefetch group i (plane z = z0+i) into slot i % (DEPTH+1), buffers:
+  // 0 x(z+1) own column, 1 y_in(z), 2..5 the x-/x+/y-/y+ neighbours at plane z
+  auto slot_of = [&](int64_t i) {
+    return ring + ((size_t)((i % (DEPTH + 1)) * kRingBuffers) * 4 * nthr + tid) * 16;
+  };
+  auto buf = [&](unsigned char* sl, int b) { return sl + (size_t)b * 4 * nthr * 16; };
   auto ring_group = [&](int64_t i) {
     if constexpr (DEPTH > 0) {
       if (z0 + i < z1) {
-        unsigned char* sl = ring + ((size_t)((i % (DEPTH + 1)) * 2) * 4 * nthr + tid) * 16;
-        const int64_t zq = nbr_plus(z0 + i, z0 + i, Lz, g.per[2], 1);
-        if (zq >= 0) ring_issue<T, VPT>(sl, nthr, X, col + plane * zq, R, rc);
-        if (Yin != nullptr) ring_issue<T, VPT>(sl + (size_t)4 * nthr * 16, nthr, Yin, col + plane * (z0 + i), R, rc);
+        unsigned char* sl = slot_of(i);
+        const int64_t zz = z0 + i;
+        const int64_t zq = nbr_plus(zz, zz, Lz, g.per[2], 1);
+        if (zq >= 0) ring_issue<T, VPT>(buf(sl, 0), nthr, Pc + zq * PS, R);
+        if (Yin != nullptr) ring_issue<T, VPT>(buf(sl, 1), nthr, Py + zz * PS, R);
+        if (cxm >= 0) ring_issue<T, VPT>(buf(sl, 2), nthr, Pxm + zz * PS, R);
+        if (cxp >= 0) ring_issue<T, VPT>(buf(sl, 3), nthr, Pxp + zz * PS, R);
+        if (cym >= 0) ring_issue<T, VPT>(buf(sl, 4), nthr, Pym + zz * PS, R);
+        if (cyp >= 0) ring_issue<T, VPT>(buf(sl, 5), nthr, Pyp + zz * PS, R);
       }
       cp_async_commit();
     }
@@ -426,28 +482,30 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
   for (int64_t z = z0; z < z1; ++z) {
     const int64_t s = col + plane * z;
     const int64_t zp = nbr_plus(z, z, Lz, g.per[2], 1);
-    Blk<T, VPT> yi;
+    Blk<T, VPT> yi, ax, bx, ay, by;
     if constexpr (DEPTH > 0) {
       const int64_t i = z - z0;
       ring_group(i + DEPTH);
       cp_async_wait<DEPTH>();  // group i has landed (own slots only: no barrier)
-      const unsigned char* sl = ring + ((size_t)((i % (DEPTH + 1)) * 2) * 4 * nthr + tid) * 16;
-      if (zp >= 0) ring_read<T, VPT>(sl, nthr, xp);
-      else zero_blk(xp);
-      if (Yin != nullptr) ring_read<T, VPT>(sl + (size_t)4 * nthr * 16, nthr, yi);
+      unsigned char* sl = slot_of(i);
+      if (zp >= 0) ring_read<T, VPT>(buf(sl, 0), nthr, xp); else zero_blk(xp);
+      if (Yin != nullptr) ring_read<T, VPT>(buf(sl, 1), nthr, yi);
+      if (cxm >= 0) ring_read<T, VPT>(buf(sl, 2), nthr, ax); else zero_blk(ax);
+      if (cxp >= 0) ring_read<T, VPT>(buf(sl, 3), nthr, bx); else zero_blk(bx);
+      if (cym >= 0) ring_read<T, VPT>(buf(sl, 4), nthr, ay); else zero_blk(ay);
+      if (cyp >= 0) ring_read<T, VPT>(buf(sl, 5), nthr, by); else zero_blk(by);
     } else {
       if (zp >= 0) load_at<T, VPT, NC>(Pc + zp * PS, R, xp);
       else zero_blk(xp);
       if (Yin != nullptr) load_at<T, VPT, false>(Py + z * PS, R, yi);
+      // issue the four in-plane neighbour loads together (one L1/L2 round trip)
+      const int64_t zoff = z * PS;
+      if (cxm >= 0) load_at<T, VPT, NC>(Pxm + zoff, R, ax); else zero_blk(ax);
+      if (cxp >= 0) load_at<T, VPT, NC>(Pxp + zoff, R, bx); else zero_blk(bx);
+      if (cym >= 0) load_at<T, VPT, NC>(Pym + zoff, R, ay); else zero_blk(ay);
+      if (cyp >= 0) load_at<T, VPT, NC>(Pyp + zoff, R, by); else zero_blk(by);
     }
-    const T Vs = T(site_potential(g, s));
-    // issue the four in-plane neighbour loads together (one L1/L2 round trip)
-    const int64_t zoff = z * PS;
-    Blk<T, VPT> ax, bx, ay, by;
-    if (cxm >= 0) load_at<T, VPT, NC>(Pxm + zoff, R, ax); else zero_blk(ax);
-    if (cxp >= 0) load_at<T, VPT, NC>(Pxp + zoff, R, bx); else zero_blk(bx);
-    if (cym >= 0) load_at<T, VPT, NC>(Pym + zoff, R, ay); else zero_blk(ay);
-    if (cyp >= 0) load_at<T, VPT, NC>(Pyp + zoff, R, by); else zero_blk(by);
+    const T Vs = site_potential_t<T>(g, s);
     Blk<T, VPT> S, D;
     // z axis: s_z, d_z
 #pragma unroll
@@ -533,11 +591,8 @@ __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p)
   const VecCoef<T, VPT> cf = load_coef<T, VPT>(p, rc);
   const T* __restrict__ X = static_cast<const T*>(p.x);
   const T* __restrict__ Yin = static_cast<const T*>(p.yin);
-  double dacc[kNumDots][VPT];
-#pragma unroll
-  for (int d = 0; d < kNumDots; ++d)
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) dacc[d][v] = 0.0;
+  DotAcc<T, VPT> dacc;
+  dacc.init();
 
   const int64_t ncolthr = plane * C;
   const int64_t nbx = (ncolthr + blockDim.x - 1) / blockDim.x;
@@ -554,8 +609,12 @@ __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p)
                              const int64_t sites[4] = {s, s, s, s};
                              epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
                            });
+    if constexpr ((FEAT & F_DOTS) != 0) dacc.flush();  // one fp64 add per column segment
   }
-  if constexpr ((FEAT & F_DOTS) != 0) reduce_dots<VPT>(p, dacc);
+  if constexpr ((FEAT & F_DOTS) != 0) {
+    dacc.flush();
+    reduce_dots<VPT>(p, dacc.d);
+  }
 }
 
 // Flat TI sweep: one (site, vector chunk) per thread and pass, no state
@@ -572,11 +631,8 @@ __global__ void __launch_bounds__(256, 2) ti_sweep_flat(const __grid_constant__ 
   const VecCoef<T, VPT> cf = load_coef<T, VPT>(p, rc);
   const T* __restrict__ X = static_cast<const T*>(p.x);
   const T* __restrict__ Yin = static_cast<const T*>(p.yin);
-  double dacc[kNumDots][VPT];
-#pragma unroll
-  for (int d = 0; d < kNumDots; ++d)
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) dacc[d][v] = 0.0;
+  DotAcc<T, VPT> dacc;
+  dacc.init();
   const int64_t nthr = p.g.n_sites * C;
   for (int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tid < nthr;
        tid += (int64_t)gridDim.x * blockDim.x) {
@@ -622,7 +678,7 @@ __global__ void __launch_bounds__(256, 2) ti_sweep_flat(const __grid_constant__ 
     }
     Blk<T, VPT> yi;
     if (Yin != nullptr) load_blk<T, VPT, false>(Yin, s, R, rc, yi);
-    const T Vs = T(site_potential(p.g, s));
+    const T Vs = site_potential_t<T>(p.g, s);
     Blk<T, VPT> yn;
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
@@ -644,7 +700,10 @@ __global__ void __launch_bounds__(256, 2) ti_sweep_flat(const __grid_constant__ 
     const int64_t sites[4] = {s, s, s, s};
     epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
   }
-  if constexpr ((FEAT & F_DOTS) != 0) reduce_dots<VPT>(p, dacc);
+  if constexpr ((FEAT & F_DOTS) != 0) {
+    dacc.flush();
+    reduce_dots<VPT>(p, dacc.d);
+  }
 }
 
 // ---------------------------------------------------------------- graphene sweep
@@ -664,11 +723,8 @@ __global__ void __launch_bounds__(256) gr_sweep(const __grid_constant__ Sweep p)
   const VecCoef<T, VPT> cf = load_coef<T, VPT>(p, rc);
   const T* __restrict__ X = static_cast<const T*>(p.x);
   const T tt = T(p.g.t);
-  double dacc[kNumDots][VPT];
-#pragma unroll
-  for (int d = 0; d < kNumDots; ++d)
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) dacc[d][v] = 0.0;
+  DotAcc<T, VPT> dacc;
+  dacc.init();
   const int64_t nthr = ncell * C;
   for (int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tid < nthr;
        tid += (int64_t)gridDim.x * blockDim.x) {
@@ -718,7 +774,7 @@ __global__ void __launch_bounds__(256) gr_sweep(const __grid_constant__ Sweep p)
     }
     T Vs[4];
 #pragma unroll
-    for (int o = 0; o < 4; ++o) Vs[o] = T(site_potential(p.g, 4 * c + o));
+    for (int o = 0; o < 4; ++o) Vs[o] = site_potential_t<T>(p.g, 4 * c + o);
     Blk<T, VPT> yn;
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
@@ -739,7 +795,10 @@ __global__ void __launch_bounds__(256) gr_sweep(const __grid_constant__ Sweep p)
     const int64_t sites[4] = {4 * c, 4 * c + 1, 4 * c + 2, 4 * c + 3};
     epilogue<T, VPT, FEAT>(p, c, rc, xc, yn, dacc, sites);
   }
-  if constexpr ((FEAT & F_DOTS) != 0) reduce_dots<VPT>(p, dacc);
+  if constexpr ((FEAT & F_DOTS) != 0) {
+    dacc.flush();
+    reduce_dots<VPT>(p, dacc.d);
+  }
 }
 
 }  // namespace pvsc

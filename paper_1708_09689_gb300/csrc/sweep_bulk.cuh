@@ -112,9 +112,8 @@ __global__ void __launch_bounds__(256) ti_sweep_bulk(const __grid_constant__ Swe
   __syncthreads();
 
   const VecCoef<T, 1> cf = load_coef<T, 1>(p, r);
-  double dacc[kNumDots][1];
-#pragma unroll
-  for (int d = 0; d < kNumDots; ++d) dacc[d][0] = 0.0;
+  DotAcc<T, 1> dacc;
+  dacc.init();
 
   const int64_t ntx = (Lx + TX - 1) / TX, nty = (Ly + TY - 1) / TY;
   const int zs = p.zslab;
@@ -330,7 +329,10 @@ __global__ void __launch_bounds__(256) ti_sweep_bulk(const __grid_constant__ Swe
     if (threadIdx.x == 0) atomicExch(&g_bulk_sweep_error, 1);
     return;
   }
-  if constexpr ((FEAT & F_DOTS) != 0) reduce_dots<1>(p, dacc);
+  if constexpr ((FEAT & F_DOTS) != 0) {
+    dacc.flush();
+    reduce_dots<1>(p, dacc.d);
+  }
 }
 
 }  // namespace pvsc
