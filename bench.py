@@ -80,7 +80,8 @@ def parse():
                          "64 lattices, adjoint gradient) and print one JSON line each")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="profiling case: run this many complex64 KPM-type sweeps (stencil, "
-                         "recurrence, dots) on the lattice and exit without timing")
+                         "recurrence, dots) on the lattice (ti_slab), or this many complex64 "
+                         "propagation time steps (graphene_qd), and exit without timing")
     ap.add_argument("--launch", default=None,
                     help="JSON launch shape (threads, blocks_per_sm, zslab, vpt, tile_x, tile_y, kernel) "
                          "to use instead of autotuning, e.g. for profiling runs")
@@ -238,6 +239,20 @@ def _hbm_roof(bytes_per_lup, lups, ms, kernel):
             "bytes_per_lup": bytes_per_lup, "peak_kind": f"{kind} hbm_gbs"}
 
 
+def series_bytes_per_site(K: int) -> float:
+    """Algorithmic HBM bytes per graphene site of one complex64 propagation time
+    step with K series terms (R = 1, fp32 copy of V): the complex128 -> complex64
+    conversion of w_0 (16 + 8), sweep 1 (x 8, w_1 8, psi 16, acc 16, V 4), sweeps
+    j = 2 .. K-2 (x 8, y_in 8, y_out 8, V 4, and acc 16 + 16 on odd j), and the
+    last sweep (x 8, y_in 8, V 4, acc 16, psi 16)."""
+    if K < 3:
+        raise ValueError("K >= 3")
+    total = 24.0 + 52.0 + 52.0
+    for j in range(2, K - 1):
+        total += 28.0 + (32.0 if j % 2 == 1 else 0.0)
+    return total
+
+
 def run_workload(args, pv, dev, rank, world):
     """The remaining workloads, one JSON line each (single GPU; rank 0 prints)."""
     import torch
@@ -278,6 +293,21 @@ def run_workload(args, pv, dev, rank, world):
         nterms = len(pv.propagation_coeffs(a * cfg.dt, cfg.trunc))
         psi0 = torch.from_numpy(cfg.packet()).to(dev)
         nsteps = args.steps if args.steps > 5 else cfg.nsteps
+        if args.sweeps_only:
+            # profiling case: this many complex64 propagation time steps, untimed
+            if args.launch:
+                shape = {k: v for k, v in json.loads(args.launch).items() if k != "time_ms"}
+                lat.set_tuning(1, pv.C64, **shape)
+            else:
+                lat.autotune(1, pv.C64)
+            work = pv.work_buffer(lat.work_bytes(pv.OP_SERIES, 1, pv.C64, nterms), dev)
+            psi = psi0.clone()
+            pv.cheb_propagate(lat, psi, cfg.dt, args.sweeps_only, a, b, cfg.trunc, prec=pv.C64, work=work)
+            torch.cuda.synchronize()
+            if rank == 0:
+                print(json.dumps({"time_steps": args.sweeps_only, "sweeps_per_time_step": nterms - 1,
+                                  "launch": lat.get_tuning(1, pv.C64)}))
+            return 0
         res = {}
         for prec, name in ((pv.C64, "c64"), (pv.C128, "c128")):
             lat.autotune(1, prec)
@@ -307,8 +337,10 @@ def run_workload(args, pv, dev, rank, world):
                      "config": {"workload": "graphene 4096x2048 four-site cells (2^25 sites), open, 8x8 "
                                             "QD array V0=0.1 R=40 w=5, Gaussian packet, dt=1, trunc 1e-14",
                                 "sweeps_per_time_step": nterms - 1},
-                     "roofline": _hbm_roof(64.0, lups, ms64 / n64,
-                                           "gr_sweep<float,1,F_ACC> (complex64 w, complex128 accumulator)"),
+                     "roofline": _hbm_roof(round(series_bytes_per_site(nterms) / (nterms - 1), 3), lups,
+                                           ms64 / n64,
+                                           "gr_sweep<float,1,*> (complex64 w, complex128 accumulator "
+                                           "touched on every other sweep), time-step average"),
                      "compare_fp64": {"c128_glups": round(v128, 3), "c64_over_c128": round(v64 / v128, 2),
                                       "c128_steps": n128,
                                       "norm_drift_c64": abs(torch.linalg.vector_norm(psi64).item() - 1),

@@ -325,7 +325,9 @@ typedef struct {
   int32_t tile_x; /* TI only: > 0 selects the shared-memory staged sweep (bulk-copy */
   int32_t tile_y; /* engine, 4-plane ring) with tiles of tile_x x tile_y columns */
   int32_t kernel; /* TI only: 0 z-marching in registers (or staged if tile_x > 0), */
-                  /* 1 flat (one site per thread and pass, neighbours folded in turn) */
+                  /* 1 flat (one site per thread and pass, neighbours folded in turn), */
+                  /* 2 z-marching with a cp.async ring of all six blocks of a plane, */
+                  /* 3 z-marching with a deep cp.async ring of the two streamed blocks */
 } pvsc_tuning;
 
 /* Device error word of the shared-memory staged sweeps: *flag = 1 if a copy

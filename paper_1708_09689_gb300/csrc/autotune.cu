@@ -154,8 +154,10 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
         for (int zs : zslab_c) cands.push_back(pvsc_tuning{th, bps, zs, 0.f, vpt, 0, 0, 0});
       if (lat->g.model == PVSC_TI) {
         cands.push_back(pvsc_tuning{th, 0, 0, 0.f, vpt, 0, 0, 1});
-        if (!(prec == PVSC_C64 && vpt == 1 && R > 1))
+        if (!(prec == PVSC_C64 && vpt == 1 && R > 1)) {
           for (int zs : {0, 16}) cands.push_back(pvsc_tuning{th, 0, zs, 0.f, vpt, 0, 0, 2});
+          cands.push_back(pvsc_tuning{th, 0, 0, 0.f, vpt, 0, 0, 3});
+        }
       }
     }
   }

@@ -118,9 +118,10 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
       const bool active = tid < plane * C;
       const int64_t z0 = bz * L.zs, z1 = min(z0 + (int64_t)L.zs, Lz);
       const int64_t col = tid / C;
-      double dacc[2][VPT];
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) dacc[0][v] = dacc[1][v] = 0.0;
+      // per-site partials in (compensated, for complex64) working precision,
+      // flushed to fp64 once per column segment
+      DotAcc<T, VPT> dacc;
+      dacc.init();
       if (ph == 0) {
         // w_0: random-phase vectors exp(2 pi i u)/sqrt(D), idx = r D + i
         if (active) {
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
         }
         if (active) {
           // x is written by this kernel in other phases: coherent loads only (NC = false)
-          ti_march<T, VPT, false, 0>(L.g, X, Yin, R, rc, col, z0, z1, cf, nullptr,
+          ti_march<T, VPT, false, 0, 2>(L.g, X, Yin, R, rc, col, z0, z1, cf, nullptr,
                                   [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
                                     store_blk<T, VPT>(Yout, s, R, rc, yn);
 #pragma unroll
@@ -172,17 +173,18 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
                                         xx = fma(p.re, p.re, fma(p.im, p.im, xx));
                                         xy = fma(q.re, p.re, fma(q.im, p.im, xy));
                                       }
-                                      dacc[0][v] += (double)xx;
-                                      dacc[1][v] += (double)xy;
+                                      dacc.add(0, v, xx);
+                                      dacc.add(1, v, xy);
                                     }
                                   });
         }
+        dacc.flush();
         // fixed-order block reduction to one row of partials for this unit
 #pragma unroll
         for (int d = 0; d < 2; ++d)
 #pragma unroll
           for (int v = 0; v < VPT; ++v) {
-            double s = dacc[d][v];
+            double s = dacc.d[d][v];
             for (int off = 16; off >= C; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
             if (lane < C) sm[warp][d][v][lane] = s;
           }

@@ -99,7 +99,18 @@ void sweep_init(Sweep& p, const pvsc_lattice* lat, int R, int prec) {
   p.cx_re = 0; p.ph_re = 1.0;
 }
 
+static int coef_kind(double re, double im) {
+  return (im == 0.0 ? 1 : 0) | (re == 0.0 ? 2 : 0);  // 1 real, 2 imaginary, 3 zero, 0 general
+}
+
 int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStream_t st) {
+  p.acc_kind = coef_kind(p.cx_re, p.cx_im) | (coef_kind(p.cy_re, p.cy_im) << 2);
+  const double cv[2][2] = {{p.cx_re, p.cx_im}, {p.cy_re, p.cy_im}};
+  for (int t = 0; t < 2; ++t)
+    for (int q = 0; q < 2; ++q) {
+      p.fc[t][q][0] = (float)cv[t][q];
+      p.fc[t][q][1] = (float)(cv[t][q] - (double)p.fc[t][q][0]);
+    }
   const LaunchShape sh = shape_for(lat, p.R, prec);
   if (lat->g.model == PVSC_TI && sh.tile_x > 0 && sh.tile_y > 0)
     return launch_sweep_staged(lat, prec, feat, p, sh, st);
@@ -110,9 +121,10 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
   int occ = 0;
   const bool flat = lat->g.model == PVSC_TI && sh.kernel == 1;
   // the prefetch ring moves 16-byte granules: not for complex64 with one vector of R > 1
-  const bool async = lat->g.model == PVSC_TI && sh.kernel == 2 &&
+  const bool async = lat->g.model == PVSC_TI && (sh.kernel == 2 || sh.kernel == 3) &&
                      !(prec == PVSC_C64 && vpt == 1 && p.R > 1);
-  const int model = flat ? kModelTIFlat : (async ? kModelTIAsync : lat->g.model);
+  const int model = flat ? kModelTIFlat
+                         : (async ? (sh.kernel == 2 ? kModelTIAsync : kModelTIAsyncDeep) : lat->g.model);
   int rc = prec == PVSC_C128 ? occupancy_c128(model, feat, threads, &occ)
                              : occupancy_c64(model, vpt, feat, threads, &occ);
   if (rc) return rc;
@@ -254,52 +266,61 @@ static int run_series(const pvsc_lattice* lat, int R, int prec, const void* x, v
       p.coef[3][r] = 0.0;
     }
   };
-  const void* prev;  // w_{k-2}
-  void* cur;         // w_{k-1}
-  // k = 1
-  if (prec == PVSC_C128) {
-    set_scal(1.0 / a, 0.0);
-    p.x = x;
-    p.yin = nullptr;
-    p.yout = wa;
-    p.acc = acc;
-    p.acc_mode = ACC_INIT;
-    p.cx_re = cw[0].real(); p.cx_im = cw[0].imag();
-    p.cy_re = cw[1].real(); p.cy_im = cw[1].imag();
-    if (int rc = launch_sweep(lat, prec, F_ACC, p, st)) return rc;
-    prev = x;
-    cur = wa;
-    if (K == 2) return launch_scale_init(acc, static_cast<double2*>(y), phase.real(), phase.imag(), n, st);
-  } else {
-    if (int rc = launch_convert_c128_to_c64(x, wb, n, st)) return rc;
-    if (int rc = launch_scale_init(x, acc, cw[0].real(), cw[0].imag(), n, st)) return rc;
-    set_scal(1.0 / a, 0.0);
-    p.x = wb;
-    p.yin = nullptr;
-    p.yout = (K == 2) ? nullptr : wa;
+  // Sweep j makes w_j from x = w_{j-1} and y_in = w_{j-2}.  The accumulator
+  // takes two terms per touch: sweep 1 starts it with cw_0 w_0 + cw_1 w_1,
+  // every odd sweep j adds cw_{j-1} w_{j-1} + cw_j w_j, even sweeps leave it
+  // alone, and the last sweep adds what is left and writes phase * acc to y.
+  auto set_acc = [&](int j, int mode, bool with_x) {
     p.acc = acc;
     p.acc_out = static_cast<double2*>(y);
-    p.acc_mode = ACC_ADD | (K == 2 ? ACC_FINAL : 0);
-    p.cy_re = cw[1].real(); p.cy_im = cw[1].imag();
-    p.ph_re = phase.real(); p.ph_im = phase.imag();
+    p.acc_mode = mode | (with_x ? ACC_X : 0);
+    p.cx_re = with_x ? cw[j - 1].real() : 0.0;
+    p.cx_im = with_x ? cw[j - 1].imag() : 0.0;
+    p.cy_re = cw[j].real();
+    p.cy_im = cw[j].imag();
+    p.ph_re = phase.real();
+    p.ph_im = phase.imag();
+  };
+  const void* prev;  // w_{j-2}
+  void* cur;         // w_{j-1}
+  // j = 1
+  set_scal(1.0 / a, 0.0);
+  if (prec == PVSC_C128) {
+    p.x = x;
+    p.yout = wa;
+    set_acc(1, ACC_INIT, true);
     if (int rc = launch_sweep(lat, prec, F_ACC, p, st)) return rc;
+    // y may alias x: the final write is a separate pass
+    if (K == 2) return launch_scale_init(acc, static_cast<double2*>(y), phase.real(), phase.imag(), n, st);
+    prev = x;
+    cur = wa;
+  } else {
+    // w_0 rounded to complex64 for the recurrence; the accumulator takes w_0 exact
+    if (int rc = launch_convert_c128_to_c64(x, wb, n, st)) return rc;
+    p.x = wb;
+    p.src = static_cast<const double2*>(x);
+    p.yout = (K == 2) ? nullptr : wa;
+    set_acc(1, ACC_INIT | ACC_XSRC | (K == 2 ? ACC_FINAL : 0), true);
+    if (int rc = launch_sweep(lat, prec, F_ACC, p, st)) return rc;
+    p.src = nullptr;
     if (K == 2) return PVSC_OK;
     prev = wb;
     cur = wa;
   }
-  for (int k = 2; k < K; ++k) {
-    const bool last = (k == K - 1);
+  p.yin = nullptr;
+  for (int j = 2; j < K; ++j) {
+    const bool last = (j == K - 1);
     void* out = (prev == x) ? wb : const_cast<void*>(prev);
     set_scal(2.0 / a, -1.0);
     p.x = cur;
     p.yin = prev;
     p.yout = last ? nullptr : out;
-    p.acc = acc;
-    p.acc_out = static_cast<double2*>(y);
-    p.acc_mode = ACC_ADD | (last ? ACC_FINAL : 0);
-    p.cy_re = cw[k].real(); p.cy_im = cw[k].imag();
-    p.ph_re = phase.real(); p.ph_im = phase.imag();
-    if (int rc = launch_sweep(lat, prec, F_ACC, p, st)) return rc;
+    int feat = 0;
+    if (j % 2 == 1 || last) {
+      set_acc(j, ACC_ADD | (last ? ACC_FINAL : 0), j % 2 == 1);
+      feat = F_ACC;
+    }
+    if (int rc = launch_sweep(lat, prec, feat, p, st)) return rc;
     prev = cur;
     cur = out;
   }
@@ -639,7 +660,7 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
     return PVSC_OK;
   }
   if (tuning->vpt < 0 || tuning->vpt > 2) return set_error(PVSC_ERR_ARG, "vpt must be 0, 1 or 2");
-  if (tuning->kernel < 0 || tuning->kernel > 2) return set_error(PVSC_ERR_ARG, "kernel must be 0, 1 or 2");
+  if (tuning->kernel < 0 || tuning->kernel > 3) return set_error(PVSC_ERR_ARG, "kernel must be 0 .. 3");
   const int C = R / vpt_tuned(tuning->vpt, R, prec);
   if (tuning->threads < 32 || tuning->threads > kMaxThreads || tuning->threads % 32 || tuning->threads % C)
     return set_error(PVSC_ERR_ARG, "threads must be a multiple of 32 and of R/VPT = %d, at most %d", C, kMaxThreads);

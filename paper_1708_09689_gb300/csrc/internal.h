@@ -35,16 +35,22 @@ struct LaunchShape {
   int vpt = 0;            // 0: automatic
   int tile_x = 0;         // > 0: shared-memory staged TI sweep with this tile
   int tile_y = 0;
-  int kernel = 0;         // TI: 0 z-marching / staged, 1 flat
+  int kernel = 0;         // TI: 0 z-marching / staged, 1 flat, 2 / 3 cp.async rings
 };
 
 // kernel-selector "model" values of the flat and the cp.async-prefetching TI
 // sweeps in the launch tables
 constexpr int kModelTIFlat = 3;
-constexpr int kModelTIAsync = 4;
-constexpr int kAsyncDepth = 1;  // planes in flight per thread in the prefetching sweep
-// ring: (depth + 1) slots x 6 buffers x 4 granules of 16 bytes per thread
-inline size_t async_ring_bytes(int threads) { return (size_t)(kAsyncDepth + 1) * 6 * 4 * threads * 16; }
+constexpr int kModelTIAsync = 4;      // ring of all six blocks of a plane, one plane ahead
+constexpr int kModelTIAsyncDeep = 5;  // ring of the two HBM streams, three planes ahead
+constexpr int kAsyncDepth = 1;
+constexpr int kAsyncDeepDepth = 3;
+// ring: (depth + 1) slots x buffers x 4 granules of 16 bytes per thread
+inline size_t async_ring_bytes(int model, int threads) {
+  if (model == kModelTIAsync) return (size_t)(kAsyncDepth + 1) * 6 * 4 * threads * 16;
+  if (model == kModelTIAsyncDeep) return (size_t)(kAsyncDeepDepth + 1) * 2 * 4 * threads * 16;
+  return 0;
+}
 int allow_max_smem(void* fn);
 
 // shared-memory staged TI sweep (sweep_c128.cu / sweep_c64.cu)

@@ -231,6 +231,60 @@ struct DotAcc {
   }
 };
 
+// ---------------------------------------------------------------- fp64 accumulation helpers
+// binary32 -> binary64 by rebuilding the IEEE 754 bit fields with integer
+// operations (sign kept, exponent rebiased by 1023 - 127 = 896, mantissa
+// shifted up by 29 bits).  Exact, like the hardware conversion, which on this
+// part issues on the narrow fp64 pipe; zero, subnormal, infinite and NaN
+// inputs take the hardware conversion.
+__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e - 1u < 254u) {
+    const unsigned hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20));
+    return __hiloint2double((int)hi, (int)(u << 29));
+  }
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)u, 0);
+  return (double)f;
+}
+
+// (ar, ai) += (cr + i ci)(xr + i xi); kind (set on the host): 1 ci == 0,
+// 2 cr == 0, 3 both zero, 0 general.  The Bessel weights of the propagation
+// alternate between real and imaginary, so one half of the products is skipped.
+__device__ __forceinline__ void cfma_acc(double cr, double ci, int kind, double xr, double xi,
+                                         double& ar, double& ai) {
+  if (kind == 1) {
+    ar = fma(cr, xr, ar);
+    ai = fma(cr, xi, ai);
+  } else if (kind == 2) {
+    ar = fma(-ci, xi, ar);
+    ai = fma(ci, xr, ai);
+  } else if (kind == 0) {
+    ar = fma(cr, xr, fma(-ci, xi, ar));
+    ai = fma(cr, xi, fma(ci, xr, ai));
+  }
+}
+
+// (sr, si) += c (xr + i xi) in fp32, same kinds as cfma_acc, with the
+// coefficient c = (re, im) as unevaluated fp32 sums hi + lo (c[part][0] hi,
+// c[part][1] lo): the product then carries the coefficient to about 2^-48,
+// and what remains is the rounding of the sum, which varies with the data
+// instead of repeating the same relative error on every series evaluation.
+__device__ __forceinline__ void cfma_f32(const float (&c)[2][2], int kind, float xr, float xi,
+                                         float& sr, float& si) {
+  if (kind == 1) {
+    sr = fmaf(c[0][0], xr, fmaf(c[0][1], xr, sr));
+    si = fmaf(c[0][0], xi, fmaf(c[0][1], xi, si));
+  } else if (kind == 2) {
+    sr = fmaf(-c[1][0], xi, fmaf(-c[1][1], xi, sr));
+    si = fmaf(c[1][0], xr, fmaf(c[1][1], xr, si));
+  } else if (kind == 0) {
+    sr = fmaf(c[0][0], xr, fmaf(-c[1][0], xi, fmaf(c[0][1], xr, fmaf(-c[1][1], xi, sr))));
+    si = fmaf(c[0][0], xi, fmaf(c[1][0], xr, fmaf(c[0][1], xi, fmaf(c[1][1], xr, si))));
+  }
+}
+
 // ---------------------------------------------------------------- the shared epilogue
 // Everything a sweep does after y_new of one block is known.
 template <typename T, int VPT, int FEAT>
@@ -264,35 +318,54 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
     store_blk<T, VPT>(static_cast<T*>(p.z), s, R, rc, zb);
   }
   if constexpr ((FEAT & F_ACC) != 0) {
-    const double cr = p.cy_re, ci = p.cy_im;
+    // acc (+)= cx x + cy y_new, where x is this sweep's input (or the
+    // complex128 source) and y_new its output: with two terms per sweep the
+    // driver touches the accumulator on every other sweep only.
+    const int mode = p.acc_mode;
 #pragma unroll
     for (int o = 0; o < 4; ++o)
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
         const int r = rc * VPT + v;
-        const double yr = (double)yn.v[o][v].re, yi = (double)yn.v[o][v].im;
-        double ar, ai;
-        if (p.acc_mode & ACC_INIT) {
-          const double xr = (double)xc.v[o][v].re, xi = (double)xc.v[o][v].im;
-          ar = p.cx_re * xr - p.cx_im * xi;
-          ai = p.cx_re * xi + p.cx_im * xr;
-        } else {
+        double ar = 0.0, ai = 0.0;
+        if (!(mode & ACC_INIT)) {
           const double2 a = *acc_ptr(p.acc, s, o, R, r);
           ar = a.x;
           ai = a.y;
         }
-        // Bessel weights are alternately real and imaginary: skip the zero half.
-        if (ci == 0.0) {
-          ar = fma(cr, yr, ar);
-          ai = fma(cr, yi, ai);
-        } else if (cr == 0.0) {
-          ar = fma(-ci, yi, ar);
-          ai = fma(ci, yr, ai);
+        if constexpr (sizeof(T) == 4) {
+          if (!(mode & ACC_XSRC)) {
+            // complex64 vectors: the one- or two-term combination in fp32,
+            // added to the fp64 accumulator with one fp64 add per part
+            float sr = 0.f, si = 0.f;
+            if (mode & ACC_X) cfma_f32(p.fc[0], p.acc_kind & 3, xc.v[o][v].re, xc.v[o][v].im, sr, si);
+            cfma_f32(p.fc[1], p.acc_kind >> 2, yn.v[o][v].re, yn.v[o][v].im, sr, si);
+            if (mode & ACC_INIT) {
+              ar = widen(sr);
+              ai = widen(si);
+            } else {
+              ar += widen(sr);
+              ai += widen(si);
+            }
+          } else {
+            const double2 h = *acc_ptr(const_cast<double2*>(p.src), s, o, R, r);
+            cfma_acc(p.cx_re, p.cx_im, p.acc_kind & 3, h.x, h.y, ar, ai);
+            cfma_acc(p.cy_re, p.cy_im, p.acc_kind >> 2, widen(yn.v[o][v].re), widen(yn.v[o][v].im),
+                     ar, ai);
+          }
         } else {
-          ar = fma(cr, yr, fma(-ci, yi, ar));
-          ai = fma(cr, yi, fma(ci, yr, ai));
+          if (mode & ACC_X) {
+            double xr = xc.v[o][v].re, xi = xc.v[o][v].im;
+            if (mode & ACC_XSRC) {
+              const double2 h = *acc_ptr(const_cast<double2*>(p.src), s, o, R, r);
+              xr = h.x;
+              xi = h.y;
+            }
+            cfma_acc(p.cx_re, p.cx_im, p.acc_kind & 3, xr, xi, ar, ai);
+          }
+          cfma_acc(p.cy_re, p.cy_im, p.acc_kind >> 2, yn.v[o][v].re, yn.v[o][v].im, ar, ai);
         }
-        if (p.acc_mode & ACC_FINAL) {
+        if (mode & ACC_FINAL) {
           *acc_ptr(p.acc_out, s, o, R, r) =
               make_double2(p.ph_re * ar - p.ph_im * ai, p.ph_re * ai + p.ph_im * ar);
         } else {
@@ -382,7 +455,8 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-constexpr int kRingBuffers = 6;  // per ring slot: x(z+1), y_in(z), four in-plane neighbours
+// Ring slots hold NBUF buffers: 2 (x(z+1), y_in(z): the HBM streams) or 6
+// (plus the four in-plane neighbours, which otherwise come from L1/L2).
 
 // Issue the 16-byte granules of one block (4 orbitals x VPT vectors) whose
 // first element is at p (p as for load_at).
@@ -422,7 +496,7 @@ __device__ __forceinline__ void ring_read(const unsigned char* buf, int nthr, Bl
   }
 }
 
-template <typename T, int VPT, bool NC, int DEPTH, class Emit>
+template <typename T, int VPT, bool NC, int DEPTH, int NBUF, class Emit>
 __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict__ X,
                                          const T* __restrict__ Yin, int R, int rc, int64_t col,
                                          int64_t z0, int64_t z1, const VecCoef<T, VPT>& cf,
@@ -458,7 +532,7 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
   // prefetch group i (plane z = z0+i) into slot i % (DEPTH+1), buffers:
   // 0 x(z+1) own column, 1 y_in(z), 2..5 the x-/x+/y-/y+ neighbours at plane z
   auto slot_of = [&](int64_t i) {
-    return ring + ((size_t)((i % (DEPTH + 1)) * kRingBuffers) * 4 * nthr + tid) * 16;
+    return ring + ((size_t)((i % (DEPTH + 1)) * NBUF) * 4 * nthr + tid) * 16;
   };
   auto buf = [&](unsigned char* sl, int b) { return sl + (size_t)b * 4 * nthr * 16; };
   auto ring_group = [&](int64_t i) {
@@ -469,10 +543,12 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
         const int64_t zq = nbr_plus(zz, zz, Lz, g.per[2], 1);
         if (zq >= 0) ring_issue<T, VPT>(buf(sl, 0), nthr, Pc + zq * PS, R);
         if (Yin != nullptr) ring_issue<T, VPT>(buf(sl, 1), nthr, Py + zz * PS, R);
-        if (cxm >= 0) ring_issue<T, VPT>(buf(sl, 2), nthr, Pxm + zz * PS, R);
-        if (cxp >= 0) ring_issue<T, VPT>(buf(sl, 3), nthr, Pxp + zz * PS, R);
-        if (cym >= 0) ring_issue<T, VPT>(buf(sl, 4), nthr, Pym + zz * PS, R);
-        if (cyp >= 0) ring_issue<T, VPT>(buf(sl, 5), nthr, Pyp + zz * PS, R);
+        if constexpr (NBUF == 6) {
+          if (cxm >= 0) ring_issue<T, VPT>(buf(sl, 2), nthr, Pxm + zz * PS, R);
+          if (cxp >= 0) ring_issue<T, VPT>(buf(sl, 3), nthr, Pxp + zz * PS, R);
+          if (cym >= 0) ring_issue<T, VPT>(buf(sl, 4), nthr, Pym + zz * PS, R);
+          if (cyp >= 0) ring_issue<T, VPT>(buf(sl, 5), nthr, Pyp + zz * PS, R);
+        }
       }
       cp_async_commit();
     }
@@ -490,10 +566,18 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
       unsigned char* sl = slot_of(i);
       if (zp >= 0) ring_read<T, VPT>(buf(sl, 0), nthr, xp); else zero_blk(xp);
       if (Yin != nullptr) ring_read<T, VPT>(buf(sl, 1), nthr, yi);
-      if (cxm >= 0) ring_read<T, VPT>(buf(sl, 2), nthr, ax); else zero_blk(ax);
-      if (cxp >= 0) ring_read<T, VPT>(buf(sl, 3), nthr, bx); else zero_blk(bx);
-      if (cym >= 0) ring_read<T, VPT>(buf(sl, 4), nthr, ay); else zero_blk(ay);
-      if (cyp >= 0) ring_read<T, VPT>(buf(sl, 5), nthr, by); else zero_blk(by);
+      if constexpr (NBUF == 6) {
+        if (cxm >= 0) ring_read<T, VPT>(buf(sl, 2), nthr, ax); else zero_blk(ax);
+        if (cxp >= 0) ring_read<T, VPT>(buf(sl, 3), nthr, bx); else zero_blk(bx);
+        if (cym >= 0) ring_read<T, VPT>(buf(sl, 4), nthr, ay); else zero_blk(ay);
+        if (cyp >= 0) ring_read<T, VPT>(buf(sl, 5), nthr, by); else zero_blk(by);
+      } else {  // in-plane neighbours from L1/L2, issued together
+        const int64_t zoff = z * PS;
+        if (cxm >= 0) load_at<T, VPT, NC>(Pxm + zoff, R, ax); else zero_blk(ax);
+        if (cxp >= 0) load_at<T, VPT, NC>(Pxp + zoff, R, bx); else zero_blk(bx);
+        if (cym >= 0) load_at<T, VPT, NC>(Pym + zoff, R, ay); else zero_blk(ay);
+        if (cyp >= 0) load_at<T, VPT, NC>(Pyp + zoff, R, by); else zero_blk(by);
+      }
     } else {
       if (zp >= 0) load_at<T, VPT, NC>(Pc + zp * PS, R, xp);
       else zero_blk(xp);
@@ -582,7 +666,7 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
   }
 }
 
-template <typename T, int VPT, int FEAT, int DEPTH = 0>
+template <typename T, int VPT, int FEAT, int DEPTH = 0, int NBUF = 2>
 __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p) {
   extern __shared__ __align__(16) unsigned char ring[];  // DEPTH > 0: cp.async prefetch ring
   const int64_t plane = p.g.L[0] * p.g.L[1], Lz = p.g.L[2];
@@ -604,7 +688,7 @@ __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p)
     const int64_t tid = bx * blockDim.x + threadIdx.x;
     if (tid >= ncolthr) continue;
     const int64_t z0 = bz * zs, z1 = min(z0 + (int64_t)zs, Lz);
-    ti_march<T, VPT, true, DEPTH>(p.g, X, Yin, R, rc, tid / C, z0, z1, cf, ring,
+    ti_march<T, VPT, true, DEPTH, NBUF>(p.g, X, Yin, R, rc, tid / C, z0, z1, cf, ring,
                            [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
                              const int64_t sites[4] = {s, s, s, s};
                              epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
@@ -725,11 +809,19 @@ __global__ void __launch_bounds__(256) gr_sweep(const __grid_constant__ Sweep p)
   const T tt = T(p.g.t);
   DotAcc<T, VPT> dacc;
   dacc.init();
-  const int64_t nthr = ncell * C;
-  for (int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tid < nthr;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = tid / C;
-    const int64_t x = c % Nx, y = c / Nx;
+  // Grid-stride loop over cells with (x, y) carried along: C is a power of
+  // two and divides blockDim, so a thread keeps its chunk rc and the only
+  // 64-bit divisions are the two below, once per thread.
+  const int cshift = __ffs(C) - 1;
+  const int64_t cstride = ((int64_t)gridDim.x * blockDim.x) >> cshift;
+  const int64_t sy = cstride / Nx, sx = cstride - sy * Nx;
+  int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> cshift;
+  int64_t y = c / Nx, x = c - y * Nx;
+  for (; c < ncell; c += cstride, x += sx, y += sy) {
+    if (x >= Nx) {
+      x -= Nx;
+      ++y;
+    }
     const int64_t cxm = nbr_minus(c, x, Nx, p.g.per[0], 1);
     const int64_t cxp = nbr_plus(c, x, Nx, p.g.per[0], 1);
     const int64_t cym = nbr_minus(c, y, Ny, p.g.per[1], Nx);

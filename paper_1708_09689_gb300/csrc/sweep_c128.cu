@@ -15,7 +15,9 @@ static void* kernel_c128() {
   if constexpr (MODEL == 1) return reinterpret_cast<void*>(&ti_sweep<double, 1, FEAT>);
   else if constexpr (MODEL == kModelTIFlat) return reinterpret_cast<void*>(&ti_sweep_flat<double, 1, FEAT>);
   else if constexpr (MODEL == kModelTIAsync)
-    return reinterpret_cast<void*>(&ti_sweep<double, 1, FEAT, kAsyncDepth>);
+    return reinterpret_cast<void*>(&ti_sweep<double, 1, FEAT, kAsyncDepth, 6>);
+  else if constexpr (MODEL == kModelTIAsyncDeep)
+    return reinterpret_cast<void*>(&ti_sweep<double, 1, FEAT, kAsyncDeepDepth, 2>);
   else return reinterpret_cast<void*>(&gr_sweep<double, 1, FEAT>);
 }
 
@@ -37,6 +39,7 @@ static void* pick(int model, int feat) {
     case 1: return pick_c128<1>(feat);
     case kModelTIFlat: return pick_c128<kModelTIFlat>(feat);
     case kModelTIAsync: return pick_c128<kModelTIAsync>(feat);
+    case kModelTIAsyncDeep: return pick_c128<kModelTIAsyncDeep>(feat);
     default: return pick_c128<2>(feat);
   }
 }
@@ -62,7 +65,7 @@ int launch_sweep_c128(int model, int feat, int grid, int threads, const Sweep& p
                       cudaStream_t st) {
   void* fn = pick(model, feat);
   if (!fn) return set_error(PVSC_ERR_UNSUPPORTED, "no complex128 sweep for feature set %d", feat);
-  const size_t smem = model == kModelTIAsync ? async_ring_bytes(threads) : 0;
+  const size_t smem = async_ring_bytes(model, threads);
   if (smem)
     if (int rc = allow_max_smem(fn)) return rc;
   void* args[] = {const_cast<Sweep*>(&p)};
@@ -73,7 +76,7 @@ int launch_sweep_c128(int model, int feat, int grid, int threads, const Sweep& p
 int occupancy_c128(int model, int feat, int threads, int* blocks) {
   void* fn = pick(model, feat);
   if (!fn) return set_error(PVSC_ERR_UNSUPPORTED, "no complex128 sweep for feature set %d", feat);
-  const size_t smem = model == kModelTIAsync ? async_ring_bytes(threads) : 0;
+  const size_t smem = async_ring_bytes(model, threads);
   if (smem)
     if (int rc = allow_max_smem(fn)) return rc;
   PVSC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, threads, smem));

@@ -13,7 +13,9 @@ static void* kernel_c64() {
   if constexpr (MODEL == 1) return reinterpret_cast<void*>(&ti_sweep<float, VPT, FEAT>);
   else if constexpr (MODEL == kModelTIFlat) return reinterpret_cast<void*>(&ti_sweep_flat<float, VPT, FEAT>);
   else if constexpr (MODEL == kModelTIAsync)
-    return reinterpret_cast<void*>(&ti_sweep<float, VPT, FEAT, kAsyncDepth>);
+    return reinterpret_cast<void*>(&ti_sweep<float, VPT, FEAT, kAsyncDepth, 6>);
+  else if constexpr (MODEL == kModelTIAsyncDeep)
+    return reinterpret_cast<void*>(&ti_sweep<float, VPT, FEAT, kAsyncDeepDepth, 2>);
   else return reinterpret_cast<void*>(&gr_sweep<float, VPT, FEAT>);
 }
 
@@ -34,6 +36,8 @@ static void* pick(int model, int vpt, int feat) {
     case 1: return vpt == 1 ? pick_c64<1, 1>(feat) : pick_c64<1, 2>(feat);
     case kModelTIFlat: return vpt == 1 ? pick_c64<kModelTIFlat, 1>(feat) : pick_c64<kModelTIFlat, 2>(feat);
     case kModelTIAsync: return vpt == 1 ? pick_c64<kModelTIAsync, 1>(feat) : pick_c64<kModelTIAsync, 2>(feat);
+    case kModelTIAsyncDeep:
+      return vpt == 1 ? pick_c64<kModelTIAsyncDeep, 1>(feat) : pick_c64<kModelTIAsyncDeep, 2>(feat);
     default: return vpt == 1 ? pick_c64<2, 1>(feat) : pick_c64<2, 2>(feat);
   }
 }
@@ -42,7 +46,7 @@ int launch_sweep_c64(int model, int vpt, int feat, int grid, int threads, const 
                      cudaStream_t st) {
   void* fn = pick(model, vpt, feat);
   if (!fn) return set_error(PVSC_ERR_UNSUPPORTED, "no complex64 sweep for feature set %d", feat);
-  const size_t smem = model == kModelTIAsync ? async_ring_bytes(threads) : 0;
+  const size_t smem = async_ring_bytes(model, threads);
   if (smem)
     if (int rc = allow_max_smem(fn)) return rc;
   void* args[] = {const_cast<Sweep*>(&p)};
@@ -53,7 +57,7 @@ int launch_sweep_c64(int model, int vpt, int feat, int grid, int threads, const 
 int occupancy_c64(int model, int vpt, int feat, int threads, int* blocks) {
   void* fn = pick(model, vpt, feat);
   if (!fn) return set_error(PVSC_ERR_UNSUPPORTED, "no complex64 sweep for feature set %d", feat);
-  const size_t smem = model == kModelTIAsync ? async_ring_bytes(threads) : 0;
+  const size_t smem = async_ring_bytes(model, threads);
   if (smem)
     if (int rc = allow_max_smem(fn)) return rc;
   PVSC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, threads, smem));

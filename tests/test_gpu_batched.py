@@ -149,7 +149,7 @@ def test_staged_kpm_and_series_match_oracle():
         assert np.linalg.norm(y - ref_y) / np.linalg.norm(ref_y) < (1e-12 if prec == pv.C128 else 1e-5)
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 @pytest.mark.parametrize("dims,per", STAGED_CASES)
 @pytest.mark.parametrize("R", [1, 2, 8, 64])
 @pytest.mark.parametrize("prec", [pv.C128, pv.C64])

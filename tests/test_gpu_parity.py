@@ -243,11 +243,14 @@ def test_chebyshev_filter_matches_oracle():
         assert relerr(host(y), ref) < tol
 
 
-@pytest.mark.parametrize("K", [1, 2, 3, 4, 9])
-def test_cheb_series_short_and_in_place(K):
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 9, 10])
+@pytest.mark.parametrize("pattern", ["complex", "zeros"])
+def test_cheb_series_short_and_in_place(K, pattern):
     lat, H, _ = gr_pair((4, 5), (0, 0))
     a, b = O.cheb_scale(*O.gershgorin(H))
     c = np.exp(1j * np.arange(K)) / (1 + np.arange(K))
+    if pattern == "zeros":  # exact zeros, and purely real / imaginary weights in between
+        c = np.where(np.arange(K) % 3 == 1, 0.0, np.where(np.arange(K) % 2 == 0, c.real, 1j * c.imag))
     x = W.gaussian_block(H.shape[0], 1, 8)
     ref = np.exp(0.3j) * O.cheb_series(H, x, c, a, b)
     for prec, tol in ((pv.C128, C128_TOL), (pv.C64, 1e-5)):
@@ -269,6 +272,19 @@ def test_propagation_graphene_qd_small():
         pv.cheb_propagate(lat, psi, 1.0, 5, a, b, prec=prec)
         assert relerr(host(psi), ref) < tol
         assert abs(np.linalg.norm(host(psi)) - 1) < (1e-12 if prec == pv.C128 else 1e-5)
+
+
+def test_propagation_c64_norm_has_no_drift():
+    # The exact propagator is unitary.  complex64 vectors add rounding that
+    # varies with the data, so the norm error stays near the fp32 storage
+    # level over many steps; a series coefficient rounded the same way on
+    # every step would instead make it grow linearly (~1e-8 per step).
+    cfg = W.GrapheneConfig(cells=(96, 64), ndots=2, R_dot=10.0, sigma=8.0, packet_offset=30.0)
+    lat = pv.Lattice.graphene(cfg.cells, (0, 0), V=cfg.potential())
+    _, _, a, b = lat.spectral_bounds()
+    psi = dev(cfg.packet()[:, None])
+    pv.cheb_propagate(lat, psi, 1.0, 400, a, b, prec=pv.C64)
+    assert abs(torch.linalg.vector_norm(psi).item() - 1) < 5e-7
 
 
 def test_propagation_ti_block():
