@@ -77,6 +77,7 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
   pvsc_tuning cached;
   if (cache_lookup(key, &cached)) {
     lat->tuning[{R, prec}] = cached;
+    drop_graphs(lat);
     if (best) *best = cached;
     return PVSC_OK;
   }
@@ -133,10 +134,10 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
     p.counter = static_cast<unsigned*>(work);
     p.partials = reinterpret_cast<double*>(static_cast<char*>(work) + kWorkHeader);
     PVSC_CUDA_TRY(cudaMemsetAsync(work, 0, kWorkHeader, st));
-    if (int r = launch_sweep(lat, prec, F_DOTS, p, st)) return r;
+    if (int r = launch_sweep(lat, prec, F_KPM, p, st)) return r;
     PVSC_CUDA_TRY(cudaEventRecord(e0, st));
     for (int rep = 0; rep < 3; ++rep)
-      if (int r = launch_sweep(lat, prec, F_DOTS, p, st)) return r;
+      if (int r = launch_sweep(lat, prec, F_KPM, p, st)) return r;
     PVSC_CUDA_TRY(cudaEventRecord(e1, st));
     PVSC_CUDA_TRY(cudaEventSynchronize(e1));
     PVSC_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
@@ -183,6 +184,7 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
     return rc;
   }
   lat->tuning[{R, prec}] = win;
+  drop_graphs(lat);
   cache_store(key, win);
   if (best) *best = win;
   return PVSC_OK;

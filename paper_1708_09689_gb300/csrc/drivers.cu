@@ -124,7 +124,8 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
   const bool async = lat->g.model == PVSC_TI && (sh.kernel == 2 || sh.kernel == 3) &&
                      !(prec == PVSC_C64 && vpt == 1 && p.R > 1);
   const int model = flat ? kModelTIFlat
-                         : (async ? (sh.kernel == 2 ? kModelTIAsync : kModelTIAsyncDeep) : lat->g.model);
+                    : async ? (sh.kernel == 2 ? kModelTIAsync : kModelTIAsyncDeep)
+                            : lat->g.model;
   int rc = prec == PVSC_C128 ? occupancy_c128(model, feat, threads, &occ)
                              : occupancy_c64(model, vpt, feat, threads, &occ);
   if (rc) return rc;
@@ -461,7 +462,7 @@ int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, u
     p.yin = nullptr;
     p.yout = wb;
     p.dot_mode = 1;
-    if (int rc = launch_sweep(lat, prec, F_DOTS, p, cs)) return rc;
+    if (int rc = launch_sweep(lat, prec, F_KPM, p, cs)) return rc;
     const void* prev = x0;
     void* cur = wb;
     const int nsteps = (M + 1) / 2;
@@ -476,7 +477,7 @@ int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, u
       p.yin = prev;
       p.yout = out;
       p.kpm_k = k;
-      if (int rc = launch_sweep(lat, prec, F_DOTS, p, cs)) return rc;
+      if (int rc = launch_sweep(lat, prec, F_KPM, p, cs)) return rc;
       prev = cur;
       cur = out;
     }
@@ -657,6 +658,7 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
   if (int rc = check_common(lat, R, prec)) return rc;
   if (!tuning) {
     lat->tuning.erase({R, prec});
+    drop_graphs(lat);
     return PVSC_OK;
   }
   if (tuning->vpt < 0 || tuning->vpt > 2) return set_error(PVSC_ERR_ARG, "vpt must be 0, 1 or 2");
@@ -675,6 +677,7 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
                        tuning->tile_y);
   }
   lat->tuning[{R, prec}] = *tuning;
+  drop_graphs(lat);
   return PVSC_OK;
 }
 

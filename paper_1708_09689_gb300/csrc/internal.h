@@ -140,6 +140,18 @@ int launch_adjoint_top(const pvsc_lattice* lat, int R, const double2* G, double 
                        cudaStream_t st);
 
 // ---------------------------------------------------------------- CUDA graph cache
+// Drop every cached graph of the lattice: a graph holds the launch shapes and
+// kernel arguments it was captured with, so a new tuning or a new potential
+// mode makes it stale.
+inline void drop_graphs(pvsc_lattice* lat) {
+  std::lock_guard<std::mutex> lk(lat->mu);
+  for (auto& kv : lat->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  lat->graphs.clear();
+}
+
 inline bool graphs_enabled() {
   const char* e = std::getenv("PVSC_NO_GRAPH");
   return !(e && e[0] && e[0] != '0');

@@ -180,12 +180,7 @@ int pvsc_set_potential(pvsc_lattice* lat, const double* V_dev, void* stream) {
     lat->g.V32 = lat->V32_dev;
     lat->g.v_mode = 1;
     // cached graphs captured with V = 0 read no potential: drop them
-    std::lock_guard<std::mutex> lk(lat->mu);
-    for (auto& kv : lat->graphs) {
-      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-      if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
-    }
-    lat->graphs.clear();
+    drop_graphs(lat);
   }
   PVSC_CUDA_TRY(cudaMemcpyAsync(lat->V_dev, V_dev, sizeof(double) * lat->g.n_sites,
                                 cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));

@@ -20,7 +20,11 @@
 
 namespace pvsc {
 
-enum Feat { F_DOTS = 1, F_Z = 2, F_ACC = 4, F_ADJ = 8 };
+// F_DOTS: the dot products selected at run time by Sweep::dot_flags;
+// F_KPM: <x|x> and Re<y_new|x> only, fixed at compile time (the KPM sweep),
+// so the other accumulators take no registers.
+enum Feat { F_DOTS = 1, F_Z = 2, F_ACC = 4, F_ADJ = 8, F_KPM = 16 };
+__host__ __device__ constexpr bool has_dots(int feat) { return (feat & (F_DOTS | F_KPM)) != 0; }
 
 template <typename T, int VPT>
 struct Blk {
@@ -400,7 +404,7 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
       }
     }
   }
-  if constexpr ((FEAT & F_DOTS) != 0) {
+  if constexpr (has_dots(FEAT)) {
     // per-site products in T, accumulated per thread (compensated for fp32)
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
@@ -410,13 +414,17 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
         const cplx<T> a = xc.v[o][v], b = yn.v[o][v];
         xx = fma(a.re, a.re, fma(a.im, a.im, xx));
         xyr = fma(b.re, a.re, fma(b.im, a.im, xyr));
-        if (p.dot_flags & 2) xyi = fma(b.re, a.im, fma(-b.im, a.re, xyi));
-        if (p.dot_flags & 4) yy = fma(b.re, b.re, fma(b.im, b.im, yy));
+        if constexpr ((FEAT & F_DOTS) != 0) {
+          if (p.dot_flags & 2) xyi = fma(b.re, a.im, fma(-b.im, a.re, xyi));
+          if (p.dot_flags & 4) yy = fma(b.re, b.re, fma(b.im, b.im, yy));
+        }
       }
       dacc.add(0, v, xx);
       dacc.add(1, v, xyr);
-      if (p.dot_flags & 2) dacc.add(2, v, xyi);
-      if (p.dot_flags & 4) dacc.add(3, v, yy);
+      if constexpr ((FEAT & F_DOTS) != 0) {
+        if (p.dot_flags & 2) dacc.add(2, v, xyi);
+        if (p.dot_flags & 4) dacc.add(3, v, yy);
+      }
     }
   }
 }
@@ -493,6 +501,90 @@ __device__ __forceinline__ void ring_read(const unsigned char* buf, int nthr, Bl
     b.v[1][0] = {a.z, a.w};
     b.v[2][0] = {c.x, c.y};
     b.v[3][0] = {c.z, c.w};
+  }
+}
+
+// ---------------------------------------------------------------- TI stencil arithmetic
+// With S = sum over the two neighbours of an axis and d = x(n - e_j) - x(n + e_j),
+// the hopping part of Eq. TB_H_topi is -(t/2) (Gamma^1 S_total + sum_j (-i Gamma^{j+1}) d_j);
+// the -i Gamma^{j+1} are signed permutations: x axis (d3, d2, -d1, -d0),
+// y axis -i (d3, d2, d1, d0), z axis (d1, -d0, d3, -d2).
+template <typename T, int VPT>
+__device__ __forceinline__ void axis_z_init(const Blk<T, VPT>& a, const Blk<T, VPT>& b, Blk<T, VPT>& S,
+                                            Blk<T, VPT>& D) {
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    cplx<T> d[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      S.v[o][v] = cadd(a.v[o][v], b.v[o][v]);
+      d[o] = csub(a.v[o][v], b.v[o][v]);
+    }
+    D.v[0][v] = d[1];
+    D.v[1][v] = {-d[0].re, -d[0].im};
+    D.v[2][v] = d[3];
+    D.v[3][v] = {-d[2].re, -d[2].im};
+  }
+}
+
+template <typename T, int VPT>
+__device__ __forceinline__ void axis_x_add(const Blk<T, VPT>& a, const Blk<T, VPT>& b, Blk<T, VPT>& S,
+                                           Blk<T, VPT>& D) {
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    cplx<T> d[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      S.v[o][v] = cadd(S.v[o][v], cadd(a.v[o][v], b.v[o][v]));
+      d[o] = csub(a.v[o][v], b.v[o][v]);
+    }
+    D.v[0][v] = cadd(D.v[0][v], d[3]);
+    D.v[1][v] = cadd(D.v[1][v], d[2]);
+    D.v[2][v] = csub(D.v[2][v], d[1]);
+    D.v[3][v] = csub(D.v[3][v], d[0]);
+  }
+}
+
+template <typename T, int VPT>
+__device__ __forceinline__ void axis_y_add(const Blk<T, VPT>& a, const Blk<T, VPT>& b, Blk<T, VPT>& S,
+                                           Blk<T, VPT>& D) {
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    cplx<T> d[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      S.v[o][v] = cadd(S.v[o][v], cadd(a.v[o][v], b.v[o][v]));
+      d[o] = csub(a.v[o][v], b.v[o][v]);
+    }
+    // -i d = (d.im, -d.re)
+    D.v[0][v] = cadd(D.v[0][v], cplx<T>{d[3].im, -d[3].re});
+    D.v[1][v] = cadd(D.v[1][v], cplx<T>{d[2].im, -d[2].re});
+    D.v[2][v] = cadd(D.v[2][v], cplx<T>{d[1].im, -d[1].re});
+    D.v[3][v] = cadd(D.v[3][v], cplx<T>{d[0].im, -d[0].re});
+  }
+}
+
+// y_new = d_o x_o + kt (Gamma^1 S + D)_o + gamma y_in,  d_o = alpha (V - beta) +- alpha m
+template <typename T, int VPT>
+__device__ __forceinline__ void ti_combine(const VecCoef<T, VPT>& cf, T Vs, const Blk<T, VPT>& xc,
+                                           const Blk<T, VPT>& S, const Blk<T, VPT>& D,
+                                           const Blk<T, VPT>* yi, Blk<T, VPT>& yn) {
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    const T e = fma(cf.alpha[v], Vs, -cf.ab[v]);
+    const T dp = e + cf.am[v], dm = e - cf.am[v];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const T dd = (o & 1) ? dm : dp;
+      const cplx<T> Tt = (o & 1) ? csub(D.v[o][v], S.v[o][v]) : cadd(D.v[o][v], S.v[o][v]);
+      T re = fma(cf.kt[v], Tt.re, dd * xc.v[o][v].re);
+      T im = fma(cf.kt[v], Tt.im, dd * xc.v[o][v].im);
+      if (yi != nullptr) {
+        re = fma(cf.gamma[v], yi->v[o][v].re, re);
+        im = fma(cf.gamma[v], yi->v[o][v].im, im);
+      }
+      yn.v[o][v] = {re, im};
+    }
   }
 }
 
@@ -591,75 +683,11 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
     }
     const T Vs = site_potential_t<T>(g, s);
     Blk<T, VPT> S, D;
-    // z axis: s_z, d_z
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      cplx<T> d[4];
-#pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        S.v[o][v] = cadd(xm.v[o][v], xp.v[o][v]);
-        d[o] = csub(xm.v[o][v], xp.v[o][v]);
-      }
-      D.v[0][v] = d[1];
-      D.v[1][v] = {-d[0].re, -d[0].im};
-      D.v[2][v] = d[3];
-      D.v[3][v] = {-d[2].re, -d[2].im};
-    }
-    // x axis
-    {
-      const Blk<T, VPT>& a = ax;
-      const Blk<T, VPT>& b = bx;
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        cplx<T> d[4];
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          S.v[o][v] = cadd(S.v[o][v], cadd(a.v[o][v], b.v[o][v]));
-          d[o] = csub(a.v[o][v], b.v[o][v]);
-        }
-        D.v[0][v] = cadd(D.v[0][v], d[3]);
-        D.v[1][v] = cadd(D.v[1][v], d[2]);
-        D.v[2][v] = csub(D.v[2][v], d[1]);
-        D.v[3][v] = csub(D.v[3][v], d[0]);
-      }
-    }
-    // y axis: -i d = (d.im, -d.re)
-    {
-      const Blk<T, VPT>& a = ay;
-      const Blk<T, VPT>& b = by;
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        cplx<T> d[4];
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          S.v[o][v] = cadd(S.v[o][v], cadd(a.v[o][v], b.v[o][v]));
-          d[o] = csub(a.v[o][v], b.v[o][v]);
-        }
-        D.v[0][v] = cadd(D.v[0][v], cplx<T>{d[3].im, -d[3].re});
-        D.v[1][v] = cadd(D.v[1][v], cplx<T>{d[2].im, -d[2].re});
-        D.v[2][v] = cadd(D.v[2][v], cplx<T>{d[1].im, -d[1].re});
-        D.v[3][v] = cadd(D.v[3][v], cplx<T>{d[0].im, -d[0].re});
-      }
-    }
-    // y_new = d_o x_o + kt (Gamma^1 S + D)_o + gamma y_in,  d_o = alpha (V - beta) +- alpha m
+    axis_z_init(xm, xp, S, D);
+    axis_x_add(ax, bx, S, D);
+    axis_y_add(ay, by, S, D);
     Blk<T, VPT> yn;
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      const T e = fma(cf.alpha[v], Vs, -cf.ab[v]);
-      const T dp = e + cf.am[v], dm = e - cf.am[v];
-#pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        const T dd = (o & 1) ? dm : dp;
-        const cplx<T> Tt = (o & 1) ? csub(D.v[o][v], S.v[o][v]) : cadd(D.v[o][v], S.v[o][v]);
-        T re = fma(cf.kt[v], Tt.re, dd * xc.v[o][v].re);
-        T im = fma(cf.kt[v], Tt.im, dd * xc.v[o][v].im);
-        if (Yin != nullptr) {
-          re = fma(cf.gamma[v], yi.v[o][v].re, re);
-          im = fma(cf.gamma[v], yi.v[o][v].im, im);
-        }
-        yn.v[o][v] = {re, im};
-      }
-    }
+    ti_combine(cf, Vs, xc, S, D, Yin != nullptr ? &yi : nullptr, yn);
     emit(s, xc, yn);
     xm = xc;
     xc = xp;
@@ -693,9 +721,9 @@ __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p)
                              const int64_t sites[4] = {s, s, s, s};
                              epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
                            });
-    if constexpr ((FEAT & F_DOTS) != 0) dacc.flush();  // one fp64 add per column segment
+    if constexpr (has_dots(FEAT)) dacc.flush();  // one fp64 add per column segment
   }
-  if constexpr ((FEAT & F_DOTS) != 0) {
+  if constexpr (has_dots(FEAT)) {
     dacc.flush();
     reduce_dots<VPT>(p, dacc.d);
   }
@@ -784,7 +812,7 @@ __global__ void __launch_bounds__(256, 2) ti_sweep_flat(const __grid_constant__ 
     const int64_t sites[4] = {s, s, s, s};
     epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
   }
-  if constexpr ((FEAT & F_DOTS) != 0) {
+  if constexpr (has_dots(FEAT)) {
     dacc.flush();
     reduce_dots<VPT>(p, dacc.d);
   }
@@ -887,7 +915,7 @@ __global__ void __launch_bounds__(256) gr_sweep(const __grid_constant__ Sweep p)
     const int64_t sites[4] = {4 * c, 4 * c + 1, 4 * c + 2, 4 * c + 3};
     epilogue<T, VPT, FEAT>(p, c, rc, xc, yn, dacc, sites);
   }
-  if constexpr ((FEAT & F_DOTS) != 0) {
+  if constexpr (has_dots(FEAT)) {
     dacc.flush();
     reduce_dots<VPT>(p, dacc.d);
   }

@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(256) ti_sweep_bulk(const __grid_constant__ Swe
     if (threadIdx.x == 0) atomicExch(&g_bulk_sweep_error, 1);
     return;
   }
-  if constexpr ((FEAT & F_DOTS) != 0) {
+  if constexpr (has_dots(FEAT)) {
     dacc.flush();
     reduce_dots<1>(p, dacc.d);
   }

@@ -174,6 +174,32 @@ def test_flat_and_prefetching_sweeps_match_oracle(kernel, dims, per, R, prec):
         assert np.max(np.abs(d[1] - dr[:, 1].real)) < 10 * tol * np.abs(dr).max()
 
 
+def test_new_tuning_replaces_captured_kpm_graph():
+    # kpm_moments replays a captured CUDA graph; a later set_tuning must take
+    # effect (the moments then equal those of a lattice tuned that way from the start)
+    dims, R, M = (12, 10, 14), 4, 24
+    shape_a = dict(threads=64, zslab=2, vpt=2)
+    shape_b = dict(threads=256, zslab=0, vpt=1)
+
+    def moments(lat, work, mu):  # same buffers on every call: the graph key repeats
+        _, _, a, b = lat.spectral_bounds()
+        pv.kpm_moments(lat, M, a, b, R=R, prec=pv.C64, seed=11, work=work, mu=mu)
+        return mu.cpu().numpy()
+
+    lat1 = pv.Lattice.ti(dims, (1, 1, 0), disorder=(1.0, 4))
+    work = pv.work_buffer(lat1.work_bytes(pv.OP_KPM, R, pv.C64, M))
+    mu = torch.empty((R, M), dtype=torch.float64, device="cuda")
+    lat1.set_tuning(R, pv.C64, **shape_a)
+    mu_a = moments(lat1, work, mu)
+    lat1.set_tuning(R, pv.C64, **shape_b)
+    mu_b1 = moments(lat1, work, mu)
+    lat2 = pv.Lattice.ti(dims, (1, 1, 0), disorder=(1.0, 4))
+    lat2.set_tuning(R, pv.C64, **shape_b)
+    mu_b2 = moments(lat2, work, mu)
+    assert np.array_equal(mu_b1, mu_b2)
+    assert np.max(np.abs(mu_a - mu_b2)) < 1e-5
+
+
 def test_explicit_tuning_shapes_all_agree():
     lat = pv.Lattice.ti((9, 11, 13), (0, 1, 1), disorder=(1.0, 8))
     x = torch.from_numpy(W.gaussian_block(lat.D, 16, 1)).cuda().to(torch.complex64)
