@@ -24,7 +24,13 @@
  *   recurrence vectors as complex64 and computes the stencil in fp32, while
  *   dot products, moments, the scaling (a, b), the Bessel coefficients and the
  *   propagation accumulator stay fp64.  Vectors the caller passes as
- *   "complex128" are complex128 in both precisions.
+ *   "complex128" are complex128 in both precisions.  PVSC_Q64 (pvsc_kpm_moments
+ *   on TI lattices only) keeps complex128-sized vectors as pairs of 64-bit
+ *   fixed-point integers: each start vector is scaled by an exact power of two
+ *   to 2-norm <= 1, values carry 59 fraction bits, stencil sums are exact
+ *   integer additions and each update is rounded once at 2^-60; the dot
+ *   products are exact 128-bit integer sums converted to fp64.  Moments agree
+ *   with the fp64 path to ~1e-15.
  * R.  1, 2, 4, 8, 16, 32 or 64 vectors per block.
  * Memory.  Every vector, work buffer and output pointer is a DEVICE pointer
  *   owned by the caller, 16-byte aligned; the library owns only the lattice
@@ -59,7 +65,7 @@ typedef enum {
 } pvsc_status;
 
 enum { PVSC_TI = 1, PVSC_GRAPHENE = 2 };
-enum { PVSC_C128 = 0, PVSC_C64 = 1 };
+enum { PVSC_C128 = 0, PVSC_C64 = 1, PVSC_Q64 = 2 };
 
 /* Source of the on-site potential V (one fp64 value per site). */
 enum {
@@ -203,6 +209,9 @@ int pvsc_cheb_step_noalloc(const pvsc_lattice* lat, int R, int prec, const void*
  * with stream 1 and idx = r D + i.  mu: device array [R][M] of doubles.
  * M >= 1.  The step loop is captured once into a CUDA graph per argument set
  * and replayed; the first call for a new argument set captures.
+ * prec == PVSC_Q64 (TI only): r0, if given, is complex128 and is not modified;
+ * [b - a, b + a] must hold the Gershgorin interval of H (PVSC_ERR_ARG
+ * otherwise; checked by one synchronous pass over the potential per call).
  * work: pvsc_work_bytes(lat, PVSC_OP_KPM, R, prec, M).
  */
 int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, uint64_t seed,

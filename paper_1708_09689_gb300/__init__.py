@@ -24,7 +24,7 @@ from .build import LIB_PATH
 PVSC_OK, PVSC_ERR_ARG, PVSC_ERR_CUDA, PVSC_ERR_OOM, PVSC_ERR_TIMEOUT, PVSC_ERR_UNSUPPORTED = \
     0, -1, -2, -3, -4, -5
 TI, GRAPHENE = 1, 2
-C128, C64 = 0, 1
+C128, C64, Q64 = 0, 1, 2  # Q64: fixed-point vectors, pvsc_kpm_moments on TI only
 V_ZERO, V_HOST, V_DEVICE, V_SEED, V_ON_THE_FLY = 0, 1, 2, 3, 4
 DOT_XX, DOT_XY, DOT_YY = 1, 2, 4
 OP_APPLY, OP_CHEB_STEP, OP_KPM, OP_SERIES, OP_ADJOINT, OP_KPM_BATCHED = 0, 1, 2, 3, 4, 5
@@ -328,7 +328,10 @@ def kpm_moments(lat: Lattice, M: int, a: float, b: float, R: int = 1, prec: int 
                 r0: torch.Tensor | None = None, seed: int = 0, work=None, mu=None, stream=None):
     """Per-vector KPM moments mu[r, k] = <r|T_k(H~)|r>, a float64 tensor (R, M)."""
     if r0 is not None:
-        R, prec = block_R(r0), prec_of(r0)
+        if prec == Q64 and r0.dtype != torch.complex128:
+            raise PvscError("Q64 moments take a complex128 start block")
+        R = block_R(r0)
+        prec = Q64 if prec == Q64 else prec_of(r0)
     mu = torch.empty((R, M), dtype=torch.float64, device="cuda") if mu is None else mu
     if work is None:
         work = work_buffer(lat.work_bytes(OP_KPM, R, prec, M))

@@ -161,7 +161,11 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
         }
         if (active) {
           // x is written by this kernel in other phases: coherent loads only (NC = false)
-          ti_march<T, VPT, false, 0, 2>(L.g, X, Yin, R, rc, col, z0, z1, cf, nullptr,
+          ti_march<T, VPT, false, 0, 2>(L.g, X, Yin, R, rc, col, z0, z1, nullptr,
+                                  [&](int64_t s, const Blk<T, VPT>& xc, const Blk<T, VPT>& S,
+                                      const Blk<T, VPT>& D, const Blk<T, VPT>* yi, Blk<T, VPT>& yn) {
+                                    ti_combine(cf, site_potential_t<T>(L.g, s), xc, S, D, yi, yn);
+                                  },
                                   [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
                                     store_blk<T, VPT>(Yout, s, R, rc, yn);
 #pragma unroll

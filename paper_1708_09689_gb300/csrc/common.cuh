@@ -126,6 +126,11 @@ struct Sweep {
   double* mu;            // [R][M]
   int M;
   int kpm_k;
+  // fixed-point KPM sweep (sweep_fx.cu)
+  const void* fx_d;      // per site (d_+, d_-) in Q3.60 for alpha = 1/a
+  long long fx_kt;       // -alpha t / 2 in Q3.60
+  int fx_dshift;         // 1: alpha = 2/a (d doubled)
+  const double* vscale;  // per vector: value of one unit of a dot product
   int zslab;             // TI z-marching depth
   int tile_x, tile_y;    // TI shared-memory staged sweep: tile of columns (0: register marching)
 };

@@ -170,6 +170,7 @@ static uint64_t bits(const void* p) { return (uint64_t)reinterpret_cast<uintptr_
 static int check_common(const pvsc_lattice* lat, int R, int prec) {
   if (int rc = check_lattice(lat)) return rc;
   if (!valid_R(R)) return set_error(PVSC_ERR_ARG, "R = %d: must be 1, 2, 4, 8, 16, 32 or 64", R);
+  if (prec == PVSC_Q64) return set_error(PVSC_ERR_ARG, "PVSC_Q64 is a precision of pvsc_kpm_moments only");
   if (prec != PVSC_C128 && prec != PVSC_C64) return set_error(PVSC_ERR_ARG, "unknown precision %d", prec);
   return PVSC_OK;
 }
@@ -335,6 +336,7 @@ using namespace pvsc;
 extern "C" {
 
 size_t pvsc_work_bytes(const pvsc_lattice* lat, int op, int R, int prec, int M) {
+  if (lat && valid_R(R) && prec == PVSC_Q64 && op == PVSC_OP_KPM) return fx_layout(lat, R).total;
   if (!lat || !valid_R(R) || (prec != PVSC_C128 && prec != PVSC_C64)) return 0;
   switch (op) {
     case PVSC_OP_APPLY:
@@ -421,9 +423,93 @@ int pvsc_cheb_step(const pvsc_lattice* lat, int R, int prec, const void* x, void
   return launch_sweep(lat, prec, feat, p, st);
 }
 
+// KPM with fixed-point vectors (sweep_fx.cu); TI lattices only.
+static int kpm_moments_fx(const pvsc_lattice* lat, int R, const void* r0, uint64_t seed, int M,
+                          double a, double b, double* mu, void* work, size_t work_bytes,
+                          cudaStream_t st) {
+  if (lat->g.model != PVSC_TI)
+    return set_error(PVSC_ERR_UNSUPPORTED, "PVSC_Q64 moments are implemented for the TI lattice only");
+  const FxLayout L = fx_layout(lat, R);
+  if (int rc = check_work(work, work_bytes, L.total)) return rc;
+  // The fixed-point range relies on ||T_k(H~)|| <= 1: (a, b) must hold the
+  // Gershgorin interval (one synchronous pass over the potential).
+  {
+    const int grid = 2 * lat->sm_count;
+    double* gw = reinterpret_cast<double*>(wptr(work, kWorkHeader));
+    if (int rc = launch_gershgorin(lat->g, gw, grid, st)) return rc;
+    std::vector<double> h(2 * grid);
+    PVSC_CUDA_TRY(cudaMemcpyAsync(h.data(), gw, sizeof(double) * 2 * grid, cudaMemcpyDeviceToHost, st));
+    PVSC_CUDA_TRY(cudaStreamSynchronize(st));
+    double lo = h[0], hi = h[1];
+    for (int i = 1; i < grid; ++i) {
+      lo = std::fmin(lo, h[2 * i]);
+      hi = std::fmax(hi, h[2 * i + 1]);
+    }
+    const double slack = 1e-12 * a;
+    if (lo < b - a - slack || hi > b + a + slack)
+      return set_error(PVSC_ERR_ARG,
+                       "PVSC_Q64 needs [b - a, b + a] to hold the spectrum bound [%.17g, %.17g] "
+                       "(a = %.17g, b = %.17g)", lo, hi, a, b);
+  }
+  const std::vector<uint64_t> key = {7, (uint64_t)R, (uint64_t)PVSC_Q64, bits(r0), seed, (uint64_t)M,
+                                     bits(a), bits(b), bits(mu), bits(work)};
+  const LaunchShape sh = shape_for(lat, R, PVSC_Q64);
+  const bool tuned = lat->tuning.count({R, PVSC_Q64}) != 0;
+  auto body = [&](cudaStream_t cs) -> int {
+    PVSC_CUDA_TRY(cudaMemsetAsync(work, 0, kWorkHeader, cs));
+    if (int rc = launch_fx_prepare(lat, R, r0, seed, a, b, work, L, cs)) return rc;
+    void* wa = wptr(work, L.wa);
+    void* wb = wptr(work, L.wb);
+    Sweep p;
+    sweep_init(p, lat, R, PVSC_C128);
+    p.C = R;
+    p.counter = reinterpret_cast<unsigned*>(work);
+    p.partials = reinterpret_cast<double*>(wptr(work, kWorkHeader));
+    p.mu = mu;
+    p.M = M;
+    p.dot_flags = 3;
+    p.fx_d = wptr(work, L.dfx);
+    p.vscale = reinterpret_cast<const double*>(wptr(work, L.vscale));
+    p.x = wa;
+    p.yin = nullptr;
+    p.yout = wb;
+    p.dot_mode = 1;
+    p.fx_dshift = 0;
+    p.fx_kt = std::llrint(std::ldexp(-0.5 * lat->g.t / a, 60));
+    if (int rc = launch_sweep_fx(lat, p, sh, tuned, cs)) return rc;
+    void* prev = wa;
+    void* cur = wb;
+    p.fx_dshift = 1;
+    p.fx_kt = std::llrint(std::ldexp(-lat->g.t / a, 60));
+    p.dot_mode = 2;
+    const int nsteps = (M + 1) / 2;
+    for (int k = 1; k < nsteps; ++k) {
+      p.x = cur;
+      p.yin = prev;
+      p.yout = prev;  // w_{k+1} overwrites w_{k-1} element by element
+      p.kpm_k = k;
+      if (int rc = launch_sweep_fx(lat, p, sh, tuned, cs)) return rc;
+      std::swap(prev, cur);
+    }
+    return PVSC_OK;
+  };
+  return run_graph(lat, key, st, body);
+}
+
 int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, uint64_t seed,
                      int M, double a, double b, double* mu, void* work, size_t work_bytes,
                      void* stream) {
+  if (prec == PVSC_Q64) {
+    if (int rc = check_lattice(lat)) return rc;
+    if (!valid_R(R)) return set_error(PVSC_ERR_ARG, "R = %d: must be 1, 2, 4, 8, 16, 32 or 64", R);
+    if (int rc = check_scaling(a, b)) return rc;
+    if (M < 1) return set_error(PVSC_ERR_ARG, "M = %d < 1", M);
+    if (!mu) return set_error(PVSC_ERR_ARG, "mu is NULL");
+    if (r0)
+      if (int rc = check_ptr(r0, "r0")) return rc;
+    return kpm_moments_fx(lat, R, r0, seed, M, a, b, mu, work, work_bytes,
+                          static_cast<cudaStream_t>(stream));
+  }
   if (int rc = check_common(lat, R, prec)) return rc;
   if (int rc = check_scaling(a, b)) return rc;
   if (M < 1) return set_error(PVSC_ERR_ARG, "M = %d < 1", M);
@@ -654,7 +740,29 @@ int pvsc_device_error(int* flag, int clear) {
   return PVSC_OK;
 }
 
+// Launch shapes of the fixed-point KPM sweep: kernel 0, 2 or 3, one vector per thread.
+static int check_q64_tuning(const pvsc_lattice* lat, int R, const pvsc_tuning* t) {
+  if (int rc = check_lattice(lat)) return rc;
+  if (!valid_R(R)) return set_error(PVSC_ERR_ARG, "R = %d: must be 1, 2, 4, 8, 16, 32 or 64", R);
+  if (lat->g.model != PVSC_TI) return set_error(PVSC_ERR_UNSUPPORTED, "PVSC_Q64 is for the TI lattice only");
+  if (!t) return PVSC_OK;
+  if (t->kernel != 0 && t->kernel != 2 && t->kernel != 3)
+    return set_error(PVSC_ERR_ARG, "PVSC_Q64 kernels are 0, 2 and 3");
+  if (t->vpt > 1 || t->tile_x || t->tile_y)
+    return set_error(PVSC_ERR_ARG, "PVSC_Q64 sweeps take one vector per thread and no staged tile");
+  if (t->threads < 32 || t->threads > kMaxThreads || t->threads % 32 || t->threads % R)
+    return set_error(PVSC_ERR_ARG, "threads must be a multiple of 32 and of R, at most %d", kMaxThreads);
+  if (t->blocks_per_sm < 0 || t->zslab < 0) return set_error(PVSC_ERR_ARG, "negative tuning value");
+  return PVSC_OK;
+}
+
 int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tuning) {
+  if (prec == PVSC_Q64) {
+    if (int rc = check_q64_tuning(lat, R, tuning)) return rc;
+    if (tuning) lat->tuning[{R, prec}] = *tuning; else lat->tuning.erase({R, prec});
+    drop_graphs(lat);
+    return PVSC_OK;
+  }
   if (int rc = check_common(lat, R, prec)) return rc;
   if (!tuning) {
     lat->tuning.erase({R, prec});
@@ -682,8 +790,18 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
 }
 
 int pvsc_get_tuning(const pvsc_lattice* lat, int R, int prec, pvsc_tuning* tuning) {
-  if (int rc = check_common(lat, R, prec)) return rc;
   if (!tuning) return set_error(PVSC_ERR_ARG, "tuning is NULL");
+  if (prec == PVSC_Q64) {
+    if (int rc = check_q64_tuning(lat, R, nullptr)) return rc;
+    auto it = lat->tuning.find({R, prec});
+    if (it != lat->tuning.end()) {
+      *tuning = it->second;
+    } else {
+      *tuning = pvsc_tuning{128, 0, 0, 0.f, 1, 0, 0, R >= 2 ? 2 : 0};
+    }
+    return PVSC_OK;
+  }
+  if (int rc = check_common(lat, R, prec)) return rc;
   auto it = lat->tuning.find({R, prec});
   if (it != lat->tuning.end()) {
     *tuning = it->second;

@@ -68,6 +68,17 @@ int occupancy_bulk(int prec, int feat, int threads, size_t smem, int* blocks);
 int bulk_sweep_error(int prec, int clear, int* flag);
 size_t bulk_smem_bytes(int TX, int TY, int R, int prec);
 
+// fixed-point KPM (sweep_fx.cu): work layout (byte offsets) and launchers
+struct FxLayout {
+  int nb;
+  size_t part, xscale, vscale, dfx, wa, wb, total;
+};
+FxLayout fx_layout(const pvsc_lattice* lat, int R);
+int launch_fx_prepare(const pvsc_lattice* lat, int R, const void* r0, uint64_t seed, double a,
+                      double b, void* work, const FxLayout& L, cudaStream_t st);
+int launch_sweep_fx(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, bool tuned,
+                    cudaStream_t st);
+
 // Vectors per thread for (R, prec) under an optional tuned value.
 int vpt_tuned(int tuned, int R, int prec);
 

@@ -26,6 +26,10 @@ namespace pvsc {
 enum Feat { F_DOTS = 1, F_Z = 2, F_ACC = 4, F_ADJ = 8, F_KPM = 16 };
 __host__ __device__ constexpr bool has_dots(int feat) { return (feat & (F_DOTS | F_KPM)) != 0; }
 
+// 16-byte vector of two 8-byte elements: complex128 (re, im) or the fixed-point pair
+template <typename T> struct Pair16 { using type = double2; };
+template <> struct Pair16<long long> { using type = longlong2; };
+
 template <typename T, int VPT>
 struct Blk {
   cplx<T> v[4][VPT];
@@ -84,9 +88,9 @@ __device__ __forceinline__ void store_blk(T* __restrict__ base, int64_t s, int R
                                           const Blk<T, VPT>& b) {
   T* p = base + 2 * ((s * 4) * (int64_t)R + rc * VPT);
   if constexpr (sizeof(T) == 8) {
+    using P2 = typename Pair16<T>::type;
 #pragma unroll
-    for (int o = 0; o < 4; ++o)
-      *reinterpret_cast<double2*>(p + 2 * o * R) = make_double2(b.v[o][0].re, b.v[o][0].im);
+    for (int o = 0; o < 4; ++o) *reinterpret_cast<P2*>(p + 2 * o * R) = P2{b.v[o][0].re, b.v[o][0].im};
   } else if constexpr (VPT == 1) {
     if (R == 1) {
       float4* q = reinterpret_cast<float4*>(p);
@@ -110,10 +114,11 @@ __device__ __forceinline__ void store_blk(T* __restrict__ base, int64_t s, int R
 template <typename T, int VPT, bool RO>
 __device__ __forceinline__ void load_at(const T* __restrict__ p, int R, Blk<T, VPT>& b) {
   if constexpr (sizeof(T) == 8) {
+    using P2 = typename Pair16<T>::type;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
-      const double2* q = reinterpret_cast<const double2*>(p + 2 * o * R);
-      double2 a = RO ? __ldg(q) : *q;
+      const P2* q = reinterpret_cast<const P2*>(p + 2 * o * R);
+      P2 a = RO ? __ldg(q) : *q;
       b.v[o][0] = {a.x, a.y};
     }
   } else if constexpr (VPT == 1) {
@@ -482,9 +487,10 @@ __device__ __forceinline__ void ring_issue(unsigned char* buf, int nthr, const T
 template <typename T, int VPT>
 __device__ __forceinline__ void ring_read(const unsigned char* buf, int nthr, Blk<T, VPT>& b) {
   if constexpr (sizeof(T) == 8) {
+    using P2 = typename Pair16<T>::type;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
-      const double2 a = *reinterpret_cast<const double2*>(buf + (size_t)o * nthr * 16);
+      const P2 a = *reinterpret_cast<const P2*>(buf + (size_t)o * nthr * 16);
       b.v[o][0] = {a.x, a.y};
     }
   } else if constexpr (VPT == 2) {
@@ -588,11 +594,11 @@ __device__ __forceinline__ void ti_combine(const VecCoef<T, VPT>& cf, T Vs, cons
   }
 }
 
-template <typename T, int VPT, bool NC, int DEPTH, int NBUF, class Emit>
+template <typename T, int VPT, bool NC, int DEPTH, int NBUF, class Combine, class Emit>
 __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict__ X,
                                          const T* __restrict__ Yin, int R, int rc, int64_t col,
-                                         int64_t z0, int64_t z1, const VecCoef<T, VPT>& cf,
-                                         unsigned char* ring, Emit&& emit) {
+                                         int64_t z0, int64_t z1, unsigned char* ring,
+                                         Combine&& combine, Emit&& emit) {
   const int64_t Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
   const int64_t plane = Lx * Ly;
   const int64_t x = col % Lx, y = col / Lx;
@@ -681,13 +687,12 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
       if (cym >= 0) load_at<T, VPT, NC>(Pym + zoff, R, ay); else zero_blk(ay);
       if (cyp >= 0) load_at<T, VPT, NC>(Pyp + zoff, R, by); else zero_blk(by);
     }
-    const T Vs = site_potential_t<T>(g, s);
     Blk<T, VPT> S, D;
     axis_z_init(xm, xp, S, D);
     axis_x_add(ax, bx, S, D);
     axis_y_add(ay, by, S, D);
     Blk<T, VPT> yn;
-    ti_combine(cf, Vs, xc, S, D, Yin != nullptr ? &yi : nullptr, yn);
+    combine(s, xc, S, D, Yin != nullptr ? &yi : nullptr, yn);
     emit(s, xc, yn);
     xm = xc;
     xc = xp;
@@ -716,7 +721,11 @@ __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p)
     const int64_t tid = bx * blockDim.x + threadIdx.x;
     if (tid >= ncolthr) continue;
     const int64_t z0 = bz * zs, z1 = min(z0 + (int64_t)zs, Lz);
-    ti_march<T, VPT, true, DEPTH, NBUF>(p.g, X, Yin, R, rc, tid / C, z0, z1, cf, ring,
+    ti_march<T, VPT, true, DEPTH, NBUF>(p.g, X, Yin, R, rc, tid / C, z0, z1, ring,
+                           [&](int64_t s, const Blk<T, VPT>& xc, const Blk<T, VPT>& S,
+                               const Blk<T, VPT>& D, const Blk<T, VPT>* yi, Blk<T, VPT>& yn) {
+                             ti_combine(cf, site_potential_t<T>(p.g, s), xc, S, D, yi, yn);
+                           },
                            [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
                              const int64_t sites[4] = {s, s, s, s};
                              epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
