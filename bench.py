@@ -79,9 +79,13 @@ def parse():
                          "workloads (16^3 cube KPM, graphene QD-array propagation, batched KPM over "
                          "64 lattices, adjoint gradient) and print one JSON line each")
     ap.add_argument("--sweeps-only", type=int, default=0,
-                    help="profiling case: run this many complex64 KPM-type sweeps (stencil, "
+                    help="profiling case: one KPM call of this many complex64 sweeps (stencil, "
                          "recurrence, dots) on the lattice (ti_slab), or this many complex64 "
                          "propagation time steps (graphene_qd), and exit without timing")
+    ap.add_argument("--batched-count", type=int, default=8,
+                    help="with --workload batched --sweeps-only: number of lattices of the batch")
+    ap.add_argument("--q64", action="store_true",
+                    help="with --sweeps-only: the fixed-point (PVSC_Q64) KPM sweep instead")
     ap.add_argument("--launch", default=None,
                     help="JSON launch shape (threads, blocks_per_sm, zslab, vpt, tile_x, tile_y, kernel) "
                          "to use instead of autotuning, e.g. for profiling runs")
@@ -349,9 +353,22 @@ def run_workload(args, pv, dev, rank, world):
                      "clocks": clk, "gpu_launches": (nterms) * n64})
     elif args.workload == "batched":
         specs = W.batched_lattices()
+        if args.sweeps_only:  # profiling case: the first --batched-count lattices, untimed
+            specs = specs[:args.batched_count]
         lats = [pv.Lattice.ti((L, L, L), (1, 1, 1), disorder=(Wd, s)) for L, Wd, s in specs]
         ab = [lat.spectral_bounds()[2:] for lat in lats]
         R, M = 16, 1024
+        if args.sweeps_only:
+            M = 2 * args.sweeps_only
+            work = pv.work_buffer(pv.batched_work_bytes(lats, R, pv.C64, M), dev)
+            mu = pv.kpm_moments_batched(lats, M, [x[0] for x in ab], [x[1] for x in ab], R=R,
+                                        prec=pv.C64, seeds=[vector_seed_for(i, rank) for i in range(len(lats))],
+                                        work=work)
+            torch.cuda.synchronize()
+            if rank == 0:
+                print(json.dumps({"lattices": [L for L, _, _ in specs], "R": R, "moments": M,
+                                  "mu0_min": float(mu[:, :, 0].min().item())}))
+            return 0
         seeds = [vector_seed_for(i, rank) for i in range(len(lats))]
         work = pv.work_buffer(pv.batched_work_bytes(lats, R, pv.C64, M), dev)
         mu = torch.empty((len(lats), R, M), dtype=torch.float64, device=dev)
@@ -474,13 +491,16 @@ def main():
     else:
         tuning = None if args.no_autotune else lat.autotune(R, pv.C64)
     if args.sweeps_only:
-        x = pv.random_vectors(lat, R, pv.C64, seed)
-        y = pv.random_vectors(lat, R, pv.C64, seed + 1)
-        w = pv.work_buffer(lat.work_bytes(pv.OP_CHEB_STEP, R, pv.C64), dev)
-        for _ in range(args.sweeps_only):
-            pv.cheb_step(lat, x, y, [2.0 / a] * R, [b] * R, [-1.0] * R, dots=3, work=w)
+        # one KPM call of this many sweeps (2 x sweeps moments) in the benchmark's kernel,
+        # or in the fixed-point kernel with --q64
+        prec = pv.Q64 if args.q64 else pv.C64
+        r0 = pv.random_vectors(lat, R, pv.C128 if args.q64 else pv.C64, seed)
+        Ms = 2 * args.sweeps_only
+        w = pv.work_buffer(lat.work_bytes(pv.OP_KPM, R, prec, Ms), dev)
+        mu = pv.kpm_moments(lat, Ms, a, b, r0=r0, prec=prec, work=w)
         torch.cuda.synchronize()
-        print(json.dumps({"sweeps": args.sweeps_only, "dims": list(dims), "R": R, "launch": tuning}))
+        print(json.dumps({"sweeps": args.sweeps_only, "dims": list(dims), "R": R, "q64": args.q64,
+                          "launch": tuning, "mu_0": float(mu[0, 0].item())}))
         return 0
     # start block: random-phase vectors from the counter hash, generated on the device
     r0 = pv.random_vectors(lat, R, pv.C64, seed)
@@ -542,6 +562,25 @@ def main():
                    "c128_moments": Mc, "c64_vs_c128_max_dmu": err,
                    "c128_bound": "fp64 pipe (0.50 T instr/s measured on GB300)"}
         del w128
+        # fixed-point vectors of the same size (exact integer stencil): same start block
+        wq = pv.work_buffer(lat.work_bytes(pv.OP_KPM, R, pv.Q64, Mc), dev)
+        muq = torch.empty((R, Mc), dtype=torch.float64, device=dev)
+        pv.kpm_moments(lat, Mc, a, b, r0=r0d, prec=pv.Q64, work=wq, mu=muq)
+        barrier()
+        c0.record(stream)
+        pv.kpm_moments(lat, Mc, a, b, r0=r0d, prec=pv.Q64, work=wq, mu=muq)
+        c1.record(stream)
+        barrier()
+        msq = c0.elapsed_time(c1)
+        vq = n_sites * R * ((Mc + 1) // 2) / (msq * 1e-3) / 1e9
+        bq = 192.0 + 16.0 / R  # x, y_in, y_out 64 B each; per-site (d+, d-) 16 B
+        compare.update({"q64_glups": round(vq, 3), "q64_over_c128": round(vq / v128, 2),
+                        "q64_vs_c128_max_dmu": float((muq - mu128).abs().max().item()),
+                        "q64_bytes_per_lup": bq,
+                        "q64_hbm_frac": round(bq * vq / peak, 4),
+                        "q64_note": "complex128-sized Q4.59 fixed-point vectors, exact integer stencil; "
+                                    "call time includes the per-call Gershgorin check and conversion"})
+        del wq
 
     # ---- end to end through the public API with host buffers
     e2e = None

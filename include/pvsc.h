@@ -284,15 +284,18 @@ int pvsc_cheb_adjoint_step(const pvsc_lattice* lat, int R, int prec, const void*
 /*
  * Batched KPM: n independent TI lattices (uneven sizes allowed) x R
  * random-phase vectors each, M moments, in one persistent cooperative launch
- * that walks a device work list of (lattice, z-slab) units and advances each
- * slab through the Chebyshev steps as soon as its neighbouring slabs of the
- * same lattice have finished the previous step (bounded spin waits).
+ * that walks a device work list of (lattice, z-slab) units; a unit of step k
+ * starts once every unit of its lattice has finished step k-1 (a per-lattice
+ * phase counter, bounded spin waits), so the lattices advance independently.
+ * Launch shape (threads per block, z-slab planes, blocks per SM): the tuning
+ * entry (R, prec) of lats[0] if one is set, else 256 threads, whole columns
+ * (one unit per column and step) and the occupancy maximum.
  * a, b: HOST arrays of n doubles.  Start vectors: counter hash, stream 1,
  * seed seeds[i] (HOST array of n).  mu: device [n][R][M] doubles.
  * Returns PVSC_ERR_TIMEOUT if a wait exceeded pvsc_set_wait_limit (the
  * kernel then stops cleanly; mu is undefined).
- * work: pvsc_work_bytes(lats[0], PVSC_OP_KPM_BATCHED, R, prec, M) summed
- * over the lattices plus 4096 bytes (use pvsc_batched_work_bytes).
+ * work: pvsc_batched_work_bytes (it depends on the launch shape: query it
+ * after any pvsc_set_tuning on lats[0]).
  */
 int pvsc_kpm_moments_batched(const pvsc_lattice* const* lats, int n, int R, int prec,
                              const uint64_t* seeds, int M, const double* a, const double* b,

@@ -134,10 +134,10 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
     p.counter = static_cast<unsigned*>(work);
     p.partials = reinterpret_cast<double*>(static_cast<char*>(work) + kWorkHeader);
     PVSC_CUDA_TRY(cudaMemsetAsync(work, 0, kWorkHeader, st));
-    if (int r = launch_sweep(lat, prec, F_KPM, p, st)) return r;
+    if (int r = launch_sweep(lat, prec, F_DOTS, p, st)) return r;
     PVSC_CUDA_TRY(cudaEventRecord(e0, st));
     for (int rep = 0; rep < 3; ++rep)
-      if (int r = launch_sweep(lat, prec, F_KPM, p, st)) return r;
+      if (int r = launch_sweep(lat, prec, F_DOTS, p, st)) return r;
     PVSC_CUDA_TRY(cudaEventRecord(e1, st));
     PVSC_CUDA_TRY(cudaEventSynchronize(e1));
     PVSC_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));

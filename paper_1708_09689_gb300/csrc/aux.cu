@@ -21,12 +21,8 @@ __global__ void random_phase_kernel(T* out, int64_t D, int R, uint64_t key, doub
   const int64_t n = D * R;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / R, r = e - i * R;
-    const double u = hash_uniform(key, (uint64_t)(r * D + i));
-    double s, c;
-    sincospi(2.0 * u, &s, &c);
-    out[2 * e] = T(c * scale);
-    out[2 * e + 1] = T(s * scale);
+    const int64_t i = udiv64(e, R), r = e - i * R;
+    random_phase_entry<T>(hash_uniform(key, (uint64_t)(r * D + i)), scale, out[2 * e], out[2 * e + 1]);
   }
 }
 

@@ -112,12 +112,12 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
       const BatchLat& L = a.lats[li];
       if (ph > 0 && !block_wait_geq(L.phase, a.inject_stall ? 0xffffffffu : (unsigned)ph, a)) return;
       const int64_t lu = u - L.unit0;
-      const int64_t bz = lu / L.nbx, bx = lu - bz * L.nbx;
+      const int64_t bz = udiv64(lu, L.nbx), bx = lu - bz * L.nbx;
       const int64_t plane = L.g.L[0] * L.g.L[1], Lz = L.g.L[2];
       const int64_t tid = bx * blockDim.x + threadIdx.x;
       const bool active = tid < plane * C;
       const int64_t z0 = bz * L.zs, z1 = min(z0 + (int64_t)L.zs, Lz);
-      const int64_t col = tid / C;
+      const int64_t col = udiv64(tid, C);
       // per-site partials in (compensated, for complex64) working precision,
       // flushed to fp64 once per column segment
       DotAcc<T, VPT> dacc;
@@ -136,9 +136,8 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
 #pragma unroll
               for (int v = 0; v < VPT; ++v) {
                 const int64_t r = rc * VPT + v, i = 4 * s + o;
-                double sn, cs;
-                sincospi(2.0 * hash_uniform(L.key, (uint64_t)(r * D + i)), &sn, &cs);
-                b.v[o][v] = {T(cs * scale), T(sn * scale)};
+                random_phase_entry<T>(hash_uniform(L.key, (uint64_t)(r * D + i)), scale, b.v[o][v].re,
+                                      b.v[o][v].im);
               }
             store_blk<T, VPT>(W0, s, R, rc, b);
           }
@@ -162,9 +161,10 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
         if (active) {
           // x is written by this kernel in other phases: coherent loads only (NC = false)
           ti_march<T, VPT, false, 0, 2>(L.g, X, Yin, R, rc, col, z0, z1, nullptr,
-                                  [&](int64_t s, const Blk<T, VPT>& xc, const Blk<T, VPT>& S,
+                                  [&](int64_t s) { return site_potential_t<T>(L.g, s); },
+                                  [&](T Vs, const Blk<T, VPT>& xc, const Blk<T, VPT>& S,
                                       const Blk<T, VPT>& D, const Blk<T, VPT>* yi, Blk<T, VPT>& yn) {
-                                    ti_combine(cf, site_potential_t<T>(L.g, s), xc, S, D, yi, yn);
+                                    ti_combine(cf, Vs, xc, S, D, yi, yn);
                                   },
                                   [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
                                     store_blk<T, VPT>(Yout, s, R, rc, yn);
@@ -247,8 +247,30 @@ static size_t batch_header_bytes(int n) {
   return (kWorkHeader + 2 * sizeof(unsigned) * (size_t)n + 255) & ~size_t(255);
 }
 
+// Launch shape of the batched kernel: threads per block, z-segment length and
+// blocks per SM, from the tuning entry (R, prec) of the first lattice when set
+// (pvsc_set_tuning), else 256 threads, whole columns (zs = 0), occupancy
+// maximum.  Whole columns measured fastest on the 64-lattice batch (each unit
+// pays a phase wait, a block reduction and a partial-row write).
+struct BatchShape {
+  int threads = 256, zs = 0, bps = 0;
+};
+static BatchShape batch_shape(const pvsc_lattice* l0, int R, int prec) {
+  BatchShape sh;
+  const int C = R / vpt_for(R, prec);
+  auto it = l0->tuning.find({R, prec});
+  if (it != l0->tuning.end()) {
+    const pvsc_tuning& t = it->second;
+    if (t.threads >= 32 && t.threads <= kMaxThreads && t.threads % 32 == 0 && t.threads % C == 0)
+      sh.threads = t.threads;
+    if (t.zslab > 0) sh.zs = t.zslab;
+    sh.bps = t.blocks_per_sm;
+  }
+  return sh;
+}
+
 static int batched_layout(const pvsc_lattice* const* lats, int n, int R, int prec, int M,
-                          std::vector<BatchLat>& out, size_t* total, int threads) {
+                          std::vector<BatchLat>& out, size_t* total, int threads, int zs) {
   const int C = R / vpt_for(R, prec);
   size_t off = batch_header_bytes(n);
   out.assign(n, BatchLat{});
@@ -261,7 +283,7 @@ static int batched_layout(const pvsc_lattice* const* lats, int n, int R, int pre
     L.g = lat->g;
     const int64_t plane = lat->g.L[0] * lat->g.L[1], Lz = lat->g.L[2];
     L.nbx = (plane * C + threads - 1) / threads;
-    L.zs = (int)(Lz < 24 ? Lz : 24);
+    L.zs = (int)(zs <= 0 || Lz < zs ? Lz : zs);
     L.units = L.nbx * ((Lz + L.zs - 1) / L.zs);
     L.unit0 = unit0;
     unit0 += L.units;
@@ -297,7 +319,9 @@ size_t pvsc_batched_work_bytes(const pvsc_lattice* const* lats, int n, int R, in
   if (!lats || n < 1 || n > kMaxBatch || !valid_R(R) || (prec != PVSC_C128 && prec != PVSC_C64) || M < 1) return 0;
   std::vector<BatchLat> L;
   size_t total = 0;
-  if (batched_layout(lats, n, R, prec, M, L, &total, 256) != PVSC_OK) return 0;
+  if (!lats[0]) return 0;
+  const BatchShape sh = batch_shape(lats[0], R, prec);
+  if (batched_layout(lats, n, R, prec, M, L, &total, sh.threads, sh.zs) != PVSC_OK) return 0;
   return total;
 }
 
@@ -313,10 +337,12 @@ int pvsc_kpm_moments_batched(const pvsc_lattice* const* lats, int n, int R, int 
     if (!(std::isfinite(a[i]) && a[i] > 0) || !std::isfinite(b[i]))
       return set_error(PVSC_ERR_ARG, "scaling of lattice %d invalid", i);
   if (int rc = check_ptr(work, "work")) return rc;
-  const int threads = 256;
+  if (!lats[0]) return set_error(PVSC_ERR_ARG, "lattice 0 is NULL");
+  const BatchShape sh = batch_shape(lats[0], R, prec);
+  const int threads = sh.threads;
   std::vector<BatchLat> L;
   size_t total = 0;
-  if (int rc = batched_layout(lats, n, R, prec, M, L, &total, threads)) return rc;
+  if (int rc = batched_layout(lats, n, R, prec, M, L, &total, threads, sh.zs)) return rc;
   if (work_bytes < total) return set_error(PVSC_ERR_ARG, "work buffer too small: %zu < %zu", work_bytes, total);
   char* base = static_cast<char*>(work);
   int* err = reinterpret_cast<int*>(base);
@@ -341,9 +367,7 @@ int pvsc_kpm_moments_batched(const pvsc_lattice* const* lats, int n, int R, int 
   if (occ < 1) return set_error(PVSC_ERR_CUDA, "batched kernel cannot be resident");
   const pvsc_lattice* l0 = lats[0];
   int bps = occ;
-  auto it = l0->tuning.find({R, prec});
-  if (it != l0->tuning.end() && it->second.blocks_per_sm > 0 && it->second.blocks_per_sm < occ)
-    bps = it->second.blocks_per_sm;
+  if (sh.bps > 0 && sh.bps < occ) bps = sh.bps;
   int64_t grid = (int64_t)l0->sm_count * bps;
   const int64_t total_units = L.back().unit0 + L.back().units;
   if (grid > total_units) grid = total_units;

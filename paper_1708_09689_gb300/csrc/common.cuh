@@ -76,6 +76,34 @@ __device__ __forceinline__ T site_potential_t(const Geometry& g, int64_t site) {
   return T(site_potential(g, site));
 }
 
+// Random-phase entry exp(2 pi i u) scale (the KPM start vectors, u from the
+// counter hash).  complex128 evaluates the phase in fp64; complex64 storage
+// rounds to fp32 anyway, so the phase is evaluated in fp32 (sincospif) and
+// stays off the narrow fp64 pipe.
+template <typename T>
+__device__ __forceinline__ void random_phase_entry(double u, double scale, T& re, T& im) {
+  if constexpr (sizeof(T) == 8) {
+    double s, c;
+    sincospi(2.0 * u, &s, &c);
+    re = c * scale;
+    im = s * scale;
+  } else {
+    float s, c;
+    sincospif((float)(2.0 * u), &s, &c);
+    re = c * (float)scale;
+    im = s * (float)scale;
+  }
+}
+
+// ---------------------------------------------------------------- index arithmetic
+// Non-negative a / b with 32-bit unsigned division when both fit: the 64-bit
+// division is a long instruction sequence that partly issues on the narrow
+// fp64 pipe of this part.
+__device__ __forceinline__ int64_t udiv64(int64_t a, int64_t b) {
+  if (((uint64_t)a | (uint64_t)b) <= 0xffffffffull) return (int64_t)((uint32_t)a / (uint32_t)b);
+  return a / b;
+}
+
 // ---------------------------------------------------------------- complex
 template <typename T> struct CT;
 template <> struct CT<double> { using c = double2; using v = double2; };  // one complex per 16 B

@@ -548,7 +548,7 @@ int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, u
     p.yin = nullptr;
     p.yout = wb;
     p.dot_mode = 1;
-    if (int rc = launch_sweep(lat, prec, F_KPM, p, cs)) return rc;
+    if (int rc = launch_sweep(lat, prec, F_DOTS, p, cs)) return rc;
     const void* prev = x0;
     void* cur = wb;
     const int nsteps = (M + 1) / 2;
@@ -563,7 +563,7 @@ int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, u
       p.yin = prev;
       p.yout = out;
       p.kpm_k = k;
-      if (int rc = launch_sweep(lat, prec, F_KPM, p, cs)) return rc;
+      if (int rc = launch_sweep(lat, prec, F_DOTS, p, cs)) return rc;
       prev = cur;
       cur = out;
     }

@@ -20,11 +20,9 @@
 
 namespace pvsc {
 
-// F_DOTS: the dot products selected at run time by Sweep::dot_flags;
-// F_KPM: <x|x> and Re<y_new|x> only, fixed at compile time (the KPM sweep),
-// so the other accumulators take no registers.
-enum Feat { F_DOTS = 1, F_Z = 2, F_ACC = 4, F_ADJ = 8, F_KPM = 16 };
-__host__ __device__ constexpr bool has_dots(int feat) { return (feat & (F_DOTS | F_KPM)) != 0; }
+// F_DOTS: the dot products selected at run time by Sweep::dot_flags.
+enum Feat { F_DOTS = 1, F_Z = 2, F_ACC = 4, F_ADJ = 8 };
+__host__ __device__ constexpr bool has_dots(int feat) { return (feat & F_DOTS) != 0; }
 
 // 16-byte vector of two 8-byte elements: complex128 (re, im) or the fixed-point pair
 template <typename T> struct Pair16 { using type = double2; };
@@ -419,17 +417,13 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
         const cplx<T> a = xc.v[o][v], b = yn.v[o][v];
         xx = fma(a.re, a.re, fma(a.im, a.im, xx));
         xyr = fma(b.re, a.re, fma(b.im, a.im, xyr));
-        if constexpr ((FEAT & F_DOTS) != 0) {
-          if (p.dot_flags & 2) xyi = fma(b.re, a.im, fma(-b.im, a.re, xyi));
-          if (p.dot_flags & 4) yy = fma(b.re, b.re, fma(b.im, b.im, yy));
-        }
+        if (p.dot_flags & 2) xyi = fma(b.re, a.im, fma(-b.im, a.re, xyi));
+        if (p.dot_flags & 4) yy = fma(b.re, b.re, fma(b.im, b.im, yy));
       }
       dacc.add(0, v, xx);
       dacc.add(1, v, xyr);
-      if constexpr ((FEAT & F_DOTS) != 0) {
-        if (p.dot_flags & 2) dacc.add(2, v, xyi);
-        if (p.dot_flags & 4) dacc.add(3, v, yy);
-      }
+      if (p.dot_flags & 2) dacc.add(2, v, xyi);
+      if (p.dot_flags & 4) dacc.add(3, v, yy);
     }
   }
 }
@@ -594,14 +588,14 @@ __device__ __forceinline__ void ti_combine(const VecCoef<T, VPT>& cf, T Vs, cons
   }
 }
 
-template <typename T, int VPT, bool NC, int DEPTH, int NBUF, class Combine, class Emit>
+template <typename T, int VPT, bool NC, int DEPTH, int NBUF, class Site, class Combine, class Emit>
 __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict__ X,
                                          const T* __restrict__ Yin, int R, int rc, int64_t col,
                                          int64_t z0, int64_t z1, unsigned char* ring,
-                                         Combine&& combine, Emit&& emit) {
+                                         Site&& site, Combine&& combine, Emit&& emit) {
   const int64_t Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
   const int64_t plane = Lx * Ly;
-  const int64_t x = col % Lx, y = col / Lx;
+  const int64_t y = udiv64(col, Lx), x = col - y * Lx;
   // in-plane neighbour columns (-1: absent)
   const int64_t cxm = nbr_minus(col, x, Lx, g.per[0], 1);
   const int64_t cxp = nbr_plus(col, x, Lx, g.per[0], 1);
@@ -687,12 +681,13 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
       if (cym >= 0) load_at<T, VPT, NC>(Pym + zoff, R, ay); else zero_blk(ay);
       if (cyp >= 0) load_at<T, VPT, NC>(Pyp + zoff, R, by); else zero_blk(by);
     }
+    const auto sv = site(s);  // per-site data (potential), issued with the loads above
     Blk<T, VPT> S, D;
     axis_z_init(xm, xp, S, D);
     axis_x_add(ax, bx, S, D);
     axis_y_add(ay, by, S, D);
     Blk<T, VPT> yn;
-    combine(s, xc, S, D, Yin != nullptr ? &yi : nullptr, yn);
+    combine(sv, xc, S, D, Yin != nullptr ? &yi : nullptr, yn);
     emit(s, xc, yn);
     xm = xc;
     xc = xp;
@@ -705,6 +700,7 @@ __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p)
   const int64_t plane = p.g.L[0] * p.g.L[1], Lz = p.g.L[2];
   const int R = p.R, C = p.C;
   const int rc = threadIdx.x % C;
+  const int cshift = __ffs(C) - 1;  // C = R / VPT is a power of two
   const VecCoef<T, VPT> cf = load_coef<T, VPT>(p, rc);
   const T* __restrict__ X = static_cast<const T*>(p.x);
   const T* __restrict__ Yin = static_cast<const T*>(p.yin);
@@ -717,14 +713,15 @@ __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p)
   const int64_t nzs = (Lz + zs - 1) / zs;
   const int64_t nunits = nbx * nzs;
   for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const int64_t bz = u / nbx, bx = u - bz * nbx;
+    const int64_t bz = udiv64(u, nbx), bx = u - bz * nbx;
     const int64_t tid = bx * blockDim.x + threadIdx.x;
     if (tid >= ncolthr) continue;
     const int64_t z0 = bz * zs, z1 = min(z0 + (int64_t)zs, Lz);
-    ti_march<T, VPT, true, DEPTH, NBUF>(p.g, X, Yin, R, rc, tid / C, z0, z1, ring,
-                           [&](int64_t s, const Blk<T, VPT>& xc, const Blk<T, VPT>& S,
+    ti_march<T, VPT, true, DEPTH, NBUF>(p.g, X, Yin, R, rc, tid >> cshift, z0, z1, ring,
+                           [&](int64_t s) { return site_potential_t<T>(p.g, s); },
+                           [&](T Vs, const Blk<T, VPT>& xc, const Blk<T, VPT>& S,
                                const Blk<T, VPT>& D, const Blk<T, VPT>* yi, Blk<T, VPT>& yn) {
-                             ti_combine(cf, site_potential_t<T>(p.g, s), xc, S, D, yi, yn);
+                             ti_combine(cf, Vs, xc, S, D, yi, yn);
                            },
                            [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
                              const int64_t sites[4] = {s, s, s, s};

@@ -26,7 +26,6 @@ static void* pick_c128(int feat) {
   switch (feat) {
     case 0: return kernel_c128<MODEL, 0>();
     case F_DOTS: return kernel_c128<MODEL, F_DOTS>();
-    case F_KPM: return kernel_c128<MODEL, F_KPM>();
     case F_Z: return kernel_c128<MODEL, F_Z>();
     case F_DOTS | F_Z: return kernel_c128<MODEL, F_DOTS | F_Z>();
     case F_ACC: return kernel_c128<MODEL, F_ACC>();
@@ -89,7 +88,6 @@ static void* pick_bulk_c128(int feat) {
   switch (feat) {
     case 0: return reinterpret_cast<void*>(&ti_sweep_bulk<double, 0>);
     case F_DOTS: return reinterpret_cast<void*>(&ti_sweep_bulk<double, F_DOTS>);
-    case F_KPM: return reinterpret_cast<void*>(&ti_sweep_bulk<double, F_KPM>);
     case F_Z: return reinterpret_cast<void*>(&ti_sweep_bulk<double, F_Z>);
     case F_DOTS | F_Z: return reinterpret_cast<void*>(&ti_sweep_bulk<double, F_DOTS | F_Z>);
     case F_ACC: return reinterpret_cast<void*>(&ti_sweep_bulk<double, F_ACC>);

@@ -24,7 +24,6 @@ static void* pick_c64(int feat) {
   switch (feat) {
     case 0: return kernel_c64<MODEL, VPT, 0>();
     case F_DOTS: return kernel_c64<MODEL, VPT, F_DOTS>();
-    case F_KPM: return kernel_c64<MODEL, VPT, F_KPM>();
     case F_Z: return kernel_c64<MODEL, VPT, F_Z>();
     case F_DOTS | F_Z: return kernel_c64<MODEL, VPT, F_DOTS | F_Z>();
     case F_ACC: return kernel_c64<MODEL, VPT, F_ACC>();
@@ -70,7 +69,6 @@ static void* pick_bulk_c64(int feat) {
   switch (feat) {
     case 0: return reinterpret_cast<void*>(&ti_sweep_bulk<float, 0>);
     case F_DOTS: return reinterpret_cast<void*>(&ti_sweep_bulk<float, F_DOTS>);
-    case F_KPM: return reinterpret_cast<void*>(&ti_sweep_bulk<float, F_KPM>);
     case F_Z: return reinterpret_cast<void*>(&ti_sweep_bulk<float, F_Z>);
     case F_DOTS | F_Z: return reinterpret_cast<void*>(&ti_sweep_bulk<float, F_DOTS | F_Z>);
     case F_ACC: return reinterpret_cast<void*>(&ti_sweep_bulk<float, F_ACC>);

@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(256) ti_sweep_fx(const __grid_constant__ Sweep
   const int64_t plane = p.g.L[0] * p.g.L[1], Lz = p.g.L[2];
   const int R = p.R, C = p.R;  // one vector per thread
   const int rc = threadIdx.x % C;
+  const int cshift = __ffs(C) - 1;  // R is a power of two
   const i64* __restrict__ X = static_cast<const i64*>(p.x);
   const i64* Yin = static_cast<const i64*>(p.yin);
   i64* Yout = static_cast<i64*>(p.yout);
@@ -71,16 +72,16 @@ __global__ void __launch_bounds__(256) ti_sweep_fx(const __grid_constant__ Sweep
   const int zs = p.zslab;
   const int64_t nunits = nbx * ((Lz + zs - 1) / zs);
   for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const int64_t bz = u / nbx, bx = u - bz * nbx;
+    const int64_t bz = udiv64(u, nbx), bx = u - bz * nbx;
     const int64_t tid = bx * blockDim.x + threadIdx.x;
     if (tid >= ncolthr) continue;
     const int64_t z0 = bz * zs, z1 = min(z0 + (int64_t)zs, Lz);
     i128 xx = 0, xy = 0;
     ti_march<i64, 1, true, DEPTH, NBUF>(
-        p.g, X, Yin, R, rc, tid / C, z0, z1, ring,
-        [&](int64_t s, const Blk<i64, 1>& xc, const Blk<i64, 1>& S, const Blk<i64, 1>& D,
+        p.g, X, Yin, R, rc, tid >> cshift, z0, z1, ring,
+        [&](int64_t s) { return __ldg(dfx + s); },
+        [&](const longlong2 dv, const Blk<i64, 1>& xc, const Blk<i64, 1>& S, const Blk<i64, 1>& D,
             const Blk<i64, 1>* yi, Blk<i64, 1>& yn) {
-          const longlong2 dv = __ldg(dfx + s);
           const i64 dp = dv.x * dmul, dm = dv.y * dmul;
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
