@@ -25,6 +25,11 @@ Contents and the passages they follow:
   propagate_adjoint         reverse-mode derivative of the propagated state
                             w.r.t. the on-site potential (not in the paper;
                             plain reverse sweep of the same recurrence)
+  jackson_kernel, lorentz_kernel, kpm_density
+                            DOS (Eq. DOS) and spectral function (Eq. ak) from
+                            KPM moments, with the damping kernels of the KPM
+                            method the paper cites
+  bloch_vectors             the Bloch states psi(k, nu) of Eq. ak
 """
 from __future__ import annotations
 
@@ -414,3 +419,60 @@ def detector_probability(psi, mask_sites, O=1):
     """L = sum over detector sites (and their orbitals) of |psi|^2."""
     p = np.abs(np.asarray(psi).reshape(-1, O)) ** 2
     return float(np.sum(p.sum(axis=1)[np.asarray(mask_sites, dtype=bool)]))
+
+
+# ----------------------------------------------------------------------------
+# Spectral densities from KPM moments (Eq. ak, Eq. DOS, Sec. 2.2; the kernel
+# polynomial method the paper cites: A. Weisse, G. Wellein, A. Alvermann,
+# H. Fehske, Rev. Mod. Phys. 78, 275 (2006), Sec. II)
+# ----------------------------------------------------------------------------
+def jackson_kernel(M: int) -> np.ndarray:
+    """Jackson damping factors g_k, k = 0..M-1, for M moments:
+    g_k = [(M - k + 1) cos(q k) + sin(q k) cot(q)] / (M + 1),  q = pi / (M + 1)."""
+    k = np.arange(M, dtype=np.float64)
+    q = math.pi / (M + 1)
+    return ((M - k + 1) * np.cos(q * k) + np.sin(q * k) / math.tan(q)) / (M + 1)
+
+
+def lorentz_kernel(M: int, lam: float) -> np.ndarray:
+    """Lorentz damping factors g_k = sinh(lam (1 - k/M)) / sinh(lam), k = 0..M-1."""
+    k = np.arange(M, dtype=np.float64)
+    return np.sinh(lam * (1.0 - k / M)) / math.sinh(lam)
+
+
+def kpm_density(mu, E, a, b, g, scale=1.0) -> np.ndarray:
+    """Density from per-vector moments mu (R, M) on energies E:
+
+        rho(E) = scale * sum_r [g_0 mu_0^r + 2 sum_{k>=1} g_k mu_k^r T_k(x)] / (pi a sqrt(1 - x^2)),
+
+    x = (E - b)/a, T_k(x) = cos(k arccos x), rho = 0 for |x| >= 1.  With the
+    stochastic-trace moments of R random vectors and scale = D/R this is the
+    DOS of Eq. DOS; with the moments of the four Bloch vectors psi(k, nu) and
+    scale = 1 it is A(k, E) of Eq. ak."""
+    mu = np.atleast_2d(np.asarray(mu, dtype=np.float64))
+    g = np.asarray(g, dtype=np.float64)
+    E = np.asarray(E, dtype=np.float64)
+    x = (E - b) / a
+    inside = np.abs(x) < 1.0
+    xs = np.where(inside, x, 0.0)
+    theta = np.arccos(xs)
+    c = g * mu.sum(axis=0)
+    c[1:] *= 2.0
+    k = np.arange(len(c))
+    series = np.cos(np.outer(theta, k)) @ c
+    rho = scale * series / (math.pi * a * np.sqrt(1.0 - xs * xs))
+    return np.where(inside, rho, 0.0)
+
+
+def bloch_vectors(dims, k) -> np.ndarray:
+    """The states psi(k, nu), nu = 0..3, of Eq. ak on a TI lattice: the plane
+    wave exp(i k.r_n)/sqrt(N) on orbital nu of every site n (r_n = the site's
+    integer coordinates), as a (4 N, 4) block in the library's layout."""
+    coords = _all_coords(dims).astype(np.float64)
+    N = coords.shape[0]
+    kv = np.asarray(k, dtype=np.float64)[: coords.shape[1]]
+    phase = np.exp(1j * (coords @ kv)) / math.sqrt(N)
+    out = np.zeros((4 * N, 4), dtype=np.complex128)
+    for nu in range(4):
+        out[nu::4, nu] = phase
+    return out

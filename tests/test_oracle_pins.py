@@ -425,3 +425,70 @@ def test_counter_hash_known_values_and_disorder_range():
     assert V.min() >= -2.0 and V.max() < 2.0 and abs(V.mean()) < 0.02
     r = W.random_phase_block(1000, 3, 3)
     assert np.allclose(np.sum(np.abs(r) ** 2, axis=0), 1.0)
+
+
+# ------------------------------------------------------------------ spectral densities (Eq. ak, Eq. DOS)
+def test_jackson_kernel_small_cases_by_hand():
+    # q = pi/(M+1); M = 2: g = (1, (2 cos q + sin q cot q)/3) = (1, 1/2);
+    # M = 3: g_1 = (3 cos(pi/4) + sin(pi/4))/4 = 1/sqrt(2), g_2 = (0 + 1)/4 = 1/4
+    assert np.allclose(O.jackson_kernel(2), [1.0, 0.5], atol=1e-15)
+    assert np.allclose(O.jackson_kernel(3), [1.0, 1.0 / math.sqrt(2.0), 0.25], atol=1e-15)
+    g = O.jackson_kernel(256)
+    assert g[0] == 1.0 and np.all(np.diff(g) < 0) and g[-1] > 0
+    gl = O.lorentz_kernel(64, 4.0)
+    assert abs(gl[0] - 1.0) < 1e-15 and np.all(np.diff(gl) < 0)
+
+
+def test_kpm_density_normalisation_by_gauss_chebyshev_quadrature():
+    # int rho dE = scale * sum_r g_0 mu_0^r, because int T_k(x) / (pi sqrt(1 - x^2)) dx = delta_k0;
+    # Gauss-Chebyshev quadrature with N > M nodes is exact for the series
+    rng = np.random.default_rng(3)
+    mu = rng.standard_normal((3, 40))
+    a, b = 2.5, 0.3
+    g = O.jackson_kernel(40)
+    N = 200
+    x = np.cos(np.pi * (np.arange(N) + 0.5) / N)
+    rho = O.kpm_density(mu, b + a * x, a, b, g, scale=0.7)
+    integral = np.pi / N * np.sum(rho * a * np.sqrt(1 - x * x))
+    assert abs(integral - 0.7 * g[0] * mu[:, 0].sum()) < 1e-12
+    assert np.all(O.kpm_density(mu, np.array([b - a - 1e-3, b + a + 1e-3]), a, b, g) == 0.0)
+
+
+def test_kpm_dos_counts_the_eigenvalues_of_dense_diagonalisation():
+    # Eq. DOS from exact trace moments (all unit vectors) of a gapped periodic
+    # disordered TI: integrated over windows whose ends lie in spectral gaps it
+    # counts the eigenvalues of scipy/numpy's dense solver; Jackson damping keeps it >= 0
+    dims = (4, 4, 4)
+    V = W.disorder_potential(64, 1.0, 7)
+    H = O.ti_hamiltonian(dims, (1, 1, 1), 1.0, 2.0, V)
+    ev = np.linalg.eigvalsh(H.toarray())
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    M = 512
+    mu = O.kpm_moments(H, np.eye(H.shape[0], dtype=np.complex128), M, a, b).real
+    E = np.linspace(b - a + 1e-9, b + a - 1e-9, 20001)
+    rho = O.kpm_density(mu, E, a, b, O.jackson_kernel(M))
+    assert rho.min() > 0
+    assert not np.any(np.abs(ev) < 0.5)  # the window edge E = 0 sits in the bulk gap
+    for lo, hi in ((b - a, 0.0), (0.0, b + a)):
+        m = (E >= lo) & (E < hi)
+        assert abs(np.trapezoid(rho[m], E[m]) - np.sum((ev >= lo) & (ev < hi))) < 1e-3
+
+
+@pytest.mark.parametrize("k", [(2 * math.pi * 2 / 8, 0.0, 0.0),
+                               (2 * math.pi / 8, 2 * math.pi * 3 / 8, 2 * math.pi / 8)])
+def test_spectral_function_of_clean_ti_peaks_at_closed_form_bands(k):
+    # Eq. ak on a clean periodic lattice: psi(k, nu) spans the Bloch block at k,
+    # whose eigenvalues are +-E(k) (closed form, reading of Eq. bloch_H_topi),
+    # each twice: A(k, E) = 2 delta(E - E(k)) + 2 delta(E + E(k)), total weight 4
+    dims = (8, 8, 8)
+    H = O.ti_hamiltonian(dims, (1, 1, 1), 1.0, 2.0, np.zeros(512))
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    Ek = math.sqrt((2.0 - sum(math.cos(c) for c in k)) ** 2 + sum(math.sin(c) ** 2 for c in k))
+    mu = O.kpm_moments(H, O.bloch_vectors(dims, k), 512, a, b).real
+    E = np.linspace(b - a + 1e-9, b + a - 1e-9, 40001)
+    A = O.kpm_density(mu, E, a, b, O.jackson_kernel(512))
+    for e0 in (Ek, -Ek):
+        m = (E > e0 - 0.4) & (E < e0 + 0.4)
+        assert abs(E[m][np.argmax(A[m])] - e0) < 2e-3
+        assert abs(np.trapezoid(A[m], E[m]) - 2.0) < 2e-3
+    assert abs(np.trapezoid(A, E) - 4.0) < 1e-3
