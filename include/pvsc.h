@@ -76,6 +76,9 @@ enum {
   PVSC_V_ON_THE_FLY = 4  /* same values, regenerated inside every stencil sweep */
 };
 
+/* Damping kernels of pvsc_kpm_density. */
+enum { PVSC_KERNEL_NONE = 0, PVSC_KERNEL_JACKSON = 1, PVSC_KERNEL_LORENTZ = 2 };
+
 /* Dot-product selection for pvsc_cheb_step. */
 enum { PVSC_DOT_XX = 1, PVSC_DOT_XY = 2, PVSC_DOT_YY = 4 };
 
@@ -300,6 +303,34 @@ int pvsc_cheb_adjoint_step(const pvsc_lattice* lat, int R, int prec, const void*
 int pvsc_kpm_moments_batched(const pvsc_lattice* const* lats, int n, int R, int prec,
                              const uint64_t* seeds, int M, const double* a, const double* b,
                              double* mu, void* work, size_t work_bytes, void* stream);
+
+/*
+ * Spectral densities from KPM moments (Sec. 2.2: the DOS of Eq. DOS and the
+ * momentum-resolved spectral function A(k, E) of Eq. ak), with the damping
+ * kernels of the kernel polynomial method the paper cites:
+ *   rho(E_j) = scale sum_r [g_0 mu_0^r + 2 sum_{k>=1} g_k mu_k^r T_k(x_j)]
+ *              / (pi a sqrt(1 - x_j^2)),   x_j = (E_j - b)/a,
+ * and rho(E_j) = 0 for |x_j| >= 1.  mu: device [R][M] doubles (as written by
+ * pvsc_kpm_moments); E, rho: device arrays of NE doubles.  kernel:
+ * PVSC_KERNEL_NONE (g_k = 1), PVSC_KERNEL_JACKSON (g_k = [(M-k+1) cos(q k)
+ * + sin(q k) cot q]/(M+1), q = pi/(M+1)) or PVSC_KERNEL_LORENTZ (g_k =
+ * sinh(lambda (1 - k/M))/sinh(lambda), lambda > 0).  DOS: random-phase
+ * moments, scale = D/R (integrates to D = 4 n_sites); A(k, E): the moments of
+ * the four states psi(k, nu) of pvsc_bloch_vectors, scale = 1 (integrates to 4).
+ */
+int pvsc_kpm_density(int R, int M, const double* mu, int kernel, double lambda, double a, double b,
+                     double scale, int NE, const double* E, double* rho, void* stream);
+
+/*
+ * The states psi(k, nu) of Eq. ak on a TI lattice, for nk in {1, 2, 4, 8, 16}
+ * k-points k[3 q .. 3 q + 2] (HOST array of 3 nk doubles, components along x,
+ * y, z in radians per lattice spacing): vector r = 4 q + nu of the block (R =
+ * 4 nk) is exp(i k_q . r_n)/sqrt(n_sites) on orbital nu of every site n
+ * (r_n its integer coordinates) and zero on the other orbitals.  out: device
+ * block (D x R) in precision prec.  Phases are evaluated in fp64.
+ */
+int pvsc_bloch_vectors(const pvsc_lattice* lat, int nk, const double* k, int prec, void* out,
+                       void* stream);
 
 /* Work bytes for pvsc_kpm_moments_batched over the given lattices. */
 size_t pvsc_batched_work_bytes(const pvsc_lattice* const* lats, int n, int R, int prec, int M);

@@ -25,6 +25,7 @@ PVSC_OK, PVSC_ERR_ARG, PVSC_ERR_CUDA, PVSC_ERR_OOM, PVSC_ERR_TIMEOUT, PVSC_ERR_U
     0, -1, -2, -3, -4, -5
 TI, GRAPHENE = 1, 2
 C128, C64, Q64 = 0, 1, 2  # Q64: fixed-point vectors, pvsc_kpm_moments on TI only
+KERNEL_NONE, KERNEL_JACKSON, KERNEL_LORENTZ = 0, 1, 2  # damping kernels of kpm_density
 V_ZERO, V_HOST, V_DEVICE, V_SEED, V_ON_THE_FLY = 0, 1, 2, 3, 4
 DOT_XX, DOT_XY, DOT_YY = 1, 2, 4
 OP_APPLY, OP_CHEB_STEP, OP_KPM, OP_SERIES, OP_ADJOINT, OP_KPM_BATCHED = 0, 1, 2, 3, 4, 5
@@ -79,6 +80,8 @@ _SIGNATURES = {
     "pvsc_cheb_step": (_i, [_vp, _i, _i, _vp, _vp, _vp, _dp, _dp, _dp, _dp, _i, _vp, _vp, _sz, _vp]),
     "pvsc_cheb_step_noalloc": (_i, [_vp, _i, _i, _vp, _vp, _vp, _dp, _dp, _dp, _dp, _i, _vp, _vp]),
     "pvsc_kpm_moments": (_i, [_vp, _i, _i, _vp, _u64, _i, _d, _d, _vp, _vp, _sz, _vp]),
+    "pvsc_kpm_density": (_i, [_i, _i, _vp, _i, _d, _d, _d, _d, _i, _vp, _vp, _vp]),
+    "pvsc_bloch_vectors": (_i, [_vp, _i, ctypes.POINTER(_d), _i, _vp, _vp]),
     "pvsc_cheb_series": (_i, [_vp, _i, _i, _vp, _vp, _dp, _i, _dp, _d, _d, _vp, _sz, _vp]),
     "pvsc_cheb_filter": (_i, [_vp, _i, _i, _vp, _vp, _dp, _i, _d, _d, _vp, _sz, _vp]),
     "pvsc_propagation_coeffs": (_i, [_d, _d, _i, _dp, ctypes.POINTER(ctypes.c_int)]),
@@ -402,6 +405,46 @@ def cheb_adjoint_step(lat: Lattice, psi_s, G, dt, a, b, dLdV, trunc=1e-14, work=
                                        float(a), float(b), float(trunc), _ptr(dLdV), _ptr(work),
                                        work.numel(), _stream(stream)))
     return G
+
+
+def kpm_density(mu: torch.Tensor, E: torch.Tensor, a: float, b: float, kernel: int = KERNEL_JACKSON,
+                lam: float = 4.0, scale: float = 1.0, out: torch.Tensor | None = None, stream=None):
+    """rho(E) = scale sum_r [g_0 mu_0^r + 2 sum_k g_k mu_k^r T_k(x)] / (pi a sqrt(1 - x^2)), x = (E-b)/a,
+    from per-vector moments mu (R, M) (float64, on the device) on energies E (float64)."""
+    mu = mu.to(torch.float64).contiguous()
+    R, M = mu.shape
+    E = E.to(device=mu.device, dtype=torch.float64).contiguous()
+    out = torch.empty_like(E) if out is None else out
+    _check(_lib.pvsc_kpm_density(R, M, _ptr(mu), int(kernel), float(lam), float(a), float(b),
+                                 float(scale), E.numel(), _ptr(E), _ptr(out), _stream(stream)))
+    return out
+
+
+def dos(lat: Lattice, mu: torch.Tensor, E, a, b, kernel: int = KERNEL_JACKSON, lam: float = 4.0):
+    """DOS(E) of Eq. DOS from the stochastic-trace moments of R random vectors (integrates to D)."""
+    return kpm_density(mu, torch.as_tensor(E, dtype=torch.float64, device="cuda"), a, b, kernel, lam,
+                       scale=lat.D / mu.shape[0])
+
+
+def bloch_vectors(lat: Lattice, ks, prec: int = C128, stream=None) -> torch.Tensor:
+    """The states psi(k, nu) of Eq. ak for up to 16 k-points: a (D, 4 nk) block, vector 4 q + nu."""
+    ks = [tuple(float(c) for c in k) + (0.0,) * (3 - len(k)) for k in ks]
+    nk = len(ks)
+    out = torch.empty((lat.D, 4 * nk), dtype=torch.complex128 if prec == C128 else torch.complex64,
+                      device="cuda")
+    flat = (ctypes.c_double * (3 * nk))(*[c for k in ks for c in k])
+    _check(_lib.pvsc_bloch_vectors(lat.handle, nk, flat, prec, _ptr(out), _stream(stream)))
+    return out
+
+
+def spectral_function(lat: Lattice, ks, M: int, a, b, E, prec: int = C64,
+                      kernel: int = KERNEL_JACKSON, lam: float = 4.0, work=None) -> torch.Tensor:
+    """A(k, E) of Eq. ak for up to 16 k-points: KPM moments of the four states psi(k, nu) of each
+    k-point (one call, R = 4 nk), summed per k-point; returns (nk, NE) float64."""
+    psi = bloch_vectors(lat, ks, prec)
+    mu = kpm_moments(lat, M, a, b, r0=psi, work=work)
+    E = torch.as_tensor(E, dtype=torch.float64, device="cuda")
+    return torch.stack([kpm_density(mu[4 * q:4 * q + 4], E, a, b, kernel, lam) for q in range(len(ks))])
 
 
 def kpm_moments_batched(lats, M, a, b, R=16, prec=C64, seeds=None, work=None, mu=None, stream=None):
