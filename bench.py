@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -74,10 +75,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default launch shape instead of the autotuned one")
     ap.add_argument("--workload", default="ti_slab",
-                    choices=["ti_slab", "ti_cube", "graphene_qd", "batched", "adjoint"],
+                    choices=["ti_slab", "ti_cube", "graphene_qd", "batched", "adjoint", "ti_akE"],
                     help="ti_slab (default): the benchmark line; the others measure the remaining "
                          "workloads (16^3 cube KPM, graphene QD-array propagation, batched KPM over "
-                         "64 lattices, adjoint gradient) and print one JSON line each")
+                         "64 lattices, adjoint gradient, A(k,E) of a clean TI) and print one JSON line each")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="profiling case: one KPM call of this many complex64 sweeps (stencil, "
                          "recurrence, dots) on the lattice (ti_slab), or this many complex64 "
@@ -351,6 +352,51 @@ def run_workload(args, pv, dev, rank, world):
                                       "norm_drift_c128": abs(torch.linalg.vector_norm(psi128).item() - 1),
                                       "c64_vs_c128_state_err": torch.linalg.vector_norm(p64 - psi128).item()},
                      "clocks": clk, "gpu_launches": (nterms) * n64})
+    elif args.workload == "ti_akE":
+        # A(k, E) along k_x of a clean TI cuboid (the dispersion figure's 512 x 64 x 8 sites,
+        # periodic): 64 k-points, 16 per KPM call (R = 64: four Bloch states each), complex64
+        dims, M, nk_call, NE = (512, 64, 8), 1024, 16, 1024
+        lat = pv.Lattice.ti(dims, (1, 1, 1), t=1.0, m=2.0)
+        emin, emax, a, b = lat.spectral_bounds()
+        R = 4 * nk_call
+        if not args.no_autotune:
+            lat.autotune(R, pv.C64)
+        kx = [2 * math.pi * (j - 32) / 64 for j in range(64)]
+        calls = [[(k, 0.0, 0.0) for k in kx[c * nk_call:(c + 1) * nk_call]] for c in range(64 // nk_call)]
+        E = torch.linspace(b - a * 0.999, b + a * 0.999, NE, dtype=torch.float64, device=dev)
+        work = pv.work_buffer(lat.work_bytes(pv.OP_KPM, R, pv.C64, M), dev)
+        mu = torch.empty((R, M), dtype=torch.float64, device=dev)
+        A = torch.empty((64, NE), dtype=torch.float64, device=dev)
+        psis = [pv.bloch_vectors(lat, ks, pv.C64) for ks in calls]
+
+        def step():
+            for c, psi in enumerate(psis):
+                pv.kpm_moments(lat, M, a, b, r0=psi, work=work, mu=mu)
+                for q in range(nk_call):
+                    pv.kpm_density(mu[4 * q:4 * q + 4], E, a, b, out=A[c * nk_call + q])
+        for _ in range(args.warmup):
+            step()
+        clocks.start()
+        ms = max_over_ranks(_timed(step, args.steps, stream), dev)
+        clk = clocks.stop()
+        # density alone (all 64 k-points), for the record
+        t_d = _timed(lambda: [pv.kpm_density(mu[4 * q:4 * q + 4], E, a, b, out=A[q]) for q in range(64 // 4)],
+                     3, stream)
+        lups = lat.n_sites * R * ((M + 1) // 2) * len(calls)
+        Ah = A.cpu().numpy()
+        En = E.cpu().numpy()
+        # upper-band peak at k = 0, where the closed form gives E = |m - 3t| = 1
+        peak = lambda q, lo, hi: float(En[(En > lo) & (En < hi)][np.argmax(Ah[q][(En > lo) & (En < hi)])])
+        line.update({"workload": "ti_akE", "value": round(world * lups / (ms * 1e-3) / 1e9, 3),
+                     "ms_per_step": round(ms, 3), "steps": args.steps, "dtype": "c64",
+                     "config": {"workload": "A(k,E) of a clean TI, 512x64x8 sites periodic, m=2, t=1: "
+                                            "64 k-points along k_x, 4 Bloch states each, 1024 moments, "
+                                            "Jackson kernel, 1024 energies",
+                                "kpm_calls_per_step": len(calls), "R_per_call": R},
+                     "density_ms_64k": round(t_d, 4),
+                     "peak_at_k0": peak(32, 0.5, 1.5), "closed_form_k0": 1.0,
+                     "roofline": _hbm_roof(96.0, lups, ms, "ti_sweep<float,2,F_DOTS> (R = 64, V = 0)"),
+                     "clocks": clk, "gpu_launches": args.steps * len(calls) * ((M + 1) // 2 + 1 + nk_call)})
     elif args.workload == "batched":
         specs = W.batched_lattices()
         if args.sweeps_only:  # profiling case: the first --batched-count lattices, untimed
