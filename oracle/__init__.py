@@ -30,6 +30,7 @@ Contents and the passages they follow:
                             KPM moments, with the damping kernels of the KPM
                             method the paper cites
   bloch_vectors             the Bloch states psi(k, nu) of Eq. ak
+  chebfd_window, chebfd     Chebyshev filter diagonalization (Sec. 5.3)
 """
 from __future__ import annotations
 
@@ -476,3 +477,41 @@ def bloch_vectors(dims, k) -> np.ndarray:
     for nu in range(4):
         out[nu::4, nu] = phase
     return out
+
+
+# ----------------------------------------------------------------------------
+# Chebyshev filter diagonalization (Sec. 5.3 "Interior eigenvalues"; the
+# ChebFD scheme of A. Pieper et al., J. Comput. Phys. 325, 226 (2016))
+# ----------------------------------------------------------------------------
+def chebfd_window(lo: float, hi: float, a: float, b: float, degree: int) -> np.ndarray:
+    """Chebyshev coefficients c_0..c_degree of the indicator of [lo, hi] on the
+    scaled axis x = (E - b)/a, damped by the Jackson kernel: with x = cos(theta),
+    c_0 = (theta_lo - theta_hi)/pi, c_k = 2 (sin(k theta_lo) - sin(k theta_hi))/(pi k)."""
+    tl = math.acos(max(-1.0, min(1.0, (lo - b) / a)))
+    th = math.acos(max(-1.0, min(1.0, (hi - b) / a)))
+    k = np.arange(1, degree + 1, dtype=np.float64)
+    c = np.empty(degree + 1)
+    c[0] = (tl - th) / math.pi
+    c[1:] = 2.0 * (np.sin(k * tl) - np.sin(k * th)) / (math.pi * k)
+    return c * jackson_kernel(degree + 1)
+
+
+def chebfd(H, X0, lo, hi, a, b, degree, max_iter, tol):
+    """Filter diagonalization in the paper's order: filter the block with the
+    window polynomial, orthonormalize (QR), Rayleigh-Ritz on the filtered
+    space, stop when every Ritz pair inside [lo, hi] has ||H x - theta x|| < tol.
+    Returns (theta, X, residuals) of the pairs inside [lo, hi] and the number
+    of iterations."""
+    c = chebfd_window(lo, hi, a, b, degree)
+    X = np.asarray(X0, dtype=np.complex128)
+    for it in range(1, max_iter + 1):
+        Y = cheb_series(H, X, c, a, b)
+        Q, _ = np.linalg.qr(Y)
+        HQ = H @ Q
+        theta, W = np.linalg.eigh(Q.conj().T @ HQ)
+        X = Q @ W
+        res = np.linalg.norm(H @ X - X * theta, axis=0)
+        inside = (theta >= lo) & (theta <= hi)
+        if np.all(res[inside] < tol):
+            break
+    return theta[inside], X[:, inside], res[inside], it

@@ -492,3 +492,37 @@ def test_spectral_function_of_clean_ti_peaks_at_closed_form_bands(k):
         assert abs(E[m][np.argmax(A[m])] - e0) < 2e-3
         assert abs(np.trapezoid(A[m], E[m]) - 2.0) < 2e-3
     assert abs(np.trapezoid(A, E) - 4.0) < 1e-3
+
+
+# ------------------------------------------------------------------ ChebFD (Sec. 5.3)
+def _window_around_zero(ev, n):
+    """[lo, hi] holding the n eigenvalues nearest 0, its ends at midpoints of spectral gaps."""
+    idx = np.sort(np.argsort(np.abs(ev))[:n])
+    i0, i1 = idx[0], idx[-1]
+    return (ev[i0 - 1] + ev[i0]) / 2, (ev[i1] + ev[i1 + 1]) / 2
+
+
+def test_chebfd_window_is_the_indicator_series():
+    # undamped coefficients of the indicator reproduce it away from the edges
+    # (quadrature check of c_k = (2 - delta_k0)/pi int chi(x) T_k(x)/sqrt(1-x^2) dx)
+    lo, hi, a, b = -0.3, 0.5, 2.0, 0.1
+    N = 4000
+    x = np.cos(np.pi * (np.arange(N) + 0.5) / N)
+    chi = ((b + a * x >= lo) & (b + a * x <= hi)).astype(float)
+    ref = np.array([(1 if k == 0 else 2) / N * np.sum(chi * np.cos(k * np.arccos(x))) for k in range(60)])
+    c = O.chebfd_window(lo, hi, a, b, 59) / O.jackson_kernel(60)
+    assert np.max(np.abs(c - ref)) < 2e-3  # midpoint rule on a discontinuous integrand
+
+
+def test_chebfd_finds_the_interior_eigenpairs_of_dense_diagonalisation():
+    dims = (6, 6, 4)
+    H = O.ti_hamiltonian(dims, (1, 1, 0), 1.0, 2.0, W.disorder_potential(144, 1.0, 3))
+    ev = np.sort(np.linalg.eigvalsh(H.toarray()))
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    lo, hi = _window_around_zero(ev, 16)
+    th, X, res, it = O.chebfd(H, W.gaussian_block(H.shape[0], 32, 1), lo, hi, a, b, 400, 40, 1e-10)
+    target = ev[(ev >= lo) & (ev <= hi)]
+    assert len(th) == len(target) == 16
+    assert np.max(np.abs(np.sort(th) - target)) < 1e-12
+    assert np.all(res < 1e-10)
+    assert np.allclose(X.conj().T @ X, np.eye(16), atol=1e-12)
