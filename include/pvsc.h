@@ -332,6 +332,44 @@ int pvsc_kpm_density(int R, int M, const double* mu, int kernel, double lambda, 
 int pvsc_bloch_vectors(const pvsc_lattice* lat, int nk, const double* k, int prec, void* out,
                        void* stream);
 
+/*
+ * Chebyshev filter diagonalization (ChebFD, Sec. 5.3 "Interior eigenvalues"):
+ * the eigenpairs of H in [lo, hi] from a block of n_search <= 64 vectors.
+ * Each iteration filters the block with the Jackson-damped Chebyshev series
+ * of the indicator of [lo, hi] (degree `degree`, recurrence vectors in
+ * `prec`), orthonormalizes it (shifted CholeskyQR3; Gram matrices by cuBLAS),
+ * and performs Rayleigh-Ritz (the n_search x n_search projection by cuBLAS,
+ * its eigen-decomposition by Jacobi rotations on the host); it stops when
+ * every Ritz value inside [lo, hi] has ||H x - theta x|| < tol, or after
+ * max_iter iterations.  The start block is the random-phase block of `seed`.
+ * Outputs: X (device complex128 D x n_search, the Ritz vectors, orthonormal),
+ * theta and resid (HOST arrays of n_search doubles, Ritz values ascending and
+ * their residual norms), *n_inside (Ritz values inside [lo, hi]),
+ * *iterations.  The search space should exceed the number of eigenvalues in
+ * the interval (about 1.5-2x).  Synchronous (reads small matrices back every
+ * iteration).  PVSC_ERR_ARG if the filtered block loses rank.
+ * work: pvsc_chebfd_work_bytes.
+ */
+typedef struct {
+  double lo, hi;   /* target interval (energies) */
+  int32_t n_search;
+  int32_t degree;  /* filter polynomial degree */
+  int32_t max_iter;
+  int32_t prec;    /* PVSC_C128 or PVSC_C64 for the filter's recurrence vectors */
+  double tol;      /* residual bound */
+  uint64_t seed;
+} pvsc_chebfd_params;
+
+int pvsc_chebfd(const pvsc_lattice* lat, const pvsc_chebfd_params* params, double a, double b,
+                void* X, double* theta, double* resid, int* n_inside, int* iterations, void* work,
+                size_t work_bytes, void* stream);
+size_t pvsc_chebfd_work_bytes(const pvsc_lattice* lat, int n_search, int prec, int degree);
+
+/* Host-only: eigen-decomposition of a Hermitian n x n matrix (column-major,
+ * interleaved re/im) by the cyclic Jacobi method ChebFD uses; w ascending,
+ * V (same layout as A) the eigenvectors.  For tests. */
+int pvsc_debug_eigh(int n, const double* A, double* w, double* V);
+
 /* Work bytes for pvsc_kpm_moments_batched over the given lattices. */
 size_t pvsc_batched_work_bytes(const pvsc_lattice* const* lats, int n, int R, int prec, int M);
 

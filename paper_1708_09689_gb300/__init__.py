@@ -17,6 +17,7 @@ import ctypes
 import math
 import os
 
+import numpy as np
 import torch
 
 from .build import LIB_PATH
@@ -81,6 +82,8 @@ _SIGNATURES = {
     "pvsc_cheb_step_noalloc": (_i, [_vp, _i, _i, _vp, _vp, _vp, _dp, _dp, _dp, _dp, _i, _vp, _vp]),
     "pvsc_kpm_moments": (_i, [_vp, _i, _i, _vp, _u64, _i, _d, _d, _vp, _vp, _sz, _vp]),
     "pvsc_kpm_density": (_i, [_i, _i, _vp, _i, _d, _d, _d, _d, _i, _vp, _vp, _vp]),
+    "pvsc_chebfd": (_i, [_vp, _vp, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "pvsc_chebfd_work_bytes": (_sz, [_vp, _i, _i, _i]),
     "pvsc_bloch_vectors": (_i, [_vp, _i, ctypes.POINTER(_d), _i, _vp, _vp]),
     "pvsc_cheb_series": (_i, [_vp, _i, _i, _vp, _vp, _dp, _i, _dp, _d, _d, _vp, _sz, _vp]),
     "pvsc_cheb_filter": (_i, [_vp, _i, _i, _vp, _vp, _dp, _i, _d, _d, _vp, _sz, _vp]),
@@ -445,6 +448,31 @@ def spectral_function(lat: Lattice, ks, M: int, a, b, E, prec: int = C64,
     mu = kpm_moments(lat, M, a, b, r0=psi, work=work)
     E = torch.as_tensor(E, dtype=torch.float64, device="cuda")
     return torch.stack([kpm_density(mu[4 * q:4 * q + 4], E, a, b, kernel, lam) for q in range(len(ks))])
+
+
+class ChebFDParams(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double), ("hi", ctypes.c_double), ("n_search", ctypes.c_int32),
+                ("degree", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+def chebfd(lat: Lattice, lo: float, hi: float, a: float, b: float, n_search: int = 64,
+           degree: int = 500, max_iter: int = 30, tol: float = 1e-10, prec: int = C128,
+           seed: int = 1, stream=None):
+    """Chebyshev filter diagonalization: the eigenpairs of H in [lo, hi].  Returns
+    (theta, resid, X, n_inside, iterations): all n_search Ritz values (ascending, numpy),
+    their residual norms, the Ritz vectors (complex128 (D, n_search) on the device)."""
+    prm = ChebFDParams(float(lo), float(hi), int(n_search), int(degree), int(max_iter), int(prec),
+                       float(tol), int(seed))
+    X = torch.empty((lat.D, n_search), dtype=torch.complex128, device="cuda")
+    work = work_buffer(_lib.pvsc_chebfd_work_bytes(lat.handle, n_search, prec, degree))
+    theta = (ctypes.c_double * n_search)()
+    resid = (ctypes.c_double * n_search)()
+    n_in, iters = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.pvsc_chebfd(lat.handle, ctypes.byref(prm), float(a), float(b), _ptr(X), theta, resid,
+                            ctypes.byref(n_in), ctypes.byref(iters), _ptr(work), work.numel(),
+                            _stream(stream)))
+    return np.array(theta[:]), np.array(resid[:]), X, n_in.value, iters.value
 
 
 def kpm_moments_batched(lats, M, a, b, R=16, prec=C64, seeds=None, work=None, mu=None, stream=None):

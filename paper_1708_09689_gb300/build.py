@@ -34,6 +34,11 @@ def nvcc_path() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libpvsc.so")
 
 
+def cuda_lib_dir(nvcc: str) -> str:
+    """lib64 of the toolkit that provides nvcc (where libcublas lives), for the runtime search path."""
+    return os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(nvcc))), "lib64")
+
+
 def _headers() -> list[str]:
     return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
         glob.glob(os.path.join(INCLUDE, "*.h"))
@@ -74,7 +79,8 @@ def build_library(verbose: bool = False, extra_flags: list[str] | None = None) -
         list(ex.map(compile_one, jobs))
     objs = [os.path.join(OBJ_DIR, os.path.basename(s)[:-3] + ".o") for s in sources]
     if jobs or _stale(LIB_PATH, objs):
-        cmd = [nvcc] + ARCH + ["-shared", "-o", LIB_PATH] + objs + ["-lpthread"]
+        cmd = [nvcc] + ARCH + ["-shared", "-o", LIB_PATH] + objs + \
+            ["-lcublas", "-Xlinker", "-rpath", "-Xlinker", cuda_lib_dir(nvcc), "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link of libpvsc.so failed:\n{r.stderr}")

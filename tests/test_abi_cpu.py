@@ -72,3 +72,24 @@ def test_argument_errors_are_reported_without_a_device(libpath):
     assert lib.pvsc_lattice_create(ctypes.byref(d), None, ctypes.byref(h)) == pv.PVSC_ERR_UNSUPPORTED
     assert lib.pvsc_apply_H(None, 1, 0, None, None, None) == pv.PVSC_ERR_ARG
     assert lib.pvsc_work_bytes(None, 0, 1, 0, 0) == 0
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (7, 1), (40, 2), (64, 3)])
+def test_host_hermitian_jacobi_matches_numpy(libpath, n, seed):
+    # the small dense eigenproblem of ChebFD's Rayleigh-Ritz step, host code only
+    lib = ctypes.CDLL(libpath)
+    lib.pvsc_debug_eigh.argtypes = [ctypes.c_int] + [ctypes.c_void_p] * 3
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = A + A.conj().T
+    if n >= 40:  # Kramers-like degenerate pairs, as in the TI spectrum
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+        A = Q @ np.diag(np.repeat(rng.standard_normal(n // 2), 2)) @ Q.conj().T
+    Af = np.asfortranarray(A).astype(np.complex128)
+    w = np.zeros(n)
+    V = np.zeros((n, n), dtype=np.complex128, order="F")
+    assert lib.pvsc_debug_eigh(n, Af.ctypes.data, w.ctypes.data, V.ctypes.data) == 0
+    scale = np.linalg.norm(A)
+    assert np.max(np.abs(w - np.linalg.eigvalsh(A))) < 1e-13 * scale
+    assert np.max(np.abs(A @ V - V * w)) < 1e-12 * scale
+    assert np.max(np.abs(V.conj().T @ V - np.eye(n))) < 1e-12
