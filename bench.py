@@ -75,10 +75,11 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default launch shape instead of the autotuned one")
     ap.add_argument("--workload", default="ti_slab",
-                    choices=["ti_slab", "ti_cube", "graphene_qd", "batched", "adjoint", "ti_akE"],
+                    choices=["ti_slab", "ti_cube", "graphene_qd", "batched", "adjoint", "ti_akE", "chebfd"],
                     help="ti_slab (default): the benchmark line; the others measure the remaining "
                          "workloads (16^3 cube KPM, graphene QD-array propagation, batched KPM over "
-                         "64 lattices, adjoint gradient, A(k,E) of a clean TI) and print one JSON line each")
+                         "64 lattices, adjoint gradient, A(k,E) of a clean TI, ChebFD interior "
+                         "eigenpairs) and print one JSON line each")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="profiling case: one KPM call of this many complex64 sweeps (stencil, "
                          "recurrence, dots) on the lattice (ti_slab), or this many complex64 "
@@ -397,6 +398,44 @@ def run_workload(args, pv, dev, rank, world):
                      "peak_at_k0": peak(32, 0.5, 1.5), "closed_form_k0": 1.0,
                      "roofline": _hbm_roof(96.0, lups, ms, "ti_sweep<float,2,F_DOTS> (R = 64, V = 0)"),
                      "clocks": clk, "gpu_launches": args.steps * len(calls) * ((M + 1) // 2 + 1 + nk_call)})
+    elif args.workload == "chebfd":
+        # interior eigenpairs of a disordered TI slab, the filter-diagonalization test case of
+        # 240 x 240 x 6 sites, 40 states around E = 0 (window from the KPM DOS), complex64 filter
+        dims = (240, 240, 6)
+        lat = pv.Lattice.ti(dims, (1, 1, 0), t=1.0, m=2.0, disorder=(1.0, 5))
+        emin, emax, a, b = lat.spectral_bounds()
+        t0 = time.perf_counter()
+        mu = pv.kpm_moments(lat, 8192, a, b, R=32, prec=pv.C64, seed=9)
+        Eg = np.linspace(-0.5, 0.5, 20001)
+        cum = np.cumsum(pv.dos(lat, mu, Eg, a, b).cpu().numpy()) * (Eg[1] - Eg[0])
+        lam = next(l for l in np.linspace(0.001, 0.5, 5000)
+                   if np.interp(l, Eg, cum) - np.interp(-l, Eg, cum) >= 40)
+        torch.cuda.synchronize()
+        t_dos = time.perf_counter() - t0
+        deg, ns = 4000, 64
+        lat.autotune(ns, pv.C64)
+        clocks.start()
+        t0 = time.perf_counter()
+        theta, res, X, n_in, iters = pv.chebfd(lat, -lam, lam, a, b, n_search=ns, degree=deg, max_iter=30,
+                                               tol=1e-6, prec=pv.C64)
+        torch.cuda.synchronize()
+        secs = max_over_ranks(time.perf_counter() - t0, dev)
+        clk = clocks.stop()
+        inside = (theta >= -lam) & (theta <= lam)
+        lups = lat.n_sites * ns * deg * iters  # filter sweeps dominate
+        line.update({"workload": "chebfd", "value": round(world * lups / secs / 1e9, 3),
+                     "ms_per_step": round(1000 * secs, 1), "steps": 1, "dtype": "c64 filter, c128 Ritz",
+                     "config": {"workload": "ChebFD: TI slab 240x240x6 (PBC x,y; open z), m=2, W=1, eigenpairs "
+                                            "in [-lambda, lambda] holding ~40 states (lambda from the KPM DOS), "
+                                            "64 search vectors, degree 4000, tol 1e-6",
+                                "lambda": lam, "dos_seconds": round(t_dos, 3)},
+                     "iterations": iters, "eigenpairs_found": int(n_in),
+                     "max_residual": float(res[inside].max()) if n_in else None,
+                     "kramers_pairs": bool(n_in % 2 == 0),
+                     "roofline": _hbm_roof(96.0 + 8.0 / ns + 64.0, lups, 1000 * secs,
+                                           "ti_sweep<float,2,*> series sweeps (R = 64; accumulator on "
+                                           "every other sweep), solver average"),
+                     "clocks": clk, "gpu_launches": None})
     elif args.workload == "batched":
         specs = W.batched_lattices()
         if args.sweeps_only:  # profiling case: the first --batched-count lattices, untimed
