@@ -109,8 +109,8 @@ typedef struct {
   int64_t dims[3];
   double t;             /* transfer integral (the paper's unit of energy) */
   double m;             /* TI mass parameter (ignored for graphene) */
-  double delta1;        /* TI Delta_1 Gamma^5: must be 0 (PVSC_ERR_UNSUPPORTED) */
-  double delta2;        /* TI Delta_2 Gamma^15: must be 0 (PVSC_ERR_UNSUPPORTED) */
+  double delta1;        /* TI on-site Delta_1 Gamma^5 (Eq. TB_H_topi); 0 for graphene */
+  double delta2;        /* TI on-site Delta_2 Gamma^15, Gamma^15 = [Gamma^1, Gamma^5]/2i */
   int32_t v_source;     /* PVSC_V_* */
   int32_t reserved;
   const double* V;      /* for PVSC_V_HOST / PVSC_V_DEVICE, else ignored */
@@ -121,7 +121,7 @@ typedef struct {
 /* Create a lattice handle.  Allocates the handle and its device copy of V,
  * copies or generates V on `stream` and synchronises it.  *out is set only
  * on success.  Errors: ARG (null, dims < 1, unknown model or v_source,
- * t not finite), UNSUPPORTED (delta1/delta2 != 0), OOM, CUDA. */
+ * t, delta not finite; delta != 0 on graphene), OOM, CUDA. */
 int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattice** out);
 
 /* Destroy a handle (NULL is accepted).  The caller must have synchronised

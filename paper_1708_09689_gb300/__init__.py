@@ -182,7 +182,8 @@ class Lattice:
     """
 
     def __init__(self, model: int, dims, periodic, t: float = 1.0, m: float = 0.0, V=None,
-                 disorder=None, on_the_fly: bool = False, stream=None):
+                 disorder=None, on_the_fly: bool = False, delta1: float = 0.0, delta2: float = 0.0,
+                 stream=None):
         d = LatticeDesc()
         d.model = model
         dims = list(dims) + [1] * (3 - len(dims))
@@ -190,7 +191,7 @@ class Lattice:
         for i in range(3):
             d.dims[i] = int(dims[i])
             d.periodic[i] = int(bool(per[i]))
-        d.t, d.m, d.delta1, d.delta2 = float(t), float(m), 0.0, 0.0
+        d.t, d.m, d.delta1, d.delta2 = float(t), float(m), float(delta1), float(delta2)
         keep = None
         if disorder is not None:
             W, seed = disorder

@@ -111,6 +111,7 @@ __global__ void gershgorin_kernel(Geometry g, double* out /* [gridDim][2] */) {
       }
       const double V = (g.v_mode == 1) ? g.V[s]
                      : (g.v_mode == 2 ? g.W * (hash_uniform(g.vkey, (uint64_t)s) - 0.5) : 0.0);
+      radius += sqrt(g.d1 * g.d1 + g.d2 * g.d2);  // one Delta entry per row, |D1 +- i D2|
       for (int sign = -1; sign <= 1; sign += 2) {  // Gamma^1 = +1 / -1 rows
         const double c = V + sign * (g.m - self * g.t);
         lo = fmin(lo, c - radius);

@@ -27,6 +27,8 @@ struct Geometry {
   int v_mode;           // 0 zero, 1 stored, 2 regenerated from the hash
   uint64_t vkey;        // mix(seed ^ stream*gamma) for stream 0
   double W;             // disorder width for v_mode 2
+  double d1, d2;        // TI on-site Delta_1 Gamma^5 + Delta_2 Gamma^15 (Eq. TB_H_topi)
+  int has_delta;        // d1 != 0 or d2 != 0
 };
 
 // Neighbour index along one axis: idx -/+ stride, wrapped on a periodic axis,

@@ -429,6 +429,8 @@ static int kpm_moments_fx(const pvsc_lattice* lat, int R, const void* r0, uint64
                           cudaStream_t st) {
   if (lat->g.model != PVSC_TI)
     return set_error(PVSC_ERR_UNSUPPORTED, "PVSC_Q64 moments are implemented for the TI lattice only");
+  if (lat->g.has_delta)
+    return set_error(PVSC_ERR_UNSUPPORTED, "PVSC_Q64 moments do not include the Delta terms");
   const FxLayout L = fx_layout(lat, R);
   if (int rc = check_work(work, work_bytes, L.total)) return rc;
   // The fixed-point range relies on ||T_k(H~)|| <= 1: (a, b) must hold the

@@ -87,8 +87,10 @@ int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattic
     return set_error(PVSC_ERR_ARG, "graphene lattices are 2D: dims[2] must be 1");
   if (!std::isfinite(desc->t) || !std::isfinite(desc->m))
     return set_error(PVSC_ERR_ARG, "t and m must be finite");
-  if (desc->delta1 != 0.0 || desc->delta2 != 0.0)
-    return set_error(PVSC_ERR_UNSUPPORTED, "Delta_1 / Delta_2 terms are not implemented");
+  if (!std::isfinite(desc->delta1) || !std::isfinite(desc->delta2))
+    return set_error(PVSC_ERR_ARG, "delta1 and delta2 must be finite");
+  if (desc->model != PVSC_TI && (desc->delta1 != 0.0 || desc->delta2 != 0.0))
+    return set_error(PVSC_ERR_ARG, "Delta terms belong to the TI model");
   if (desc->v_source < PVSC_V_ZERO || desc->v_source > PVSC_V_ON_THE_FLY)
     return set_error(PVSC_ERR_ARG, "unknown v_source %d", desc->v_source);
   if ((desc->v_source == PVSC_V_HOST || desc->v_source == PVSC_V_DEVICE) && !desc->V)
@@ -110,6 +112,9 @@ int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattic
                                      : 4 * desc->dims[0] * desc->dims[1];
   g.t = desc->t;
   g.m = desc->model == PVSC_TI ? desc->m : 0.0;
+  g.d1 = desc->model == PVSC_TI ? desc->delta1 : 0.0;
+  g.d2 = desc->model == PVSC_TI ? desc->delta2 : 0.0;
+  g.has_delta = (g.d1 != 0.0 || g.d2 != 0.0) ? 1 : 0;
   g.v_mode = 0;
   g.W = desc->W;
   g.vkey = hash_key(desc->seed, 0);

@@ -68,8 +68,11 @@ def test_argument_errors_are_reported_without_a_device(libpath):
     d.model = pv.TI
     for i in range(3):
         d.dims[i] = 4
-    d.delta1 = 0.5
-    assert lib.pvsc_lattice_create(ctypes.byref(d), None, ctypes.byref(h)) == pv.PVSC_ERR_UNSUPPORTED
+    d.delta1 = float("nan")
+    assert lib.pvsc_lattice_create(ctypes.byref(d), None, ctypes.byref(h)) == pv.PVSC_ERR_ARG
+    d.model, d.dims[2], d.delta1 = pv.GRAPHENE, 1, 0.5  # Delta terms belong to the TI
+    assert lib.pvsc_lattice_create(ctypes.byref(d), None, ctypes.byref(h)) == pv.PVSC_ERR_ARG
+    assert b"Delta" in lib.pvsc_last_error()
     assert lib.pvsc_apply_H(None, 1, 0, None, None, None) == pv.PVSC_ERR_ARG
     assert lib.pvsc_work_bytes(None, 0, 1, 0, 0) == 0
 

@@ -526,3 +526,29 @@ def test_chebfd_finds_the_interior_eigenpairs_of_dense_diagonalisation():
     assert np.max(np.abs(np.sort(th) - target)) < 1e-12
     assert np.all(res < 1e-10)
     assert np.allclose(X.conj().T @ X, np.eye(16), atol=1e-12)
+
+
+@pytest.mark.parametrize("d1,d2", [(0.4, 0.0), (0.0, -0.3), (0.35, 0.25)])
+def test_ti_delta_terms_match_the_bloch_spectrum(d1, d2):
+    # Delta_1 Gamma^5 + Delta_2 Gamma^15 (Eq. TB_H_topi) on a clean periodic lattice: the
+    # spectrum is the union over the lattice momenta of the eigenvalues of the 4x4 Bloch
+    # matrix H(k) = E0 + sum_j (T_j e^{-i k_j} + T_j^+ e^{i k_j}), T_j = -(t/2)(Gamma^1 - i Gamma^{j+1})
+    # the block from site n to n + e_j, with Gamma^15 = [Gamma^1, Gamma^5]/(2i)
+    dims, t, m = (4, 3, 5), 1.0, 1.5
+    H = O.ti_hamiltonian(dims, (1, 1, 1), t, m, np.zeros(60), d1, d2)
+    ev = np.sort(np.linalg.eigvalsh(H.toarray()))
+    G = O.gamma_matrices()
+    G15 = (G[1] @ G[5] - G[5] @ G[1]) / 2j
+    E0 = m * G[1] + d1 * G[5] + d2 * G15
+    T = [-(t / 2) * (G[1] - 1j * G[j + 1]) for j in (1, 2, 3)]
+    bloch = []
+    for kx in 2 * np.pi * np.arange(dims[0]) / dims[0]:
+        for ky in 2 * np.pi * np.arange(dims[1]) / dims[1]:
+            for kz in 2 * np.pi * np.arange(dims[2]) / dims[2]:
+                Hk = E0.copy()
+                for Tj, kj in zip(T, (kx, ky, kz)):
+                    Hk = Hk + Tj * np.exp(-1j * kj) + Tj.conj().T * np.exp(1j * kj)
+                bloch.extend(np.linalg.eigvalsh(Hk))
+    assert np.max(np.abs(np.sort(bloch) - ev)) < 1e-12
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    assert b - a <= ev[0] and ev[-1] <= b + a
