@@ -157,8 +157,6 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
           cf.kt[v] = T(-0.5 * alpha * L.g.t);
           cf.gamma[v] = T(k == 0 ? 0.0 : -1.0);
           cf.delta[v] = T(0);
-          cf.ad1[v] = T(alpha * L.g.d1);
-          cf.ad2[v] = T(alpha * L.g.d2);
         }
         if (active) {
           // x is written by this kernel in other phases: coherent loads only (NC = false)
@@ -166,7 +164,7 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
                                   [&](int64_t s) { return site_potential_t<T>(L.g, s); },
                                   [&](T Vs, const Blk<T, VPT>& xc, const Blk<T, VPT>& S,
                                       const Blk<T, VPT>& D, const Blk<T, VPT>* yi, Blk<T, VPT>& yn) {
-                                    ti_combine(cf, Vs, xc, S, D, yi, yn, L.g.has_delta);
+                                    ti_combine(cf, Vs, xc, S, D, yi, yn, L.g);
                                   },
                                   [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
                                     store_blk<T, VPT>(Yout, s, R, rc, yn);

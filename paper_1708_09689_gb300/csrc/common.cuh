@@ -28,6 +28,7 @@ struct Geometry {
   uint64_t vkey;        // mix(seed ^ stream*gamma) for stream 0
   double W;             // disorder width for v_mode 2
   double d1, d2;        // TI on-site Delta_1 Gamma^5 + Delta_2 Gamma^15 (Eq. TB_H_topi)
+  float d1f, d2f;       // the same rounded to fp32, for complex64 sweeps
   int has_delta;        // d1 != 0 or d2 != 0
 };
 

@@ -114,6 +114,8 @@ int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattic
   g.m = desc->model == PVSC_TI ? desc->m : 0.0;
   g.d1 = desc->model == PVSC_TI ? desc->delta1 : 0.0;
   g.d2 = desc->model == PVSC_TI ? desc->delta2 : 0.0;
+  g.d1f = (float)g.d1;
+  g.d2f = (float)g.d2;
   g.has_delta = (g.d1 != 0.0 || g.d2 != 0.0) ? 1 : 0;
   g.v_mode = 0;
   g.W = desc->W;

@@ -174,7 +174,6 @@ __device__ __forceinline__ double2* acc_ptr(double2* base, int64_t s, int o, int
 template <typename T, int VPT>
 struct VecCoef {
   T alpha[VPT], ab[VPT], am[VPT], kt[VPT], gamma[VPT], delta[VPT];
-  T ad1[VPT], ad2[VPT];  // alpha Delta_1, alpha Delta_2 (TI)
 };
 
 template <typename T, int VPT>
@@ -190,8 +189,6 @@ __device__ __forceinline__ VecCoef<T, VPT> load_coef(const Sweep& p, int rc) {
     c.kt[v] = T(-0.5 * a * p.g.t);
     c.gamma[v] = T(p.coef[2][r]);
     c.delta[v] = T(p.coef[3][r]);
-    c.ad1[v] = T(a * p.g.d1);
-    c.ad2[v] = T(a * p.g.d2);
   }
   return c;
 }
@@ -571,12 +568,15 @@ __device__ __forceinline__ void axis_y_add(const Blk<T, VPT>& a, const Blk<T, VP
 // Eq. TB_H_topi.  Gamma^5 = sigma_z (x) s_x and Gamma^15 = [Gamma^1, Gamma^5]/2i =
 // sigma_z (x) s_y, so orbital 0 takes (D1 - i D2) x_1, orbital 1 (D1 + i D2) x_0,
 // orbital 2 -(D1 - i D2) x_3 and orbital 3 -(D1 + i D2) x_2.
+// The Delta values are read from the geometry (kernel parameter space) where
+// they are used, so the common Delta = 0 sweep holds no registers for them.
 template <typename T, int VPT>
-__device__ __forceinline__ void ti_add_delta(const VecCoef<T, VPT>& cf, const Blk<T, VPT>& x,
-                                             Blk<T, VPT>& y) {
+__device__ __forceinline__ void ti_add_delta(const Geometry& g, const VecCoef<T, VPT>& cf,
+                                             const Blk<T, VPT>& x, Blk<T, VPT>& y) {
+  const T d1 = sizeof(T) == 4 ? T(g.d1f) : T(g.d1), d2 = sizeof(T) == 4 ? T(g.d2f) : T(g.d2);
 #pragma unroll
   for (int v = 0; v < VPT; ++v) {
-    const T a1 = cf.ad1[v], a2 = cf.ad2[v];
+    const T a1 = cf.alpha[v] * d1, a2 = cf.alpha[v] * d2;
     const cplx<T> x0 = x.v[0][v], x1 = x.v[1][v], x2 = x.v[2][v], x3 = x.v[3][v];
     y.v[0][v].re += fma(a1, x1.re, a2 * x1.im);
     y.v[0][v].im += fma(a1, x1.im, -a2 * x1.re);
@@ -594,7 +594,7 @@ __device__ __forceinline__ void ti_add_delta(const VecCoef<T, VPT>& cf, const Bl
 template <typename T, int VPT>
 __device__ __forceinline__ void ti_combine(const VecCoef<T, VPT>& cf, T Vs, const Blk<T, VPT>& xc,
                                            const Blk<T, VPT>& S, const Blk<T, VPT>& D,
-                                           const Blk<T, VPT>* yi, Blk<T, VPT>& yn, bool has_delta) {
+                                           const Blk<T, VPT>* yi, Blk<T, VPT>& yn, const Geometry& g) {
 #pragma unroll
   for (int v = 0; v < VPT; ++v) {
     const T e = fma(cf.alpha[v], Vs, -cf.ab[v]);
@@ -612,7 +612,7 @@ __device__ __forceinline__ void ti_combine(const VecCoef<T, VPT>& cf, T Vs, cons
       yn.v[o][v] = {re, im};
     }
   }
-  if (has_delta) ti_add_delta(cf, xc, yn);
+  if (g.has_delta) ti_add_delta(g, cf, xc, yn);
 }
 
 template <typename T, int VPT, bool NC, int DEPTH, int NBUF, class Site, class Combine, class Emit>
@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p)
                            [&](int64_t s) { return site_potential_t<T>(p.g, s); },
                            [&](T Vs, const Blk<T, VPT>& xc, const Blk<T, VPT>& S,
                                const Blk<T, VPT>& D, const Blk<T, VPT>* yi, Blk<T, VPT>& yn) {
-                             ti_combine(cf, Vs, xc, S, D, yi, yn, p.g.has_delta);
+                             ti_combine(cf, Vs, xc, S, D, yi, yn, p.g);
                            },
                            [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
                              const int64_t sites[4] = {s, s, s, s};
@@ -842,7 +842,7 @@ __global__ void __launch_bounds__(256, 2) ti_sweep_flat(const __grid_constant__ 
         yn.v[o][v] = {re, im};
       }
     }
-    if (p.g.has_delta) ti_add_delta(cf, xc, yn);
+    if (p.g.has_delta) ti_add_delta(p.g, cf, xc, yn);
     const int64_t sites[4] = {s, s, s, s};
     epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
   }

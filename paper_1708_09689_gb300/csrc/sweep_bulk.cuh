@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(256) ti_sweep_bulk(const __grid_constant__ Swe
             }
             yn.v[o][0] = {re, im};
           }
-          if (p.g.has_delta) ti_add_delta(cf, xc, yn);
+          if (p.g.has_delta) ti_add_delta(p.g, cf, xc, yn);
         }
         const int64_t sites[4] = {s, s, s, s};
         epilogue<T, 1, FEAT>(p, s, r, xc, yn, dacc, sites);
