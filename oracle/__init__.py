@@ -16,6 +16,7 @@ Contents and the passages they follow:
   gamma_matrices            Dirac matrices of Sec. 2.2 (Eq. TB_H_topi)
   ti_hamiltonian            Eq. TB_H_topi (cubic 4-band topological insulator)
   graphene_hamiltonian      Eq. graphene_model (4-site rectangular cell)
+  wsm_hamiltonian           Eq. TB_H_wsm (two-band Weyl semimetal)
   gershgorin, cheb_scale    Sec. 4.1 (a = (Emax-Emin+eps)/2, b = (Emax+Emin)/2)
   cheb_step                 fused spMVM semantics of Listing graphenec (Sec. 3.2)
   kpm_moments               mu_k = <r|T_k(H~)|r> (Sec. 2.2, Sec. 4), direct recurrence
@@ -172,6 +173,29 @@ def ti_hamiltonian(dims, periodic, t, m, V, delta1=0.0, delta2=0.0, rows=None):
     onsite = E0[None, :, :] + V[:, None, None] * G[0][None, :, :]
     hops = [(j, -(t / 2.0) * (G[1] - 1j * G[j + 2])) for j in range(3)]
     return _assemble(dims, periodic, 4, onsite, hops, rows)
+
+
+# Pauli matrices of the two-band Weyl semimetal (Eq. TB_H_wsm)
+_PAULI = (np.array([[0, 1], [1, 0]], dtype=np.complex128),
+          np.array([[0, -1j], [1j, 0]], dtype=np.complex128),
+          np.array([[1, 0], [0, -1]], dtype=np.complex128))
+
+
+def wsm_hamiltonian(dims, periodic, V, k0=math.pi / 2, rows=None):
+    """Eq. TB_H_wsm on an Lx x Ly x Lz cuboid, as a (2N x 2N) CSR matrix.
+
+    Two orbitals per site (row index = 2 site + orbital).  Bond n -> n + e_x:
+    Psi_{n+x}^+ (sigma_x / 2) Psi_n; bond n -> n + e_j, j = y, z:
+    Psi_{n+j}^+ ((sigma_x + i sigma_j) / 2) Psi_n; each plus its Hermitian
+    conjugate.  On-site block V_n - sigma_x (2 + cos k0).  Transfer element 1.
+    """
+    sx, sy, sz = _PAULI
+    dims = tuple(int(d) for d in dims)
+    n_sites = int(np.prod(dims))
+    V = np.asarray(V, dtype=np.float64).reshape(n_sites)
+    onsite = V[:, None, None] * np.eye(2)[None, :, :] - (2.0 + math.cos(k0)) * sx[None, :, :]
+    hops = [(0, sx / 2.0), (1, (sx + 1j * sy) / 2.0), (2, (sx + 1j * sz) / 2.0)]
+    return _assemble(dims, periodic, 2, onsite, hops, rows)
 
 
 # The 4x4 matrices of Eq. graphene_model (entries in units of t)

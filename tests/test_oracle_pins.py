@@ -552,3 +552,35 @@ def test_ti_delta_terms_match_the_bloch_spectrum(d1, d2):
     assert np.max(np.abs(np.sort(bloch) - ev)) < 1e-12
     a, b = O.cheb_scale(*O.gershgorin(H))
     assert b - a <= ev[0] and ev[-1] <= b + a
+
+
+# ------------------------------------------------------------------ Weyl semimetal (Eq. TB_H_wsm)
+@pytest.mark.parametrize("dims,k0", [((8, 3, 4), math.pi / 2), ((4, 4, 2), math.pi / 2), ((6, 5, 3), 1.1)])
+def test_wsm_periodic_spectrum_is_the_closed_form_band(dims, k0):
+    # Eq. band_h_wsm: eps(k) = sigma_x (cos kx - cos k0 + cos ky + cos kz - 2) + sigma_y sin ky
+    # + sigma_z sin kz, eigenvalues +-|d(k)|, over the lattice momenta of a periodic cuboid
+    H = O.wsm_hamiltonian(dims, (1, 1, 1), np.zeros(int(np.prod(dims))), k0)
+    assert abs(H - H.conj().T).max() == 0
+    ev = np.sort(np.linalg.eigvalsh(H.toarray()))
+    band = []
+    for kx in 2 * np.pi * np.arange(dims[0]) / dims[0]:
+        for ky in 2 * np.pi * np.arange(dims[1]) / dims[1]:
+            for kz in 2 * np.pi * np.arange(dims[2]) / dims[2]:
+                d = np.array([math.cos(kx) - math.cos(k0) + math.cos(ky) + math.cos(kz) - 2.0,
+                              math.sin(ky), math.sin(kz)])
+                band += [np.linalg.norm(d), -np.linalg.norm(d)]
+    assert np.max(np.abs(np.sort(band) - ev)) < 1e-12
+
+
+def test_wsm_weyl_nodes_and_open_boundaries():
+    # Weyl nodes at (+-k0, 0, 0), k0 = pi/2: a periodic cuboid with Lx = 8 contains both,
+    # so E = 0 appears four times (two nodes, two bands each); an open axis drops the
+    # bonds that leave the cuboid (the Hermitian matrix then differs only there)
+    H = O.wsm_hamiltonian((8, 4, 4), (1, 1, 1), np.zeros(128))
+    ev = np.linalg.eigvalsh(H.toarray())
+    assert np.sum(np.abs(ev) < 1e-12) == 4
+    Ho = O.wsm_hamiltonian((8, 4, 4), (1, 1, 0), np.zeros(128))
+    diff = (H - Ho).tocoo()
+    rows = diff.row // 2
+    z = rows // 32
+    assert set(np.unique(z)) == {0, 3}  # only the bonds across the z boundary differ
