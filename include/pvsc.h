@@ -64,7 +64,7 @@ typedef enum {
   PVSC_ERR_UNSUPPORTED = -5  /* valid but not implemented combination */
 } pvsc_status;
 
-enum { PVSC_TI = 1, PVSC_GRAPHENE = 2 };
+enum { PVSC_TI = 1, PVSC_GRAPHENE = 2, PVSC_WSM = 3 };
 enum { PVSC_C128 = 0, PVSC_C64 = 1, PVSC_Q64 = 2 };
 
 /* Source of the on-site potential V (one fp64 value per site). */
@@ -104,7 +104,7 @@ enum {
  * disorder from a box of width W (gamma), V_n in [-W/2, W/2) (Sec. 4.2).
  */
 typedef struct {
-  int32_t model;        /* PVSC_TI or PVSC_GRAPHENE */
+  int32_t model;        /* PVSC_TI, PVSC_GRAPHENE or PVSC_WSM */
   int32_t periodic[3];
   int64_t dims[3];
   double t;             /* transfer integral (the paper's unit of energy) */
@@ -116,6 +116,7 @@ typedef struct {
   const double* V;      /* for PVSC_V_HOST / PVSC_V_DEVICE, else ignored */
   uint64_t seed;        /* for PVSC_V_SEED / PVSC_V_ON_THE_FLY */
   double W;             /* disorder width for PVSC_V_SEED / PVSC_V_ON_THE_FLY */
+  double k0;            /* PVSC_WSM: Weyl nodes at (+-k0, 0, 0) (Eq. TB_H_wsm); else ignored */
 } pvsc_lattice_desc;
 
 /* Create a lattice handle.  Allocates the handle and its device copy of V,

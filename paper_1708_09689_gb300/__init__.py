@@ -24,7 +24,7 @@ from .build import LIB_PATH
 
 PVSC_OK, PVSC_ERR_ARG, PVSC_ERR_CUDA, PVSC_ERR_OOM, PVSC_ERR_TIMEOUT, PVSC_ERR_UNSUPPORTED = \
     0, -1, -2, -3, -4, -5
-TI, GRAPHENE = 1, 2
+TI, GRAPHENE, WSM = 1, 2, 3
 C128, C64, Q64 = 0, 1, 2  # Q64: fixed-point vectors, pvsc_kpm_moments on TI only
 KERNEL_NONE, KERNEL_JACKSON, KERNEL_LORENTZ = 0, 1, 2  # damping kernels of kpm_density
 V_ZERO, V_HOST, V_DEVICE, V_SEED, V_ON_THE_FLY = 0, 1, 2, 3, 4
@@ -52,6 +52,7 @@ class LatticeDesc(ctypes.Structure):
         ("V", ctypes.c_void_p),
         ("seed", ctypes.c_uint64),
         ("W", ctypes.c_double),
+        ("k0", ctypes.c_double),
     ]
 
 
@@ -183,7 +184,7 @@ class Lattice:
 
     def __init__(self, model: int, dims, periodic, t: float = 1.0, m: float = 0.0, V=None,
                  disorder=None, on_the_fly: bool = False, delta1: float = 0.0, delta2: float = 0.0,
-                 stream=None):
+                 k0: float = 0.0, stream=None):
         d = LatticeDesc()
         d.model = model
         dims = list(dims) + [1] * (3 - len(dims))
@@ -192,6 +193,7 @@ class Lattice:
             d.dims[i] = int(dims[i])
             d.periodic[i] = int(bool(per[i]))
         d.t, d.m, d.delta1, d.delta2 = float(t), float(m), float(delta1), float(delta2)
+        d.k0 = float(k0)
         keep = None
         if disorder is not None:
             W, seed = disorder
@@ -222,6 +224,11 @@ class Lattice:
     @classmethod
     def ti(cls, dims, periodic, t=1.0, m=2.0, **kw):
         return cls(TI, dims, periodic, t=t, m=m, **kw)
+
+    @classmethod
+    def wsm(cls, dims, periodic, k0=math.pi / 2, **kw):
+        """Two-band Weyl semimetal of Eq. TB_H_wsm (Weyl nodes at (+-k0, 0, 0)); Lx even."""
+        return cls(WSM, dims, periodic, k0=k0, **kw)
 
     @classmethod
     def graphene(cls, cells, periodic, t=1.0, **kw):

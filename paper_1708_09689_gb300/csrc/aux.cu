@@ -118,6 +118,44 @@ __global__ void gershgorin_kernel(Geometry g, double* out /* [gridDim][2] */) {
         hi = fmax(hi, c + radius);
       }
     }
+  } else if (g.model == 3) {
+    // Weyl semimetal (Eq. TB_H_wsm), rows a and b of each site: |A_x| rows 1/2,
+    // A_y = [[0,1],[0,0]] reaches row a from y-1 and row b (A_y^+) from y+1,
+    // |A_z| rows 1; a periodic axis of length 2 folds both bonds into sigma_x
+    // (row sum 1), of length 1 into the on-site sigma_x coefficient -c0 + 1.
+    const int64_t Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.n_sites;
+         s += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t x = s % Lx, y = (s / Lx) % Ly, z = s / (Lx * Ly);
+      const int64_t co[3] = {x, y, z};
+      double ra = 0.0, rb = 0.0, sx = -g.m;
+      for (int d = 0; d < 3; ++d) {
+        const int64_t mn = nbr_minus(co[d], co[d], g.L[d], g.per[d], 1);
+        const int64_t pl = nbr_plus(co[d], co[d], g.L[d], g.per[d], 1);
+        if (mn == co[d]) {
+          sx += 1.0;
+        } else if (mn >= 0 && mn == pl) {
+          ra += 1.0;
+          rb += 1.0;
+        } else if (d == 0) {
+          const double h = 0.5 * ((mn >= 0) + (pl >= 0));
+          ra += h;
+          rb += h;
+        } else if (d == 1) {
+          ra += (mn >= 0) ? 1.0 : 0.0;
+          rb += (pl >= 0) ? 1.0 : 0.0;
+        } else {
+          const double h = (double)((mn >= 0) + (pl >= 0));
+          ra += h;
+          rb += h;
+        }
+      }
+      const double V = (g.v_mode == 1) ? g.V[s]
+                     : (g.v_mode == 2 ? g.W * (hash_uniform(g.vkey, (uint64_t)s) - 0.5) : 0.0);
+      const double r = fmax(ra, rb) + fabs(sx);
+      lo = fmin(lo, V - r);
+      hi = fmax(hi, V + r);
+    }
   } else {
     const int64_t Nx = g.L[0], Ny = g.L[1];
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.n_sites;
@@ -159,7 +197,7 @@ __global__ void gershgorin_kernel(Geometry g, double* out /* [gridDim][2] */) {
 
 // Neighbour table with the sweeps' own index helpers.
 __global__ void neighbours_kernel(Geometry g, int64_t* nbr) {
-  if (g.model == 1) {
+  if (g.model != 2) {  // cubic lattices (TI, Weyl semimetal): per site
     const int64_t Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], plane = Lx * Ly;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.n_sites;
          s += (int64_t)gridDim.x * blockDim.x) {
@@ -222,7 +260,7 @@ int launch_scale_init(const void* x128, double2* acc, double cr, double ci, int6
 int launch_adjoint_top(const pvsc_lattice* lat, int R, const double2* G, double sr, double si,
                        double2* uM, const double2* w, double gscale, double* grad,
                        cudaStream_t st) {
-  const int per_site = (lat->g.model == 1 ? 4 : 1) * R;
+  const int per_site = orbitals_of(lat->g.model) * R;
   adjoint_top_kernel<<<grid_for(lat->g.n_sites, 256), 256, 0, st>>>(G, sr, si, uM, w, gscale, grad,
                                                                   lat->g.n_sites, per_site);
   PVSC_CUDA_TRY(cudaGetLastError());
@@ -254,7 +292,7 @@ int launch_gershgorin(const Geometry& g, double* out, int grid, cudaStream_t st)
 }
 
 int launch_neighbours(const Geometry& g, int64_t* nbr, cudaStream_t st) {
-  const int64_t n = g.model == 1 ? g.n_sites : g.L[0] * g.L[1];
+  const int64_t n = g.model != 2 ? g.n_sites : g.L[0] * g.L[1];
   neighbours_kernel<<<grid_for(n, 256), 256, 0, st>>>(g, nbr);
   PVSC_CUDA_TRY(cudaGetLastError());
   return PVSC_OK;

@@ -266,7 +266,7 @@ int pvsc_chebfd(const pvsc_lattice* lat, const pvsc_chebfd_params* prm, double a
   if (int rc = check_ptr(work, "work")) return rc;
   if (work_bytes < L.total) return set_error(PVSC_ERR_ARG, "work too small: %zu < %zu", work_bytes, L.total);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int64_t D = lat->g.n_sites * (lat->g.model == PVSC_TI ? 4 : 1);
+  const int64_t D = lat->g.n_sites * orbitals_of(lat->g.model);
   void* Y = at(work, L.y);
   void* HQ = at(work, L.hq);
   void* dG = at(work, L.gram);

@@ -17,11 +17,11 @@ constexpr int kNumDots = 4;  // <x|x>, Re<y|x>, Im<y|x>, <y|y>
 
 // ---------------------------------------------------------------- geometry
 struct Geometry {
-  int model;            // 1 TI, 2 graphene
+  int model;            // 1 TI, 2 graphene, 3 Weyl semimetal
   int per[3];           // periodic flags
   int64_t L[3];         // TI: Lx, Ly, Lz sites; graphene: Nx, Ny cells, 1
   int64_t n_sites;      // TI: Lx Ly Lz; graphene: 4 Nx Ny
-  double t, m;          // hopping, TI mass
+  double t, m;          // hopping; TI mass, or for the Weyl semimetal 2 + cos k0
   const double* V;      // device [n_sites] when v_mode == 1
   const float* V32;     // the same potential rounded to fp32, for complex64 sweeps
   int v_mode;           // 0 zero, 1 stored, 2 regenerated from the hash
@@ -31,6 +31,11 @@ struct Geometry {
   float d1f, d2f;       // the same rounded to fp32, for complex64 sweeps
   int has_delta;        // d1 != 0 or d2 != 0
 };
+
+// Orbitals per site: 4 (TI), 1 (graphene site), 2 (Weyl semimetal).
+__host__ __device__ __forceinline__ int orbitals_of(int model) {
+  return model == 1 ? 4 : (model == 3 ? 2 : 1);
+}
 
 // Neighbour index along one axis: idx -/+ stride, wrapped on a periodic axis,
 // -1 where an open axis ends.  A periodic axis of length 1 returns idx itself

@@ -125,6 +125,7 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
                      !(prec == PVSC_C64 && vpt == 1 && p.R > 1);
   const int model = flat ? kModelTIFlat
                     : async ? (sh.kernel == 2 ? kModelTIAsync : kModelTIAsyncDeep)
+                    : lat->g.model == PVSC_WSM ? kModelWSM
                             : lat->g.model;
   int rc = prec == PVSC_C128 ? occupancy_c128(model, feat, threads, &occ)
                              : occupancy_c64(model, vpt, feat, threads, &occ);
@@ -151,7 +152,8 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
     p.zslab = (int)zs;
     units = nbx * ((Lz + zs - 1) / zs);
   } else {
-    const int64_t ncell = lat->g.L[0] * lat->g.L[1];
+    // graphene: 4-site cells; Weyl semimetal: cells of two sites
+    const int64_t ncell = lat->g.model == PVSC_WSM ? lat->g.n_sites / 2 : lat->g.L[0] * lat->g.L[1];
     units = (ncell * p.C + threads - 1) / threads;
   }
   const int grid = (int)(units < grid_max ? units : grid_max);
@@ -249,7 +251,7 @@ static int run_series(const pvsc_lattice* lat, int R, int prec, const void* x, v
                       const std::vector<cd>& cw, cd phase, double a, double b, void* work,
                       cudaStream_t st) {
   const SeriesLayout L = series_layout(lat, R, prec);
-  const int64_t n = lat->g.n_sites * (lat->g.model == PVSC_TI ? 4 : 1) * (int64_t)R;
+  const int64_t n = lat->g.n_sites * orbitals_of(lat->g.model) * (int64_t)R;
   void* wa = wptr(work, L.wa);
   void* wb = wptr(work, L.wb);
   double2* acc = reinterpret_cast<double2*>(wptr(work, L.acc));
@@ -360,7 +362,7 @@ int pvsc_random_vectors(const pvsc_lattice* lat, int R, int prec, uint64_t seed,
                         void* stream) {
   if (int rc = check_common(lat, R, prec)) return rc;
   if (int rc = check_ptr(out, "out")) return rc;
-  const int64_t D = lat->g.n_sites * (lat->g.model == PVSC_TI ? 4 : 1);
+  const int64_t D = lat->g.n_sites * orbitals_of(lat->g.model);
   return launch_random_phase(out, prec, D, R, seed, static_cast<cudaStream_t>(stream));
 }
 
@@ -524,7 +526,7 @@ int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, u
   const size_t voff = (dots_work_bytes(lat, R) + 255) & ~size_t(255);
   void* wa = wptr(work, voff);
   void* wb = wptr(work, voff + vec_bytes(lat, R, prec));
-  const int64_t D = lat->g.n_sites * (lat->g.model == PVSC_TI ? 4 : 1);
+  const int64_t D = lat->g.n_sites * orbitals_of(lat->g.model);
   const std::vector<uint64_t> key = {1, (uint64_t)R, (uint64_t)prec, bits(r0), seed, (uint64_t)M,
                                      bits(a), bits(b), bits(mu), bits(work)};
   auto body = [&](cudaStream_t cs) -> int {
@@ -665,7 +667,7 @@ int pvsc_cheb_adjoint_step(const pvsc_lattice* lat, int R, int prec, const void*
                    wptr(work, kWorkHeader + (size_t)(M > 1 ? M : 1) * vb)};
   const cd cphi = std::exp(cd(0, b * dt));  // conj(e^{-i b dt})
   auto sigma = [&](int k) { return std::conj(cw[k]) * cphi; };
-  const int64_t n = lat->g.n_sites * (lat->g.model == PVSC_TI ? 4 : 1);
+  const int64_t n = lat->g.n_sites * orbitals_of(lat->g.model);
   if (M == 0) {
     const cd s0 = sigma(0);
     return launch_scale_init(G, static_cast<double2*>(G), s0.real(), s0.imag(), n, st);

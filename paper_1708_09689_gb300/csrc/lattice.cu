@@ -49,7 +49,7 @@ int check_ptr(const void* p, const char* name) {
 }
 
 size_t vec_bytes(const pvsc_lattice* lat, int R, int prec) {
-  const int64_t D = lat->g.n_sites * (lat->g.model == 1 ? 4 : 1);
+  const int64_t D = lat->g.n_sites * orbitals_of(lat->g.model);
   const size_t b = (size_t)D * R * (prec == PVSC_C128 ? 16 : 8);
   return (b + 255) & ~size_t(255);
 }
@@ -79,8 +79,11 @@ const char* pvsc_version(void) { return "pvsc-gb300 1.0 (sm_103a)"; }
 
 int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattice** out) {
   if (!desc || !out) return set_error(PVSC_ERR_ARG, "desc and out must not be NULL");
-  if (desc->model != PVSC_TI && desc->model != PVSC_GRAPHENE)
+  if (desc->model != PVSC_TI && desc->model != PVSC_GRAPHENE && desc->model != PVSC_WSM)
     return set_error(PVSC_ERR_ARG, "unknown model %d", desc->model);
+  if (desc->model == PVSC_WSM && (desc->dims[0] % 2 != 0 || !std::isfinite(desc->k0)))
+    return set_error(PVSC_ERR_ARG, "the Weyl semimetal needs an even Lx (its sweep pairs sites "
+                     "along x) and a finite k0");
   for (int d = 0; d < 3; ++d)
     if (desc->dims[d] < 1) return set_error(PVSC_ERR_ARG, "dims[%d] = %lld < 1", d, (long long)desc->dims[d]);
   if (desc->model == PVSC_GRAPHENE && desc->dims[2] != 1)
@@ -108,10 +111,10 @@ int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattic
     g.per[d] = desc->periodic[d] ? 1 : 0;
     g.L[d] = desc->dims[d];
   }
-  g.n_sites = desc->model == PVSC_TI ? desc->dims[0] * desc->dims[1] * desc->dims[2]
-                                     : 4 * desc->dims[0] * desc->dims[1];
+  g.n_sites = desc->model == PVSC_GRAPHENE ? 4 * desc->dims[0] * desc->dims[1]
+                                          : desc->dims[0] * desc->dims[1] * desc->dims[2];
   g.t = desc->t;
-  g.m = desc->model == PVSC_TI ? desc->m : 0.0;
+  g.m = desc->model == PVSC_TI ? desc->m : (desc->model == PVSC_WSM ? 2.0 + std::cos(desc->k0) : 0.0);
   g.d1 = desc->model == PVSC_TI ? desc->delta1 : 0.0;
   g.d2 = desc->model == PVSC_TI ? desc->delta2 : 0.0;
   g.d1f = (float)g.d1;
@@ -171,7 +174,7 @@ int pvsc_lattice_destroy(pvsc_lattice* lat) {
 int pvsc_lattice_info(const pvsc_lattice* lat, int64_t* n_sites, int32_t* orbitals) {
   if (int rc = check_lattice(lat)) return rc;
   if (n_sites) *n_sites = lat->g.n_sites;
-  if (orbitals) *orbitals = lat->g.model == PVSC_TI ? 4 : 1;
+  if (orbitals) *orbitals = orbitals_of(lat->g.model);
   return PVSC_OK;
 }
 

@@ -955,4 +955,126 @@ __global__ void __launch_bounds__(256) gr_sweep(const __grid_constant__ Sweep p)
   }
 }
 
+// ---------------------------------------------------------------- Weyl semimetal sweep
+// Eq. TB_H_wsm: two orbitals (a, b) per site, bonds n -> n + e_x with
+// sigma_x/2 and n -> n + e_j (j = y, z) with (sigma_x + i sigma_j)/2, each with
+// its Hermitian conjugate, on-site V_n - c0 sigma_x, c0 = 2 + cos k0 (kept in
+// g.m).  Acting on a site:
+//   (H x)_a = V a - c0 b + (b_x- + b_x+)/2 + b_y- + (b_z- + b_z+)/2 + i (a_z- - a_z+)/2
+//   (H x)_b = V b - c0 a + (a_x- + a_x+)/2 + a_y+ + (a_z- + a_z+)/2 + i (b_z+ - b_z-)/2
+// A thread owns a cell of two x-adjacent sites (2X, 2X+1): its four
+// components (site 2X: a, b; site 2X+1: a, b) are the four consecutive block
+// components of the layout, so cell c = X + (Lx/2)(y + Ly z) is loaded and
+// stored like a 4-orbital block and shares the epilogue of the other sweeps.
+template <typename T, int VPT, int FEAT>
+__global__ void __launch_bounds__(256) wsm_sweep(const __grid_constant__ Sweep p) {
+  const int64_t NX = p.g.L[0] / 2, Ly = p.g.L[1], Lz = p.g.L[2];
+  const int64_t ncell = NX * Ly * Lz;
+  const int64_t plane = NX * Ly;  // cells per z plane
+  const int R = p.R, C = p.C;
+  const int rc = threadIdx.x % C;
+  const VecCoef<T, VPT> cf = load_coef<T, VPT>(p, rc);
+  const T* __restrict__ X = static_cast<const T*>(p.x);
+  DotAcc<T, VPT> dacc;
+  dacc.init();
+  const int cshift = __ffs(C) - 1;  // C = R / VPT is a power of two
+  const int64_t cstride = ((int64_t)gridDim.x * blockDim.x) >> cshift;
+  const int64_t szs = cstride / plane, rem = cstride - szs * plane;
+  const int64_t sys = rem / NX, sxs = rem - sys * NX;
+  int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> cshift;
+  int64_t z = c / plane, xy = c - z * plane;
+  int64_t y = xy / NX, x = xy - y * NX;
+  const T half = T(0.5);
+  for (; c < ncell; c += cstride, x += sxs, y += sys, z += szs) {
+    if (x >= NX) {
+      x -= NX;
+      ++y;
+    }
+    if (y >= Ly) {
+      y -= Ly;
+      ++z;
+    }
+    const int64_t cxm = nbr_minus(c, x, NX, p.g.per[0], 1), cxp = nbr_plus(c, x, NX, p.g.per[0], 1);
+    const int64_t cym = nbr_minus(c, y, Ly, p.g.per[1], NX), cyp = nbr_plus(c, y, Ly, p.g.per[1], NX);
+    const int64_t czm = nbr_minus(c, z, Lz, p.g.per[2], plane), czp = nbr_plus(c, z, Lz, p.g.per[2], plane);
+    Blk<T, VPT> xc, yi, zm, zp;
+    load_blk<T, VPT, true>(X, c, R, rc, xc);
+    if (p.yin != nullptr) load_blk<T, VPT, false>(static_cast<const T*>(p.yin), c, R, rc, yi);
+    if (czm >= 0) load_blk<T, VPT, true>(X, czm, R, rc, zm); else zero_blk(zm);
+    if (czp >= 0) load_blk<T, VPT, true>(X, czp, R, rc, zp); else zero_blk(zp);
+    // x neighbours of the pair: site 2X-1 is component 2, 3 of cell X-1, site
+    // 2X+2 component 0, 1 of cell X+1 (with one site per cell row wrapping
+    // onto itself when NX = 1)
+    cplx<T> xma[VPT], xmb[VPT], xpa[VPT], xpb[VPT], yma0[VPT], yma1[VPT], ypa0[VPT], ypa1[VPT];
+    if (cxm >= 0) {
+      load_one<T, VPT>(X, cxm, 2, R, rc, xma);
+      load_one<T, VPT>(X, cxm, 3, R, rc, xmb);
+    }
+    if (cxp >= 0) {
+      load_one<T, VPT>(X, cxp, 0, R, rc, xpa);
+      load_one<T, VPT>(X, cxp, 1, R, rc, xpb);
+    }
+    // y-: the b of both sites of cell y-1; y+: the a of both sites of cell y+1
+    if (cym >= 0) {
+      load_one<T, VPT>(X, cym, 1, R, rc, yma0);
+      load_one<T, VPT>(X, cym, 3, R, rc, yma1);
+    }
+    if (cyp >= 0) {
+      load_one<T, VPT>(X, cyp, 0, R, rc, ypa0);
+      load_one<T, VPT>(X, cyp, 2, R, rc, ypa1);
+    }
+    const T V0 = site_potential_t<T>(p.g, 2 * c), V1 = site_potential_t<T>(p.g, 2 * c + 1);
+    Blk<T, VPT> yn;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const cplx<T> zero{T(0), T(0)};
+      // in-pair x bonds: site 0's x+ neighbour is site 1, site 1's x- neighbour is site 0
+      const cplx<T> a0 = xc.v[0][v], b0 = xc.v[1][v], a1 = xc.v[2][v], b1 = xc.v[3][v];
+      const cplx<T> lxa = cxm >= 0 ? xma[v] : zero, lxb = cxm >= 0 ? xmb[v] : zero;
+      const cplx<T> rxa = cxp >= 0 ? xpa[v] : zero, rxb = cxp >= 0 ? xpb[v] : zero;
+      const cplx<T> yb0 = cym >= 0 ? yma0[v] : zero, yb1 = cym >= 0 ? yma1[v] : zero;
+      const cplx<T> ya0 = cyp >= 0 ? ypa0[v] : zero, ya1 = cyp >= 0 ? ypa1[v] : zero;
+      // hopping part T of each component (before the alpha scaling)
+      cplx<T> T4[4];
+      {  // site 0: x- = (lxa, lxb), x+ = (a1, b1)
+        const cplx<T> Sb = cadd(cadd(lxb, b1), cadd(zm.v[1][v], zp.v[1][v]));
+        const cplx<T> Da = csub(zm.v[0][v], zp.v[0][v]);  // a_z- - a_z+
+        T4[0] = {fma(half, Sb.re, yb0.re) - half * Da.im, fma(half, Sb.im, yb0.im) + half * Da.re};
+        const cplx<T> Sa = cadd(cadd(lxa, a1), cadd(zm.v[0][v], zp.v[0][v]));
+        const cplx<T> Db = csub(zp.v[1][v], zm.v[1][v]);  // b_z+ - b_z-
+        T4[1] = {fma(half, Sa.re, ya0.re) - half * Db.im, fma(half, Sa.im, ya0.im) + half * Db.re};
+      }
+      {  // site 1: x- = (a0, b0), x+ = (rxa, rxb)
+        const cplx<T> Sb = cadd(cadd(b0, rxb), cadd(zm.v[3][v], zp.v[3][v]));
+        const cplx<T> Da = csub(zm.v[2][v], zp.v[2][v]);
+        T4[2] = {fma(half, Sb.re, yb1.re) - half * Da.im, fma(half, Sb.im, yb1.im) + half * Da.re};
+        const cplx<T> Sa = cadd(cadd(a0, rxa), cadd(zm.v[2][v], zp.v[2][v]));
+        const cplx<T> Db = csub(zp.v[3][v], zm.v[3][v]);
+        T4[3] = {fma(half, Sa.re, ya1.re) - half * Db.im, fma(half, Sa.im, ya1.im) + half * Db.re};
+      }
+      // y_new = alpha (V - beta) x - alpha c0 sigma_x x + alpha T + gamma y_in
+      const T e0 = fma(cf.alpha[v], V0, -cf.ab[v]), e1 = fma(cf.alpha[v], V1, -cf.ab[v]);
+      const T ac0 = cf.am[v];  // alpha c0
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const T dd = o < 2 ? e0 : e1;
+        const cplx<T> partner = xc.v[o ^ 1][v];  // sigma_x: a <-> b of the same site
+        T re = fma(cf.alpha[v], T4[o].re, fma(dd, xc.v[o][v].re, -ac0 * partner.re));
+        T im = fma(cf.alpha[v], T4[o].im, fma(dd, xc.v[o][v].im, -ac0 * partner.im));
+        if (p.yin != nullptr) {
+          re = fma(cf.gamma[v], yi.v[o][v].re, re);
+          im = fma(cf.gamma[v], yi.v[o][v].im, im);
+        }
+        yn.v[o][v] = {re, im};
+      }
+    }
+    const int64_t sites[4] = {2 * c, 2 * c, 2 * c + 1, 2 * c + 1};
+    epilogue<T, VPT, FEAT>(p, c, rc, xc, yn, dacc, sites);
+  }
+  if constexpr (has_dots(FEAT)) {
+    dacc.flush();
+    reduce_dots<VPT>(p, dacc.d);
+  }
+}
+
 }  // namespace pvsc

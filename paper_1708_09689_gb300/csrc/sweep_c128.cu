@@ -18,6 +18,7 @@ static void* kernel_c128() {
     return reinterpret_cast<void*>(&ti_sweep<double, 1, FEAT, kAsyncDepth, 6>);
   else if constexpr (MODEL == kModelTIAsyncDeep)
     return reinterpret_cast<void*>(&ti_sweep<double, 1, FEAT, kAsyncDeepDepth, 2>);
+  else if constexpr (MODEL == kModelWSM) return reinterpret_cast<void*>(&wsm_sweep<double, 1, FEAT>);
   else return reinterpret_cast<void*>(&gr_sweep<double, 1, FEAT>);
 }
 
@@ -40,6 +41,7 @@ static void* pick(int model, int feat) {
     case kModelTIFlat: return pick_c128<kModelTIFlat>(feat);
     case kModelTIAsync: return pick_c128<kModelTIAsync>(feat);
     case kModelTIAsyncDeep: return pick_c128<kModelTIAsyncDeep>(feat);
+    case kModelWSM: return pick_c128<kModelWSM>(feat);
     default: return pick_c128<2>(feat);
   }
 }

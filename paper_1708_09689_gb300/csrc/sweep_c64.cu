@@ -16,6 +16,7 @@ static void* kernel_c64() {
     return reinterpret_cast<void*>(&ti_sweep<float, VPT, FEAT, kAsyncDepth, 6>);
   else if constexpr (MODEL == kModelTIAsyncDeep)
     return reinterpret_cast<void*>(&ti_sweep<float, VPT, FEAT, kAsyncDeepDepth, 2>);
+  else if constexpr (MODEL == kModelWSM) return reinterpret_cast<void*>(&wsm_sweep<float, VPT, FEAT>);
   else return reinterpret_cast<void*>(&gr_sweep<float, VPT, FEAT>);
 }
 
@@ -38,6 +39,7 @@ static void* pick(int model, int vpt, int feat) {
     case kModelTIAsync: return vpt == 1 ? pick_c64<kModelTIAsync, 1>(feat) : pick_c64<kModelTIAsync, 2>(feat);
     case kModelTIAsyncDeep:
       return vpt == 1 ? pick_c64<kModelTIAsyncDeep, 1>(feat) : pick_c64<kModelTIAsyncDeep, 2>(feat);
+    case kModelWSM: return vpt == 1 ? pick_c64<kModelWSM, 1>(feat) : pick_c64<kModelWSM, 2>(feat);
     default: return vpt == 1 ? pick_c64<2, 1>(feat) : pick_c64<2, 2>(feat);
   }
 }
