@@ -75,11 +75,12 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default launch shape instead of the autotuned one")
     ap.add_argument("--workload", default="ti_slab",
-                    choices=["ti_slab", "ti_cube", "graphene_qd", "batched", "adjoint", "ti_akE", "chebfd"],
+                    choices=["ti_slab", "ti_cube", "graphene_qd", "batched", "adjoint", "ti_akE", "chebfd",
+                             "wsm_kpm"],
                     help="ti_slab (default): the benchmark line; the others measure the remaining "
                          "workloads (16^3 cube KPM, graphene QD-array propagation, batched KPM over "
                          "64 lattices, adjoint gradient, A(k,E) of a clean TI, ChebFD interior "
-                         "eigenpairs) and print one JSON line each")
+                         "eigenpairs, Weyl-semimetal KPM) and print one JSON line each")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="profiling case: one KPM call of this many complex64 sweeps (stencil, "
                          "recurrence, dots) on the lattice (ti_slab), or this many complex64 "
@@ -436,6 +437,33 @@ def run_workload(args, pv, dev, rank, world):
                                            "ti_sweep<float,2,*> series sweeps (R = 64; accumulator on "
                                            "every other sweep), solver average"),
                      "clocks": clk, "gpu_launches": None})
+    elif args.workload == "wsm_kpm":
+        # KPM DOS of the Weyl semimetal on the dispersion figure's 256 x 32 x 32 cuboid (periodic
+        # x, y; open z), box disorder W = 1, 16 random-phase vectors, 2048 moments, complex64
+        dims, R, M = (256, 32, 32), 16, 2048
+        lat = pv.Lattice.wsm(dims, (1, 1, 0), disorder=(1.0, 11))
+        emin, emax, a, b = lat.spectral_bounds()
+        if not args.no_autotune:
+            lat.autotune(R, pv.C64)
+        r0 = pv.random_vectors(lat, R, pv.C64, 13)
+        work = pv.work_buffer(lat.work_bytes(pv.OP_KPM, R, pv.C64, M), dev)
+        mu = torch.empty((R, M), dtype=torch.float64, device=dev)
+        run = lambda: pv.kpm_moments(lat, M, a, b, r0=r0, work=work, mu=mu)
+        for _ in range(args.warmup):
+            run()
+        clocks.start()
+        ms = max_over_ranks(_timed(run, args.steps, stream), dev)
+        clk = clocks.stop()
+        lups = lat.n_sites * R * (M // 2)
+        E0 = torch.tensor([0.0], dtype=torch.float64, device=dev)
+        line.update({"workload": "wsm_kpm", "value": round(world * lups / (ms * 1e-3) / 1e9, 3),
+                     "ms_per_step": round(ms, 3), "steps": args.steps, "dtype": "c64",
+                     "config": {"workload": "Weyl semimetal KPM: 256x32x32 sites (PBC x,y; open z), k0=pi/2, "
+                                            "W=1, 16 random-phase vectors, 2048 moments"},
+                     "dos_at_E0_per_site": float(pv.dos(lat, mu, E0, a, b)[0].item()) / lat.n_sites,
+                     "roofline": _hbm_roof(48.0 + 4.0 / R, lups, ms,
+                                           "wsm_sweep<float,2,F_DOTS> (two-site cells)"),
+                     "clocks": clk, "gpu_launches": args.steps * (M // 2)})
     elif args.workload == "batched":
         specs = W.batched_lattices()
         if args.sweeps_only:  # profiling case: the first --batched-count lattices, untimed

@@ -316,19 +316,20 @@ int pvsc_kpm_moments_batched(const pvsc_lattice* const* lats, int n, int R, int 
  * PVSC_KERNEL_NONE (g_k = 1), PVSC_KERNEL_JACKSON (g_k = [(M-k+1) cos(q k)
  * + sin(q k) cot q]/(M+1), q = pi/(M+1)) or PVSC_KERNEL_LORENTZ (g_k =
  * sinh(lambda (1 - k/M))/sinh(lambda), lambda > 0).  DOS: random-phase
- * moments, scale = D/R (integrates to D = 4 n_sites); A(k, E): the moments of
- * the four states psi(k, nu) of pvsc_bloch_vectors, scale = 1 (integrates to 4).
+ * moments, scale = D/R (integrates to D); A(k, E): the moments of the O states
+ * psi(k, nu) of pvsc_bloch_vectors, scale = 1 (integrates to O).
  */
 int pvsc_kpm_density(int R, int M, const double* mu, int kernel, double lambda, double a, double b,
                      double scale, int NE, const double* E, double* rho, void* stream);
 
 /*
- * The states psi(k, nu) of Eq. ak on a TI lattice, for nk in {1, 2, 4, 8, 16}
- * k-points k[3 q .. 3 q + 2] (HOST array of 3 nk doubles, components along x,
- * y, z in radians per lattice spacing): vector r = 4 q + nu of the block (R =
- * 4 nk) is exp(i k_q . r_n)/sqrt(n_sites) on orbital nu of every site n
- * (r_n its integer coordinates) and zero on the other orbitals.  out: device
- * block (D x R) in precision prec.  Phases are evaluated in fp64.
+ * The states psi(k, nu) of Eq. ak on a cubic lattice with O orbitals per site
+ * (TI: O = 4, Weyl semimetal: O = 2), for nk k-points k[3 q .. 3 q + 2]
+ * (HOST array of 3 nk doubles, components along x, y, z in radians per
+ * lattice spacing; O nk a power of two <= 64, nk <= 16): vector r = O q + nu
+ * of the block (R = O nk) is exp(i k_q . r_n)/sqrt(n_sites) on orbital nu of
+ * every site n (r_n its integer coordinates) and zero on the other orbitals.
+ * out: device block (D x R) in precision prec.  Phases are evaluated in fp64.
  */
 int pvsc_bloch_vectors(const pvsc_lattice* lat, int nk, const double* k, int prec, void* out,
                        void* stream);

@@ -489,17 +489,18 @@ def kpm_density(mu, E, a, b, g, scale=1.0) -> np.ndarray:
     return np.where(inside, rho, 0.0)
 
 
-def bloch_vectors(dims, k) -> np.ndarray:
-    """The states psi(k, nu), nu = 0..3, of Eq. ak on a TI lattice: the plane
-    wave exp(i k.r_n)/sqrt(N) on orbital nu of every site n (r_n = the site's
-    integer coordinates), as a (4 N, 4) block in the library's layout."""
+def bloch_vectors(dims, k, O=4) -> np.ndarray:
+    """The states psi(k, nu), nu = 0..O-1, of Eq. ak on a cubic lattice with O
+    orbitals per site (TI 4, Weyl semimetal 2): the plane wave
+    exp(i k.r_n)/sqrt(N) on orbital nu of every site n (r_n = the site's integer
+    coordinates), as an (O N, O) block in the library's layout."""
     coords = _all_coords(dims).astype(np.float64)
     N = coords.shape[0]
     kv = np.asarray(k, dtype=np.float64)[: coords.shape[1]]
     phase = np.exp(1j * (coords @ kv)) / math.sqrt(N)
-    out = np.zeros((4 * N, 4), dtype=np.complex128)
-    for nu in range(4):
-        out[nu::4, nu] = phase
+    out = np.zeros((O * N, O), dtype=np.complex128)
+    for nu in range(O):
+        out[nu::O, nu] = phase
     return out
 
 

@@ -438,10 +438,11 @@ def dos(lat: Lattice, mu: torch.Tensor, E, a, b, kernel: int = KERNEL_JACKSON, l
 
 
 def bloch_vectors(lat: Lattice, ks, prec: int = C128, stream=None) -> torch.Tensor:
-    """The states psi(k, nu) of Eq. ak for up to 16 k-points: a (D, 4 nk) block, vector 4 q + nu."""
+    """The states psi(k, nu) of Eq. ak for up to 16 k-points: a (D, O nk) block, vector O q + nu
+    (O = orbitals per site: TI 4, Weyl semimetal 2)."""
     ks = [tuple(float(c) for c in k) + (0.0,) * (3 - len(k)) for k in ks]
     nk = len(ks)
-    out = torch.empty((lat.D, 4 * nk), dtype=torch.complex128 if prec == C128 else torch.complex64,
+    out = torch.empty((lat.D, lat.orbitals * nk), dtype=torch.complex128 if prec == C128 else torch.complex64,
                       device="cuda")
     flat = (ctypes.c_double * (3 * nk))(*[c for k in ks for c in k])
     _check(_lib.pvsc_bloch_vectors(lat.handle, nk, flat, prec, _ptr(out), _stream(stream)))
@@ -450,12 +451,13 @@ def bloch_vectors(lat: Lattice, ks, prec: int = C128, stream=None) -> torch.Tens
 
 def spectral_function(lat: Lattice, ks, M: int, a, b, E, prec: int = C64,
                       kernel: int = KERNEL_JACKSON, lam: float = 4.0, work=None) -> torch.Tensor:
-    """A(k, E) of Eq. ak for up to 16 k-points: KPM moments of the four states psi(k, nu) of each
-    k-point (one call, R = 4 nk), summed per k-point; returns (nk, NE) float64."""
+    """A(k, E) of Eq. ak for up to 16 k-points: KPM moments of the O states psi(k, nu) of each
+    k-point (one call, R = O nk), summed per k-point; returns (nk, NE) float64."""
     psi = bloch_vectors(lat, ks, prec)
     mu = kpm_moments(lat, M, a, b, r0=psi, work=work)
     E = torch.as_tensor(E, dtype=torch.float64, device="cuda")
-    return torch.stack([kpm_density(mu[4 * q:4 * q + 4], E, a, b, kernel, lam) for q in range(len(ks))])
+    O = lat.orbitals
+    return torch.stack([kpm_density(mu[O * q:O * q + O], E, a, b, kernel, lam) for q in range(len(ks))])
 
 
 class ChebFDParams(ctypes.Structure):

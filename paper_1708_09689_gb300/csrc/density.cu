@@ -62,26 +62,27 @@ __global__ void __launch_bounds__(256) kpm_density_kernel(int R, int M, const do
   if (j < NE) rho[j] = inside ? scale * sum / (M_PI * a * sqrt(1.0 - x * x)) : 0.0;
 }
 
-// psi(k_q, nu) for nk k-points: vector r = 4 q + nu holds exp(i k_q . r_n)/sqrt(N)
-// on orbital nu of every site n, zero elsewhere.  Phases in fp64 (k.r reaches
+// psi(k_q, nu) for nk k-points on a lattice of O orbitals per site (TI 4,
+// Weyl semimetal 2): vector r = O q + nu holds exp(i k_q . r_n)/sqrt(N) on
+// orbital nu of every site n, zero elsewhere.  Phases in fp64 (k.r reaches
 // thousands of radians), rounded to the storage type.
 struct KPoints {
   double k[16][3];
 };
 
 template <typename T>
-__global__ void bloch_kernel(const Geometry g, int R, const KPoints kp, T* out) {
-  const int64_t n = 4 * g.n_sites * (int64_t)R;  // complex elements
+__global__ void bloch_kernel(const Geometry g, int O, int R, const KPoints kp, T* out) {
+  const int64_t n = O * g.n_sites * (int64_t)R;  // complex elements
   const double inv = 1.0 / sqrt((double)g.n_sites);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = udiv64(e, R);  // site * 4 + orbital
+    const int64_t i = udiv64(e, R);  // site * O + orbital
     const int r = (int)(e - i * R);
-    const int64_t s = i >> 2;
-    const int o = (int)(i & 3);
+    const int64_t s = i / O;
+    const int o = (int)(i - s * O);
     double re = 0.0, im = 0.0;
-    if ((r & 3) == o) {
-      const int q = r >> 2;
+    if (r % O == o) {
+      const int q = r / O;
       const int64_t yz = udiv64(s, g.L[0]);
       const int64_t x = s - yz * g.L[0];
       const int64_t z = udiv64(yz, g.L[1]);
@@ -107,14 +108,15 @@ static int launch_kpm_density(int R, int M, const double* mu, int kernel, double
   return PVSC_OK;
 }
 
-static int launch_bloch(const Geometry& g, int R, int prec, const KPoints& kp, void* out, cudaStream_t st) {
-  const int64_t n = 4 * g.n_sites * (int64_t)R;
+static int launch_bloch(const Geometry& g, int O, int R, int prec, const KPoints& kp, void* out,
+                        cudaStream_t st) {
+  const int64_t n = O * g.n_sites * (int64_t)R;
   int64_t blocks = (n + 255) / 256;
   if (blocks > 65535) blocks = 65535;
   if (prec == PVSC_C128)
-    bloch_kernel<double><<<(int)blocks, 256, 0, st>>>(g, R, kp, static_cast<double*>(out));
+    bloch_kernel<double><<<(int)blocks, 256, 0, st>>>(g, O, R, kp, static_cast<double*>(out));
   else
-    bloch_kernel<float><<<(int)blocks, 256, 0, st>>>(g, R, kp, static_cast<float*>(out));
+    bloch_kernel<float><<<(int)blocks, 256, 0, st>>>(g, O, R, kp, static_cast<float*>(out));
   PVSC_CUDA_TRY(cudaGetLastError());
   return PVSC_OK;
 }
@@ -145,9 +147,11 @@ int pvsc_kpm_density(int R, int M, const double* mu, int kernel, double lambda, 
 int pvsc_bloch_vectors(const pvsc_lattice* lat, int nk, const double* k, int prec, void* out,
                        void* stream) {
   if (int rc = check_lattice(lat)) return rc;
-  if (lat->g.model != PVSC_TI) return set_error(PVSC_ERR_UNSUPPORTED, "Bloch states are built for the TI lattice");
-  if (!(nk == 1 || nk == 2 || nk == 4 || nk == 8 || nk == 16))
-    return set_error(PVSC_ERR_ARG, "nk = %d: must be 1, 2, 4, 8 or 16 (R = 4 nk)", nk);
+  if (lat->g.model == PVSC_GRAPHENE)
+    return set_error(PVSC_ERR_UNSUPPORTED, "Bloch states are built for the cubic lattices (TI, Weyl semimetal)");
+  const int O = orbitals_of(lat->g.model);
+  if (!valid_R(O * nk) || nk > 16)
+    return set_error(PVSC_ERR_ARG, "nk = %d: %d nk must be a block width 1 .. 64", nk, O);
   if (prec != PVSC_C128 && prec != PVSC_C64) return set_error(PVSC_ERR_ARG, "unknown precision %d", prec);
   if (!k) return set_error(PVSC_ERR_ARG, "k is NULL");
   for (int i = 0; i < 3 * nk; ++i)
@@ -156,7 +160,7 @@ int pvsc_bloch_vectors(const pvsc_lattice* lat, int nk, const double* k, int pre
   KPoints kp{};  // passed by value in the kernel parameters
   for (int q = 0; q < nk; ++q)
     for (int d = 0; d < 3; ++d) kp.k[q][d] = k[3 * q + d];
-  return launch_bloch(lat->g, 4 * nk, prec, kp, out, static_cast<cudaStream_t>(stream));
+  return launch_bloch(lat->g, O, O * nk, prec, kp, out, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -111,3 +111,21 @@ def test_wsm_on_the_fly_potential_and_unsupported_paths():
         pv.kpm_moments(lat_s, 8, a, b, R=1, prec=pv.Q64)
     with pytest.raises(pv.PvscError):
         pv.kpm_moments_batched([lat_s], 8, [a], [b], R=1, prec=pv.C64, seeds=[1])
+
+
+def test_wsm_bloch_states_and_spectral_function_on_gpu():
+    dims = (8, 4, 4)
+    lat = pv.Lattice.wsm(dims, (1, 1, 1))
+    ks = [(math.pi / 2, 0.0, 0.0), (math.pi / 4, math.pi / 2, math.pi)]
+    v = pv.bloch_vectors(lat, ks).cpu().numpy()
+    ref = np.concatenate([O.bloch_vectors(dims, k, O=2) for k in ks], axis=1)
+    assert v.shape == (256, 4) and np.max(np.abs(v - ref)) < 1e-15
+    _, _, a, b = lat.spectral_bounds()
+    E = np.linspace(b - a + 1e-9, b + a - 1e-9, 40001)
+    A = pv.spectral_function(lat, ks, 512, a, b, E, prec=pv.C128).cpu().numpy()
+    H = O.wsm_hamiltonian(dims, (1, 1, 1), np.zeros(128))
+    for q, k in enumerate(ks):
+        mu = O.kpm_moments(H, O.bloch_vectors(dims, k, O=2), 512, a, b).real
+        refA = O.kpm_density(mu, E, a, b, O.jackson_kernel(512))
+        assert np.max(np.abs(A[q] - refA)) < 1e-9 * np.max(refA)
+        assert abs(np.trapezoid(A[q], E) - 2.0) < 1e-3

@@ -584,3 +584,23 @@ def test_wsm_weyl_nodes_and_open_boundaries():
     rows = diff.row // 2
     z = rows // 32
     assert set(np.unique(z)) == {0, 3}  # only the bonds across the z boundary differ
+
+
+@pytest.mark.parametrize("k", [(math.pi / 2, 0.0, 0.0), (math.pi / 4, math.pi / 2, math.pi)])
+def test_wsm_spectral_function_peaks_at_the_closed_form_band(k):
+    # Eq. ak for the Weyl semimetal: the two states psi(k, nu) span the 2x2 Bloch block of
+    # Eq. band_h_wsm with eigenvalues +-|d(k)|, one each; at the Weyl node both sit at E = 0
+    dims = (8, 4, 4)
+    H = O.wsm_hamiltonian(dims, (1, 1, 1), np.zeros(128))
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    d = np.array([math.cos(k[0]) + math.cos(k[1]) + math.cos(k[2]) - 2.0 - math.cos(math.pi / 2),
+                  math.sin(k[1]), math.sin(k[2])])
+    e0 = float(np.linalg.norm(d))
+    mu = O.kpm_moments(H, O.bloch_vectors(dims, k, O=2), 512, a, b).real
+    E = np.linspace(b - a + 1e-9, b + a - 1e-9, 40001)
+    A = O.kpm_density(mu, E, a, b, O.jackson_kernel(512))
+    assert abs(np.trapezoid(A, E) - 2.0) < 1e-3
+    for e in ((0.0,) if e0 < 1e-12 else (e0, -e0)):
+        m = (E > e - 0.3) & (E < e + 0.3)
+        assert abs(E[m][np.argmax(A[m])] - e) < 2e-3
+        assert abs(np.trapezoid(A[m], E[m]) - (2.0 if e0 < 1e-12 else 1.0)) < 3e-3
