@@ -25,21 +25,37 @@
 namespace pvsc {
 
 using i64 = long long;
-using i128 = __int128;
 
 constexpr int kFxVal = 59;   // fraction bits of vector values
 constexpr int kFxCoef = 60;  // fraction bits of coefficients
 
-// round((c1 x1 + c2 x2) 2^-60): Q3.60 x Q4.59 -> Q4.59
-__device__ __forceinline__ i64 fx_mul2(i64 c1, i64 x1, i64 c2, i64 x2) {
-  const i128 P = (i128)c1 * x1 + (i128)c2 * x2 + ((i128)1 << (kFxCoef - 1));
-  return (i64)(P >> kFxCoef);
+// 128-bit two's-complement values as (hi, lo) pairs, built from the signed
+// 64 x 64 -> 128 product (mul.hi.s64 and the wrapping low product).
+struct W128 {
+  i64 hi;
+  unsigned long long lo;
+};
+
+__device__ __forceinline__ W128 wmul(i64 a, i64 b) {
+  return W128{__mul64hi(a, b), (unsigned long long)a * (unsigned long long)b};
 }
 
-__device__ __forceinline__ double i128_to_double(i128 v) {
-  const i64 hi = (i64)(v >> 64);
-  const unsigned long long lo = (unsigned long long)v;
-  return fma((double)hi, 0x1p64, (double)lo);
+__device__ __forceinline__ void wadd(W128& acc, const W128& v) {
+  const unsigned long long lo = acc.lo + v.lo;
+  acc.hi += v.hi + (lo < acc.lo ? 1 : 0);
+  acc.lo = lo;
+}
+
+// round((c1 x1 + c2 x2) 2^-60): Q3.60 x Q4.59 -> Q4.59 (round half up)
+__device__ __forceinline__ i64 fx_mul2(i64 c1, i64 x1, i64 c2, i64 x2) {
+  W128 P = wmul(c1, x1);
+  wadd(P, wmul(c2, x2));
+  wadd(P, W128{0, 1ull << (kFxCoef - 1)});
+  return (i64)(((unsigned long long)P.hi << (64 - kFxCoef)) | (P.lo >> kFxCoef));
+}
+
+__device__ __forceinline__ double w128_to_double(const W128& v) {
+  return fma((double)v.hi, 0x1p64, (double)v.lo);
 }
 
 // One KPM sweep on fixed-point vectors, z-marching as the floating-point
@@ -76,7 +92,7 @@ __global__ void __launch_bounds__(256) ti_sweep_fx(const __grid_constant__ Sweep
     const int64_t tid = bx * blockDim.x + threadIdx.x;
     if (tid >= ncolthr) continue;
     const int64_t z0 = bz * zs, z1 = min(z0 + (int64_t)zs, Lz);
-    i128 xx = 0, xy = 0;
+    W128 xx{0, 0}, xy{0, 0};
     ti_march<i64, 1, true, DEPTH, NBUF>(
         p.g, X, Yin, R, rc, tid >> cshift, z0, z1, ring,
         [&](int64_t s) { return __ldg(dfx + s); },
@@ -101,12 +117,14 @@ __global__ void __launch_bounds__(256) ti_sweep_fx(const __grid_constant__ Sweep
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
             const cplx<i64> a = xc.v[o][0], b = yn.v[o][0];
-            xx += (i128)a.re * a.re + (i128)a.im * a.im;
-            xy += (i128)b.re * a.re + (i128)b.im * a.im;
+            wadd(xx, wmul(a.re, a.re));
+            wadd(xx, wmul(a.im, a.im));
+            wadd(xy, wmul(b.re, a.re));
+            wadd(xy, wmul(b.im, a.im));
           }
         });
-    dd[0][0] += i128_to_double(xx) * vs;
-    dd[1][0] += i128_to_double(xy) * vs;
+    dd[0][0] += w128_to_double(xx) * vs;
+    dd[1][0] += w128_to_double(xy) * vs;
   }
   reduce_dots<1>(p, dd);
 }
