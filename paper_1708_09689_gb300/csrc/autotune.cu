@@ -107,7 +107,8 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
   std::vector<int> vpt_c = {1};
   if (prec == PVSC_C64 && R >= 2) vpt_c.push_back(2);
   std::vector<int> zslab_c = {0};
-  if (lat->g.model == PVSC_TI)
+  const bool march = lat->g.model == PVSC_TI || lat->g.model == PVSC_WSM;  // z-marching sweeps
+  if (march)
     for (int z : {4, 8, 16, 32, 64})
       if (z < lat->g.L[2]) zslab_c.push_back(z);
   const std::vector<int> bps_c = {0, 1, 2};
@@ -153,8 +154,8 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
       if (th % C != 0 || th < C) continue;
       for (int bps : bps_c)
         for (int zs : zslab_c) cands.push_back(pvsc_tuning{th, bps, zs, 0.f, vpt, 0, 0, 0});
+      if (march) cands.push_back(pvsc_tuning{th, 0, 0, 0.f, vpt, 0, 0, 1});  // flat variant
       if (lat->g.model == PVSC_TI) {
-        cands.push_back(pvsc_tuning{th, 0, 0, 0.f, vpt, 0, 0, 1});
         if (!(prec == PVSC_C64 && vpt == 1 && R > 1)) {
           for (int zs : {0, 16}) cands.push_back(pvsc_tuning{th, 0, zs, 0.f, vpt, 0, 0, 2});
           cands.push_back(pvsc_tuning{th, 0, 0, 0.f, vpt, 0, 0, 3});

@@ -162,8 +162,12 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
           // x is written by this kernel in other phases: coherent loads only (NC = false)
           ti_march<T, VPT, false, 0, 2>(L.g, X, Yin, R, rc, col, z0, z1, nullptr,
                                   [&](int64_t s) { return site_potential_t<T>(L.g, s); },
-                                  [&](T Vs, const Blk<T, VPT>& xc, const Blk<T, VPT>& S,
-                                      const Blk<T, VPT>& D, const Blk<T, VPT>* yi, Blk<T, VPT>& yn) {
+                                  [&](T Vs, const Blk<T, VPT>& xm, const Blk<T, VPT>& xc,
+                                      const Blk<T, VPT>& xp, const Blk<T, VPT>& ax, const Blk<T, VPT>& bx,
+                                      const Blk<T, VPT>& ay, const Blk<T, VPT>& by,
+                                      const Blk<T, VPT>* yi, Blk<T, VPT>& yn) {
+                                    Blk<T, VPT> S, D;
+                                    ti_axes(xm, xp, ax, bx, ay, by, S, D);
                                     ti_combine(cf, Vs, xc, S, D, yi, yn, L.g);
                                   },
                                   [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {

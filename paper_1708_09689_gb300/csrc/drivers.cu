@@ -123,9 +123,13 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
   // the prefetch ring moves 16-byte granules: not for complex64 with one vector of R > 1
   const bool async = lat->g.model == PVSC_TI && (sh.kernel == 2 || sh.kernel == 3) &&
                      !(prec == PVSC_C64 && vpt == 1 && p.R > 1);
+  // Weyl semimetal: the flat cell sweep (measured faster on the paper's 256 x 32 x 32
+  // cuboid) unless a tuning entry selects the z-marching one (kernel 0)
+  const bool wsm = lat->g.model == PVSC_WSM;
+  const bool wsm_flat = wsm && (lat->tuning.count({p.R, prec}) == 0 || sh.kernel == 1);
   const int model = flat ? kModelTIFlat
                     : async ? (sh.kernel == 2 ? kModelTIAsync : kModelTIAsyncDeep)
-                    : lat->g.model == PVSC_WSM ? kModelWSM
+                    : wsm ? (wsm_flat ? kModelWSM : kModelWSMMarch)
                             : lat->g.model;
   int rc = prec == PVSC_C128 ? occupancy_c128(model, feat, threads, &occ)
                              : occupancy_c64(model, vpt, feat, threads, &occ);
@@ -138,8 +142,9 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
   int64_t units;
   if (flat) {
     units = (lat->g.n_sites * p.C + threads - 1) / threads;
-  } else if (lat->g.model == PVSC_TI) {
-    const int64_t plane = lat->g.L[0] * lat->g.L[1], Lz = lat->g.L[2];
+  } else if (lat->g.model == PVSC_TI || (wsm && !wsm_flat)) {
+    // z-marching columns: TI sites, or Weyl cells (two sites along x)
+    const int64_t plane = (wsm ? lat->g.L[0] / 2 : lat->g.L[0]) * lat->g.L[1], Lz = lat->g.L[2];
     const int64_t nbx = (plane * p.C + threads - 1) / threads;
     int64_t zs = sh.zslab;
     if (zs <= 0) {

@@ -43,7 +43,8 @@ struct LaunchShape {
 constexpr int kModelTIFlat = 3;
 constexpr int kModelTIAsync = 4;      // ring of all six blocks of a plane, one plane ahead
 constexpr int kModelTIAsyncDeep = 5;  // ring of the two HBM streams, three planes ahead
-constexpr int kModelWSM = 8;         // Weyl semimetal cell sweep
+constexpr int kModelWSM = 8;         // Weyl semimetal flat cell sweep
+constexpr int kModelWSMMarch = 9;    // Weyl semimetal z-marching cell sweep
 constexpr int kAsyncDepth = 1;
 constexpr int kAsyncDeepDepth = 3;
 // ring: (depth + 1) slots x buffers x 4 granules of 16 bytes per thread

@@ -564,6 +564,16 @@ __device__ __forceinline__ void axis_y_add(const Blk<T, VPT>& a, const Blk<T, VP
   }
 }
 
+// S and D of all three axes from the six neighbour blocks (z-, z+, x-, x+, y-, y+).
+template <typename T, int VPT>
+__device__ __forceinline__ void ti_axes(const Blk<T, VPT>& zm, const Blk<T, VPT>& zp, const Blk<T, VPT>& xm,
+                                        const Blk<T, VPT>& xp, const Blk<T, VPT>& ym, const Blk<T, VPT>& yp,
+                                        Blk<T, VPT>& S, Blk<T, VPT>& D) {
+  axis_z_init(zm, zp, S, D);
+  axis_x_add(xm, xp, S, D);
+  axis_y_add(ym, yp, S, D);
+}
+
 // y += alpha (Delta_1 Gamma^5 + Delta_2 Gamma^15) x, the on-site Delta terms of
 // Eq. TB_H_topi.  Gamma^5 = sigma_z (x) s_x and Gamma^15 = [Gamma^1, Gamma^5]/2i =
 // sigma_z (x) s_y, so orbital 0 takes (D1 - i D2) x_1, orbital 1 (D1 + i D2) x_0,
@@ -709,12 +719,8 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
       if (cyp >= 0) load_at<T, VPT, NC>(Pyp + zoff, R, by); else zero_blk(by);
     }
     const auto sv = site(s);  // per-site data (potential), issued with the loads above
-    Blk<T, VPT> S, D;
-    axis_z_init(xm, xp, S, D);
-    axis_x_add(ax, bx, S, D);
-    axis_y_add(ay, by, S, D);
     Blk<T, VPT> yn;
-    combine(sv, xc, S, D, Yin != nullptr ? &yi : nullptr, yn);
+    combine(sv, xm, xc, xp, ax, bx, ay, by, Yin != nullptr ? &yi : nullptr, yn);
     emit(s, xc, yn);
     xm = xc;
     xc = xp;
@@ -746,8 +752,12 @@ __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p)
     const int64_t z0 = bz * zs, z1 = min(z0 + (int64_t)zs, Lz);
     ti_march<T, VPT, true, DEPTH, NBUF>(p.g, X, Yin, R, rc, tid >> cshift, z0, z1, ring,
                            [&](int64_t s) { return site_potential_t<T>(p.g, s); },
-                           [&](T Vs, const Blk<T, VPT>& xc, const Blk<T, VPT>& S,
-                               const Blk<T, VPT>& D, const Blk<T, VPT>* yi, Blk<T, VPT>& yn) {
+                           [&](T Vs, const Blk<T, VPT>& xm, const Blk<T, VPT>& xc,
+                               const Blk<T, VPT>& xp, const Blk<T, VPT>& ax, const Blk<T, VPT>& bx,
+                               const Blk<T, VPT>& ay, const Blk<T, VPT>& by, const Blk<T, VPT>* yi,
+                               Blk<T, VPT>& yn) {
+                             Blk<T, VPT> S, D;
+                             ti_axes(xm, xp, ax, bx, ay, by, S, D);
                              ti_combine(cf, Vs, xc, S, D, yi, yn, p.g);
                            },
                            [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
@@ -955,7 +965,7 @@ __global__ void __launch_bounds__(256) gr_sweep(const __grid_constant__ Sweep p)
   }
 }
 
-// ---------------------------------------------------------------- Weyl semimetal sweep
+// ---------------------------------------------------------------- Weyl semimetal sweeps
 // Eq. TB_H_wsm: two orbitals (a, b) per site, bonds n -> n + e_x with
 // sigma_x/2 and n -> n + e_j (j = y, z) with (sigma_x + i sigma_j)/2, each with
 // its Hermitian conjugate, on-site V_n - c0 sigma_x, c0 = 2 + cos k0 (kept in
@@ -966,6 +976,58 @@ __global__ void __launch_bounds__(256) gr_sweep(const __grid_constant__ Sweep p)
 // components (site 2X: a, b; site 2X+1: a, b) are the four consecutive block
 // components of the layout, so cell c = X + (Lx/2)(y + Ly z) is loaded and
 // stored like a 4-orbital block and shares the epilogue of the other sweeps.
+
+// y_new of one cell from the cell blocks around it (absent neighbours zero):
+// zm, zp the cells at z -+ 1, xm, xp at X -+ 1, ym, yp at y -+ 1; V0, V1 the
+// potentials of the two sites; y_new = alpha (H - beta) x + gamma y_in.
+template <typename T, int VPT>
+__device__ __forceinline__ void wsm_cell_update(const VecCoef<T, VPT>& cf, T V0, T V1,
+                                                const Blk<T, VPT>& zm, const Blk<T, VPT>& xc,
+                                                const Blk<T, VPT>& zp, const Blk<T, VPT>& xm,
+                                                const Blk<T, VPT>& xp, const Blk<T, VPT>& ym,
+                                                const Blk<T, VPT>& yp, const Blk<T, VPT>* yi,
+                                                Blk<T, VPT>& yn) {
+  const T half = T(0.5);
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    const cplx<T> a0 = xc.v[0][v], b0 = xc.v[1][v], a1 = xc.v[2][v], b1 = xc.v[3][v];
+    cplx<T> T4[4];  // hopping part of each component, before the alpha scaling
+    {  // site 0: x- is site 1 of cell X-1, x+ is site 1 of this cell; y- b, y+ a of site 0
+      const cplx<T> Sb = cadd(cadd(xm.v[3][v], b1), cadd(zm.v[1][v], zp.v[1][v]));
+      const cplx<T> Da = csub(zm.v[0][v], zp.v[0][v]);  // a_z- - a_z+
+      T4[0] = {fma(half, Sb.re, ym.v[1][v].re) - half * Da.im, fma(half, Sb.im, ym.v[1][v].im) + half * Da.re};
+      const cplx<T> Sa = cadd(cadd(xm.v[2][v], a1), cadd(zm.v[0][v], zp.v[0][v]));
+      const cplx<T> Db = csub(zp.v[1][v], zm.v[1][v]);  // b_z+ - b_z-
+      T4[1] = {fma(half, Sa.re, yp.v[0][v].re) - half * Db.im, fma(half, Sa.im, yp.v[0][v].im) + half * Db.re};
+    }
+    {  // site 1: x- is site 0 of this cell, x+ is site 0 of cell X+1
+      const cplx<T> Sb = cadd(cadd(b0, xp.v[1][v]), cadd(zm.v[3][v], zp.v[3][v]));
+      const cplx<T> Da = csub(zm.v[2][v], zp.v[2][v]);
+      T4[2] = {fma(half, Sb.re, ym.v[3][v].re) - half * Da.im, fma(half, Sb.im, ym.v[3][v].im) + half * Da.re};
+      const cplx<T> Sa = cadd(cadd(a0, xp.v[0][v]), cadd(zm.v[2][v], zp.v[2][v]));
+      const cplx<T> Db = csub(zp.v[3][v], zm.v[3][v]);
+      T4[3] = {fma(half, Sa.re, yp.v[2][v].re) - half * Db.im, fma(half, Sa.im, yp.v[2][v].im) + half * Db.re};
+    }
+    const T e0 = fma(cf.alpha[v], V0, -cf.ab[v]), e1 = fma(cf.alpha[v], V1, -cf.ab[v]);
+    const T ac0 = cf.am[v];  // alpha c0
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const T dd = o < 2 ? e0 : e1;
+      const cplx<T> partner = xc.v[o ^ 1][v];  // sigma_x: a <-> b of the same site
+      T re = fma(cf.alpha[v], T4[o].re, fma(dd, xc.v[o][v].re, -ac0 * partner.re));
+      T im = fma(cf.alpha[v], T4[o].im, fma(dd, xc.v[o][v].im, -ac0 * partner.im));
+      if (yi != nullptr) {
+        re = fma(cf.gamma[v], yi->v[o][v].re, re);
+        im = fma(cf.gamma[v], yi->v[o][v].im, im);
+      }
+      yn.v[o][v] = {re, im};
+    }
+  }
+}
+
+// Flat cell sweep: one cell per thread and pass; of the in-plane neighbour
+// cells only the components the update reads are loaded (x-: site 1, x+: site
+// 0, y-: the b components, y+: the a components).
 template <typename T, int VPT, int FEAT>
 __global__ void __launch_bounds__(256) wsm_sweep(const __grid_constant__ Sweep p) {
   const int64_t NX = p.g.L[0] / 2, Ly = p.g.L[1], Lz = p.g.L[2];
@@ -984,7 +1046,6 @@ __global__ void __launch_bounds__(256) wsm_sweep(const __grid_constant__ Sweep p
   int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> cshift;
   int64_t z = c / plane, xy = c - z * plane;
   int64_t y = xy / NX, x = xy - y * NX;
-  const T half = T(0.5);
   for (; c < ncell; c += cstride, x += sxs, y += sys, z += szs) {
     if (x >= NX) {
       x -= NX;
@@ -994,82 +1055,75 @@ __global__ void __launch_bounds__(256) wsm_sweep(const __grid_constant__ Sweep p
       y -= Ly;
       ++z;
     }
-    const int64_t cxm = nbr_minus(c, x, NX, p.g.per[0], 1), cxp = nbr_plus(c, x, NX, p.g.per[0], 1);
-    const int64_t cym = nbr_minus(c, y, Ly, p.g.per[1], NX), cyp = nbr_plus(c, y, Ly, p.g.per[1], NX);
-    const int64_t czm = nbr_minus(c, z, Lz, p.g.per[2], plane), czp = nbr_plus(c, z, Lz, p.g.per[2], plane);
-    Blk<T, VPT> xc, yi, zm, zp;
+    const int64_t nb[6] = {nbr_minus(c, z, Lz, p.g.per[2], plane), nbr_plus(c, z, Lz, p.g.per[2], plane),
+                           nbr_minus(c, x, NX, p.g.per[0], 1),     nbr_plus(c, x, NX, p.g.per[0], 1),
+                           nbr_minus(c, y, Ly, p.g.per[1], NX),    nbr_plus(c, y, Ly, p.g.per[1], NX)};
+    Blk<T, VPT> xc, yi, n[6];
     load_blk<T, VPT, true>(X, c, R, rc, xc);
     if (p.yin != nullptr) load_blk<T, VPT, false>(static_cast<const T*>(p.yin), c, R, rc, yi);
-    if (czm >= 0) load_blk<T, VPT, true>(X, czm, R, rc, zm); else zero_blk(zm);
-    if (czp >= 0) load_blk<T, VPT, true>(X, czp, R, rc, zp); else zero_blk(zp);
-    // x neighbours of the pair: site 2X-1 is component 2, 3 of cell X-1, site
-    // 2X+2 component 0, 1 of cell X+1 (with one site per cell row wrapping
-    // onto itself when NX = 1)
-    cplx<T> xma[VPT], xmb[VPT], xpa[VPT], xpb[VPT], yma0[VPT], yma1[VPT], ypa0[VPT], ypa1[VPT];
-    if (cxm >= 0) {
-      load_one<T, VPT>(X, cxm, 2, R, rc, xma);
-      load_one<T, VPT>(X, cxm, 3, R, rc, xmb);
-    }
-    if (cxp >= 0) {
-      load_one<T, VPT>(X, cxp, 0, R, rc, xpa);
-      load_one<T, VPT>(X, cxp, 1, R, rc, xpb);
-    }
-    // y-: the b of both sites of cell y-1; y+: the a of both sites of cell y+1
-    if (cym >= 0) {
-      load_one<T, VPT>(X, cym, 1, R, rc, yma0);
-      load_one<T, VPT>(X, cym, 3, R, rc, yma1);
-    }
-    if (cyp >= 0) {
-      load_one<T, VPT>(X, cyp, 0, R, rc, ypa0);
-      load_one<T, VPT>(X, cyp, 2, R, rc, ypa1);
-    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) zero_blk(n[k]);
+    if (nb[0] >= 0) load_blk<T, VPT, true>(X, nb[0], R, rc, n[0]);
+    if (nb[1] >= 0) load_blk<T, VPT, true>(X, nb[1], R, rc, n[1]);
+    const int want[4][2] = {{2, 3}, {0, 1}, {1, 3}, {0, 2}};  // x-, x+, y-, y+
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (nb[2 + k] >= 0) {
+        load_one<T, VPT>(X, nb[2 + k], want[k][0], R, rc, n[2 + k].v[want[k][0]]);
+        load_one<T, VPT>(X, nb[2 + k], want[k][1], R, rc, n[2 + k].v[want[k][1]]);
+      }
     const T V0 = site_potential_t<T>(p.g, 2 * c), V1 = site_potential_t<T>(p.g, 2 * c + 1);
     Blk<T, VPT> yn;
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      const cplx<T> zero{T(0), T(0)};
-      // in-pair x bonds: site 0's x+ neighbour is site 1, site 1's x- neighbour is site 0
-      const cplx<T> a0 = xc.v[0][v], b0 = xc.v[1][v], a1 = xc.v[2][v], b1 = xc.v[3][v];
-      const cplx<T> lxa = cxm >= 0 ? xma[v] : zero, lxb = cxm >= 0 ? xmb[v] : zero;
-      const cplx<T> rxa = cxp >= 0 ? xpa[v] : zero, rxb = cxp >= 0 ? xpb[v] : zero;
-      const cplx<T> yb0 = cym >= 0 ? yma0[v] : zero, yb1 = cym >= 0 ? yma1[v] : zero;
-      const cplx<T> ya0 = cyp >= 0 ? ypa0[v] : zero, ya1 = cyp >= 0 ? ypa1[v] : zero;
-      // hopping part T of each component (before the alpha scaling)
-      cplx<T> T4[4];
-      {  // site 0: x- = (lxa, lxb), x+ = (a1, b1)
-        const cplx<T> Sb = cadd(cadd(lxb, b1), cadd(zm.v[1][v], zp.v[1][v]));
-        const cplx<T> Da = csub(zm.v[0][v], zp.v[0][v]);  // a_z- - a_z+
-        T4[0] = {fma(half, Sb.re, yb0.re) - half * Da.im, fma(half, Sb.im, yb0.im) + half * Da.re};
-        const cplx<T> Sa = cadd(cadd(lxa, a1), cadd(zm.v[0][v], zp.v[0][v]));
-        const cplx<T> Db = csub(zp.v[1][v], zm.v[1][v]);  // b_z+ - b_z-
-        T4[1] = {fma(half, Sa.re, ya0.re) - half * Db.im, fma(half, Sa.im, ya0.im) + half * Db.re};
-      }
-      {  // site 1: x- = (a0, b0), x+ = (rxa, rxb)
-        const cplx<T> Sb = cadd(cadd(b0, rxb), cadd(zm.v[3][v], zp.v[3][v]));
-        const cplx<T> Da = csub(zm.v[2][v], zp.v[2][v]);
-        T4[2] = {fma(half, Sb.re, yb1.re) - half * Da.im, fma(half, Sb.im, yb1.im) + half * Da.re};
-        const cplx<T> Sa = cadd(cadd(a0, rxa), cadd(zm.v[2][v], zp.v[2][v]));
-        const cplx<T> Db = csub(zp.v[3][v], zm.v[3][v]);
-        T4[3] = {fma(half, Sa.re, ya1.re) - half * Db.im, fma(half, Sa.im, ya1.im) + half * Db.re};
-      }
-      // y_new = alpha (V - beta) x - alpha c0 sigma_x x + alpha T + gamma y_in
-      const T e0 = fma(cf.alpha[v], V0, -cf.ab[v]), e1 = fma(cf.alpha[v], V1, -cf.ab[v]);
-      const T ac0 = cf.am[v];  // alpha c0
-#pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        const T dd = o < 2 ? e0 : e1;
-        const cplx<T> partner = xc.v[o ^ 1][v];  // sigma_x: a <-> b of the same site
-        T re = fma(cf.alpha[v], T4[o].re, fma(dd, xc.v[o][v].re, -ac0 * partner.re));
-        T im = fma(cf.alpha[v], T4[o].im, fma(dd, xc.v[o][v].im, -ac0 * partner.im));
-        if (p.yin != nullptr) {
-          re = fma(cf.gamma[v], yi.v[o][v].re, re);
-          im = fma(cf.gamma[v], yi.v[o][v].im, im);
-        }
-        yn.v[o][v] = {re, im};
-      }
-    }
+    wsm_cell_update(cf, V0, V1, n[0], xc, n[1], n[2], n[3], n[4], n[5], p.yin != nullptr ? &yi : nullptr,
+                    yn);
     const int64_t sites[4] = {2 * c, 2 * c, 2 * c + 1, 2 * c + 1};
     epilogue<T, VPT, FEAT>(p, c, rc, xc, yn, dacc, sites);
+  }
+  if constexpr (has_dots(FEAT)) {
+    dacc.flush();
+    reduce_dots<VPT>(p, dacc.d);
+  }
+}
+
+// z-marching cell sweep: the cells form columns along z like the TI sites, so
+// ti_march runs on the cell geometry (Lx/2 cells along x) with the Weyl update.
+template <typename T, int VPT, int FEAT>
+__global__ void __launch_bounds__(256) wsm_march_sweep(const __grid_constant__ Sweep p) {
+  Geometry gc = p.g;
+  gc.L[0] = p.g.L[0] / 2;
+  const int64_t plane = gc.L[0] * gc.L[1], Lz = gc.L[2];
+  const int R = p.R, C = p.C;
+  const int rc = threadIdx.x % C;
+  const int cshift = __ffs(C) - 1;
+  const VecCoef<T, VPT> cf = load_coef<T, VPT>(p, rc);
+  const T* __restrict__ X = static_cast<const T*>(p.x);
+  const T* __restrict__ Yin = static_cast<const T*>(p.yin);
+  DotAcc<T, VPT> dacc;
+  dacc.init();
+  const int64_t ncolthr = plane * C;
+  const int64_t nbx = (ncolthr + blockDim.x - 1) / blockDim.x;
+  const int zs = p.zslab;
+  const int64_t nunits = nbx * ((Lz + zs - 1) / zs);
+  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int64_t bz = udiv64(u, nbx), bx = u - bz * nbx;
+    const int64_t tid = bx * blockDim.x + threadIdx.x;
+    if (tid >= ncolthr) continue;
+    const int64_t z0 = bz * zs, z1 = min(z0 + (int64_t)zs, Lz);
+    ti_march<T, VPT, true, 0, 2>(
+        gc, X, Yin, R, rc, tid >> cshift, z0, z1, nullptr,
+        [&](int64_t c) {
+          return cplx<T>{site_potential_t<T>(p.g, 2 * c), site_potential_t<T>(p.g, 2 * c + 1)};
+        },
+        [&](cplx<T> V, const Blk<T, VPT>& zm, const Blk<T, VPT>& xc, const Blk<T, VPT>& zp,
+            const Blk<T, VPT>& xm, const Blk<T, VPT>& xp, const Blk<T, VPT>& ym, const Blk<T, VPT>& yp,
+            const Blk<T, VPT>* yi, Blk<T, VPT>& yn) {
+          wsm_cell_update(cf, V.re, V.im, zm, xc, zp, xm, xp, ym, yp, yi, yn);
+        },
+        [&](int64_t c, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
+          const int64_t sites[4] = {2 * c, 2 * c, 2 * c + 1, 2 * c + 1};
+          epilogue<T, VPT, FEAT>(p, c, rc, xc, yn, dacc, sites);
+        });
+    if constexpr (has_dots(FEAT)) dacc.flush();
   }
   if constexpr (has_dots(FEAT)) {
     dacc.flush();

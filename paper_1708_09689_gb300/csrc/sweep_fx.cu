@@ -96,8 +96,11 @@ __global__ void __launch_bounds__(256) ti_sweep_fx(const __grid_constant__ Sweep
     ti_march<i64, 1, true, DEPTH, NBUF>(
         p.g, X, Yin, R, rc, tid >> cshift, z0, z1, ring,
         [&](int64_t s) { return __ldg(dfx + s); },
-        [&](const longlong2 dv, const Blk<i64, 1>& xc, const Blk<i64, 1>& S, const Blk<i64, 1>& D,
+        [&](const longlong2 dv, const Blk<i64, 1>& xm, const Blk<i64, 1>& xc, const Blk<i64, 1>& xp,
+            const Blk<i64, 1>& ax, const Blk<i64, 1>& bx, const Blk<i64, 1>& ay, const Blk<i64, 1>& by,
             const Blk<i64, 1>* yi, Blk<i64, 1>& yn) {
+          Blk<i64, 1> S, D;
+          ti_axes(xm, xp, ax, bx, ay, by, S, D);
           const i64 dp = dv.x * dmul, dm = dv.y * dmul;
 #pragma unroll
           for (int o = 0; o < 4; ++o) {

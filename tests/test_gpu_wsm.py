@@ -129,3 +129,18 @@ def test_wsm_bloch_states_and_spectral_function_on_gpu():
         refA = O.kpm_density(mu, E, a, b, O.jackson_kernel(512))
         assert np.max(np.abs(A[q] - refA)) < 1e-9 * np.max(refA)
         assert abs(np.trapezoid(A[q], E) - 2.0) < 1e-3
+
+
+@pytest.mark.parametrize("shape", [dict(kernel=1, threads=128), dict(kernel=0, threads=128, zslab=2),
+                                   dict(kernel=0, threads=64, zslab=0)])
+@pytest.mark.parametrize("prec,tol", [(pv.C128, 1e-13), (pv.C64, 2e-6)])
+def test_wsm_flat_and_marching_sweeps_match_oracle(shape, prec, tol):
+    for dims, per in CASES:
+        lat, H = _pair(dims, per)
+        R = 4
+        lat.set_tuning(R, prec, vpt=1, **shape)
+        x = W.gaussian_block(H.shape[0], R, 4)
+        cdt = torch.complex128 if prec == pv.C128 else torch.complex64
+        y = pv.apply_H(lat, torch.from_numpy(x).to("cuda", cdt)).cpu().numpy().astype(np.complex128)
+        xr = x.astype(np.complex64).astype(np.complex128) if prec == pv.C64 else x
+        assert _rel(y, H @ xr) < tol, (dims, per)
