@@ -38,6 +38,9 @@
  *   with pvsc_work_bytes.
  * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
  *   that launch kernels are asynchronous on that stream unless stated.
+ * Threads.  A lattice handle is used by one host thread at a time (its
+ *   tuning table and graph cache are not locked against concurrent tuning);
+ *   distinct handles may be used from different threads concurrently.
  * Errors.  Every call returns PVSC_OK or a negative pvsc_status and leaves a
  *   message for pvsc_last_error() (thread-local).  Invalid arguments are
  *   reported before anything is launched; device-side waits are bounded and

@@ -21,6 +21,7 @@
 // order by every block).
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -375,8 +376,13 @@ int pvsc_kpm_moments_batched(const pvsc_lattice* const* lats, int n, int R, int 
   int64_t grid = (int64_t)l0->sm_count * bps;
   const int64_t total_units = L.back().unit0 + L.back().units;
   if (grid > total_units) grid = total_units;
-  static BatchArgs args;  // ~30 KB: kept off the host stack
+  // ~30 KB: kept off the host stack; one block shared by all calls, so calls
+  // from several host threads take turns from here to the launch (the launch
+  // copies the parameters)
+  static BatchArgs args;
+  static std::mutex args_mu;
   static_assert(sizeof(BatchArgs) <= 32000, "kernel parameter block too large");
+  std::lock_guard<std::mutex> args_lock(args_mu);
   std::memset(&args, 0, sizeof(args));
   for (int i = 0; i < n; ++i) args.lats[i] = L[i];
   args.nlat = n;
