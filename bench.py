@@ -645,17 +645,26 @@ def main():
     mu64 = mu.clone()
 
     # ---- roofline of the dominant kernel (the complex64 TI KPM sweep)
-    bytes_per_lup = 96.0 + 8.0 / R          # x 32 + y_in 32 + y_out 32 (B), V 8 per site
-    sweep_ms = ms / sweeps                   # upper bound: includes launch gaps of the graph
-    achieved = bytes_per_lup * n_sites * R / (sweep_ms * 1e-3) / 1e9
+    two_step = bool(tuning) and tuning.get("kernel") == 4
+    if two_step:
+        # two recurrence steps per launch: w_{k-1}, w_k read and w_{k+1}, w_{k+2} written
+        # once (4 x 32 B per site and vector over two steps), the fp32 potential once
+        bytes_per_lup = 64.0 + 2.0 / R
+        launches = 1 + (sweeps - 1) // 2 + (sweeps - 1) % 2
+        kname = "ti_kpm2_sweep (complex64, two KPM steps per sweep)"
+    else:
+        bytes_per_lup = 96.0 + 4.0 / R      # x 32 + y_in 32 + y_out 32 (B), fp32 V 4 per site
+        launches = sweeps
+        kname = "ti_sweep<float,2,F_DOTS> (complex64 KPM sweep)"
+    launch_ms = ms / launches                # upper bound: includes launch gaps of the graph
+    achieved = bytes_per_lup * lups_per_step / (ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "ti_sweep<float,2,F_DOTS> (complex64 KPM sweep)",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": kname,
                 "bytes_per_lup": bytes_per_lup, "peak_kind": f"{peak_kind} hbm_gbs",
-                "launch_ms": round(sweep_ms, 4)}
+                "launch_ms": round(launch_ms, 4)}
     tr = TRAFFIC.get(("ti_slab", R)) if tuple(dims) == tuple(W.CONFIG_TI_SLAB.dims) else None
-    if tr and tr["source_sha256_16"] == kernel_source_hash():
+    if tr and not two_step and tr["source_sha256_16"] == kernel_source_hash():
         roofline["traffic"] = tr["bytes_per_launch"]
         roofline["traffic_over_algorithmic"] = round(tr["bytes_per_launch"] / (bytes_per_lup * n_sites * R), 3)
 
@@ -730,7 +739,7 @@ def main():
                 "data": "synthetic",
                 "config": {**slab_config(args), "launch": tuning},
                 "roofline": roofline, "compare_fp64": compare, "e2e": e2e,
-                "gpu_launches": sweeps * args.steps, "clocks": clk, "cpu_baseline": cpu,
+                "gpu_launches": launches * args.steps, "clocks": clk, "cpu_baseline": cpu,
                 "spectral": {"emin": emin, "emax": emax, "a": a, "b": b}}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -219,6 +219,10 @@ int pvsc_cheb_step_noalloc(const pvsc_lattice* lat, int R, int prec, const void*
  * prec == PVSC_Q64 (TI only): r0, if given, is complex128 and is not modified;
  * [b - a, b + a] must hold the Gershgorin interval of H (PVSC_ERR_ARG
  * otherwise; checked by one synchronous pass over the potential per call).
+ * complex64 on a TI lattice with tuning kernel 4: two recurrence steps per
+ * sweep (dots <w_k|w_k>, Re<w_{k+1}|w_k>, <w_{k+1}|w_{k+1}>, Re<w_{k+2}|w_{k+1}>
+ * give mu_2k .. mu_2k+3), the same vectors as the single sweeps; r0 is then
+ * still read only.
  * work: pvsc_work_bytes(lat, PVSC_OP_KPM, R, prec, M).
  */
 int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, uint64_t seed,
@@ -413,7 +417,15 @@ typedef struct {
   int32_t kernel; /* TI only: 0 z-marching in registers (or staged if tile_x > 0), */
                   /* 1 flat (one site per thread and pass, neighbours folded in turn), */
                   /* 2 z-marching with a cp.async ring of all six blocks of a plane, */
-                  /* 3 z-marching with a deep cp.async ring of the two streamed blocks */
+                  /* 3 z-marching with a deep cp.async ring of the two streamed blocks, */
+                  /* 4 (complex64, R >= 2; pvsc_kpm_moments only, other calls keep the */
+                  /* default sweep): two recurrence steps per sweep (temporal blocking), */
+                  /* blocks of tile_x x tile_y columns plus a recomputed one-column ring, */
+                  /* (tile_x tile_y + 2 (tile_x + tile_y)) R/2 <= 384 threads; 0 = the */
+                  /* default tile of that R (16x12, 10x8, 8x8, 5x5, 3x3, 2x2 for R = 2..64); */
+                  /* zslab = z-range of one block (0: whole columns).  Same vectors as */
+                  /* two single sweeps bit for bit; needs the larger KPM work buffer */
+                  /* (four vectors) that pvsc_work_bytes reports for complex64 TI */
 } pvsc_tuning;
 
 /* Device error word of the shared-memory staged sweeps: *flag = 1 if a copy

@@ -138,6 +138,7 @@ struct Sweep {
   const void* x;
   const void* yin;       // may be null (gamma = 0)
   void* yout;            // may be null (final series step)
+  void* yout2;           // two-step KPM sweep: w_{k+2} (yout holds w_{k+1})
   void* z;               // may be null
   double coef[4][kMaxR]; // alpha, beta, gamma, delta per vector
   // series accumulation (complex128 accumulator)
@@ -155,7 +156,7 @@ struct Sweep {
   double gscale;
   // dot products
   int dot_flags;         // bit0 xx, bit1 xy, bit2 yy
-  int dot_mode;          // 0 write dots[4][R]; 1 KPM first step; 2 KPM step k
+  int dot_mode;          // 0 write dots[4][R]; 1 KPM first step; 2 KPM step k; 3 KPM steps k, k+1
   double* partials;      // [gridDim][4][R]
   unsigned* counter;     // zero before the first sweep; reset by the last block
   double* dots;          // [4][R]
@@ -183,10 +184,51 @@ enum AccMode { ACC_NONE = 0, ACC_INIT = 1, ACC_ADD = 2, ACC_FINAL = 4, ACC_X = 8
 // block to arrive sums the rows in block order and writes the outputs.  The
 // result is bitwise reproducible for a given launch configuration.
 constexpr int kMaxThreads = 256;
-template <int VPT>
-__device__ void reduce_dots(const Sweep& p, double (&acc)[kNumDots][VPT]) {
-  __shared__ double sm[kMaxThreads / 32][kNumDots][VPT][32];  // [warp][dot][v][lane]
+
+// After every block has written its row of `partials`: the last block to
+// arrive sums the rows in block order and writes the outputs of dot_mode.
+__device__ __forceinline__ void finish_dots(const Sweep& p) {
   __shared__ int s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(p.counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nb = gridDim.x;
+  for (int q = warp; q < kNumDots * p.R; q += nwarps) {
+    const int d = q / p.R, r = q % p.R;
+    if (!((p.dot_flags >> (d == 0 ? 0 : (d == 3 ? 2 : 1))) & 1)) continue;
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += __ldcg(p.partials + (size_t)b * kNumDots * p.R + q);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+      double* mu = p.mu + (size_t)r * p.M;
+      if (p.dot_mode == 0) {
+        p.dots[q] = s;
+      } else if (p.dot_mode == 1) {  // KPM step 0: mu_0 = <w0|w0>, mu_1 = Re<w1|w0>
+        if (d == 0) mu[0] = s;
+        if (d == 1 && p.M > 1) mu[1] = s;
+      } else if (p.dot_mode == 2) {  // KPM step k: mu_2k = 2<wk|wk> - mu_0, mu_2k+1 = 2 Re<wk+1|wk> - mu_1
+        const int k = p.kpm_k;
+        if (d == 0 && 2 * k < p.M) mu[2 * k] = 2.0 * s - __ldcg(mu);
+        if (d == 1 && 2 * k + 1 < p.M) mu[2 * k + 1] = 2.0 * s - __ldcg(mu + 1);
+      } else {  // KPM steps k and k+1 in one sweep: dots <wk|wk>, Re<wk+1|wk>,
+                // <wk+1|wk+1>, Re<wk+2|wk+1> give mu_2k .. mu_2k+3
+        const int m = 2 * p.kpm_k + d;
+        if (m < p.M) mu[m] = 2.0 * s - __ldcg(mu + (d & 1));
+      }
+    }
+  }
+  if (threadIdx.x == 0) *p.counter = 0u;
+}
+
+template <int VPT, int MAXW = kMaxThreads / 32>
+__device__ void reduce_dots(const Sweep& p, double (&acc)[kNumDots][VPT]) {
+  __shared__ double sm[MAXW][kNumDots][VPT][32];  // [warp][dot][v][lane]
   const int C = p.C;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -211,35 +253,8 @@ __device__ void reduce_dots(const Sweep& p, double (&acc)[kNumDots][VPT]) {
         row[d * p.R + t * VPT + v] = s;
       }
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(p.counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  const int nb = gridDim.x;
-  for (int q = warp; q < kNumDots * p.R; q += nwarps) {
-    const int d = q / p.R, r = q % p.R;
-    if (!((p.dot_flags >> (d == 0 ? 0 : (d == 3 ? 2 : 1))) & 1)) continue;
-    double s = 0.0;
-    for (int b = lane; b < nb; b += 32) s += __ldcg(p.partials + (size_t)b * kNumDots * p.R + q);
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) {
-      if (p.dot_mode == 0) {
-        p.dots[q] = s;
-      } else if (p.dot_mode == 1) {  // KPM step 0: mu_0 = <w0|w0>, mu_1 = Re<w1|w0>
-        if (d == 0) p.mu[(size_t)r * p.M + 0] = s;
-        if (d == 1 && p.M > 1) p.mu[(size_t)r * p.M + 1] = s;
-      } else {  // KPM step k: mu_2k = 2<wk|wk> - mu_0, mu_2k+1 = 2 Re<wk+1|wk> - mu_1
-        const int k = p.kpm_k;
-        if (d == 0 && 2 * k < p.M) p.mu[(size_t)r * p.M + 2 * k] = 2.0 * s - __ldcg(p.mu + (size_t)r * p.M);
-        if (d == 1 && 2 * k + 1 < p.M)
-          p.mu[(size_t)r * p.M + 2 * k + 1] = 2.0 * s - __ldcg(p.mu + (size_t)r * p.M + 1);
-      }
-    }
-  }
-  if (threadIdx.x == 0) *p.counter = 0u;
+  finish_dots(p);
 }
+
 
 }  // namespace pvsc

@@ -111,7 +111,8 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
       p.fc[t][q][0] = (float)cv[t][q];
       p.fc[t][q][1] = (float)(cv[t][q] - (double)p.fc[t][q][0]);
     }
-  const LaunchShape sh = shape_for(lat, p.R, prec);
+  LaunchShape sh = shape_for(lat, p.R, prec);
+  if (sh.kernel == kKernelKpm2) sh = LaunchShape{};  // a KPM-only choice: single sweeps take the default
   if (lat->g.model == PVSC_TI && sh.tile_x > 0 && sh.tile_y > 0)
     return launch_sweep_staged(lat, prec, feat, p, sh, st);
   const int vpt = vpt_tuned(sh.vpt, p.R, prec);
@@ -342,6 +343,11 @@ using namespace pvsc;
 
 extern "C" {
 
+// The two-step KPM sweep exists for complex64 TI lattices with R >= 2.
+static bool kpm2_possible(const pvsc_lattice* lat, int R, int prec) {
+  return lat->g.model == PVSC_TI && prec == PVSC_C64 && R >= 2;
+}
+
 size_t pvsc_work_bytes(const pvsc_lattice* lat, int op, int R, int prec, int M) {
   if (lat && valid_R(R) && prec == PVSC_Q64 && op == PVSC_OP_KPM) return fx_layout(lat, R).total;
   if (!lat || !valid_R(R) || (prec != PVSC_C128 && prec != PVSC_C64)) return 0;
@@ -350,8 +356,9 @@ size_t pvsc_work_bytes(const pvsc_lattice* lat, int op, int R, int prec, int M) 
       return kWorkHeader + sizeof(double) * 2 * 2 * (size_t)lat->sm_count;
     case PVSC_OP_CHEB_STEP:
       return dots_work_bytes(lat, R);
-    case PVSC_OP_KPM:
-      return ((dots_work_bytes(lat, R) + 255) & ~size_t(255)) + 2 * vec_bytes(lat, R, prec);
+    case PVSC_OP_KPM:  // two vectors, four where the two-step sweep may run
+      return ((dots_work_bytes(lat, R) + 255) & ~size_t(255)) +
+             (kpm2_possible(lat, R, prec) ? 4 : 2) * vec_bytes(lat, R, prec);
     case PVSC_OP_SERIES:
       return series_layout(lat, R, prec).total;
     case PVSC_OP_ADJOINT: {
@@ -532,6 +539,8 @@ int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, u
   void* wa = wptr(work, voff);
   void* wb = wptr(work, voff + vec_bytes(lat, R, prec));
   const int64_t D = lat->g.n_sites * orbitals_of(lat->g.model);
+  const LaunchShape sh = shape_for(lat, R, prec);
+  const bool two = kpm2_possible(lat, R, prec) && sh.kernel == kKernelKpm2;
   const std::vector<uint64_t> key = {1, (uint64_t)R, (uint64_t)prec, bits(r0), seed, (uint64_t)M,
                                      bits(a), bits(b), bits(mu), bits(work)};
   auto body = [&](cudaStream_t cs) -> int {
@@ -565,9 +574,33 @@ int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, u
       p.coef[0][r] = 2.0 / a;
       p.coef[2][r] = -1.0;
     }
+    int k = 1;
+    if (two) {
+      // steps k, k+1 per sweep into two buffers distinct from both inputs
+      void* pool[4] = {wa, wb, wptr(work, voff + 2 * vec_bytes(lat, R, prec)),
+                       wptr(work, voff + 3 * vec_bytes(lat, R, prec))};
+      p.dot_mode = 3;
+      p.dot_flags = 7;
+      for (; k + 1 < nsteps; k += 2) {
+        void* o[2];
+        int no = 0;
+        for (void* q : pool)
+          if (q != prev && q != cur && no < 2) o[no++] = q;
+        p.x = cur;
+        p.yin = prev;
+        p.yout = o[0];
+        p.yout2 = o[1];
+        p.kpm_k = k;
+        if (int rc = launch_kpm2_sweep(lat, p, sh, cs)) return rc;
+        prev = o[0];
+        cur = o[1];
+      }
+      p.dot_flags = 3;
+      p.yout2 = nullptr;
+    }
     p.dot_mode = 2;
-    for (int k = 1; k < nsteps; ++k) {
-      void* out = (r0 && prev == r0) ? wa : const_cast<void*>(prev);
+    for (; k < nsteps; ++k) {
+      void* out = (r0 && prev == r0) ? (cur == wa ? wb : wa) : const_cast<void*>(prev);
       p.x = cur;
       p.yin = prev;
       p.yout = out;
@@ -779,7 +812,17 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
     return PVSC_OK;
   }
   if (tuning->vpt < 0 || tuning->vpt > 2) return set_error(PVSC_ERR_ARG, "vpt must be 0, 1 or 2");
-  if (tuning->kernel < 0 || tuning->kernel > 3) return set_error(PVSC_ERR_ARG, "kernel must be 0 .. 3");
+  if (tuning->kernel < 0 || tuning->kernel > 4) return set_error(PVSC_ERR_ARG, "kernel must be 0 .. 4");
+  if (tuning->kernel == kKernelKpm2) {
+    if (tuning->blocks_per_sm < 0 || tuning->zslab < 0 || tuning->tile_x < 0 || tuning->tile_y < 0)
+      return set_error(PVSC_ERR_ARG, "negative tuning value");
+    if (!kpm2_possible(lat, R, prec))
+      return set_error(PVSC_ERR_ARG, "kernel 4 (two KPM steps per sweep) needs a TI lattice, complex64 and R >= 2");
+    if (int rc = kpm2_check_tile(tuning->tile_x, tuning->tile_y, R)) return rc;
+    lat->tuning[{R, prec}] = *tuning;
+    drop_graphs(lat);
+    return PVSC_OK;
+  }
   const int C = R / vpt_tuned(tuning->vpt, R, prec);
   if (tuning->threads < 32 || tuning->threads > kMaxThreads || tuning->threads % 32 || tuning->threads % C)
     return set_error(PVSC_ERR_ARG, "threads must be a multiple of 32 and of R/VPT = %d, at most %d", C, kMaxThreads);

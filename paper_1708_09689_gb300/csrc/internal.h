@@ -35,7 +35,8 @@ struct LaunchShape {
   int vpt = 0;            // 0: automatic
   int tile_x = 0;         // > 0: shared-memory staged TI sweep with this tile
   int tile_y = 0;
-  int kernel = 0;         // TI: 0 z-marching / staged, 1 flat, 2 / 3 cp.async rings
+  int kernel = 0;         // TI: 0 z-marching / staged, 1 flat, 2 / 3 cp.async rings,
+                          // 4 two KPM steps per sweep (tile_x x tile_y tiles)
 };
 
 // kernel-selector "model" values of the flat and the cp.async-prefetching TI
@@ -80,6 +81,11 @@ int launch_fx_prepare(const pvsc_lattice* lat, int R, const void* r0, uint64_t s
                       double b, void* work, const FxLayout& L, cudaStream_t st);
 int launch_sweep_fx(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, bool tuned,
                     cudaStream_t st);
+
+// two KPM recurrence steps per sweep (sweep_kpm2.cu): complex64 TI lattices, R >= 2
+constexpr int kKernelKpm2 = 4;
+int launch_kpm2_sweep(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, cudaStream_t st);
+int kpm2_check_tile(int TX, int TY, int R);
 
 // Vectors per thread for (R, prec) under an optional tuned value.
 int vpt_tuned(int tuned, int R, int prec);
