@@ -44,7 +44,7 @@ UNIT = "GLUP/s"
 # kernel at the benchmark size, from the ncu capture summarised in
 # profiles/ti_sweep_c64_R8_ncu.md (a half-depth slab, scaled by the number of sites).  It is
 # reported only while the kernel sources still hash to the captured version.
-TRAFFIC = {("ti_slab", 8): {"bytes_per_launch": 3.220e9, "source_sha256_16": "ff4264462c0e1b1d"}}
+TRAFFIC = {("ti_slab", 8): {"bytes_per_launch": 3.222e9, "source_sha256_16": "5bd0d6c28d71cddb"}}
 KERNEL_SOURCES = ("paper_1708_09689_gb300/csrc/sweep.cuh", "paper_1708_09689_gb300/csrc/common.cuh")
 
 
@@ -89,6 +89,9 @@ def parse():
                     help="with --workload batched --sweeps-only: number of lattices of the batch")
     ap.add_argument("--q64", action="store_true",
                     help="with --sweeps-only: the fixed-point (PVSC_Q64) KPM sweep instead")
+    ap.add_argument("--qd-on-the-fly", action="store_true",
+                    help="graphene_qd: regenerate the quantum-dot potential inside the sweeps "
+                         "instead of reading it")
     ap.add_argument("--launch", default=None,
                     help="JSON launch shape (threads, blocks_per_sm, zslab, vpt, tile_x, tile_y, kernel) "
                          "to use instead of autotuning, e.g. for profiling runs")
@@ -246,17 +249,18 @@ def _hbm_roof(bytes_per_lup, lups, ms, kernel):
             "bytes_per_lup": bytes_per_lup, "peak_kind": f"{kind} hbm_gbs"}
 
 
-def series_bytes_per_site(K: int) -> float:
+def series_bytes_per_site(K: int, vb: float = 4.0) -> float:
     """Algorithmic HBM bytes per graphene site of one complex64 propagation time
-    step with K series terms (R = 1, fp32 copy of V): the complex128 -> complex64
-    conversion of w_0 (16 + 8), sweep 1 (x 8, w_1 8, psi 16, acc 16, V 4), sweeps
-    j = 2 .. K-2 (x 8, y_in 8, y_out 8, V 4, and acc 16 + 16 on odd j), and the
-    last sweep (x 8, y_in 8, V 4, acc 16, psi 16)."""
+    step with K series terms (R = 1, fp32 copy of V: vb = 4 bytes per sweep, 0 when
+    the potential is regenerated in the sweep): the complex128 -> complex64
+    conversion of w_0 (16 + 8), sweep 1 (x 8, w_1 8, psi 16, acc 16, V), sweeps
+    j = 2 .. K-2 (x 8, y_in 8, y_out 8, V, and acc 16 + 16 on odd j), and the
+    last sweep (x 8, y_in 8, V, acc 16, psi 16)."""
     if K < 3:
         raise ValueError("K >= 3")
-    total = 24.0 + 52.0 + 52.0
+    total = 24.0 + 2 * (48.0 + vb)
     for j in range(2, K - 1):
-        total += 28.0 + (32.0 if j % 2 == 1 else 0.0)
+        total += 24.0 + vb + (32.0 if j % 2 == 1 else 0.0)
     return total
 
 
@@ -295,7 +299,11 @@ def run_workload(args, pv, dev, rank, world):
                      "mu_0": float(mu[0, 0].item())})
     elif args.workload == "graphene_qd":
         cfg = W.CONFIG_GRAPHENE_QD
-        lat = pv.Lattice.graphene(cfg.cells, (0, 0), t=cfg.t, V=cfg.potential())
+        if args.qd_on_the_fly:  # Eq. qdotarray regenerated inside every sweep
+            lat = pv.Lattice.graphene(cfg.cells, (0, 0), t=cfg.t,
+                                      qdots=(cfg.ndots, cfg.R_dot, cfg.V0, cfg.w))
+        else:
+            lat = pv.Lattice.graphene(cfg.cells, (0, 0), t=cfg.t, V=cfg.potential())
         emin, emax, a, b = lat.spectral_bounds()
         nterms = len(pv.propagation_coeffs(a * cfg.dt, cfg.trunc))
         psi0 = torch.from_numpy(cfg.packet()).to(dev)
@@ -343,8 +351,11 @@ def run_workload(args, pv, dev, rank, world):
                      "ms_per_step": round(ms64 / n64, 4), "steps": n64, "dtype": "c64",
                      "config": {"workload": "graphene 4096x2048 four-site cells (2^25 sites), open, 8x8 "
                                             "QD array V0=0.1 R=40 w=5, Gaussian packet, dt=1, trunc 1e-14",
-                                "sweeps_per_time_step": nterms - 1},
-                     "roofline": _hbm_roof(round(series_bytes_per_site(nterms) / (nterms - 1), 3), lups,
+                                "sweeps_per_time_step": nterms - 1,
+                                "potential": "regenerated in the sweep" if args.qd_on_the_fly
+                                             else "stored (fp32 copy read by the sweep)"},
+                     "roofline": _hbm_roof(round(series_bytes_per_site(nterms, 0.0 if args.qd_on_the_fly
+                                                                        else 4.0) / (nterms - 1), 3), lups,
                                            ms64 / n64,
                                            "gr_sweep<float,1,*> (complex64 w, complex128 accumulator "
                                            "touched on every other sweep), time-step average"),

@@ -76,7 +76,9 @@ enum {
   PVSC_V_HOST = 1,       /* copied from desc.V, a host array of n_sites doubles */
   PVSC_V_DEVICE = 2,     /* copied from desc.V, a device array of n_sites doubles */
   PVSC_V_SEED = 3,       /* V_n = W (u_n - 1/2), u_n from the counter hash, stored */
-  PVSC_V_ON_THE_FLY = 4  /* same values, regenerated inside every stencil sweep */
+  PVSC_V_ON_THE_FLY = 4, /* same values, regenerated inside every stencil sweep */
+  PVSC_V_QDOT = 5        /* graphene: gate-defined quantum-dot array (Eq. qdotarray), */
+                         /* regenerated inside every sweep from the qd_* fields */
 };
 
 /* Damping kernels of pvsc_kpm_density. */
@@ -120,12 +122,27 @@ typedef struct {
   uint64_t seed;        /* for PVSC_V_SEED / PVSC_V_ON_THE_FLY */
   double W;             /* disorder width for PVSC_V_SEED / PVSC_V_ON_THE_FLY */
   double k0;            /* PVSC_WSM: Weyl nodes at (+-k0, 0, 0) (Eq. TB_H_wsm); else ignored */
+  /* PVSC_V_QDOT (graphene): qd_count x qd_count dots of radius qd_radius on a
+   * square grid of spacing 4 qd_radius centred in the sample; dot (l, k) at
+   * physical (X_l, Y_k) = (X_c + (l - (K-1)/2) 4R, Y_c + (k - (K-1)/2) 4R),
+   * (X_c, Y_c) = (3 Ny / 2, sqrt(3) Nx / 2), height V_k = qd_V0 + qd_dV |k - K/2|;
+   * V(r) = sum_{l,k} V_k S(R - |r - (X_l, Y_k)|) with the step smoothed to
+   * S(s) = (1 + tanh(s / qd_width)) / 2 within R + 20 qd_width of a centre and
+   * 0 beyond.  Site nu of cell (x, y) sits at X = 3 y + {0, 1/2, 3/2, 2}[nu],
+   * Y = sqrt(3) x + {sqrt(3)/2, 0, 0, sqrt(3)/2}[nu] (C-C distance 1).
+   * complex64 sweeps evaluate it in fp32 (within ~1e-7 qd_V0 of the fp64
+   * value), complex128 sweeps and the spectral bounds in fp64. */
+  int32_t qd_count;     /* 1 .. 16 */
+  int32_t qd_reserved;
+  double qd_radius, qd_V0, qd_width, qd_dV;
 } pvsc_lattice_desc;
 
 /* Create a lattice handle.  Allocates the handle and its device copy of V,
  * copies or generates V on `stream` and synchronises it.  *out is set only
  * on success.  Errors: ARG (null, dims < 1, unknown model or v_source,
- * t, delta not finite; delta != 0 on graphene), OOM, CUDA. */
+ * t, delta not finite; delta != 0 on graphene; PVSC_V_QDOT on another model
+ * or with qd_count outside 1..16, qd_radius or qd_width not positive and
+ * finite), OOM, CUDA. */
 int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattice** out);
 
 /* Destroy a handle (NULL is accepted).  The caller must have synchronised
@@ -137,7 +154,7 @@ int pvsc_lattice_info(const pvsc_lattice* lat, int64_t* n_sites, int32_t* orbita
 
 /* Replace the stored on-site potential from a device array of n_sites
  * doubles (for gradient loops over the gate potential).  Not allowed for
- * PVSC_V_ON_THE_FLY lattices (ARG).  Asynchronous on stream. */
+ * PVSC_V_ON_THE_FLY and PVSC_V_QDOT lattices (ARG).  Asynchronous on stream. */
 int pvsc_set_potential(pvsc_lattice* lat, const double* V_dev, void* stream);
 
 /* Write the potential the stencil uses (stored or regenerated) to a device

@@ -27,7 +27,7 @@ PVSC_OK, PVSC_ERR_ARG, PVSC_ERR_CUDA, PVSC_ERR_OOM, PVSC_ERR_TIMEOUT, PVSC_ERR_U
 TI, GRAPHENE, WSM = 1, 2, 3
 C128, C64, Q64 = 0, 1, 2  # Q64: fixed-point vectors, pvsc_kpm_moments on TI only
 KERNEL_NONE, KERNEL_JACKSON, KERNEL_LORENTZ = 0, 1, 2  # damping kernels of kpm_density
-V_ZERO, V_HOST, V_DEVICE, V_SEED, V_ON_THE_FLY = 0, 1, 2, 3, 4
+V_ZERO, V_HOST, V_DEVICE, V_SEED, V_ON_THE_FLY, V_QDOT = 0, 1, 2, 3, 4, 5
 DOT_XX, DOT_XY, DOT_YY = 1, 2, 4
 OP_APPLY, OP_CHEB_STEP, OP_KPM, OP_SERIES, OP_ADJOINT, OP_KPM_BATCHED = 0, 1, 2, 3, 4, 5
 
@@ -53,6 +53,12 @@ class LatticeDesc(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("W", ctypes.c_double),
         ("k0", ctypes.c_double),
+        ("qd_count", ctypes.c_int32),
+        ("qd_reserved", ctypes.c_int32),
+        ("qd_radius", ctypes.c_double),
+        ("qd_V0", ctypes.c_double),
+        ("qd_width", ctypes.c_double),
+        ("qd_dV", ctypes.c_double),
     ]
 
 
@@ -179,12 +185,14 @@ class Lattice:
 
     V: None (zero), a torch CUDA float64 tensor, or a numpy/CPU float64 array
     (copied into the handle); or disorder=(W, seed) for box disorder from the
-    counter hash, stored (on_the_fly=False) or regenerated in every sweep.
+    counter hash, stored (on_the_fly=False) or regenerated in every sweep; or, for
+    graphene, qdots=(count, radius, V0, width[, dV]) for the gate-defined quantum-dot
+    array of Eq. qdotarray regenerated in every sweep.
     """
 
     def __init__(self, model: int, dims, periodic, t: float = 1.0, m: float = 0.0, V=None,
                  disorder=None, on_the_fly: bool = False, delta1: float = 0.0, delta2: float = 0.0,
-                 k0: float = 0.0, stream=None):
+                 k0: float = 0.0, qdots=None, stream=None):
         d = LatticeDesc()
         d.model = model
         dims = list(dims) + [1] * (3 - len(dims))
@@ -195,7 +203,12 @@ class Lattice:
         d.t, d.m, d.delta1, d.delta2 = float(t), float(m), float(delta1), float(delta2)
         d.k0 = float(k0)
         keep = None
-        if disorder is not None:
+        if qdots is not None:
+            q = list(qdots) + [0.0] * (5 - len(qdots))
+            d.v_source = V_QDOT
+            d.qd_count, d.qd_radius, d.qd_V0, d.qd_width, d.qd_dV = (
+                int(q[0]), float(q[1]), float(q[2]), float(q[3]), float(q[4]))
+        elif disorder is not None:
             W, seed = disorder
             d.v_source = V_ON_THE_FLY if on_the_fly else V_SEED
             d.W, d.seed = float(W), int(seed)

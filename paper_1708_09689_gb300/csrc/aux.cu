@@ -78,10 +78,7 @@ __global__ void potential_f32_kernel(const double* __restrict__ V, float* __rest
 __global__ void get_potential_kernel(Geometry g, double* out) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.n_sites;
        s += (int64_t)gridDim.x * blockDim.x) {
-    double v = 0.0;
-    if (g.v_mode == 1) v = g.V[s];
-    else if (g.v_mode == 2) v = g.W * (hash_uniform(g.vkey, (uint64_t)s) - 0.5);
-    out[s] = v;
+    out[s] = site_potential_any(g, s);
   }
 }
 
@@ -109,8 +106,7 @@ __global__ void gershgorin_kernel(Geometry g, double* out /* [gridDim][2] */) {
           if (pl >= 0) radius += at;
         }
       }
-      const double V = (g.v_mode == 1) ? g.V[s]
-                     : (g.v_mode == 2 ? g.W * (hash_uniform(g.vkey, (uint64_t)s) - 0.5) : 0.0);
+      const double V = site_potential_any(g, s);
       radius += sqrt(g.d1 * g.d1 + g.d2 * g.d2);  // one Delta entry per row, |D1 +- i D2|
       for (int sign = -1; sign <= 1; sign += 2) {  // Gamma^1 = +1 / -1 rows
         const double c = V + sign * (g.m - self * g.t);
@@ -150,8 +146,7 @@ __global__ void gershgorin_kernel(Geometry g, double* out /* [gridDim][2] */) {
           rb += h;
         }
       }
-      const double V = (g.v_mode == 1) ? g.V[s]
-                     : (g.v_mode == 2 ? g.W * (hash_uniform(g.vkey, (uint64_t)s) - 0.5) : 0.0);
+      const double V = site_potential_any(g, s);
       const double r = fmax(ra, rb) + fabs(sx);
       lo = fmin(lo, V - r);
       hi = fmax(hi, V + r);
@@ -172,8 +167,7 @@ __global__ void gershgorin_kernel(Geometry g, double* out /* [gridDim][2] */) {
       if (nu == 1) nb = 2 + (hxm ? 1 : 0);
       if (nu == 2) nb = 2 + (hxm ? 1 : 0);
       if (nu == 3) nb = 1 + (hx ? 1 : 0) + (hyp ? 1 : 0);
-      const double V = (g.v_mode == 1) ? g.V[s]
-                     : (g.v_mode == 2 ? g.W * (hash_uniform(g.vkey, (uint64_t)s) - 0.5) : 0.0);
+      const double V = site_potential_any(g, s);
       lo = fmin(lo, V - nb * at);
       hi = fmax(hi, V + nb * at);
     }

@@ -16,6 +16,33 @@ constexpr int kMaxR = 64;
 constexpr int kNumDots = 4;  // <x|x>, Re<y|x>, Im<y|x>, <y|y>
 
 // ---------------------------------------------------------------- geometry
+// Gate-defined quantum-dot array of Eq. qdotarray on the graphene lattice,
+// regenerated inside the sweeps (v_mode 3): K x K dots of radius R on a square
+// grid of spacing D = 4 R centred in the sample, dot (l, k) at physical
+// (X_l, Y_k) with height V_k = V0 + dV |k - K/2|, and the step Theta smoothed
+// to S(s) = (1 + tanh(s / w)) / 2, evaluated within rcut = R + 20 w of a dot
+// centre (beyond it S < 4e-18).  Site positions in units of the C-C distance:
+// X = 3 y + {0, 1/2, 3/2, 2}[nu], Y = sqrt(3) x + {sqrt(3)/2, 0, 0, sqrt(3)/2}[nu]
+// for site nu of cell (x, y).  The dot centres are kept relative to a nearby
+// cell row / column, X_l = 3 row[l] + ex[l] and Y_k = sqrt(3) col[k] + ey[k]
+// with small residuals, so that X - X_l and Y - Y_k of the sites that matter
+// are formed from small integers and keep their accuracy in fp32.
+constexpr int kMaxQDots = 16;
+// What the sweeps take as kernel parameters: the cell range test (dot (0, 0),
+// cut-off, 1 / spacing) and the dot table (rows / columns with their
+// residuals, heights), in fp32 and fp64.
+struct QDScal {
+  int K, row0, col0;
+  float ex0f, ey0f, rcutf, invDf, Rf, inv_wf;
+  double ex0, ey0, rcut, invD, R, w;
+  int row[kMaxQDots], col[kMaxQDots];
+  float exf[kMaxQDots], eyf[kMaxQDots], Vkf[kMaxQDots];
+  double ex[kMaxQDots], ey[kMaxQDots], Vk[kMaxQDots];
+};
+struct QDots {
+  QDScal s;
+};
+
 struct Geometry {
   int model;            // 1 TI, 2 graphene, 3 Weyl semimetal
   int per[3];           // periodic flags
@@ -24,12 +51,13 @@ struct Geometry {
   double t, m;          // hopping; TI mass, or for the Weyl semimetal 2 + cos k0
   const double* V;      // device [n_sites] when v_mode == 1
   const float* V32;     // the same potential rounded to fp32, for complex64 sweeps
-  int v_mode;           // 0 zero, 1 stored, 2 regenerated from the hash
+  int v_mode;           // 0 zero, 1 stored, 2 regenerated from the hash, 3 quantum-dot array
   uint64_t vkey;        // mix(seed ^ stream*gamma) for stream 0
   double W;             // disorder width for v_mode 2
   double d1, d2;        // TI on-site Delta_1 Gamma^5 + Delta_2 Gamma^15 (Eq. TB_H_topi)
   float d1f, d2f;       // the same rounded to fp32, for complex64 sweeps
   int has_delta;        // d1 != 0 or d2 != 0
+  const QDots* qd;      // v_mode 3 (graphene): device copy owned by the lattice
 };
 
 // Orbitals per site: 4 (TI), 1 (graphene site), 2 (Weyl semimetal).
@@ -47,6 +75,15 @@ __host__ __device__ __forceinline__ int64_t nbr_minus(int64_t idx, int64_t coord
 __host__ __device__ __forceinline__ int64_t nbr_plus(int64_t idx, int64_t coord, int64_t L,
                                                      int per, int64_t stride) {
   return coord < L - 1 ? idx + stride : (per ? idx - (L - 1) * stride : -1);
+}
+
+// ---------------------------------------------------------------- index arithmetic
+// Non-negative a / b with 32-bit unsigned division when both fit: the 64-bit
+// division is a long instruction sequence that partly issues on the narrow
+// fp64 pipe of this part.
+__device__ __forceinline__ int64_t udiv64(int64_t a, int64_t b) {
+  if (((uint64_t)a | (uint64_t)b) <= 0xffffffffull) return (int64_t)((uint32_t)a / (uint32_t)b);
+  return a / b;
 }
 
 // SplitMix64 output finaliser (Steele, Lea & Flood 2014).
@@ -67,10 +104,78 @@ __host__ __device__ __forceinline__ double hash_uniform(uint64_t key, uint64_t i
   return (double)(mix64(key + idx) >> 11) * 0x1.0p-53;
 }
 
+// Eq. qdotarray at the four sites of graphene cell (x, y), in the arithmetic
+// type T.  One range test on the cell (its sites span [0, 2] in X and
+// [0, sqrt(3)/2] in Y from the cell origin) finds the dot rows l and columns k
+// that can lie within rcut; most cells have none and get zeros.  The dots
+// (l, k) in range are then visited in order, the four sites together:
+// V += V_k S with S = (1 + tanh((R - d) / w)) / 2 where d < rcut.  fp32 forms
+// S as the equal 1 / (1 + exp(-2 (R - d) / w)).
+template <typename T>
+__device__ __forceinline__ void qd_cell_potentials(const QDScal& q, int64_t x, int64_t y, T (&V)[4]) {
+  constexpr bool f = sizeof(T) == 4;
+  const T s3 = T(1.7320508075688772), h3 = T(0.8660254037844386);
+  const T rcut = f ? T(q.rcutf) : T(q.rcut), invD = f ? T(q.invDf) : T(q.invD);
+  const T tx = T(3) * T(y - q.row0) - (f ? T(q.ex0f) : T(q.ex0));  // X - X_0 at the cell origin
+  const T ty = s3 * T(x - q.col0) - (f ? T(q.ey0f) : T(q.ey0));    // Y - Y_0
+  // conservative index ranges: floor / ceil leave one spare index per side
+  const int l0 = max(0, (int)floor((tx - rcut) * invD));
+  const int l1 = min(q.K - 1, (int)ceil((tx + T(2) + rcut) * invD));
+  const int k0 = max(0, (int)floor((ty - rcut) * invD));
+  const int k1 = min(q.K - 1, (int)ceil((ty + h3 + rcut) * invD));
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) V[nu] = T(0);
+  if (l0 > l1 || k0 > k1) return;
+  const T R = f ? T(q.Rf) : T(q.R);
+  const T ox[4] = {T(0), T(0.5), T(1.5), T(2)}, oy[4] = {h3, T(0), T(0), h3};
+  for (int l = l0; l <= l1; ++l) {
+    const T dx0 = T(3) * T(y - q.row[l]) - (f ? T(q.exf[l]) : T(q.ex[l]));  // X - X_l at the origin
+    if (!(dx0 + T(2) > -rcut && dx0 < rcut)) continue;
+    for (int k = k0; k <= k1; ++k) {
+      const T dy0 = s3 * T(x - q.col[k]) - (f ? T(q.eyf[k]) : T(q.ey[k]));
+      if (!(dy0 + h3 > -rcut && dy0 < rcut)) continue;
+      const T Vk = f ? T(q.Vkf[k]) : T(q.Vk[k]);
+#pragma unroll
+      for (int nu = 0; nu < 4; ++nu) {
+        const T dx = dx0 + ox[nu], dy = dy0 + oy[nu];
+        const T d = sqrt(fma(dx, dx, dy * dy));
+        T S;
+        if constexpr (f) S = 1.0f / (1.0f + __expf(-2.0f * (R - d) * q.inv_wf));
+        else S = 0.5 * (1.0 + tanh((R - d) / q.w));
+        if (d < rcut) V[nu] += Vk * S;
+      }
+    }
+  }
+}
+
+// site -> (cell x, cell y, nu) of the graphene lattice
+__device__ __forceinline__ void gr_site_coords(const Geometry& g, int64_t site, int64_t& x, int64_t& y,
+                                               int& nu) {
+  const int64_t c = site >> 2;
+  nu = (int)(site & 3);
+  y = udiv64(c, g.L[0]);
+  x = c - y * g.L[0];
+}
+
+// Stored or hashed potential (the sweeps; the graphene sweep has its own
+// instantiation for the quantum-dot array, so no other kernel carries that code).
 __device__ __forceinline__ double site_potential(const Geometry& g, int64_t site) {
   if (g.v_mode == 1) return __ldg(g.V + site);
   if (g.v_mode == 2) return g.W * (hash_uniform(g.vkey, (uint64_t)site) - 0.5);
   return 0.0;
+}
+
+// Any potential mode, in fp64 (bounds, potential read-back).
+__device__ __forceinline__ double site_potential_any(const Geometry& g, int64_t site) {
+  if (g.v_mode == 3) {
+    int64_t x, y;
+    int nu;
+    gr_site_coords(g, site, x, y, nu);
+    double V[4];
+    qd_cell_potentials<double>(g.qd->s, x, y, V);
+    return V[nu];
+  }
+  return site_potential(g, site);
 }
 
 // The potential in the sweep's arithmetic type: complex64 sweeps read the fp32
@@ -101,15 +206,6 @@ __device__ __forceinline__ void random_phase_entry(double u, double scale, T& re
     re = c * (float)scale;
     im = s * (float)scale;
   }
-}
-
-// ---------------------------------------------------------------- index arithmetic
-// Non-negative a / b with 32-bit unsigned division when both fit: the 64-bit
-// division is a long instruction sequence that partly issues on the narrow
-// fp64 pipe of this part.
-__device__ __forceinline__ int64_t udiv64(int64_t a, int64_t b) {
-  if (((uint64_t)a | (uint64_t)b) <= 0xffffffffull) return (int64_t)((uint32_t)a / (uint32_t)b);
-  return a / b;
 }
 
 // ---------------------------------------------------------------- complex
@@ -170,6 +266,7 @@ struct Sweep {
   const double* vscale;  // per vector: value of one unit of a dot product
   int zslab;             // TI z-marching depth
   int tile_x, tile_y;    // TI shared-memory staged sweep: tile of columns (0: register marching)
+  QDScal qds;            // graphene quantum-dot array (g.v_mode 3): range-test scalars
 };
 
 // acc_new = [INIT ? 0 : acc] + [X ? cx x : 0] + cy y_new, with x the sweep's

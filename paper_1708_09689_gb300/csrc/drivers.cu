@@ -93,6 +93,7 @@ static int launch_sweep_staged(const pvsc_lattice* lat, int prec, int feat, Swee
 void sweep_init(Sweep& p, const pvsc_lattice* lat, int R, int prec) {
   std::memset(&p, 0, sizeof(Sweep));
   p.g = lat->g;
+  p.qds = lat->qds;
   p.R = R;
   p.C = R / vpt_for(R, prec);
   for (int r = 0; r < R; ++r) p.coef[0][r] = 1.0;
@@ -128,9 +129,11 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
   // cuboid) unless a tuning entry selects the z-marching one (kernel 0)
   const bool wsm = lat->g.model == PVSC_WSM;
   const bool wsm_flat = wsm && (lat->tuning.count({p.R, prec}) == 0 || sh.kernel == 1);
+  const bool qd = lat->g.model == PVSC_GRAPHENE && lat->g.v_mode == 3;
   const int model = flat ? kModelTIFlat
                     : async ? (sh.kernel == 2 ? kModelTIAsync : kModelTIAsyncDeep)
                     : wsm ? (wsm_flat ? kModelWSM : kModelWSMMarch)
+                    : qd ? kModelGrapheneQD
                             : lat->g.model;
   int rc = prec == PVSC_C128 ? occupancy_c128(model, feat, threads, &occ)
                              : occupancy_c64(model, vpt, feat, threads, &occ);

@@ -46,6 +46,7 @@ constexpr int kModelTIAsync = 4;      // ring of all six blocks of a plane, one 
 constexpr int kModelTIAsyncDeep = 5;  // ring of the two HBM streams, three planes ahead
 constexpr int kModelWSM = 8;         // Weyl semimetal flat cell sweep
 constexpr int kModelWSMMarch = 9;    // Weyl semimetal z-marching cell sweep
+constexpr int kModelGrapheneQD = 10; // graphene sweep with the regenerated quantum-dot array
 constexpr int kAsyncDepth = 1;
 constexpr int kAsyncDeepDepth = 3;
 // ring: (depth + 1) slots x buffers x 4 granules of 16 bytes per thread
@@ -107,6 +108,8 @@ struct pvsc_lattice {
   pvsc::Geometry g{};
   double* V_dev = nullptr;  // owned when v_mode == 1
   float* V32_dev = nullptr; // fp32 copy of V_dev for complex64 sweeps
+  pvsc::QDots* qd_dev = nullptr;  // quantum-dot array parameters (v_mode 3)
+  pvsc::QDScal qds{};             // and the scalars the sweeps take as parameters
   int v_source = 0;
   uint64_t seed = 0;
   int device = 0;

@@ -67,9 +67,48 @@ pvsc_lattice::~pvsc_lattice() {
   }
   if (V_dev) cudaFree(V_dev);
   if (V32_dev) cudaFree(V32_dev);
+  if (qd_dev) cudaFree(qd_dev);
 }
 
 using namespace pvsc;
+
+// Dot centres of Eq. qdotarray relative to the nearest cell row / column
+// (see QDScal): X_l = 3 row[l] + ex[l], Y_k = sqrt(3) col[k] + ey[k].
+static void qdots_setup(const pvsc_lattice_desc& d, QDScal& q) {
+  const double s3 = std::sqrt(3.0);
+  const int K = d.qd_count;
+  const double Nx = (double)d.dims[0], Ny = (double)d.dims[1];
+  const double Xc = 1.5 * Ny, Yc = 0.5 * s3 * Nx;
+  const double D = 4.0 * d.qd_radius;
+  q = QDScal{};
+  q.K = K;
+  q.R = d.qd_radius;
+  q.w = d.qd_width;
+  q.rcut = q.R + 20.0 * q.w;
+  q.invD = 1.0 / D;
+  for (int i = 0; i < K; ++i) {
+    const double off = (i - (K - 1) / 2.0) * D;
+    const double X = Xc + off, Y = Yc + off;
+    q.row[i] = (int)std::llround(X / 3.0);
+    q.ex[i] = X - 3.0 * q.row[i];
+    q.col[i] = (int)std::llround(Y / s3);
+    q.ey[i] = Y - s3 * q.col[i];
+    q.Vk[i] = d.qd_V0 + d.qd_dV * std::fabs(i - K / 2.0);
+    q.exf[i] = (float)q.ex[i];
+    q.eyf[i] = (float)q.ey[i];
+    q.Vkf[i] = (float)q.Vk[i];
+  }
+  q.row0 = q.row[0];
+  q.col0 = q.col[0];
+  q.ex0 = q.ex[0];
+  q.ey0 = q.ey[0];
+  q.ex0f = (float)q.ex0;
+  q.ey0f = (float)q.ey0;
+  q.rcutf = (float)q.rcut;
+  q.invDf = (float)q.invD;
+  q.Rf = (float)q.R;
+  q.inv_wf = (float)(1.0 / q.w);
+}
 
 extern "C" {
 
@@ -94,8 +133,18 @@ int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattic
     return set_error(PVSC_ERR_ARG, "delta1 and delta2 must be finite");
   if (desc->model != PVSC_TI && (desc->delta1 != 0.0 || desc->delta2 != 0.0))
     return set_error(PVSC_ERR_ARG, "Delta terms belong to the TI model");
-  if (desc->v_source < PVSC_V_ZERO || desc->v_source > PVSC_V_ON_THE_FLY)
+  if (desc->v_source < PVSC_V_ZERO || desc->v_source > PVSC_V_QDOT)
     return set_error(PVSC_ERR_ARG, "unknown v_source %d", desc->v_source);
+  if (desc->v_source == PVSC_V_QDOT) {
+    if (desc->model != PVSC_GRAPHENE)
+      return set_error(PVSC_ERR_ARG, "the quantum-dot array potential belongs to the graphene model");
+    if (desc->qd_count < 1 || desc->qd_count > kMaxQDots)
+      return set_error(PVSC_ERR_ARG, "qd_count = %d: must be 1 .. %d", desc->qd_count, kMaxQDots);
+    if (!(std::isfinite(desc->qd_radius) && desc->qd_radius > 0.0) ||
+        !(std::isfinite(desc->qd_width) && desc->qd_width > 0.0) || !std::isfinite(desc->qd_V0) ||
+        !std::isfinite(desc->qd_dV))
+      return set_error(PVSC_ERR_ARG, "quantum dots need a positive finite radius and width and finite V0, dV");
+  }
   if ((desc->v_source == PVSC_V_HOST || desc->v_source == PVSC_V_DEVICE) && !desc->V)
     return set_error(PVSC_ERR_ARG, "v_source needs desc->V");
   if ((desc->v_source == PVSC_V_SEED || desc->v_source == PVSC_V_ON_THE_FLY) && !std::isfinite(desc->W))
@@ -153,6 +202,19 @@ int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattic
     if (rc == PVSC_OK) rc = launch_potential_f32(lat->V_dev, lat->V32_dev, g.n_sites, st);
   } else if (desc->v_source == PVSC_V_ON_THE_FLY) {
     g.v_mode = 2;
+  } else if (desc->v_source == PVSC_V_QDOT) {
+    QDots q;
+    qdots_setup(*desc, q.s);
+    e = cudaMalloc(&lat->qd_dev, sizeof(QDots));
+    if (e != cudaSuccess) {
+      delete lat;
+      return set_error(PVSC_ERR_OOM, "cudaMalloc of the quantum-dot table failed: %s", cudaGetErrorString(e));
+    }
+    e = cudaMemcpyAsync(lat->qd_dev, &q, sizeof(QDots), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) rc = set_error(PVSC_ERR_CUDA, "copy of the quantum-dot table failed: %s", cudaGetErrorString(e));
+    g.qd = lat->qd_dev;
+    lat->qds = q.s;
+    g.v_mode = 3;
   }
   if (rc == PVSC_OK) {
     e = cudaStreamSynchronize(st);
@@ -181,7 +243,8 @@ int pvsc_lattice_info(const pvsc_lattice* lat, int64_t* n_sites, int32_t* orbita
 int pvsc_set_potential(pvsc_lattice* lat, const double* V_dev, void* stream) {
   if (int rc = check_lattice(lat)) return rc;
   if (!V_dev) return set_error(PVSC_ERR_ARG, "V_dev is NULL");
-  if (lat->g.v_mode == 2) return set_error(PVSC_ERR_ARG, "the potential of this lattice is regenerated on the fly");
+  if (lat->g.v_mode == 2 || lat->g.v_mode == 3)
+    return set_error(PVSC_ERR_ARG, "the potential of this lattice is regenerated on the fly");
   if (!lat->V_dev) {
     cudaError_t e = cudaMalloc(&lat->V_dev, sizeof(double) * lat->g.n_sites);
     if (e == cudaSuccess) e = cudaMalloc(&lat->V32_dev, sizeof(float) * lat->g.n_sites);

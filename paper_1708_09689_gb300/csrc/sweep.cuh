@@ -870,7 +870,9 @@ __global__ void __launch_bounds__(256, 2) ti_sweep_flat(const __grid_constant__ 
 //   (Hx)_{c,3} = v3 x_{c,3} - t (x_{c,2} + x_{c+x,2} + x_{c+y,0})
 // (T_x couples site 0 to site 1 of cell c + x and site 3 to site 2; T_y site 0
 // to site 3 of cell c - y; T_n is the chain 0-1-2-3.)
-template <typename T, int VPT, int FEAT>
+// QD: the potential is the quantum-dot array of Eq. qdotarray, evaluated per
+// site from the carried cell coordinates (v_mode 3).
+template <typename T, int VPT, int FEAT, bool QD = false>
 __global__ void __launch_bounds__(256) gr_sweep(const __grid_constant__ Sweep p) {
   const int64_t Nx = p.g.L[0], Ny = p.g.L[1];
   const int64_t ncell = Nx * Ny;
@@ -898,6 +900,15 @@ __global__ void __launch_bounds__(256) gr_sweep(const __grid_constant__ Sweep p)
     const int64_t cxp = nbr_plus(c, x, Nx, p.g.per[0], 1);
     const int64_t cym = nbr_minus(c, y, Ny, p.g.per[1], Nx);
     const int64_t cyp = nbr_plus(c, y, Ny, p.g.per[1], Nx);
+    // the potentials first: loads issued early, and a regenerated quantum-dot
+    // array evaluated while few registers are live
+    T Vs[4];
+    if constexpr (QD) {
+      qd_cell_potentials<T>(p.qds, x, y, Vs);
+    } else {
+#pragma unroll
+      for (int o = 0; o < 4; ++o) Vs[o] = site_potential_t<T>(p.g, 4 * c + o);
+    }
     Blk<T, VPT> xc, yi;
     load_blk<T, VPT, true>(X, c, R, rc, xc);
     if (p.yin != nullptr) load_blk<T, VPT, false>(static_cast<const T*>(p.yin), c, R, rc, yi);
@@ -936,9 +947,6 @@ __global__ void __launch_bounds__(256) gr_sweep(const __grid_constant__ Sweep p)
 #pragma unroll
       for (int v = 0; v < VPT; ++v) n3[v] = cadd(n3[v], a[v]);
     }
-    T Vs[4];
-#pragma unroll
-    for (int o = 0; o < 4; ++o) Vs[o] = site_potential_t<T>(p.g, 4 * c + o);
     Blk<T, VPT> yn;
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {

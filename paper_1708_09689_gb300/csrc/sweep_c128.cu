@@ -20,6 +20,7 @@ static void* kernel_c128() {
     return reinterpret_cast<void*>(&ti_sweep<double, 1, FEAT, kAsyncDeepDepth, 2>);
   else if constexpr (MODEL == kModelWSM) return reinterpret_cast<void*>(&wsm_sweep<double, 1, FEAT>);
   else if constexpr (MODEL == kModelWSMMarch) return reinterpret_cast<void*>(&wsm_march_sweep<double, 1, FEAT>);
+  else if constexpr (MODEL == kModelGrapheneQD) return reinterpret_cast<void*>(&gr_sweep<double, 1, FEAT, true>);
   else return reinterpret_cast<void*>(&gr_sweep<double, 1, FEAT>);
 }
 
@@ -44,6 +45,7 @@ static void* pick(int model, int feat) {
     case kModelTIAsyncDeep: return pick_c128<kModelTIAsyncDeep>(feat);
     case kModelWSM: return pick_c128<kModelWSM>(feat);
     case kModelWSMMarch: return pick_c128<kModelWSMMarch>(feat);
+    case kModelGrapheneQD: return pick_c128<kModelGrapheneQD>(feat);
     default: return pick_c128<2>(feat);
   }
 }

@@ -18,6 +18,7 @@ static void* kernel_c64() {
     return reinterpret_cast<void*>(&ti_sweep<float, VPT, FEAT, kAsyncDeepDepth, 2>);
   else if constexpr (MODEL == kModelWSM) return reinterpret_cast<void*>(&wsm_sweep<float, VPT, FEAT>);
   else if constexpr (MODEL == kModelWSMMarch) return reinterpret_cast<void*>(&wsm_march_sweep<float, VPT, FEAT>);
+  else if constexpr (MODEL == kModelGrapheneQD) return reinterpret_cast<void*>(&gr_sweep<float, VPT, FEAT, true>);
   else return reinterpret_cast<void*>(&gr_sweep<float, VPT, FEAT>);
 }
 
@@ -43,6 +44,8 @@ static void* pick(int model, int vpt, int feat) {
     case kModelWSM: return vpt == 1 ? pick_c64<kModelWSM, 1>(feat) : pick_c64<kModelWSM, 2>(feat);
     case kModelWSMMarch:
       return vpt == 1 ? pick_c64<kModelWSMMarch, 1>(feat) : pick_c64<kModelWSMMarch, 2>(feat);
+    case kModelGrapheneQD:
+      return vpt == 1 ? pick_c64<kModelGrapheneQD, 1>(feat) : pick_c64<kModelGrapheneQD, 2>(feat);
     default: return vpt == 1 ? pick_c64<2, 1>(feat) : pick_c64<2, 2>(feat);
   }
 }
