@@ -442,7 +442,9 @@ typedef struct {
                   /* default tile of that R (16x12, 10x8, 8x8, 5x5, 3x3, 2x2 for R = 2..64); */
                   /* zslab = z-range of one block (0: whole columns).  Same vectors as */
                   /* two single sweeps bit for bit; needs the larger KPM work buffer */
-                  /* (four vectors) that pvsc_work_bytes reports for complex64 TI */
+                  /* (four vectors) that pvsc_work_bytes reports for complex64 TI, */
+                  /* 5 z-marching over tiles of tile_x x tile_y columns per block */
+                  /* (threads = tile_x tile_y R/vpt, a multiple of 32, at most 256) */
 } pvsc_tuning;
 
 /* Device error word of the shared-memory staged sweeps: *flag = 1 if a copy

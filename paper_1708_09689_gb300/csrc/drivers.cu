@@ -114,12 +114,22 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
     }
   LaunchShape sh = shape_for(lat, p.R, prec);
   if (sh.kernel == kKernelKpm2) sh = LaunchShape{};  // a KPM-only choice: single sweeps take the default
-  if (lat->g.model == PVSC_TI && sh.tile_x > 0 && sh.tile_y > 0)
+  p.tile_x = p.tile_y = 0;  // set below by the tiled and staged sweeps only (p may come from another launch)
+  const bool tiled = lat->g.model == PVSC_TI && sh.kernel == kKernelTiles;
+  if (lat->g.model == PVSC_TI && !tiled && sh.tile_x > 0 && sh.tile_y > 0)
     return launch_sweep_staged(lat, prec, feat, p, sh, st);
   const int vpt = vpt_tuned(sh.vpt, p.R, prec);
   p.C = p.R / vpt;
   int threads = sh.threads;
-  if (threads < 32 || threads > kMaxThreads || threads % 32 != 0 || threads % p.C != 0) threads = 256;
+  if (tiled) {  // z-marching sweep over tile_x x tile_y column tiles (checked by pvsc_set_tuning)
+    threads = sh.tile_x * sh.tile_y * p.C;
+    p.tile_x = sh.tile_x;
+    p.tile_y = sh.tile_y;
+  }
+  if (threads < 32 || threads > kMaxThreads || threads % 32 != 0 || threads % p.C != 0) {
+    threads = 256;
+    p.tile_x = p.tile_y = 0;
+  }
   int occ = 0;
   const bool flat = lat->g.model == PVSC_TI && sh.kernel == 1;
   // the prefetch ring moves 16-byte granules: not for complex64 with one vector of R > 1
@@ -149,7 +159,9 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
   } else if (lat->g.model == PVSC_TI || (wsm && !wsm_flat)) {
     // z-marching columns: TI sites, or Weyl cells (two sites along x)
     const int64_t plane = (wsm ? lat->g.L[0] / 2 : lat->g.L[0]) * lat->g.L[1], Lz = lat->g.L[2];
-    const int64_t nbx = (plane * p.C + threads - 1) / threads;
+    const int64_t nbx = p.tile_x > 0 ? ((lat->g.L[0] + p.tile_x - 1) / p.tile_x) *
+                                           ((lat->g.L[1] + p.tile_y - 1) / p.tile_y)
+                                     : (plane * p.C + threads - 1) / threads;
     int64_t zs = sh.zslab;
     if (zs <= 0) {
       int64_t nz = (6 * grid_max + nbx - 1) / nbx;
@@ -815,7 +827,19 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
     return PVSC_OK;
   }
   if (tuning->vpt < 0 || tuning->vpt > 2) return set_error(PVSC_ERR_ARG, "vpt must be 0, 1 or 2");
-  if (tuning->kernel < 0 || tuning->kernel > 4) return set_error(PVSC_ERR_ARG, "kernel must be 0 .. 4");
+  if (tuning->kernel < 0 || tuning->kernel > 5) return set_error(PVSC_ERR_ARG, "kernel must be 0 .. 5");
+  if (tuning->kernel == kKernelTiles) {
+    const int C = R / vpt_tuned(tuning->vpt, R, prec);
+    const int n = tuning->tile_x * tuning->tile_y * C;
+    if (lat->g.model != PVSC_TI || tuning->tile_x < 1 || tuning->tile_y < 1 || n % 32 || n > kMaxThreads)
+      return set_error(PVSC_ERR_ARG, "kernel 5 (column tiles) needs a TI lattice and tile_x tile_y R/VPT "
+                       "a multiple of 32, at most %d (got %d)", kMaxThreads, n);
+    if (tuning->vpt < 0 || tuning->vpt > 2 || tuning->blocks_per_sm < 0 || tuning->zslab < 0)
+      return set_error(PVSC_ERR_ARG, "invalid tuning value");
+    lat->tuning[{R, prec}] = *tuning;
+    drop_graphs(lat);
+    return PVSC_OK;
+  }
   if (tuning->kernel == kKernelKpm2) {
     if (tuning->blocks_per_sm < 0 || tuning->zslab < 0 || tuning->tile_x < 0 || tuning->tile_y < 0)
       return set_error(PVSC_ERR_ARG, "negative tuning value");

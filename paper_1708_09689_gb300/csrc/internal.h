@@ -36,7 +36,8 @@ struct LaunchShape {
   int tile_x = 0;         // > 0: shared-memory staged TI sweep with this tile
   int tile_y = 0;
   int kernel = 0;         // TI: 0 z-marching / staged, 1 flat, 2 / 3 cp.async rings,
-                          // 4 two KPM steps per sweep (tile_x x tile_y tiles)
+                          // 4 two KPM steps per sweep (tile_x x tile_y tiles),
+                          // 5 z-marching over tile_x x tile_y column tiles
 };
 
 // kernel-selector "model" values of the flat and the cp.async-prefetching TI
@@ -85,6 +86,8 @@ int launch_sweep_fx(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, bo
 
 // two KPM recurrence steps per sweep (sweep_kpm2.cu): complex64 TI lattices, R >= 2
 constexpr int kKernelKpm2 = 4;
+// z-marching TI sweep over 2D column tiles (tile_x x tile_y columns per block)
+constexpr int kKernelTiles = 5;
 int launch_kpm2_sweep(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, cudaStream_t st);
 int kpm2_check_tile(int TX, int TY, int R);
 

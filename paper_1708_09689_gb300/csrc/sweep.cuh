@@ -740,17 +740,33 @@ __global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p)
   DotAcc<T, VPT> dacc;
   dacc.init();
 
+  // column groups: runs of blockDim / C consecutive columns, or with
+  // p.tile_x > 0 tiles of tile_x x tile_y columns (in-plane y neighbours then
+  // mostly inside the block, loaded one plane earlier by their own threads)
   const int64_t ncolthr = plane * C;
-  const int64_t nbx = (ncolthr + blockDim.x - 1) / blockDim.x;
+  const int TX = p.tile_x, TY = p.tile_y;
+  const int64_t ntx = TX > 0 ? (p.g.L[0] + TX - 1) / TX : 0;
+  const int64_t nbx = TX > 0 ? ntx * ((p.g.L[1] + TY - 1) / TY) : (ncolthr + blockDim.x - 1) / blockDim.x;
   const int zs = p.zslab;
   const int64_t nzs = (Lz + zs - 1) / zs;
   const int64_t nunits = nbx * nzs;
+  const int sl = threadIdx.x >> cshift;  // column of this thread within a tile
   for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
     const int64_t bz = udiv64(u, nbx), bx = u - bz * nbx;
-    const int64_t tid = bx * blockDim.x + threadIdx.x;
-    if (tid >= ncolthr) continue;
+    int64_t col;
+    if (TX > 0) {
+      if (sl >= TX * TY) continue;
+      const int64_t ty = udiv64(bx, ntx), tx = bx - ty * ntx;
+      const int64_t x = tx * TX + sl % TX, y = ty * TY + sl / TX;
+      if (x >= p.g.L[0] || y >= p.g.L[1]) continue;
+      col = x + p.g.L[0] * y;
+    } else {
+      const int64_t tid = bx * blockDim.x + threadIdx.x;
+      if (tid >= ncolthr) continue;
+      col = tid >> cshift;
+    }
     const int64_t z0 = bz * zs, z1 = min(z0 + (int64_t)zs, Lz);
-    ti_march<T, VPT, true, DEPTH, NBUF>(p.g, X, Yin, R, rc, tid >> cshift, z0, z1, ring,
+    ti_march<T, VPT, true, DEPTH, NBUF>(p.g, X, Yin, R, rc, col, z0, z1, ring,
                            [&](int64_t s) { return site_potential_t<T>(p.g, s); },
                            [&](T Vs, const Blk<T, VPT>& xm, const Blk<T, VPT>& xc,
                                const Blk<T, VPT>& xp, const Blk<T, VPT>& ax, const Blk<T, VPT>& bx,

@@ -1,0 +1,51 @@
+"""The z-marching TI sweep over 2D column tiles (tuning kernel 5) against the
+default row-segment grouping: the per-site arithmetic is the same, so the
+vectors are bit-identical; moments differ only in the order of the dot sums."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+
+pv = pytest.importorskip("paper_1708_09689_gb300")
+pytestmark = pytest.mark.gpu
+
+CASES = [((7, 5, 6), (1, 0, 1)), ((4, 4, 4), (1, 1, 1)), ((3, 2, 5), (0, 1, 0)),
+         ((1, 3, 2), (1, 1, 1)), ((19, 13, 4), (1, 1, 0))]
+# (R, precision, vpt, tile_x, tile_y): tile_x tile_y R / vpt threads, a multiple of 32
+SHAPES = [(8, pv.C64, 2, 8, 4), (8, pv.C64, 2, 4, 4), (4, pv.C64, 2, 4, 8), (1, pv.C64, 1, 8, 4),
+          (4, pv.C128, 1, 4, 2), (8, pv.C128, 1, 4, 8), (2, pv.C64, 2, 16, 2)]
+
+
+@pytest.mark.parametrize("dims,per", CASES)
+@pytest.mark.parametrize("R,prec,vpt,tx,ty", SHAPES)
+def test_column_tiles_equal_the_default_sweep(dims, per, R, prec, vpt, tx, ty):
+    n = int(np.prod(dims))
+    lat = pv.Lattice.ti(dims, per, disorder=(1.5, 2))
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, W.disorder_potential(n, 1.5, 2))
+    cdt = torch.complex128 if prec == pv.C128 else torch.complex64
+    x = torch.from_numpy(W.gaussian_block(H.shape[0], R, 1)).to("cuda", cdt)
+    y0 = pv.apply_H(lat, x)
+    lat.set_tuning(R, prec, threads=tx * ty * R // vpt, vpt=vpt, tile_x=tx, tile_y=ty, kernel=5)
+    y1 = pv.apply_H(lat, x)
+    assert torch.equal(y0, y1)
+    ref = H @ x.cpu().numpy().astype(np.complex128)
+    tol = 1e-12 if prec == pv.C128 else 2e-6
+    assert np.linalg.norm(y1.cpu().numpy() - ref) / np.linalg.norm(ref) < tol
+    _, _, a, b = lat.spectral_bounds()
+    mu1 = pv.kpm_moments(lat, 20, a, b, r0=x / torch.linalg.vector_norm(x, dim=0), prec=prec).cpu().numpy()
+    lat.set_tuning(R, prec)
+    mu0 = pv.kpm_moments(lat, 20, a, b, r0=x / torch.linalg.vector_norm(x, dim=0), prec=prec).cpu().numpy()
+    assert np.max(np.abs(mu1 - mu0)) < 1e-10
+
+
+def test_column_tile_shapes_are_checked():
+    lat = pv.Lattice.ti((8, 8, 4), (1, 1, 1))
+    with pytest.raises(pv.PvscError, match="kernel 5"):
+        lat.set_tuning(8, pv.C64, vpt=2, tile_x=3, tile_y=3, kernel=5)  # 36 threads
+    with pytest.raises(pv.PvscError, match="kernel 5"):
+        lat.set_tuning(8, pv.C64, vpt=2, tile_x=16, tile_y=8, kernel=5)  # 512 threads
+    gl = pv.Lattice.graphene((4, 4), (1, 1))
+    with pytest.raises(pv.PvscError, match="kernel 5"):
+        gl.set_tuning(1, pv.C64, tile_x=8, tile_y=4, kernel=5)
