@@ -1053,7 +1053,7 @@ __device__ __forceinline__ void wsm_cell_update(const VecCoef<T, VPT>& cf, T V0,
 // cells only the components the update reads are loaded (x-: site 1, x+: site
 // 0, y-: the b components, y+: the a components).
 template <typename T, int VPT, int FEAT>
-__global__ void __launch_bounds__(256) wsm_sweep(const __grid_constant__ Sweep p) {
+__global__ void __launch_bounds__(256, 2) wsm_sweep(const __grid_constant__ Sweep p) {
   const int64_t NX = p.g.L[0] / 2, Ly = p.g.L[1], Lz = p.g.L[2];
   const int64_t ncell = NX * Ly * Lz;
   const int64_t plane = NX * Ly;  // cells per z plane
