@@ -727,8 +727,10 @@ __device__ __forceinline__ void ti_march(const Geometry& g, const T* __restrict_
   }
 }
 
+// complex64 with one vector per thread holds half the state of two: capped at
+// 128 registers, two 256-thread blocks (16 warps) share an SM.
 template <typename T, int VPT, int FEAT, int DEPTH = 0, int NBUF = 2>
-__global__ void __launch_bounds__(256) ti_sweep(const __grid_constant__ Sweep p) {
+__global__ void __launch_bounds__(256, (VPT == 1 && sizeof(T) == 4) ? 2 : 1) ti_sweep(const __grid_constant__ Sweep p) {
   extern __shared__ __align__(16) unsigned char ring[];  // DEPTH > 0: cp.async prefetch ring
   const int64_t plane = p.g.L[0] * p.g.L[1], Lz = p.g.L[2];
   const int R = p.R, C = p.C;
