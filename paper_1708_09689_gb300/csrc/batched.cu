@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -159,7 +160,10 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
           cf.gamma[v] = T(k == 0 ? 0.0 : -1.0);
           cf.delta[v] = T(0);
         }
-        if (active) {
+        // the Delta terms are decided once per unit, outside the march: the
+        // lattice (and its geometry) is picked at run time from the parameter
+        // block, and a per-site branch on it costs the march its load overlap
+        auto march = [&](auto with_delta) {
           // x is written by this kernel in other phases: coherent loads only (NC = false)
           ti_march<T, VPT, false, 0, 2>(L.g, X, Yin, R, rc, col, z0, z1, nullptr,
                                   [&](int64_t s) { return site_potential_t<T>(L.g, s); },
@@ -169,7 +173,8 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
                                       const Blk<T, VPT>* yi, Blk<T, VPT>& yn) {
                                     Blk<T, VPT> S, D;
                                     ti_axes(xm, xp, ax, bx, ay, by, S, D);
-                                    ti_combine(cf, Vs, xc, S, D, yi, yn, L.g);
+                                    ti_combine_core(cf, Vs, xc, S, D, yi, yn);
+                                    if constexpr (decltype(with_delta)::value) ti_add_delta(L.g, cf, xc, yn);
                                   },
                                   [&](int64_t s, const Blk<T, VPT>& xc, Blk<T, VPT>& yn) {
                                     store_blk<T, VPT>(Yout, s, R, rc, yn);
@@ -186,6 +191,10 @@ __global__ void __launch_bounds__(256) kpm_batched_kernel(const __grid_constant_
                                       dacc.add(1, v, xy);
                                     }
                                   });
+        };
+        if (active) {
+          if (L.g.has_delta) march(std::true_type{});
+          else march(std::false_type{});
         }
         dacc.flush();
         // fixed-order block reduction to one row of partials for this unit

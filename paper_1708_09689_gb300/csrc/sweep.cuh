@@ -600,11 +600,11 @@ __device__ __forceinline__ void ti_add_delta(const Geometry& g, const VecCoef<T,
 }
 
 // y_new = d_o x_o + kt (Gamma^1 S + D)_o + gamma y_in,  d_o = alpha (V - beta) +- alpha m
-// (+ the Delta terms when the geometry has them)
+// (ti_combine adds the Delta terms when the geometry has them)
 template <typename T, int VPT>
-__device__ __forceinline__ void ti_combine(const VecCoef<T, VPT>& cf, T Vs, const Blk<T, VPT>& xc,
-                                           const Blk<T, VPT>& S, const Blk<T, VPT>& D,
-                                           const Blk<T, VPT>* yi, Blk<T, VPT>& yn, const Geometry& g) {
+__device__ __forceinline__ void ti_combine_core(const VecCoef<T, VPT>& cf, T Vs, const Blk<T, VPT>& xc,
+                                                const Blk<T, VPT>& S, const Blk<T, VPT>& D,
+                                                const Blk<T, VPT>* yi, Blk<T, VPT>& yn) {
 #pragma unroll
   for (int v = 0; v < VPT; ++v) {
     const T e = fma(cf.alpha[v], Vs, -cf.ab[v]);
@@ -622,6 +622,13 @@ __device__ __forceinline__ void ti_combine(const VecCoef<T, VPT>& cf, T Vs, cons
       yn.v[o][v] = {re, im};
     }
   }
+}
+
+template <typename T, int VPT>
+__device__ __forceinline__ void ti_combine(const VecCoef<T, VPT>& cf, T Vs, const Blk<T, VPT>& xc,
+                                           const Blk<T, VPT>& S, const Blk<T, VPT>& D,
+                                           const Blk<T, VPT>* yi, Blk<T, VPT>& yn, const Geometry& g) {
+  ti_combine_core(cf, Vs, xc, S, D, yi, yn);
   if (g.has_delta) ti_add_delta(g, cf, xc, yn);
 }
 
