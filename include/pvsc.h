@@ -441,8 +441,8 @@ typedef struct {
                   /* (tile_x tile_y + 2 (tile_x + tile_y)) R/2 <= 384 threads; 0 = the */
                   /* default tile of that R (16x12, 10x8, 8x8, 5x5, 3x3, 2x2 for R = 2..64); */
                   /* zslab = z-range of one block (0: whole columns).  Same vectors as */
-                  /* two single sweeps bit for bit; needs the larger KPM work buffer */
-                  /* (four vectors) that pvsc_work_bytes reports for complex64 TI, */
+                  /* two single sweeps bit for bit; needs a KPM work buffer of four */
+                  /* vectors, which pvsc_work_bytes reports once this entry is set, */
                   /* 5 z-marching over tiles of tile_x x tile_y columns per block */
                   /* (threads = tile_x tile_y R/vpt, a multiple of 32, at most 256) */
 } pvsc_tuning;

@@ -358,9 +358,15 @@ using namespace pvsc;
 
 extern "C" {
 
-// The two-step KPM sweep exists for complex64 TI lattices with R >= 2.
+// The two-step KPM sweep exists for complex64 TI lattices with R >= 2 and runs
+// when the tuning entry of (R, prec) selects it.
 static bool kpm2_possible(const pvsc_lattice* lat, int R, int prec) {
   return lat->g.model == PVSC_TI && prec == PVSC_C64 && R >= 2;
+}
+static bool kpm2_selected(const pvsc_lattice* lat, int R, int prec) {
+  if (!kpm2_possible(lat, R, prec)) return false;
+  auto it = lat->tuning.find({R, prec});
+  return it != lat->tuning.end() && it->second.kernel == kKernelKpm2;
 }
 
 size_t pvsc_work_bytes(const pvsc_lattice* lat, int op, int R, int prec, int M) {
@@ -371,9 +377,9 @@ size_t pvsc_work_bytes(const pvsc_lattice* lat, int op, int R, int prec, int M) 
       return kWorkHeader + sizeof(double) * 2 * 2 * (size_t)lat->sm_count;
     case PVSC_OP_CHEB_STEP:
       return dots_work_bytes(lat, R);
-    case PVSC_OP_KPM:  // two vectors, four where the two-step sweep may run
+    case PVSC_OP_KPM:  // two vectors, four when the tuning in force selects the two-step sweep
       return ((dots_work_bytes(lat, R) + 255) & ~size_t(255)) +
-             (kpm2_possible(lat, R, prec) ? 4 : 2) * vec_bytes(lat, R, prec);
+             (kpm2_selected(lat, R, prec) ? 4 : 2) * vec_bytes(lat, R, prec);
     case PVSC_OP_SERIES:
       return series_layout(lat, R, prec).total;
     case PVSC_OP_ADJOINT: {
@@ -555,7 +561,7 @@ int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, u
   void* wb = wptr(work, voff + vec_bytes(lat, R, prec));
   const int64_t D = lat->g.n_sites * orbitals_of(lat->g.model);
   const LaunchShape sh = shape_for(lat, R, prec);
-  const bool two = kpm2_possible(lat, R, prec) && sh.kernel == kKernelKpm2;
+  const bool two = kpm2_selected(lat, R, prec);
   const std::vector<uint64_t> key = {1, (uint64_t)R, (uint64_t)prec, bits(r0), seed, (uint64_t)M,
                                      bits(a), bits(b), bits(mu), bits(work)};
   auto body = [&](cudaStream_t cs) -> int {

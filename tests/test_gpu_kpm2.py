@@ -141,3 +141,18 @@ def test_two_step_kpm_full_slab_against_single_steps():
     assert np.allclose(mu2[:, 0], 1.0, atol=1e-6)
     assert np.max(np.abs(mu2)) <= 1.0 + 1e-6
     assert np.max(np.abs(mu2 - mu1)) < 1e-10
+
+
+def test_two_step_work_buffer_follows_the_tuning():
+    lat, H = _pair((6, 5, 4), (1, 1, 1))
+    _, _, a, b = lat.spectral_bounds()
+    R, M = 4, 16
+    wb = lat.work_bytes(pv.OP_KPM, R, pv.C64, M)
+    lat.set_tuning(R, pv.C64, kernel=4)
+    wb4 = lat.work_bytes(pv.OP_KPM, R, pv.C64, M)
+    vec = (lat.n_sites * 4 * R * 8 + 255) // 256 * 256  # one complex64 block, 256-byte aligned
+    assert wb4 == wb + 2 * vec
+    with pytest.raises(pv.PvscError, match="work buffer"):
+        pv.kpm_moments(lat, M, a, b, R=R, prec=pv.C64, seed=1, work=pv.work_buffer(wb))
+    mu = pv.kpm_moments(lat, M, a, b, R=R, prec=pv.C64, seed=1, work=pv.work_buffer(wb4))
+    assert np.allclose(mu.cpu().numpy()[:, 0], 1.0, atol=1e-6)
