@@ -96,3 +96,31 @@ def test_host_hermitian_jacobi_matches_numpy(libpath, n, seed):
     assert np.max(np.abs(w - np.linalg.eigvalsh(A))) < 1e-13 * scale
     assert np.max(np.abs(A @ V - V * w)) < 1e-12 * scale
     assert np.max(np.abs(V.conj().T @ V - np.eye(n))) < 1e-12
+
+
+@pytest.mark.parametrize("cname,pyname", [("pvsc_lattice_desc", "LatticeDesc"), ("pvsc_tuning", "Tuning"),
+                                          ("pvsc_chebfd_params", "ChebFDParams")])
+def test_binding_structs_match_the_c_layout(libpath, tmp_path, cname, pyname):
+    # the ctypes mirrors of the C structs: same size and the same offset for every field
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mod = pytest.importorskip("paper_1708_09689_gb300")
+    py = getattr(mod, pyname)
+    fields = [f[0] for f in py._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "pvsc.h"', "int main(void) {",
+             f'  printf("size %zu\\n", sizeof({cname}));']
+    lines += [f'  printf("{f} %zu\\n", offsetof({cname}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                  text=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(py)
+    for f in fields:
+        assert int(out[f]) == getattr(py, f).offset, f
