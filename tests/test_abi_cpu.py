@@ -77,6 +77,34 @@ def test_argument_errors_are_reported_without_a_device(libpath):
     assert lib.pvsc_work_bytes(None, 0, 1, 0, 0) == 0
 
 
+def test_quantum_dot_descriptor_errors_without_a_device(libpath):
+    # PVSC_V_QDOT is checked before any device call: graphene only, 1..16 dots per row,
+    # positive finite radius and width, finite heights
+    import paper_1708_09689_gb300 as pv
+    lib = pv.lib()
+    h = ctypes.c_void_p()
+
+    def desc(model=pv.GRAPHENE, count=2, radius=3.0, V0=0.1, width=1.0, dV=0.0):
+        d = pv.LatticeDesc()
+        d.model = model
+        d.dims[0], d.dims[1], d.dims[2] = 8, 8, (4 if model == pv.TI else 1)
+        d.t = 1.0
+        d.v_source = pv.V_QDOT
+        d.qd_count, d.qd_radius, d.qd_V0, d.qd_width, d.qd_dV = count, radius, V0, width, dV
+        return d
+
+    for bad, word in [(desc(model=pv.TI), b"graphene"), (desc(count=0), b"qd_count"),
+                      (desc(count=17), b"qd_count"), (desc(radius=0.0), b"radius"),
+                      (desc(width=-1.0), b"width"), (desc(V0=float("nan")), b"V0"),
+                      (desc(dV=float("inf")), b"dV")]:
+        assert lib.pvsc_lattice_create(ctypes.byref(bad), None, ctypes.byref(h)) == pv.PVSC_ERR_ARG
+        assert word in lib.pvsc_last_error()
+    d = desc()
+    d.v_source = 6  # past the last potential source
+    assert lib.pvsc_lattice_create(ctypes.byref(d), None, ctypes.byref(h)) == pv.PVSC_ERR_ARG
+    assert b"v_source" in lib.pvsc_last_error()
+
+
 @pytest.mark.parametrize("n,seed", [(1, 0), (7, 1), (40, 2), (64, 3)])
 def test_host_hermitian_jacobi_matches_numpy(libpath, n, seed):
     # the small dense eigenproblem of ChebFD's Rayleigh-Ritz step, host code only
