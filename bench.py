@@ -44,7 +44,10 @@ UNIT = "GLUP/s"
 # kernel at the benchmark size, from the ncu capture summarised in
 # profiles/ti_sweep_c64_R8_ncu.md (a half-depth slab, scaled by the number of sites).  It is
 # reported only while the kernel sources still hash to the captured version.
-TRAFFIC = {("ti_slab", 8): {"bytes_per_launch": 3.222e9, "source_sha256_16": "44e9b79b741166d7"}}
+# DRAM bytes of one launch of the benchmark's sweep (ncu, scaled to the slab), per
+# (workload, R, kernel); reported only while the kernel sources hash the same
+TRAFFIC = {("ti_slab", 8, "ti_sweep"): {"bytes_per_launch": 3.220e9, "source_sha256_16": "df26e831c975b98f"},
+           ("ti_slab", 8, "ti_sweep_xmarch"): {"bytes_per_launch": 3.222e9, "source_sha256_16": "df26e831c975b98f"}}
 KERNEL_SOURCES = ("paper_1708_09689_gb300/csrc/sweep.cuh", "paper_1708_09689_gb300/csrc/common.cuh")
 
 
@@ -663,6 +666,10 @@ def main():
         bytes_per_lup = 64.0 + 2.0 / R
         launches = 1 + (sweeps - 1) // 2 + (sweeps - 1) % 2
         kname = "ti_kpm2_sweep (complex64, two KPM steps per sweep)"
+    elif bool(tuning) and tuning.get("kernel") == 6:
+        bytes_per_lup = 96.0 + 4.0 / R
+        launches = sweeps
+        kname = f"ti_sweep_xmarch<float,{tuning.get('vpt') or 2},F_DOTS> (complex64 KPM sweep marching along x)"
     else:
         bytes_per_lup = 96.0 + 4.0 / R      # x 32 + y_in 32 + y_out 32 (B), fp32 V 4 per site
         launches = sweeps
@@ -674,7 +681,8 @@ def main():
                 "frac": round(achieved / peak, 4), "traffic": None, "kernel": kname,
                 "bytes_per_lup": bytes_per_lup, "peak_kind": f"{peak_kind} hbm_gbs",
                 "launch_ms": round(launch_ms, 4)}
-    tr = TRAFFIC.get(("ti_slab", R)) if tuple(dims) == tuple(W.CONFIG_TI_SLAB.dims) else None
+    kkey = kname.split("<")[0]
+    tr = TRAFFIC.get(("ti_slab", R, kkey)) if tuple(dims) == tuple(W.CONFIG_TI_SLAB.dims) else None
     if tr and not two_step and tr["source_sha256_16"] == kernel_source_hash():
         roofline["traffic"] = tr["bytes_per_launch"]
         roofline["traffic_over_algorithmic"] = round(tr["bytes_per_launch"] / (bytes_per_lup * n_sites * R), 3)

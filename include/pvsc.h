@@ -444,7 +444,8 @@ typedef struct {
                   /* two single sweeps bit for bit; needs a KPM work buffer of four */
                   /* vectors, which pvsc_work_bytes reports once this entry is set, */
                   /* 5 z-marching over tiles of tile_x x tile_y columns per block */
-                  /* (threads = tile_x tile_y R/vpt, a multiple of 32, at most 256) */
+                  /* (threads = tile_x tile_y R/vpt, a multiple of 32, at most 256), */
+                  /* 6 marching along x over lines (y, z), zslab = x-segment length */
 } pvsc_tuning;
 
 /* Device error word of the shared-memory staged sweeps: *flag = 1 if a copy

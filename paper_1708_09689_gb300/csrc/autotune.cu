@@ -160,6 +160,8 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
         const int tiles5[][2] = {{4, 4}, {8, 4}, {4, 8}, {8, 8}, {16, 4}, {16, 2}, {2, 8}};
         for (const auto& t : tiles5)
           if (t[0] * t[1] * C == th) cands.push_back(pvsc_tuning{th, 0, 0, 0.f, vpt, t[0], t[1], 5});
+        // marching along x (lattices with a short z extent)
+        if (lat->g.L[0] > lat->g.L[2]) cands.push_back(pvsc_tuning{th, 0, 0, 0.f, vpt, 0, 0, 6});
         if (!(prec == PVSC_C64 && vpt == 1 && R > 1)) {
           for (int zs : {0, 16}) cands.push_back(pvsc_tuning{th, 0, zs, 0.f, vpt, 0, 0, 2});
           cands.push_back(pvsc_tuning{th, 0, 0, 0.f, vpt, 0, 0, 3});

@@ -140,7 +140,9 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
   const bool wsm = lat->g.model == PVSC_WSM;
   const bool wsm_flat = wsm && (lat->tuning.count({p.R, prec}) == 0 || sh.kernel == 1);
   const bool qd = lat->g.model == PVSC_GRAPHENE && lat->g.v_mode == 3;
-  const int model = flat ? kModelTIFlat
+  const bool xmarch = lat->g.model == PVSC_TI && sh.kernel == kKernelXMarch;
+  const int model = xmarch ? kModelTIXMarch
+                    : flat ? kModelTIFlat
                     : async ? (sh.kernel == 2 ? kModelTIAsync : kModelTIAsyncDeep)
                     : wsm ? (wsm_flat ? kModelWSM : kModelWSMMarch)
                     : qd ? kModelGrapheneQD
@@ -156,6 +158,20 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
   int64_t units;
   if (flat) {
     units = (lat->g.n_sites * p.C + threads - 1) / threads;
+  } else if (xmarch) {
+    // lines (y, z) marched along x; x-segments of p.zslab sites
+    const int64_t Lx = lat->g.L[0];
+    const int64_t nbx = (lat->g.L[1] * lat->g.L[2] * p.C + threads - 1) / threads;
+    int64_t xs = sh.zslab;
+    if (xs <= 0) {
+      int64_t nx = (6 * grid_max + nbx - 1) / nbx;
+      if (nx < 1) nx = 1;
+      if (nx > Lx) nx = Lx;
+      xs = (Lx + nx - 1) / nx;
+    }
+    if (xs > Lx) xs = Lx;
+    p.zslab = (int)xs;
+    units = nbx * ((Lx + xs - 1) / xs);
   } else if (lat->g.model == PVSC_TI || (wsm && !wsm_flat)) {
     // z-marching columns: TI sites, or Weyl cells (two sites along x)
     const int64_t plane = (wsm ? lat->g.L[0] / 2 : lat->g.L[0]) * lat->g.L[1], Lz = lat->g.L[2];
@@ -833,7 +849,9 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
     return PVSC_OK;
   }
   if (tuning->vpt < 0 || tuning->vpt > 2) return set_error(PVSC_ERR_ARG, "vpt must be 0, 1 or 2");
-  if (tuning->kernel < 0 || tuning->kernel > 5) return set_error(PVSC_ERR_ARG, "kernel must be 0 .. 5");
+  if (tuning->kernel < 0 || tuning->kernel > 6) return set_error(PVSC_ERR_ARG, "kernel must be 0 .. 6");
+  if (tuning->kernel == kKernelXMarch && lat->g.model != PVSC_TI)
+    return set_error(PVSC_ERR_ARG, "kernel 6 (marching along x) needs a TI lattice");
   if (tuning->kernel == kKernelTiles) {
     const int C = R / vpt_tuned(tuning->vpt, R, prec);
     const int n = tuning->tile_x * tuning->tile_y * C;

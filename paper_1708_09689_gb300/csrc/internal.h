@@ -37,7 +37,7 @@ struct LaunchShape {
   int tile_y = 0;
   int kernel = 0;         // TI: 0 z-marching / staged, 1 flat, 2 / 3 cp.async rings,
                           // 4 two KPM steps per sweep (tile_x x tile_y tiles),
-                          // 5 z-marching over tile_x x tile_y column tiles
+                          // 5 z-marching over tile_x x tile_y column tiles, 6 marching along x
 };
 
 // kernel-selector "model" values of the flat and the cp.async-prefetching TI
@@ -48,6 +48,7 @@ constexpr int kModelTIAsyncDeep = 5;  // ring of the two HBM streams, three plan
 constexpr int kModelWSM = 8;         // Weyl semimetal flat cell sweep
 constexpr int kModelWSMMarch = 9;    // Weyl semimetal z-marching cell sweep
 constexpr int kModelGrapheneQD = 10; // graphene sweep with the regenerated quantum-dot array
+constexpr int kModelTIXMarch = 11;   // TI sweep marching along x (tuning kernel 6)
 constexpr int kAsyncDepth = 1;
 constexpr int kAsyncDeepDepth = 3;
 // ring: (depth + 1) slots x buffers x 4 granules of 16 bytes per thread
@@ -88,6 +89,8 @@ int launch_sweep_fx(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, bo
 constexpr int kKernelKpm2 = 4;
 // z-marching TI sweep over 2D column tiles (tile_x x tile_y columns per block)
 constexpr int kKernelTiles = 5;
+// TI sweep marching along x instead of z (short z extents)
+constexpr int kKernelXMarch = 6;
 int launch_kpm2_sweep(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, cudaStream_t st);
 int kpm2_check_tile(int TX, int TY, int R);
 

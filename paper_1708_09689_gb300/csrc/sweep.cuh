@@ -797,6 +797,74 @@ __global__ void __launch_bounds__(256, (VPT == 1 && sizeof(T) == 4) ? 2 : 1) ti_
   }
 }
 
+// TI sweep marching along x (for lattices whose z extent is short): a thread
+// keeps sites x-1, x, x+1 of its line (y, z) in registers and reads the y and
+// z neighbours, which the threads of neighbouring lines load, from L1/L2.  The
+// neighbours enter ti_axes in the same order as in the z-march (z pair, x
+// pair, y pair), so the result equals the z-marching sweep's bit for bit.
+// Units: groups of blockDim / C lines (y fastest) times x-segments of p.zslab
+// sites (whole lines when p.zslab >= Lx).
+template <typename T, int VPT, int FEAT>
+__global__ void __launch_bounds__(256) ti_sweep_xmarch(const __grid_constant__ Sweep p) {
+  const Geometry& g = p.g;
+  const int64_t Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
+  const int R = p.R, C = p.C;
+  const int rc = threadIdx.x % C;
+  const int cshift = __ffs(C) - 1;
+  const VecCoef<T, VPT> cf = load_coef<T, VPT>(p, rc);
+  const T* __restrict__ X = static_cast<const T*>(p.x);
+  const T* __restrict__ Yin = static_cast<const T*>(p.yin);
+  DotAcc<T, VPT> dacc;
+  dacc.init();
+  const int64_t nlines = Ly * Lz, nthr_lines = nlines * C;
+  const int64_t nbx = (nthr_lines + blockDim.x - 1) / blockDim.x;
+  const int64_t xs = p.zslab, nxs = (Lx + xs - 1) / xs;
+  const int64_t nunits = nbx * nxs;
+  const int64_t SS = (int64_t)8 * R, cofs = 2 * rc * VPT;
+  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int64_t bxs = udiv64(u, nbx), bl = u - bxs * nbx;
+    const int64_t tid = bl * blockDim.x + threadIdx.x;
+    if (tid >= nthr_lines) continue;
+    const int64_t line = tid >> cshift;
+    const int64_t z = udiv64(line, Ly), y = line - z * Ly;
+    const int64_t x0 = bxs * xs, x1 = min(x0 + xs, Lx);
+    const int64_t base = Lx * (y + Ly * z);  // site of x = 0 on this line
+    // neighbour lines (site offsets), -1: absent
+    const int64_t lym = nbr_minus(base, y, Ly, g.per[1], Lx), lyp = nbr_plus(base, y, Ly, g.per[1], Lx);
+    const int64_t lzm = nbr_minus(base, z, Lz, g.per[2], Lx * Ly), lzp = nbr_plus(base, z, Lz, g.per[2], Lx * Ly);
+    auto at = [&](int64_t site) { return X + site * SS + cofs; };
+    Blk<T, VPT> xm, xc, xp;
+    load_at<T, VPT, true>(at(base + x0), R, xc);
+    {
+      const int64_t q = nbr_minus(x0, x0, Lx, g.per[0], 1);
+      if (q >= 0) load_at<T, VPT, true>(at(base + q), R, xm); else zero_blk(xm);
+    }
+    for (int64_t x = x0; x < x1; ++x) {
+      const int64_t s = base + x;
+      const int64_t q = nbr_plus(x, x, Lx, g.per[0], 1);
+      if (q >= 0) load_at<T, VPT, true>(at(base + q), R, xp); else zero_blk(xp);
+      Blk<T, VPT> yi, za, zb, ya, yb, S, D, yn;
+      if (Yin != nullptr) load_at<T, VPT, false>(Yin + s * SS + cofs, R, yi);
+      if (lzm >= 0) load_at<T, VPT, true>(at(lzm + x), R, za); else zero_blk(za);
+      if (lzp >= 0) load_at<T, VPT, true>(at(lzp + x), R, zb); else zero_blk(zb);
+      if (lym >= 0) load_at<T, VPT, true>(at(lym + x), R, ya); else zero_blk(ya);
+      if (lyp >= 0) load_at<T, VPT, true>(at(lyp + x), R, yb); else zero_blk(yb);
+      const T Vs = site_potential_t<T>(g, s);
+      ti_axes(za, zb, xm, xp, ya, yb, S, D);
+      ti_combine(cf, Vs, xc, S, D, Yin != nullptr ? &yi : nullptr, yn, g);
+      const int64_t sites[4] = {s, s, s, s};
+      epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
+      xm = xc;
+      xc = xp;
+    }
+    if constexpr (has_dots(FEAT)) dacc.flush();
+  }
+  if constexpr (has_dots(FEAT)) {
+    dacc.flush();
+    reduce_dots<VPT>(p, dacc.d);
+  }
+}
+
 // Flat TI sweep: one (site, vector chunk) per thread and pass, no state
 // carried between planes.  The six neighbours are folded into S and D one at
 // a time (each load consumed at once), which keeps the register footprint

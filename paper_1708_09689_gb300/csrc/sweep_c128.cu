@@ -21,6 +21,7 @@ static void* kernel_c128() {
   else if constexpr (MODEL == kModelWSM) return reinterpret_cast<void*>(&wsm_sweep<double, 1, FEAT>);
   else if constexpr (MODEL == kModelWSMMarch) return reinterpret_cast<void*>(&wsm_march_sweep<double, 1, FEAT>);
   else if constexpr (MODEL == kModelGrapheneQD) return reinterpret_cast<void*>(&gr_sweep<double, 1, FEAT, true>);
+  else if constexpr (MODEL == kModelTIXMarch) return reinterpret_cast<void*>(&ti_sweep_xmarch<double, 1, FEAT>);
   else return reinterpret_cast<void*>(&gr_sweep<double, 1, FEAT>);
 }
 
@@ -46,6 +47,7 @@ static void* pick(int model, int feat) {
     case kModelWSM: return pick_c128<kModelWSM>(feat);
     case kModelWSMMarch: return pick_c128<kModelWSMMarch>(feat);
     case kModelGrapheneQD: return pick_c128<kModelGrapheneQD>(feat);
+    case kModelTIXMarch: return pick_c128<kModelTIXMarch>(feat);
     default: return pick_c128<2>(feat);
   }
 }

@@ -19,6 +19,7 @@ static void* kernel_c64() {
   else if constexpr (MODEL == kModelWSM) return reinterpret_cast<void*>(&wsm_sweep<float, VPT, FEAT>);
   else if constexpr (MODEL == kModelWSMMarch) return reinterpret_cast<void*>(&wsm_march_sweep<float, VPT, FEAT>);
   else if constexpr (MODEL == kModelGrapheneQD) return reinterpret_cast<void*>(&gr_sweep<float, VPT, FEAT, true>);
+  else if constexpr (MODEL == kModelTIXMarch) return reinterpret_cast<void*>(&ti_sweep_xmarch<float, VPT, FEAT>);
   else return reinterpret_cast<void*>(&gr_sweep<float, VPT, FEAT>);
 }
 
@@ -46,6 +47,8 @@ static void* pick(int model, int vpt, int feat) {
       return vpt == 1 ? pick_c64<kModelWSMMarch, 1>(feat) : pick_c64<kModelWSMMarch, 2>(feat);
     case kModelGrapheneQD:
       return vpt == 1 ? pick_c64<kModelGrapheneQD, 1>(feat) : pick_c64<kModelGrapheneQD, 2>(feat);
+    case kModelTIXMarch:
+      return vpt == 1 ? pick_c64<kModelTIXMarch, 1>(feat) : pick_c64<kModelTIXMarch, 2>(feat);
     default: return vpt == 1 ? pick_c64<2, 1>(feat) : pick_c64<2, 2>(feat);
   }
 }

@@ -49,3 +49,36 @@ def test_column_tile_shapes_are_checked():
     gl = pv.Lattice.graphene((4, 4), (1, 1))
     with pytest.raises(pv.PvscError, match="kernel 5"):
         gl.set_tuning(1, pv.C64, tile_x=8, tile_y=4, kernel=5)
+
+
+XCASES = CASES + [((2, 5, 3), (1, 1, 0)), ((1, 4, 3), (1, 0, 1)), ((24, 3, 2), (0, 1, 1))]
+
+
+@pytest.mark.parametrize("dims,per", XCASES)
+@pytest.mark.parametrize("R,prec,vpt,threads,xseg", [(8, pv.C64, 2, 128, 0), (8, pv.C64, 2, 64, 3),
+                                                     (1, pv.C64, 1, 128, 0), (4, pv.C128, 1, 128, 5),
+                                                     (64, pv.C64, 1, 128, 0)])
+def test_march_along_x_equals_the_default_sweep(dims, per, R, prec, vpt, threads, xseg):
+    n = int(np.prod(dims))
+    lat = pv.Lattice.ti(dims, per, disorder=(1.5, 2), delta1=0.2)
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, W.disorder_potential(n, 1.5, 2), 0.2, 0.0)
+    cdt = torch.complex128 if prec == pv.C128 else torch.complex64
+    x = torch.from_numpy(W.gaussian_block(H.shape[0], R, 1)).to("cuda", cdt)
+    y0 = pv.apply_H(lat, x)
+    _, _, a, b = lat.spectral_bounds()
+    r0 = x / torch.linalg.vector_norm(x, dim=0)
+    mu0 = pv.kpm_moments(lat, 20, a, b, r0=r0, prec=prec).cpu().numpy()
+    lat.set_tuning(R, prec, threads=threads, vpt=vpt, zslab=xseg, kernel=6)
+    y1 = pv.apply_H(lat, x)
+    assert torch.equal(y0, y1)  # same arithmetic in the same order
+    ref = H @ x.cpu().numpy().astype(np.complex128)
+    tol = 1e-12 if prec == pv.C128 else 2e-6
+    assert np.linalg.norm(y1.cpu().numpy() - ref) / np.linalg.norm(ref) < tol
+    mu1 = pv.kpm_moments(lat, 20, a, b, r0=r0, prec=prec).cpu().numpy()
+    assert np.max(np.abs(mu1 - mu0)) < 1e-10
+
+
+def test_march_along_x_needs_a_ti_lattice():
+    gl = pv.Lattice.graphene((4, 4), (1, 1))
+    with pytest.raises(pv.PvscError, match="kernel 6"):
+        gl.set_tuning(1, pv.C64, kernel=6)
