@@ -82,3 +82,31 @@ def test_march_along_x_needs_a_ti_lattice():
     gl = pv.Lattice.graphene((4, 4), (1, 1))
     with pytest.raises(pv.PvscError, match="kernel 6"):
         gl.set_tuning(1, pv.C64, kernel=6)
+
+
+@pytest.mark.parametrize("prec,tol", [(pv.C128, 1e-12), (pv.C64, 1e-5)])
+def test_march_along_x_series_propagation_and_step(prec, tol):
+    # the accumulating (series) and fused-step features of the sweep marching along x
+    dims, per = (9, 4, 3), (1, 0, 1)
+    n = int(np.prod(dims))
+    lat = pv.Lattice.ti(dims, per, disorder=(1.0, 6))
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, W.disorder_potential(n, 1.0, 6))
+    R = 4
+    lat.set_tuning(R, prec, threads=128, vpt=2 if prec == pv.C64 else 1, kernel=6)
+    _, _, a, b = lat.spectral_bounds()
+    x = W.gaussian_block(H.shape[0], R, 3)
+    x /= np.linalg.norm(x, axis=0)
+    psi = torch.from_numpy(x).cuda()
+    pv.cheb_propagate(lat, psi, 0.6, 3, a, b, prec=prec)
+    ref = O.propagate(H, x, 0.6, 3, a, b)
+    assert np.linalg.norm(psi.cpu().numpy() - ref) / np.linalg.norm(ref) < tol
+    cdt = torch.complex128 if prec == pv.C128 else torch.complex64
+    xs = torch.from_numpy(x).to("cuda", cdt)
+    y0 = W.gaussian_block(H.shape[0], R, 4)
+    yt = torch.from_numpy(y0).to("cuda", cdt)
+    pv.cheb_step(lat, xs, yt, [0.3] * R, [0.1] * R, [-1.0] * R)
+    xr = xs.cpu().numpy().astype(np.complex128)
+    yr, _, _ = O.cheb_step(H, xr, torch.from_numpy(y0).to(cdt).numpy().astype(np.complex128),
+                           [0.3] * R, [0.1] * R, [-1.0] * R)
+    got = yt.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - yr) / np.linalg.norm(yr) < (1e-12 if prec == pv.C128 else 2e-6)
