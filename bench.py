@@ -40,12 +40,10 @@ import workloads as W  # noqa: E402
 METRIC = "stencil GLUP/s & %HBM roofline: FP32/batched vs plain FP64, same accuracy"
 UNIT = "GLUP/s"
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the benchmark
-# kernel at the benchmark size, from the ncu capture summarised in
-# profiles/ti_sweep_c64_R8_ncu.md (a half-depth slab, scaled by the number of sites).  It is
-# reported only while the kernel sources still hash to the captured version.
-# DRAM bytes of one launch of the benchmark's sweep (ncu, scaled to the slab), per
-# (workload, R, kernel); reported only while the kernel sources hash the same
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# benchmark's sweep, from an ncu capture of a half-depth slab scaled by the number of
+# sites, per (workload, R, kernel); reported only while the kernel sources still hash to
+# the captured version
 TRAFFIC = {("ti_slab", 8, "ti_sweep"): {"bytes_per_launch": 3.220e9, "source_sha256_16": "df26e831c975b98f"},
            ("ti_slab", 8, "ti_sweep_xmarch"): {"bytes_per_launch": 3.222e9, "source_sha256_16": "df26e831c975b98f"}}
 KERNEL_SOURCES = ("paper_1708_09689_gb300/csrc/sweep.cuh", "paper_1708_09689_gb300/csrc/common.cuh")
@@ -70,8 +68,8 @@ def parse():
     ap.add_argument("--M", type=int, default=2048)
     ap.add_argument("--W", type=float, default=2.0)
     ap.add_argument("--dims", type=int, nargs=3, default=list(W.CONFIG_TI_SLAB.dims))
-    ap.add_argument("--fp64-moments", type=int, default=64,
-                    help="moments of the complex128 comparison run")
+    ap.add_argument("--fp64-moments", type=int, default=0,
+                    help="moments of the complex128 comparison run (0: all M moments)")
     ap.add_argument("--no-compare", action="store_true", help="skip the complex128 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -171,31 +169,125 @@ def measured_peaks():
 
 
 # --------------------------------------------------------------------------- CPU baseline
-def cpu_baseline(dims, R, Wd, budget_s=15.0):
-    """The fp64 CSR oracle timed on a bounded sample of the same workload:
-    a 4-plane slab of the lattice (same x/y extent and couplings), R vectors,
-    as many KPM recurrence steps as fit the budget."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_worker(conn, dims, R, Wd, seed_r):
+    """One host core: the fp64 CSR oracle on the bounded sample, driven by
+    ("run", seconds) messages; replies (spMVM steps, seconds) per run."""
     import oracle as O
-    sdims = (dims[0], dims[1], min(4, dims[2]))
-    n = sdims[0] * sdims[1] * sdims[2]
+    n = dims[0] * dims[1] * dims[2]
     V = W.disorder_potential(n, Wd, 2)
-    H = O.ti_hamiltonian(sdims, (1, 1, 0), 1.0, 2.0, V)
+    H = O.ti_hamiltonian(dims, (1, 1, 0), 1.0, 2.0, V)
     a, b = O.cheb_scale(*O.gershgorin(H))
-    r = W.random_phase_block(4 * n, R, 3)
-    O.kpm_moments(H, r, 4, a, b)  # warm
-    steps, t0 = 0, time.perf_counter()
+    r = W.random_phase_block(4 * n, R, seed_r)
+    O.kpm_moments(H, r, 3, a, b)  # warm
+    conn.send("ready")
     M = 8
     while True:
-        O.kpm_moments(H, r, M, a, b)
-        steps += M - 1
-        if time.perf_counter() - t0 > budget_s or steps > 4000:
+        msg = conn.recv()
+        if msg[0] != "run":
             break
-    dt = time.perf_counter() - t0
-    value = n * R * steps / dt / 1e9
-    return {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"fp64 CSR oracle KPM recurrence (scipy, single thread) on a "
-                      f"{sdims[0]}x{sdims[1]}x{sdims[2]} slab of the workload, R={R}, "
-                      f"{steps} spMVM steps in {dt:.1f} s"}
+        steps, t0 = 0, time.perf_counter()
+        while True:
+            O.kpm_moments(H, r, M, a, b)
+            steps += M - 1
+            if time.perf_counter() - t0 > msg[1]:
+                break
+        conn.send((steps, time.perf_counter() - t0))
+    conn.close()
+
+
+class OracleOnHostCores:
+    """The fp64 CSR oracle timed on every host core: one spawned process per
+    core runs the oracle's KPM recurrence on its own block of R random-phase
+    vectors over a bounded sample of the workload (a 4-plane slab of the lattice,
+    the same x/y extent, couplings and disorder).  The processes start together;
+    the rate is all processes' lattice updates over the longest of their times."""
+
+    def __init__(self, dims, R, Wd, cores=None):
+        import multiprocessing as mp
+        self.sdims = (dims[0], dims[1], min(4, dims[2]))
+        self.R = R
+        self.cores = cores or host_cores()
+        ctx = mp.get_context("spawn")
+        env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in env_keep:
+            os.environ[k] = "1"   # one thread per worker process
+        self.conns, self.procs = [], []
+        try:
+            for i in range(self.cores):
+                a, b = ctx.Pipe()
+                p = ctx.Process(target=_oracle_worker, args=(b, self.sdims, R, Wd, 3 + i), daemon=True)
+                p.start()
+                self.conns.append(a)
+                self.procs.append(p)
+        finally:
+            for k, v in env_keep.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        for c in self.conns:
+            assert c.recv() == "ready"
+
+    def measure(self, seconds: float) -> dict:
+        for c in self.conns:
+            c.send(("run", seconds))
+        res = [c.recv() for c in self.conns]
+        steps = sum(r[0] for r in res)
+        dt = max(r[1] for r in res)
+        n = self.sdims[0] * self.sdims[1] * self.sdims[2]
+        value = n * self.R * steps / dt / 1e9
+        return {"value": round(value, 5), "unit": UNIT, "cores": self.cores, "kind": "oracle",
+                "cpu_model": cpu_model(),
+                "sample": f"fp64 CSR oracle KPM recurrence (scipy), one process per host core "
+                          f"({self.cores}), each on its own block of R={self.R} random-phase vectors "
+                          f"over a {self.sdims[0]}x{self.sdims[1]}x{self.sdims[2]} slab of the workload "
+                          f"(same x/y extent, couplings, disorder): {steps} spMVM block steps in "
+                          f"{dt:.1f} s; the per-LUP rate is extrapolated to the full slab"}
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(("stop",))
+            except (OSError, BrokenPipeError):
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+
+
+def cpu_baseline(dims, R, Wd, budget_s=15.0):
+    """The oracle on all host cores, on a bounded sample of the workload."""
+    ob = OracleOnHostCores(dims, R, Wd)
+    try:
+        return ob.measure(budget_s)
+    finally:
+        ob.close()
 
 
 def slab_config(args) -> dict:
@@ -211,14 +303,17 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    cb = cpu_baseline(args.dims, args.R, args.W, budget_s=8.0)
-    vals = []
-    for _ in range(args.warmup):
-        cpu_baseline(args.dims, args.R, args.W, budget_s=2.0)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(args.dims, args.R, args.W, budget_s=4.0)["value"])
-    elapsed = time.perf_counter() - t0
+    ob = OracleOnHostCores(args.dims, args.R, args.W)
+    try:
+        for _ in range(args.warmup):
+            ob.measure(1.0)
+        vals, t0 = [], time.perf_counter()
+        for _ in range(args.steps):
+            cb = ob.measure(3.0)
+            vals.append(cb["value"])
+        elapsed = time.perf_counter() - t0
+    finally:
+        ob.close()
     value = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * elapsed / args.steps, 1),
@@ -693,7 +788,7 @@ def main():
     # ---- complex128 / fp64 comparison (same lattice, same start block, fewer moments)
     compare = None
     if not args.no_compare:
-        Mc = args.fp64_moments
+        Mc = min(args.fp64_moments or M, M)
         if not args.no_autotune:
             lat.autotune(R, pv.C128)
         r0d = r0.to(torch.complex128)
@@ -708,9 +803,15 @@ def main():
         barrier()
         ms128 = c0.elapsed_time(c1)
         v128 = n_sites * R * ((Mc + 1) // 2) / (ms128 * 1e-3) / 1e9
-        err = float((mu64[:, :Mc] - mu128).abs().max().item())
+        # complex64 moment error against complex128 on the same start block, per moment
+        # (max over the R vectors, relative to mu_0), reported in bands of 128 moments
+        dmu = ((mu64[:, :Mc] - mu128).abs() / mu128[:, :1].abs()).amax(dim=0).cpu().numpy()
+        band = 128
         compare = {"c128_glups": round(v128, 3), "c64_over_c128": round(value / world / v128, 2),
-                   "c128_moments": Mc, "c64_vs_c128_max_dmu": err,
+                   "c128_moments": Mc, "c64_vs_c128_max_dmu": float(dmu.max()),
+                   "c64_vs_c128_argmax_moment": int(dmu.argmax()),
+                   "c64_vs_c128_dmu_by_band": {f"{lo}-{min(lo + band, Mc) - 1}": float(dmu[lo:lo + band].max())
+                                               for lo in range(0, Mc, band)},
                    "c128_bound": "fp64 pipe (0.50 T instr/s measured on GB300)"}
         del w128
         # fixed-point vectors of the same size (exact integer stencil): same start block
@@ -726,7 +827,7 @@ def main():
         vq = n_sites * R * ((Mc + 1) // 2) / (msq * 1e-3) / 1e9
         bq = 192.0 + 16.0 / R  # x, y_in, y_out 64 B each; per-site (d+, d-) 16 B
         compare.update({"q64_glups": round(vq, 3), "q64_over_c128": round(vq / v128, 2),
-                        "q64_vs_c128_max_dmu": float((muq - mu128).abs().max().item()),
+                        "q64_vs_c128_max_dmu": float(((muq - mu128).abs() / mu128[:, :1].abs()).max().item()),
                         "q64_bytes_per_lup": bq,
                         "q64_hbm_frac": round(bq * vq / peak, 4),
                         "q64_note": "complex128-sized Q4.59 fixed-point vectors, exact integer stencil; "

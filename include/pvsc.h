@@ -212,8 +212,9 @@ int pvsc_cheb_step(const pvsc_lattice* lat, int R, int prec, const void* x, void
  * results except `work`.  Its dot-product scratch is a 2 MiB array inside the
  * library image; nothing is allocated.  Sizes that need more scratch than
  * that (on a 152-SM GB300: R >= 32 with dots) are rejected with PVSC_ERR_ARG.
- * The first call on a device looks up the array's device address (make it
- * before any stream capture) and the current device must be the lattice's.
+ * Every call looks up the array's device address on the current device,
+ * which must be the lattice's; the first call on a device also loads the
+ * library's module there (make it before any stream capture).
  * All calls on a device share the array: calls whose kernels overlap on the
  * GPU race, so order them on one stream.  With dot_flags == 0 it needs no
  * scratch at all.

@@ -356,7 +356,7 @@ def kpm_moments(lat: Lattice, M: int, a: float, b: float, R: int = 1, prec: int 
     """Per-vector KPM moments mu[r, k] = <r|T_k(H~)|r>, a float64 tensor (R, M)."""
     if r0 is not None:
         if prec == Q64 and r0.dtype != torch.complex128:
-            raise PvscError("Q64 moments take a complex128 start block")
+            raise PvscError(PVSC_ERR_ARG, "Q64 moments take a complex128 start block")
         R = block_R(r0)
         prec = Q64 if prec == Q64 else prec_of(r0)
     mu = torch.empty((R, M), dtype=torch.float64, device="cuda") if mu is None else mu

@@ -411,7 +411,7 @@ int pvsc_kpm_moments_batched(const pvsc_lattice* const* lats, int n, int R, int 
     uint64_t ab[2];
     std::memcpy(&ab[0], &a[i], 8);
     std::memcpy(&ab[1], &b[i], 8);
-    key.insert(key.end(), {(uint64_t)(uintptr_t)lats[i], seeds[i], ab[0], ab[1]});
+    key.insert(key.end(), {(uint64_t)(uintptr_t)lats[i], lats[i]->generation, seeds[i], ab[0], ab[1]});
   }
   auto body = [&](cudaStream_t cs) -> int {
     PVSC_CUDA_TRY(cudaMemsetAsync(base, 0, batch_header_bytes(n), cs));

@@ -116,7 +116,7 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
   if (sh.kernel == kKernelKpm2) sh = LaunchShape{};  // a KPM-only choice: single sweeps take the default
   p.tile_x = p.tile_y = 0;  // set below by the tiled and staged sweeps only (p may come from another launch)
   const bool tiled = lat->g.model == PVSC_TI && sh.kernel == kKernelTiles;
-  if (lat->g.model == PVSC_TI && !tiled && sh.tile_x > 0 && sh.tile_y > 0)
+  if (lat->g.model == PVSC_TI && !tiled && sh.kernel == 0 && sh.tile_x > 0 && sh.tile_y > 0)
     return launch_sweep_staged(lat, prec, feat, p, sh, st);
   const int vpt = vpt_tuned(sh.vpt, p.R, prec);
   p.C = p.R / vpt;
@@ -880,6 +880,9 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
   if (tuning->blocks_per_sm < 0 || tuning->zslab < 0 || tuning->tile_x < 0 || tuning->tile_y < 0)
     return set_error(PVSC_ERR_ARG, "negative tuning value");
   if (tuning->tile_x > 0 || tuning->tile_y > 0) {
+    if (tuning->kernel != 0)
+      return set_error(PVSC_ERR_ARG, "kernel %d takes no tile: tile_x and tile_y select the staged "
+                       "sweep of kernel 0 (and the tiles of kernels 4 and 5)", tuning->kernel);
     if (lat->g.model != PVSC_TI || tuning->tile_x < 1 || tuning->tile_y < 1)
       return set_error(PVSC_ERR_ARG, "a staged tile needs a TI lattice and tile_x, tile_y >= 1");
     if (tuning->threads % R) return set_error(PVSC_ERR_ARG, "staged sweeps need threads %% R == 0");

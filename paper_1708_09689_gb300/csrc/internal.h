@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdlib>
 
 #include <map>
@@ -123,6 +124,11 @@ struct pvsc_lattice {
   std::map<std::pair<int, int>, pvsc_tuning> tuning;  // (R, prec) -> tuning
   // cached CUDA graphs keyed by the full argument set of a captured loop
   std::map<std::vector<uint64_t>, pvsc::Graph> graphs;
+  // Process-unique stamp of the lattice's state, renewed whenever its cached
+  // graphs go stale (creation, new potential, new tuning): graphs that capture
+  // other lattices' geometry (the batched KPM) key on it, so that a changed
+  // potential or a new lattice at a reused address never replays old arguments.
+  uint64_t generation = 0;
   std::mutex mu;
   ~pvsc_lattice();
 };
@@ -171,8 +177,14 @@ int launch_adjoint_top(const pvsc_lattice* lat, int R, const double2* G, double 
 // Drop every cached graph of the lattice: a graph holds the launch shapes and
 // kernel arguments it was captured with, so a new tuning or a new potential
 // mode makes it stale.
+inline uint64_t next_generation() {
+  static std::atomic<uint64_t> counter{0};
+  return ++counter;
+}
+
 inline void drop_graphs(pvsc_lattice* lat) {
   std::lock_guard<std::mutex> lk(lat->mu);
+  lat->generation = next_generation();
   for (auto& kv : lat->graphs) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (kv.second.graph) cudaGraphDestroy(kv.second.graph);

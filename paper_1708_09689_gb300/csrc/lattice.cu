@@ -224,6 +224,7 @@ int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattic
     delete lat;
     return rc;
   }
+  lat->generation = next_generation();
   *out = lat;
   return PVSC_OK;
 }

@@ -12,43 +12,32 @@
 // is allocated by the library or by the caller.
 //
 // The array is kNoAllocScratchBytes = 2 MiB.  In host code its name is only a
-// host-side stand-in, never a device address: the device address is looked up
-// once per device with cudaGetSymbolAddress, with that device current, on the
-// first call made on that device, and cached.  Make that first call before any
-// stream capture.  Every call on a device shares the one array and it keeps
+// host-side stand-in, never a device address: every call looks the device
+// address up with cudaGetSymbolAddress, with the lattice's device current (a
+// cheap host call once the module is loaded; nothing is cached, so the address
+// stays right after cudaDeviceReset reloads the module).  The first call on a
+// device loads the module there: make it before any stream capture.  Every
+// call on a device shares the one array and it keeps
 // the contents the previous call left; the arrival counter at its start is
 // cleared (cudaMemsetAsync on the caller's stream) before each sweep.  Calls
 // whose kernels overlap on the GPU (different streams, no ordering) race on
 // the array: order them on one stream or synchronise between them.
-#include <mutex>
-
 #include "internal.h"
 
 namespace pvsc {
 
 constexpr size_t kNoAllocScratchBytes = size_t(2) << 20;
-constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once).
-static int noalloc_scratch(int device, void** out) {
-  if (device < 0 || device >= kNoAllocMaxDevices)
-    return set_error(PVSC_ERR_UNSUPPORTED, "device %d beyond the %d devices the scratch table covers",
-                     device, kNoAllocMaxDevices);
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return set_error(PVSC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
-                       cudaGetErrorString(e));
-    g_noalloc_ptr[device] = p;
-  }
-  *out = g_noalloc_ptr[device];
+// Device address of the scratch array on the current device.
+static int noalloc_scratch(void** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return set_error(PVSC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                     cudaGetErrorString(e));
+  *out = p;
   return PVSC_OK;
 }
 
@@ -77,7 +66,7 @@ extern "C" int pvsc_cheb_step_noalloc(const pvsc_lattice* lat, int R, int prec, 
                      "more than the static %zu bytes; use pvsc_cheb_step with a work buffer",
                      R, need, kNoAllocScratchBytes);
   void* scratch = nullptr;
-  if (int rc = noalloc_scratch(device, &scratch)) return rc;
+  if (int rc = noalloc_scratch(&scratch)) return rc;
   return pvsc_cheb_step(lat, R, prec, x, y, z, alpha, beta, gamma, delta, dot_flags, dots, scratch,
                         kNoAllocScratchBytes, stream);
 }

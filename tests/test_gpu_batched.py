@@ -57,6 +57,34 @@ def test_batched_kpm_repeat_is_reproducible_and_replays_graph():
     assert torch.equal(m1, m2)
 
 
+def test_batched_graph_follows_a_new_potential_on_a_later_lattice():
+    # the batched graph is cached on lattice 0 but captures every lattice's geometry:
+    # giving lattice 1 a potential between two calls with the same buffers must be seen
+    dims0, dims1 = (5, 5, 5), (6, 4, 5)
+    lat0 = pv.Lattice.ti(dims0, (1, 1, 1), disorder=(1.0, 51))
+    lat1 = pv.Lattice.ti(dims1, (1, 1, 1))
+    n1 = int(np.prod(dims1))
+    H0 = O.ti_hamiltonian(dims0, (1, 1, 1), 1.0, 2.0, W.disorder_potential(125, 1.0, 51))
+    V1 = W.disorder_potential(n1, 3.0, 52)
+    ab0 = O.cheb_scale(*O.gershgorin(H0))
+    H1 = O.ti_hamiltonian(dims1, (1, 1, 1), 1.0, 2.0, V1)
+    ab1 = O.cheb_scale(*O.gershgorin(H1))   # holds the clean spectrum of lattice 1 too
+    R, M = 2, 24
+    work = pv.work_buffer(pv.batched_work_bytes([lat0, lat1], R, pv.C128, M))
+    mu = torch.empty((2, R, M), dtype=torch.float64, device="cuda")
+    args = ([ab0[0], ab1[0]], [ab0[1], ab1[1]])
+    for _ in range(2):   # capture, then replay
+        pv.kpm_moments_batched([lat0, lat1], M, *args, R=R, prec=pv.C128, seeds=[1, 2], work=work, mu=mu)
+    clean = O.ti_hamiltonian(dims1, (1, 1, 1), 1.0, 2.0, np.zeros(n1))
+    r1 = W.random_phase_block(4 * n1, R, 2)
+    assert np.max(np.abs(mu[1].cpu().numpy() - O.kpm_moments(clean, r1, M, *ab1).real)) < 1e-12
+    lat1.set_potential(torch.from_numpy(V1).cuda())
+    pv.kpm_moments_batched([lat0, lat1], M, *args, R=R, prec=pv.C128, seeds=[1, 2], work=work, mu=mu)
+    assert np.max(np.abs(mu[1].cpu().numpy() - O.kpm_moments(H1, r1, M, *ab1).real)) < 1e-12
+    r0 = W.random_phase_block(4 * 125, R, 1)
+    assert np.max(np.abs(mu[0].cpu().numpy() - O.kpm_moments(H0, r0, M, *ab0).real)) < 1e-12
+
+
 def test_batched_wait_timeout_is_reported_and_context_survives():
     lats, Hs, ab = _lattices([(12, 1.0, 41), (10, 1.0, 42)])
     args = ([x[0] for x in ab], [x[1] for x in ab])

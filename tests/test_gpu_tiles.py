@@ -84,6 +84,15 @@ def test_march_along_x_needs_a_ti_lattice():
         gl.set_tuning(1, pv.C64, kernel=6)
 
 
+@pytest.mark.parametrize("kernel", [1, 2, 3, 6])
+def test_kernels_without_tiles_reject_a_tile(kernel):
+    # a tile selects the staged sweep of kernel 0 only; other kernels must not be
+    # replaced by it silently
+    lat = pv.Lattice.ti((8, 8, 4), (1, 1, 0))
+    with pytest.raises(pv.PvscError, match="takes no tile"):
+        lat.set_tuning(8, pv.C64, threads=128, tile_x=4, tile_y=4, kernel=kernel)
+
+
 @pytest.mark.parametrize("prec,tol", [(pv.C128, 1e-12), (pv.C64, 1e-5)])
 def test_march_along_x_series_propagation_and_step(prec, tol):
     # the accumulating (series) and fused-step features of the sweep marching along x

@@ -160,35 +160,43 @@ def test_graphene_bonds_have_unit_length():
     assert deg.max() == 3
 
 
-def _dsl_hamiltonian(Nx, Ny, periodic, V):
-    rows, cols, vals = [], [], []
-    path = os.path.join(GOLDEN, "graphene_dsl_couplings.txt")
-    entries = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+# Bonds of Eq. graphene_model as (dx, dy, site a of cell c + (dx, dy), site b of cell c):
+# the chain 0-1-2-3 inside a cell, T_x (site 1 of cell n + x with site 0 of n, site 2
+# of n + x with site 3 of n) and T_y (site 0 of cell n + y with site 3 of n).
+EQ_BONDS = [(0, 0, 1, 0), (0, 0, 2, 1), (0, 0, 3, 2), (1, 0, 1, 0), (1, 0, 2, 3), (0, 1, 0, 3)]
+
+
+def _mirrored_hamiltonian(Nx, Ny, periodic, V):
+    """The honeycomb of the paper's DSL statement of the stencil (Sec. 3.2), which
+    couples site 0 to site 1 of cell n - x where the equation uses n + x: the bonds
+    of Eq. graphene_model with dx -> -dx, assembled bond by bond (hopping -1, on-site
+    V), independently of the oracle's assembly."""
+    import scipy.sparse as sp
+    rows, cols, vals = list(range(4 * Nx * Ny)), list(range(4 * Nx * Ny)), list(V)
     for x in range(Nx):
         for y in range(Ny):
             c = x + Nx * y
-            for dx, dy, r, col, val in entries:
-                xx, yy = x + int(dx), y + int(dy)
+            for dx, dy, sa, sb in EQ_BONDS:
+                xx, yy = x - dx, y + dy
                 if periodic[0]:
                     xx %= Nx
                 if periodic[1]:
                     yy %= Ny
                 if not (0 <= xx < Nx and 0 <= yy < Ny):
                     continue
-                cc = xx + Nx * yy
-                rows.append(4 * c + int(r))
-                cols.append(4 * cc + int(col))
-                vals.append(V[4 * c + int(r)] if val == "v" else float(val))
+                i, j = 4 * (xx + Nx * yy) + sa, 4 * c + sb
+                rows += [i, j]
+                cols += [j, i]
+                vals += [-1.0, -1.0]
     D = 4 * Nx * Ny
-    import scipy.sparse as sp
     return sp.coo_matrix((vals, (rows, cols)), shape=(D, D)).tocsr()
 
 
 @pytest.mark.parametrize("periodic", [(1, 1), (0, 0), (1, 0)])
-def test_graphene_equation_equals_dsl_listing_up_to_mirror(periodic):
+def test_graphene_equation_equals_dsl_form_up_to_mirror(periodic):
     Nx, Ny = 5, 4
     V = W.disorder_potential(4 * Nx * Ny, 1.0, 3)
-    Hd = _dsl_hamiltonian(Nx, Ny, periodic, V).toarray()
+    Hd = _mirrored_hamiltonian(Nx, Ny, periodic, V).toarray()
     # mirror x -> Nx-1-x of the equation form (V mirrored along with it)
     perm = np.array([4 * ((Nx - 1 - (c % Nx)) + Nx * (c // Nx)) + nu
                      for c in range(Nx * Ny) for nu in range(4)])
@@ -435,8 +443,59 @@ def test_jackson_kernel_small_cases_by_hand():
     assert np.allclose(O.jackson_kernel(3), [1.0, 1.0 / math.sqrt(2.0), 0.25], atol=1e-15)
     g = O.jackson_kernel(256)
     assert g[0] == 1.0 and np.all(np.diff(g) < 0) and g[-1] > 0
-    gl = O.lorentz_kernel(64, 4.0)
-    assert abs(gl[0] - 1.0) < 1e-15 and np.all(np.diff(gl) < 0)
+
+
+def test_lorentz_kernel_small_cases_by_hand():
+    # M = 2: g_1 = sinh(lam / 2) / sinh(lam) = 1 / (2 cosh(lam / 2)) (sinh 2u = 2 sinh u cosh u);
+    # M = 3: g_1 = sinh(2 lam / 3) / sinh(lam), g_2 = sinh(lam / 3) / sinh(lam), and with
+    # u = lam / 3, sinh 3u = sinh u (4 cosh^2 u - 1), so g_2 = 1 / (4 cosh^2(lam / 3) - 1)
+    for lam in (0.5, 2.0, 4.0):
+        assert np.allclose(O.lorentz_kernel(2, lam), [1.0, 0.5 / math.cosh(lam / 2)], rtol=1e-14)
+        g3 = O.lorentz_kernel(3, lam)
+        assert abs(g3[2] - 1.0 / (4.0 * math.cosh(lam / 3) ** 2 - 1.0)) < 1e-14
+        assert abs(g3[1] - 2.0 * math.cosh(lam / 3) * g3[2]) < 1e-14  # sinh 2u = 2 cosh u sinh u
+    # the damping is a two-point boundary problem of the recurrence
+    # g_{k+1} + g_{k-1} = 2 cosh(lam / M) g_k with g_0 = 1 and g_M = 0
+    M, lam = 64, 4.0
+    g = np.append(O.lorentz_kernel(M, lam), 0.0)
+    assert abs(g[0] - 1.0) < 1e-15
+    assert np.max(np.abs(g[2:] + g[:-2] - 2.0 * math.cosh(lam / M) * g[1:-1])) < 1e-14
+
+
+def test_lorentz_damped_delta_peak_equals_geometric_series_closed_form():
+    # One eigenvalue E0 has moments mu_k = T_k(x0).  With the Lorentz factors
+    # g_k = [r^k - e^{-2 lam} r^{-k}] / (1 - e^{-2 lam}), r = e^{-lam/M} (the
+    # exponential form of sinh(lam (1 - k/M)) / sinh(lam)), the damped series
+    # sum_k (2 - delta_k0) g_k cos(k th0) cos(k th) is a combination of finite
+    # geometric sums sum_{k<M} q^k cos(k phi) = Re[(1 - z^M) / (1 - z)], z = q e^{i phi},
+    # at phi = th -+ th0: the Lorentzian peak of width ~lam/M in th of the KPM review
+    # the paper cites (Weisse et al., Rev. Mod. Phys. 78, 275, Sec. II.C).
+    M, lam, a, b = 200, 4.0, 3.0, 0.5
+    E0 = 1.1
+    x0 = (E0 - b) / a
+    th0 = math.acos(x0)
+    mu = np.cos(np.arange(M) * th0)[None, :]
+    E = np.linspace(b - a + 1e-6, b + a - 1e-6, 4001)
+    rho = O.kpm_density(mu, E, a, b, O.lorentz_kernel(M, lam))
+    th = np.arccos((E - b) / a)
+
+    def geo(q, phi):
+        z = q * np.exp(1j * phi)
+        return np.real((1.0 - z ** M) / (1.0 - z))
+
+    def damped(q):
+        return geo(q, th - th0) + geo(q, th + th0) - 1.0
+
+    r = math.exp(-lam / M)
+    series = (damped(r) - math.exp(-2 * lam) * damped(1.0 / r)) / (1.0 - math.exp(-2 * lam))
+    ref = series / (math.pi * a * np.sin(th))
+    assert np.max(np.abs(rho - ref)) < 1e-10 * np.max(np.abs(ref))
+    # the peak sits at E0 and its half width in th is close to lam / M
+    i = int(np.argmax(rho * np.sin(th)))
+    assert abs(E[i] - E0) <= 2 * (E[1] - E[0])
+    prof = rho * np.sin(th)
+    half = th[prof >= 0.5 * prof[i]]
+    assert abs((half.max() - half.min()) / 2 - lam / M) < 0.25 * lam / M
 
 
 def test_kpm_density_normalisation_by_gauss_chebyshev_quadrature():
