@@ -46,7 +46,8 @@ UNIT = "GLUP/s"
 # the captured version
 TRAFFIC = {("ti_slab", 8, "ti_sweep"): {"bytes_per_launch": 3.220e9, "source_sha256_16": "df26e831c975b98f"},
            ("ti_slab", 8, "ti_sweep_xmarch"): {"bytes_per_launch": 3.222e9, "source_sha256_16": "df26e831c975b98f"}}
-KERNEL_SOURCES = ("paper_1708_09689_gb300/csrc/sweep.cuh", "paper_1708_09689_gb300/csrc/common.cuh")
+KERNEL_SOURCES = ("paper_1708_09689_gb300/csrc/sweep.cuh", "paper_1708_09689_gb300/csrc/common.cuh",
+                  "paper_1708_09689_gb300/csrc/sweep_tma.cu")
 
 
 def kernel_source_hash() -> str:
@@ -764,6 +765,10 @@ def main():
         bytes_per_lup = 64.0 + 2.0 / R
         launches = 1 + (sweeps - 1) // 2 + (sweeps - 1) % 2
         kname = "ti_kpm2_sweep (complex64, two KPM steps per sweep)"
+    elif bool(tuning) and tuning.get("kernel") == 7:
+        bytes_per_lup = 96.0 + 4.0 / R
+        launches = sweeps
+        kname = f"ti_sweep_tma<{R},F_DOTS> (complex64 KPM sweep, TMA-staged plane tiles)"
     elif bool(tuning) and tuning.get("kernel") == 6:
         bytes_per_lup = 96.0 + 4.0 / R
         launches = sweeps

@@ -446,7 +446,13 @@ typedef struct {
                   /* vectors, which pvsc_work_bytes reports once this entry is set, */
                   /* 5 z-marching over tiles of tile_x x tile_y columns per block */
                   /* (threads = tile_x tile_y R/vpt, a multiple of 32, at most 256), */
-                  /* 6 marching along x over lines (y, z), zslab = x-segment length */
+                  /* 6 marching along x over lines (y, z), zslab = x-segment length, */
+                  /* 7 (complex64, R = 4, 8 or 16, Lx a multiple of 4) TMA-staged */
+                  /* plane tiles: one block per SM copies each z-plane of a tile of */
+                  /* 16x16, 16x8 or 8x8 columns with its one-site halo strips into a */
+                  /* shared-memory ring (cp.async.bulk.tensor, mbarriers) for eight */
+                  /* warps; zslab = z-chunk depth (0: chosen from the grid size); */
+                  /* threads, vpt and the tile fields are ignored (tile_x, tile_y 0) */
 } pvsc_tuning;
 
 /* Device error word of the shared-memory staged sweeps: *flag = 1 if a copy

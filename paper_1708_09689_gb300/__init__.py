@@ -512,6 +512,14 @@ def kpm_moments_batched(lats, M, a, b, R=16, prec=C64, seeds=None, work=None, mu
     return mu
 
 
+def device_error(clear: bool = True) -> int:
+    """The device error word of the staged sweeps (1 if a copy wait ran out since
+    the last clear; the sweep's outputs are then invalid).  Synchronises the device."""
+    flag = ctypes.c_int(0)
+    _check(_lib.pvsc_device_error(ctypes.byref(flag), int(bool(clear))))
+    return int(flag.value)
+
+
 def set_wait_limit(spins: int):
     _check(_lib.pvsc_set_wait_limit(int(spins)))
 

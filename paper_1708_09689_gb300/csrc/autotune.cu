@@ -169,6 +169,15 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
       }
     }
   }
+  // TMA-staged plane tiles (kernel 7): z-chunks chosen automatically or a few fixed depths
+  if (tma_sweep_possible(lat, R, prec)) {
+    const int deep_y = R == 4 ? 8 : 4, deep_x = R == 16 ? 8 : 16;
+    for (int zs : {0, 16, 32, 64})
+      if (zs == 0 || zs < lat->g.L[2]) {
+        cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, 0, 0, kKernelTma});
+        cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, deep_x, deep_y, kKernelTma});
+      }
+  }
   if (lat->g.model == PVSC_TI)
     for (int th : {128, 256}) {
       if (th % R) continue;

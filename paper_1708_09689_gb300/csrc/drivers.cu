@@ -114,6 +114,11 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
     }
   LaunchShape sh = shape_for(lat, p.R, prec);
   if (sh.kernel == kKernelKpm2) sh = LaunchShape{};  // a KPM-only choice: single sweeps take the default
+  if (sh.kernel == kKernelTma) {
+    p.tile_x = p.tile_y = 0;
+    if (tma_sweep_possible(lat, p.R, prec) && !(feat & F_ADJ)) return launch_sweep_tma(lat, feat, p, sh, st);
+    sh = LaunchShape{};  // complex128 (or a shape it does not cover) on a lattice tuned for complex64
+  }
   p.tile_x = p.tile_y = 0;  // set below by the tiled and staged sweeps only (p may come from another launch)
   const bool tiled = lat->g.model == PVSC_TI && sh.kernel == kKernelTiles;
   if (lat->g.model == PVSC_TI && !tiled && sh.kernel == 0 && sh.tile_x > 0 && sh.tile_y > 0)
@@ -812,10 +817,11 @@ int pvsc_cheb_adjoint_step(const pvsc_lattice* lat, int R, int prec, const void*
 int pvsc_device_error(int* flag, int clear) {
   if (!flag) return set_error(PVSC_ERR_ARG, "flag is NULL");
   PVSC_CUDA_TRY(cudaDeviceSynchronize());
-  int a = 0, b = 0;
+  int a = 0, b = 0, c = 0;
   if (int rc = bulk_sweep_error(PVSC_C128, clear, &a)) return rc;
   if (int rc = bulk_sweep_error(PVSC_C64, clear, &b)) return rc;
-  *flag = (a || b) ? 1 : 0;
+  if (int rc = tma_error(clear, &c)) return rc;
+  *flag = (a || b || c) ? 1 : 0;
   return PVSC_OK;
 }
 
@@ -849,7 +855,19 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
     return PVSC_OK;
   }
   if (tuning->vpt < 0 || tuning->vpt > 2) return set_error(PVSC_ERR_ARG, "vpt must be 0, 1 or 2");
-  if (tuning->kernel < 0 || tuning->kernel > 6) return set_error(PVSC_ERR_ARG, "kernel must be 0 .. 6");
+  if (tuning->kernel < 0 || tuning->kernel > 7) return set_error(PVSC_ERR_ARG, "kernel must be 0 .. 7");
+  if (tuning->kernel == kKernelTma) {
+    if (!tma_sweep_possible(lat, R, prec))
+      return set_error(PVSC_ERR_ARG, "kernel 7 (TMA-staged tiles) needs a TI lattice, complex64, R = 4, 8 "
+                       "or 16 and Lx a multiple of 4");
+    if (!tma_tile_valid(R, tuning->tile_x, tuning->tile_y))
+      return set_error(PVSC_ERR_ARG, "kernel 7 takes no tile other than the two of R = %d (%dx%d given)", R,
+                       tuning->tile_x, tuning->tile_y);
+    if (tuning->blocks_per_sm < 0 || tuning->zslab < 0) return set_error(PVSC_ERR_ARG, "negative tuning value");
+    lat->tuning[{R, prec}] = *tuning;
+    drop_graphs(lat);
+    return PVSC_OK;
+  }
   if (tuning->kernel == kKernelXMarch && lat->g.model != PVSC_TI)
     return set_error(PVSC_ERR_ARG, "kernel 6 (marching along x) needs a TI lattice");
   if (tuning->kernel == kKernelTiles) {

@@ -38,7 +38,8 @@ struct LaunchShape {
   int tile_y = 0;
   int kernel = 0;         // TI: 0 z-marching / staged, 1 flat, 2 / 3 cp.async rings,
                           // 4 two KPM steps per sweep (tile_x x tile_y tiles),
-                          // 5 z-marching over tile_x x tile_y column tiles, 6 marching along x
+                          // 5 z-marching over tile_x x tile_y column tiles, 6 marching along x,
+                          // 7 TMA-staged plane tiles (warp-specialised)
 };
 
 // kernel-selector "model" values of the flat and the cp.async-prefetching TI
@@ -92,6 +93,14 @@ constexpr int kKernelKpm2 = 4;
 constexpr int kKernelTiles = 5;
 // TI sweep marching along x instead of z (short z extents)
 constexpr int kKernelXMarch = 6;
+// TI sweep with TMA-staged z-plane tiles and warp specialisation (sweep_tma.cu):
+// complex64, R = 4, 8 or 16, Lx a multiple of 4
+constexpr int kKernelTma = 7;
+bool tma_sweep_possible(const pvsc_lattice* lat, int R, int prec);
+int launch_sweep_tma(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st);
+int tma_error(int clear, int* flag);
+bool tma_tile_valid(int R, int tile_x, int tile_y);  // (0, 0) or one of the two tiles of this R
+bool tma_tile_deep(int R, int tile_y);
 int launch_kpm2_sweep(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, cudaStream_t st);
 int kpm2_check_tile(int TX, int TY, int R);
 

@@ -51,13 +51,14 @@ def _moments(shape, a, b):
 
 
 SHAPES = [
-    dict(threads=256, vpt=1, kernel=6),   # the benchmark's sweep marching along x
+    dict(threads=256, vpt=1, kernel=6),   # the sweep marching along x
     dict(threads=256, vpt=2, kernel=0),   # the default z-march
+    dict(kernel=7),                       # TMA-staged plane tiles
     "autotune",
 ]
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=["xmarch", "zmarch", "autotuned"])
+@pytest.mark.parametrize("shape", SHAPES, ids=["xmarch", "zmarch", "tma", "autotuned"])
 def test_c64_kpm_all_2048_moments_match_the_oracle(case, shape):
     a, b, ref = case
     mu, tuning = _moments(shape, a, b)

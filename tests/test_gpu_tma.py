@@ -1,0 +1,150 @@
+"""The TI sweep with TMA-staged plane tiles (tuning kernel 7, complex64, R = 4, 8, 16).
+
+Its stencil arithmetic is the register z-march's, in the same order, so the
+vectors it writes must equal the default sweep's bit for bit; they are also
+checked against the oracle.  The cases cover every boundary mix, partial tiles
+(Lx, Ly not multiples of the tile), periodic lengths 1 and 2 (a site is its own
+or its double neighbour), one-plane z-chunks (every unit shorter than the copy
+ring), the three potential sources and the Delta terms.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+pv = pytest.importorskip("paper_1708_09689_gb300")
+
+CASES = [
+    # dims, periodic, z-chunk depth
+    ((32, 16, 6), (1, 1, 0), 0),
+    ((20, 12, 5), (1, 1, 1), 2),      # partial tiles along x and y
+    ((16, 8, 7), (0, 0, 0), 1),       # open everywhere, one-plane chunks
+    ((4, 2, 3), (1, 1, 1), 0),        # x shorter than a tile, y of length 2
+    ((8, 1, 4), (1, 1, 0), 3),        # y of length 1: its own neighbour
+    ((36, 9, 1), (0, 1, 1), 0),       # one plane, periodic z of length 1
+]
+
+
+def _lattice(dims, per, vmode, delta):
+    n = int(np.prod(dims))
+    kw = dict(delta1=0.3, delta2=-0.2) if delta else {}
+    if vmode == "stored":
+        V = W.disorder_potential(n, 2.0, 7)
+        return pv.Lattice.ti(dims, per, disorder=(2.0, 7), **kw), V
+    if vmode == "fly":
+        V = W.disorder_potential(n, 2.0, 7)
+        return pv.Lattice.ti(dims, per, disorder=(2.0, 7), on_the_fly=True, **kw), V
+    return pv.Lattice.ti(dims, per, **kw), np.zeros(n)
+
+
+DEEP_TILE = {4: (16, 8), 8: (16, 4), 16: (8, 4)}   # the half tiles with three planes in flight
+
+
+@pytest.mark.parametrize("dims,per,zs", CASES)
+@pytest.mark.parametrize("R", [4, 8, 16])
+@pytest.mark.parametrize("deep", [False, True])
+def test_tma_sweep_equals_default_sweep_and_oracle(dims, per, zs, R, deep):
+    lat, V = _lattice(dims, per, "stored", False)
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
+    x = torch.from_numpy(W.gaussian_block(H.shape[0], R, 1)).to("cuda", torch.complex64)
+    y0 = pv.apply_H(lat, x)
+    tile = dict(zip(("tile_x", "tile_y"), DEEP_TILE[R])) if deep else {}
+    lat.set_tuning(R, pv.C64, kernel=7, zslab=zs, **tile)
+    y1 = pv.apply_H(lat, x)
+    assert torch.equal(y0, y1)
+    ref = H @ x.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(y1.cpu().numpy() - ref) / np.linalg.norm(ref) < 2e-6
+
+
+@pytest.mark.parametrize("vmode,delta", [("stored", True), ("fly", False), ("zero", True)])
+@pytest.mark.parametrize("R", [4, 8, 16])
+def test_tma_fused_step_with_z_and_dots(vmode, delta, R):
+    dims, per = (24, 16, 5), (1, 0, 1)
+    lat, V = _lattice(dims, per, vmode, delta)
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V, 0.3 if delta else 0.0, -0.2 if delta else 0.0)
+    D = H.shape[0]
+    x = torch.from_numpy(W.gaussian_block(D, R, 2)).to("cuda", torch.complex64)
+    yin = torch.from_numpy(W.gaussian_block(D, R, 3)).to("cuda", torch.complex64)
+    zin = torch.from_numpy(W.gaussian_block(D, R, 4)).to("cuda", torch.complex64)
+    al = [0.2 + 0.01 * r for r in range(R)]
+    be = [0.1 * (r - 2) for r in range(R)]
+    ga = [-1.0 + 0.05 * r for r in range(R)]
+    de = [0.5] * R
+    ya, za = yin.clone(), zin.clone()
+    da = pv.cheb_step(lat, x, ya, al, be, ga, z=za, delta=de, dots=7)
+    lat.set_tuning(R, pv.C64, kernel=7)
+    yb, zb = yin.clone(), zin.clone()
+    db = pv.cheb_step(lat, x, yb, al, be, ga, z=zb, delta=de, dots=7)
+    assert torch.equal(ya, yb) and torch.equal(za, zb)
+    scale = da.abs().max().item()
+    assert (da - db).abs().max().item() <= 1e-6 * scale
+    xr = x.cpu().numpy().astype(np.complex128)
+    yr, zr, dots = O.cheb_step(H, xr, yin.cpu().numpy().astype(np.complex128), al, be, ga,
+                               zin.cpu().numpy().astype(np.complex128), de)
+    assert np.linalg.norm(yb.cpu().numpy() - yr) / np.linalg.norm(yr) < 2e-6
+    assert np.linalg.norm(zb.cpu().numpy() - zr) / np.linalg.norm(zr) < 2e-6
+    got = db.cpu().numpy()
+    # <x|x>, Re<y|x>, Im<y|x>, <y|y> of the written vectors, against the oracle's fp64 sums
+    assert np.allclose(got[0], dots[:, 0].real, rtol=1e-5)
+    assert np.allclose(got[1], dots[:, 1].real, rtol=1e-5, atol=1e-5 * np.abs(dots[:, 1]).max())
+    assert np.allclose(got[2], dots[:, 1].imag, rtol=1e-5, atol=1e-5 * np.abs(dots[:, 1]).max())
+    assert np.allclose(got[3], dots[:, 2].real, rtol=1e-5)
+
+
+@pytest.mark.parametrize("dims,per,zs", CASES[:3])
+@pytest.mark.parametrize("R", [4, 8, 16])
+@pytest.mark.parametrize("deep", [False, True])
+def test_tma_kpm_moments_match_oracle_and_default(dims, per, zs, R, deep):
+    lat, V = _lattice(dims, per, "stored", False)
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    M = 64
+    r = W.random_phase_block(H.shape[0], R, 5)
+    r0 = torch.from_numpy(r).to("cuda", torch.complex64)
+    mu0 = pv.kpm_moments(lat, M, a, b, r0=r0).cpu().numpy()
+    tile = dict(zip(("tile_x", "tile_y"), DEEP_TILE[R])) if deep else {}
+    lat.set_tuning(R, pv.C64, kernel=7, zslab=zs, **tile)
+    mu1 = pv.kpm_moments(lat, M, a, b, r0=r0).cpu().numpy()
+    assert np.max(np.abs(mu1 - mu0)) < 1e-9
+    ref = O.kpm_moments(H, r, M, a, b).real
+    assert np.max(np.abs(mu1 - ref)) / ref[0, 0] < 1e-4
+
+
+def test_tma_series_and_propagation():
+    dims, per, R = (16, 16, 6), (1, 1, 0), 8
+    lat, V = _lattice(dims, per, "stored", False)
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
+    lat.set_tuning(R, pv.C64, kernel=7)
+    _, _, a, b = lat.spectral_bounds()
+    x = W.gaussian_block(H.shape[0], R, 3)
+    x /= np.linalg.norm(x, axis=0)
+    psi = torch.from_numpy(x).cuda()
+    pv.cheb_propagate(lat, psi, 0.6, 3, a, b, prec=pv.C64)
+    ref = O.propagate(H, x, 0.6, 3, a, b)
+    assert np.linalg.norm(psi.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_tma_kernel_is_refused_where_it_does_not_apply():
+    lat = pv.Lattice.ti((16, 8, 4), (1, 1, 0))
+    for R, prec in ((8, pv.C128), (2, pv.C64), (32, pv.C64)):
+        with pytest.raises(pv.PvscError, match="kernel 7"):
+            lat.set_tuning(R, prec, kernel=7)
+    with pytest.raises(pv.PvscError, match="kernel 7"):
+        pv.Lattice.ti((18, 8, 4), (1, 1, 0)).set_tuning(8, pv.C64, kernel=7)  # Lx % 4 != 0
+    with pytest.raises(pv.PvscError, match="kernel 7 takes no tile"):
+        lat.set_tuning(8, pv.C64, kernel=7, tile_x=8, tile_y=8)
+    gl = pv.Lattice.graphene((8, 8), (1, 1))
+    with pytest.raises(pv.PvscError, match="kernel 7"):
+        gl.set_tuning(8, pv.C64, kernel=7)
+
+
+def test_tma_sweep_reports_no_device_error():
+    lat = pv.Lattice.ti((32, 32, 8), (1, 1, 0), disorder=(1.0, 3))
+    lat.set_tuning(8, pv.C64, kernel=7)
+    x = pv.random_vectors(lat, 8, pv.C64, 1)
+    pv.apply_H(lat, x)
+    assert pv.device_error() == 0
