@@ -451,8 +451,11 @@ typedef struct {
                   /* plane tiles: one block per SM copies each z-plane of a tile of */
                   /* 16x16, 16x8 or 8x8 columns with its one-site halo strips into a */
                   /* shared-memory ring (cp.async.bulk.tensor, mbarriers) for eight */
-                  /* warps; zslab = z-chunk depth (0: chosen from the grid size); */
-                  /* threads, vpt and the tile fields are ignored (tile_x, tile_y 0) */
+                  /* warps (threads 256, two (site, vector pair) items per thread) or */
+                  /* sixteen (threads 512, one item); tile_x x tile_y = the half tile */
+                  /* (16x8, 16x4, 8x4 for R = 4, 8, 16) selects rings one plane */
+                  /* deeper on eight warps; zslab = z-chunk depth (0: chosen from */
+                  /* the grid size); vpt is ignored */
 } pvsc_tuning;
 
 /* Device error word of the shared-memory staged sweeps: *flag = 1 if a copy

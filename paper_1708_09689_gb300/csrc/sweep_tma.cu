@@ -46,10 +46,8 @@
 
 namespace pvsc {
 
-constexpr int kTmaWarps = 8;
-constexpr int kTmaThreads = 32 * kTmaWarps;
 constexpr unsigned kTmaWaitLimit = 1u << 24;
-constexpr int kTmaMaxUnits = 1024;  // work units of one block (a table in shared memory)
+constexpr int kTmaMaxUnits = 512;  // work units of one block (a table in shared memory)
 
 // Tile of TX x TY sites per R: 256 (site, vector pair) items, one per thread,
 // and NXS x-plane / NYS y_in-plane ring slots: three planes of copies in flight
@@ -66,15 +64,16 @@ template <> struct TmaTile<16, false> { static constexpr int TX = 8, TY = 8, NXS
 
 constexpr int round_up_1k(int b) { return (b + 1023) & ~1023; }
 
-template <int R, bool DEEP>
+template <int R, bool DEEP, int NW>
 struct TmaLayout {
+  static constexpr int NWARPS = NW;  // warps per block (8 or 16), one block per SM
   static constexpr int TX = TmaTile<R, DEEP>::TX, TY = TmaTile<R, DEEP>::TY;
   static constexpr int SITE_B = 32 * R;          // 4 orbitals x R complex64
   static constexpr int ROWS = SITE_B / 128;      // 128-byte swizzle rows per site
   static constexpr int CPS = R / 2;              // threads per site
   static constexpr int SPW = 32 / CPS;           // sites per warp
   static constexpr int ITEMS = TX * TY * CPS;
-  static constexpr int IPT = ITEMS / (32 * kTmaWarps);  // items per consumer thread
+  static constexpr int IPT = ITEMS / (32 * NW);  // items per thread
   static constexpr int INT_B = TX * TY * SITE_B;  // interior tile
   static constexpr int XS_B = TY * SITE_B;        // x-/x+ halo column
   static constexpr int YS_B = TX * SITE_B;        // y-/y+ halo row
@@ -87,11 +86,11 @@ struct TmaLayout {
   static constexpr int NXS = TmaTile<R, DEEP>::NXS, NYS = TmaTile<R, DEEP>::NYS;
   static constexpr int BAR_OFF = NXS * XSTAGE + NYS * YSTAGE;
   static constexpr int DOT_OFF = BAR_OFF + 128;  // fp64 dot partials [warp][dot][v][c]
-  static constexpr int DOT_B = kTmaWarps * 4 * 2 * CPS * 8;
+  static constexpr int DOT_B = NW * 4 * 2 * CPS * 8;
   static constexpr int TAB_OFF = DOT_OFF + DOT_B;  // the block's units: (x0 | y0 << 16, z0 | n << 16)
   static constexpr int TAB_B = kTmaMaxUnits * 8;
   static constexpr size_t SMEM = 1024 + (size_t)TAB_OFF + TAB_B;  // + alignment slack
-  static_assert(ITEMS % (32 * kTmaWarps) == 0, "tile items");
+  static_assert(IPT >= 1 && ITEMS % (32 * NW) == 0, "tile items");
   static_assert(NXS >= 3 && NYS >= 2, "ring depth");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -201,11 +200,11 @@ __device__ __forceinline__ void tma_lds_blk(const unsigned char* buf, uint32_t B
   }
 }
 
-template <int R, bool DEEP, int FEAT>
-__global__ void __launch_bounds__(kTmaThreads, 1)
+template <int R, bool DEEP, int NW, int FEAT>
+__global__ void __launch_bounds__(32 * NW, 1)
     ti_sweep_tma(const __grid_constant__ Sweep p, const __grid_constant__ TmaMaps m) {
-  using L = TmaLayout<R, DEEP>;
-  constexpr int NCW = kTmaWarps, IPT = L::IPT, TX = L::TX, TY = L::TY;
+  using L = TmaLayout<R, DEEP, NW>;
+  constexpr int NCW = NW, IPT = L::IPT, TX = L::TX, TY = L::TY;
   extern __shared__ unsigned char smem_raw[];
   __shared__ int s_abort;
   __shared__ unsigned s_cnt[L::NXS + L::NYS];  // releases per slot (x slots, then y slots)
@@ -419,16 +418,30 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
       for (int i = 0; i < IPT; ++i) {
         if (!ok[i]) continue;
         const int64_t s = col[i] + plane * z;
-        Blk<float, 2> xc, xp, ax, bx, ay, by, yi, S, D, yn;
-        tma_lds_blk<R>(s1, Bc[i], xp);
-        tma_lds_blk<R>(s0, Bxm[i], ax);
-        tma_lds_blk<R>(s0, Bxp[i], bx);
-        tma_lds_blk<R>(s0, Bym[i], ay);
-        tma_lds_blk<R>(s0, Byp[i], by);
+        // the axes in ti_axes' order (z pair, x pair, y pair), each pair loaded
+        // just before it is folded in, so that few blocks are live at a time
+        Blk<float, 2> S, D, yn;
+        {
+          Blk<float, 2> xp;
+          tma_lds_blk<R>(s1, Bc[i], xp);
+          axis_z_init(xmr[i], xp, S, D);
+        }
+        {
+          Blk<float, 2> ax, bx;
+          tma_lds_blk<R>(s0, Bxm[i], ax);
+          tma_lds_blk<R>(s0, Bxp[i], bx);
+          axis_x_add(ax, bx, S, D);
+        }
+        {
+          Blk<float, 2> ay, by;
+          tma_lds_blk<R>(s0, Bym[i], ay);
+          tma_lds_blk<R>(s0, Byp[i], by);
+          axis_y_add(ay, by, S, D);
+        }
+        Blk<float, 2> xc, yi;
         tma_lds_blk<R>(s0, Bc[i], xc);
         if (m.has_yin) tma_lds_blk<R>(sy, Bc[i], yi);
         const float Vs = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i]) : site_potential_t<float>(g, s);
-        ti_axes(xmr[i], xp, ax, bx, ay, by, S, D);
         ti_combine(cf, Vs, xc, S, D, m.has_yin ? &yi : nullptr, yn, g);
         const int64_t sites[4] = {s, s, s, s};
         epilogue<float, 2, FEAT>(p, s, c, xc, yn, dacc, sites);
@@ -492,7 +505,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
 
 template <int R, bool DEEP>
 static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
-  using L = TmaLayout<R, DEEP>;
+  using L = TmaLayout<R, DEEP, 8>;
   auto enc = encode_tiled();
   if (!enc) return set_error(PVSC_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
   const cuuint64_t Lx = lat->g.L[0], Ly = lat->g.L[1], Lz = lat->g.L[2];
@@ -528,14 +541,14 @@ static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
   return PVSC_OK;
 }
 
-template <int R, bool DEEP>
+template <int R, bool DEEP, int NW>
 static void* tma_kernel(int feat) {
   switch (feat) {
-    case 0: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, 0>);
-    case F_DOTS: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, F_DOTS>);
-    case F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, F_Z>);
-    case F_DOTS | F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, F_DOTS | F_Z>);
-    case F_ACC: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, F_ACC>);
+    case 0: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, 0>);
+    case F_DOTS: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS>);
+    case F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_Z>);
+    case F_DOTS | F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS | F_Z>);
+    case F_ACC: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_ACC>);
     default: return nullptr;
   }
 }
@@ -558,7 +571,7 @@ static int auto_chunks(int64_t ntiles, int64_t Lz, int64_t grid) {
 
 template <int R>
 static int64_t tma_tiles(const Geometry& g) {  // the smaller (deep-ring) tiles: the most units
-  using L = TmaLayout<R, true>;
+  using L = TmaLayout<R, true, 8>;
   return ((g.L[0] + L::TX - 1) / L::TX) * ((g.L[1] + L::TY - 1) / L::TY);
 }
 
@@ -573,14 +586,14 @@ bool tma_sweep_possible(const pvsc_lattice* lat, int R, int prec) {
   return ntiles <= (int64_t)kTmaMaxUnits * lat->sm_count;
 }
 
-template <int R, bool DEEP>
+template <int R, bool DEEP, int NW>
 static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
-  using L = TmaLayout<R, DEEP>;
-  void* fn = tma_kernel<R, DEEP>(feat);
+  using L = TmaLayout<R, DEEP, NW>;
+  void* fn = tma_kernel<R, DEEP, NW>(feat);
   if (!fn) return set_error(PVSC_ERR_UNSUPPORTED, "no TMA-staged sweep for feature set %d", feat);
   if (int rc = allow_max_smem(fn)) return rc;
   int occ = 0;
-  PVSC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTmaThreads, L::SMEM));
+  PVSC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * NW, L::SMEM));
   if (occ < 1) return set_error(PVSC_ERR_CUDA, "the TMA-staged sweep does not fit an SM");
   p.C = R / 2;
   p.tile_x = L::TX;
@@ -601,19 +614,19 @@ static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const Launc
   p.zslab = (int)((Lz + nch - 1) / nch);
   const int grid = (int)(m.nunits < grid_max ? m.nunits : grid_max);
   void* args[] = {&p, &m};
-  PVSC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(kTmaThreads), args, L::SMEM, st));
+  PVSC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(32 * NW), args, L::SMEM, st));
   return PVSC_OK;
 }
 
 // The two tiles of kernel 7 per R, as (tile_x, tile_y): {large, deep}.
 static void tma_tiles_of(int R, int* tx_large, int* ty_large, int* tx_deep, int* ty_deep) {
   switch (R) {
-    case 4: *tx_large = TmaLayout<4, false>::TX; *ty_large = TmaLayout<4, false>::TY;
-            *tx_deep = TmaLayout<4, true>::TX; *ty_deep = TmaLayout<4, true>::TY; break;
-    case 8: *tx_large = TmaLayout<8, false>::TX; *ty_large = TmaLayout<8, false>::TY;
-            *tx_deep = TmaLayout<8, true>::TX; *ty_deep = TmaLayout<8, true>::TY; break;
-    default: *tx_large = TmaLayout<16, false>::TX; *ty_large = TmaLayout<16, false>::TY;
-             *tx_deep = TmaLayout<16, true>::TX; *ty_deep = TmaLayout<16, true>::TY; break;
+    case 4: *tx_large = TmaLayout<4, false, 8>::TX; *ty_large = TmaLayout<4, false, 8>::TY;
+            *tx_deep = TmaLayout<4, true, 8>::TX; *ty_deep = TmaLayout<4, true, 8>::TY; break;
+    case 8: *tx_large = TmaLayout<8, false, 8>::TX; *ty_large = TmaLayout<8, false, 8>::TY;
+            *tx_deep = TmaLayout<8, true, 8>::TX; *ty_deep = TmaLayout<8, true, 8>::TY; break;
+    default: *tx_large = TmaLayout<16, false, 8>::TX; *ty_large = TmaLayout<16, false, 8>::TY;
+             *tx_deep = TmaLayout<16, true, 8>::TX; *ty_deep = TmaLayout<16, true, 8>::TY; break;
   }
 }
 
@@ -636,12 +649,22 @@ int launch_sweep_tma(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchSh
                      "or 16 and Lx a multiple of 4");
   // tile_y selects the tile (and ring depth) of this R: the larger tile with
   // two planes in flight, or half of it with three (0: the default)
+  // and threads = 512 the large tile with one item per thread (16 warps)
   const bool deep = tma_tile_deep(p.R, sh.tile_y);
+  const bool wide = !deep && sh.threads == 512;
   switch (p.R) {
-    case 4: return deep ? launch_tma_r<4, true>(lat, feat, p, sh, st) : launch_tma_r<4, false>(lat, feat, p, sh, st);
-    case 8: return deep ? launch_tma_r<8, true>(lat, feat, p, sh, st) : launch_tma_r<8, false>(lat, feat, p, sh, st);
+    case 4:
+      return deep ? launch_tma_r<4, true, 8>(lat, feat, p, sh, st)
+                  : (wide ? launch_tma_r<4, false, 16>(lat, feat, p, sh, st)
+                          : launch_tma_r<4, false, 8>(lat, feat, p, sh, st));
+    case 8:
+      return deep ? launch_tma_r<8, true, 8>(lat, feat, p, sh, st)
+                  : (wide ? launch_tma_r<8, false, 16>(lat, feat, p, sh, st)
+                          : launch_tma_r<8, false, 8>(lat, feat, p, sh, st));
     default:
-      return deep ? launch_tma_r<16, true>(lat, feat, p, sh, st) : launch_tma_r<16, false>(lat, feat, p, sh, st);
+      return deep ? launch_tma_r<16, true, 8>(lat, feat, p, sh, st)
+                  : (wide ? launch_tma_r<16, false, 16>(lat, feat, p, sh, st)
+                          : launch_tma_r<16, false, 8>(lat, feat, p, sh, st));
   }
 }
 

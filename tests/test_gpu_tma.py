@@ -44,16 +44,23 @@ def _lattice(dims, per, vmode, delta):
 DEEP_TILE = {4: (16, 8), 8: (16, 4), 16: (8, 4)}   # the half tiles with three planes in flight
 
 
+def _variant(R, v):
+    """Launch variants of kernel 7: the large tile on 8 warps (two items per
+    thread) or on 16 warps (one item), and the half tile with the deeper rings."""
+    if v == "deep":
+        return dict(zip(("tile_x", "tile_y"), DEEP_TILE[R]))
+    return dict(threads=512) if v == "wide" else {}
+
+
 @pytest.mark.parametrize("dims,per,zs", CASES)
 @pytest.mark.parametrize("R", [4, 8, 16])
-@pytest.mark.parametrize("deep", [False, True])
-def test_tma_sweep_equals_default_sweep_and_oracle(dims, per, zs, R, deep):
+@pytest.mark.parametrize("variant", ["large", "wide", "deep"])
+def test_tma_sweep_equals_default_sweep_and_oracle(dims, per, zs, R, variant):
     lat, V = _lattice(dims, per, "stored", False)
     H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
     x = torch.from_numpy(W.gaussian_block(H.shape[0], R, 1)).to("cuda", torch.complex64)
     y0 = pv.apply_H(lat, x)
-    tile = dict(zip(("tile_x", "tile_y"), DEEP_TILE[R])) if deep else {}
-    lat.set_tuning(R, pv.C64, kernel=7, zslab=zs, **tile)
+    lat.set_tuning(R, pv.C64, kernel=7, zslab=zs, **_variant(R, variant))
     y1 = pv.apply_H(lat, x)
     assert torch.equal(y0, y1)
     ref = H @ x.cpu().numpy().astype(np.complex128)
@@ -62,7 +69,8 @@ def test_tma_sweep_equals_default_sweep_and_oracle(dims, per, zs, R, deep):
 
 @pytest.mark.parametrize("vmode,delta", [("stored", True), ("fly", False), ("zero", True)])
 @pytest.mark.parametrize("R", [4, 8, 16])
-def test_tma_fused_step_with_z_and_dots(vmode, delta, R):
+@pytest.mark.parametrize("variant", ["large", "wide"])
+def test_tma_fused_step_with_z_and_dots(vmode, delta, R, variant):
     dims, per = (24, 16, 5), (1, 0, 1)
     lat, V = _lattice(dims, per, vmode, delta)
     H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V, 0.3 if delta else 0.0, -0.2 if delta else 0.0)
@@ -76,7 +84,7 @@ def test_tma_fused_step_with_z_and_dots(vmode, delta, R):
     de = [0.5] * R
     ya, za = yin.clone(), zin.clone()
     da = pv.cheb_step(lat, x, ya, al, be, ga, z=za, delta=de, dots=7)
-    lat.set_tuning(R, pv.C64, kernel=7)
+    lat.set_tuning(R, pv.C64, kernel=7, **_variant(R, variant))
     yb, zb = yin.clone(), zin.clone()
     db = pv.cheb_step(lat, x, yb, al, be, ga, z=zb, delta=de, dots=7)
     assert torch.equal(ya, yb) and torch.equal(za, zb)
@@ -97,8 +105,8 @@ def test_tma_fused_step_with_z_and_dots(vmode, delta, R):
 
 @pytest.mark.parametrize("dims,per,zs", CASES[:3])
 @pytest.mark.parametrize("R", [4, 8, 16])
-@pytest.mark.parametrize("deep", [False, True])
-def test_tma_kpm_moments_match_oracle_and_default(dims, per, zs, R, deep):
+@pytest.mark.parametrize("variant", ["large", "wide", "deep"])
+def test_tma_kpm_moments_match_oracle_and_default(dims, per, zs, R, variant):
     lat, V = _lattice(dims, per, "stored", False)
     H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
     a, b = O.cheb_scale(*O.gershgorin(H))
@@ -106,8 +114,7 @@ def test_tma_kpm_moments_match_oracle_and_default(dims, per, zs, R, deep):
     r = W.random_phase_block(H.shape[0], R, 5)
     r0 = torch.from_numpy(r).to("cuda", torch.complex64)
     mu0 = pv.kpm_moments(lat, M, a, b, r0=r0).cpu().numpy()
-    tile = dict(zip(("tile_x", "tile_y"), DEEP_TILE[R])) if deep else {}
-    lat.set_tuning(R, pv.C64, kernel=7, zslab=zs, **tile)
+    lat.set_tuning(R, pv.C64, kernel=7, zslab=zs, **_variant(R, variant))
     mu1 = pv.kpm_moments(lat, M, a, b, r0=r0).cpu().numpy()
     assert np.max(np.abs(mu1 - mu0)) < 1e-9
     ref = O.kpm_moments(H, r, M, a, b).real
