@@ -236,7 +236,10 @@ int pvsc_cheb_step_noalloc(const pvsc_lattice* lat, int R, int prec, const void*
  * and replayed; the first call for a new argument set captures.
  * prec == PVSC_Q64 (TI only): r0, if given, is complex128 and is not modified;
  * [b - a, b + a] must hold the Gershgorin interval of H (PVSC_ERR_ARG
- * otherwise; checked by one synchronous pass over the potential per call).
+ * otherwise).  The interval is computed by one pass over the potential that
+ * synchronises the host with the stream, on the first PVSC_Q64 call after the
+ * lattice is created or its potential is set, and kept in the handle; later
+ * calls check against it and stay asynchronous.
  * complex64 on a TI lattice with tuning kernel 4: two recurrence steps per
  * sweep (dots <w_k|w_k>, Re<w_{k+1}|w_k>, <w_{k+1}|w_{k+1}>, Re<w_{k+2}|w_{k+1}>
  * give mu_2k .. mu_2k+3), the same vectors as the single sweeps; r0 is then
@@ -309,6 +312,44 @@ int pvsc_cheb_propagate(const pvsc_lattice* lat, int R, int prec, void* psi, dou
 int pvsc_cheb_adjoint_step(const pvsc_lattice* lat, int R, int prec, const void* psi_s,
                            void* G, double dt, double a, double b, double trunc,
                            double* dLdV, void* work, size_t work_bytes, void* stream);
+
+/*
+ * Chebyshev time propagation that also keeps checkpoints for the adjoint
+ * (Sec. 4.1, Eq. U_1; the checkpoints are not in the paper): the same nsteps
+ * time steps as pvsc_cheb_propagate on psi (device complex128, in/out), and
+ * before segment s (steps s*every .. min((s+1)*every, nsteps) - 1) the state
+ * psi_{s*every} is copied to ckpts + s * D * R complex128 values, for the
+ * ceil(nsteps / every) segments.  ckpts: device, caller-owned, 16-byte
+ * aligned, not overlapping psi or work.  every >= 1.
+ * work: pvsc_work_bytes(lat, PVSC_OP_SERIES, R, prec, M+1).
+ */
+int pvsc_cheb_propagate_checkpointed(const pvsc_lattice* lat, int R, int prec, void* psi,
+                                     double dt, int nsteps, int every, double a, double b,
+                                     double trunc, void* ckpts, void* work, size_t work_bytes,
+                                     void* stream);
+
+/*
+ * Adjoint of a whole checkpointed propagation with respect to the on-site
+ * potential (the paper has no adjoint): given the checkpoints written by
+ * pvsc_cheb_propagate_checkpointed (same lat, R, dt, nsteps, every, a, b,
+ * trunc, potential) and G = dL/dpsi_nsteps (device complex128, convention
+ * dL = Re <G|dpsi>), walks the segments in reverse: recomputes the states of a
+ * segment from its checkpoint with the forward series, then applies
+ * pvsc_cheb_adjoint_step from its last step to its first.  On return G holds
+ * dL/dpsi_0 and dLdV (device, n_sites doubles) has dL/dV_n added (not
+ * cleared).  a, b are held fixed.  R must be 1 and prec PVSC_C128.
+ * Runs on the stream without a CUDA graph (the recomputed states differ in
+ * every segment).  work: pvsc_propagate_adjoint_work_bytes.
+ */
+int pvsc_cheb_propagate_adjoint(const pvsc_lattice* lat, int R, int prec, const void* ckpts,
+                                double dt, int nsteps, int every, double a, double b,
+                                double trunc, void* G, double* dLdV, void* work,
+                                size_t work_bytes, void* stream);
+
+/* Work bytes of pvsc_cheb_propagate_adjoint: the states of one segment
+ * (every vectors) plus the series and adjoint-step scratch; 0 on bad input. */
+size_t pvsc_propagate_adjoint_work_bytes(const pvsc_lattice* lat, int R, int every, double a_dt,
+                                         double trunc);
 
 /*
  * Batched KPM: n independent TI lattices (uneven sizes allowed) x R
@@ -471,6 +512,18 @@ int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* best, void* s
  * (self, -x, +x, -y, +y) padded to 7 with -1, absent neighbours -1.
  * Computed by a device kernel into nbr_dev (int64, n_sites*7 or n_cells*7). */
 int pvsc_debug_neighbours(const pvsc_lattice* lat, int64_t* nbr_dev, void* stream);
+
+/* Sparsity pattern of H as the stencil applies it (debug/parity; Sec. 3.1:
+ * the matrix the matrix-free stencil never stores), as CSR over the
+ * D = n_sites * orbitals rows in the vector layout: one entry per stencil
+ * term, so a neighbour that coincides with another (a periodic axis of
+ * length 1 or 2) appears once per term and the entries of a row count the
+ * terms that land on each column; terms whose block entry is structurally
+ * zero (the zeros of the 4x4 Dirac and graphene blocks) are not listed.
+ * Host only, no device work.  rowptr: HOST array of D + 1 (always written);
+ * col: HOST array of rowptr[D] int32 column indices, or NULL to size it
+ * first.  D at most 2^24 (PVSC_ERR_ARG otherwise). */
+int pvsc_debug_export_pattern(const pvsc_lattice* lat, int64_t* rowptr, int32_t* col);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* pvsc_last_error(void);

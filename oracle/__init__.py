@@ -105,14 +105,16 @@ def _all_coords(dims) -> np.ndarray:
     return np.stack(cols, axis=1)
 
 
-def _assemble(dims, periodic, O, onsite_blocks, hop_blocks, rows=None):
+def _assemble(dims, periodic, O, onsite_blocks, hop_blocks, rows=None, terms=False):
     """Generic block assembly of sum_n Psi_n^+ E_n Psi_n + sum_{n,j}(Psi_{n+e_j}^+ B_j Psi_n + h.c.).
 
     onsite_blocks: array (n_sites, O, O) of E_n.
     hop_blocks: list of (axis, B) with B an (O, O) matrix for the bond n -> n + e_axis.
     rows: optional array of site indices whose rows are wanted (others left empty).
     Duplicate (row, col) entries, which arise for lengths 1 and 2 with periodic
-    boundaries, are summed when converting to CSR.
+    boundaries, are summed when converting to CSR.  With terms=True the COO
+    triplets are returned instead, before any summation: one (row, col, value)
+    per nonzero entry of every on-site and bond block.
     """
     n_sites = int(np.prod(dims))
     D = n_sites * O
@@ -150,13 +152,16 @@ def _assemble(dims, periodic, O, onsite_blocks, hop_blocks, rows=None):
     else:
         r = c = np.zeros(0, dtype=np.int64)
         v = np.zeros(0, dtype=np.complex128)
+    if terms:
+        nz = v != 0
+        return r[nz], c[nz], v[nz]
     H = sp.coo_matrix((v, (r, c)), shape=(D, D)).tocsr()
     H.sum_duplicates()
     H.eliminate_zeros()      # drop the structural zeros of the dense 4x4 blocks
     return H
 
 
-def ti_hamiltonian(dims, periodic, t, m, V, delta1=0.0, delta2=0.0, rows=None):
+def ti_hamiltonian(dims, periodic, t, m, V, delta1=0.0, delta2=0.0, rows=None, terms=False):
     """Eq. TB_H_topi on an Lx x Ly x Lz cuboid, as a (4N x 4N) CSR matrix.
 
     On-site block: m Gamma^1 + Delta1 Gamma^5 + Delta2 Gamma^15 + V_n Gamma^0.
@@ -172,7 +177,7 @@ def ti_hamiltonian(dims, periodic, t, m, V, delta1=0.0, delta2=0.0, rows=None):
     E0 = m * G[1] + delta1 * G[5] + delta2 * gamma_commutator(G, 1, 5)
     onsite = E0[None, :, :] + V[:, None, None] * G[0][None, :, :]
     hops = [(j, -(t / 2.0) * (G[1] - 1j * G[j + 2])) for j in range(3)]
-    return _assemble(dims, periodic, 4, onsite, hops, rows)
+    return _assemble(dims, periodic, 4, onsite, hops, rows, terms)
 
 
 # Pauli matrices of the two-band Weyl semimetal (Eq. TB_H_wsm)
@@ -181,7 +186,7 @@ _PAULI = (np.array([[0, 1], [1, 0]], dtype=np.complex128),
           np.array([[1, 0], [0, -1]], dtype=np.complex128))
 
 
-def wsm_hamiltonian(dims, periodic, V, k0=math.pi / 2, rows=None):
+def wsm_hamiltonian(dims, periodic, V, k0=math.pi / 2, rows=None, terms=False):
     """Eq. TB_H_wsm on an Lx x Ly x Lz cuboid, as a (2N x 2N) CSR matrix.
 
     Two orbitals per site (row index = 2 site + orbital).  Bond n -> n + e_x:
@@ -195,7 +200,7 @@ def wsm_hamiltonian(dims, periodic, V, k0=math.pi / 2, rows=None):
     V = np.asarray(V, dtype=np.float64).reshape(n_sites)
     onsite = V[:, None, None] * np.eye(2)[None, :, :] - (2.0 + math.cos(k0)) * sx[None, :, :]
     hops = [(0, sx / 2.0), (1, (sx + 1j * sy) / 2.0), (2, (sx + 1j * sz) / 2.0)]
-    return _assemble(dims, periodic, 2, onsite, hops, rows)
+    return _assemble(dims, periodic, 2, onsite, hops, rows, terms)
 
 
 # The 4x4 matrices of Eq. graphene_model (entries in units of t)
@@ -204,7 +209,7 @@ GRAPHENE_TY = np.array([[0, 0, 0, -1], [0, 0, 0, 0], [0, 0, 0, 0], [0, 0, 0, 0]]
 GRAPHENE_TN = np.array([[0, -1, 0, 0], [-1, 0, -1, 0], [0, -1, 0, -1], [0, 0, -1, 0]], dtype=np.complex128)
 
 
-def graphene_hamiltonian(cells, periodic, t, V, rows=None, Tx=None, Ty=None, Tn=None):
+def graphene_hamiltonian(cells, periodic, t, V, rows=None, Tx=None, Ty=None, Tn=None, terms=False):
     """Eq. graphene_model on an Nx x Ny array of 4-site cells, as a (4NxNy)^2 CSR matrix.
 
     H = sum_n (Psi_{n+x}^+ T_x Psi_n + Psi_{n+y}^+ T_y Psi_n + h.c.)
@@ -221,7 +226,7 @@ def graphene_hamiltonian(cells, periodic, t, V, rows=None, Tx=None, Ty=None, Tn=
     V = np.asarray(V, dtype=np.float64).reshape(n_cells, 4)
     onsite = t * Tn[None, :, :] + np.einsum("ca,ab->cab", V, np.eye(4))
     hops = [(0, t * Tx), (1, t * Ty)]
-    return _assemble(dims, periodic, 4, onsite, hops, rows)
+    return _assemble(dims, periodic, 4, onsite, hops, rows, terms)
 
 
 # ----------------------------------------------------------------------------

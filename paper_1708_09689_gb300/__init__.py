@@ -97,6 +97,10 @@ _SIGNATURES = {
     "pvsc_propagation_coeffs": (_i, [_d, _d, _i, _dp, ctypes.POINTER(ctypes.c_int)]),
     "pvsc_cheb_propagate": (_i, [_vp, _i, _i, _vp, _d, _i, _d, _d, _d, _vp, _sz, _vp]),
     "pvsc_cheb_adjoint_step": (_i, [_vp, _i, _i, _vp, _vp, _d, _d, _d, _d, _vp, _vp, _sz, _vp]),
+    "pvsc_cheb_propagate_checkpointed": (_i, [_vp, _i, _i, _vp, _d, _i, _i, _d, _d, _d, _vp, _vp, _sz, _vp]),
+    "pvsc_cheb_propagate_adjoint": (_i, [_vp, _i, _i, _vp, _d, _i, _i, _d, _d, _d, _vp, _vp, _vp, _sz, _vp]),
+    "pvsc_propagate_adjoint_work_bytes": (_sz, [_vp, _i, _i, _d, _d]),
+    "pvsc_debug_export_pattern": (_i, [_vp, _vp, _vp]),
     "pvsc_kpm_moments_batched": (_i, [ctypes.POINTER(_vp), _i, _i, _i, ctypes.POINTER(_u64), _i,
                                       _dp, _dp, _vp, _vp, _sz, _vp]),
     "pvsc_batched_work_bytes": (_sz, [ctypes.POINTER(_vp), _i, _i, _i, _i]),
@@ -289,6 +293,15 @@ class Lattice:
         _check(_lib.pvsc_debug_neighbours(self._h, _ptr(out), _stream(stream)))
         return out
 
+    def export_pattern(self):
+        """(rowptr, col) numpy arrays: the stencil's terms per row (pvsc_debug_export_pattern)."""
+        import numpy as np
+        rowptr = np.zeros(self.D + 1, dtype=np.int64)
+        _check(_lib.pvsc_debug_export_pattern(self._h, rowptr.ctypes.data, None))
+        col = np.zeros(int(rowptr[-1]), dtype=np.int32)
+        _check(_lib.pvsc_debug_export_pattern(self._h, rowptr.ctypes.data, col.ctypes.data))
+        return rowptr, col
+
     def set_tuning(self, R: int, prec: int, threads: int = 256, blocks_per_sm: int = 0,
                    zslab: int = 0, vpt: int = 0, tile_x: int = 0, tile_y: int = 0,
                    kernel: int = 0):
@@ -428,6 +441,36 @@ def cheb_adjoint_step(lat: Lattice, psi_s, G, dt, a, b, dLdV, trunc=1e-14, work=
     _check(_lib.pvsc_cheb_adjoint_step(lat.handle, block_R(psi_s), C128, _ptr(psi_s), _ptr(G), float(dt),
                                        float(a), float(b), float(trunc), _ptr(dLdV), _ptr(work),
                                        work.numel(), _stream(stream)))
+    return G
+
+
+def cheb_propagate_checkpointed(lat: Lattice, psi, dt, nsteps, every, a, b, trunc=1e-14, ckpts=None,
+                                work=None, stream=None):
+    """psi <- U(dt)^nsteps psi in place (complex128), keeping psi at steps 0, every,
+    2 every, ... in ckpts (a complex128 tensor (nseg, D[, R]), allocated if None)."""
+    R = block_R(psi)
+    nseg = (int(nsteps) + int(every) - 1) // int(every)
+    if ckpts is None:
+        ckpts = torch.empty((max(nseg, 1),) + tuple(psi.shape), dtype=torch.complex128, device=psi.device)
+    if work is None:
+        K = len(propagation_coeffs(a * dt, trunc))
+        work = work_buffer(lat.work_bytes(OP_SERIES, R, C128, K))
+    _check(_lib.pvsc_cheb_propagate_checkpointed(
+        lat.handle, R, C128, _ptr(psi), float(dt), int(nsteps), int(every), float(a), float(b), float(trunc),
+        _ptr(ckpts), _ptr(work), work.numel(), _stream(stream)))
+    return psi, ckpts
+
+
+def cheb_propagate_adjoint(lat: Lattice, ckpts, G, dt, nsteps, every, a, b, dLdV, trunc=1e-14, work=None,
+                           stream=None):
+    """G <- dL/dpsi_0 and dLdV += dL/dV of the whole checkpointed propagation
+    (G holds dL/dpsi_nsteps on entry)."""
+    if work is None:
+        nb = int(_lib.pvsc_propagate_adjoint_work_bytes(lat.handle, 1, int(every), float(a * dt), float(trunc)))
+        work = work_buffer(nb)
+    _check(_lib.pvsc_cheb_propagate_adjoint(
+        lat.handle, block_R(G), C128, _ptr(ckpts), float(dt), int(nsteps), int(every), float(a), float(b),
+        float(trunc), _ptr(G), _ptr(dLdV), _ptr(work), work.numel(), _stream(stream)))
     return G
 
 

@@ -490,19 +490,29 @@ static int kpm_moments_fx(const pvsc_lattice* lat, int R, const void* r0, uint64
   const FxLayout L = fx_layout(lat, R);
   if (int rc = check_work(work, work_bytes, L.total)) return rc;
   // The fixed-point range relies on ||T_k(H~)|| <= 1: (a, b) must hold the
-  // Gershgorin interval (one synchronous pass over the potential).
+  // Gershgorin interval.  It is computed once per potential (one synchronous
+  // pass, on the first call after lattice creation or pvsc_set_potential) and
+  // kept in the handle; later calls check against it without synchronising.
   {
-    const int grid = 2 * lat->sm_count;
-    double* gw = reinterpret_cast<double*>(wptr(work, kWorkHeader));
-    if (int rc = launch_gershgorin(lat->g, gw, grid, st)) return rc;
-    std::vector<double> h(2 * grid);
-    PVSC_CUDA_TRY(cudaMemcpyAsync(h.data(), gw, sizeof(double) * 2 * grid, cudaMemcpyDeviceToHost, st));
-    PVSC_CUDA_TRY(cudaStreamSynchronize(st));
-    double lo = h[0], hi = h[1];
-    for (int i = 1; i < grid; ++i) {
-      lo = std::fmin(lo, h[2 * i]);
-      hi = std::fmax(hi, h[2 * i + 1]);
+    pvsc_lattice* ml = const_cast<pvsc_lattice*>(lat);
+    if (!lat->gersh_valid) {
+      const int grid = 2 * lat->sm_count;
+      double* gw = reinterpret_cast<double*>(wptr(work, kWorkHeader));
+      if (int rc = launch_gershgorin(lat->g, gw, grid, st)) return rc;
+      std::vector<double> h(2 * grid);
+      PVSC_CUDA_TRY(cudaMemcpyAsync(h.data(), gw, sizeof(double) * 2 * grid, cudaMemcpyDeviceToHost, st));
+      PVSC_CUDA_TRY(cudaStreamSynchronize(st));
+      double lo = h[0], hi = h[1];
+      for (int i = 1; i < grid; ++i) {
+        lo = std::fmin(lo, h[2 * i]);
+        hi = std::fmax(hi, h[2 * i + 1]);
+      }
+      std::lock_guard<std::mutex> lk(ml->mu);
+      ml->gersh_lo = lo;
+      ml->gersh_hi = hi;
+      ml->gersh_valid = true;
     }
+    const double lo = lat->gersh_lo, hi = lat->gersh_hi;
     const double slack = 1e-12 * a;
     if (lo < b - a - slack || hi > b + a + slack)
       return set_error(PVSC_ERR_ARG,
@@ -810,6 +820,88 @@ int pvsc_cheb_adjoint_step(const pvsc_lattice* lat, int R, int prec, const void*
     p.wg = nullptr;
     p.grad = nullptr;
     if (int rc = launch_sweep(lat, prec, F_ADJ, p, st)) return rc;
+  }
+  return PVSC_OK;
+}
+
+int pvsc_cheb_propagate_checkpointed(const pvsc_lattice* lat, int R, int prec, void* psi, double dt,
+                                     int nsteps, int every, double a, double b, double trunc, void* ckpts,
+                                     void* work, size_t work_bytes, void* stream) {
+  if (int rc = check_common(lat, R, prec)) return rc;
+  if (int rc = check_ptr(psi, "psi")) return rc;
+  if (int rc = check_ptr(ckpts, "ckpts")) return rc;
+  if (every < 1) return set_error(PVSC_ERR_ARG, "every = %d < 1", every);
+  if (nsteps < 0) return set_error(PVSC_ERR_ARG, "nsteps = %d < 0", nsteps);
+  if (ckpts == psi || ckpts == work) return set_error(PVSC_ERR_ARG, "ckpts must not overlap psi or work");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t vb = vec_bytes(lat, R, PVSC_C128);
+  for (int s0 = 0, seg = 0; s0 < nsteps; s0 += every, ++seg) {
+    PVSC_CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(ckpts) + (size_t)seg * vb, psi, vb,
+                                  cudaMemcpyDeviceToDevice, st));
+    const int n = nsteps - s0 < every ? nsteps - s0 : every;
+    if (int rc = pvsc_cheb_propagate(lat, R, prec, psi, dt, n, a, b, trunc, work, work_bytes, stream))
+      return rc;
+  }
+  return PVSC_OK;
+}
+
+size_t pvsc_propagate_adjoint_work_bytes(const pvsc_lattice* lat, int R, int every, double a_dt,
+                                         double trunc) {
+  if (!lat || R != 1 || every < 1) return 0;
+  std::vector<cd> cw;
+  if (propagation_weights(a_dt, trunc, cw) != PVSC_OK) return 0;
+  const int K = (int)cw.size();
+  const size_t vb = vec_bytes(lat, R, PVSC_C128);
+  const size_t ser = (pvsc_work_bytes(lat, PVSC_OP_SERIES, R, PVSC_C128, K) + 255) & ~size_t(255);
+  const size_t adj = pvsc_work_bytes(lat, PVSC_OP_ADJOINT, R, PVSC_C128, K);
+  return (size_t)every * vb + ser + adj;
+}
+
+int pvsc_cheb_propagate_adjoint(const pvsc_lattice* lat, int R, int prec, const void* ckpts, double dt,
+                                int nsteps, int every, double a, double b, double trunc, void* G,
+                                double* dLdV, void* work, size_t work_bytes, void* stream) {
+  if (int rc = check_common(lat, R, prec)) return rc;
+  if (prec != PVSC_C128) return set_error(PVSC_ERR_UNSUPPORTED, "the adjoint runs in complex128 only");
+  if (R != 1) return set_error(PVSC_ERR_UNSUPPORTED, "the adjoint takes one vector (R = 1)");
+  if (int rc = check_scaling(a, b)) return rc;
+  if (int rc = check_ptr(ckpts, "ckpts")) return rc;
+  if (int rc = check_ptr(G, "G")) return rc;
+  if (!dLdV) return set_error(PVSC_ERR_ARG, "dLdV is NULL");
+  if (every < 1) return set_error(PVSC_ERR_ARG, "every = %d < 1", every);
+  if (nsteps < 0) return set_error(PVSC_ERR_ARG, "nsteps = %d < 0", nsteps);
+  if (!std::isfinite(dt)) return set_error(PVSC_ERR_ARG, "dt is not finite");
+  const size_t need = pvsc_propagate_adjoint_work_bytes(lat, R, every, a * dt, trunc);
+  if (need == 0) return set_error(PVSC_ERR_ARG, "invalid a * dt or trunc");
+  if (int rc = check_work(work, work_bytes, need)) return rc;
+  if (nsteps == 0) return PVSC_OK;
+  std::vector<cd> cw;
+  if (int rc = propagation_weights(a * dt, trunc, cw)) return rc;
+  const int K = (int)cw.size();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t vb = vec_bytes(lat, R, PVSC_C128);
+  const size_t ser = (pvsc_work_bytes(lat, PVSC_OP_SERIES, R, PVSC_C128, K) + 255) & ~size_t(255);
+  const size_t adj = pvsc_work_bytes(lat, PVSC_OP_ADJOINT, R, PVSC_C128, K);
+  char* states = static_cast<char*>(work);
+  void* swork = states + (size_t)every * vb;
+  void* awork = states + (size_t)every * vb + ser;
+  const cd ph = std::exp(cd(0, -b * dt));
+  const int nseg = (nsteps + every - 1) / every;
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int s0 = seg * every;
+    const int n = nsteps - s0 < every ? nsteps - s0 : every;
+    // the states psi_{s0} .. psi_{s0+n-1} of this segment, from its checkpoint
+    PVSC_CUDA_TRY(cudaMemcpyAsync(states, static_cast<const char*>(ckpts) + (size_t)seg * vb, vb,
+                                  cudaMemcpyDeviceToDevice, st));
+    for (int j = 1; j < n; ++j) {
+      void* sj = states + (size_t)j * vb;
+      PVSC_CUDA_TRY(cudaMemcpyAsync(sj, states + (size_t)(j - 1) * vb, vb, cudaMemcpyDeviceToDevice, st));
+      if (int rc = run_series(lat, R, PVSC_C128, sj, sj, cw, ph, a, b, swork, st)) return rc;
+    }
+    // the adjoint steps, last to first
+    for (int j = n - 1; j >= 0; --j)
+      if (int rc = pvsc_cheb_adjoint_step(lat, R, prec, states + (size_t)j * vb, G, dt, a, b, trunc, dLdV,
+                                          awork, adj, stream))
+        return rc;
   }
   return PVSC_OK;
 }

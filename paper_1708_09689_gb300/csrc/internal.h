@@ -138,6 +138,10 @@ struct pvsc_lattice {
   // other lattices' geometry (the batched KPM) key on it, so that a changed
   // potential or a new lattice at a reused address never replays old arguments.
   uint64_t generation = 0;
+  // exact Gershgorin interval of H, kept once computed (the fixed-point KPM
+  // checks its scaling against it); cleared when the potential changes
+  bool gersh_valid = false;
+  double gersh_lo = 0.0, gersh_hi = 0.0;
   std::mutex mu;
   ~pvsc_lattice();
 };

@@ -8,6 +8,8 @@
 #include <new>
 #include <string>
 
+#include <vector>
+
 #include "internal.h"
 
 namespace pvsc {
@@ -256,6 +258,7 @@ int pvsc_set_potential(pvsc_lattice* lat, const double* V_dev, void* stream) {
     // cached graphs captured with V = 0 read no potential: drop them
     drop_graphs(lat);
   }
+  lat->gersh_valid = false;
   PVSC_CUDA_TRY(cudaMemcpyAsync(lat->V_dev, V_dev, sizeof(double) * lat->g.n_sites,
                                 cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
   return launch_potential_f32(lat->V_dev, lat->V32_dev, lat->g.n_sites, static_cast<cudaStream_t>(stream));
@@ -296,6 +299,77 @@ int pvsc_debug_neighbours(const pvsc_lattice* lat, int64_t* nbr_dev, void* strea
   if (int rc = check_lattice(lat)) return rc;
   if (!nbr_dev) return set_error(PVSC_ERR_ARG, "nbr_dev is NULL");
   return launch_neighbours(lat->g, nbr_dev, static_cast<cudaStream_t>(stream));
+}
+
+// Sparsity pattern of H as the stencil applies it (host only).  Per row, one
+// entry per stencil term in the order the sweeps take them; a term whose
+// coefficient block entry is structurally zero is not listed.
+//   TI (row = 4 n + o): the diagonal (m Gamma^1 + V), the Delta terms (o ^ 1)
+//     when present, then for the neighbours z-, z+, x-, x+, y-, y+ the
+//     Gamma^1 part (same orbital) and the Gamma^{j+1} part (orbital 3 - o along
+//     x and y, o ^ 1 along z) of the bond block.
+//   Graphene (row = 4 c + nu): the diagonal, then the chain and bond couplings
+//     of Eq. graphene_model in the order of the graphene sweep.
+//   Weyl semimetal (row = 2 n + o): the diagonal, the on-site sigma_x term
+//     (orbital 1 - o), the x-/x+ bonds (1 - o), then one term each along y
+//     and z (row 0 takes orbital 1 of n - e_j, row 1 orbital 0 of n + e_j).
+int pvsc_debug_export_pattern(const pvsc_lattice* lat, int64_t* rowptr, int32_t* col) {
+  if (int rc = check_lattice(lat)) return rc;
+  if (!rowptr) return set_error(PVSC_ERR_ARG, "rowptr is NULL");
+  const Geometry& g = lat->g;
+  const int O = orbitals_of(g.model);
+  const int64_t D = g.n_sites * O;
+  if (D > (int64_t(1) << 24)) return set_error(PVSC_ERR_ARG, "pattern export is for small lattices (D = %lld > 2^24)", (long long)D);
+  std::vector<int64_t> cols;
+  cols.reserve(16);
+  int64_t nnz = 0;
+  auto put = [&](int64_t c) {
+    if (c >= 0) cols.push_back(c);
+  };
+  for (int64_t row = 0; row < D; ++row) {
+    cols.clear();
+    if (g.model == PVSC_GRAPHENE) {
+      const int64_t Nx = g.L[0], Ny = g.L[1];
+      const int64_t c = row >> 2, nu = row & 3, y = c / Nx, x = c - y * Nx;
+      const int64_t cxm = nbr_minus(c, x, Nx, g.per[0], 1), cxp = nbr_plus(c, x, Nx, g.per[0], 1);
+      const int64_t cym = nbr_minus(c, y, Ny, g.per[1], Nx), cyp = nbr_plus(c, y, Ny, g.per[1], Nx);
+      auto at = [](int64_t cell, int s) { return cell >= 0 ? 4 * cell + s : (int64_t)-1; };
+      put(row);
+      if (nu == 0) { put(at(c, 1)); put(at(cxp, 1)); put(at(cym, 3)); }
+      if (nu == 1) { put(at(c, 0)); put(at(c, 2)); put(at(cxm, 0)); }
+      if (nu == 2) { put(at(c, 1)); put(at(c, 3)); put(at(cxm, 3)); }
+      if (nu == 3) { put(at(c, 2)); put(at(cxp, 2)); put(at(cyp, 0)); }
+    } else {
+      const int64_t Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], plane = Lx * Ly;
+      const int64_t n = row / O, o = row - n * O;
+      const int64_t z = n / plane, y = (n - z * plane) / Lx, x = n - z * plane - y * Lx;
+      const int64_t zm = nbr_minus(n, z, Lz, g.per[2], plane), zp = nbr_plus(n, z, Lz, g.per[2], plane);
+      const int64_t xm = nbr_minus(n, x, Lx, g.per[0], 1), xp = nbr_plus(n, x, Lx, g.per[0], 1);
+      const int64_t ym = nbr_minus(n, y, Ly, g.per[1], Lx), yp = nbr_plus(n, y, Ly, g.per[1], Lx);
+      auto at = [&](int64_t site, int64_t orb) { return site >= 0 ? O * site + orb : (int64_t)-1; };
+      put(row);
+      if (g.model == PVSC_TI) {
+        if (g.has_delta) put(at(n, o ^ 1));
+        const int64_t nb[6] = {zm, zp, xm, xp, ym, yp};
+        for (int k = 0; k < 6; ++k) {
+          put(at(nb[k], o));                                // Gamma^1 part of the bond block
+          put(at(nb[k], k < 2 ? (o ^ 1) : (3 - o)));        // Gamma^{j+1} part
+        }
+      } else {  // Weyl semimetal
+        put(at(n, 1 - o));
+        put(at(xm, 1 - o));
+        put(at(xp, 1 - o));
+        put(o == 0 ? at(ym, 1) : at(yp, 0));
+        put(o == 0 ? at(zm, 1) : at(zp, 0));
+      }
+    }
+    rowptr[row] = nnz;
+    if (col)
+      for (size_t k = 0; k < cols.size(); ++k) col[nnz + (int64_t)k] = (int32_t)cols[k];
+    nnz += (int64_t)cols.size();
+  }
+  rowptr[D] = nnz;
+  return PVSC_OK;
 }
 
 }  // extern "C"

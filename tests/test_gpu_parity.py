@@ -317,3 +317,84 @@ def test_adjoint_step_matches_oracle_gradient():
     loss.backward()
     g = host(Vt.grad)
     assert np.max(np.abs(g - ref)) / np.max(np.abs(ref)) < 1e-9
+
+
+@pytest.mark.parametrize("S,every", [(7, 3), (6, 6), (5, 1), (4, 10)])
+def test_whole_propagation_adjoint_through_the_c_abi(S, every):
+    # pvsc_cheb_propagate_checkpointed + pvsc_cheb_propagate_adjoint (one call each)
+    # against the oracle's reverse sweep: dL/dV and dL/dpsi_0, segments of every
+    # length (a last partial segment, one segment, one-step segments, every > S)
+    cfg = W.GrapheneConfig(cells=(10, 8), ndots=2, R_dot=3.0, sigma=4.0, packet_offset=5.0)
+    V = cfg.potential()
+    psi0 = cfg.packet()
+    H = O.graphene_hamiltonian(cfg.cells, (0, 0), 1.0, V)
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    dt = 0.9
+    psiS = O.propagate(H, psi0, dt, S, a, b)
+    mask = cfg.detector() | (np.arange(len(V)) % 5 == 0)
+    Gf = 2.0 * mask * psiS
+    ref, refG0 = O.propagate_adjoint(H, psi0, dt, S, a, b, Gf, O=1)
+    lat = pv.Lattice.graphene(cfg.cells, (0, 0), V=V)
+    psi = dev(psi0)
+    psi, ckpts = pv.cheb_propagate_checkpointed(lat, psi, dt, S, every, a, b)
+    assert relerr(host(psi), psiS) < 1e-12
+    assert ckpts.shape[0] == -(-S // every)
+    assert relerr(host(ckpts[0]), psi0) == 0.0
+    G = dev(Gf)
+    dLdV = torch.zeros(len(V), dtype=torch.float64, device="cuda")
+    pv.cheb_propagate_adjoint(lat, ckpts, G, dt, S, every, a, b, dLdV)
+    g = host(dLdV)
+    assert np.max(np.abs(g - ref)) / np.max(np.abs(ref)) < 1e-9
+    assert relerr(host(G), refG0[:, 0]) < 1e-9
+
+
+def test_whole_propagation_adjoint_rejects_bad_arguments():
+    lat = pv.Lattice.graphene((4, 4), (0, 0))
+    x = torch.zeros(64, dtype=torch.complex128, device="cuda")
+    ck = torch.zeros((2, 64), dtype=torch.complex128, device="cuda")
+    g = torch.zeros(16 * 4, dtype=torch.float64, device="cuda")
+    with pytest.raises(pv.PvscError, match="every"):
+        pv.cheb_propagate_adjoint(lat, ck, x, 1.0, 2, 0, 3.1, 0.0, g,
+                                  work=pv.work_buffer(1 << 20))
+    x2 = torch.zeros((64, 2), dtype=torch.complex128, device="cuda")
+    with pytest.raises(pv.PvscError, match="R = 1"):
+        pv.cheb_propagate_adjoint(lat, ck, x2, 1.0, 2, 1, 3.1, 0.0, g, work=pv.work_buffer(1 << 22))
+
+
+def _rows_multisets(rowptr, col):
+    return [sorted(col[rowptr[i]:rowptr[i + 1]].tolist()) for i in range(len(rowptr) - 1)]
+
+
+@pytest.mark.parametrize("model,dims,per", [
+    ("ti", (4, 3, 5), (1, 1, 0)), ("ti", (2, 1, 3), (1, 1, 1)), ("ti", (3, 2, 2), (0, 1, 1)),
+    ("ti_delta", (3, 4, 2), (1, 0, 1)), ("graphene", (4, 3), (1, 0)), ("graphene", (2, 1), (1, 1)),
+    ("wsm", (4, 3, 2), (1, 1, 0)), ("wsm", (2, 2, 1), (1, 1, 1))])
+def test_exported_pattern_counts_every_stencil_term_of_the_oracle(model, dims, per):
+    # the C ABI's CSR pattern (one entry per stencil term, duplicates kept) equals,
+    # row by row as a multiset, the oracle's COO terms before they are summed;
+    # periodic lengths 1 and 2 make coinciding neighbours, counted once per term
+    n = int(np.prod(dims))
+    if model.startswith("ti"):
+        V = W.disorder_potential(n, 1.0, 4)
+        kw = dict(delta1=0.3, delta2=0.2) if model == "ti_delta" else {}
+        lat = pv.Lattice.ti(dims, per, V=V, **kw)
+        r, c, _ = O.ti_hamiltonian(dims, per, 1.0, 2.0, V, kw.get("delta1", 0.0), kw.get("delta2", 0.0),
+                                   terms=True)
+        D = 4 * n
+    elif model == "graphene":
+        V = W.disorder_potential(4 * n, 1.0, 4)
+        lat = pv.Lattice.graphene(dims, per, V=V)
+        r, c, _ = O.graphene_hamiltonian(dims, per, 1.0, V, terms=True)
+        D = 4 * n
+    else:
+        V = W.disorder_potential(n, 1.0, 4)
+        lat = pv.Lattice.wsm(dims, per, V=V)
+        r, c, _ = O.wsm_hamiltonian(dims, per, V, terms=True)
+        D = 2 * n
+    rowptr, col = lat.export_pattern()
+    assert len(rowptr) == D + 1 and rowptr[-1] == len(c)
+    order = np.lexsort((c, r))
+    ref = [[] for _ in range(D)]
+    for i, j in zip(r[order], c[order]):
+        ref[i].append(int(j))
+    assert _rows_multisets(rowptr, col) == ref

@@ -129,3 +129,24 @@ def test_q64_prefetch_variants_are_bitwise_identical():
         shape.update(bad)
         with pytest.raises(pv.PvscError):
             lat.set_tuning(4, pv.Q64, **shape)
+
+
+def test_q64_scaling_check_follows_a_new_potential():
+    # the Gershgorin interval is kept in the handle after the first call; a new
+    # potential must renew it, so a scaling that held the old spectrum is refused
+    dims, per = (6, 5, 4), (1, 1, 0)
+    n = int(np.prod(dims))
+    lat = pv.Lattice.ti(dims, per, V=np.zeros(n))
+    _, _, a, b = lat.spectral_bounds()
+    r0 = torch.from_numpy(W.random_phase_block(4 * n, 2, 3)).cuda()
+    pv.kpm_moments(lat, 8, a, b, r0=r0, prec=pv.Q64)
+    pv.kpm_moments(lat, 8, a, b, r0=r0, prec=pv.Q64)  # the kept interval
+    lat.set_potential(torch.from_numpy(W.disorder_potential(n, 6.0, 1)).cuda())
+    with pytest.raises(pv.PvscError) as e:
+        pv.kpm_moments(lat, 8, a, b, r0=r0, prec=pv.Q64)
+    assert e.value.code == pv.PVSC_ERR_ARG
+    _, _, a2, b2 = lat.spectral_bounds()
+    mu = pv.kpm_moments(lat, 8, a2, b2, r0=r0, prec=pv.Q64).cpu().numpy()
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, W.disorder_potential(n, 6.0, 1))
+    ref = O.kpm_moments(H, r0.cpu().numpy(), 8, a2, b2).real
+    assert np.max(np.abs(mu - ref)) < TOL

@@ -663,3 +663,28 @@ def test_wsm_spectral_function_peaks_at_the_closed_form_band(k):
         m = (E > e - 0.3) & (E < e + 0.3)
         assert abs(E[m][np.argmax(A[m])] - e) < 2e-3
         assert abs(np.trapezoid(A[m], E[m]) - (2.0 if e0 < 1e-12 else 1.0)) < 3e-3
+
+
+def test_oracle_terms_count_the_couplings_of_every_row():
+    # Eq. TB_H_topi per row: the diagonal plus, for each of the six neighbours,
+    # the Gamma^1 entry and the one Gamma^{j+1} entry of the bond block: 13 terms.
+    # On a periodic axis of length 2 both neighbours are the same site: the 13
+    # terms fall on 11 distinct columns, and in the summed matrix the Gamma^{j+1}
+    # parts of A_j and A_j^+ cancel (A_j + A_j^+ = -t Gamma^1), leaving 10.
+    V = W.disorder_potential(27, 1.0, 3)
+    r, c, _ = O.ti_hamiltonian((3, 3, 3), (1, 1, 1), 1.0, 2.0, V, terms=True)
+    assert np.all(np.bincount(r) == 13)
+    assert all(len(set(c[r == i])) == 13 for i in range(0, 108, 7))
+    V = W.disorder_potential(18, 1.0, 3)
+    r, c, _ = O.ti_hamiltonian((3, 2, 3), (1, 1, 1), 1.0, 2.0, V, terms=True)
+    assert np.all(np.bincount(r) == 13)
+    assert all(len(set(c[r == i])) == 11 for i in range(72))
+    H = O.ti_hamiltonian((3, 2, 3), (1, 1, 1), 1.0, 2.0, V)
+    assert np.all(np.diff(H.indptr) == 10)
+    # open corner site of a 3x3x3 cube: the diagonal and three bonds
+    r, c, _ = O.ti_hamiltonian((3, 3, 3), (0, 0, 0), 1.0, 2.0, W.disorder_potential(27, 1.0, 3), terms=True)
+    assert np.bincount(r)[0] == 7
+    # graphene (Eq. graphene_model): every site has three bonds plus its potential
+    V = W.disorder_potential(48, 1.0, 2)
+    r, _, _ = O.graphene_hamiltonian((4, 3), (1, 1), 1.0, V, terms=True)
+    assert np.all(np.bincount(r) == 4)
