@@ -311,8 +311,9 @@ int pvsc_debug_neighbours(const pvsc_lattice* lat, int64_t* nbr_dev, void* strea
 //   Graphene (row = 4 c + nu): the diagonal, then the chain and bond couplings
 //     of Eq. graphene_model in the order of the graphene sweep.
 //   Weyl semimetal (row = 2 n + o): the diagonal, the on-site sigma_x term
-//     (orbital 1 - o), the x-/x+ bonds (1 - o), then one term each along y
-//     and z (row 0 takes orbital 1 of n - e_j, row 1 orbital 0 of n + e_j).
+//     (orbital 1 - o), the x-/x+ bonds (1 - o), one term along y (row 0 takes
+//     orbital 1 of n - e_y, row 1 orbital 0 of n + e_y), and along z both
+//     orbitals of both neighbours ((sigma_x + i sigma_z)/2 has no zero entry).
 int pvsc_debug_export_pattern(const pvsc_lattice* lat, int64_t* rowptr, int32_t* col) {
   if (int rc = check_lattice(lat)) return rc;
   if (!rowptr) return set_error(PVSC_ERR_ARG, "rowptr is NULL");
@@ -360,7 +361,10 @@ int pvsc_debug_export_pattern(const pvsc_lattice* lat, int64_t* rowptr, int32_t*
         put(at(xm, 1 - o));
         put(at(xp, 1 - o));
         put(o == 0 ? at(ym, 1) : at(yp, 0));
-        put(o == 0 ? at(zm, 1) : at(zp, 0));
+        put(at(zm, 1 - o));  // (sigma_x + i sigma_z)/2 and its conjugate: both orbitals
+        put(at(zp, 1 - o));
+        put(at(zm, o));
+        put(at(zp, o));
       }
     }
     rowptr[row] = nnz;
