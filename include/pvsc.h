@@ -98,6 +98,22 @@ enum {
 };
 
 /*
+ * Lattice flags.  PVSC_LATTICE_Z_HALO_LO / _HI (TI only; the z axis open, at
+ * least one plane besides the halo planes, the potential zero or given on the
+ * host or device as the slab's part of the global potential, halo planes
+ * included): the lattice is one z-slab of a larger lattice split along z (the
+ * domain decomposition of Sec. 3.4).  With _LO plane 0, with _HI plane Lz-1 is
+ * a halo plane that holds a copy of the neighbouring slab's boundary plane:
+ * every sweep reads it as the z-neighbour of the plane next to it but updates,
+ * writes and reduces (dot products, moments) the other planes only, the
+ * spectral bounds cover the rows of those planes only, and the launch shape is
+ * the default z-march whatever the tuning.  A slab at an open end of the
+ * global lattice has no halo plane on that side.  The caller fills the halo
+ * planes of every sweep input.  Not for the batched or fixed-point KPM.
+ */
+enum { PVSC_LATTICE_Z_HALO_LO = 1, PVSC_LATTICE_Z_HALO_HI = 2, PVSC_LATTICE_Z_HALO = 3 };
+
+/*
  * Lattice description.  Defines H for one lattice: the model equation, the
  * cuboid and its boundary conditions (Sec. 3.4: per-dimension periodic or
  * open), the couplings and the on-site potential.  dims: TI (Lx, Ly, Lz)
@@ -117,7 +133,7 @@ typedef struct {
   double delta1;        /* TI on-site Delta_1 Gamma^5 (Eq. TB_H_topi); 0 for graphene */
   double delta2;        /* TI on-site Delta_2 Gamma^15, Gamma^15 = [Gamma^1, Gamma^5]/2i */
   int32_t v_source;     /* PVSC_V_* */
-  int32_t reserved;
+  int32_t flags;        /* 0 or PVSC_LATTICE_Z_HALO_LO | PVSC_LATTICE_Z_HALO_HI */
   const double* V;      /* for PVSC_V_HOST / PVSC_V_DEVICE, else ignored */
   uint64_t seed;        /* for PVSC_V_SEED / PVSC_V_ON_THE_FLY */
   double W;             /* disorder width for PVSC_V_SEED / PVSC_V_ON_THE_FLY */
@@ -312,6 +328,27 @@ int pvsc_cheb_propagate(const pvsc_lattice* lat, int R, int prec, void* psi, dou
 int pvsc_cheb_adjoint_step(const pvsc_lattice* lat, int R, int prec, const void* psi_s,
                            void* G, double dt, double a, double b, double trunc,
                            double* dLdV, void* work, size_t work_bytes, void* stream);
+
+/*
+ * KPM recurrence sweeps k_begin .. k_end-1 with caller-held vectors (the
+ * recurrence and doubling identities of pvsc_kpm_moments, Sec. 2.2, Sec. 4):
+ * resumable KPM (two calls over [0, K) and [K, K') give the moments and vectors
+ * of one call over [0, K') bit for bit) and the per-sweep form that a
+ * domain-decomposed lattice needs between halo exchanges.  Sweep k makes
+ * w_{k+1} = 2 H~ w_k - w_{k-1} (k = 0: w_1 = H~ w_0) fused with the dot
+ * products that give mu_{2k} = 2 <w_k|w_k> - mu_0 and mu_{2k+1} =
+ * 2 Re <w_{k+1}|w_k> - mu_1 (k = 0: mu_0, mu_1), written to mu [R][M]
+ * (device; sweeps k >= 1 read mu_0 and mu_1 from it).  w_j lives in wa for
+ * even j and in wb for odd j: w_{k+1} overwrites w_{k-1} element by element.
+ * On a lattice with halo planes (PVSC_LATTICE_Z_HALO_*) the dots (and so the
+ * moments) cover the other planes only: summed over the slabs of a lattice
+ * split along z they give the global moments.
+ * 0 <= k_begin <= k_end <= ceil(M/2).  Direct launches (no CUDA graph).
+ * work: pvsc_work_bytes(lat, PVSC_OP_CHEB_STEP, R, prec, 0).
+ */
+int pvsc_kpm_sweeps(const pvsc_lattice* lat, int R, int prec, int k_begin, int k_end, void* wa,
+                    void* wb, double a, double b, double* mu, int M, void* work, size_t work_bytes,
+                    void* stream);
 
 /*
  * Chebyshev time propagation that also keeps checkpoints for the adjoint

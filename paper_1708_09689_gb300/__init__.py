@@ -30,6 +30,7 @@ KERNEL_NONE, KERNEL_JACKSON, KERNEL_LORENTZ = 0, 1, 2  # damping kernels of kpm_
 V_ZERO, V_HOST, V_DEVICE, V_SEED, V_ON_THE_FLY, V_QDOT = 0, 1, 2, 3, 4, 5
 DOT_XX, DOT_XY, DOT_YY = 1, 2, 4
 OP_APPLY, OP_CHEB_STEP, OP_KPM, OP_SERIES, OP_ADJOINT, OP_KPM_BATCHED = 0, 1, 2, 3, 4, 5
+LATTICE_Z_HALO_LO, LATTICE_Z_HALO_HI = 1, 2  # z-slab lattices: halo plane below / above
 
 
 class PvscError(RuntimeError):
@@ -48,7 +49,7 @@ class LatticeDesc(ctypes.Structure):
         ("delta1", ctypes.c_double),
         ("delta2", ctypes.c_double),
         ("v_source", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
         ("V", ctypes.c_void_p),
         ("seed", ctypes.c_uint64),
         ("W", ctypes.c_double),
@@ -101,6 +102,7 @@ _SIGNATURES = {
     "pvsc_cheb_propagate_adjoint": (_i, [_vp, _i, _i, _vp, _d, _i, _i, _d, _d, _d, _vp, _vp, _vp, _sz, _vp]),
     "pvsc_propagate_adjoint_work_bytes": (_sz, [_vp, _i, _i, _d, _d]),
     "pvsc_debug_export_pattern": (_i, [_vp, _vp, _vp]),
+    "pvsc_kpm_sweeps": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _d, _d, _vp, _i, _vp, _sz, _vp]),
     "pvsc_kpm_moments_batched": (_i, [ctypes.POINTER(_vp), _i, _i, _i, ctypes.POINTER(_u64), _i,
                                       _dp, _dp, _vp, _vp, _sz, _vp]),
     "pvsc_batched_work_bytes": (_sz, [ctypes.POINTER(_vp), _i, _i, _i, _i]),
@@ -196,9 +198,10 @@ class Lattice:
 
     def __init__(self, model: int, dims, periodic, t: float = 1.0, m: float = 0.0, V=None,
                  disorder=None, on_the_fly: bool = False, delta1: float = 0.0, delta2: float = 0.0,
-                 k0: float = 0.0, qdots=None, stream=None):
+                 k0: float = 0.0, qdots=None, z_halo: int = 0, stream=None):
         d = LatticeDesc()
         d.model = model
+        d.flags = int(z_halo)  # LATTICE_Z_HALO_LO | LATTICE_Z_HALO_HI for a slab with halo planes
         dims = list(dims) + [1] * (3 - len(dims))
         per = list(periodic) + [0] * (3 - len(periodic))
         for i in range(3):
@@ -377,6 +380,17 @@ def kpm_moments(lat: Lattice, M: int, a: float, b: float, R: int = 1, prec: int 
         work = work_buffer(lat.work_bytes(OP_KPM, R, prec, M))
     _check(_lib.pvsc_kpm_moments(lat.handle, R, prec, _ptr(r0), int(seed), int(M), float(a),
                                  float(b), _ptr(mu), _ptr(work), work.numel(), _stream(stream)))
+    return mu
+
+
+def kpm_sweeps(lat: Lattice, k_begin: int, k_end: int, wa, wb, a, b, mu, work=None, stream=None):
+    """KPM sweeps k_begin .. k_end-1 on caller-held vectors (pvsc_kpm_sweeps): w_j in wa
+    for even j, in wb for odd j; moments into mu (float64 (R, M) on the device)."""
+    R, prec = block_R(wa), prec_of(wa)
+    if work is None:
+        work = work_buffer(lat.work_bytes(OP_CHEB_STEP, R, prec))
+    _check(_lib.pvsc_kpm_sweeps(lat.handle, R, prec, int(k_begin), int(k_end), _ptr(wa), _ptr(wb), float(a),
+                                float(b), _ptr(mu), int(mu.shape[-1]), _ptr(work), work.numel(), _stream(stream)))
     return mu
 
 

@@ -91,6 +91,7 @@ __global__ void gershgorin_kernel(Geometry g, double* out /* [gridDim][2] */) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.n_sites;
          s += (int64_t)gridDim.x * blockDim.x) {
       const int64_t x = s % Lx, y = (s / Lx) % Ly, z = s / (Lx * Ly);
+      if (z < (g.zhalo & 1) || z >= Lz - (g.zhalo >> 1)) continue;  // halo planes: rows of another domain
       const int64_t co[3] = {x, y, z};
       double radius = 0.0, self = 0.0;  // self: coefficient of -t Gamma^1 from length-1 periodic axes
       for (int d = 0; d < 3; ++d) {

@@ -293,6 +293,7 @@ static int batched_layout(const pvsc_lattice* const* lats, int n, int R, int pre
     const pvsc_lattice* lat = lats[i];
     if (!lat) return set_error(PVSC_ERR_ARG, "lattice %d is NULL", i);
     if (lat->g.model != PVSC_TI) return set_error(PVSC_ERR_UNSUPPORTED, "batched KPM takes TI lattices");
+    if (lat->g.zhalo) return set_error(PVSC_ERR_UNSUPPORTED, "batched KPM does not take halo lattices");
     BatchLat& L = out[i];
     L.g = lat->g;
     const int64_t plane = lat->g.L[0] * lat->g.L[1], Lz = lat->g.L[2];

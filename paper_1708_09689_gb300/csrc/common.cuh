@@ -57,6 +57,8 @@ struct Geometry {
   double d1, d2;        // TI on-site Delta_1 Gamma^5 + Delta_2 Gamma^15 (Eq. TB_H_topi)
   float d1f, d2f;       // the same rounded to fp32, for complex64 sweeps
   int has_delta;        // d1 != 0 or d2 != 0
+  int zhalo;            // TI: bit 0 a halo plane below, bit 1 above the updated planes
+                        // (read as z-neighbours, never updated)
   const QDots* qd;      // v_mode 3 (graphene): device copy owned by the lattice
 };
 

@@ -114,6 +114,11 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
     }
   LaunchShape sh = shape_for(lat, p.R, prec);
   if (sh.kernel == kKernelKpm2) sh = LaunchShape{};  // a KPM-only choice: single sweeps take the default
+  if (lat->g.zhalo) {  // a slab with halo planes: the z-march over its inner planes
+    const int zs = sh.zslab;
+    sh = LaunchShape{};
+    sh.zslab = zs;
+  }
   if (sh.kernel == kKernelTma) {
     p.tile_x = p.tile_y = 0;
     if (tma_sweep_possible(lat, p.R, prec) && !(feat & F_ADJ)) return launch_sweep_tma(lat, feat, p, sh, st);
@@ -178,8 +183,10 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
     p.zslab = (int)xs;
     units = nbx * ((Lx + xs - 1) / xs);
   } else if (lat->g.model == PVSC_TI || (wsm && !wsm_flat)) {
-    // z-marching columns: TI sites, or Weyl cells (two sites along x)
-    const int64_t plane = (wsm ? lat->g.L[0] / 2 : lat->g.L[0]) * lat->g.L[1], Lz = lat->g.L[2];
+    // z-marching columns: TI sites, or Weyl cells (two sites along x); a
+    // lattice with halo planes updates its inner planes only
+    const int64_t plane = (wsm ? lat->g.L[0] / 2 : lat->g.L[0]) * lat->g.L[1];
+    const int64_t Lz = lat->g.L[2] - (lat->g.zhalo & 1) - (lat->g.zhalo >> 1);
     const int64_t nbx = p.tile_x > 0 ? ((lat->g.L[0] + p.tile_x - 1) / p.tile_x) *
                                            ((lat->g.L[1] + p.tile_y - 1) / p.tile_y)
                                      : (plane * p.C + threads - 1) / threads;
@@ -382,7 +389,7 @@ extern "C" {
 // The two-step KPM sweep exists for complex64 TI lattices with R >= 2 and runs
 // when the tuning entry of (R, prec) selects it.
 static bool kpm2_possible(const pvsc_lattice* lat, int R, int prec) {
-  return lat->g.model == PVSC_TI && prec == PVSC_C64 && R >= 2;
+  return lat->g.model == PVSC_TI && prec == PVSC_C64 && R >= 2 && !lat->g.zhalo;
 }
 static bool kpm2_selected(const pvsc_lattice* lat, int R, int prec) {
   if (!kpm2_possible(lat, R, prec)) return false;
@@ -487,6 +494,7 @@ static int kpm_moments_fx(const pvsc_lattice* lat, int R, const void* r0, uint64
     return set_error(PVSC_ERR_UNSUPPORTED, "PVSC_Q64 moments are implemented for the TI lattice only");
   if (lat->g.has_delta)
     return set_error(PVSC_ERR_UNSUPPORTED, "PVSC_Q64 moments do not include the Delta terms");
+  if (lat->g.zhalo) return set_error(PVSC_ERR_UNSUPPORTED, "PVSC_Q64 moments do not take halo lattices");
   const FxLayout L = fx_layout(lat, R);
   if (int rc = check_work(work, work_bytes, L.total)) return rc;
   // The fixed-point range relies on ||T_k(H~)|| <= 1: (a, b) must hold the
@@ -664,6 +672,46 @@ int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, u
     return PVSC_OK;
   };
   return run_graph(lat, key, st, body);
+}
+
+int pvsc_kpm_sweeps(const pvsc_lattice* lat, int R, int prec, int k_begin, int k_end, void* wa, void* wb,
+                    double a, double b, double* mu, int M, void* work, size_t work_bytes, void* stream) {
+  if (int rc = check_common(lat, R, prec)) return rc;
+  if (int rc = check_scaling(a, b)) return rc;
+  if (int rc = check_ptr(wa, "wa")) return rc;
+  if (int rc = check_ptr(wb, "wb")) return rc;
+  if (wa == wb) return set_error(PVSC_ERR_ARG, "wa and wb must not overlap");
+  if (M < 1 || !mu) return set_error(PVSC_ERR_ARG, "need M >= 1 and mu");
+  const int nsweeps = (M + 1) / 2;
+  if (k_begin < 0 || k_end < k_begin || k_end > nsweeps)
+    return set_error(PVSC_ERR_ARG, "sweeps [%d, %d) outside [0, %d) for M = %d", k_begin, k_end, nsweeps, M);
+  if (int rc = check_work(work, work_bytes, dots_work_bytes(lat, R))) return rc;
+  if (k_end == k_begin) return PVSC_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PVSC_CUDA_TRY(cudaMemsetAsync(work, 0, kWorkHeader, st));
+  Sweep p;
+  sweep_init(p, lat, R, prec);
+  p.counter = reinterpret_cast<unsigned*>(work);
+  p.partials = reinterpret_cast<double*>(wptr(work, kWorkHeader));
+  p.mu = mu;
+  p.M = M;
+  p.dot_flags = 3;
+  for (int k = k_begin; k < k_end; ++k) {
+    void* wk = (k % 2 == 0) ? wa : wb;    // w_j lives in wa for even j, in wb for odd j
+    void* other = (k % 2 == 0) ? wb : wa;  // w_{k-1}, overwritten by w_{k+1}
+    for (int r = 0; r < R; ++r) {
+      p.coef[0][r] = (k == 0 ? 1.0 : 2.0) / a;
+      p.coef[1][r] = b;
+      p.coef[2][r] = k == 0 ? 0.0 : -1.0;
+    }
+    p.x = wk;
+    p.yin = k == 0 ? nullptr : other;
+    p.yout = other;
+    p.dot_mode = k == 0 ? 1 : 2;
+    p.kpm_k = k;
+    if (int rc = launch_sweep(lat, prec, F_DOTS, p, st)) return rc;
+  }
+  return PVSC_OK;
 }
 
 int pvsc_cheb_series(const pvsc_lattice* lat, int R, int prec, const void* x, void* y,

@@ -153,6 +153,13 @@ int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattic
     return set_error(PVSC_ERR_ARG, "W must be finite");
   const double cells = (double)desc->dims[0] * (double)desc->dims[1] * (double)desc->dims[2];
   if (cells * 4.0 * kMaxR > 4.0e18) return set_error(PVSC_ERR_ARG, "lattice too large");
+  if (desc->flags & ~PVSC_LATTICE_Z_HALO) return set_error(PVSC_ERR_ARG, "unknown lattice flags 0x%x", desc->flags);
+  const int nhalo = ((desc->flags & PVSC_LATTICE_Z_HALO_LO) ? 1 : 0) + ((desc->flags & PVSC_LATTICE_Z_HALO_HI) ? 1 : 0);
+  if (nhalo &&
+      (desc->model != PVSC_TI || desc->periodic[2] || desc->dims[2] < nhalo + 1 ||
+       !(desc->v_source == PVSC_V_ZERO || desc->v_source == PVSC_V_HOST || desc->v_source == PVSC_V_DEVICE)))
+    return set_error(PVSC_ERR_ARG, "halo planes need a TI lattice, an open z axis with at least one plane "
+                     "besides them and a given potential (zero, host or device: the slab's part of the global one)");
 
   pvsc_lattice* lat = new (std::nothrow) pvsc_lattice();
   if (!lat) return set_error(PVSC_ERR_OOM, "out of host memory");
@@ -171,6 +178,7 @@ int pvsc_lattice_create(const pvsc_lattice_desc* desc, void* stream, pvsc_lattic
   g.d1f = (float)g.d1;
   g.d2f = (float)g.d2;
   g.has_delta = (g.d1 != 0.0 || g.d2 != 0.0) ? 1 : 0;
+  g.zhalo = desc->flags & PVSC_LATTICE_Z_HALO;
   g.v_mode = 0;
   g.W = desc->W;
   g.vkey = hash_key(desc->seed, 0);

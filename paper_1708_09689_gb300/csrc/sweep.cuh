@@ -757,7 +757,10 @@ __global__ void __launch_bounds__(256, (VPT == 1 && sizeof(T) == 4) ? 2 : 1) ti_
   const int64_t ntx = TX > 0 ? (p.g.L[0] + TX - 1) / TX : 0;
   const int64_t nbx = TX > 0 ? ntx * ((p.g.L[1] + TY - 1) / TY) : (ncolthr + blockDim.x - 1) / blockDim.x;
   const int zs = p.zslab;
-  const int64_t nzs = (Lz + zs - 1) / zs;
+  // planes updated: all, or on a lattice with halo planes those between them
+  // (the halo planes are read as z-neighbours only)
+  const int64_t zlo = p.g.zhalo & 1, zn = Lz - (p.g.zhalo & 1) - (p.g.zhalo >> 1);
+  const int64_t nzs = (zn + zs - 1) / zs;
   const int64_t nunits = nbx * nzs;
   const int sl = threadIdx.x >> cshift;  // column of this thread within a tile
   for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
@@ -774,7 +777,7 @@ __global__ void __launch_bounds__(256, (VPT == 1 && sizeof(T) == 4) ? 2 : 1) ti_
       if (tid >= ncolthr) continue;
       col = tid >> cshift;
     }
-    const int64_t z0 = bz * zs, z1 = min(z0 + (int64_t)zs, Lz);
+    const int64_t z0 = zlo + bz * zs, z1 = min(z0 + (int64_t)zs, zlo + zn);
     ti_march<T, VPT, true, DEPTH, NBUF>(p.g, X, Yin, R, rc, col, z0, z1, ring,
                            [&](int64_t s) { return site_potential_t<T>(p.g, s); },
                            [&](T Vs, const Blk<T, VPT>& xm, const Blk<T, VPT>& xc,

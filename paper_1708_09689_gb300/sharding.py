@@ -9,9 +9,9 @@ final per-unit results (moments, timings) are gathered.  The split is
 deterministic in (rank, world size) so that every unit is computed exactly
 once and with the same seed it would get in a single-process run.
 
-A single lattice too large for one GPU would instead be cut into z-slabs with
-a one-plane halo exchange per sweep (the paper's domain decomposition,
-Sec. 3.4); that path is not built because every workload here fits one GB300.
+A single lattice too large for one GPU is instead cut into z-slabs with a
+one-plane halo exchange per sweep (the paper's domain decomposition, Sec. 3.4):
+see slab.py.
 """
 from __future__ import annotations
 
