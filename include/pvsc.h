@@ -525,12 +525,13 @@ typedef struct {
                   /* 5 z-marching over tiles of tile_x x tile_y columns per block */
                   /* (threads = tile_x tile_y R/vpt, a multiple of 32, at most 256), */
                   /* 6 marching along x over lines (y, z), zslab = x-segment length, */
-                  /* 7 (complex64, R = 4, 8 or 16, Lx a multiple of 4) TMA-staged */
+                  /* 7 (complex64, R = 4, 8, 16 or 32, Lx a multiple of 4) TMA-staged */
                   /* plane tiles: one block per SM copies each z-plane of a tile of */
-                  /* 16x16, 16x8 or 8x8 columns with its one-site halo strips into a */
+                  /* 16x16, 16x8, 8x8 or 4x4 columns with its one-site halo strips into a */
                   /* shared-memory ring (cp.async.bulk.tensor, mbarriers) for eight */
                   /* warps (threads 256, two (site, vector pair) items per thread) or */
-                  /* sixteen (threads 512, one item); tile_x x tile_y = the half tile */
+                  /* sixteen (threads 512, one item; not R = 32, whose 4x4 tile has */
+                  /* one item per thread); tile_x x tile_y = the half tile */
                   /* (16x8, 16x4, 8x4 for R = 4, 8, 16) selects rings one plane */
                   /* deeper on eight warps; zslab = z-chunk depth (0: chosen from */
                   /* the grid size); vpt is ignored */

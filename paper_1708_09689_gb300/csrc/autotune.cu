@@ -175,8 +175,10 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
     for (int zs : {0, 16, 32, 64})
       if (zs == 0 || zs < lat->g.L[2]) {
         cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, 0, 0, kKernelTma});
-        cands.push_back(pvsc_tuning{512, 0, zs, 0.f, 2, 0, 0, kKernelTma});
-        cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, deep_x, deep_y, kKernelTma});
+        if (R != 32) {  // R = 32 has one tile, one item per thread
+          cands.push_back(pvsc_tuning{512, 0, zs, 0.f, 2, 0, 0, kKernelTma});
+          cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, deep_x, deep_y, kKernelTma});
+        }
       }
   }
   if (lat->g.model == PVSC_TI)
