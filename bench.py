@@ -525,9 +525,9 @@ def run_workload(args, pv, dev, rank, world):
         torch.cuda.synchronize()
         t_dos = time.perf_counter() - t0
         deg, ns = 4000, 64
-        # default launch shape (z-march): the autotuner times dot-product sweeps, and its pick
-        # for this lattice (the sweep marching along x) ran the filter's series sweeps slower
-        # (72.1 s against 60.9 s)
+        # the filter runs series sweeps (accumulating + plain): tune the launch shape on those
+        if not args.no_autotune:
+            lat.autotune(ns, pv.C64, op=pv.OP_SERIES)
         clocks.start()
         t0 = time.perf_counter()
         theta, res, X, n_in, iters = pv.chebfd(lat, -lam, lam, a, b, n_search=ns, degree=deg, max_iter=30,

@@ -183,6 +183,8 @@ int pvsc_get_potential(const pvsc_lattice* lat, double* V_out_dev, void* stream)
  * per row, coinciding neighbours combined first.  Then a = (emax - emin +
  * eps)/2 and b = (emax + emin)/2, so that (H - b)/a has its spectrum inside
  * [-1, 1].  Any output pointer may be NULL.  Synchronous (host results).
+ * A non-finite potential anywhere (a NaN or an infinity, e.g. a poisoned input)
+ * is reported as PVSC_ERR_ARG instead of being dropped by the min / max.
  * `work` needs pvsc_work_bytes(lat, PVSC_OP_APPLY, 1, ...) bytes. */
 int pvsc_spectral_bounds(const pvsc_lattice* lat, double eps, double* emin, double* emax,
                          double* a, double* b, void* work, size_t work_bytes, void* stream);
@@ -525,12 +527,12 @@ typedef struct {
                   /* 5 z-marching over tiles of tile_x x tile_y columns per block */
                   /* (threads = tile_x tile_y R/vpt, a multiple of 32, at most 256), */
                   /* 6 marching along x over lines (y, z), zslab = x-segment length, */
-                  /* 7 (complex64, R = 4, 8, 16 or 32, Lx a multiple of 4) TMA-staged */
+                  /* 7 (complex64, R = 4 .. 64, Lx a multiple of 4) TMA-staged */
                   /* plane tiles: one block per SM copies each z-plane of a tile of */
-                  /* 16x16, 16x8, 8x8 or 4x4 columns with its one-site halo strips into a */
+                  /* 16x16, 16x8, 8x8, 4x4 or 4x2 columns with its one-site halo strips into a */
                   /* shared-memory ring (cp.async.bulk.tensor, mbarriers) for eight */
                   /* warps (threads 256, two (site, vector pair) items per thread) or */
-                  /* sixteen (threads 512, one item; not R = 32, whose 4x4 tile has */
+                  /* sixteen (threads 512, one item; not R = 32, 64, whose tiles have */
                   /* one item per thread); tile_x x tile_y = the half tile */
                   /* (16x8, 16x4, 8x4 for R = 4, 8, 16) selects rings one plane */
                   /* deeper on eight warps; zslab = z-chunk depth (0: chosen from */
@@ -544,6 +546,13 @@ int pvsc_device_error(int* flag, int clear);
 int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tuning);
 int pvsc_get_tuning(const pvsc_lattice* lat, int R, int prec, pvsc_tuning* tuning);
 int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* best, void* stream);
+/* pvsc_autotune timing the sweeps of one operation: PVSC_OP_KPM (what
+ * pvsc_autotune times: the recurrence sweep with its dot products),
+ * PVSC_OP_SERIES (the accumulating and the plain sweep of pvsc_cheb_series,
+ * pvsc_cheb_filter, pvsc_cheb_propagate and ChebFD's filter) or PVSC_OP_APPLY
+ * (the plain sweep).  The winner replaces the (R, prec) tuning entry; the
+ * on-disk cache keys on the operation too. */
+int pvsc_autotune_op(pvsc_lattice* lat, int R, int prec, int op, pvsc_tuning* best, void* stream);
 
 /* Neighbour table the stencil uses (debug/parity): for every site, 7 site
  * indices (TI: self, -x, +x, -y, +y, -z, +z) or, for graphene, per cell

@@ -112,6 +112,7 @@ _SIGNATURES = {
     "pvsc_set_tuning": (_i, [_vp, _i, _i, ctypes.POINTER(Tuning)]),
     "pvsc_get_tuning": (_i, [_vp, _i, _i, ctypes.POINTER(Tuning)]),
     "pvsc_autotune": (_i, [_vp, _i, _i, ctypes.POINTER(Tuning), _vp]),
+    "pvsc_autotune_op": (_i, [_vp, _i, _i, _i, ctypes.POINTER(Tuning), _vp]),
     "pvsc_debug_neighbours": (_i, [_vp, _vp, _vp]),
     "pvsc_last_error": (ctypes.c_char_p, []),
     "pvsc_version": (ctypes.c_char_p, []),
@@ -316,9 +317,11 @@ class Lattice:
         _check(_lib.pvsc_get_tuning(self._h, R, prec, ctypes.byref(t)))
         return t.as_dict()
 
-    def autotune(self, R: int, prec: int, stream=None) -> dict:
+    def autotune(self, R: int, prec: int, op: int = OP_KPM, stream=None) -> dict:
+        """Time the launch shapes with the sweeps of `op` (OP_KPM, OP_SERIES or
+        OP_APPLY) and keep the fastest for (R, prec)."""
         t = Tuning()
-        _check(_lib.pvsc_autotune(self._h, R, prec, ctypes.byref(t), _stream(stream)))
+        _check(_lib.pvsc_autotune_op(self._h, R, prec, int(op), ctypes.byref(t), _stream(stream)))
         return t.as_dict()
 
 

@@ -4,8 +4,10 @@
 // condition, Sec. 3.1); here the launch shape of the z-marching sweep is
 // chosen by measurement instead: threads per block, resident blocks per SM
 // and z-slab depth are swept with CUDA events on the caller's stream, timing
-// the KPM-type sweep (recurrence update + fp64 dot products) that dominates
-// every recurrence, and the fastest shape is stored in the lattice handle.
+// the sweeps of the operation that will run (KPM: recurrence update + fp64 dot
+// products; series: the accumulating sweep and the plain one it alternates
+// with; apply: the plain sweep), and the fastest shape is stored in the
+// lattice handle.
 // With PVSC_TUNE_CACHE=<file> results are kept on disk, keyed by model,
 // dimensions, boundary conditions, R, precision and device name.
 #include <cstdio>
@@ -19,16 +21,16 @@
 
 namespace pvsc {
 
-static std::string cache_key(const pvsc_lattice* lat, int R, int prec) {
+static std::string cache_key(const pvsc_lattice* lat, int R, int prec, int op) {
   cudaDeviceProp prop;
   std::string dev = "gpu";
   if (cudaGetDeviceProperties(&prop, lat->device) == cudaSuccess) dev = prop.name;
   for (auto& c : dev)
     if (c == ' ') c = '_';
   char buf[512];
-  snprintf(buf, sizeof(buf), "%d %lld %lld %lld %d%d%d %d %d %s", lat->g.model, (long long)lat->g.L[0],
+  snprintf(buf, sizeof(buf), "%d %lld %lld %lld %d%d%d %d %d %s%s", lat->g.model, (long long)lat->g.L[0],
            (long long)lat->g.L[1], (long long)lat->g.L[2], lat->g.per[0], lat->g.per[1], lat->g.per[2], R,
-           prec, dev.c_str());
+           prec, dev.c_str(), op == PVSC_OP_KPM ? "" : (op == PVSC_OP_SERIES ? " series" : " apply"));
   return buf;
 }
 
@@ -69,11 +71,13 @@ static void cache_store(const std::string& key, const pvsc_tuning& t) {
 
 using namespace pvsc;
 
-extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* best, void* stream) {
+extern "C" int pvsc_autotune_op(pvsc_lattice* lat, int R, int prec, int op, pvsc_tuning* best, void* stream) {
   if (int rc = check_lattice(lat)) return rc;
   if (!valid_R(R)) return set_error(PVSC_ERR_ARG, "R = %d: must be 1, 2, 4, 8, 16, 32 or 64", R);
   if (prec != PVSC_C128 && prec != PVSC_C64) return set_error(PVSC_ERR_ARG, "unknown precision %d", prec);
-  const std::string key = cache_key(lat, R, prec);
+  if (op != PVSC_OP_KPM && op != PVSC_OP_SERIES && op != PVSC_OP_APPLY)
+    return set_error(PVSC_ERR_ARG, "autotune op must be PVSC_OP_KPM, PVSC_OP_SERIES or PVSC_OP_APPLY");
+  const std::string key = cache_key(lat, R, prec, op);
   pvsc_tuning cached;
   if (cache_lookup(key, &cached)) {
     lat->tuning[{R, prec}] = cached;
@@ -83,7 +87,7 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t vb = vec_bytes(lat, R, prec), wb = dots_work_bytes(lat, R);
-  void *x = nullptr, *y = nullptr, *work = nullptr;
+  void *x = nullptr, *y = nullptr, *work = nullptr, *acc = nullptr;
   double* dots = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = PVSC_OK;
@@ -94,14 +98,18 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
     cudaFree(y);
     cudaFree(work);
     cudaFree(dots);
+    cudaFree(acc);
   };
+  const size_t ab = op == PVSC_OP_SERIES ? vec_bytes(lat, R, PVSC_C128) : 16;
   if (cudaMalloc(&x, vb) != cudaSuccess || cudaMalloc(&y, vb) != cudaSuccess ||
-      cudaMalloc(&work, wb) != cudaSuccess || cudaMalloc(&dots, sizeof(double) * 4 * R) != cudaSuccess) {
+      cudaMalloc(&work, wb) != cudaSuccess || cudaMalloc(&dots, sizeof(double) * 4 * R) != cudaSuccess ||
+      cudaMalloc(&acc, ab) != cudaSuccess) {
     cleanup();
     return set_error(PVSC_ERR_OOM, "autotune could not allocate its sweep vectors");
   }
   cudaMemsetAsync(x, 0, vb, st);
   cudaMemsetAsync(y, 0, vb, st);
+  cudaMemsetAsync(acc, 0, ab, st);
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   std::vector<int> vpt_c = {1};
@@ -116,7 +124,9 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
   const bool had = saved != lat->tuning.end();
   const pvsc_tuning old = had ? saved->second : pvsc_tuning{};
   pvsc_tuning win{256, 0, 0, 1e30f, 0, 0, 0, 0};
-  // time one candidate shape: one warm sweep, then the mean of three
+  // time one candidate shape: one warm sweep, then the mean of three, with the
+  // sweep features of the operation: KPM (recurrence + dots), series (the
+  // accumulating sweep and the plain one it alternates with), apply (plain)
   auto time_one = [&](const pvsc_tuning& cand, float* ms) -> int {
     lat->tuning[{R, prec}] = cand;
     Sweep p;
@@ -124,21 +134,32 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
     for (int r = 0; r < R; ++r) {
       p.coef[0][r] = 0.2;
       p.coef[1][r] = 0.0;
-      p.coef[2][r] = -1.0;
+      p.coef[2][r] = op == PVSC_OP_APPLY ? 0.0 : -1.0;
     }
     p.x = x;
-    p.yin = y;
+    p.yin = op == PVSC_OP_APPLY ? nullptr : y;
     p.yout = y;
     p.dot_flags = 3;
     p.dot_mode = 0;
     p.dots = dots;
     p.counter = static_cast<unsigned*>(work);
     p.partials = reinterpret_cast<double*>(static_cast<char*>(work) + kWorkHeader);
+    p.acc = static_cast<double2*>(acc);
+    p.acc_out = static_cast<double2*>(acc);
+    p.acc_mode = ACC_ADD | ACC_X;
+    p.cx_re = 0.3;
+    p.cy_im = -0.2;
     PVSC_CUDA_TRY(cudaMemsetAsync(work, 0, kWorkHeader, st));
-    if (int r = launch_sweep(lat, prec, F_DOTS, p, st)) return r;
+    auto one = [&]() -> int {
+      if (op == PVSC_OP_KPM) return launch_sweep(lat, prec, F_DOTS, p, st);
+      if (op == PVSC_OP_APPLY) return launch_sweep(lat, prec, 0, p, st);
+      if (int r = launch_sweep(lat, prec, F_ACC, p, st)) return r;
+      return launch_sweep(lat, prec, 0, p, st);
+    };
+    if (int r = one()) return r;
     PVSC_CUDA_TRY(cudaEventRecord(e0, st));
     for (int rep = 0; rep < 3; ++rep)
-      if (int r = launch_sweep(lat, prec, F_DOTS, p, st)) return r;
+      if (int r = one()) return r;
     PVSC_CUDA_TRY(cudaEventRecord(e1, st));
     PVSC_CUDA_TRY(cudaEventSynchronize(e1));
     PVSC_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
@@ -175,7 +196,7 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
     for (int zs : {0, 16, 32, 64})
       if (zs == 0 || zs < lat->g.L[2]) {
         cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, 0, 0, kKernelTma});
-        if (R != 32) {  // R = 32 has one tile, one item per thread
+        if (R < 32) {  // R = 32, 64 have one tile, one item per thread
           cands.push_back(pvsc_tuning{512, 0, zs, 0.f, 2, 0, 0, kKernelTma});
           cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, deep_x, deep_y, kKernelTma});
         }
@@ -207,4 +228,8 @@ extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* be
   cache_store(key, win);
   if (best) *best = win;
   return PVSC_OK;
+}
+
+extern "C" int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* best, void* stream) {
+  return pvsc_autotune_op(lat, R, prec, PVSC_OP_KPM, best, stream);
 }

@@ -85,6 +85,7 @@ __global__ void get_potential_kernel(Geometry g, double* out) {
 // Per-row Gershgorin interval, reduced to one (min, max) per block.
 __global__ void gershgorin_kernel(Geometry g, double* out /* [gridDim][2] */) {
   double lo = 1e300, hi = -1e300;
+  bool bad = false;  // a non-finite potential (fmin / fmax would drop it silently)
   const double at = fabs(g.t);
   if (g.model == 1) {
     const int64_t Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
@@ -108,6 +109,7 @@ __global__ void gershgorin_kernel(Geometry g, double* out /* [gridDim][2] */) {
         }
       }
       const double V = site_potential_any(g, s);
+      bad |= !isfinite(V);
       radius += sqrt(g.d1 * g.d1 + g.d2 * g.d2);  // one Delta entry per row, |D1 +- i D2|
       for (int sign = -1; sign <= 1; sign += 2) {  // Gamma^1 = +1 / -1 rows
         const double c = V + sign * (g.m - self * g.t);
@@ -148,6 +150,7 @@ __global__ void gershgorin_kernel(Geometry g, double* out /* [gridDim][2] */) {
         }
       }
       const double V = site_potential_any(g, s);
+      bad |= !isfinite(V);
       const double r = fmax(ra, rb) + fabs(sx);
       lo = fmin(lo, V - r);
       hi = fmax(hi, V + r);
@@ -169,6 +172,7 @@ __global__ void gershgorin_kernel(Geometry g, double* out /* [gridDim][2] */) {
       if (nu == 2) nb = 2 + (hxm ? 1 : 0);
       if (nu == 3) nb = 1 + (hx ? 1 : 0) + (hyp ? 1 : 0);
       const double V = site_potential_any(g, s);
+      bad |= !isfinite(V);
       lo = fmin(lo, V - nb * at);
       hi = fmax(hi, V + nb * at);
     }
@@ -176,7 +180,7 @@ __global__ void gershgorin_kernel(Geometry g, double* out /* [gridDim][2] */) {
   __shared__ double slo[256], shi[256];
   slo[threadIdx.x] = lo;
   shi[threadIdx.x] = hi;
-  __syncthreads();
+  bad = __syncthreads_or(bad) != 0;
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
       slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + w]);
@@ -184,9 +188,9 @@ __global__ void gershgorin_kernel(Geometry g, double* out /* [gridDim][2] */) {
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    out[2 * blockIdx.x] = slo[0];
-    out[2 * blockIdx.x + 1] = shi[0];
+  if (threadIdx.x == 0) {  // a block that met a non-finite potential reports NaN
+    out[2 * blockIdx.x] = bad ? __longlong_as_double(0x7ff8000000000000ll) : slo[0];
+    out[2 * blockIdx.x + 1] = bad ? __longlong_as_double(0x7ff8000000000000ll) : shi[0];
   }
 }
 

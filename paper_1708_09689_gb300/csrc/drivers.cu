@@ -511,7 +511,9 @@ static int kpm_moments_fx(const pvsc_lattice* lat, int R, const void* r0, uint64
       PVSC_CUDA_TRY(cudaMemcpyAsync(h.data(), gw, sizeof(double) * 2 * grid, cudaMemcpyDeviceToHost, st));
       PVSC_CUDA_TRY(cudaStreamSynchronize(st));
       double lo = h[0], hi = h[1];
-      for (int i = 1; i < grid; ++i) {
+      for (int i = 0; i < grid; ++i) {
+        if (std::isnan(h[2 * i]) || std::isnan(h[2 * i + 1]))
+          return set_error(PVSC_ERR_ARG, "the potential holds a non-finite value (PVSC_Q64 needs a bounded spectrum)");
         lo = std::fmin(lo, h[2 * i]);
         hi = std::fmax(hi, h[2 * i + 1]);
       }
@@ -998,8 +1000,8 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
   if (tuning->kernel < 0 || tuning->kernel > 7) return set_error(PVSC_ERR_ARG, "kernel must be 0 .. 7");
   if (tuning->kernel == kKernelTma) {
     if (!tma_sweep_possible(lat, R, prec))
-      return set_error(PVSC_ERR_ARG, "kernel 7 (TMA-staged tiles) needs a TI lattice, complex64, R = 4, 8, "
-                       "16 or 32 and Lx a multiple of 4");
+      return set_error(PVSC_ERR_ARG, "kernel 7 (TMA-staged tiles) needs a TI lattice, complex64, R >= 4 "
+                       "and Lx a multiple of 4");
     if (!tma_tile_valid(R, tuning->tile_x, tuning->tile_y))
       return set_error(PVSC_ERR_ARG, "kernel 7 takes no tile other than the two of R = %d (%dx%d given)", R,
                        tuning->tile_x, tuning->tile_y);

@@ -292,7 +292,9 @@ int pvsc_spectral_bounds(const pvsc_lattice* lat, double eps, double* emin, doub
   PVSC_CUDA_TRY(cudaMemcpyAsync(h.data(), work, sizeof(double) * 2 * grid, cudaMemcpyDeviceToHost, st));
   PVSC_CUDA_TRY(cudaStreamSynchronize(st));
   double lo = h[0], hi = h[1];
-  for (int i = 1; i < grid; ++i) {
+  for (int i = 0; i < grid; ++i) {
+    if (std::isnan(h[2 * i]) || std::isnan(h[2 * i + 1]))
+      return set_error(PVSC_ERR_ARG, "the potential holds a non-finite value (spectral bounds undefined)");
     lo = std::fmin(lo, h[2 * i]);
     hi = std::fmax(hi, h[2 * i + 1]);
   }

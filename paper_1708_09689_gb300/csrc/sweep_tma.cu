@@ -1,5 +1,5 @@
 // TI sweep with tensor-memory-accelerator (TMA) staging of z-plane tiles
-// (tuning kernel 7), complex64 storage, R = 4, 8, 16 or 32.
+// (tuning kernel 7), complex64 storage, R = 4 .. 64.
 //
 // The stencil of Eq. TB_H_topi reads every x element of a plane seven times
 // (the site itself and its six neighbours).  Here a block owns a tile of
@@ -64,6 +64,9 @@ template <> struct TmaTile<16, false> { static constexpr int TX = 8, TY = 8, NXS
 // R = 32: 1 KB sites, 4 x 4 tiles of 256 items (the "deep" variant one slot deeper)
 template <> struct TmaTile<32, false> { static constexpr int TX = 4, TY = 4, NXS = 3, NYS = 2; };
 template <> struct TmaTile<32, true> { static constexpr int TX = 4, TY = 4, NXS = 4, NYS = 3; };
+// R = 64: 2 KB sites, 4 x 2 tiles of 256 items, one warp per site
+template <> struct TmaTile<64, false> { static constexpr int TX = 4, TY = 2, NXS = 3, NYS = 2; };
+template <> struct TmaTile<64, true> { static constexpr int TX = 4, TY = 2, NXS = 3, NYS = 2; };
 
 constexpr int round_up_1k(int b) { return (b + 1023) & ~1023; }
 
@@ -182,9 +185,9 @@ __device__ __forceinline__ int tma_site_perm(int q) {
 // Swizzled offset of the 16-byte chunk of vectors (2c, 2c+1), orbital 0, of the
 // site at byte offset O (a multiple of 32 R) in a tile buffer: the logical
 // offset L = O + 16 c with its chunk bits XORed with its row bits.  Orbital o
-// then sits at (B ^ (K_o << 4)) + (K2_o << 7) with the compile-time K of
-// tma_lds_blk (the row offset of orbital o never carries into the row bits of
-// L for R = 4 .. 32).
+// then sits at (B ^ (K_o << 4)) + (its row offset) with the compile-time K of
+// tma_lds_blk (the row offset of orbital o modulo 8 never carries into the row
+// bits of L for R = 4 .. 64).
 template <int R>
 __device__ __forceinline__ uint32_t tma_swz(uint32_t O, int c) {
   const uint32_t L = O + 16u * (uint32_t)c;
@@ -201,7 +204,7 @@ __device__ __forceinline__ void tma_lds_blk(const unsigned char* buf, uint32_t B
   for (int o = 0; o < 4; ++o) {
     const int ao = o * 8 * R;                      // byte offset of orbital o in the site
     const int K1 = (ao >> 4) & 7, K2 = (ao >> 7) & 7;
-    const float4 v = *reinterpret_cast<const float4*>(buf + ((B ^ (uint32_t)((K1 ^ K2) << 4)) + (uint32_t)(K2 << 7)));
+    const float4 v = *reinterpret_cast<const float4*>(buf + ((B ^ (uint32_t)((K1 ^ K2) << 4)) + (uint32_t)(ao & ~127)));
     b.v[o][0] = {v.x, v.y};
     b.v[o][1] = {v.z, v.w};
   }
@@ -586,11 +589,15 @@ static int64_t tma_tiles(const Geometry& g) {  // the smaller (deep-ring) tiles:
 // 16-bit fields, at most kTmaMaxUnits of them (one z-chunk per column at least).
 bool tma_sweep_possible(const pvsc_lattice* lat, int R, int prec) {
   const Geometry& g = lat->g;
-  if (!(g.model == PVSC_TI && prec == PVSC_C64 && (R == 4 || R == 8 || R == 16 || R == 32) && g.L[0] % 4 == 0 &&
+  if (!(g.model == PVSC_TI && prec == PVSC_C64 && (R == 4 || R == 8 || R == 16 || R == 32 || R == 64) &&
+        g.L[0] % 4 == 0 &&
         g.L[0] < 65536 && g.L[1] < 65536 && g.L[2] < 65536))
     return false;
-  const int64_t ntiles =
-      R == 4 ? tma_tiles<4>(g) : (R == 8 ? tma_tiles<8>(g) : (R == 16 ? tma_tiles<16>(g) : tma_tiles<32>(g)));
+  const int64_t ntiles = R == 4    ? tma_tiles<4>(g)
+                         : R == 8  ? tma_tiles<8>(g)
+                         : R == 16 ? tma_tiles<16>(g)
+                         : R == 32 ? tma_tiles<32>(g)
+                                   : tma_tiles<64>(g);
   return ntiles <= (int64_t)kTmaMaxUnits * lat->sm_count;
 }
 
@@ -635,8 +642,10 @@ static void tma_tiles_of(int R, int* tx_large, int* ty_large, int* tx_deep, int*
             *tx_deep = TmaLayout<8, true, 8>::TX; *ty_deep = TmaLayout<8, true, 8>::TY; break;
     case 16: *tx_large = TmaLayout<16, false, 8>::TX; *ty_large = TmaLayout<16, false, 8>::TY;
              *tx_deep = TmaLayout<16, true, 8>::TX; *ty_deep = TmaLayout<16, true, 8>::TY; break;
-    default: *tx_large = TmaLayout<32, false, 8>::TX; *ty_large = TmaLayout<32, false, 8>::TY;
-             *tx_deep = -1; *ty_deep = -1; break;  // one tile; the deeper rings by tile_y = -1 are not offered
+    case 32: *tx_large = TmaLayout<32, false, 8>::TX; *ty_large = TmaLayout<32, false, 8>::TY;
+             *tx_deep = -1; *ty_deep = -1; break;  // one tile, no deeper-ring variant
+    default: *tx_large = TmaLayout<64, false, 8>::TX; *ty_large = TmaLayout<64, false, 8>::TY;
+             *tx_deep = -1; *ty_deep = -1; break;
   }
 }
 
@@ -655,16 +664,18 @@ bool tma_tile_valid(int R, int tile_x, int tile_y) {
 
 int launch_sweep_tma(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
   if (!tma_sweep_possible(lat, p.R, PVSC_C64))
-    return set_error(PVSC_ERR_UNSUPPORTED, "the TMA-staged sweep needs a complex64 TI lattice, R = 4, 8, "
-                     "16 or 32 and Lx a multiple of 4");
+    return set_error(PVSC_ERR_UNSUPPORTED, "the TMA-staged sweep needs a complex64 TI lattice, R >= 4 "
+                     "and Lx a multiple of 4");
   // tile_y selects the tile (and ring depth) of this R: the larger tile with
   // two planes in flight, or half of it with three (0: the default)
   // and threads = 512 the large tile with one item per thread (16 warps)
   const bool deep = tma_tile_deep(p.R, sh.tile_y);
-  const bool wide = !deep && sh.threads == 512 && p.R != 32;  // R = 32: 256 items, one per thread
+  const bool wide = !deep && sh.threads == 512 && p.R < 32;  // R = 32, 64: 256 items, one per thread
   switch (p.R) {
     case 32:
       return launch_tma_r<32, false, 8>(lat, feat, p, sh, st);
+    case 64:
+      return launch_tma_r<64, false, 8>(lat, feat, p, sh, st);
     case 4:
       return deep ? launch_tma_r<4, true, 8>(lat, feat, p, sh, st)
                   : (wide ? launch_tma_r<4, false, 16>(lat, feat, p, sh, st)

@@ -97,3 +97,25 @@ def test_density_and_bloch_argument_errors():
         pv.bloch_vectors(lat, [(0, 0, 0)] * 3)  # nk must be a power of two up to 16
     with pytest.raises(pv.PvscError):
         pv.bloch_vectors(pv.Lattice.graphene((4, 3), (1, 1)), [(0, 0, 0)])
+
+
+def test_disorder_fills_the_bulk_gap_of_the_ti_dos():
+    # the trend of the paper's disordered-TI DOS (Sec. 4.2): the clean m = 2
+    # bulk has a gap |E| < 1; box disorder of growing width W puts states into
+    # it.  Stochastic-trace KPM DOS of a periodic 14^3 lattice (no surfaces),
+    # the same scaling for every W; the weight inside |E| < 0.5 grows with W
+    # and is negligible without disorder
+    dims, per = (14, 14, 14), (1, 1, 1)
+    Ws = [0.0, 2.0, 4.0, 6.0]
+    lats = [pv.Lattice.ti(dims, per, disorder=(Wd, 21)) if Wd else pv.Lattice.ti(dims, per) for Wd in Ws]
+    _, _, a, b = lats[-1].spectral_bounds()   # the widest spectrum holds all of them
+    M, R = 512, 16
+    E = np.linspace(-0.5, 0.5, 201)
+    inside = []
+    for lat in lats:
+        mu = pv.kpm_moments(lat, M, a, b, R=R, prec=pv.C64, seed=7)
+        rho = pv.dos(lat, mu, E, a, b).cpu().numpy()
+        inside.append(float(np.sum(rho) * (E[1] - E[0])) / lat.D)
+    assert inside[0] < 2e-3                       # the clean gap (KPM broadening leaks a little)
+    assert all(x < y for x, y in zip(inside, inside[1:])), inside
+    assert inside[-1] > 10 * max(inside[0], 1e-4)

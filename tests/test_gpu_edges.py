@@ -89,3 +89,34 @@ def test_propagation_with_the_shortest_series(dt, K_expected):
         psi = torch.from_numpy(x).cuda()
         pv.cheb_propagate(lat, psi, dt, 3, a, b, prec=prec)
         assert np.linalg.norm(psi.cpu().numpy() - ref) / np.linalg.norm(ref) < tol
+
+
+def test_poisoned_potential_is_detected_on_the_host_without_a_device_fault():
+    # failure detection without a GPU fault: a NaN planted in the potential (on
+    # the host side of the input) is reported by the spectral bounds as an
+    # error, propagates into mu_1 and every later moment while mu_0 = <r|r> stays
+    # finite, and into the norm of a propagated state; the context stays usable
+    dims, per = (6, 5, 4), (1, 1, 0)
+    n = int(np.prod(dims))
+    V = W.disorder_potential(n, 1.0, 3)
+    lat = pv.Lattice.ti(dims, per, V=V)
+    _, _, a, b = lat.spectral_bounds()
+    bad = V.copy()
+    bad[17] = np.nan
+    lat.set_potential(torch.from_numpy(bad).cuda())
+    with pytest.raises(pv.PvscError) as e:
+        lat.spectral_bounds()
+    assert e.value.code == pv.PVSC_ERR_ARG and "non-finite" in str(e.value)
+    for prec in (pv.C128, pv.C64):
+        mu = pv.kpm_moments(lat, 16, a, b, R=2, prec=prec, seed=4).cpu().numpy()
+        assert np.all(np.isfinite(mu[:, 0])) and np.all(np.isnan(mu[:, 1:]))
+    psi = torch.from_numpy(W.gaussian_block(4 * n, 1, 2)[:, 0]).cuda()
+    pv.cheb_propagate(lat, psi, 0.5, 2, a, b)
+    assert not torch.isfinite(torch.linalg.vector_norm(psi)).item()
+    # a clean potential restores everything, with no device error pending
+    lat.set_potential(torch.from_numpy(V).cuda())
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
+    mu = pv.kpm_moments(lat, 16, a, b, R=2, prec=pv.C128, seed=4).cpu().numpy()
+    ref = O.kpm_moments(H, W.random_phase_block(4 * n, 2, 4), 16, a, b).real
+    assert np.max(np.abs(mu - ref)) < 1e-12
+    assert pv.device_error() == 0

@@ -119,3 +119,24 @@ def test_march_along_x_series_propagation_and_step(prec, tol):
                            [0.3] * R, [0.1] * R, [-1.0] * R)
     got = yt.cpu().numpy().astype(np.complex128)
     assert np.linalg.norm(got - yr) / np.linalg.norm(yr) < (1e-12 if prec == pv.C128 else 2e-6)
+
+
+@pytest.mark.parametrize("op", [pv.OP_SERIES, pv.OP_APPLY, pv.OP_KPM])
+def test_autotune_per_operation_keeps_results(op):
+    # the launch shape tuned on an operation's own sweeps changes no result:
+    # the filter series and the moments against the oracle
+    dims, per, R = (32, 16, 6), (1, 1, 0), 8
+    n = int(np.prod(dims))
+    lat = pv.Lattice.ti(dims, per, disorder=(1.0, 4))
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, W.disorder_potential(n, 1.0, 4))
+    t = lat.autotune(R, pv.C64, op=op)
+    assert t["time_ms"] > 0
+    _, _, a, b = lat.spectral_bounds()
+    x = W.gaussian_block(H.shape[0], R, 5)
+    g = [1.0, 0.5, -0.25, 0.125, 0.3]
+    y = pv.cheb_filter(lat, torch.from_numpy(x).cuda(), g, a, b, prec=pv.C64).cpu().numpy()
+    ref = O.cheb_series(H, x, np.array(g, dtype=np.complex128), a, b)
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-5
+    mu = pv.kpm_moments(lat, 24, a, b, R=R, prec=pv.C64, seed=3).cpu().numpy()
+    refm = O.kpm_moments(H, W.random_phase_block(4 * n, R, 3), 24, a, b).real
+    assert np.max(np.abs(mu - refm)) < 1e-4
