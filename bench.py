@@ -349,6 +349,17 @@ def _hbm_roof(bytes_per_lup, lups, ms, kernel):
             "bytes_per_lup": bytes_per_lup, "peak_kind": f"{kind} hbm_gbs"}
 
 
+TI_KERNEL_NAMES = {0: "ti_sweep (z-march)", 1: "ti_sweep_flat", 2: "ti_sweep (cp.async ring)",
+                   3: "ti_sweep (deep cp.async ring)", 4: "ti_kpm2_sweep", 5: "ti_sweep (column tiles)",
+                   6: "ti_sweep_xmarch", 7: "ti_sweep_tma (TMA-staged plane tiles)"}
+
+
+def ti_kernel_name(tuning: dict, what: str) -> str:
+    """The TI sweep a tuning entry selects, for the roofline record."""
+    k = int(tuning.get("kernel", 0)) if tuning else 0
+    return f"{TI_KERNEL_NAMES.get(k, 'ti_sweep')} {what}"
+
+
 def series_bytes_per_site(K: int, vb: float = 4.0) -> float:
     """Algorithmic HBM bytes per graphene site of one complex64 propagation time
     step with K series terms (R = 1, fp32 copy of V: vb = 4 bytes per sweep, 0 when
@@ -505,10 +516,12 @@ def run_workload(args, pv, dev, rank, world):
                      "config": {"workload": "A(k,E) of a clean TI, 512x64x8 sites periodic, m=2, t=1: "
                                             "64 k-points along k_x, 4 Bloch states each, 1024 moments, "
                                             "Jackson kernel, 1024 energies",
-                                "kpm_calls_per_step": len(calls), "R_per_call": R},
+                                "kpm_calls_per_step": len(calls), "R_per_call": R,
+                                "launch": lat.get_tuning(R, pv.C64)},
                      "density_ms_64k": round(t_d, 4),
                      "peak_at_k0": peak(32, 0.5, 1.5), "closed_form_k0": 1.0,
-                     "roofline": _hbm_roof(96.0, lups, ms, "ti_sweep<float,2,F_DOTS> (R = 64, V = 0)"),
+                     "roofline": _hbm_roof(96.0, lups, ms, ti_kernel_name(lat.get_tuning(R, pv.C64),
+                                                                         "KPM sweeps (R = 64, V = 0)")),
                      "clocks": clk, "gpu_launches": args.steps * len(calls) * ((M + 1) // 2 + 1 + nk_call)})
     elif args.workload == "chebfd":
         # interior eigenpairs of a disordered TI slab, the filter-diagonalization test case of
@@ -543,13 +556,14 @@ def run_workload(args, pv, dev, rank, world):
                                             "in [-lambda, lambda] holding ~40 states (lambda from the KPM DOS), "
                                             "64 search vectors, degree 4000, tol 1e-6",
                                 "lambda": lam, "dos_seconds": round(t_dos, 3),
-                                "launch": "default (z-marching sweep)"},
+                                "launch": lat.get_tuning(ns, pv.C64)},
                      "iterations": iters, "eigenpairs_found": int(n_in),
                      "max_residual": float(res[inside].max()) if n_in else None,
                      "kramers_pairs": bool(n_in % 2 == 0),
                      "roofline": _hbm_roof(96.0 + 8.0 / ns + 64.0, lups, 1000 * secs,
-                                           "ti_sweep<float,2,*> series sweeps (R = 64; accumulator on "
-                                           "every other sweep), solver average"),
+                                           ti_kernel_name(lat.get_tuning(ns, pv.C64),
+                                                          "series sweeps (R = 64; accumulator on every "
+                                                          "other sweep), solver average")),
                      "clocks": clk, "gpu_launches": None})
     elif args.workload == "wsm_kpm":
         # KPM DOS of the Weyl semimetal on the dispersion figure's 256 x 32 x 32 cuboid (periodic
