@@ -48,7 +48,7 @@ TRAFFIC = {("ti_slab", 8, "ti_sweep"): {"bytes_per_launch": 3.220e9, "source_sha
            ("ti_slab", 8, "ti_sweep_xmarch"): {"bytes_per_launch": 3.222e9, "source_sha256_16": "df26e831c975b98f"},
            ("ti_slab", 8, "ti_sweep_tma"): {"bytes_per_launch": 3.253e9, "source_sha256_16": "c7fe6d983aefe6ff"}}
 KERNEL_SOURCES = ("paper_1708_09689_gb300/csrc/sweep.cuh", "paper_1708_09689_gb300/csrc/common.cuh",
-                  "paper_1708_09689_gb300/csrc/sweep_tma.cu")
+                  "paper_1708_09689_gb300/csrc/sweep_tma.cuh")
 
 
 def kernel_source_hash() -> str:

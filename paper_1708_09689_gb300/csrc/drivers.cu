@@ -1000,7 +1000,7 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
   if (tuning->kernel < 0 || tuning->kernel > 7) return set_error(PVSC_ERR_ARG, "kernel must be 0 .. 7");
   if (tuning->kernel == kKernelTma) {
     if (!tma_sweep_possible(lat, R, prec))
-      return set_error(PVSC_ERR_ARG, "kernel 7 (TMA-staged tiles) needs a TI lattice, complex64, R >= 4 "
+      return set_error(PVSC_ERR_ARG, "kernel 7 (TMA-staged tiles) needs a TI or Weyl lattice, complex64, R >= 4 "
                        "and Lx a multiple of 4");
     if (!tma_tile_valid(R, tuning->tile_x, tuning->tile_y))
       return set_error(PVSC_ERR_ARG, "kernel 7 takes no tile other than the two of R = %d (%dx%d given)", R,

@@ -1,0 +1,644 @@
+// TI sweep with tensor-memory-accelerator (TMA) staging of z-plane tiles
+// (tuning kernel 7), complex64 storage, R = 4 .. 64.
+//
+// The stencil of Eq. TB_H_topi reads every x element of a plane seven times
+// (the site itself and its six neighbours).  Here a block owns a tile of
+// TX x TY columns and marches it along z.  Per plane, cp.async.bulk.tensor
+// copies bring the tile of x with its four one-site halo strips (x-/x+
+// columns, y-/y+ rows; no corners, the stencil has none) and, per updated
+// plane, the tile of y_in and of the fp32 potential into shared memory: a ring
+// of x planes and a ring of y_in planes, deep enough to keep three planes of
+// copies (about 130 KB per SM) in flight.  Eight warps take all six neighbours
+// and y_in from shared memory and keep only x(z-1) of their sites in
+// registers, so no register waits on HBM.  Each slot has a full mbarrier
+// (copy bytes) and a release count: the warp that releases a slot last issues
+// the copy that refills it, so no thread ever blocks waiting for a free slot.
+// Halo strips are taken with the wrapped coordinate on a periodic axis and read
+// zeros past an open edge (the copy's out-of-range fill), so one code path
+// serves every boundary mix and partial tiles.
+//
+// Shared-memory layout: the x and y_in tiles use the 128-byte swizzle (the
+// 16-byte chunk index of every 128-byte row XORed with the row index modulo
+// 8).  A thread owns two vectors (16 bytes per orbital) of one site; R/2
+// threads share a site, and the sites of a warp are permuted so that the 8
+// threads of every quarter-warp hit 8 distinct bank groups for the centre,
+// x+-1, y+-1 and z+1 blocks alike (conflict-free 128-bit shared loads).
+//
+// Work units are (z-chunk, tile) pairs taken in wave order (tiles fastest),
+// unit u on block u mod grid: the grid (one block per SM) works on adjacent
+// tiles at the same depth, so halo strips that another tile also reads come
+// from L2.  The arithmetic, its order and the epilogue are those of the
+// register z-march (ti_axes / ti_combine / epilogue of sweep.cuh), so the
+// vectors equal that sweep's bit for bit.
+//
+// Every mbarrier wait is bounded: a wait that runs out sets a device error
+// word (read by pvsc_device_error) and a block-wide abort flag; every warp then
+// leaves its loop, one thread waits (bounded) for the copies still in flight,
+// and the block finishes without touching the output further.
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+#include "sweep_bulk.cuh"
+
+namespace pvsc {
+
+constexpr unsigned kTmaWaitLimit = 1u << 24;
+constexpr int kTmaMaxUnits = 512;  // work units of one block (a table in shared memory)
+
+// Tile of TX x TY sites per R: 256 (site, vector pair) items, one per thread,
+// and NXS x-plane / NYS y_in-plane ring slots: three planes of copies in flight
+// beyond the two x planes and the y_in plane being read (DEEP = true).
+// DEEP = false: twice the tile (512 items, two per thread) with two planes of
+// copies in flight.
+template <int R, bool DEEP> struct TmaTile;
+template <> struct TmaTile<4, true> { static constexpr int TX = 16, TY = 8, NXS = 5, NYS = 4; };
+template <> struct TmaTile<8, true> { static constexpr int TX = 16, TY = 4, NXS = 5, NYS = 4; };
+template <> struct TmaTile<16, true> { static constexpr int TX = 8, TY = 4, NXS = 5, NYS = 4; };
+template <> struct TmaTile<4, false> { static constexpr int TX = 16, TY = 16, NXS = 3, NYS = 2; };
+template <> struct TmaTile<8, false> { static constexpr int TX = 16, TY = 8, NXS = 3, NYS = 2; };
+template <> struct TmaTile<16, false> { static constexpr int TX = 8, TY = 8, NXS = 3, NYS = 2; };
+// R = 32: 1 KB sites, 4 x 4 tiles of 256 items (the "deep" variant one slot deeper)
+template <> struct TmaTile<32, false> { static constexpr int TX = 4, TY = 4, NXS = 3, NYS = 2; };
+template <> struct TmaTile<32, true> { static constexpr int TX = 4, TY = 4, NXS = 4, NYS = 3; };
+// R = 64: 2 KB sites, 4 x 2 tiles of 256 items, one warp per site
+template <> struct TmaTile<64, false> { static constexpr int TX = 4, TY = 2, NXS = 3, NYS = 2; };
+template <> struct TmaTile<64, true> { static constexpr int TX = 4, TY = 2, NXS = 3, NYS = 2; };
+
+constexpr int round_up_1k(int b) { return (b + 1023) & ~1023; }
+
+template <int R, bool DEEP, int NW>
+struct TmaLayout {
+  static constexpr int NWARPS = NW;  // warps per block (8 or 16), one block per SM
+  static constexpr int TX = TmaTile<R, DEEP>::TX, TY = TmaTile<R, DEEP>::TY;
+  static constexpr int SITE_B = 32 * R;          // 4 orbitals x R complex64
+  static constexpr int ROWS = SITE_B / 128;      // 128-byte swizzle rows per site
+  static constexpr int CPS = R / 2;              // threads per site
+  static constexpr int SPW = 32 / CPS;           // sites per warp
+  static constexpr int ITEMS = TX * TY * CPS;
+  static constexpr int IPT = ITEMS / (32 * NW);  // items per thread
+  static constexpr int INT_B = TX * TY * SITE_B;  // interior tile
+  static constexpr int XS_B = TY * SITE_B;        // x-/x+ halo column
+  static constexpr int YS_B = TX * SITE_B;        // y-/y+ halo row
+  static constexpr int OFF_XM = INT_B, OFF_XP = INT_B + XS_B;
+  static constexpr int OFF_YM = INT_B + 2 * XS_B, OFF_YP = INT_B + 2 * XS_B + YS_B;
+  static constexpr int X_BYTES = INT_B + 2 * XS_B + 2 * YS_B;  // copied per x plane
+  static constexpr int XSTAGE = round_up_1k(X_BYTES);
+  static constexpr int V_B = TX * TY * 4;                  // fp32 potential per tile point
+  static constexpr int YSTAGE = INT_B + round_up_1k(2 * V_B);  // room for two (Weyl cells)
+  static constexpr int NXS = TmaTile<R, DEEP>::NXS, NYS = TmaTile<R, DEEP>::NYS;
+  static constexpr int BAR_OFF = NXS * XSTAGE + NYS * YSTAGE;
+  static constexpr int DOT_OFF = BAR_OFF + 128;  // fp64 dot partials [warp][dot][v][c]
+  static constexpr int DOT_B = NW * 4 * 2 * CPS * 8;
+  static constexpr int TAB_OFF = DOT_OFF + DOT_B;  // the block's units: (x0 | y0 << 16, z0 | n << 16)
+  static constexpr int TAB_B = kTmaMaxUnits * 8;
+  static constexpr size_t SMEM = 1024 + (size_t)TAB_OFF + TAB_B;  // + alignment slack
+  static_assert(IPT >= 1 && ITEMS % (32 * NW) == 0, "tile items");
+  static_assert(NXS >= 3 && NYS >= 2, "ring depth");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+// The tensor maps of one launch (kernel parameter, 64-byte aligned entries).
+struct TmaMaps {
+  CUtensorMap xi;   // x: interior tile box {32, ROWS, TX, TY, 1}
+  CUtensorMap xs;   // x: halo column box {32, ROWS, 1, TY, 1}
+  CUtensorMap ys;   // x: halo row box {32, ROWS, TX, 1, 1}
+  CUtensorMap yi;   // y_in: interior tile box
+  CUtensorMap v;    // fp32 potential: box {TX, TY, 1}
+  int has_yin;      // y_in present (gamma != 0)
+  int v_tma;        // potential copied with the y_in tile (stored potential)
+  int nch;          // z-chunks per column
+  int ntx, nty;     // tiles along x and y
+  long long nunits;
+};
+
+static __device__ int g_tma_sweep_error;
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            int c3, int c4, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+      "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Shared-memory counter increment with acquire-release ordering at block
+// scope: a warp's reads of a ring slot happen before its release count, and
+// the warp that brings the count to completion sees all of them before it
+// refills the slot.
+__device__ __forceinline__ unsigned release_count(unsigned* ctr) {
+  unsigned old;
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;" : "=r"(old) : "r"(smem_addr(ctr)) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// Bounded wait for the phase of the given parity; false if it ran out or the
+// block is aborting.
+__device__ __forceinline__ bool tma_wait(uint64_t* bar, unsigned parity, volatile int* abort) {
+  for (unsigned n = 0; n < kTmaWaitLimit; ++n) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((n & 255u) == 255u && *abort) return false;
+  }
+  atomicExch(&g_tma_sweep_error, 1);
+  *abort = 1;
+  return false;
+}
+
+// Site of a tile owned by quarter-warp slot q of a warp: consecutive sites in
+// one quarter-warp would meet the same bank group under the 128-byte swizzle
+// whenever their rows agree modulo 8; this permutation spreads them.
+template <int R>
+__device__ __forceinline__ int tma_site_perm(int q) {
+  if constexpr (R >= 16) {
+    return q;  // one site per quarter-warp
+  } else if constexpr (R == 8) {
+    return (q & 4) | ((q & 1) << 1) | ((q >> 1) & 1);  // quarter-warp: sites a, a + 2
+  } else {
+    const int ph = q >> 2, i = q & 3;  // quarter-warp: sites a, a + 2, a + 4, a + 6
+    return ((ph >> 1) << 3) + (ph & 1) + 2 * i;
+  }
+}
+
+// Swizzled offset of the 16-byte chunk of vectors (2c, 2c+1), orbital 0, of the
+// site at byte offset O (a multiple of 32 R) in a tile buffer: the logical
+// offset L = O + 16 c with its chunk bits XORed with its row bits.  Orbital o
+// then sits at (B ^ (K_o << 4)) + (its row offset) with the compile-time K of
+// tma_lds_blk (the row offset of orbital o modulo 8 never carries into the row
+// bits of L for R = 4 .. 64).
+template <int R>
+__device__ __forceinline__ uint32_t tma_swz(uint32_t O, int c) {
+  const uint32_t L = O + 16u * (uint32_t)c;
+  return L ^ (((L >> 7) & 7u) << 4);
+}
+
+// All four orbitals (two vectors each) of one site from a swizzled tile
+// buffer: buf = the buffer (1024-byte aligned), B = tma_swz of the site.
+// Plain shared-memory loads, so that the compiler schedules them; the
+// mbarrier waits (asm volatile with a memory clobber) order them after the copies.
+template <int R>
+__device__ __forceinline__ void tma_lds_blk(const unsigned char* buf, uint32_t B, Blk<float, 2>& b) {
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const int ao = o * 8 * R;                      // byte offset of orbital o in the site
+    const int K1 = (ao >> 4) & 7, K2 = (ao >> 7) & 7;
+    const float4 v = *reinterpret_cast<const float4*>(buf + ((B ^ (uint32_t)((K1 ^ K2) << 4)) + (uint32_t)(ao & ~127)));
+    b.v[o][0] = {v.x, v.y};
+    b.v[o][1] = {v.z, v.w};
+  }
+}
+
+// MODEL 1: TI sites; MODEL 3: Weyl-semimetal cells of two x-adjacent sites
+// (Eq. TB_H_wsm), whose four components form the same block as a TI site, with
+// the cell update of the Weyl sweeps and two potentials per cell.
+template <int R, bool DEEP, int NW, int FEAT, int MODEL>
+__global__ void __launch_bounds__(32 * NW, 1)
+    ti_sweep_tma(const __grid_constant__ Sweep p, const __grid_constant__ TmaMaps m) {
+  using L = TmaLayout<R, DEEP, NW>;
+  constexpr int NCW = NW, IPT = L::IPT, TX = L::TX, TY = L::TY;
+  constexpr bool WSM = MODEL == 3;
+  constexpr int VPC = WSM ? 2 : 1;  // potentials (sites) per tile point
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ int s_abort;
+  __shared__ unsigned s_cnt[L::NXS + L::NYS];  // releases per slot (x slots, then y slots)
+  __shared__ unsigned s_issued[2];             // x, y copies issued
+  const uint32_t raw = smem_addr(smem_raw);
+  unsigned char* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  const uint32_t sbase = smem_addr(base);
+  uint64_t* full_x = reinterpret_cast<uint64_t*>(base + L::BAR_OFF);
+  uint64_t* full_y = full_x + L::NXS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < L::NXS; ++s) mbar_init(&full_x[s], 1);
+    for (int s = 0; s < L::NYS; ++s) mbar_init(&full_y[s], 1);
+    for (int s = 0; s < L::NXS + L::NYS; ++s) s_cnt[s] = 0;
+    s_issued[0] = s_issued[1] = 0;
+    s_abort = 0;
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+
+  const Geometry& g = p.g;
+  const int Lx = (int)(g.L[0] / VPC), Ly = (int)g.L[1], Lz = (int)g.L[2];  // tile points along x
+  const int64_t plane = (int64_t)Lx * Ly;
+  const int G = gridDim.x;
+  volatile int* abort = &s_abort;
+  // This block's units u = blockIdx.x + lu G (lu = 0 .. nlu-1), decoded once into
+  // a shared table, so that the per-plane copy logic does no division.
+  const int nlu = (int)((m.nunits - blockIdx.x + G - 1) / G);
+  uint2* tab = reinterpret_cast<uint2*>(base + L::TAB_OFF);
+  for (int i = threadIdx.x; i < nlu; i += blockDim.x) {
+    const int64_t u = blockIdx.x + (int64_t)i * G;
+    const int64_t ntiles = (int64_t)m.ntx * m.nty;
+    const int64_t ch = u / ntiles, t = u - ch * ntiles, ty = t / m.ntx;
+    const uint32_t x0 = (uint32_t)((t - ty * m.ntx) * TX), y0 = (uint32_t)(ty * TY);
+    const uint32_t z0 = (uint32_t)(ch * Lz / m.nch), z1 = (uint32_t)((ch + 1) * Lz / m.nch);
+    tab[i] = make_uint2(x0 | (y0 << 16), z0 | ((z1 - z0) << 16));
+  }
+  __syncthreads();
+  auto planes_of = [&](int lu) { return (int)(tab[lu].y >> 16); };
+  // The copies of a block, in the order they are consumed: per unit (of n
+  // planes z0 .. z0+n-1) the x planes z0-1 .. z0+n (positions j = -1 .. n) and
+  // the y_in / potential planes z0 .. z0+n-1 (positions j = 0 .. n-1).  Copy k
+  // of a ring goes to slot k mod (ring size); when the last warp releases copy
+  // k, that warp issues copy k + ring size into the freed slot.  Positions
+  // k steps further along the sequence:
+  auto ahead_x = [&](int& lu, int& j, int steps) -> bool {
+    j += steps;
+    while (lu < nlu) {
+      const int n = planes_of(lu);
+      if (j <= n) return true;
+      j -= n + 2;
+      ++lu;
+    }
+    return false;
+  };
+  auto ahead_y = [&](int& lu, int& j, int steps) -> bool {
+    j += steps;
+    while (lu < nlu) {
+      const int n = planes_of(lu);
+      if (j < n) return true;
+      j -= n;
+      ++lu;
+    }
+    return false;
+  };
+  auto issue_x = [&](int lu, int j, uint32_t k) {
+    const uint2 e = tab[lu];
+    const int x0 = (int)(e.x & 0xffffu), y0 = (int)(e.x >> 16), z0 = (int)(e.y & 0xffffu);
+    const int TXe = min(TX, Lx - x0), TYe = min(TY, Ly - y0);
+    // halo coordinates: wrapped on a periodic axis, out of range (zeros) past an open edge
+    const int hxm = x0 > 0 ? x0 - 1 : (g.per[0] ? Lx - 1 : -1);
+    const int hxp = x0 + TXe < Lx ? x0 + TXe : (g.per[0] ? 0 : Lx);
+    const int hym = y0 > 0 ? y0 - 1 : (g.per[1] ? Ly - 1 : -1);
+    const int hyp = y0 + TYe < Ly ? y0 + TYe : (g.per[1] ? 0 : Ly);
+    int zx = z0 + j;
+    if (g.per[2]) zx = zx < 0 ? zx + Lz : (zx >= Lz ? zx - Lz : zx);
+    const uint32_t slot = k % L::NXS;
+    const uint32_t dst = sbase + slot * L::XSTAGE;
+    mbar_arrive_expect_tx(&full_x[slot], L::X_BYTES);
+    tma_load_5d(dst, &m.xi, 0, 0, x0, y0, zx, &full_x[slot]);
+    tma_load_5d(dst + L::OFF_XM, &m.xs, 0, 0, hxm, y0, zx, &full_x[slot]);
+    tma_load_5d(dst + L::OFF_XP, &m.xs, 0, 0, hxp, y0, zx, &full_x[slot]);
+    tma_load_5d(dst + L::OFF_YM, &m.ys, 0, 0, x0, hym, zx, &full_x[slot]);
+    tma_load_5d(dst + L::OFF_YP, &m.ys, 0, 0, x0, hyp, zx, &full_x[slot]);
+    atomicMax(&s_issued[0], k + 1);
+  };
+  const unsigned ybytes = (m.has_yin ? L::INT_B : 0) + (m.v_tma ? VPC * L::V_B : 0);
+  auto issue_y = [&](int lu, int j, uint32_t k) {
+    const uint2 e = tab[lu];
+    const int x0 = (int)(e.x & 0xffffu), y0 = (int)(e.x >> 16), z0 = (int)(e.y & 0xffffu);
+    const uint32_t slot = k % L::NYS;
+    const uint32_t dst = sbase + L::NXS * L::XSTAGE + slot * L::YSTAGE;
+    if (ybytes) {
+      mbar_arrive_expect_tx(&full_y[slot], ybytes);
+      if (m.has_yin) tma_load_5d(dst, &m.yi, 0, 0, x0, y0, z0 + j, &full_y[slot]);
+      if (m.v_tma) tma_load_3d(dst + L::INT_B, &m.v, VPC * x0, y0, z0 + j, &full_y[slot]);
+    } else {
+      mbar_arrive(&full_y[slot]);
+    }
+    atomicMax(&s_issued[1], k + 1);
+  };
+  // release copy k (unit lu, position j) of a ring by this warp; the last warp refills
+  auto release_x = [&](uint32_t k, int lu, int j) {
+    __syncwarp();
+    if (lane == 0 && release_count(&s_cnt[k % L::NXS]) % NCW == NCW - 1)
+      if (ahead_x(lu, j, L::NXS)) issue_x(lu, j, k + L::NXS);
+  };
+  auto release_y = [&](uint32_t k, int lu, int j) {
+    __syncwarp();
+    if (lane == 0 && release_count(&s_cnt[L::NXS + k % L::NYS]) % NCW == NCW - 1)
+      if (ahead_y(lu, j, L::NYS)) issue_y(lu, j, k + L::NYS);
+  };
+
+  if (threadIdx.x == 0) {
+    prefetch_map(&m.xi);
+    prefetch_map(&m.xs);
+    prefetch_map(&m.ys);
+    if (m.has_yin) prefetch_map(&m.yi);
+    if (m.v_tma) prefetch_map(&m.v);
+    // the first copies of both rings
+    int lu = 0, j = -1;
+    for (uint32_t k = 0; k < (uint32_t)L::NXS; ++k) {
+      if (k > 0 && !ahead_x(lu, j, 1)) break;
+      issue_x(lu, j, k);
+    }
+    lu = 0;
+    j = 0;
+    for (uint32_t k = 0; k < (uint32_t)L::NYS; ++k) {
+      if (k > 0 && !ahead_y(lu, j, 1)) break;
+      issue_y(lu, j, k);
+    }
+  }
+
+  const int c = lane % L::CPS;
+  const int q = lane / L::CPS;
+  const VecCoef<float, 2> cf = load_coef<float, 2>(p, c);
+  DotAcc<float, 2> dacc;  // compensated fp32 sums; their fp64 part lives in shared memory
+  dacc.init();
+  double* wdots = reinterpret_cast<double*>(base + L::DOT_OFF) + warp * kNumDots * 2 * L::CPS;
+  if constexpr (has_dots(FEAT)) {
+    if (lane < L::CPS)
+      for (int k = 0; k < kNumDots * 2; ++k) wdots[k * L::CPS + lane] = 0.0;
+  }
+  // flush a unit's compensated fp32 sums into this warp's fp64 partials (fixed order)
+  auto flush_dots = [&]() {
+#pragma unroll
+    for (int d = 0; d < kNumDots; ++d)
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        double t = widen(dacc.s[d][v]) + widen(dacc.c[d][v]);
+        dacc.s[d][v] = 0.f;
+        dacc.c[d][v] = 0.f;
+        for (int off = 16; off >= L::CPS; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane < L::CPS) wdots[(d * 2 + v) * L::CPS + lane] += t;
+      }
+  };
+  Blk<float, 2> xmr[IPT];
+  uint32_t kx = 0, ky = 0;
+  const unsigned char* ybase = base + L::NXS * L::XSTAGE;
+  bool alive = true;
+  for (int lu = 0; lu < nlu && alive; ++lu) {
+    const uint2 e = tab[lu];
+    const int x0 = (int)(e.x & 0xffffu), y0 = (int)(e.x >> 16), z0 = (int)(e.y & 0xffffu);
+    const int n = (int)(e.y >> 16);
+    const int TXe = min(TX, Lx - x0), TYe = min(TY, Ly - y0);
+    uint32_t Bc[IPT], Bxm[IPT], Bxp[IPT], Bym[IPT], Byp[IPT], Vo[IPT];
+    bool ok[IPT];
+    int64_t col[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const int li = (i * NCW + warp) * L::SPW + tma_site_perm<R>(q);
+      const int ly = li / TX, lx = li - ly * TX;
+      ok[i] = lx < TXe && ly < TYe;
+      const uint32_t SB = L::SITE_B;
+      Bc[i] = tma_swz<R>(li * SB, c);
+      Bxm[i] = tma_swz<R>(lx > 0 ? (li - 1) * SB : L::OFF_XM + ly * SB, c);
+      Bxp[i] = tma_swz<R>(lx + 1 < TXe ? (li + 1) * SB : L::OFF_XP + ly * SB, c);
+      Bym[i] = tma_swz<R>(ly > 0 ? (li - TX) * SB : L::OFF_YM + lx * SB, c);
+      Byp[i] = tma_swz<R>(ly + 1 < TYe ? (li + TX) * SB : L::OFF_YP + lx * SB, c);
+      Vo[i] = L::INT_B + 4 * VPC * li;
+      col[i] = (int64_t)(x0 + lx) + (int64_t)Lx * (y0 + ly);
+    }
+    // plane z0 - 1: x(z-1) of every site into registers
+    if (!tma_wait(&full_x[kx % L::NXS], (kx / L::NXS) & 1, abort)) {
+      alive = false;
+      break;
+    }
+    {
+      const unsigned char* s0 = base + (kx % L::NXS) * L::XSTAGE;
+#pragma unroll
+      for (int i = 0; i < IPT; ++i)
+        if (ok[i]) tma_lds_blk<R>(s0, Bc[i], xmr[i]);
+    }
+    release_x(kx, lu, -1);
+    ++kx;
+    if (!tma_wait(&full_x[kx % L::NXS], (kx / L::NXS) & 1, abort)) {
+      alive = false;
+      break;
+    }
+    for (int j = 0; j < n; ++j) {
+      if (!tma_wait(&full_x[(kx + 1) % L::NXS], ((kx + 1) / L::NXS) & 1, abort) ||
+          !tma_wait(&full_y[ky % L::NYS], (ky / L::NYS) & 1, abort)) {
+        alive = false;
+        break;
+      }
+      const int z = z0 + j;
+      const unsigned char* s0 = base + (kx % L::NXS) * L::XSTAGE;
+      const unsigned char* s1 = base + ((kx + 1) % L::NXS) * L::XSTAGE;
+      const unsigned char* sy = ybase + (ky % L::NYS) * L::YSTAGE;
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        if (!ok[i]) continue;
+        const int64_t s = col[i] + plane * z;
+        if constexpr (WSM) {
+          // the Weyl cell update of the Weyl sweeps, on the cell blocks around the cell
+          Blk<float, 2> xp, ax, bx, ay, by, xc, yi, yn;
+          tma_lds_blk<R>(s1, Bc[i], xp);
+          tma_lds_blk<R>(s0, Bxm[i], ax);
+          tma_lds_blk<R>(s0, Bxp[i], bx);
+          tma_lds_blk<R>(s0, Bym[i], ay);
+          tma_lds_blk<R>(s0, Byp[i], by);
+          tma_lds_blk<R>(s0, Bc[i], xc);
+          if (m.has_yin) tma_lds_blk<R>(sy, Bc[i], yi);
+          const float V0 = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i])
+                                   : site_potential_t<float>(g, 2 * s);
+          const float V1 = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i] + 4)
+                                   : site_potential_t<float>(g, 2 * s + 1);
+          wsm_cell_update(cf, V0, V1, xmr[i], xc, xp, ax, bx, ay, by, m.has_yin ? &yi : nullptr, yn);
+          const int64_t sites[4] = {2 * s, 2 * s, 2 * s + 1, 2 * s + 1};
+          epilogue<float, 2, FEAT>(p, s, c, xc, yn, dacc, sites);
+          xmr[i] = xc;
+          continue;
+        }
+        // the axes in ti_axes' order (z pair, x pair, y pair), each pair loaded
+        // just before it is folded in, so that few blocks are live at a time
+        Blk<float, 2> S, D, yn;
+        {
+          Blk<float, 2> xp;
+          tma_lds_blk<R>(s1, Bc[i], xp);
+          axis_z_init(xmr[i], xp, S, D);
+        }
+        {
+          Blk<float, 2> ax, bx;
+          tma_lds_blk<R>(s0, Bxm[i], ax);
+          tma_lds_blk<R>(s0, Bxp[i], bx);
+          axis_x_add(ax, bx, S, D);
+        }
+        {
+          Blk<float, 2> ay, by;
+          tma_lds_blk<R>(s0, Bym[i], ay);
+          tma_lds_blk<R>(s0, Byp[i], by);
+          axis_y_add(ay, by, S, D);
+        }
+        Blk<float, 2> xc, yi;
+        tma_lds_blk<R>(s0, Bc[i], xc);
+        if (m.has_yin) tma_lds_blk<R>(sy, Bc[i], yi);
+        const float Vs = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i]) : site_potential_t<float>(g, s);
+        ti_combine(cf, Vs, xc, S, D, m.has_yin ? &yi : nullptr, yn, g);
+        const int64_t sites[4] = {s, s, s, s};
+        epilogue<float, 2, FEAT>(p, s, c, xc, yn, dacc, sites);
+        xmr[i] = xc;
+      }
+      release_x(kx, lu, j);
+      release_y(ky, lu, j);
+      ++kx;
+      ++ky;
+    }
+    if (!alive) break;
+    // plane z1 (waited on as z + 1 by the last plane) is no longer needed
+    release_x(kx, lu, n);
+    ++kx;
+    if constexpr (has_dots(FEAT)) flush_dots();  // once per unit
+  }
+  __syncthreads();  // every warp has left the rings: no copy is issued after this
+  if (threadIdx.x == 0) {
+    // drain: wait (bounded) for the last copy issued into every slot, so that no
+    // copy is in flight when the block reuses its shared memory or exits (after
+    // an abort some of them were never waited for)
+    const uint32_t nx = s_issued[0], ny = s_issued[1];
+    for (uint32_t k = nx > (uint32_t)L::NXS ? nx - L::NXS : 0; k < nx; ++k)
+      for (unsigned t = 0; t < kTmaWaitLimit && !mbar_try_wait(&full_x[k % L::NXS], (k / L::NXS) & 1); ++t) {
+      }
+    for (uint32_t k = ny > (uint32_t)L::NYS ? ny - L::NYS : 0; k < ny; ++k)
+      for (unsigned t = 0; t < kTmaWaitLimit && !mbar_try_wait(&full_y[k % L::NYS], (k / L::NYS) & 1); ++t) {
+      }
+  }
+  __syncthreads();
+  if constexpr (has_dots(FEAT)) {
+    // fixed-order reduction: the warps' partials in index order, then the
+    // blocks in finish_dots (after an abort the values are garbage, but the
+    // arrival counter stays consistent)
+    const double* wd = reinterpret_cast<const double*>(base + L::DOT_OFF);
+    double* row = p.partials + (size_t)blockIdx.x * kNumDots * R;
+    for (int t = threadIdx.x; t < kNumDots * R; t += blockDim.x) {
+      const int d = t / R, r = t - d * R;
+      double sum = 0.0;
+      for (int w = 0; w < NCW; ++w) sum += wd[((w * kNumDots + d) * 2 + (r & 1)) * L::CPS + (r >> 1)];
+      row[t] = sum;
+    }
+    finish_dots(p);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+inline PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+template <int R, bool DEEP>
+static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
+  using L = TmaLayout<R, DEEP, 8>;
+  auto enc = encode_tiled();
+  if (!enc) return set_error(PVSC_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
+  const int vpc = lat->g.model == PVSC_WSM ? 2 : 1;  // Weyl cells: two sites each
+  const cuuint64_t Lx = lat->g.L[0] / vpc, Ly = lat->g.L[1], Lz = lat->g.L[2];
+  const cuuint64_t dims[5] = {32, (cuuint64_t)L::ROWS, Lx, Ly, Lz};
+  const cuuint64_t strides[4] = {128, (cuuint64_t)L::SITE_B, (cuuint64_t)L::SITE_B * Lx,
+                                 (cuuint64_t)L::SITE_B * Lx * Ly};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  auto tile5 = [&](CUtensorMap* map, const void* ptr, cuuint32_t bx, cuuint32_t by) -> int {
+    const cuuint32_t box[5] = {32, (cuuint32_t)L::ROWS, bx, by, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(ptr), dims, strides,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(PVSC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return PVSC_OK;
+  };
+  std::memset(&m, 0, sizeof(m));
+  if (int rc = tile5(&m.xi, p.x, L::TX, L::TY)) return rc;
+  if (int rc = tile5(&m.xs, p.x, 1, L::TY)) return rc;
+  if (int rc = tile5(&m.ys, p.x, L::TX, 1)) return rc;
+  m.has_yin = p.yin != nullptr;
+  if (m.has_yin)
+    if (int rc = tile5(&m.yi, p.yin, L::TX, L::TY)) return rc;
+  m.v_tma = lat->g.v_mode == 1;
+  if (m.v_tma) {
+    const cuuint64_t vd[3] = {vpc * Lx, Ly, Lz};  // the potential is per site
+    const cuuint64_t vs[2] = {4 * vpc * Lx, 4 * vpc * Lx * Ly};
+    const cuuint32_t vb[3] = {(cuuint32_t)(vpc * L::TX), (cuuint32_t)L::TY, 1};
+    const CUresult r = enc(&m.v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(lat->g.V32), vd, vs, vb,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(PVSC_ERR_CUDA, "cuTensorMapEncodeTiled (potential) failed (%d)", (int)r);
+  }
+  return PVSC_OK;
+}
+
+template <int R, bool DEEP, int NW, int MODEL>
+static void* tma_kernel(int feat) {
+  switch (feat) {
+    case 0: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, 0, MODEL>);
+    case F_DOTS: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS, MODEL>);
+    case F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_Z, MODEL>);
+    case F_DOTS | F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS | F_Z, MODEL>);
+    case F_ACC: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_ACC, MODEL>);
+    default: return nullptr;
+  }
+}
+
+// z-chunks per column: the count whose wave quantisation and per-unit halo
+// planes (two extra x planes, about a third of a plane's traffic each) cost least.
+static int auto_chunks(int64_t ntiles, int64_t Lz, int64_t grid) {
+  int best = 1;
+  double best_cost = 1e300;
+  for (int64_t nch = 1; nch <= Lz; ++nch) {
+    const int64_t waves = (ntiles * nch + grid - 1) / grid;
+    const double cost = (double)waves * ((double)((Lz + nch - 1) / nch) + 0.7);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = (int)nch;
+    }
+  }
+  return best;
+}
+
+
+template <int R, bool DEEP, int NW, int MODEL = PVSC_TI>
+static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
+  using L = TmaLayout<R, DEEP, NW>;
+  void* fn = tma_kernel<R, DEEP, NW, MODEL>(feat);
+  if (!fn) return set_error(PVSC_ERR_UNSUPPORTED, "no TMA-staged sweep for feature set %d", feat);
+  if (int rc = allow_max_smem(fn)) return rc;
+  int occ = 0;
+  PVSC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * NW, L::SMEM));
+  if (occ < 1) return set_error(PVSC_ERR_CUDA, "the TMA-staged sweep does not fit an SM");
+  p.C = R / 2;
+  p.tile_x = L::TX;
+  p.tile_y = L::TY;
+  TmaMaps m;
+  if (int rc = encode_maps<R, DEEP>(lat, p, m)) return rc;
+  const int64_t Lx = lat->g.L[0] / (MODEL == PVSC_WSM ? 2 : 1), Ly = lat->g.L[1], Lz = lat->g.L[2];
+  m.ntx = (int)((Lx + L::TX - 1) / L::TX);
+  m.nty = (int)((Ly + L::TY - 1) / L::TY);
+  const int64_t ntiles = (int64_t)m.ntx * m.nty;
+  const int64_t grid_max = (int64_t)lat->sm_count * occ;
+  int nch = sh.zslab > 0 ? (int)((Lz + sh.zslab - 1) / sh.zslab) : auto_chunks(ntiles, Lz, grid_max);
+  if (nch < 1) nch = 1;
+  if (nch > Lz) nch = (int)Lz;
+  while (nch > 1 && (ntiles * nch + grid_max - 1) / grid_max > kTmaMaxUnits) --nch;  // unit table
+  m.nch = nch;
+  m.nunits = ntiles * nch;
+  p.zslab = (int)((Lz + nch - 1) / nch);
+  const int grid = (int)(m.nunits < grid_max ? m.nunits : grid_max);
+  void* args[] = {&p, &m};
+  PVSC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(32 * NW), args, L::SMEM, st));
+  return PVSC_OK;
+}
+
+// The two tiles of kernel 7 per R, as (tile_x, tile_y): {large, deep}.
+}  // namespace pvsc

@@ -155,3 +155,40 @@ def test_tma_sweep_reports_no_device_error():
     x = pv.random_vectors(lat, 8, pv.C64, 1)
     pv.apply_H(lat, x)
     assert pv.device_error() == 0
+
+
+# Weyl-semimetal cells (two x-adjacent sites) on the TMA-staged sweep: Lx a
+# multiple of 4; periodic y of length 1 and 2, open and periodic z, partial tiles
+WSM_CASES = [((16, 5, 4), (1, 1, 0)), ((36, 2, 3), (1, 1, 1)), ((8, 1, 5), (0, 1, 1)), ((12, 9, 2), (0, 0, 0))]
+
+
+@pytest.mark.parametrize("dims,per", WSM_CASES)
+@pytest.mark.parametrize("R", [4, 8, 16, 32, 64])
+def test_tma_weyl_cells_equal_the_cell_sweeps_and_oracle(dims, per, R):
+    n = int(np.prod(dims))
+    V = W.disorder_potential(n, 1.5, 6)
+    lat = pv.Lattice.wsm(dims, per, V=V)
+    H = O.wsm_hamiltonian(dims, per, V)
+    x = torch.from_numpy(W.gaussian_block(H.shape[0], R, 1)).to("cuda", torch.complex64)
+    y_flat = pv.apply_H(lat, x)              # default: the flat cell sweep
+    lat.set_tuning(R, pv.C64, threads=128, kernel=0)
+    y_march = pv.apply_H(lat, x)             # the z-marching cell sweep
+    lat.set_tuning(R, pv.C64, kernel=7)
+    y_tma = pv.apply_H(lat, x)
+    assert torch.equal(y_tma, y_march) and torch.equal(y_tma, y_flat)
+    ref = H @ x.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(y_tma.cpu().numpy() - ref) / np.linalg.norm(ref) < 2e-6
+    # KPM moments and a fused step with z and dots
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    r = W.random_phase_block(H.shape[0], R, 5)
+    mu = pv.kpm_moments(lat, 24, a, b, r0=torch.from_numpy(r).to("cuda", torch.complex64)).cpu().numpy()
+    refm = O.kpm_moments(H, r, 24, a, b).real
+    assert np.max(np.abs(mu - refm)) < 1e-4
+    yin = torch.from_numpy(W.gaussian_block(H.shape[0], R, 3)).to("cuda", torch.complex64)
+    z0 = torch.from_numpy(W.gaussian_block(H.shape[0], R, 4)).to("cuda", torch.complex64)
+    ya, za = yin.clone(), z0.clone()
+    pv.cheb_step(lat, x, ya, [0.2] * R, [0.1] * R, [-1.0] * R, z=za, delta=[0.5] * R, dots=7)
+    lat.set_tuning(R, pv.C64, threads=128, kernel=0)
+    yb, zb = yin.clone(), z0.clone()
+    pv.cheb_step(lat, x, yb, [0.2] * R, [0.1] * R, [-1.0] * R, z=zb, delta=[0.5] * R, dots=7)
+    assert torch.equal(ya, yb) and torch.equal(za, zb)
