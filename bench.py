@@ -594,10 +594,13 @@ def run_workload(args, pv, dev, rank, world):
         line.update({"workload": "wsm_kpm", "value": round(world * lups / (ms * 1e-3) / 1e9, 3),
                      "ms_per_step": round(ms, 3), "steps": args.steps, "dtype": "c64",
                      "config": {"workload": "Weyl semimetal KPM: 256x32x32 sites (PBC x,y; open z), k0=pi/2, "
-                                            "W=1, 16 random-phase vectors, 2048 moments"},
+                                            "W=1, 16 random-phase vectors, 2048 moments", "launch": lat.get_tuning(R, pv.C64)},
                      "dos_at_E0_per_site": float(pv.dos(lat, mu, E0, a, b)[0].item()) / lat.n_sites,
                      "roofline": _hbm_roof(48.0 + 4.0 / R, lups, ms,
-                                           "wsm_sweep<float,2,F_DOTS> (two-site cells)"),
+                                           {7: "ti_sweep_tma<*,*,8,F_DOTS,3> (TMA-staged Weyl cells)",
+                                            0: "wsm_march_sweep<float,2,F_DOTS> (z-marching cells)"}.get(
+                                               int(lat.get_tuning(R, pv.C64).get("kernel", 1)),
+                                               "wsm_sweep<float,2,F_DOTS> (flat two-site cells)")),
                      "clocks": clk, "gpu_launches": args.steps * (M // 2)})
     elif args.workload == "batched":
         specs = W.batched_lattices()
