@@ -621,6 +621,10 @@ def run_workload(args, pv, dev, rank, world):
                                   "mu0_min": float(mu[:, :, 0].min().item())}))
             return 0
         seeds = [vector_seed_for(i, rank) for i in range(len(lats))]
+        tuning = None
+        if not args.no_autotune:  # the launch shape timed on the batch itself, 32 moments
+            tuning = pv.autotune_batched(lats, 32, [x[0] for x in ab], [x[1] for x in ab], R=R, prec=pv.C64,
+                                         seeds=seeds)
         work = pv.work_buffer(pv.batched_work_bytes(lats, R, pv.C64, M), dev)
         mu = torch.empty((len(lats), R, M), dtype=torch.float64, device=dev)
         run = lambda: pv.kpm_moments_batched(lats, M, [x[0] for x in ab], [x[1] for x in ab], R=R,
@@ -636,7 +640,7 @@ def run_workload(args, pv, dev, rank, world):
                      "ms_per_step": round(ms, 3), "steps": args.steps, "dtype": "c64",
                      "config": {"workload": "64 periodic TI cubes, L from {24,32,48,64,96}, W~U[0,5), R=16, "
                                             "1024 moments, one persistent cooperative launch in a CUDA graph",
-                                "sites": sites, "mu0_min": float(mu[:, :, 0].min().item())},
+                                "sites": sites, "mu0_min": float(mu[:, :, 0].min().item()), "launch": tuning},
                      "roofline": _hbm_roof(96.0 + 8.0 / R, lups, ms, "kpm_batched_kernel<float,2>"),
                      "clocks": clk, "gpu_launches": args.steps})
     elif args.workload == "adjoint":

@@ -113,6 +113,7 @@ _SIGNATURES = {
     "pvsc_get_tuning": (_i, [_vp, _i, _i, ctypes.POINTER(Tuning)]),
     "pvsc_autotune": (_i, [_vp, _i, _i, ctypes.POINTER(Tuning), _vp]),
     "pvsc_autotune_op": (_i, [_vp, _i, _i, _i, ctypes.POINTER(Tuning), _vp]),
+    "pvsc_autotune_batched": (_i, [_vp, _i, _i, _i, _vp, _i, _vp, _vp, ctypes.POINTER(Tuning), _vp]),
     "pvsc_debug_neighbours": (_i, [_vp, _vp, _vp]),
     "pvsc_last_error": (ctypes.c_char_p, []),
     "pvsc_version": (ctypes.c_char_p, []),
@@ -570,6 +571,18 @@ def kpm_moments_batched(lats, M, a, b, R=16, prec=C64, seeds=None, work=None, mu
     _check(_lib.pvsc_kpm_moments_batched(hs, n, R, prec, sarr, int(M), _darr(a), _darr(b), _ptr(mu),
                                          _ptr(work), work.numel(), _stream(stream)))
     return mu
+
+
+def autotune_batched(lats, M, a, b, R=16, prec=C64, seeds=None, stream=None) -> dict:
+    """Tune the batched KPM's launch shape on the batch itself (pvsc_autotune_batched)."""
+    n = len(lats)
+    hs = (ctypes.c_void_p * n)(*[l.handle.value for l in lats])
+    seeds = list(seeds) if seeds is not None else list(range(n))
+    sarr = (ctypes.c_uint64 * n)(*[int(s) for s in seeds])
+    t = Tuning()
+    _check(_lib.pvsc_autotune_batched(hs, n, R, prec, sarr, int(M), _darr(a), _darr(b), ctypes.byref(t),
+                                      _stream(stream)))
+    return t.as_dict()
 
 
 def device_error(clear: bool = True) -> int:

@@ -25,6 +25,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "sweep.cuh"
 
@@ -425,6 +427,87 @@ int pvsc_kpm_moments_batched(const pvsc_lattice* const* lats, int n, int R, int 
   PVSC_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   PVSC_CUDA_TRY(cudaStreamSynchronize(st));
   if (herr) return set_error(PVSC_ERR_TIMEOUT, "a batched-KPM wait exceeded %llu spins", g_wait_limit);
+  return PVSC_OK;
+}
+
+// Launch-shape autotuner of the batched KPM over the whole batch: threads per
+// block (and so the vectors per block), z-segment length of the units and
+// blocks per SM are timed on the batch itself with a short moment count, and
+// the fastest shape becomes the (R, prec) tuning entry of lats[0], which the
+// batched calls read.
+int pvsc_autotune_batched(pvsc_lattice* const* lats, int n, int R, int prec, const uint64_t* seeds,
+                          int M, const double* a, const double* b, pvsc_tuning* best, void* stream) {
+  if (!lats || n < 1 || n > kMaxBatch || !lats[0])
+    return set_error(PVSC_ERR_ARG, "need 1 to %d lattices", kMaxBatch);
+  if (!valid_R(R)) return set_error(PVSC_ERR_ARG, "R = %d: must be 1, 2, 4, 8, 16, 32 or 64", R);
+  if (prec != PVSC_C128 && prec != PVSC_C64) return set_error(PVSC_ERR_ARG, "unknown precision %d", prec);
+  if (M < 2 || !seeds || !a || !b) return set_error(PVSC_ERR_ARG, "need M >= 2, seeds, a and b");
+  pvsc_lattice* l0 = lats[0];
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int C = R / vpt_for(R, prec);
+  int64_t Lzmax = 1;
+  for (int i = 0; i < n; ++i) {
+    if (!lats[i]) return set_error(PVSC_ERR_ARG, "lattice %d is NULL", i);
+    Lzmax = std::max<int64_t>(Lzmax, lats[i]->g.L[2]);
+  }
+  std::vector<pvsc_tuning> cands;
+  for (int th : {128, 256})
+    if (th % C == 0)
+      for (int zs : {0, 16, 24, 32, 48, 64})
+        if (zs == 0 || zs < Lzmax)
+          for (int bps : {0, 1}) cands.push_back(pvsc_tuning{th, bps, zs, 0.f, 0, 0, 0, 0});
+  auto saved = l0->tuning.find({R, prec});
+  const bool had = saved != l0->tuning.end();
+  const pvsc_tuning old = had ? saved->second : pvsc_tuning{};
+  size_t wmax = 0;
+  for (const pvsc_tuning& c : cands) {
+    l0->tuning[{R, prec}] = c;
+    wmax = std::max(wmax, pvsc_batched_work_bytes(lats, n, R, prec, M));
+  }
+  void *work = nullptr, *mu = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(work);
+    cudaFree(mu);
+  };
+  int rc = PVSC_OK;
+  if (wmax == 0 || cudaMalloc(&work, wmax) != cudaSuccess ||
+      cudaMalloc(&mu, sizeof(double) * (size_t)n * R * M) != cudaSuccess) {
+    cleanup();
+    if (had) l0->tuning[{R, prec}] = old; else l0->tuning.erase({R, prec});
+    return set_error(PVSC_ERR_OOM, "batched autotune could not allocate its buffers");
+  }
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  pvsc_tuning win{256, 0, 0, 1e30f, 0, 0, 0, 0};
+  for (const pvsc_tuning& c : cands) {
+    l0->tuning[{R, prec}] = c;
+    drop_graphs(l0);
+    const size_t wb = pvsc_batched_work_bytes(lats, n, R, prec, M);
+    double* mp = static_cast<double*>(mu);
+    if ((rc = pvsc_kpm_moments_batched(lats, n, R, prec, seeds, M, a, b, mp, work, wb, stream)) != PVSC_OK) break;
+    float ms = 0.f;
+    if (cudaEventRecord(e0, st) != cudaSuccess) { rc = set_error(PVSC_ERR_CUDA, "event record failed"); break; }
+    if ((rc = pvsc_kpm_moments_batched(lats, n, R, prec, seeds, M, a, b, mp, work, wb, stream)) != PVSC_OK) break;
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < win.time_ms) {
+      win = c;
+      win.time_ms = ms;
+    }
+  }
+  cleanup();
+  if (rc != PVSC_OK) {
+    if (had) l0->tuning[{R, prec}] = old; else l0->tuning.erase({R, prec});
+    drop_graphs(l0);
+    return rc;
+  }
+  l0->tuning[{R, prec}] = win;
+  drop_graphs(l0);
+  if (best) *best = win;
   return PVSC_OK;
 }
 

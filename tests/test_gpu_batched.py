@@ -237,3 +237,18 @@ def test_explicit_tuning_shapes_all_agree():
         assert torch.equal(pv.apply_H(lat, x), ref)
     with pytest.raises(pv.PvscError):
         lat.set_tuning(16, pv.C64, 100, 0, 0)  # not a multiple of 32
+
+
+def test_batch_autotuner_picks_a_shape_and_results_hold():
+    specs = [(6, 1.0, 61), ((9, 8, 12), 2.0, 62), (4, 0.5, 63), ((5, 7, 20), 3.0, 64)]
+    lats, Hs, ab = _lattices(specs)
+    R, M = 4, 24
+    seeds = [70 + i for i in range(len(lats))]
+    args = ([x[0] for x in ab], [x[1] for x in ab])
+    t = pv.autotune_batched(lats, 8, *args, R=R, prec=pv.C64, seeds=seeds)
+    assert t["threads"] in (128, 256) and t["time_ms"] > 0
+    assert lats[0].get_tuning(R, pv.C64)["zslab"] == t["zslab"]
+    mu = pv.kpm_moments_batched(lats, M, *args, R=R, prec=pv.C64, seeds=seeds).cpu().numpy()
+    for i, (H, (a, b)) in enumerate(zip(Hs, ab)):
+        ref = O.kpm_moments(H, W.random_phase_block(H.shape[0], R, seeds[i]), M, a, b).real
+        assert np.max(np.abs(mu[i] - ref)) / ref[0, 0] < 1e-4, i
