@@ -410,16 +410,6 @@ int pvsc_kpm_moments_batched(const pvsc_lattice* const* lats, int n, int R, int 
                              const uint64_t* seeds, int M, const double* a, const double* b,
                              double* mu, void* work, size_t work_bytes, void* stream);
 
-/* Launch-shape autotuner of the batched KPM over the whole batch (the batched
- * calls read the (R, prec) tuning entry of lats[0]): threads per block (128,
- * 256), z-segment length of the work units (whole columns, 16 .. 64 planes)
- * and blocks per SM (occupancy maximum, 1) are timed with CUDA events on the
- * batch itself running M moments, and the fastest becomes that entry.
- * Allocates and frees its own buffers; synchronises the stream.  Query
- * pvsc_batched_work_bytes again afterwards (it depends on the shape). */
-int pvsc_autotune_batched(pvsc_lattice* const* lats, int n, int R, int prec, const uint64_t* seeds,
-                          int M, const double* a, const double* b, pvsc_tuning* best, void* stream);
-
 /*
  * Spectral densities from KPM moments (Sec. 2.2: the DOS of Eq. DOS and the
  * momentum-resolved spectral function A(k, E) of Eq. ak), with the damping
@@ -563,6 +553,16 @@ int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* best, void* s
  * (the plain sweep).  The winner replaces the (R, prec) tuning entry; the
  * on-disk cache keys on the operation too. */
 int pvsc_autotune_op(pvsc_lattice* lat, int R, int prec, int op, pvsc_tuning* best, void* stream);
+
+/* Launch-shape autotuner of the batched KPM over the whole batch (the batched
+ * calls read the (R, prec) tuning entry of lats[0]): threads per block (128,
+ * 256), z-segment length of the work units (whole columns, 16 .. 64 planes)
+ * and blocks per SM (occupancy maximum, 1) are timed with CUDA events on the
+ * batch itself running M moments, and the fastest becomes that entry.
+ * Allocates and frees its own buffers; synchronises the stream.  Query
+ * pvsc_batched_work_bytes again afterwards (it depends on the shape). */
+int pvsc_autotune_batched(pvsc_lattice* const* lats, int n, int R, int prec, const uint64_t* seeds,
+                          int M, const double* a, const double* b, pvsc_tuning* best, void* stream);
 
 /* Neighbour table the stencil uses (debug/parity): for every site, 7 site
  * indices (TI: self, -x, +x, -y, +y, -z, +z) or, for graphene, per cell
