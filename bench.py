@@ -98,6 +98,8 @@ def parse():
     ap.add_argument("--launch", default=None,
                     help="JSON launch shape (threads, blocks_per_sm, zslab, vpt, tile_x, tile_y, kernel) "
                          "to use instead of autotuning, e.g. for profiling runs")
+    ap.add_argument("--q64-launch", default=None,
+                    help="JSON launch shape of the fixed-point (PVSC_Q64) sweep (its default otherwise)")
     return ap.parse_args()
 
 
@@ -745,6 +747,8 @@ def main():
         tuning = lat.get_tuning(R, pv.C64)
     else:
         tuning = None if args.no_autotune else lat.autotune(R, pv.C64)
+    if args.q64_launch:
+        lat.set_tuning(R, pv.Q64, **{k: v for k, v in json.loads(args.q64_launch).items() if k != "time_ms"})
     if args.sweeps_only:
         # one KPM call of this many sweeps (2 x sweeps moments) in the benchmark's kernel,
         # or in the fixed-point kernel with --q64
@@ -857,6 +861,7 @@ def main():
                         "q64_vs_c128_max_dmu": float(((muq - mu128).abs() / mu128[:, :1].abs()).max().item()),
                         "q64_bytes_per_lup": bq,
                         "q64_hbm_frac": round(bq * vq / peak, 4),
+                        "q64_launch": lat.get_tuning(R, pv.Q64) if args.q64_launch else "default",
                         "q64_note": "complex128-sized Q4.59 fixed-point vectors, exact integer stencil; "
                                     "call time includes the per-call Gershgorin check and conversion"})
         del wq

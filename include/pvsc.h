@@ -29,8 +29,9 @@
  *   fixed-point integers: each start vector is scaled by an exact power of two
  *   to 2-norm <= 1, values carry 59 fraction bits, stencil sums are exact
  *   integer additions and each update is rounded once at 2^-60; the dot
- *   products are exact 128-bit integer sums converted to fp64.  Moments agree
- *   with the fp64 path to ~1e-15.
+ *   products are exact integer sums converted to fp64.  Products are formed
+ *   exactly from 32 x 32 -> 64-bit limb products (pvsc_debug_fx_arith runs
+ *   them on given operands).  Moments agree with the fp64 path to ~1e-15.
  * R.  1, 2, 4, 8, 16, 32 or 64 vectors per block.
  * Memory.  Every vector, work buffer and output pointer is a DEVICE pointer
  *   owned by the caller, 16-byte aligned; the library owns only the lattice
@@ -536,7 +537,14 @@ typedef struct {
                   /* one item per thread); tile_x x tile_y = the half tile */
                   /* (16x8, 16x4, 8x4 for R = 4, 8, 16) selects rings one plane */
                   /* deeper on eight warps; zslab = z-chunk depth (0: chosen from */
-                  /* the grid size); vpt is ignored */
+                  /* the grid size); vpt is ignored. */
+                  /* PVSC_Q64 (KPM on TI lattices) takes kernels 0, 2, 3 (threads a */
+                  /* multiple of R, one vector per thread, no tile) and 7 for R = 2 .. 32 */
+                  /* (any Lx): the tiles, rings and variants of the complex64 layout */
+                  /* of 2R vectors (a fixed-point value is 16 bytes), one vector of one */
+                  /* site per item.  Untuned it runs kernel 7 on sixteen warps for */
+                  /* R = 2 .. 8, kernel 7 on eight for R = 16, 32, kernel 2 for R = 64 */
+                  /* and kernel 0 for R = 1. */
 } pvsc_tuning;
 
 /* Device error word of the shared-memory staged sweeps: *flag = 1 if a copy
@@ -581,6 +589,25 @@ int pvsc_debug_neighbours(const pvsc_lattice* lat, int64_t* nbr_dev, void* strea
  * col: HOST array of rowptr[D] int32 column indices, or NULL to size it
  * first.  D at most 2^24 (PVSC_ERR_ARG otherwise). */
 int pvsc_debug_export_pattern(const pvsc_lattice* lat, int64_t* rowptr, int32_t* col);
+
+/* Fixed-point arithmetic of the PVSC_Q64 sweeps (debug/parity): runs the
+ * device routines those sweeps use on caller-given 64-bit integers, so that
+ * they can be checked against exact integer arithmetic.
+ *   op 0: in holds n records (c1, x1, c2, x2); out[i] = floor((c1 x1 + c2 x2
+ *         + 2^59) / 2^60), the once-rounded Q3.60 x Q4.59 update of a value.
+ *         Valid for |c1|, |c2| <= 2^61, |x1| <= 2^59, |x2| <= 6 * 2^59 (the
+ *         coefficients, vector entries and neighbour combinations a sweep
+ *         meets under its scaling checks).
+ *   op 1: in holds n records (x_0 .. x_7, y_0 .. y_7) (the eight values of a
+ *         site block of two vectors); out[0..3] = the exact sums over all
+ *         records of x_k^2 and of y_k x_k, each as a 128-bit two's-complement
+ *         (hi, lo) pair.  Valid for |x_k|, |y_k| <= 2^59 with sum x_k^2 and
+ *         sum y_k^2 <= 2^118 (two vectors of 2-norm <= 1).  One thread:
+ *         meant for small n.
+ * Outside those ranges the results are unspecified (no fault).  in, out:
+ * DEVICE int64 arrays (in may be NULL when n = 0); n >= 0.  Asynchronous on
+ * stream. */
+int pvsc_debug_fx_arith(int op, const int64_t* in, int64_t n, int64_t* out, void* stream);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* pvsc_last_error(void);

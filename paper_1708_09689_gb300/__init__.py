@@ -102,6 +102,7 @@ _SIGNATURES = {
     "pvsc_cheb_propagate_adjoint": (_i, [_vp, _i, _i, _vp, _d, _i, _i, _d, _d, _d, _vp, _vp, _vp, _sz, _vp]),
     "pvsc_propagate_adjoint_work_bytes": (_sz, [_vp, _i, _i, _d, _d]),
     "pvsc_debug_export_pattern": (_i, [_vp, _vp, _vp]),
+    "pvsc_debug_fx_arith": (_i, [_i, _vp, ctypes.c_int64, _vp, _vp]),
     "pvsc_kpm_sweeps": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _d, _d, _vp, _i, _vp, _sz, _vp]),
     "pvsc_kpm_moments_batched": (_i, [ctypes.POINTER(_vp), _i, _i, _i, ctypes.POINTER(_u64), _i,
                                       _dp, _dp, _vp, _vp, _sz, _vp]),
@@ -591,6 +592,23 @@ def device_error(clear: bool = True) -> int:
     flag = ctypes.c_int(0)
     _check(_lib.pvsc_device_error(ctypes.byref(flag), int(bool(clear))))
     return int(flag.value)
+
+
+def debug_fx_arith(op: int, values, stream=None):
+    """The fixed-point sweep arithmetic on given int64 operands (pvsc_debug_fx_arith).
+    op 0: values (n, 4) = (c1, x1, c2, x2) -> (n,) rounded updates; op 1: values
+    (n, 16) = (x_0..7, y_0..7) -> (4,) exact sums (hi, lo) of x^2 and y x.
+    values: a CUDA int64 tensor."""
+    v = values.contiguous()
+    if v.dtype != torch.int64 or not v.is_cuda:
+        raise PvscError(PVSC_ERR_ARG, "values must be a CUDA int64 tensor")
+    width = 4 if op == 0 else 16
+    if v.dim() != 2 or v.shape[1] != width:
+        raise PvscError(PVSC_ERR_ARG, f"values must have shape (n, {width})")
+    n = v.shape[0]
+    out = torch.zeros((n if op == 0 else 4,), dtype=torch.int64, device=v.device)
+    _check(_lib.pvsc_debug_fx_arith(int(op), _ptr(v) if n else None, n, _ptr(out), _stream(stream)))
+    return out
 
 
 def set_wait_limit(spins: int):

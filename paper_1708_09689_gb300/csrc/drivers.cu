@@ -967,14 +967,24 @@ int pvsc_device_error(int* flag, int clear) {
   return PVSC_OK;
 }
 
-// Launch shapes of the fixed-point KPM sweep: kernel 0, 2 or 3, one vector per thread.
+// Launch shapes of the fixed-point KPM sweep: kernel 0, 2 or 3, one vector per
+// thread; or kernel 7, the TMA-staged tiles of the complex64 layout of 2R vectors.
 static int check_q64_tuning(const pvsc_lattice* lat, int R, const pvsc_tuning* t) {
   if (int rc = check_lattice(lat)) return rc;
   if (!valid_R(R)) return set_error(PVSC_ERR_ARG, "R = %d: must be 1, 2, 4, 8, 16, 32 or 64", R);
   if (lat->g.model != PVSC_TI) return set_error(PVSC_ERR_UNSUPPORTED, "PVSC_Q64 is for the TI lattice only");
   if (!t) return PVSC_OK;
+  if (t->kernel == kKernelTma) {
+    if (!tma_fx_possible(lat, R))
+      return set_error(PVSC_ERR_ARG, "PVSC_Q64 kernel 7 (TMA-staged tiles) needs R = 2 .. 32");
+    if (!tma_tile_valid(2 * R, t->tile_x, t->tile_y))
+      return set_error(PVSC_ERR_ARG, "PVSC_Q64 kernel 7 takes no tile other than the two of R = %d (%dx%d given)",
+                       R, t->tile_x, t->tile_y);
+    if (t->blocks_per_sm < 0 || t->zslab < 0) return set_error(PVSC_ERR_ARG, "negative tuning value");
+    return PVSC_OK;
+  }
   if (t->kernel != 0 && t->kernel != 2 && t->kernel != 3)
-    return set_error(PVSC_ERR_ARG, "PVSC_Q64 kernels are 0, 2 and 3");
+    return set_error(PVSC_ERR_ARG, "PVSC_Q64 kernels are 0, 2, 3 and 7");
   if (t->vpt > 1 || t->tile_x || t->tile_y)
     return set_error(PVSC_ERR_ARG, "PVSC_Q64 sweeps take one vector per thread and no staged tile");
   if (t->threads < 32 || t->threads > kMaxThreads || t->threads % 32 || t->threads % R)

@@ -1,0 +1,134 @@
+// Integer arithmetic of the fixed-point (PVSC_Q64) KPM sweeps on 32-bit limbs.
+//
+// Values are Q4.59 vector entries and Q3.60 coefficients held in 64-bit
+// integers (sweep_fx.cu gives the format).  Every 64 x 64-bit product the
+// sweep needs is assembled from 32 x 32 -> 64-bit products (one wide
+// multiply-add each) of the limbs v = v_h 2^31 + v_l, v_l in [0, 2^31),
+// v_h = v >> 31, with the partial sums kept exact in 64 bits by the bounds
+// below; no 128-bit product is ever formed.
+//
+// Bounds (they follow from the checks the driver makes before a fixed-point
+// run: [b - a, b + a] holds the Gershgorin interval, a >= |t| / 2, and the
+// start block has 2-norm <= 1 per vector):
+//   * a vector entry |x| <= 1 (||w_k|| <= ||w_0|| <= 1 since ||T_k(H~)|| <= 1),
+//     so |x_h| <= 2^28;
+//   * a neighbour combination T of the stencil (a signed sum of at most twelve
+//     entries of one vector, or six copies of one entry on a one-site periodic
+//     axis) has |T| <= 6, so |T_h| < 1.5 2^30;
+//   * a coefficient (d_+-, possibly doubled for alpha = 2/a, and kt) has
+//     |c| <= 2, so |c_h| <= 2^30.
+// With these, the partial sums in fx_mul2 and fx_dot_item stay below 2^63 in
+// magnitude (worked out at each sum).
+#pragma once
+
+namespace pvsc {
+
+using i64 = long long;
+using u64 = unsigned long long;
+
+constexpr int kFxVal = 59;   // fraction bits of vector values
+constexpr int kFxCoef = 60;  // fraction bits of coefficients
+
+struct FxLimbs {
+  int h;  // v >> 31 (arithmetic)
+  int l;  // v mod 2^31, in [0, 2^31)
+};
+
+__device__ __forceinline__ FxLimbs fx_split(i64 v) {
+  return FxLimbs{(int)(v >> 31), (int)(v & 0x7fffffff)};
+}
+
+__device__ __forceinline__ i64 wmul32(int a, int b) { return (i64)a * (i64)b; }
+
+// round((c1 x1 + c2 x2) 2^-60), half up: Q3.60 x Q4.59 -> Q4.59.
+// With P = c1 x1 + c2 x2 + 2^59 = H 2^62 + M 2^31 + L:
+//   H = c1_h x1_h + c2_h x2_h               (|H| < 2^61)
+//   M = c1_h x1_l + c1_l x1_h + c2_h x2_l + c2_l x2_h + 2^28
+//       (|M| <= 2^61 + 2^59 + 2^61 + 1.5 2^61 + 2^28 < 2^63)
+//   L = c1_l x1_l + c2_l x2_l               (0 <= L < 2^63)
+// and, with N = M + floor(L / 2^31), floor(P / 2^60) = 4 H + floor(N / 2^29)
+// (the remainder L mod 2^31 < 2^31 cannot carry across a multiple of 2^60).
+__device__ __forceinline__ i64 fx_mul2(FxLimbs c1, FxLimbs x1, FxLimbs c2, FxLimbs x2) {
+  const i64 H = wmul32(c1.h, x1.h) + wmul32(c2.h, x2.h);
+  i64 M = (i64)1 << (kFxVal - 31) ;
+  M += wmul32(c1.h, x1.l);
+  M += wmul32(c1.l, x1.h);
+  M += wmul32(c2.h, x2.l);
+  M += wmul32(c2.l, x2.h);
+  const i64 L = wmul32(c1.l, x1.l) + wmul32(c2.l, x2.l);
+  const i64 N = M + (L >> 31);
+  return H * 4 + (N >> 29);
+}
+
+// An exact dot-product sum: V = u 2^62 + (hi 2^64 + lo) (two's complement,
+// u and hi signed).  u collects the products of the high limbs, whose sum over
+// a vector is bounded by its norm, so it needs no carry handling.
+struct FxAcc {
+  i64 u;
+  u64 lo;
+  i64 hi;
+};
+
+__device__ __forceinline__ void fx_acc_zero(FxAcc& a) {
+  a.u = 0;
+  a.lo = 0;
+  a.hi = 0;
+}
+
+// (hi, lo) += v (unsigned 64-bit)
+__device__ __forceinline__ void fx_acc_add(FxAcc& a, u64 v) {
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.s64 %1, %1, 0;" : "+l"(a.lo), "+l"(a.hi) : "l"(v));
+}
+
+// (hi, lo) += v 2^s for a signed v and 0 < s < 64
+template <int S>
+__device__ __forceinline__ void fx_acc_add_shl(FxAcc& a, i64 v) {
+  const u64 l = (u64)v << S;
+  const i64 h = v >> (64 - S);
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.s64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(l), "l"(h));
+}
+
+// The value of an accumulator times `unit` (the fp64 weight of one unit),
+// rounded once per term: the high-limb part u 2^62 is folded in exactly first.
+__device__ __forceinline__ double fx_acc_value(FxAcc a, double unit) {
+  fx_acc_add_shl<62>(a, a.u);
+  return fma((double)a.hi, 0x1p64, (double)a.lo) * unit;
+}
+
+// The dot products of one site block (four orbitals, real and imaginary
+// parts: eight entries) added to the accumulators:
+//   xx += sum x^2   = sum x_h^2 2^62 + (sum x_h x_l) 2^32 + sum x_l^2
+//   xy += sum y x   = sum y_h x_h 2^62 + (sum y_h x_l + y_l x_h) 2^31 + sum y_l x_l
+// Per block: |sum x_h x_l| <= 2^31 sum |x_h| <= 2^31 sqrt(8) 2^28 < 2^62;
+// |sum (y_h x_l + y_l x_h)| <= 2^31 (sum |y_h| + sum |x_h|) < 2^63; the low
+// products (< 2^62 each) are summed four at a time as unsigned numbers.
+__device__ __forceinline__ void fx_dot_item(const FxLimbs (&x)[8], const FxLimbs (&y)[8], FxAcc& xx, FxAcc& xy) {
+  i64 ah = 0, am = 0, bh = 0, bm = 0;
+  u64 al0 = 0, al1 = 0, bl0 = 0, bl1 = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const unsigned xl = (unsigned)x[k].l, yl = (unsigned)y[k].l;
+    ah += wmul32(x[k].h, x[k].h);
+    am += wmul32(x[k].h, x[k].l);
+    bh += wmul32(y[k].h, x[k].h);
+    bm += wmul32(y[k].h, x[k].l);
+    bm += wmul32(y[k].l, x[k].h);
+    if (k < 4) {
+      al0 += (u64)xl * xl;
+      bl0 += (u64)yl * xl;
+    } else {
+      al1 += (u64)xl * xl;
+      bl1 += (u64)yl * xl;
+    }
+  }
+  xx.u += ah;
+  fx_acc_add_shl<32>(xx, am);
+  fx_acc_add(xx, al0);
+  fx_acc_add(xx, al1);
+  xy.u += bh;
+  fx_acc_add_shl<31>(xy, bm);
+  fx_acc_add(xy, bl0);
+  fx_acc_add(xy, bl1);
+}
+
+}  // namespace pvsc

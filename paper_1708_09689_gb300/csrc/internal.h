@@ -51,6 +51,7 @@ constexpr int kModelWSM = 8;         // Weyl semimetal flat cell sweep
 constexpr int kModelWSMMarch = 9;    // Weyl semimetal z-marching cell sweep
 constexpr int kModelGrapheneQD = 10; // graphene sweep with the regenerated quantum-dot array
 constexpr int kModelTIXMarch = 11;   // TI sweep marching along x (tuning kernel 6)
+constexpr int kModelTIFx = 12;       // TI KPM sweep on fixed-point (PVSC_Q64) vectors
 constexpr int kAsyncDepth = 1;
 constexpr int kAsyncDeepDepth = 3;
 // ring: (depth + 1) slots x buffers x 4 granules of 16 bytes per thread
@@ -99,6 +100,10 @@ constexpr int kKernelTma = 7;
 bool tma_sweep_possible(const pvsc_lattice* lat, int R, int prec);
 int launch_sweep_tma(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st);
 int tma_error(int clear, int* flag);
+// fixed-point (PVSC_Q64) KPM sweep on TMA-staged tiles (sweep_tma_fx.cu)
+bool tma_fx_possible(const pvsc_lattice* lat, int R);
+int launch_sweep_tma_fx(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, cudaStream_t st);
+int tma_error_fx(int clear, int* flag);
 bool tma_tile_valid(int R, int tile_x, int tile_y);  // (0, 0) or one of the two tiles of this R
 bool tma_tile_deep(int R, int tile_y);
 int launch_kpm2_sweep(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, cudaStream_t st);

@@ -12,51 +12,18 @@
 // an exact power-of-two scaling 2^-e_r per vector r chosen so that the start
 // vector has 2-norm <= 1).  With (a, b) from an interval that holds the
 // spectrum, ||T_k(H~)|| <= 1, so every |w_k| <= 1, the stencil's neighbour
-// sums are <= 12 and the three-term update stays < 16 (no overflow).  The
-// coefficients d_o = (V_n - b)/a +- m/a and kt = -t/(2a) of the sweep are
-// Q3.60; every output is d x + kt T summed exactly in 128 bits and rounded
-// once (2^-60, round half up), then - y_in added exactly.  The dot products
-// are exact 128-bit sums of 128-bit products per thread, converted to fp64
-// once per column segment and reduced in fp64 in a fixed order as in the
-// other sweeps.
+// combinations are <= 6 and the three-term update stays < 16 (no overflow).
+// The coefficients d_o = (V_n - b)/a +- m/a and kt = -t/(2a) of the sweep are
+// Q3.60; every output is d x + kt T, formed exactly and rounded once (2^-60,
+// round half up), then - y_in added exactly.  The dot products are exact sums
+// of the exact products per thread, converted to fp64 once per column segment
+// and reduced in fp64 in a fixed order as in the other sweeps.  Products and
+// sums are assembled from 32 x 32 -> 64-bit limb products (fx_arith.cuh).
 #include "internal.h"
+#include "fx_arith.cuh"
 #include "sweep.cuh"
 
 namespace pvsc {
-
-using i64 = long long;
-
-constexpr int kFxVal = 59;   // fraction bits of vector values
-constexpr int kFxCoef = 60;  // fraction bits of coefficients
-
-// 128-bit two's-complement values as (hi, lo) pairs, built from the signed
-// 64 x 64 -> 128 product (mul.hi.s64 and the wrapping low product).
-struct W128 {
-  i64 hi;
-  unsigned long long lo;
-};
-
-__device__ __forceinline__ W128 wmul(i64 a, i64 b) {
-  return W128{__mul64hi(a, b), (unsigned long long)a * (unsigned long long)b};
-}
-
-__device__ __forceinline__ void wadd(W128& acc, const W128& v) {
-  const unsigned long long lo = acc.lo + v.lo;
-  acc.hi += v.hi + (lo < acc.lo ? 1 : 0);
-  acc.lo = lo;
-}
-
-// round((c1 x1 + c2 x2) 2^-60): Q3.60 x Q4.59 -> Q4.59 (round half up)
-__device__ __forceinline__ i64 fx_mul2(i64 c1, i64 x1, i64 c2, i64 x2) {
-  W128 P = wmul(c1, x1);
-  wadd(P, wmul(c2, x2));
-  wadd(P, W128{0, 1ull << (kFxCoef - 1)});
-  return (i64)(((unsigned long long)P.hi << (64 - kFxCoef)) | (P.lo >> kFxCoef));
-}
-
-__device__ __forceinline__ double w128_to_double(const W128& v) {
-  return fma((double)v.hi, 0x1p64, (double)v.lo);
-}
 
 // One KPM sweep on fixed-point vectors, z-marching as the floating-point
 // sweeps (ti_march): y = alpha (H - b) x, minus y_in when given (gamma = -1),
@@ -76,7 +43,7 @@ __global__ void __launch_bounds__(256) ti_sweep_fx(const __grid_constant__ Sweep
   const i64* Yin = static_cast<const i64*>(p.yin);
   i64* Yout = static_cast<i64*>(p.yout);
   const longlong2* __restrict__ dfx = static_cast<const longlong2*>(p.fx_d);
-  const i64 kt = p.fx_kt;
+  const FxLimbs kt = fx_split(p.fx_kt);
   const i64 dmul = p.fx_dshift ? 2 : 1;
   const double vs = p.vscale[rc];
   double dd[kNumDots][1];
@@ -92,7 +59,9 @@ __global__ void __launch_bounds__(256) ti_sweep_fx(const __grid_constant__ Sweep
     const int64_t tid = bx * blockDim.x + threadIdx.x;
     if (tid >= ncolthr) continue;
     const int64_t z0 = bz * zs, z1 = min(z0 + (int64_t)zs, Lz);
-    W128 xx{0, 0}, xy{0, 0};
+    FxAcc xx, xy;
+    fx_acc_zero(xx);
+    fx_acc_zero(xy);
     ti_march<i64, 1, true, DEPTH, NBUF>(
         p.g, X, Yin, R, rc, tid >> cshift, z0, z1, ring,
         [&](int64_t s) { return __ldg(dfx + s); },
@@ -101,13 +70,13 @@ __global__ void __launch_bounds__(256) ti_sweep_fx(const __grid_constant__ Sweep
             const Blk<i64, 1>* yi, Blk<i64, 1>& yn) {
           Blk<i64, 1> S, D;
           ti_axes(xm, xp, ax, bx, ay, by, S, D);
-          const i64 dp = dv.x * dmul, dm = dv.y * dmul;
+          const FxLimbs dp = fx_split(dv.x * dmul), dm = fx_split(dv.y * dmul);
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
-            const i64 d = (o & 1) ? dm : dp;
+            const FxLimbs d = (o & 1) ? dm : dp;
             const cplx<i64> T = (o & 1) ? csub(D.v[o][0], S.v[o][0]) : cadd(D.v[o][0], S.v[o][0]);
-            i64 re = fx_mul2(d, xc.v[o][0].re, kt, T.re);
-            i64 im = fx_mul2(d, xc.v[o][0].im, kt, T.im);
+            i64 re = fx_mul2(d, fx_split(xc.v[o][0].re), kt, fx_split(T.re));
+            i64 im = fx_mul2(d, fx_split(xc.v[o][0].im), kt, fx_split(T.im));
             if (yi != nullptr) {
               re -= yi->v[o][0].re;
               im -= yi->v[o][0].im;
@@ -117,17 +86,18 @@ __global__ void __launch_bounds__(256) ti_sweep_fx(const __grid_constant__ Sweep
         },
         [&](int64_t s, const Blk<i64, 1>& xc, Blk<i64, 1>& yn) {
           store_blk<i64, 1>(Yout, s, R, rc, yn);
+          FxLimbs xs[8], ys[8];
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
-            const cplx<i64> a = xc.v[o][0], b = yn.v[o][0];
-            wadd(xx, wmul(a.re, a.re));
-            wadd(xx, wmul(a.im, a.im));
-            wadd(xy, wmul(b.re, a.re));
-            wadd(xy, wmul(b.im, a.im));
+            xs[2 * o] = fx_split(xc.v[o][0].re);
+            xs[2 * o + 1] = fx_split(xc.v[o][0].im);
+            ys[2 * o] = fx_split(yn.v[o][0].re);
+            ys[2 * o + 1] = fx_split(yn.v[o][0].im);
           }
+          fx_dot_item(xs, ys, xx, xy);
         });
-    dd[0][0] += w128_to_double(xx) * vs;
-    dd[1][0] += w128_to_double(xy) * vs;
+    dd[0][0] += fx_acc_value(xx, vs);
+    dd[1][0] += fx_acc_value(xy, vs);
   }
   reduce_dots<1>(p, dd);
 }
@@ -241,8 +211,16 @@ static void* fx_kernel(int kernel) {
 
 int launch_sweep_fx(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, bool tuned,
                     cudaStream_t st) {
-  // untuned: the six-block ring for R >= 2, plain loads for R = 1 (measured)
+  // untuned (measured on the 256 x 256 x 64 slab): the TMA-staged tiles, on 16
+  // warps for R = 2 .. 8 (0.63 of the HBM roof at R = 4 and 8, against 0.49 for
+  // the cp.async ring); plain loads for R = 1 and the six-block ring for R = 64
+  if (!tuned && tma_fx_possible(lat, p.R)) {
+    LaunchShape d;
+    d.threads = p.R <= 8 ? 512 : 256;
+    return launch_sweep_tma_fx(lat, p, d, st);
+  }
   const int kernel = tuned ? sh.kernel : (p.R >= 2 ? 2 : 0);
+  if (kernel == kKernelTma) return launch_sweep_tma_fx(lat, p, sh, st);
   int threads = tuned ? sh.threads : 128;
   if (threads < 32 || threads > kMaxThreads || threads % 32 || threads % p.R) threads = 128;
   void* fn = fx_kernel(kernel);
@@ -273,4 +251,61 @@ int launch_sweep_fx(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, bo
   return PVSC_OK;
 }
 
+// ---------------------------------------------------------------- arithmetic checks
+// The limb routines of fx_arith.cuh on caller-given operands (pvsc_debug_fx_arith).
+__global__ void fx_debug_mul2(const i64* __restrict__ in, int64_t n, i64* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const i64* r = in + 4 * i;
+    out[i] = fx_mul2(fx_split(r[0]), fx_split(r[1]), fx_split(r[2]), fx_split(r[3]));
+  }
+}
+
+// one thread: the exact sums over all records, as the sweep accumulates them
+__global__ void fx_debug_dots(const i64* __restrict__ in, int64_t n, i64* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  FxAcc xx, xy;
+  fx_acc_zero(xx);
+  fx_acc_zero(xy);
+  for (int64_t i = 0; i < n; ++i) {
+    FxLimbs xs[8], ys[8];
+    for (int k = 0; k < 8; ++k) {
+      xs[k] = fx_split(in[16 * i + k]);
+      ys[k] = fx_split(in[16 * i + 8 + k]);
+    }
+    fx_dot_item(xs, ys, xx, xy);
+  }
+  fx_acc_add_shl<62>(xx, xx.u);
+  fx_acc_add_shl<62>(xy, xy.u);
+  out[0] = xx.hi;
+  out[1] = (i64)xx.lo;
+  out[2] = xy.hi;
+  out[3] = (i64)xy.lo;
+}
+
 }  // namespace pvsc
+
+using namespace pvsc;
+
+extern "C" {
+
+int pvsc_debug_fx_arith(int op, const int64_t* in, int64_t n, int64_t* out, void* stream) {
+  if (op != 0 && op != 1) return set_error(PVSC_ERR_ARG, "op = %d: must be 0 (update) or 1 (dot sums)", op);
+  if (n < 0) return set_error(PVSC_ERR_ARG, "n = %lld < 0", (long long)n);
+  if (int rc = check_ptr(out, "out")) return rc;
+  if (n > 0)
+    if (int rc = check_ptr(in, "in")) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const i64* src = reinterpret_cast<const i64*>(in);
+  i64* dst = reinterpret_cast<i64*>(out);
+  if (op == 0) {
+    if (n == 0) return PVSC_OK;
+    const int64_t blocks = (n + 255) / 256;
+    fx_debug_mul2<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(src, n, dst);
+  } else {
+    fx_debug_dots<<<1, 32, 0, st>>>(src, n, dst);
+  }
+  PVSC_CUDA_TRY(cudaGetLastError());
+  return PVSC_OK;
+}
+
+}  // extern "C"

@@ -73,10 +73,11 @@ int launch_sweep_tma(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchSh
 }
 
 int tma_error(int clear, int* flag) {
-  int a = 0, b = 0;
+  int a = 0, b = 0, c = 0;
   if (int rc = tma_error_ti(clear, &a)) return rc;
   if (int rc = tma_error_wide(clear, &b)) return rc;
-  *flag = (a || b) ? 1 : 0;
+  if (int rc = tma_error_fx(clear, &c)) return rc;
+  *flag = (a || b || c) ? 1 : 0;
   return PVSC_OK;
 }
 

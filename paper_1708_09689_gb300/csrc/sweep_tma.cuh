@@ -42,7 +42,9 @@
 
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
+#include "fx_arith.cuh"
 #include "internal.h"
 #include "sweep_bulk.cuh"
 
@@ -72,7 +74,10 @@ template <> struct TmaTile<64, true> { static constexpr int TX = 4, TY = 2, NXS 
 
 constexpr int round_up_1k(int b) { return (b + 1023) & ~1023; }
 
-template <int R, bool DEEP, int NW>
+// VF: 4-byte words of potential data per tile point that a y stage holds room
+// for (two fp32 potentials of a Weyl cell; the fixed-point sweep's (d+, d-) pair
+// of 64-bit coefficients takes four).
+template <int R, bool DEEP, int NW, int VF = 2>
 struct TmaLayout {
   static constexpr int NWARPS = NW;  // warps per block (8 or 16), one block per SM
   static constexpr int TX = TmaTile<R, DEEP>::TX, TY = TmaTile<R, DEEP>::TY;
@@ -90,7 +95,7 @@ struct TmaLayout {
   static constexpr int X_BYTES = INT_B + 2 * XS_B + 2 * YS_B;  // copied per x plane
   static constexpr int XSTAGE = round_up_1k(X_BYTES);
   static constexpr int V_B = TX * TY * 4;                  // fp32 potential per tile point
-  static constexpr int YSTAGE = INT_B + round_up_1k(2 * V_B);  // room for two (Weyl cells)
+  static constexpr int YSTAGE = INT_B + round_up_1k(VF * V_B);
   static constexpr int NXS = TmaTile<R, DEEP>::NXS, NYS = TmaTile<R, DEEP>::NYS;
   static constexpr int BAR_OFF = NXS * XSTAGE + NYS * YSTAGE;
   static constexpr int DOT_OFF = BAR_OFF + 128;  // fp64 dot partials [warp][dot][v][c]
@@ -212,16 +217,36 @@ __device__ __forceinline__ void tma_lds_blk(const unsigned char* buf, uint32_t B
   }
 }
 
+// The same four orbitals of a fixed-point block: a site of R/2 vectors of
+// 16-byte (re, im) 64-bit pairs has the byte layout of a complex64 site of R
+// vectors, and vector c is the 16-byte chunk c of every orbital.
+template <int R>
+__device__ __forceinline__ void tma_lds_blk(const unsigned char* buf, uint32_t B, Blk<long long, 1>& b) {
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const int ao = o * 8 * R;
+    const int K1 = (ao >> 4) & 7, K2 = (ao >> 7) & 7;
+    const longlong2 v =
+        *reinterpret_cast<const longlong2*>(buf + ((B ^ (uint32_t)((K1 ^ K2) << 4)) + (uint32_t)(ao & ~127)));
+    b.v[o][0] = {v.x, v.y};
+  }
+}
+
 // MODEL 1: TI sites; MODEL 3: Weyl-semimetal cells of two x-adjacent sites
 // (Eq. TB_H_wsm), whose four components form the same block as a TI site, with
-// the cell update of the Weyl sweeps and two potentials per cell.
+// the cell update of the Weyl sweeps and two potentials per cell;
+// kModelTIFx: the TI KPM sweep of sweep_fx.cu on fixed-point vectors (R/2
+// vectors in the byte layout of R complex64 vectors, one vector per thread,
+// the per-site coefficient pair in place of the potential, exact dot sums).
 template <int R, bool DEEP, int NW, int FEAT, int MODEL>
 __global__ void __launch_bounds__(32 * NW, 1)
     ti_sweep_tma(const __grid_constant__ Sweep p, const __grid_constant__ TmaMaps m) {
-  using L = TmaLayout<R, DEEP, NW>;
-  constexpr int NCW = NW, IPT = L::IPT, TX = L::TX, TY = L::TY;
   constexpr bool WSM = MODEL == 3;
-  constexpr int VPC = WSM ? 2 : 1;  // potentials (sites) per tile point
+  constexpr bool FX = MODEL == kModelTIFx;
+  constexpr int VPC = WSM ? 2 : 1;               // sites per tile point
+  constexpr int VF = WSM ? 2 : (FX ? 4 : 1);     // 4-byte words of potential data per tile point
+  using L = TmaLayout<R, DEEP, NW, FX ? 4 : 2>;
+  constexpr int NCW = NW, IPT = L::IPT, TX = L::TX, TY = L::TY;
   extern __shared__ unsigned char smem_raw[];
   __shared__ int s_abort;
   __shared__ unsigned s_cnt[L::NXS + L::NYS];  // releases per slot (x slots, then y slots)
@@ -308,7 +333,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
     tma_load_5d(dst + L::OFF_YP, &m.ys, 0, 0, x0, hyp, zx, &full_x[slot]);
     atomicMax(&s_issued[0], k + 1);
   };
-  const unsigned ybytes = (m.has_yin ? L::INT_B : 0) + (m.v_tma ? VPC * L::V_B : 0);
+  const unsigned ybytes = (m.has_yin ? L::INT_B : 0) + (m.v_tma ? VF * L::V_B : 0);
   auto issue_y = [&](int lu, int j, uint32_t k) {
     const uint2 e = tab[lu];
     const int x0 = (int)(e.x & 0xffffu), y0 = (int)(e.x >> 16), z0 = (int)(e.y & 0xffffu);
@@ -317,7 +342,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
     if (ybytes) {
       mbar_arrive_expect_tx(&full_y[slot], ybytes);
       if (m.has_yin) tma_load_5d(dst, &m.yi, 0, 0, x0, y0, z0 + j, &full_y[slot]);
-      if (m.v_tma) tma_load_3d(dst + L::INT_B, &m.v, VPC * x0, y0, z0 + j, &full_y[slot]);
+      if (m.v_tma) tma_load_3d(dst + L::INT_B, &m.v, VF * x0, y0, z0 + j, &full_y[slot]);
     } else {
       mbar_arrive(&full_y[slot]);
     }
@@ -357,9 +382,18 @@ __global__ void __launch_bounds__(32 * NW, 1)
 
   const int c = lane % L::CPS;
   const int q = lane / L::CPS;
-  const VecCoef<float, 2> cf = load_coef<float, 2>(p, c);
+  VecCoef<float, 2> cf;
+  if constexpr (!FX) cf = load_coef<float, 2>(p, c);
   DotAcc<float, 2> dacc;  // compensated fp32 sums; their fp64 part lives in shared memory
   dacc.init();
+  // fixed point: exact per-unit dot sums of this thread's vector c, the
+  // coefficient limbs and the fp64 value of one dot unit
+  FxAcc fxx, fxy;
+  fx_acc_zero(fxx);
+  fx_acc_zero(fxy);
+  const FxLimbs fkt = fx_split(FX ? p.fx_kt : 0);
+  const long long fdmul = p.fx_dshift ? 2 : 1;
+  const double fvs = FX ? p.vscale[c] : 0.0;
   double* wdots = reinterpret_cast<double*>(base + L::DOT_OFF) + warp * kNumDots * 2 * L::CPS;
   if constexpr (has_dots(FEAT)) {
     if (lane < L::CPS)
@@ -367,6 +401,20 @@ __global__ void __launch_bounds__(32 * NW, 1)
   }
   // flush a unit's compensated fp32 sums into this warp's fp64 partials (fixed order)
   auto flush_dots = [&]() {
+    if constexpr (FX) {
+      double t0 = fx_acc_value(fxx, fvs), t1 = fx_acc_value(fxy, fvs);
+      fx_acc_zero(fxx);
+      fx_acc_zero(fxy);
+      for (int off = 16; off >= L::CPS; off >>= 1) {
+        t0 += __shfl_xor_sync(0xffffffffu, t0, off);
+        t1 += __shfl_xor_sync(0xffffffffu, t1, off);
+      }
+      if (lane < L::CPS) {
+        wdots[lane] += t0;
+        wdots[L::CPS + lane] += t1;
+      }
+      return;
+    }
 #pragma unroll
     for (int d = 0; d < kNumDots; ++d)
 #pragma unroll
@@ -378,7 +426,8 @@ __global__ void __launch_bounds__(32 * NW, 1)
         if (lane < L::CPS) wdots[(d * 2 + v) * L::CPS + lane] += t;
       }
   };
-  Blk<float, 2> xmr[IPT];
+  using XBlk = typename std::conditional<FX, Blk<long long, 1>, Blk<float, 2>>::type;
+  XBlk xmr[IPT];
   uint32_t kx = 0, ky = 0;
   const unsigned char* ybase = base + L::NXS * L::XSTAGE;
   bool alive = true;
@@ -401,7 +450,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
       Bxp[i] = tma_swz<R>(lx + 1 < TXe ? (li + 1) * SB : L::OFF_XP + ly * SB, c);
       Bym[i] = tma_swz<R>(ly > 0 ? (li - TX) * SB : L::OFF_YM + lx * SB, c);
       Byp[i] = tma_swz<R>(ly + 1 < TYe ? (li + TX) * SB : L::OFF_YP + lx * SB, c);
-      Vo[i] = L::INT_B + 4 * VPC * li;
+      Vo[i] = L::INT_B + 4 * VF * li;
       col[i] = (int64_t)(x0 + lx) + (int64_t)Lx * (y0 + ly);
     }
     // plane z0 - 1: x(z-1) of every site into registers
@@ -435,54 +484,102 @@ __global__ void __launch_bounds__(32 * NW, 1)
       for (int i = 0; i < IPT; ++i) {
         if (!ok[i]) continue;
         const int64_t s = col[i] + plane * z;
-        if constexpr (WSM) {
-          // the Weyl cell update of the Weyl sweeps, on the cell blocks around the cell
-          Blk<float, 2> xp, ax, bx, ay, by, xc, yi, yn;
-          tma_lds_blk<R>(s1, Bc[i], xp);
-          tma_lds_blk<R>(s0, Bxm[i], ax);
-          tma_lds_blk<R>(s0, Bxp[i], bx);
-          tma_lds_blk<R>(s0, Bym[i], ay);
-          tma_lds_blk<R>(s0, Byp[i], by);
+        if constexpr (FX) {
+          // the fixed-point update of sweep_fx.cu: y = d x + kt T (- y_in), exact
+          // with one rounding, then the exact dot sums of the site
+          Blk<long long, 1> S, D, yn;
+          {
+            Blk<long long, 1> xp;
+            tma_lds_blk<R>(s1, Bc[i], xp);
+            axis_z_init(xmr[i], xp, S, D);
+          }
+          {
+            Blk<long long, 1> ax, bx;
+            tma_lds_blk<R>(s0, Bxm[i], ax);
+            tma_lds_blk<R>(s0, Bxp[i], bx);
+            axis_x_add(ax, bx, S, D);
+          }
+          {
+            Blk<long long, 1> ay, by;
+            tma_lds_blk<R>(s0, Bym[i], ay);
+            tma_lds_blk<R>(s0, Byp[i], by);
+            axis_y_add(ay, by, S, D);
+          }
+          Blk<long long, 1> xc, yi;
           tma_lds_blk<R>(s0, Bc[i], xc);
           if (m.has_yin) tma_lds_blk<R>(sy, Bc[i], yi);
-          const float V0 = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i])
-                                   : site_potential_t<float>(g, 2 * s);
-          const float V1 = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i] + 4)
-                                   : site_potential_t<float>(g, 2 * s + 1);
-          wsm_cell_update(cf, V0, V1, xmr[i], xc, xp, ax, bx, ay, by, m.has_yin ? &yi : nullptr, yn);
-          const int64_t sites[4] = {2 * s, 2 * s, 2 * s + 1, 2 * s + 1};
+          const longlong2 dv = *reinterpret_cast<const longlong2*>(sy + Vo[i]);
+          const FxLimbs dp = fx_split(dv.x * fdmul), dm = fx_split(dv.y * fdmul);
+          FxLimbs xs[8], ys[8];
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            const FxLimbs d = (o & 1) ? dm : dp;
+            const cplx<long long> T = (o & 1) ? csub(D.v[o][0], S.v[o][0]) : cadd(D.v[o][0], S.v[o][0]);
+            xs[2 * o] = fx_split(xc.v[o][0].re);
+            xs[2 * o + 1] = fx_split(xc.v[o][0].im);
+            long long re = fx_mul2(d, xs[2 * o], fkt, fx_split(T.re));
+            long long im = fx_mul2(d, xs[2 * o + 1], fkt, fx_split(T.im));
+            if (m.has_yin) {
+              re -= yi.v[o][0].re;
+              im -= yi.v[o][0].im;
+            }
+            yn.v[o][0] = {re, im};
+            ys[2 * o] = fx_split(re);
+            ys[2 * o + 1] = fx_split(im);
+          }
+          store_blk<long long, 1>(static_cast<long long*>(p.yout), s, R / 2, c, yn);
+          fx_dot_item(xs, ys, fxx, fxy);
+          xmr[i] = xc;
+        } else {
+          if constexpr (WSM) {
+            // the Weyl cell update of the Weyl sweeps, on the cell blocks around the cell
+            Blk<float, 2> xp, ax, bx, ay, by, xc, yi, yn;
+            tma_lds_blk<R>(s1, Bc[i], xp);
+            tma_lds_blk<R>(s0, Bxm[i], ax);
+            tma_lds_blk<R>(s0, Bxp[i], bx);
+            tma_lds_blk<R>(s0, Bym[i], ay);
+            tma_lds_blk<R>(s0, Byp[i], by);
+            tma_lds_blk<R>(s0, Bc[i], xc);
+            if (m.has_yin) tma_lds_blk<R>(sy, Bc[i], yi);
+            const float V0 = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i])
+                                     : site_potential_t<float>(g, 2 * s);
+            const float V1 = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i] + 4)
+                                     : site_potential_t<float>(g, 2 * s + 1);
+            wsm_cell_update(cf, V0, V1, xmr[i], xc, xp, ax, bx, ay, by, m.has_yin ? &yi : nullptr, yn);
+            const int64_t sites[4] = {2 * s, 2 * s, 2 * s + 1, 2 * s + 1};
+            epilogue<float, 2, FEAT>(p, s, c, xc, yn, dacc, sites);
+            xmr[i] = xc;
+            continue;
+          }
+          // the axes in ti_axes' order (z pair, x pair, y pair), each pair loaded
+          // just before it is folded in, so that few blocks are live at a time
+          Blk<float, 2> S, D, yn;
+          {
+            Blk<float, 2> xp;
+            tma_lds_blk<R>(s1, Bc[i], xp);
+            axis_z_init(xmr[i], xp, S, D);
+          }
+          {
+            Blk<float, 2> ax, bx;
+            tma_lds_blk<R>(s0, Bxm[i], ax);
+            tma_lds_blk<R>(s0, Bxp[i], bx);
+            axis_x_add(ax, bx, S, D);
+          }
+          {
+            Blk<float, 2> ay, by;
+            tma_lds_blk<R>(s0, Bym[i], ay);
+            tma_lds_blk<R>(s0, Byp[i], by);
+            axis_y_add(ay, by, S, D);
+          }
+          Blk<float, 2> xc, yi;
+          tma_lds_blk<R>(s0, Bc[i], xc);
+          if (m.has_yin) tma_lds_blk<R>(sy, Bc[i], yi);
+          const float Vs = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i]) : site_potential_t<float>(g, s);
+          ti_combine(cf, Vs, xc, S, D, m.has_yin ? &yi : nullptr, yn, g);
+          const int64_t sites[4] = {s, s, s, s};
           epilogue<float, 2, FEAT>(p, s, c, xc, yn, dacc, sites);
           xmr[i] = xc;
-          continue;
         }
-        // the axes in ti_axes' order (z pair, x pair, y pair), each pair loaded
-        // just before it is folded in, so that few blocks are live at a time
-        Blk<float, 2> S, D, yn;
-        {
-          Blk<float, 2> xp;
-          tma_lds_blk<R>(s1, Bc[i], xp);
-          axis_z_init(xmr[i], xp, S, D);
-        }
-        {
-          Blk<float, 2> ax, bx;
-          tma_lds_blk<R>(s0, Bxm[i], ax);
-          tma_lds_blk<R>(s0, Bxp[i], bx);
-          axis_x_add(ax, bx, S, D);
-        }
-        {
-          Blk<float, 2> ay, by;
-          tma_lds_blk<R>(s0, Bym[i], ay);
-          tma_lds_blk<R>(s0, Byp[i], by);
-          axis_y_add(ay, by, S, D);
-        }
-        Blk<float, 2> xc, yi;
-        tma_lds_blk<R>(s0, Bc[i], xc);
-        if (m.has_yin) tma_lds_blk<R>(sy, Bc[i], yi);
-        const float Vs = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i]) : site_potential_t<float>(g, s);
-        ti_combine(cf, Vs, xc, S, D, m.has_yin ? &yi : nullptr, yn, g);
-        const int64_t sites[4] = {s, s, s, s};
-        epilogue<float, 2, FEAT>(p, s, c, xc, yn, dacc, sites);
-        xmr[i] = xc;
       }
       release_x(kx, lu, j);
       release_y(ky, lu, j);
@@ -514,11 +611,17 @@ __global__ void __launch_bounds__(32 * NW, 1)
     // blocks in finish_dots (after an abort the values are garbage, but the
     // arrival counter stays consistent)
     const double* wd = reinterpret_cast<const double*>(base + L::DOT_OFF);
-    double* row = p.partials + (size_t)blockIdx.x * kNumDots * R;
-    for (int t = threadIdx.x; t < kNumDots * R; t += blockDim.x) {
-      const int d = t / R, r = t - d * R;
+    constexpr int RV = FX ? R / 2 : R;  // vectors of the block
+    double* row = p.partials + (size_t)blockIdx.x * kNumDots * RV;
+    for (int t = threadIdx.x; t < kNumDots * RV; t += blockDim.x) {
+      const int d = t / RV, r = t - d * RV;
       double sum = 0.0;
-      for (int w = 0; w < NCW; ++w) sum += wd[((w * kNumDots + d) * 2 + (r & 1)) * L::CPS + (r >> 1)];
+      if constexpr (FX) {
+        if (d < 2)
+          for (int w = 0; w < NCW; ++w) sum += wd[w * kNumDots * 2 * L::CPS + d * L::CPS + r];
+      } else {
+        for (int w = 0; w < NCW; ++w) sum += wd[((w * kNumDots + d) * 2 + (r & 1)) * L::CPS + (r >> 1)];
+      }
       row[t] = sum;
     }
     finish_dots(p);
@@ -540,12 +643,15 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
-template <int R, bool DEEP>
+template <int R, bool DEEP, int MODEL = PVSC_TI>
 static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
   using L = TmaLayout<R, DEEP, 8>;
   auto enc = encode_tiled();
   if (!enc) return set_error(PVSC_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
   const int vpc = lat->g.model == PVSC_WSM ? 2 : 1;  // Weyl cells: two sites each
+  // 4-byte words of potential data per tile point: fp32 potentials, or the
+  // fixed-point sweep's per-site (d+, d-) pair of 64-bit coefficients
+  const int vf = MODEL == kModelTIFx ? 4 : vpc;
   const cuuint64_t Lx = lat->g.L[0] / vpc, Ly = lat->g.L[1], Lz = lat->g.L[2];
   const cuuint64_t dims[5] = {32, (cuuint64_t)L::ROWS, Lx, Ly, Lz};
   const cuuint64_t strides[4] = {128, (cuuint64_t)L::SITE_B, (cuuint64_t)L::SITE_B * Lx,
@@ -566,12 +672,13 @@ static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
   m.has_yin = p.yin != nullptr;
   if (m.has_yin)
     if (int rc = tile5(&m.yi, p.yin, L::TX, L::TY)) return rc;
-  m.v_tma = lat->g.v_mode == 1;
+  m.v_tma = MODEL == kModelTIFx ? 1 : lat->g.v_mode == 1;
   if (m.v_tma) {
-    const cuuint64_t vd[3] = {vpc * Lx, Ly, Lz};  // the potential is per site
-    const cuuint64_t vs[2] = {4 * vpc * Lx, 4 * vpc * Lx * Ly};
-    const cuuint32_t vb[3] = {(cuuint32_t)(vpc * L::TX), (cuuint32_t)L::TY, 1};
-    const CUresult r = enc(&m.v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(lat->g.V32), vd, vs, vb,
+    const cuuint64_t vd[3] = {vf * Lx, Ly, Lz};  // per site
+    const cuuint64_t vs[2] = {4 * vf * Lx, 4 * vf * Lx * Ly};
+    const cuuint32_t vb[3] = {(cuuint32_t)(vf * L::TX), (cuuint32_t)L::TY, 1};
+    void* vptr = MODEL == kModelTIFx ? const_cast<void*>(p.fx_d) : static_cast<void*>(const_cast<float*>(lat->g.V32));
+    const CUresult r = enc(&m.v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, vptr, vd, vs, vb,
                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(PVSC_ERR_CUDA, "cuTensorMapEncodeTiled (potential) failed (%d)", (int)r);
@@ -581,13 +688,17 @@ static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
 
 template <int R, bool DEEP, int NW, int MODEL>
 static void* tma_kernel(int feat) {
-  switch (feat) {
-    case 0: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, 0, MODEL>);
-    case F_DOTS: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS, MODEL>);
-    case F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_Z, MODEL>);
-    case F_DOTS | F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS | F_Z, MODEL>);
-    case F_ACC: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_ACC, MODEL>);
-    default: return nullptr;
+  if constexpr (MODEL == kModelTIFx) {  // KPM sweeps only
+    return feat == F_DOTS ? reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS, MODEL>) : nullptr;
+  } else {
+    switch (feat) {
+      case 0: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, 0, MODEL>);
+      case F_DOTS: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS, MODEL>);
+      case F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_Z, MODEL>);
+      case F_DOTS | F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS | F_Z, MODEL>);
+      case F_ACC: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_ACC, MODEL>);
+      default: return nullptr;
+    }
   }
 }
 
@@ -610,7 +721,7 @@ static int auto_chunks(int64_t ntiles, int64_t Lz, int64_t grid) {
 
 template <int R, bool DEEP, int NW, int MODEL = PVSC_TI>
 static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
-  using L = TmaLayout<R, DEEP, NW>;
+  using L = TmaLayout<R, DEEP, NW, MODEL == kModelTIFx ? 4 : 2>;
   void* fn = tma_kernel<R, DEEP, NW, MODEL>(feat);
   if (!fn) return set_error(PVSC_ERR_UNSUPPORTED, "no TMA-staged sweep for feature set %d", feat);
   if (int rc = allow_max_smem(fn)) return rc;
@@ -621,7 +732,7 @@ static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const Launc
   p.tile_x = L::TX;
   p.tile_y = L::TY;
   TmaMaps m;
-  if (int rc = encode_maps<R, DEEP>(lat, p, m)) return rc;
+  if (int rc = encode_maps<R, DEEP, MODEL>(lat, p, m)) return rc;
   const int64_t Lx = lat->g.L[0] / (MODEL == PVSC_WSM ? 2 : 1), Ly = lat->g.L[1], Lz = lat->g.L[2];
   m.ntx = (int)((Lx + L::TX - 1) / L::TX);
   m.nty = (int)((Ly + L::TY - 1) / L::TY);
