@@ -522,6 +522,11 @@ static int kpm_moments_fx(const pvsc_lattice* lat, int R, const void* r0, uint64
       ml->gersh_hi = hi;
       ml->gersh_valid = true;
     }
+    // the coupling coefficient kt = -t/a of the alpha = 2/a sweeps stays within
+    // the range of the fixed-point products (|kt| <= 2); a lattice with any bond
+    // has a >= |t| from the Gershgorin interval alone
+    if (std::fabs(lat->g.t) > 2.0 * a)
+      return set_error(PVSC_ERR_ARG, "PVSC_Q64 needs a >= |t| / 2 (a = %.17g, t = %.17g)", a, lat->g.t);
     const double lo = lat->gersh_lo, hi = lat->gersh_hi;
     const double slack = 1e-12 * a;
     if (lo < b - a - slack || hi > b + a + slack)

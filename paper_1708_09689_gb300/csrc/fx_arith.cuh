@@ -21,6 +21,8 @@
 // magnitude (worked out at each sum).
 #pragma once
 
+#include "sweep.cuh"
+
 namespace pvsc {
 
 using i64 = long long;
@@ -50,14 +52,59 @@ __device__ __forceinline__ i64 wmul32(int a, int b) { return (i64)a * (i64)b; }
 // (the remainder L mod 2^31 < 2^31 cannot carry across a multiple of 2^60).
 __device__ __forceinline__ i64 fx_mul2(FxLimbs c1, FxLimbs x1, FxLimbs c2, FxLimbs x2) {
   const i64 H = wmul32(c1.h, x1.h) + wmul32(c2.h, x2.h);
-  i64 M = (i64)1 << (kFxVal - 31) ;
+  i64 M = (i64)1 << (kFxVal - 31);
   M += wmul32(c1.h, x1.l);
   M += wmul32(c1.l, x1.h);
   M += wmul32(c2.h, x2.l);
   M += wmul32(c2.l, x2.h);
   const i64 L = wmul32(c1.l, x1.l) + wmul32(c2.l, x2.l);
-  const i64 N = M + (L >> 31);
+  const i64 N = M + (i64)(unsigned)((u64)L >> 31);  // L >= 0: floor(L / 2^31) < 2^32
   return H * 4 + (N >> 29);
+}
+
+// The neighbour combination of the TI stencil (Eq. TB_H_topi) per orbital o:
+// with S_o the sum of the six neighbours and D_o the signed, permuted axis
+// differences d_j = x(n - e_j) - x(n + e_j) of the -i Gamma^{j+1} terms, the
+// hopping part of the update is kt T_o, T_o = D_o + S_o for even o and
+// D_o - S_o for odd o (the Gamma^1 sign).  T is accumulated axis by axis from
+// the two neighbour blocks a = x(n - e_j), b = x(n + e_j): per value four
+// terms, sigma_o (a_o + b_o) + (the axis's permuted difference of orbital
+// p(o)), summed as two three-operand additions.  Integer sums are exact, so
+// the order is free.  AXIS 0: z (d-permutation (d1, -d0, d3, -d2)), 1: x
+// ((d3, d2, -d1, -d0)), 2: y (-i (d3, d2, d1, d0)).
+template <int AXIS, bool INIT>
+__device__ __forceinline__ void fx_axis_T(const Blk<i64, 1>& a, const Blk<i64, 1>& b, Blk<i64, 1>& T) {
+  constexpr int P[3][4] = {{1, 0, 3, 2}, {3, 2, 1, 0}, {3, 2, 1, 0}};
+  constexpr int SGN[2][4] = {{1, -1, 1, -1}, {1, 1, -1, -1}};  // z, x: sign of the difference
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const bool even = (o & 1) == 0;
+    const int p = P[AXIS][o];
+    const cplx<i64> ao = a.v[o][0], bo = b.v[o][0], ap = a.v[p][0], bp = b.v[p][0];
+    // the permuted difference (dr, di) as (plus - minus) pairs
+    i64 dr_p, dr_m, di_p, di_m;
+    if constexpr (AXIS == 2) {  // -i (ap - bp) = (ap.im - bp.im, bp.re - ap.re)
+      dr_p = ap.im;
+      dr_m = bp.im;
+      di_p = bp.re;
+      di_m = ap.re;
+    } else {
+      const bool pos = SGN[AXIS][o] > 0;
+      dr_p = pos ? ap.re : bp.re;
+      dr_m = pos ? bp.re : ap.re;
+      di_p = pos ? ap.im : bp.im;
+      di_m = pos ? bp.im : ap.im;
+    }
+    if constexpr (INIT) {
+      const i64 re = even ? (ao.re + bo.re + dr_p) : (dr_p - ao.re - bo.re);
+      const i64 im = even ? (ao.im + bo.im + di_p) : (di_p - ao.im - bo.im);
+      T.v[o][0] = {re - dr_m, im - di_m};
+    } else {
+      const i64 re = even ? (T.v[o][0].re + ao.re + bo.re) : (T.v[o][0].re - ao.re - bo.re);
+      const i64 im = even ? (T.v[o][0].im + ao.im + bo.im) : (T.v[o][0].im - ao.im - bo.im);
+      T.v[o][0] = {re + dr_p - dr_m, im + di_p - di_m};
+    }
+  }
 }
 
 // An exact dot-product sum: V = u 2^62 + (hi 2^64 + lo) (two's complement,

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) ti_sweep_fx(const __grid_constant__ Sweep
   i64* Yout = static_cast<i64*>(p.yout);
   const longlong2* __restrict__ dfx = static_cast<const longlong2*>(p.fx_d);
   const FxLimbs kt = fx_split(p.fx_kt);
-  const i64 dmul = p.fx_dshift ? 2 : 1;
+  const int dshift = p.fx_dshift ? 1 : 0;  // alpha = 2/a: coefficients doubled
   const double vs = p.vscale[rc];
   double dd[kNumDots][1];
 #pragma unroll
@@ -68,15 +68,16 @@ __global__ void __launch_bounds__(256) ti_sweep_fx(const __grid_constant__ Sweep
         [&](const longlong2 dv, const Blk<i64, 1>& xm, const Blk<i64, 1>& xc, const Blk<i64, 1>& xp,
             const Blk<i64, 1>& ax, const Blk<i64, 1>& bx, const Blk<i64, 1>& ay, const Blk<i64, 1>& by,
             const Blk<i64, 1>* yi, Blk<i64, 1>& yn) {
-          Blk<i64, 1> S, D;
-          ti_axes(xm, xp, ax, bx, ay, by, S, D);
-          const FxLimbs dp = fx_split(dv.x * dmul), dm = fx_split(dv.y * dmul);
+          Blk<i64, 1> T;
+          fx_axis_T<0, true>(xm, xp, T);
+          fx_axis_T<1, false>(ax, bx, T);
+          fx_axis_T<2, false>(ay, by, T);
+          const FxLimbs dp = fx_split((i64)((u64)dv.x << dshift)), dm = fx_split((i64)((u64)dv.y << dshift));
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
             const FxLimbs d = (o & 1) ? dm : dp;
-            const cplx<i64> T = (o & 1) ? csub(D.v[o][0], S.v[o][0]) : cadd(D.v[o][0], S.v[o][0]);
-            i64 re = fx_mul2(d, fx_split(xc.v[o][0].re), kt, fx_split(T.re));
-            i64 im = fx_mul2(d, fx_split(xc.v[o][0].im), kt, fx_split(T.im));
+            i64 re = fx_mul2(d, fx_split(xc.v[o][0].re), kt, fx_split(T.v[o][0].re));
+            i64 im = fx_mul2(d, fx_split(xc.v[o][0].im), kt, fx_split(T.v[o][0].im));
             if (yi != nullptr) {
               re -= yi->v[o][0].re;
               im -= yi->v[o][0].im;

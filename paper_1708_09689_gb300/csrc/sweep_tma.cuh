@@ -194,10 +194,12 @@ __device__ __forceinline__ int tma_site_perm(int q) {
 // offset L = O + 16 c with its chunk bits XORed with its row bits.  Orbital o
 // then sits at (B ^ (K_o << 4)) + (its row offset) with the compile-time K of
 // tma_lds_blk (the row offset of orbital o modulo 8 never carries into the row
-// bits of L for R = 4 .. 64).
-template <int R>
+// bits of L for R = 4 .. 64).  SWZ = false: tiles copied without swizzle
+// (the logical offset itself).
+template <int R, bool SWZ = true>
 __device__ __forceinline__ uint32_t tma_swz(uint32_t O, int c) {
   const uint32_t L = O + 16u * (uint32_t)c;
+  if constexpr (!SWZ) return L;
   return L ^ (((L >> 7) & 7u) << 4);
 }
 
@@ -219,15 +221,16 @@ __device__ __forceinline__ void tma_lds_blk(const unsigned char* buf, uint32_t B
 
 // The same four orbitals of a fixed-point block: a site of R/2 vectors of
 // 16-byte (re, im) 64-bit pairs has the byte layout of a complex64 site of R
-// vectors, and vector c is the 16-byte chunk c of every orbital.
-template <int R>
+// vectors, and vector c is the 16-byte chunk c of every orbital.  SWZ = false
+// (unswizzled tiles): orbital o at B + its offset, an immediate of the load.
+template <int R, bool SWZ = true>
 __device__ __forceinline__ void tma_lds_blk(const unsigned char* buf, uint32_t B, Blk<long long, 1>& b) {
 #pragma unroll
   for (int o = 0; o < 4; ++o) {
     const int ao = o * 8 * R;
     const int K1 = (ao >> 4) & 7, K2 = (ao >> 7) & 7;
-    const longlong2 v =
-        *reinterpret_cast<const longlong2*>(buf + ((B ^ (uint32_t)((K1 ^ K2) << 4)) + (uint32_t)(ao & ~127)));
+    const uint32_t off = SWZ ? (B ^ (uint32_t)((K1 ^ K2) << 4)) + (uint32_t)(ao & ~127) : B + (uint32_t)ao;
+    const longlong2 v = *reinterpret_cast<const longlong2*>(buf + off);
     b.v[o][0] = {v.x, v.y};
   }
 }
@@ -243,6 +246,9 @@ __global__ void __launch_bounds__(32 * NW, 1)
     ti_sweep_tma(const __grid_constant__ Sweep p, const __grid_constant__ TmaMaps m) {
   constexpr bool WSM = MODEL == 3;
   constexpr bool FX = MODEL == kModelTIFx;
+  // fixed point with R/2 >= 8 vectors: a quarter-warp reads one whole 128-byte
+  // row of an orbital, conflict-free without the swizzle (no XOR per load)
+  constexpr bool SWZ = !(FX && R >= 16);
   constexpr int VPC = WSM ? 2 : 1;               // sites per tile point
   constexpr int VF = WSM ? 2 : (FX ? 4 : 1);     // 4-byte words of potential data per tile point
   using L = TmaLayout<R, DEEP, NW, FX ? 4 : 2>;
@@ -392,7 +398,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
   fx_acc_zero(fxx);
   fx_acc_zero(fxy);
   const FxLimbs fkt = fx_split(FX ? p.fx_kt : 0);
-  const long long fdmul = p.fx_dshift ? 2 : 1;
+  const int fdshift = p.fx_dshift ? 1 : 0;  // alpha = 2/a: coefficients doubled
   const double fvs = FX ? p.vscale[c] : 0.0;
   double* wdots = reinterpret_cast<double*>(base + L::DOT_OFF) + warp * kNumDots * 2 * L::CPS;
   if constexpr (has_dots(FEAT)) {
@@ -445,11 +451,11 @@ __global__ void __launch_bounds__(32 * NW, 1)
       const int ly = li / TX, lx = li - ly * TX;
       ok[i] = lx < TXe && ly < TYe;
       const uint32_t SB = L::SITE_B;
-      Bc[i] = tma_swz<R>(li * SB, c);
-      Bxm[i] = tma_swz<R>(lx > 0 ? (li - 1) * SB : L::OFF_XM + ly * SB, c);
-      Bxp[i] = tma_swz<R>(lx + 1 < TXe ? (li + 1) * SB : L::OFF_XP + ly * SB, c);
-      Bym[i] = tma_swz<R>(ly > 0 ? (li - TX) * SB : L::OFF_YM + lx * SB, c);
-      Byp[i] = tma_swz<R>(ly + 1 < TYe ? (li + TX) * SB : L::OFF_YP + lx * SB, c);
+      Bc[i] = tma_swz<R, SWZ>(li * SB, c);
+      Bxm[i] = tma_swz<R, SWZ>(lx > 0 ? (li - 1) * SB : L::OFF_XM + ly * SB, c);
+      Bxp[i] = tma_swz<R, SWZ>(lx + 1 < TXe ? (li + 1) * SB : L::OFF_XP + ly * SB, c);
+      Bym[i] = tma_swz<R, SWZ>(ly > 0 ? (li - TX) * SB : L::OFF_YM + lx * SB, c);
+      Byp[i] = tma_swz<R, SWZ>(ly + 1 < TYe ? (li + TX) * SB : L::OFF_YP + lx * SB, c);
       Vo[i] = L::INT_B + 4 * VF * li;
       col[i] = (int64_t)(x0 + lx) + (int64_t)Lx * (y0 + ly);
     }
@@ -462,7 +468,12 @@ __global__ void __launch_bounds__(32 * NW, 1)
       const unsigned char* s0 = base + (kx % L::NXS) * L::XSTAGE;
 #pragma unroll
       for (int i = 0; i < IPT; ++i)
-        if (ok[i]) tma_lds_blk<R>(s0, Bc[i], xmr[i]);
+        if (ok[i]) {
+          if constexpr (FX)
+            tma_lds_blk<R, SWZ>(s0, Bc[i], xmr[i]);
+          else
+            tma_lds_blk<R>(s0, Bc[i], xmr[i]);
+        }
     }
     release_x(kx, lu, -1);
     ++kx;
@@ -487,38 +498,38 @@ __global__ void __launch_bounds__(32 * NW, 1)
         if constexpr (FX) {
           // the fixed-point update of sweep_fx.cu: y = d x + kt T (- y_in), exact
           // with one rounding, then the exact dot sums of the site
-          Blk<long long, 1> S, D, yn;
+          Blk<long long, 1> T, yn;
           {
             Blk<long long, 1> xp;
-            tma_lds_blk<R>(s1, Bc[i], xp);
-            axis_z_init(xmr[i], xp, S, D);
+            tma_lds_blk<R, SWZ>(s1, Bc[i], xp);
+            fx_axis_T<0, true>(xmr[i], xp, T);
           }
           {
             Blk<long long, 1> ax, bx;
-            tma_lds_blk<R>(s0, Bxm[i], ax);
-            tma_lds_blk<R>(s0, Bxp[i], bx);
-            axis_x_add(ax, bx, S, D);
+            tma_lds_blk<R, SWZ>(s0, Bxm[i], ax);
+            tma_lds_blk<R, SWZ>(s0, Bxp[i], bx);
+            fx_axis_T<1, false>(ax, bx, T);
           }
           {
             Blk<long long, 1> ay, by;
-            tma_lds_blk<R>(s0, Bym[i], ay);
-            tma_lds_blk<R>(s0, Byp[i], by);
-            axis_y_add(ay, by, S, D);
+            tma_lds_blk<R, SWZ>(s0, Bym[i], ay);
+            tma_lds_blk<R, SWZ>(s0, Byp[i], by);
+            fx_axis_T<2, false>(ay, by, T);
           }
           Blk<long long, 1> xc, yi;
-          tma_lds_blk<R>(s0, Bc[i], xc);
-          if (m.has_yin) tma_lds_blk<R>(sy, Bc[i], yi);
+          tma_lds_blk<R, SWZ>(s0, Bc[i], xc);
+          if (m.has_yin) tma_lds_blk<R, SWZ>(sy, Bc[i], yi);
           const longlong2 dv = *reinterpret_cast<const longlong2*>(sy + Vo[i]);
-          const FxLimbs dp = fx_split(dv.x * fdmul), dm = fx_split(dv.y * fdmul);
+          const FxLimbs dp = fx_split((long long)((unsigned long long)dv.x << fdshift)),
+                        dm = fx_split((long long)((unsigned long long)dv.y << fdshift));
           FxLimbs xs[8], ys[8];
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
             const FxLimbs d = (o & 1) ? dm : dp;
-            const cplx<long long> T = (o & 1) ? csub(D.v[o][0], S.v[o][0]) : cadd(D.v[o][0], S.v[o][0]);
             xs[2 * o] = fx_split(xc.v[o][0].re);
             xs[2 * o + 1] = fx_split(xc.v[o][0].im);
-            long long re = fx_mul2(d, xs[2 * o], fkt, fx_split(T.re));
-            long long im = fx_mul2(d, xs[2 * o + 1], fkt, fx_split(T.im));
+            long long re = fx_mul2(d, xs[2 * o], fkt, fx_split(T.v[o][0].re));
+            long long im = fx_mul2(d, xs[2 * o + 1], fkt, fx_split(T.v[o][0].im));
             if (m.has_yin) {
               re -= yi.v[o][0].re;
               im -= yi.v[o][0].im;
@@ -657,10 +668,13 @@ static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
   const cuuint64_t strides[4] = {128, (cuuint64_t)L::SITE_B, (cuuint64_t)L::SITE_B * Lx,
                                  (cuuint64_t)L::SITE_B * Lx * Ly};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  // the kernel's addressing: unswizzled tiles for fixed point with R/2 >= 8 vectors
+  const CUtensorMapSwizzle swz =
+      (MODEL == kModelTIFx && R >= 16) ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B;
   auto tile5 = [&](CUtensorMap* map, const void* ptr, cuuint32_t bx, cuuint32_t by) -> int {
     const cuuint32_t box[5] = {32, (cuuint32_t)L::ROWS, bx, by, 1};
     const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(ptr), dims, strides,
-                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(PVSC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return PVSC_OK;
