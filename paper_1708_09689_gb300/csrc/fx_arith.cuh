@@ -42,6 +42,19 @@ __device__ __forceinline__ FxLimbs fx_split(i64 v) {
 
 __device__ __forceinline__ i64 wmul32(int a, int b) { return (i64)a * (i64)b; }
 
+// c + a b as one wide multiply-add (32 x 32 -> 64 bits, 64-bit addend)
+__device__ __forceinline__ i64 wmad32(int a, int b, i64 c) {
+  i64 d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+
+__device__ __forceinline__ u64 wmad32u(unsigned a, unsigned b, u64 c) {
+  u64 d;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+
 // round((c1 x1 + c2 x2) 2^-60), half up: Q3.60 x Q4.59 -> Q4.59.
 // With P = c1 x1 + c2 x2 + 2^59 = H 2^62 + M 2^31 + L:
 //   H = c1_h x1_h + c2_h x2_h               (|H| < 2^61)
@@ -51,13 +64,9 @@ __device__ __forceinline__ i64 wmul32(int a, int b) { return (i64)a * (i64)b; }
 // and, with N = M + floor(L / 2^31), floor(P / 2^60) = 4 H + floor(N / 2^29)
 // (the remainder L mod 2^31 < 2^31 cannot carry across a multiple of 2^60).
 __device__ __forceinline__ i64 fx_mul2(FxLimbs c1, FxLimbs x1, FxLimbs c2, FxLimbs x2) {
-  const i64 H = wmul32(c1.h, x1.h) + wmul32(c2.h, x2.h);
-  i64 M = (i64)1 << (kFxVal - 31);
-  M += wmul32(c1.h, x1.l);
-  M += wmul32(c1.l, x1.h);
-  M += wmul32(c2.h, x2.l);
-  M += wmul32(c2.l, x2.h);
-  const i64 L = wmul32(c1.l, x1.l) + wmul32(c2.l, x2.l);
+  const i64 H = wmad32(c2.h, x2.h, wmul32(c1.h, x1.h));
+  const i64 M = wmad32(c2.l, x2.h, wmad32(c2.h, x2.l, wmad32(c1.l, x1.h, wmad32(c1.h, x1.l, (i64)1 << (kFxVal - 31)))));
+  const i64 L = wmad32(c2.l, x2.l, wmul32(c1.l, x1.l));
   const i64 N = M + (i64)(unsigned)((u64)L >> 31);  // L >= 0: floor(L / 2^31) < 2^32
   return H * 4 + (N >> 29);
 }
@@ -155,17 +164,16 @@ __device__ __forceinline__ void fx_dot_item(const FxLimbs (&x)[8], const FxLimbs
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const unsigned xl = (unsigned)x[k].l, yl = (unsigned)y[k].l;
-    ah += wmul32(x[k].h, x[k].h);
-    am += wmul32(x[k].h, x[k].l);
-    bh += wmul32(y[k].h, x[k].h);
-    bm += wmul32(y[k].h, x[k].l);
-    bm += wmul32(y[k].l, x[k].h);
+    ah = wmad32(x[k].h, x[k].h, ah);
+    am = wmad32(x[k].h, x[k].l, am);
+    bh = wmad32(y[k].h, x[k].h, bh);
+    bm = wmad32(y[k].l, x[k].h, wmad32(y[k].h, x[k].l, bm));
     if (k < 4) {
-      al0 += (u64)xl * xl;
-      bl0 += (u64)yl * xl;
+      al0 = wmad32u(xl, xl, al0);
+      bl0 = wmad32u(yl, xl, bl0);
     } else {
-      al1 += (u64)xl * xl;
-      bl1 += (u64)yl * xl;
+      al1 = wmad32u(xl, xl, al1);
+      bl1 = wmad32u(yl, xl, bl1);
     }
   }
   xx.u += ah;
