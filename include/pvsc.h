@@ -530,21 +530,22 @@ typedef struct {
                   /* 6 marching along x over lines (y, z), zslab = x-segment length, */
                   /* 7 (complex64, R = 4 .. 64, Lx a multiple of 4) TMA-staged */
                   /* plane tiles: one block per SM copies each z-plane of a tile of */
-                  /* 16x16, 16x8, 8x8, 4x4 or 4x2 columns with its one-site halo strips into a */
-                  /* shared-memory ring (cp.async.bulk.tensor, mbarriers) for eight */
-                  /* warps (threads 256, two (site, vector pair) items per thread) or */
-                  /* sixteen (threads 512, one item; not R = 32, 64, whose tiles have */
-                  /* one item per thread); tile_x x tile_y = the half tile */
-                  /* (16x8, 16x4, 8x4 for R = 4, 8, 16) selects rings one plane */
-                  /* deeper on eight warps; zslab = z-chunk depth (0: chosen from */
-                  /* the grid size); vpt is ignored. */
+                  /* 16x16, 16x8 or 8x8 columns (R = 4, 8, 16) with its one-site halo */
+                  /* strips into a shared-memory ring (cp.async.bulk.tensor, */
+                  /* mbarriers) for eight warps (threads 256, two (site, vector pair) */
+                  /* items per thread) or sixteen (threads 512, one item); R = 32 and */
+                  /* 64 run as 2 and 4 slices of 16 vectors on the 8x8 tiles, one slice */
+                  /* per block; tile_x x tile_y = the half tile (16x8, 16x4, 8x4, 8x4, */
+                  /* 8x4 for R = 4 .. 64) selects rings one plane deeper on eight warps */
+                  /* (TI; Weyl cells run the large tile on eight warps); zslab = z-chunk */
+                  /* depth (0: chosen from the grid size); vpt is ignored. */
                   /* PVSC_Q64 (KPM on TI lattices) takes kernels 0, 2, 3 (threads a */
                   /* multiple of R, one vector per thread, no tile) and 7 for R = 2 .. 32 */
                   /* (any Lx): the tiles, rings and variants of the complex64 layout */
-                  /* of 2R vectors (a fixed-point value is 16 bytes), one vector of one */
-                  /* site per item.  Untuned it runs kernel 7 on sixteen warps for */
-                  /* R = 2 .. 8, kernel 7 on eight for R = 16, 32, kernel 2 for R = 64 */
-                  /* and kernel 0 for R = 1. */
+                  /* of 2R vectors (a fixed-point value is 16 bytes; R = 16, 32 as */
+                  /* slices of 8), one vector of one site per item.  Untuned it runs */
+                  /* kernel 7 on sixteen warps for R = 2 .. 8 and on eight for R = 16, */
+                  /* 32, kernel 2 for R = 64 and kernel 0 for R = 1. */
 } pvsc_tuning;
 
 /* Device error word of the shared-memory staged sweeps: *flag = 1 if a copy

@@ -192,11 +192,12 @@ extern "C" int pvsc_autotune_op(pvsc_lattice* lat, int R, int prec, int op, pvsc
   }
   // TMA-staged plane tiles (kernel 7): z-chunks chosen automatically or a few fixed depths
   if (tma_sweep_possible(lat, R, prec)) {
-    const int deep_y = R == 4 ? 8 : 4, deep_x = R == 16 ? 8 : 16;
+    // the half tiles of the deeper rings (R = 32, 64: slices on the tiles of R = 16)
+    const int deep_y = R == 4 ? 8 : 4, deep_x = R >= 16 ? 8 : 16;
     for (int zs : {0, 16, 32, 64})
       if (zs == 0 || zs < lat->g.L[2]) {
         cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, 0, 0, kKernelTma});
-        if (R < 32) {  // R = 32, 64 have one tile, one item per thread
+        if (lat->g.model == PVSC_TI) {  // the Weyl cells run the large tile only
           cands.push_back(pvsc_tuning{512, 0, zs, 0.f, 2, 0, 0, kKernelTma});
           cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, deep_x, deep_y, kKernelTma});
         }

@@ -1,22 +1,28 @@
 // TMA-staged plane-tile sweep (tuning kernel 7): host-side eligibility, tile
 // choices and dispatch.  The kernels are instantiated in sweep_tma_ti.cu (TI,
-// R = 4, 8, 16, all launch variants) and sweep_tma_wide.cu (TI R = 32, 64 and
-// the Weyl-semimetal cells), compiled in parallel; the kernel itself is in
-// sweep_tma.cuh.
+// R = 4, 8, 16, all launch variants), sweep_tma_wide.cu (the Weyl-semimetal
+// cells, R = 4 .. 16) and sweep_tma_sliced.cu (R = 32 and 64 as two or four
+// slices of 16 vectors on the tiles of R = 16, TI and Weyl cells), compiled in
+// parallel; the kernel itself is in sweep_tma.cuh.
 #include "sweep_tma.cuh"
 
 namespace pvsc {
 
 int launch_tma_ti(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st);
 int launch_tma_wide(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st);
+int launch_tma_sliced(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st);
 int tma_error_ti(int clear, int* flag);
 int tma_error_wide(int clear, int* flag);
+int tma_error_sliced(int clear, int* flag);
 
+// work units of a sweep on the smaller (deep-ring) tiles, the most there are; R = 32
+// and 64 run as 2 and 4 slices of the 16-vector tiles
 template <int R>
-static int64_t tma_tiles(const Geometry& g) {  // the smaller (deep-ring) tiles: the most units
-  using L = TmaLayout<R, true, 8>;
+static int64_t tma_tiles(const Geometry& g) {
+  constexpr int RT = R > 16 ? 16 : R, SL = R > 16 ? R / 16 : 1;
+  using L = TmaLayout<RT, true, 8>;
   const int64_t Lx = g.model == PVSC_WSM ? g.L[0] / 2 : g.L[0];
-  return ((Lx + L::TX - 1) / L::TX) * ((g.L[1] + L::TY - 1) / L::TY);
+  return SL * ((Lx + L::TX - 1) / L::TX) * ((g.L[1] + L::TY - 1) / L::TY);
 }
 
 // The kernel's unit table holds the (x0, y0, z0, planes) of a block's units in
@@ -44,10 +50,9 @@ static void tma_tiles_of(int R, int* tx_large, int* ty_large, int* tx_deep, int*
             *tx_deep = TmaLayout<8, true, 8>::TX; *ty_deep = TmaLayout<8, true, 8>::TY; break;
     case 16: *tx_large = TmaLayout<16, false, 8>::TX; *ty_large = TmaLayout<16, false, 8>::TY;
              *tx_deep = TmaLayout<16, true, 8>::TX; *ty_deep = TmaLayout<16, true, 8>::TY; break;
-    case 32: *tx_large = TmaLayout<32, false, 8>::TX; *ty_large = TmaLayout<32, false, 8>::TY;
-             *tx_deep = -1; *ty_deep = -1; break;  // one tile, no deeper-ring variant
-    default: *tx_large = TmaLayout<64, false, 8>::TX; *ty_large = TmaLayout<64, false, 8>::TY;
-             *tx_deep = -1; *ty_deep = -1; break;
+    default:  // R = 32, 64: slices of 16 vectors on the tiles of R = 16
+             *tx_large = TmaLayout<16, false, 8>::TX; *ty_large = TmaLayout<16, false, 8>::TY;
+             *tx_deep = TmaLayout<16, true, 8>::TX; *ty_deep = TmaLayout<16, true, 8>::TY; break;
   }
 }
 
@@ -68,16 +73,18 @@ int launch_sweep_tma(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchSh
   if (!tma_sweep_possible(lat, p.R, PVSC_C64))
     return set_error(PVSC_ERR_UNSUPPORTED, "the TMA-staged sweep needs a complex64 TI or Weyl lattice, R >= 4 "
                      "and Lx a multiple of 4");
-  if (lat->g.model == PVSC_WSM || p.R >= 32) return launch_tma_wide(lat, feat, p, sh, st);
+  if (p.R >= 32) return launch_tma_sliced(lat, feat, p, sh, st);
+  if (lat->g.model == PVSC_WSM) return launch_tma_wide(lat, feat, p, sh, st);
   return launch_tma_ti(lat, feat, p, sh, st);
 }
 
 int tma_error(int clear, int* flag) {
-  int a = 0, b = 0, c = 0;
+  int a = 0, b = 0, c = 0, d = 0;
   if (int rc = tma_error_ti(clear, &a)) return rc;
   if (int rc = tma_error_wide(clear, &b)) return rc;
   if (int rc = tma_error_fx(clear, &c)) return rc;
-  *flag = (a || b || c) ? 1 : 0;
+  if (int rc = tma_error_sliced(clear, &d)) return rc;
+  *flag = (a || b || c || d) ? 1 : 0;
   return PVSC_OK;
 }
 

@@ -241,9 +241,16 @@ __device__ __forceinline__ void tma_lds_blk(const unsigned char* buf, uint32_t B
 // kModelTIFx: the TI KPM sweep of sweep_fx.cu on fixed-point vectors (R/2
 // vectors in the byte layout of R complex64 vectors, one vector per thread,
 // the per-site coefficient pair in place of the potential, exact dot sums).
-template <int R, bool DEEP, int NW, int FEAT, int MODEL>
+// SL > 1: the block of R SL vectors is swept as SL slices of R vectors
+// (R = 16, the layout of the 8 x 8 tiles): block b takes slice b mod SL
+// (the grid is a multiple of SL), whose 128-byte rows the tensor maps select
+// by their innermost coordinate, and the units b / SL + lu G / SL of that
+// slice; the epilogue addresses the whole block.
+template <int R, bool DEEP, int NW, int FEAT, int MODEL, int SL = 1>
 __global__ void __launch_bounds__(32 * NW, 1)
     ti_sweep_tma(const __grid_constant__ Sweep p, const __grid_constant__ TmaMaps m) {
+  static_assert(SL == 1 || R == 16, "vector slices of 16 complex64 (8 fixed-point) vectors");
+  constexpr int RF = R * SL;  // vectors (complex64 layout) of the whole block
   constexpr bool WSM = MODEL == 3;
   constexpr bool FX = MODEL == kModelTIFx;
   // fixed point with R/2 >= 8 vectors: a quarter-warp reads one whole 128-byte
@@ -276,14 +283,17 @@ __global__ void __launch_bounds__(32 * NW, 1)
   const Geometry& g = p.g;
   const int Lx = (int)(g.L[0] / VPC), Ly = (int)g.L[1], Lz = (int)g.L[2];  // tile points along x
   const int64_t plane = (int64_t)Lx * Ly;
-  const int G = gridDim.x;
+  const int sl = SL > 1 ? (int)(blockIdx.x % SL) : 0;  // this block's vector slice
+  const int vb = SL > 1 ? (int)(blockIdx.x / SL) : (int)blockIdx.x;
+  const int G = gridDim.x / SL;  // blocks per slice
+  const int c0 = 32 * sl;       // the slice's rows: innermost tensor-map coordinate
   volatile int* abort = &s_abort;
-  // This block's units u = blockIdx.x + lu G (lu = 0 .. nlu-1), decoded once into
-  // a shared table, so that the per-plane copy logic does no division.
-  const int nlu = (int)((m.nunits - blockIdx.x + G - 1) / G);
+  // This block's units u = vb + lu G (lu = 0 .. nlu-1) of its slice, decoded once
+  // into a shared table, so that the per-plane copy logic does no division.
+  const int nlu = (int)((m.nunits - vb + G - 1) / G);
   uint2* tab = reinterpret_cast<uint2*>(base + L::TAB_OFF);
   for (int i = threadIdx.x; i < nlu; i += blockDim.x) {
-    const int64_t u = blockIdx.x + (int64_t)i * G;
+    const int64_t u = vb + (int64_t)i * G;
     const int64_t ntiles = (int64_t)m.ntx * m.nty;
     const int64_t ch = u / ntiles, t = u - ch * ntiles, ty = t / m.ntx;
     const uint32_t x0 = (uint32_t)((t - ty * m.ntx) * TX), y0 = (uint32_t)(ty * TY);
@@ -332,11 +342,11 @@ __global__ void __launch_bounds__(32 * NW, 1)
     const uint32_t slot = k % L::NXS;
     const uint32_t dst = sbase + slot * L::XSTAGE;
     mbar_arrive_expect_tx(&full_x[slot], L::X_BYTES);
-    tma_load_5d(dst, &m.xi, 0, 0, x0, y0, zx, &full_x[slot]);
-    tma_load_5d(dst + L::OFF_XM, &m.xs, 0, 0, hxm, y0, zx, &full_x[slot]);
-    tma_load_5d(dst + L::OFF_XP, &m.xs, 0, 0, hxp, y0, zx, &full_x[slot]);
-    tma_load_5d(dst + L::OFF_YM, &m.ys, 0, 0, x0, hym, zx, &full_x[slot]);
-    tma_load_5d(dst + L::OFF_YP, &m.ys, 0, 0, x0, hyp, zx, &full_x[slot]);
+    tma_load_5d(dst, &m.xi, c0, 0, x0, y0, zx, &full_x[slot]);
+    tma_load_5d(dst + L::OFF_XM, &m.xs, c0, 0, hxm, y0, zx, &full_x[slot]);
+    tma_load_5d(dst + L::OFF_XP, &m.xs, c0, 0, hxp, y0, zx, &full_x[slot]);
+    tma_load_5d(dst + L::OFF_YM, &m.ys, c0, 0, x0, hym, zx, &full_x[slot]);
+    tma_load_5d(dst + L::OFF_YP, &m.ys, c0, 0, x0, hyp, zx, &full_x[slot]);
     atomicMax(&s_issued[0], k + 1);
   };
   const unsigned ybytes = (m.has_yin ? L::INT_B : 0) + (m.v_tma ? VF * L::V_B : 0);
@@ -347,7 +357,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
     const uint32_t dst = sbase + L::NXS * L::XSTAGE + slot * L::YSTAGE;
     if (ybytes) {
       mbar_arrive_expect_tx(&full_y[slot], ybytes);
-      if (m.has_yin) tma_load_5d(dst, &m.yi, 0, 0, x0, y0, z0 + j, &full_y[slot]);
+      if (m.has_yin) tma_load_5d(dst, &m.yi, c0, 0, x0, y0, z0 + j, &full_y[slot]);
       if (m.v_tma) tma_load_3d(dst + L::INT_B, &m.v, VF * x0, y0, z0 + j, &full_y[slot]);
     } else {
       mbar_arrive(&full_y[slot]);
@@ -388,8 +398,9 @@ __global__ void __launch_bounds__(32 * NW, 1)
 
   const int c = lane % L::CPS;
   const int q = lane / L::CPS;
+  const int cg = c + sl * L::CPS;  // the chunk (complex64) or vector (fixed point) in the block
   VecCoef<float, 2> cf;
-  if constexpr (!FX) cf = load_coef<float, 2>(p, c);
+  if constexpr (!FX) cf = load_coef<float, 2>(p, cg);
   DotAcc<float, 2> dacc;  // compensated fp32 sums; their fp64 part lives in shared memory
   dacc.init();
   // fixed point: exact per-unit dot sums of this thread's vector c, the
@@ -399,7 +410,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
   fx_acc_zero(fxy);
   const FxLimbs fkt = fx_split(FX ? p.fx_kt : 0);
   const int fdshift = p.fx_dshift ? 1 : 0;  // alpha = 2/a: coefficients doubled
-  const double fvs = FX ? p.vscale[c] : 0.0;
+  const double fvs = FX ? p.vscale[cg] : 0.0;
   double* wdots = reinterpret_cast<double*>(base + L::DOT_OFF) + warp * kNumDots * 2 * L::CPS;
   if constexpr (has_dots(FEAT)) {
     if (lane < L::CPS)
@@ -538,7 +549,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
             ys[2 * o] = fx_split(re);
             ys[2 * o + 1] = fx_split(im);
           }
-          store_blk<long long, 1>(static_cast<long long*>(p.yout), s, R / 2, c, yn);
+          store_blk<long long, 1>(static_cast<long long*>(p.yout), s, RF / 2, cg, yn);
           fx_dot_item(xs, ys, fxx, fxy);
           xmr[i] = xc;
         } else {
@@ -558,7 +569,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
                                      : site_potential_t<float>(g, 2 * s + 1);
             wsm_cell_update(cf, V0, V1, xmr[i], xc, xp, ax, bx, ay, by, m.has_yin ? &yi : nullptr, yn);
             const int64_t sites[4] = {2 * s, 2 * s, 2 * s + 1, 2 * s + 1};
-            epilogue<float, 2, FEAT>(p, s, c, xc, yn, dacc, sites);
+            epilogue<float, 2, FEAT>(p, s, cg, xc, yn, dacc, sites);
             xmr[i] = xc;
             continue;
           }
@@ -588,7 +599,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
           const float Vs = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i]) : site_potential_t<float>(g, s);
           ti_combine(cf, Vs, xc, S, D, m.has_yin ? &yi : nullptr, yn, g);
           const int64_t sites[4] = {s, s, s, s};
-          epilogue<float, 2, FEAT>(p, s, c, xc, yn, dacc, sites);
+          epilogue<float, 2, FEAT>(p, s, cg, xc, yn, dacc, sites);
           xmr[i] = xc;
         }
       }
@@ -622,16 +633,19 @@ __global__ void __launch_bounds__(32 * NW, 1)
     // blocks in finish_dots (after an abort the values are garbage, but the
     // arrival counter stays consistent)
     const double* wd = reinterpret_cast<const double*>(base + L::DOT_OFF);
-    constexpr int RV = FX ? R / 2 : R;  // vectors of the block
-    double* row = p.partials + (size_t)blockIdx.x * kNumDots * RV;
-    for (int t = threadIdx.x; t < kNumDots * RV; t += blockDim.x) {
-      const int d = t / RV, r = t - d * RV;
+    constexpr int RV = FX ? R / 2 : R;  // vectors of a slice
+    constexpr int RVF = RV * SL;        // of the block (zeros outside this block's slice)
+    double* row = p.partials + (size_t)blockIdx.x * kNumDots * RVF;
+    for (int t = threadIdx.x; t < kNumDots * RVF; t += blockDim.x) {
+      const int d = t / RVF, r = t - d * RVF - sl * RV;
       double sum = 0.0;
-      if constexpr (FX) {
-        if (d < 2)
-          for (int w = 0; w < NCW; ++w) sum += wd[w * kNumDots * 2 * L::CPS + d * L::CPS + r];
-      } else {
-        for (int w = 0; w < NCW; ++w) sum += wd[((w * kNumDots + d) * 2 + (r & 1)) * L::CPS + (r >> 1)];
+      if (r >= 0 && r < RV) {
+        if constexpr (FX) {
+          if (d < 2)
+            for (int w = 0; w < NCW; ++w) sum += wd[w * kNumDots * 2 * L::CPS + d * L::CPS + r];
+        } else {
+          for (int w = 0; w < NCW; ++w) sum += wd[((w * kNumDots + d) * 2 + (r & 1)) * L::CPS + (r >> 1)];
+        }
       }
       row[t] = sum;
     }
@@ -654,7 +668,7 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
-template <int R, bool DEEP, int MODEL = PVSC_TI>
+template <int R, bool DEEP, int MODEL = PVSC_TI, int SL = 1>
 static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
   using L = TmaLayout<R, DEEP, 8>;
   auto enc = encode_tiled();
@@ -664,9 +678,11 @@ static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
   // fixed-point sweep's per-site (d+, d-) pair of 64-bit coefficients
   const int vf = MODEL == kModelTIFx ? 4 : vpc;
   const cuuint64_t Lx = lat->g.L[0] / vpc, Ly = lat->g.L[1], Lz = lat->g.L[2];
-  const cuuint64_t dims[5] = {32, (cuuint64_t)L::ROWS, Lx, Ly, Lz};
-  const cuuint64_t strides[4] = {128, (cuuint64_t)L::SITE_B, (cuuint64_t)L::SITE_B * Lx,
-                                 (cuuint64_t)L::SITE_B * Lx * Ly};
+  // rows of 32 floats; with SL slices a row of the block holds SL slice rows side by
+  // side (the innermost coordinate selects one) and a site SL times the slice's bytes
+  const cuuint64_t SB = (cuuint64_t)L::SITE_B * SL;
+  const cuuint64_t dims[5] = {(cuuint64_t)32 * SL, (cuuint64_t)L::ROWS, Lx, Ly, Lz};
+  const cuuint64_t strides[4] = {(cuuint64_t)128 * SL, SB, SB * Lx, SB * Lx * Ly};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   // the kernel's addressing: unswizzled tiles for fixed point with R/2 >= 8 vectors
   const CUtensorMapSwizzle swz =
@@ -700,17 +716,17 @@ static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
   return PVSC_OK;
 }
 
-template <int R, bool DEEP, int NW, int MODEL>
+template <int R, bool DEEP, int NW, int MODEL, int SL = 1>
 static void* tma_kernel(int feat) {
   if constexpr (MODEL == kModelTIFx) {  // KPM sweeps only
-    return feat == F_DOTS ? reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS, MODEL>) : nullptr;
+    return feat == F_DOTS ? reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS, MODEL, SL>) : nullptr;
   } else {
     switch (feat) {
-      case 0: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, 0, MODEL>);
-      case F_DOTS: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS, MODEL>);
-      case F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_Z, MODEL>);
-      case F_DOTS | F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS | F_Z, MODEL>);
-      case F_ACC: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_ACC, MODEL>);
+      case 0: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, 0, MODEL, SL>);
+      case F_DOTS: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS, MODEL, SL>);
+      case F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_Z, MODEL, SL>);
+      case F_DOTS | F_Z: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS | F_Z, MODEL, SL>);
+      case F_ACC: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_ACC, MODEL, SL>);
       default: return nullptr;
     }
   }
@@ -733,10 +749,12 @@ static int auto_chunks(int64_t ntiles, int64_t Lz, int64_t grid) {
 }
 
 
-template <int R, bool DEEP, int NW, int MODEL = PVSC_TI>
+// SL > 1: the block of R SL vectors in SL slices of R (one slice per block; the
+// grid a multiple of SL, each slice's units spread over grid / SL blocks).
+template <int R, bool DEEP, int NW, int MODEL = PVSC_TI, int SL = 1>
 static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
   using L = TmaLayout<R, DEEP, NW, MODEL == kModelTIFx ? 4 : 2>;
-  void* fn = tma_kernel<R, DEEP, NW, MODEL>(feat);
+  void* fn = tma_kernel<R, DEEP, NW, MODEL, SL>(feat);
   if (!fn) return set_error(PVSC_ERR_UNSUPPORTED, "no TMA-staged sweep for feature set %d", feat);
   if (int rc = allow_max_smem(fn)) return rc;
   int occ = 0;
@@ -746,20 +764,21 @@ static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const Launc
   p.tile_x = L::TX;
   p.tile_y = L::TY;
   TmaMaps m;
-  if (int rc = encode_maps<R, DEEP, MODEL>(lat, p, m)) return rc;
+  if (int rc = encode_maps<R, DEEP, MODEL, SL>(lat, p, m)) return rc;
   const int64_t Lx = lat->g.L[0] / (MODEL == PVSC_WSM ? 2 : 1), Ly = lat->g.L[1], Lz = lat->g.L[2];
   m.ntx = (int)((Lx + L::TX - 1) / L::TX);
   m.nty = (int)((Ly + L::TY - 1) / L::TY);
   const int64_t ntiles = (int64_t)m.ntx * m.nty;
-  const int64_t grid_max = (int64_t)lat->sm_count * occ;
+  int64_t grid_max = (int64_t)lat->sm_count * occ / SL;  // blocks per slice
+  if (grid_max < 1) grid_max = 1;
   int nch = sh.zslab > 0 ? (int)((Lz + sh.zslab - 1) / sh.zslab) : auto_chunks(ntiles, Lz, grid_max);
   if (nch < 1) nch = 1;
   if (nch > Lz) nch = (int)Lz;
   while (nch > 1 && (ntiles * nch + grid_max - 1) / grid_max > kTmaMaxUnits) --nch;  // unit table
   m.nch = nch;
-  m.nunits = ntiles * nch;
+  m.nunits = ntiles * nch;  // per slice
   p.zslab = (int)((Lz + nch - 1) / nch);
-  const int grid = (int)(m.nunits < grid_max ? m.nunits : grid_max);
+  const int grid = (int)(SL * (m.nunits < grid_max ? m.nunits : grid_max));
   void* args[] = {&p, &m};
   PVSC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(32 * NW), args, L::SMEM, st));
   return PVSC_OK;

@@ -10,10 +10,13 @@ namespace pvsc {
 
 bool tma_tile_deep(int R, int tile_y);
 
+// work units on the smaller (deep-ring) tiles, the most there are; R = 16 and 32
+// (layouts of 32 and 64) run as 2 and 4 slices of 8 vectors on the tiles of layout 16
 template <int R2>
-static int64_t tma_fx_tiles(const Geometry& g) {  // the smaller (deep-ring) tiles: the most units
-  using L = TmaLayout<R2, true, 8, 4>;
-  return ((g.L[0] + L::TX - 1) / L::TX) * ((g.L[1] + L::TY - 1) / L::TY);
+static int64_t tma_fx_tiles(const Geometry& g) {
+  constexpr int RT = R2 > 16 ? 16 : R2, SL = R2 > 16 ? R2 / 16 : 1;
+  using L = TmaLayout<RT, true, 8, 4>;
+  return SL * ((g.L[0] + L::TX - 1) / L::TX) * ((g.L[1] + L::TY - 1) / L::TY);
 }
 
 bool tma_fx_possible(const pvsc_lattice* lat, int R) {
@@ -30,13 +33,14 @@ bool tma_fx_possible(const pvsc_lattice* lat, int R) {
 }
 
 // As the complex64 TI sweep: tile_y selects the large tile (two planes of
-// copies in flight) or half of it (three); threads = 512 runs the large tile
-// with one item per thread.  The block of R vectors uses the layout of 2R.
+// copies in flight) or half of it (three); threads = 512 runs the large
+// tile with one item per thread.  The block of R vectors uses the layout of 2R
+// (R = 16 and 32: slices of 8 vectors, each in the layout of 16).
 int launch_sweep_tma_fx(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
   if (!tma_fx_possible(lat, p.R))
     return set_error(PVSC_ERR_UNSUPPORTED, "the TMA-staged fixed-point sweep needs a TI lattice and R = 2 .. 32");
-  const bool deep = p.R <= 8 && tma_tile_deep(2 * p.R, sh.tile_y);
-  const bool wide = !deep && p.R <= 8 && sh.threads == 512;
+  const bool deep = tma_tile_deep(2 * p.R, sh.tile_y);
+  const bool wide = !deep && sh.threads == 512;
   constexpr int F = kModelTIFx;
   switch (p.R) {
     case 2:
@@ -51,10 +55,14 @@ int launch_sweep_tma_fx(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh
       return deep ? launch_tma_r<16, true, 8, F>(lat, F_DOTS, p, sh, st)
                   : (wide ? launch_tma_r<16, false, 16, F>(lat, F_DOTS, p, sh, st)
                           : launch_tma_r<16, false, 8, F>(lat, F_DOTS, p, sh, st));
-    case 16:
-      return launch_tma_r<32, false, 8, F>(lat, F_DOTS, p, sh, st);
-    default:
-      return launch_tma_r<64, false, 8, F>(lat, F_DOTS, p, sh, st);
+    case 16:  // two slices of 8 vectors
+      return deep ? launch_tma_r<16, true, 8, F, 2>(lat, F_DOTS, p, sh, st)
+                  : (wide ? launch_tma_r<16, false, 16, F, 2>(lat, F_DOTS, p, sh, st)
+                          : launch_tma_r<16, false, 8, F, 2>(lat, F_DOTS, p, sh, st));
+    default:  // four slices of 8 vectors
+      return deep ? launch_tma_r<16, true, 8, F, 4>(lat, F_DOTS, p, sh, st)
+                  : (wide ? launch_tma_r<16, false, 16, F, 4>(lat, F_DOTS, p, sh, st)
+                          : launch_tma_r<16, false, 8, F, 4>(lat, F_DOTS, p, sh, st));
   }
 }
 

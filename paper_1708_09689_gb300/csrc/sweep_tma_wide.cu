@@ -1,22 +1,16 @@
-// Instantiations of the TMA-staged sweep (sweep_tma.cuh) for TI lattices with
-// R = 32 and 64 (one tile each, one item per thread) and for the Weyl-semimetal
-// cells at every R (the large tile on 8 warps).  This unit's kernels report
+// Instantiations of the TMA-staged sweep (sweep_tma.cuh) for the Weyl-semimetal
+// cells at R = 4, 8, 16 (the large tile on 8 warps).  This unit's kernels report
 // copy-wait timeouts in its own error word.
 #include "sweep_tma.cuh"
 
 namespace pvsc {
 
 int launch_tma_wide(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
-  if (lat->g.model == PVSC_WSM) {
-    switch (p.R) {
-      case 4: return launch_tma_r<4, false, 8, PVSC_WSM>(lat, feat, p, sh, st);
-      case 8: return launch_tma_r<8, false, 8, PVSC_WSM>(lat, feat, p, sh, st);
-      case 16: return launch_tma_r<16, false, 8, PVSC_WSM>(lat, feat, p, sh, st);
-      case 32: return launch_tma_r<32, false, 8, PVSC_WSM>(lat, feat, p, sh, st);
-      default: return launch_tma_r<64, false, 8, PVSC_WSM>(lat, feat, p, sh, st);
-    }
+  switch (p.R) {
+    case 4: return launch_tma_r<4, false, 8, PVSC_WSM>(lat, feat, p, sh, st);
+    case 8: return launch_tma_r<8, false, 8, PVSC_WSM>(lat, feat, p, sh, st);
+    default: return launch_tma_r<16, false, 8, PVSC_WSM>(lat, feat, p, sh, st);
   }
-  return p.R == 32 ? launch_tma_r<32, false, 8>(lat, feat, p, sh, st) : launch_tma_r<64, false, 8>(lat, feat, p, sh, st);
 }
 
 int tma_error_wide(int clear, int* flag) {

@@ -123,7 +123,8 @@ CASES = [
     ((13, 9, 1), (0, 1, 1), 0),       # one plane, periodic z of length 1
 ]
 
-DEEP_TILE = {2: (16, 8), 4: (16, 4), 8: (8, 4)}  # the half tiles of the layout of 2R complex64 vectors
+# the half tiles of the layout of 2R complex64 vectors (R = 16, 32: slices of 8 vectors in the layout of 16)
+DEEP_TILE = {2: (16, 8), 4: (16, 4), 8: (8, 4), 16: (8, 4), 32: (8, 4)}
 
 
 def _variant(R, v):
@@ -133,8 +134,7 @@ def _variant(R, v):
 
 
 @pytest.mark.parametrize("dims,per,zs", CASES)
-@pytest.mark.parametrize("R,variant", [(R, v) for R in (2, 4, 8) for v in ("large", "wide", "deep")] +
-                         [(16, "large"), (32, "large")])
+@pytest.mark.parametrize("R,variant", [(R, v) for R in (2, 4, 8, 16, 32) for v in ("large", "wide", "deep")])
 def test_q64_tma_sweep_matches_zmarch_and_oracle(dims, per, zs, R, variant):
     n = int(np.prod(dims))
     V = W.disorder_potential(n, 2.0, 7)

@@ -1,4 +1,5 @@
-"""The TI sweep with TMA-staged plane tiles (tuning kernel 7, complex64, R = 4 .. 64).
+"""The TI sweep with TMA-staged plane tiles (tuning kernel 7, complex64, R = 4 .. 64;
+R = 32 and 64 as slices of 16 vectors).
 
 Its stencil arithmetic is the register z-march's, in the same order, so the
 vectors it writes must equal the default sweep's bit for bit; they are also
@@ -41,7 +42,8 @@ def _lattice(dims, per, vmode, delta):
     return pv.Lattice.ti(dims, per, **kw), np.zeros(n)
 
 
-DEEP_TILE = {4: (16, 8), 8: (16, 4), 16: (8, 4)}   # the half tiles with three planes in flight
+# the half tiles with three planes in flight (R = 32, 64: slices of 16 vectors on the tiles of R = 16)
+DEEP_TILE = {4: (16, 8), 8: (16, 4), 16: (8, 4), 32: (8, 4), 64: (8, 4)}
 
 
 def _variant(R, v):
@@ -53,8 +55,7 @@ def _variant(R, v):
 
 
 @pytest.mark.parametrize("dims,per,zs", CASES)
-@pytest.mark.parametrize("R,variant", [(R, v) for R in (4, 8, 16) for v in ("large", "wide", "deep")] +
-                         [(32, "large"), (64, "large")])
+@pytest.mark.parametrize("R,variant", [(R, v) for R in (4, 8, 16, 32, 64) for v in ("large", "wide", "deep")])
 def test_tma_sweep_equals_default_sweep_and_oracle(dims, per, zs, R, variant):
     lat, V = _lattice(dims, per, "stored", False)
     H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
@@ -68,8 +69,7 @@ def test_tma_sweep_equals_default_sweep_and_oracle(dims, per, zs, R, variant):
 
 
 @pytest.mark.parametrize("vmode,delta", [("stored", True), ("fly", False), ("zero", True)])
-@pytest.mark.parametrize("R,variant", [(R, v) for R in (4, 8, 16) for v in ("large", "wide")] +
-                         [(32, "large"), (64, "large")])
+@pytest.mark.parametrize("R,variant", [(R, v) for R in (4, 8, 16, 32, 64) for v in ("large", "wide")])
 def test_tma_fused_step_with_z_and_dots(vmode, delta, R, variant):
     dims, per = (24, 16, 5), (1, 0, 1)
     lat, V = _lattice(dims, per, vmode, delta)
@@ -104,8 +104,7 @@ def test_tma_fused_step_with_z_and_dots(vmode, delta, R, variant):
 
 
 @pytest.mark.parametrize("dims,per,zs", CASES[:3])
-@pytest.mark.parametrize("R,variant", [(R, v) for R in (4, 8, 16) for v in ("large", "wide", "deep")] +
-                         [(32, "large"), (64, "large")])
+@pytest.mark.parametrize("R,variant", [(R, v) for R in (4, 8, 16, 32, 64) for v in ("large", "wide", "deep")])
 def test_tma_kpm_moments_match_oracle_and_default(dims, per, zs, R, variant):
     lat, V = _lattice(dims, per, "stored", False)
     H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
