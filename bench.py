@@ -353,7 +353,8 @@ def _hbm_roof(bytes_per_lup, lups, ms, kernel):
 
 TI_KERNEL_NAMES = {0: "ti_sweep (z-march)", 1: "ti_sweep_flat", 2: "ti_sweep (cp.async ring)",
                    3: "ti_sweep (deep cp.async ring)", 4: "ti_kpm2_sweep", 5: "ti_sweep (column tiles)",
-                   6: "ti_sweep_xmarch", 7: "ti_sweep_tma (TMA-staged plane tiles)"}
+                   6: "ti_sweep_xmarch", 7: "ti_sweep_tma (TMA-staged plane tiles)",
+                   8: "ti_sweep_tma (TMA-staged tiles marching along x)"}
 
 
 def ti_kernel_name(tuning: dict, what: str) -> str:
@@ -795,6 +796,10 @@ def main():
         bytes_per_lup = 96.0 + 4.0 / R
         launches = sweeps
         kname = f"ti_sweep_tma<{R},F_DOTS> (complex64 KPM sweep, TMA-staged plane tiles)"
+    elif bool(tuning) and tuning.get("kernel") == 8:
+        bytes_per_lup = 96.0 + 4.0 / R
+        launches = sweeps
+        kname = f"ti_sweep_tma_xm<{R},F_DOTS> (complex64 KPM sweep, TMA-staged tiles marching along x)"
     elif bool(tuning) and tuning.get("kernel") == 6:
         bytes_per_lup = 96.0 + 4.0 / R
         launches = sweeps

@@ -202,6 +202,13 @@ extern "C" int pvsc_autotune_op(pvsc_lattice* lat, int R, int prec, int op, pvsc
           cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, deep_x, deep_y, kKernelTma});
         }
       }
+    // the same tiles marching along x, where the z columns are the shorter
+    if (lat->g.L[0] > lat->g.L[2] && tma_xm_possible(lat, R, prec))
+      for (int zs : {0, 32, 64})
+        if (zs == 0 || zs < lat->g.L[0]) {
+          cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, 0, 0, kKernelTmaX});
+          cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, deep_x, deep_y, kKernelTmaX});
+        }
   }
   if (lat->g.model == PVSC_TI)
     for (int th : {128, 256}) {

@@ -119,8 +119,10 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
     sh = LaunchShape{};
     sh.zslab = zs;
   }
-  if (sh.kernel == kKernelTma) {
+  if (sh.kernel == kKernelTma || sh.kernel == kKernelTmaX) {
     p.tile_x = p.tile_y = 0;
+    if (sh.kernel == kKernelTmaX && tma_xm_possible(lat, p.R, prec) && !(feat & F_ADJ))
+      return launch_sweep_tma_xm(lat, feat, p, sh, st);
     if (tma_sweep_possible(lat, p.R, prec) && !(feat & F_ADJ)) return launch_sweep_tma(lat, feat, p, sh, st);
     sh = LaunchShape{};  // complex128 (or a shape it does not cover) on a lattice tuned for complex64
   }
@@ -1012,13 +1014,19 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
     return PVSC_OK;
   }
   if (tuning->vpt < 0 || tuning->vpt > 2) return set_error(PVSC_ERR_ARG, "vpt must be 0, 1 or 2");
-  if (tuning->kernel < 0 || tuning->kernel > 7) return set_error(PVSC_ERR_ARG, "kernel must be 0 .. 7");
-  if (tuning->kernel == kKernelTma) {
-    if (!tma_sweep_possible(lat, R, prec))
+  if (tuning->kernel < 0 || tuning->kernel > 8) return set_error(PVSC_ERR_ARG, "kernel must be 0 .. 8");
+  if (tuning->kernel == kKernelTma || tuning->kernel == kKernelTmaX) {
+    const int k = tuning->kernel;
+    if (k == kKernelTma && !tma_sweep_possible(lat, R, prec))
       return set_error(PVSC_ERR_ARG, "kernel 7 (TMA-staged tiles) needs a TI or Weyl lattice, complex64, R >= 4 "
                        "and Lx a multiple of 4");
+    if (k == kKernelTmaX && !tma_xm_possible(lat, R, prec))
+      return set_error(PVSC_ERR_ARG, "kernel 8 (TMA-staged tiles marching along x) needs a TI lattice, "
+                       "complex64, R >= 4 and Lx a multiple of 4");
+    if (k == kKernelTmaX && tuning->threads == 512)
+      return set_error(PVSC_ERR_ARG, "kernel 8 runs eight warps (threads 256)");
     if (!tma_tile_valid(R, tuning->tile_x, tuning->tile_y))
-      return set_error(PVSC_ERR_ARG, "kernel 7 takes no tile other than the two of R = %d (%dx%d given)", R,
+      return set_error(PVSC_ERR_ARG, "kernel %d takes no tile other than the two of R = %d (%dx%d given)", k, R,
                        tuning->tile_x, tuning->tile_y);
     if (tuning->blocks_per_sm < 0 || tuning->zslab < 0) return set_error(PVSC_ERR_ARG, "negative tuning value");
     lat->tuning[{R, prec}] = *tuning;

@@ -94,11 +94,16 @@ constexpr int kKernelKpm2 = 4;
 constexpr int kKernelTiles = 5;
 // TI sweep marching along x instead of z (short z extents)
 constexpr int kKernelXMarch = 6;
-// TI sweep with TMA-staged z-plane tiles and warp specialisation (sweep_tma.cu):
-// complex64, R = 4, 8 or 16, Lx a multiple of 4
+// TI (and Weyl-cell) sweep with TMA-staged z-plane tiles (sweep_tma.cu):
+// complex64, R = 4 .. 64, Lx a multiple of 4
 constexpr int kKernelTma = 7;
 bool tma_sweep_possible(const pvsc_lattice* lat, int R, int prec);
 int launch_sweep_tma(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st);
+// the same tiles marching along x (tiles over (y, z) columns): TI, complex64; the
+// fused step with z falls back to kernel 7
+constexpr int kKernelTmaX = 8;
+bool tma_xm_possible(const pvsc_lattice* lat, int R, int prec);
+int launch_sweep_tma_xm(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st);
 int tma_error(int clear, int* flag);
 // fixed-point (PVSC_Q64) KPM sweep on TMA-staged tiles (sweep_tma_fx.cu)
 bool tma_fx_possible(const pvsc_lattice* lat, int R);

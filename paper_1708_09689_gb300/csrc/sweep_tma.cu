@@ -14,6 +14,9 @@ int launch_tma_sliced(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchS
 int tma_error_ti(int clear, int* flag);
 int tma_error_wide(int clear, int* flag);
 int tma_error_sliced(int clear, int* flag);
+int launch_tma_xm(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st);
+bool tma_xm_feature(int feat);
+int tma_error_xm(int clear, int* flag);
 
 // work units of a sweep on the smaller (deep-ring) tiles, the most there are; R = 32
 // and 64 run as 2 and 4 slices of the 16-vector tiles
@@ -78,13 +81,32 @@ int launch_sweep_tma(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchSh
   return launch_tma_ti(lat, feat, p, sh, st);
 }
 
+// Marching along x: tiles over the (y, z) columns, the same unit-table limits.
+bool tma_xm_possible(const pvsc_lattice* lat, int R, int prec) {
+  const Geometry& g = lat->g;
+  if (g.model != PVSC_TI || !tma_sweep_possible(lat, R, prec)) return false;
+  constexpr int TXd = TmaLayout<16, true, 8>::TX, TYd = TmaLayout<16, true, 8>::TY;  // the smallest tiles
+  const int64_t SL = R > 16 ? R / 16 : 1;
+  const int64_t ntiles = SL * ((g.L[1] + TXd - 1) / TXd) * ((g.L[2] + TYd - 1) / TYd);
+  return ntiles <= (int64_t)kTmaMaxUnits * lat->sm_count;
+}
+
+int launch_sweep_tma_xm(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
+  if (!tma_xm_possible(lat, p.R, PVSC_C64))
+    return set_error(PVSC_ERR_UNSUPPORTED, "kernel 8 (TMA-staged tiles marching along x) needs a complex64 TI "
+                     "lattice, R >= 4 and Lx a multiple of 4");
+  if (!tma_xm_feature(feat)) return launch_sweep_tma(lat, feat, p, sh, st);  // the fused step with z
+  return launch_tma_xm(lat, feat, p, sh, st);
+}
+
 int tma_error(int clear, int* flag) {
-  int a = 0, b = 0, c = 0, d = 0;
+  int a = 0, b = 0, c = 0, d = 0, e = 0;
   if (int rc = tma_error_ti(clear, &a)) return rc;
   if (int rc = tma_error_wide(clear, &b)) return rc;
   if (int rc = tma_error_fx(clear, &c)) return rc;
   if (int rc = tma_error_sliced(clear, &d)) return rc;
-  *flag = (a || b || c || d) ? 1 : 0;
+  if (int rc = tma_error_xm(clear, &e)) return rc;
+  *flag = (a || b || c || d || e) ? 1 : 0;
   return PVSC_OK;
 }
 

@@ -246,10 +246,17 @@ __device__ __forceinline__ void tma_lds_blk(const unsigned char* buf, uint32_t B
 // (the grid is a multiple of SL), whose 128-byte rows the tensor maps select
 // by their innermost coordinate, and the units b / SL + lu G / SL of that
 // slice; the epilogue addresses the whole block.
-template <int R, bool DEEP, int NW, int FEAT, int MODEL, int SL = 1>
+// XM (TI, complex64): march along the lattice's x axis: the kernel's tile axes
+// (X, Y) and march axis Z are the lattice's (y, z) and x (the tensor maps take
+// the permuted strides), for lattices whose z columns are short; the neighbour
+// pairs are folded in the z-march's order (z, x, y), so the vectors stay equal
+// to the z-march's bit for bit; the potential is read per site (its plane is
+// not a tile of a contiguous row).
+template <int R, bool DEEP, int NW, int FEAT, int MODEL, int SL = 1, bool XM = false>
 __global__ void __launch_bounds__(32 * NW, 1)
     ti_sweep_tma(const __grid_constant__ Sweep p, const __grid_constant__ TmaMaps m) {
   static_assert(SL == 1 || R == 16, "vector slices of 16 complex64 (8 fixed-point) vectors");
+  static_assert(!XM || MODEL == PVSC_TI, "marching along x: TI sites, complex64");
   constexpr int RF = R * SL;  // vectors (complex64 layout) of the whole block
   constexpr bool WSM = MODEL == 3;
   constexpr bool FX = MODEL == kModelTIFx;
@@ -281,8 +288,12 @@ __global__ void __launch_bounds__(32 * NW, 1)
   __syncthreads();
 
   const Geometry& g = p.g;
-  const int Lx = (int)(g.L[0] / VPC), Ly = (int)g.L[1], Lz = (int)g.L[2];  // tile points along x
-  const int64_t plane = (int64_t)Lx * Ly;
+  // the kernel's tile axes X, Y and march axis Z: the lattice's (x, y, z) (x in
+  // tile points), or (y, z, x) when marching along x
+  const int LX = (int)(g.L[0] / VPC), LY = (int)g.L[1], LZ = (int)g.L[2];
+  const int Lx = XM ? LY : LX, Ly = XM ? LZ : LY, Lz = XM ? LX : LZ;
+  const int perX = XM ? g.per[1] : g.per[0], perY = XM ? g.per[2] : g.per[1], perZ = XM ? g.per[0] : g.per[2];
+  const int64_t plane = XM ? 1 : (int64_t)Lx * Ly;  // site stride of one step along Z
   const int sl = SL > 1 ? (int)(blockIdx.x % SL) : 0;  // this block's vector slice
   const int vb = SL > 1 ? (int)(blockIdx.x / SL) : (int)blockIdx.x;
   const int G = gridDim.x / SL;  // blocks per slice
@@ -333,12 +344,12 @@ __global__ void __launch_bounds__(32 * NW, 1)
     const int x0 = (int)(e.x & 0xffffu), y0 = (int)(e.x >> 16), z0 = (int)(e.y & 0xffffu);
     const int TXe = min(TX, Lx - x0), TYe = min(TY, Ly - y0);
     // halo coordinates: wrapped on a periodic axis, out of range (zeros) past an open edge
-    const int hxm = x0 > 0 ? x0 - 1 : (g.per[0] ? Lx - 1 : -1);
-    const int hxp = x0 + TXe < Lx ? x0 + TXe : (g.per[0] ? 0 : Lx);
-    const int hym = y0 > 0 ? y0 - 1 : (g.per[1] ? Ly - 1 : -1);
-    const int hyp = y0 + TYe < Ly ? y0 + TYe : (g.per[1] ? 0 : Ly);
+    const int hxm = x0 > 0 ? x0 - 1 : (perX ? Lx - 1 : -1);
+    const int hxp = x0 + TXe < Lx ? x0 + TXe : (perX ? 0 : Lx);
+    const int hym = y0 > 0 ? y0 - 1 : (perY ? Ly - 1 : -1);
+    const int hyp = y0 + TYe < Ly ? y0 + TYe : (perY ? 0 : Ly);
     int zx = z0 + j;
-    if (g.per[2]) zx = zx < 0 ? zx + Lz : (zx >= Lz ? zx - Lz : zx);
+    if (perZ) zx = zx < 0 ? zx + Lz : (zx >= Lz ? zx - Lz : zx);
     const uint32_t slot = k % L::NXS;
     const uint32_t dst = sbase + slot * L::XSTAGE;
     mbar_arrive_expect_tx(&full_x[slot], L::X_BYTES);
@@ -468,7 +479,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
       Bym[i] = tma_swz<R, SWZ>(ly > 0 ? (li - TX) * SB : L::OFF_YM + lx * SB, c);
       Byp[i] = tma_swz<R, SWZ>(ly + 1 < TYe ? (li + TX) * SB : L::OFF_YP + lx * SB, c);
       Vo[i] = L::INT_B + 4 * VF * li;
-      col[i] = (int64_t)(x0 + lx) + (int64_t)Lx * (y0 + ly);
+      col[i] = XM ? (int64_t)LX * ((x0 + lx) + (int64_t)LY * (y0 + ly)) : (int64_t)(x0 + lx) + (int64_t)Lx * (y0 + ly);
     }
     // plane z0 - 1: x(z-1) of every site into registers
     if (!tma_wait(&full_x[kx % L::NXS], (kx / L::NXS) & 1, abort)) {
@@ -576,22 +587,42 @@ __global__ void __launch_bounds__(32 * NW, 1)
           // the axes in ti_axes' order (z pair, x pair, y pair), each pair loaded
           // just before it is folded in, so that few blocks are live at a time
           Blk<float, 2> S, D, yn;
-          {
-            Blk<float, 2> xp;
-            tma_lds_blk<R>(s1, Bc[i], xp);
-            axis_z_init(xmr[i], xp, S, D);
-          }
-          {
-            Blk<float, 2> ax, bx;
-            tma_lds_blk<R>(s0, Bxm[i], ax);
-            tma_lds_blk<R>(s0, Bxp[i], bx);
-            axis_x_add(ax, bx, S, D);
-          }
-          {
-            Blk<float, 2> ay, by;
-            tma_lds_blk<R>(s0, Bym[i], ay);
-            tma_lds_blk<R>(s0, Byp[i], by);
-            axis_y_add(ay, by, S, D);
+          if constexpr (XM) {  // lattice z = the Y halos, x = the march, y = the X halos
+            {
+              Blk<float, 2> zm, zp;
+              tma_lds_blk<R>(s0, Bym[i], zm);
+              tma_lds_blk<R>(s0, Byp[i], zp);
+              axis_z_init(zm, zp, S, D);
+            }
+            {
+              Blk<float, 2> xp;
+              tma_lds_blk<R>(s1, Bc[i], xp);
+              axis_x_add(xmr[i], xp, S, D);
+            }
+            {
+              Blk<float, 2> ay, by;
+              tma_lds_blk<R>(s0, Bxm[i], ay);
+              tma_lds_blk<R>(s0, Bxp[i], by);
+              axis_y_add(ay, by, S, D);
+            }
+          } else {
+            {
+              Blk<float, 2> xp;
+              tma_lds_blk<R>(s1, Bc[i], xp);
+              axis_z_init(xmr[i], xp, S, D);
+            }
+            {
+              Blk<float, 2> ax, bx;
+              tma_lds_blk<R>(s0, Bxm[i], ax);
+              tma_lds_blk<R>(s0, Bxp[i], bx);
+              axis_x_add(ax, bx, S, D);
+            }
+            {
+              Blk<float, 2> ay, by;
+              tma_lds_blk<R>(s0, Bym[i], ay);
+              tma_lds_blk<R>(s0, Byp[i], by);
+              axis_y_add(ay, by, S, D);
+            }
           }
           Blk<float, 2> xc, yi;
           tma_lds_blk<R>(s0, Bc[i], xc);
@@ -668,7 +699,7 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
-template <int R, bool DEEP, int MODEL = PVSC_TI, int SL = 1>
+template <int R, bool DEEP, int MODEL = PVSC_TI, int SL = 1, bool XM = false>
 static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
   using L = TmaLayout<R, DEEP, 8>;
   auto enc = encode_tiled();
@@ -681,8 +712,10 @@ static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
   // rows of 32 floats; with SL slices a row of the block holds SL slice rows side by
   // side (the innermost coordinate selects one) and a site SL times the slice's bytes
   const cuuint64_t SB = (cuuint64_t)L::SITE_B * SL;
-  const cuuint64_t dims[5] = {(cuuint64_t)32 * SL, (cuuint64_t)L::ROWS, Lx, Ly, Lz};
-  const cuuint64_t strides[4] = {(cuuint64_t)128 * SL, SB, SB * Lx, SB * Lx * Ly};
+  // the kernel's axes (X, Y, Z): (x, y, z), or (y, z, x) when marching along x
+  const cuuint64_t dims[5] = {(cuuint64_t)32 * SL, (cuuint64_t)L::ROWS, XM ? Ly : Lx, XM ? Lz : Ly, XM ? Lx : Lz};
+  const cuuint64_t strides[4] = {(cuuint64_t)128 * SL, XM ? SB * Lx : SB, XM ? SB * Lx * Ly : SB * Lx,
+                                 XM ? SB : SB * Lx * Ly};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   // the kernel's addressing: unswizzled tiles for fixed point with R/2 >= 8 vectors
   const CUtensorMapSwizzle swz =
@@ -702,7 +735,7 @@ static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
   m.has_yin = p.yin != nullptr;
   if (m.has_yin)
     if (int rc = tile5(&m.yi, p.yin, L::TX, L::TY)) return rc;
-  m.v_tma = MODEL == kModelTIFx ? 1 : lat->g.v_mode == 1;
+  m.v_tma = MODEL == kModelTIFx ? 1 : (!XM && lat->g.v_mode == 1);
   if (m.v_tma) {
     const cuuint64_t vd[3] = {vf * Lx, Ly, Lz};  // per site
     const cuuint64_t vs[2] = {4 * vf * Lx, 4 * vf * Lx * Ly};
@@ -716,10 +749,17 @@ static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
   return PVSC_OK;
 }
 
-template <int R, bool DEEP, int NW, int MODEL, int SL = 1>
+template <int R, bool DEEP, int NW, int MODEL, int SL = 1, bool XM = false>
 static void* tma_kernel(int feat) {
   if constexpr (MODEL == kModelTIFx) {  // KPM sweeps only
     return feat == F_DOTS ? reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS, MODEL, SL>) : nullptr;
+  } else if constexpr (XM) {  // the KPM, series and plain sweeps
+    switch (feat) {
+      case 0: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, 0, MODEL, SL, true>);
+      case F_DOTS: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_DOTS, MODEL, SL, true>);
+      case F_ACC: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, F_ACC, MODEL, SL, true>);
+      default: return nullptr;
+    }
   } else {
     switch (feat) {
       case 0: return reinterpret_cast<void*>(&ti_sweep_tma<R, DEEP, NW, 0, MODEL, SL>);
@@ -751,10 +791,12 @@ static int auto_chunks(int64_t ntiles, int64_t Lz, int64_t grid) {
 
 // SL > 1: the block of R SL vectors in SL slices of R (one slice per block; the
 // grid a multiple of SL, each slice's units spread over grid / SL blocks).
-template <int R, bool DEEP, int NW, int MODEL = PVSC_TI, int SL = 1>
+// XM: marching along x (tiles over (y, z)); a feature set it has no kernel for
+// returns PVSC_ERR_UNSUPPORTED with nothing launched.
+template <int R, bool DEEP, int NW, int MODEL = PVSC_TI, int SL = 1, bool XM = false>
 static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
   using L = TmaLayout<R, DEEP, NW, MODEL == kModelTIFx ? 4 : 2>;
-  void* fn = tma_kernel<R, DEEP, NW, MODEL, SL>(feat);
+  void* fn = tma_kernel<R, DEEP, NW, MODEL, SL, XM>(feat);
   if (!fn) return set_error(PVSC_ERR_UNSUPPORTED, "no TMA-staged sweep for feature set %d", feat);
   if (int rc = allow_max_smem(fn)) return rc;
   int occ = 0;
@@ -764,8 +806,9 @@ static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const Launc
   p.tile_x = L::TX;
   p.tile_y = L::TY;
   TmaMaps m;
-  if (int rc = encode_maps<R, DEEP, MODEL, SL>(lat, p, m)) return rc;
-  const int64_t Lx = lat->g.L[0] / (MODEL == PVSC_WSM ? 2 : 1), Ly = lat->g.L[1], Lz = lat->g.L[2];
+  if (int rc = encode_maps<R, DEEP, MODEL, SL, XM>(lat, p, m)) return rc;
+  const int64_t LX = lat->g.L[0] / (MODEL == PVSC_WSM ? 2 : 1), LY = lat->g.L[1], LZ = lat->g.L[2];
+  const int64_t Lx = XM ? LY : LX, Ly = XM ? LZ : LY, Lz = XM ? LX : LZ;  // the kernel's axes
   m.ntx = (int)((Lx + L::TX - 1) / L::TX);
   m.nty = (int)((Ly + L::TY - 1) / L::TY);
   const int64_t ntiles = (int64_t)m.ntx * m.nty;

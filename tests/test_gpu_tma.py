@@ -191,3 +191,77 @@ def test_tma_weyl_cells_equal_the_cell_sweeps_and_oracle(dims, per, R):
     yb, zb = yin.clone(), z0.clone()
     pv.cheb_step(lat, x, yb, [0.2] * R, [0.1] * R, [-1.0] * R, z=zb, delta=[0.5] * R, dots=7)
     assert torch.equal(ya, yb) and torch.equal(za, zb)
+
+
+# Kernel 8: the same tiles marching along x (tiles over the (y, z) columns), for
+# lattices whose z columns are short; x is the march axis, so its length is free.
+XM_CASES = [
+    ((24, 16, 6), (1, 1, 0), 0),
+    ((20, 12, 5), (1, 1, 1), 7),      # partial tiles along y and z, x-chunks of 7
+    ((16, 9, 3), (0, 0, 0), 1),       # open everywhere, one-plane chunks
+    ((8, 2, 1), (1, 1, 1), 0),        # z of length 1 (its own neighbour), y of length 2
+    ((12, 1, 8), (1, 1, 0), 3),       # y of length 1
+    ((4, 9, 10), (1, 0, 1), 0),       # x of length 4 (shorter than the columns)
+]
+
+
+@pytest.mark.parametrize("dims,per,zs", XM_CASES)
+@pytest.mark.parametrize("R,variant", [(R, v) for R in (4, 8, 16, 32, 64) for v in ("large", "deep")])
+def test_tma_x_march_equals_default_sweep_and_oracle(dims, per, zs, R, variant):
+    lat, V = _lattice(dims, per, "stored", False)
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
+    x = torch.from_numpy(W.gaussian_block(H.shape[0], R, 1)).to("cuda", torch.complex64)
+    y0 = pv.apply_H(lat, x)
+    lat.set_tuning(R, pv.C64, kernel=8, zslab=zs, **_variant(R, variant))
+    y1 = pv.apply_H(lat, x)
+    assert torch.equal(y0, y1)
+    ref = H @ x.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(y1.cpu().numpy() - ref) / np.linalg.norm(ref) < 2e-6
+    a, b = O.cheb_scale(*O.gershgorin(H))
+    r = W.random_phase_block(H.shape[0], R, 5)
+    r0 = torch.from_numpy(r).to("cuda", torch.complex64)
+    mu1 = pv.kpm_moments(lat, 40, a, b, r0=r0).cpu().numpy()
+    lat.set_tuning(R, pv.C64, threads=128, kernel=0)
+    mu0 = pv.kpm_moments(lat, 40, a, b, r0=r0).cpu().numpy()
+    assert np.max(np.abs(mu1 - mu0)) < 1e-9
+    assert pv.device_error() == 0
+
+
+@pytest.mark.parametrize("vmode,delta", [("stored", True), ("fly", False), ("zero", True)])
+def test_tma_x_march_series_and_the_step_with_z(vmode, delta):
+    dims, per, R = (24, 8, 6), (1, 0, 1), 16
+    lat, V = _lattice(dims, per, vmode, delta)
+    H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V, 0.3 if delta else 0.0, -0.2 if delta else 0.0)
+    D = H.shape[0]
+    _, _, a, b = lat.spectral_bounds()
+    x = W.gaussian_block(D, R, 3)
+    x /= np.linalg.norm(x, axis=0)
+    psi0 = torch.from_numpy(x).cuda()
+    outs = []
+    for kernel in (0, 8):
+        lat.set_tuning(R, pv.C64, threads=128 if kernel == 0 else 256, kernel=kernel)
+        psi = psi0.clone()
+        pv.cheb_propagate(lat, psi, 0.6, 3, a, b, prec=pv.C64)  # series sweeps with the accumulator
+        xc = torch.from_numpy(W.gaussian_block(D, R, 2)).to("cuda", torch.complex64)
+        yin = torch.from_numpy(W.gaussian_block(D, R, 4)).to("cuda", torch.complex64)
+        zin = torch.from_numpy(W.gaussian_block(D, R, 6)).to("cuda", torch.complex64)
+        pv.cheb_step(lat, xc, yin, [0.2] * R, [0.1] * R, [-1.0] * R, z=zin, delta=[0.5] * R, dots=7)
+        outs.append((psi, yin, zin))
+    assert torch.equal(outs[0][1], outs[1][1]) and torch.equal(outs[0][2], outs[1][2])
+    assert torch.equal(outs[0][0], outs[1][0])
+    ref = O.propagate(H, x, 0.6, 3, a, b)
+    assert np.linalg.norm(outs[1][0].cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_tma_x_march_is_validated():
+    lat = pv.Lattice.ti((16, 8, 4), (1, 1, 0))
+    with pytest.raises(pv.PvscError, match="kernel 8"):
+        lat.set_tuning(8, pv.C64, kernel=8, threads=512)
+    with pytest.raises(pv.PvscError, match="kernel 8"):
+        lat.set_tuning(8, pv.C128, kernel=8)
+    with pytest.raises(pv.PvscError, match="kernel 8"):
+        pv.Lattice.wsm((16, 4, 4), (1, 1, 0)).set_tuning(8, pv.C64, kernel=8)
+    with pytest.raises(pv.PvscError, match="kernel must be"):
+        lat.set_tuning(8, pv.C64, kernel=9)
+    lat.set_tuning(8, pv.C64, kernel=8, tile_x=16, tile_y=4)
+    assert lat.get_tuning(8, pv.C64)["kernel"] == 8
