@@ -158,6 +158,11 @@ __device__ __forceinline__ unsigned release_count(unsigned* ctr) {
   return old;
 }
 
+// L2 prefetch of one global line (a hint; the address is a valid element).
+__device__ __forceinline__ void prefetch_l2(const void* ptr) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -517,6 +522,20 @@ __global__ void __launch_bounds__(32 * NW, 1)
       for (int i = 0; i < IPT; ++i) {
         if (!ok[i]) continue;
         const int64_t s = col[i] + plane * z;
+        if constexpr ((FEAT & F_ACC) != 0) {
+          // the accumulator (and source) lines of this site two planes ahead into
+          // L2, so that the epilogue's fp64 reads do not wait on HBM; one thread
+          // per 128-byte line of its chunks
+          if (z + 2 < Lz && (cg & 3) == 0) {
+            const int64_t s2 = s + 2 * plane;
+            const bool rd = !(p.acc_mode & ACC_INIT), rs = (p.acc_mode & ACC_XSRC) != 0;
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+              if (rd) prefetch_l2(acc_ptr(p.acc, s2, o, RF, 2 * cg));
+              if (rs) prefetch_l2(acc_ptr(const_cast<double2*>(p.src), s2, o, RF, 2 * cg));
+            }
+          }
+        }
         if constexpr (FX) {
           // the fixed-point update of sweep_fx.cu: y = d x + kt T (- y_in), exact
           // with one rounding, then the exact dot sums of the site
