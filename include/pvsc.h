@@ -539,10 +539,10 @@ typedef struct {
                   /* 8x4 for R = 4 .. 64) selects rings one plane deeper on eight warps */
                   /* (TI; Weyl cells run the large tile on eight warps); zslab = z-chunk */
                   /* depth (0: chosen from the grid size); vpt is ignored. */
-                  /* 8 (TI, complex64, as kernel 7) the same tiles marching along x over */
-                  /* (y, z) columns, for lattices whose z columns are short; eight warps, */
-                  /* the large or the half tile; zslab = x-chunk depth; same vectors as */
-                  /* the z-march bit for bit; the fused step with z runs kernel 7. */
+                  /* 8 (as kernel 7) the same tiles marching along x over (y, z) columns, */
+                  /* for lattices whose z columns are short; eight warps, the large or */
+                  /* (TI) the half tile; zslab = x-chunk depth; same vectors as the */
+                  /* z-march bit for bit; the fused step with z runs kernel 7. */
                   /* PVSC_Q64 (KPM on TI lattices) takes kernels 0, 2, 3 (threads a */
                   /* multiple of R, one vector per thread, no tile) and 7 for R = 2 .. 32 */
                   /* (any Lx): the tiles, rings and variants of the complex64 layout */

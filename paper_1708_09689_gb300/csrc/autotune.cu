@@ -207,7 +207,7 @@ extern "C" int pvsc_autotune_op(pvsc_lattice* lat, int R, int prec, int op, pvsc
       for (int zs : {0, 32, 64})
         if (zs == 0 || zs < lat->g.L[0]) {
           cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, 0, 0, kKernelTmaX});
-          cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, deep_x, deep_y, kKernelTmaX});
+          if (lat->g.model == PVSC_TI) cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, deep_x, deep_y, kKernelTmaX});
         }
   }
   if (lat->g.model == PVSC_TI)

@@ -1021,10 +1021,12 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
       return set_error(PVSC_ERR_ARG, "kernel 7 (TMA-staged tiles) needs a TI or Weyl lattice, complex64, R >= 4 "
                        "and Lx a multiple of 4");
     if (k == kKernelTmaX && !tma_xm_possible(lat, R, prec))
-      return set_error(PVSC_ERR_ARG, "kernel 8 (TMA-staged tiles marching along x) needs a TI lattice, "
+      return set_error(PVSC_ERR_ARG, "kernel 8 (TMA-staged tiles marching along x) needs a TI or Weyl lattice, "
                        "complex64, R >= 4 and Lx a multiple of 4");
     if (k == kKernelTmaX && tuning->threads == 512)
       return set_error(PVSC_ERR_ARG, "kernel 8 runs eight warps (threads 256)");
+    if (k == kKernelTmaX && lat->g.model == PVSC_WSM && tuning->tile_y != 0 && tma_tile_deep(R, tuning->tile_y))
+      return set_error(PVSC_ERR_ARG, "kernel 8 runs the large tile on Weyl cells");
     if (!tma_tile_valid(R, tuning->tile_x, tuning->tile_y))
       return set_error(PVSC_ERR_ARG, "kernel %d takes no tile other than the two of R = %d (%dx%d given)", k, R,
                        tuning->tile_x, tuning->tile_y);

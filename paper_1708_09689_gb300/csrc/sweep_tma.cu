@@ -84,7 +84,7 @@ int launch_sweep_tma(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchSh
 // Marching along x: tiles over the (y, z) columns, the same unit-table limits.
 bool tma_xm_possible(const pvsc_lattice* lat, int R, int prec) {
   const Geometry& g = lat->g;
-  if (g.model != PVSC_TI || !tma_sweep_possible(lat, R, prec)) return false;
+  if (!tma_sweep_possible(lat, R, prec)) return false;  // TI sites or Weyl cells, complex64
   constexpr int TXd = TmaLayout<16, true, 8>::TX, TYd = TmaLayout<16, true, 8>::TY;  // the smallest tiles
   const int64_t SL = R > 16 ? R / 16 : 1;
   const int64_t ntiles = SL * ((g.L[1] + TXd - 1) / TXd) * ((g.L[2] + TYd - 1) / TYd);
@@ -94,7 +94,7 @@ bool tma_xm_possible(const pvsc_lattice* lat, int R, int prec) {
 int launch_sweep_tma_xm(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
   if (!tma_xm_possible(lat, p.R, PVSC_C64))
     return set_error(PVSC_ERR_UNSUPPORTED, "kernel 8 (TMA-staged tiles marching along x) needs a complex64 TI "
-                     "lattice, R >= 4 and Lx a multiple of 4");
+                     "or Weyl lattice, R >= 4 and Lx a multiple of 4");
   if (!tma_xm_feature(feat)) return launch_sweep_tma(lat, feat, p, sh, st);  // the fused step with z
   return launch_tma_xm(lat, feat, p, sh, st);
 }

@@ -251,7 +251,7 @@ __device__ __forceinline__ void tma_lds_blk(const unsigned char* buf, uint32_t B
 // (the grid is a multiple of SL), whose 128-byte rows the tensor maps select
 // by their innermost coordinate, and the units b / SL + lu G / SL of that
 // slice; the epilogue addresses the whole block.
-// XM (TI, complex64): march along the lattice's x axis: the kernel's tile axes
+// XM (TI sites or Weyl cells, complex64): march along the lattice's x axis: the kernel's tile axes
 // (X, Y) and march axis Z are the lattice's (y, z) and x (the tensor maps take
 // the permuted strides), for lattices whose z columns are short; the neighbour
 // pairs are folded in the z-march's order (z, x, y), so the vectors stay equal
@@ -261,7 +261,7 @@ template <int R, bool DEEP, int NW, int FEAT, int MODEL, int SL = 1, bool XM = f
 __global__ void __launch_bounds__(32 * NW, 1)
     ti_sweep_tma(const __grid_constant__ Sweep p, const __grid_constant__ TmaMaps m) {
   static_assert(SL == 1 || R == 16, "vector slices of 16 complex64 (8 fixed-point) vectors");
-  static_assert(!XM || MODEL == PVSC_TI, "marching along x: TI sites, complex64");
+  static_assert(!XM || MODEL == PVSC_TI || MODEL == PVSC_WSM, "marching along x: TI sites or Weyl cells");
   constexpr int RF = R * SL;  // vectors (complex64 layout) of the whole block
   constexpr bool WSM = MODEL == 3;
   constexpr bool FX = MODEL == kModelTIFx;
@@ -597,7 +597,10 @@ __global__ void __launch_bounds__(32 * NW, 1)
                                      : site_potential_t<float>(g, 2 * s);
             const float V1 = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i] + 4)
                                      : site_potential_t<float>(g, 2 * s + 1);
-            wsm_cell_update(cf, V0, V1, xmr[i], xc, xp, ax, bx, ay, by, m.has_yin ? &yi : nullptr, yn);
+            if constexpr (XM)  // lattice z = the Y halos, x cells = the march, y = the X halos
+              wsm_cell_update(cf, V0, V1, ay, xc, by, xmr[i], xp, ax, bx, m.has_yin ? &yi : nullptr, yn);
+            else
+              wsm_cell_update(cf, V0, V1, xmr[i], xc, xp, ax, bx, ay, by, m.has_yin ? &yi : nullptr, yn);
             const int64_t sites[4] = {2 * s, 2 * s, 2 * s + 1, 2 * s + 1};
             epilogue<float, 2, FEAT>(p, s, cg, xc, yn, dacc, sites);
             xmr[i] = xc;

@@ -1,11 +1,12 @@
 // Instantiations of the TMA-staged sweep (sweep_tma.cuh) marching along the
-// lattice's x axis (tuning kernel 8): tiles over (y, z) columns, for TI
-// lattices whose z columns are short (the cuboids of the dispersion and
+// lattice's x axis (tuning kernel 8): tiles over (y, z) columns, for lattices
+// whose z columns are short (the cuboids of the dispersion and
 // filter-diagonalisation runs, 6 to 8 planes, where a z-march pays two extra x
 // planes per few planes swept).  R = 4, 8, 16, and 32, 64 as slices of 16
-// vectors; the large tile and the half tile with deeper rings; the KPM, series
-// and plain sweeps (the fused step with z runs the z-march of kernel 7).  This
-// unit's kernels report copy-wait timeouts in its own error word.
+// vectors; TI sites on the large tile and the half tile with deeper rings,
+// Weyl cells on the large tile; the KPM, series and plain sweeps (the fused
+// step with z runs the z-march of kernel 7).  This unit's kernels report
+// copy-wait timeouts in its own error word.
 #include "sweep_tma.cuh"
 
 namespace pvsc {
@@ -14,6 +15,7 @@ bool tma_tile_deep(int R, int tile_y);
 
 template <int R, int SL>
 static int launch_xm(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
+  if (lat->g.model == PVSC_WSM) return launch_tma_r<R, false, 8, PVSC_WSM, SL, true>(lat, feat, p, sh, st);
   if (tma_tile_deep(R * SL, sh.tile_y)) return launch_tma_r<R, true, 8, PVSC_TI, SL, true>(lat, feat, p, sh, st);
   return launch_tma_r<R, false, 8, PVSC_TI, SL, true>(lat, feat, p, sh, st);
 }

@@ -172,9 +172,11 @@ def test_tma_weyl_cells_equal_the_cell_sweeps_and_oracle(dims, per, R):
     y_flat = pv.apply_H(lat, x)              # default: the flat cell sweep
     lat.set_tuning(R, pv.C64, threads=128, kernel=0)
     y_march = pv.apply_H(lat, x)             # the z-marching cell sweep
+    lat.set_tuning(R, pv.C64, kernel=8)           # the cells marching along x
+    y_xm = pv.apply_H(lat, x)
     lat.set_tuning(R, pv.C64, kernel=7)
     y_tma = pv.apply_H(lat, x)
-    assert torch.equal(y_tma, y_march) and torch.equal(y_tma, y_flat)
+    assert torch.equal(y_tma, y_march) and torch.equal(y_tma, y_flat) and torch.equal(y_xm, y_flat)
     ref = H @ x.cpu().numpy().astype(np.complex128)
     assert np.linalg.norm(y_tma.cpu().numpy() - ref) / np.linalg.norm(ref) < 2e-6
     # KPM moments and a fused step with z and dots
@@ -260,7 +262,9 @@ def test_tma_x_march_is_validated():
     with pytest.raises(pv.PvscError, match="kernel 8"):
         lat.set_tuning(8, pv.C128, kernel=8)
     with pytest.raises(pv.PvscError, match="kernel 8"):
-        pv.Lattice.wsm((16, 4, 4), (1, 1, 0)).set_tuning(8, pv.C64, kernel=8)
+        pv.Lattice.wsm((16, 4, 4), (1, 1, 0)).set_tuning(8, pv.C64, kernel=8, tile_x=16, tile_y=4)
+    with pytest.raises(pv.PvscError, match="kernel 8"):
+        pv.Lattice.graphene((8, 8), (1, 1)).set_tuning(8, pv.C64, kernel=8)
     with pytest.raises(pv.PvscError, match="kernel must be"):
         lat.set_tuning(8, pv.C64, kernel=9)
     lat.set_tuning(8, pv.C64, kernel=8, tile_x=16, tile_y=4)
