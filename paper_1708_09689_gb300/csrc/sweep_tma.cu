@@ -22,10 +22,16 @@ int tma_error_xm(int clear, int* flag);
 // and 64 run as 2 and 4 slices of the 16-vector tiles
 template <int R>
 static int64_t tma_tiles(const Geometry& g) {
-  constexpr int RT = R > 16 ? 16 : R, SL = R > 16 ? R / 16 : 1;
+  constexpr int RT = R > 16 ? 16 : R;
   using L = TmaLayout<RT, true, 8>;
   const int64_t Lx = g.model == PVSC_WSM ? g.L[0] / 2 : g.L[0];
-  return SL * ((Lx + L::TX - 1) / L::TX) * ((g.L[1] + L::TY - 1) / L::TY);
+  return ((Lx + L::TX - 1) / L::TX) * ((g.L[1] + L::TY - 1) / L::TY);
+}
+
+// whole-column units of a slice that the blocks of that slice can hold in their tables
+static bool tma_units_fit(const pvsc_lattice* lat, int64_t tiles_per_slice, int R) {
+  const int64_t SL = R > 16 ? R / 16 : 1;
+  return tiles_per_slice <= (int64_t)kTmaUnitsPerSm * (lat->sm_count / SL);
 }
 
 // The kernel's unit table holds the (x0, y0, z0, planes) of a block's units in
@@ -41,7 +47,7 @@ bool tma_sweep_possible(const pvsc_lattice* lat, int R, int prec) {
                          : R == 16 ? tma_tiles<16>(g)
                          : R == 32 ? tma_tiles<32>(g)
                                    : tma_tiles<64>(g);
-  return ntiles <= (int64_t)kTmaMaxUnits * lat->sm_count;
+  return tma_units_fit(lat, ntiles, R);
 }
 
 
@@ -86,9 +92,8 @@ bool tma_xm_possible(const pvsc_lattice* lat, int R, int prec) {
   const Geometry& g = lat->g;
   if (!tma_sweep_possible(lat, R, prec)) return false;  // TI sites or Weyl cells, complex64
   constexpr int TXd = TmaLayout<16, true, 8>::TX, TYd = TmaLayout<16, true, 8>::TY;  // the smallest tiles
-  const int64_t SL = R > 16 ? R / 16 : 1;
-  const int64_t ntiles = SL * ((g.L[1] + TXd - 1) / TXd) * ((g.L[2] + TYd - 1) / TYd);
-  return ntiles <= (int64_t)kTmaMaxUnits * lat->sm_count;
+  const int64_t ntiles = ((g.L[1] + TXd - 1) / TXd) * ((g.L[2] + TYd - 1) / TYd);
+  return tma_units_fit(lat, ntiles, R);
 }
 
 int launch_sweep_tma_xm(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {

@@ -52,6 +52,7 @@ namespace pvsc {
 
 constexpr unsigned kTmaWaitLimit = 1u << 24;
 constexpr int kTmaMaxUnits = 512;  // work units of one block (a table in shared memory)
+constexpr int kTmaUnitsPerSm = kTmaMaxUnits - 4;  // whole-column units per SM the launch checks allow
 
 // Tile of TX x TY sites per R: 256 (site, vector pair) items, one per thread,
 // and NXS x-plane / NYS y_in-plane ring slots: three planes of copies in flight
@@ -304,19 +305,62 @@ __global__ void __launch_bounds__(32 * NW, 1)
   const int G = gridDim.x / SL;  // blocks per slice
   const int c0 = 32 * sl;       // the slice's rows: innermost tensor-map coordinate
   volatile int* abort = &s_abort;
-  // This block's units u = vb + lu G (lu = 0 .. nlu-1) of its slice, decoded once
-  // into a shared table, so that the per-plane copy logic does no division.
-  const int nlu = (int)((m.nunits - vb + G - 1) / G);
-  uint2* tab = reinterpret_cast<uint2*>(base + L::TAB_OFF);
-  for (int i = threadIdx.x; i < nlu; i += blockDim.x) {
-    const int64_t u = vb + (int64_t)i * G;
-    const int64_t ntiles = (int64_t)m.ntx * m.nty;
+  // This block's units, decoded once into a shared table (x0 | y0 << 16, z0 |
+  // planes << 16), so that the per-plane copy logic does no division: in the full
+  // waves, units u = vb + lu G (lu < nfull) of the slice in wave order (tiles
+  // fastest, so the grid works on adjacent tiles at one depth); the planes of the
+  // units left after the last full wave, taken in wave order, are split evenly
+  // over the G blocks, a block's share being pieces of one to three units.
+  const int64_t ntiles = (int64_t)m.ntx * m.nty;
+  const int nfull = (int)(m.nunits / G);
+  const int64_t tail0 = (int64_t)nfull * G;  // first unit of the tail
+  auto unit = [&](int64_t u, uint32_t& xy, uint32_t& z0, uint32_t& n) {
     const int64_t ch = u / ntiles, t = u - ch * ntiles, ty = t / m.ntx;
-    const uint32_t x0 = (uint32_t)((t - ty * m.ntx) * TX), y0 = (uint32_t)(ty * TY);
-    const uint32_t z0 = (uint32_t)(ch * Lz / m.nch), z1 = (uint32_t)((ch + 1) * Lz / m.nch);
-    tab[i] = make_uint2(x0 | (y0 << 16), z0 | ((z1 - z0) << 16));
+    xy = (uint32_t)((t - ty * m.ntx) * TX) | ((uint32_t)(ty * TY) << 16);
+    z0 = (uint32_t)(ch * Lz / m.nch);
+    n = (uint32_t)((ch + 1) * Lz / m.nch) - z0;
+  };
+  uint2* tab = reinterpret_cast<uint2*>(base + L::TAB_OFF);
+  for (int i = threadIdx.x; i < nfull; i += blockDim.x) {
+    uint32_t xy, z0, n;
+    unit(vb + (int64_t)i * G, xy, z0, n);
+    tab[i] = make_uint2(xy, z0 | (n << 16));
+  }
+  __shared__ int s_ntail;
+  if (threadIdx.x == 0) {
+    // the tail spans few chunks (units are chunk-major) and a chunk's units all
+    // have its depth, so the walk goes chunk by chunk
+    int nt = 0;
+    if (tail0 < m.nunits) {
+      const int64_t cha = tail0 / ntiles, chb = (m.nunits - 1) / ntiles;
+      int64_t P = 0;  // planes of the tail
+      for (int64_t ch = cha; ch <= chb; ++ch) {
+        const int64_t ua = tail0 > ch * ntiles ? tail0 : ch * ntiles;
+        const int64_t ub = m.nunits < (ch + 1) * ntiles ? m.nunits : (ch + 1) * ntiles;
+        P += (ub - ua) * ((ch + 1) * Lz / m.nch - ch * Lz / m.nch);
+      }
+      const int64_t lo = P * vb / G, hi = P * (vb + 1) / G;  // this block's planes of the tail
+      int64_t off = 0;
+      for (int64_t ch = cha; ch <= chb && off < hi; ++ch) {
+        const int64_t ua = tail0 > ch * ntiles ? tail0 : ch * ntiles;
+        const int64_t ub = m.nunits < (ch + 1) * ntiles ? m.nunits : (ch + 1) * ntiles;
+        const int64_t z0 = ch * Lz / m.nch, n = (ch + 1) * Lz / m.nch - z0;  // n >= 1
+        for (int64_t k = lo > off ? (lo - off) / n : 0; ua + k < ub && off + k * n < hi; ++k) {
+          const int64_t uo = off + k * n;
+          const int64_t a = lo > uo ? lo : uo, b = hi < uo + n ? hi : uo + n;
+          if (a < b) {
+            uint32_t xy, zu, nu;
+            unit(ua + k, xy, zu, nu);
+            tab[nfull + nt++] = make_uint2(xy, (zu + (uint32_t)(a - uo)) | ((uint32_t)(b - a) << 16));
+          }
+        }
+        off += (ub - ua) * n;
+      }
+    }
+    s_ntail = nt;
   }
   __syncthreads();
+  const int nlu = nfull + s_ntail;
   auto planes_of = [&](int lu) { return (int)(tab[lu].y >> 16); };
   // The copies of a block, in the order they are consumed: per unit (of n
   // planes z0 .. z0+n-1) the x planes z0-1 .. z0+n (positions j = -1 .. n) and
@@ -800,8 +844,10 @@ static int auto_chunks(int64_t ntiles, int64_t Lz, int64_t grid) {
   int best = 1;
   double best_cost = 1e300;
   for (int64_t nch = 1; nch <= Lz; ++nch) {
-    const int64_t waves = (ntiles * nch + grid - 1) / grid;
-    const double cost = (double)waves * ((double)((Lz + nch - 1) / nch) + 0.7);
+    // full waves of whole units, then the tail's planes spread evenly over the grid
+    const int64_t units = ntiles * nch, full = units / grid, tail = units - full * grid;
+    const double depth = (double)((Lz + nch - 1) / nch) + 0.7;
+    const double cost = (double)full * depth + (tail ? (double)tail * Lz / nch / grid + 1.4 : 0.0);
     if (cost < best_cost - 1e-9) {
       best_cost = cost;
       best = (int)nch;
@@ -839,7 +885,11 @@ static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const Launc
   int nch = sh.zslab > 0 ? (int)((Lz + sh.zslab - 1) / sh.zslab) : auto_chunks(ntiles, Lz, grid_max);
   if (nch < 1) nch = 1;
   if (nch > Lz) nch = (int)Lz;
-  while (nch > 1 && (ntiles * nch + grid_max - 1) / grid_max > kTmaMaxUnits) --nch;  // unit table
+  // unit table: the full waves plus at most two pieces of the tail (a margin of four)
+  while (nch > 1 && ntiles * nch / grid_max + 4 > kTmaMaxUnits) --nch;
+  if (ntiles * nch / grid_max + 4 > kTmaMaxUnits)
+    return set_error(PVSC_ERR_UNSUPPORTED, "the TMA-staged sweep's unit table cannot hold %lld tiles per block",
+                     (long long)(ntiles / grid_max));
   m.nch = nch;
   m.nunits = ntiles * nch;  // per slice
   p.zslab = (int)((Lz + nch - 1) / nch);

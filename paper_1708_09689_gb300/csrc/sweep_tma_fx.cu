@@ -14,9 +14,9 @@ bool tma_tile_deep(int R, int tile_y);
 // (layouts of 32 and 64) run as 2 and 4 slices of 8 vectors on the tiles of layout 16
 template <int R2>
 static int64_t tma_fx_tiles(const Geometry& g) {
-  constexpr int RT = R2 > 16 ? 16 : R2, SL = R2 > 16 ? R2 / 16 : 1;
+  constexpr int RT = R2 > 16 ? 16 : R2;
   using L = TmaLayout<RT, true, 8, 4>;
-  return SL * ((g.L[0] + L::TX - 1) / L::TX) * ((g.L[1] + L::TY - 1) / L::TY);
+  return ((g.L[0] + L::TX - 1) / L::TX) * ((g.L[1] + L::TY - 1) / L::TY);
 }
 
 bool tma_fx_possible(const pvsc_lattice* lat, int R) {
@@ -29,7 +29,8 @@ bool tma_fx_possible(const pvsc_lattice* lat, int R) {
                          : R == 8  ? tma_fx_tiles<16>(g)
                          : R == 16 ? tma_fx_tiles<32>(g)
                                    : tma_fx_tiles<64>(g);
-  return ntiles <= (int64_t)kTmaMaxUnits * lat->sm_count;
+  const int64_t SL = R > 8 ? R / 8 : 1;  // slices of 8 vectors for R = 16, 32
+  return ntiles <= (int64_t)kTmaUnitsPerSm * (lat->sm_count / SL);
 }
 
 // As the complex64 TI sweep: tile_y selects the large tile (two planes of
