@@ -528,15 +528,16 @@ typedef struct {
                   /* 5 z-marching over tiles of tile_x x tile_y columns per block */
                   /* (threads = tile_x tile_y R/vpt, a multiple of 32, at most 256), */
                   /* 6 marching along x over lines (y, z), zslab = x-segment length, */
-                  /* 7 (complex64, R = 4 .. 64, Lx a multiple of 4) TMA-staged */
+                  /* 7 (complex64, R = 1 .. 64, Lx a multiple of 4) TMA-staged */
                   /* plane tiles: one block per SM copies each z-plane of a tile of */
-                  /* 16x16, 16x8 or 8x8 columns (R = 4, 8, 16) with its one-site halo */
+                  /* 32x32, 32x16, 16x16, 16x8 or 8x8 columns (R = 1, 2, 4, 8, 16; R = 1, */
+                  /* 2: one thread per 32- or 64-byte site) with its one-site halo */
                   /* strips into a shared-memory ring (cp.async.bulk.tensor, */
                   /* mbarriers) for eight warps (threads 256, two (site, vector pair) */
                   /* items per thread) or sixteen (threads 512, one item); R = 32 and */
                   /* 64 run as 2 and 4 slices of 16 vectors on the 8x8 tiles, one slice */
-                  /* per block; tile_x x tile_y = the half tile (16x8, 16x4, 8x4, 8x4, */
-                  /* 8x4 for R = 4 .. 64) selects rings one plane deeper on eight warps */
+                  /* per block; tile_x x tile_y = the half tile (32x16, 32x8, 16x8, 16x4, */
+                  /* 8x4, 8x4, 8x4 for R = 1 .. 64) selects rings one plane deeper on eight warps */
                   /* (TI; Weyl cells run the large tile on eight warps); zslab = z-chunk */
                   /* depth (0: chosen from the grid size); vpt is ignored. */
                   /* 8 (as kernel 7) the same tiles marching along x over (y, z) columns, */
@@ -544,12 +545,12 @@ typedef struct {
                   /* (TI) the half tile; zslab = x-chunk depth; same vectors as the */
                   /* z-march bit for bit; the fused step with z runs kernel 7. */
                   /* PVSC_Q64 (KPM on TI lattices) takes kernels 0, 2, 3 (threads a */
-                  /* multiple of R, one vector per thread, no tile) and 7 for R = 2 .. 32 */
+                  /* multiple of R, one vector per thread, no tile) and 7 for R = 1 .. 32 */
                   /* (any Lx): the tiles, rings and variants of the complex64 layout */
                   /* of 2R vectors (a fixed-point value is 16 bytes; R = 16, 32 as */
                   /* slices of 8), one vector of one site per item.  Untuned it runs */
-                  /* kernel 7 on sixteen warps for R = 2 .. 8 and on eight for R = 16, */
-                  /* 32, kernel 2 for R = 64 and kernel 0 for R = 1. */
+                  /* kernel 7 on sixteen warps for R = 2 .. 8 and on eight for R = 1, */
+                  /* 16, 32, and kernel 2 for R = 64. */
 } pvsc_tuning;
 
 /* Device error word of the shared-memory staged sweeps: *flag = 1 if a copy

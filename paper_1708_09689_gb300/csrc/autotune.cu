@@ -193,7 +193,7 @@ extern "C" int pvsc_autotune_op(pvsc_lattice* lat, int R, int prec, int op, pvsc
   // TMA-staged plane tiles (kernel 7): z-chunks chosen automatically or a few fixed depths
   if (tma_sweep_possible(lat, R, prec)) {
     // the half tiles of the deeper rings (R = 32, 64: slices on the tiles of R = 16)
-    const int deep_y = R == 4 ? 8 : 4, deep_x = R >= 16 ? 8 : 16;
+    const int deep_y = R == 1 ? 16 : (R == 2 || R == 4) ? 8 : 4, deep_x = R >= 16 ? 8 : (R <= 2 ? 32 : 16);
     for (int zs : {0, 16, 32, 64})
       if (zs == 0 || zs < lat->g.L[2]) {
         cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, 0, 0, kKernelTma});

@@ -983,7 +983,7 @@ static int check_q64_tuning(const pvsc_lattice* lat, int R, const pvsc_tuning* t
   if (!t) return PVSC_OK;
   if (t->kernel == kKernelTma) {
     if (!tma_fx_possible(lat, R))
-      return set_error(PVSC_ERR_ARG, "PVSC_Q64 kernel 7 (TMA-staged tiles) needs R = 2 .. 32");
+      return set_error(PVSC_ERR_ARG, "PVSC_Q64 kernel 7 (TMA-staged tiles) needs R = 1 .. 32");
     if (!tma_tile_valid(2 * R, t->tile_x, t->tile_y))
       return set_error(PVSC_ERR_ARG, "PVSC_Q64 kernel 7 takes no tile other than the two of R = %d (%dx%d given)",
                        R, t->tile_x, t->tile_y);
@@ -1018,7 +1018,7 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
   if (tuning->kernel == kKernelTma || tuning->kernel == kKernelTmaX) {
     const int k = tuning->kernel;
     if (k == kKernelTma && !tma_sweep_possible(lat, R, prec))
-      return set_error(PVSC_ERR_ARG, "kernel 7 (TMA-staged tiles) needs a TI or Weyl lattice, complex64, R >= 4 "
+      return set_error(PVSC_ERR_ARG, "kernel 7 (TMA-staged tiles) needs a TI or Weyl lattice, complex64 "
                        "and Lx a multiple of 4");
     if (k == kKernelTmaX && !tma_xm_possible(lat, R, prec))
       return set_error(PVSC_ERR_ARG, "kernel 8 (TMA-staged tiles marching along x) needs a TI or Weyl lattice, "

@@ -213,12 +213,12 @@ static void* fx_kernel(int kernel) {
 int launch_sweep_fx(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, bool tuned,
                     cudaStream_t st) {
   // untuned (measured on the 256 x 256 x 64 slab): the TMA-staged tiles, on 16
-  // warps for R = 2 .. 8 and on 8 for the slices of R = 16, 32 (0.67 to 0.74 of
-  // the HBM roof, against 0.42 to 0.53 for the cp.async ring); plain loads for
-  // R = 1 and the six-block ring for R = 64
+  // warps for R = 2 .. 8 and on 8 for R = 1 and the slices of R = 16, 32 (0.61
+  // to 0.79 of the HBM roof, against 0.30 to 0.53 for the cp.async ring); the
+  // six-block ring for R = 64
   if (!tuned && tma_fx_possible(lat, p.R)) {
     LaunchShape d;
-    d.threads = p.R <= 8 ? 512 : 256;
+    d.threads = p.R >= 2 && p.R <= 8 ? 512 : 256;
     return launch_sweep_tma_fx(lat, p, d, st);
   }
   const int kernel = tuned ? sh.kernel : (p.R >= 2 ? 2 : 0);

@@ -58,20 +58,19 @@ constexpr int kTmaUnitsPerSm = kTmaMaxUnits - 4;  // whole-column units per SM t
 // and NXS x-plane / NYS y_in-plane ring slots: three planes of copies in flight
 // beyond the two x planes and the y_in plane being read (DEEP = true).
 // DEEP = false: twice the tile (512 items, two per thread) with two planes of
-// copies in flight.
+// copies in flight.  R = 1, 2: one thread per site (sites of 32 and 64 bytes).
+// R = 32, 64 run as slices of 16 vectors on the tiles of R = 16.
 template <int R, bool DEEP> struct TmaTile;
+template <> struct TmaTile<1, true> { static constexpr int TX = 32, TY = 16, NXS = 5, NYS = 4; };
+template <> struct TmaTile<2, true> { static constexpr int TX = 32, TY = 8, NXS = 5, NYS = 4; };
+template <> struct TmaTile<1, false> { static constexpr int TX = 32, TY = 32, NXS = 3, NYS = 2; };
+template <> struct TmaTile<2, false> { static constexpr int TX = 32, TY = 16, NXS = 3, NYS = 2; };
 template <> struct TmaTile<4, true> { static constexpr int TX = 16, TY = 8, NXS = 5, NYS = 4; };
 template <> struct TmaTile<8, true> { static constexpr int TX = 16, TY = 4, NXS = 5, NYS = 4; };
 template <> struct TmaTile<16, true> { static constexpr int TX = 8, TY = 4, NXS = 5, NYS = 4; };
 template <> struct TmaTile<4, false> { static constexpr int TX = 16, TY = 16, NXS = 3, NYS = 2; };
 template <> struct TmaTile<8, false> { static constexpr int TX = 16, TY = 8, NXS = 3, NYS = 2; };
 template <> struct TmaTile<16, false> { static constexpr int TX = 8, TY = 8, NXS = 3, NYS = 2; };
-// R = 32: 1 KB sites, 4 x 4 tiles of 256 items (the "deep" variant one slot deeper)
-template <> struct TmaTile<32, false> { static constexpr int TX = 4, TY = 4, NXS = 3, NYS = 2; };
-template <> struct TmaTile<32, true> { static constexpr int TX = 4, TY = 4, NXS = 4, NYS = 3; };
-// R = 64: 2 KB sites, 4 x 2 tiles of 256 items, one warp per site
-template <> struct TmaTile<64, false> { static constexpr int TX = 4, TY = 2, NXS = 3, NYS = 2; };
-template <> struct TmaTile<64, true> { static constexpr int TX = 4, TY = 2, NXS = 3, NYS = 2; };
 
 constexpr int round_up_1k(int b) { return (b + 1023) & ~1023; }
 
@@ -83,8 +82,9 @@ struct TmaLayout {
   static constexpr int NWARPS = NW;  // warps per block (8 or 16), one block per SM
   static constexpr int TX = TmaTile<R, DEEP>::TX, TY = TmaTile<R, DEEP>::TY;
   static constexpr int SITE_B = 32 * R;          // 4 orbitals x R complex64
-  static constexpr int ROWS = SITE_B / 128;      // 128-byte swizzle rows per site
-  static constexpr int CPS = R / 2;              // threads per site
+  static constexpr int ROWB = SITE_B < 128 ? SITE_B : 128;  // bytes of a copied row (the swizzle span)
+  static constexpr int ROWS = SITE_B / ROWB;     // rows per site
+  static constexpr int CPS = R >= 2 ? R / 2 : 1;  // threads per site
   static constexpr int SPW = 32 / CPS;           // sites per warp
   static constexpr int ITEMS = TX * TY * CPS;
   static constexpr int IPT = ITEMS / (32 * NW);  // items per thread
@@ -185,8 +185,8 @@ __device__ __forceinline__ bool tma_wait(uint64_t* bar, unsigned parity, volatil
 // whenever their rows agree modulo 8; this permutation spreads them.
 template <int R>
 __device__ __forceinline__ int tma_site_perm(int q) {
-  if constexpr (R >= 16) {
-    return q;  // one site per quarter-warp
+  if constexpr (R >= 16 || R <= 2) {
+    return q;  // one site per quarter-warp, or consecutive sites under the 64 / 32-byte swizzle
   } else if constexpr (R == 8) {
     return (q & 4) | ((q & 1) << 1) | ((q >> 1) & 1);  // quarter-warp: sites a, a + 2
   } else {
@@ -206,7 +206,10 @@ template <int R, bool SWZ = true>
 __device__ __forceinline__ uint32_t tma_swz(uint32_t O, int c) {
   const uint32_t L = O + 16u * (uint32_t)c;
   if constexpr (!SWZ) return L;
-  return L ^ (((L >> 7) & 7u) << 4);
+  // the swizzle of the copy: 128-byte (R >= 4), 64-byte (R = 2) or 32-byte (R = 1)
+  // span, the 16-byte chunk bits XORed with the bits above bit 7
+  constexpr uint32_t MASK = R >= 4 ? 7u : (R == 2 ? 3u : 1u);
+  return L ^ (((L >> 7) & MASK) << 4);
 }
 
 // All four orbitals (two vectors each) of one site from a swizzled tile
@@ -223,6 +226,19 @@ __device__ __forceinline__ void tma_lds_blk(const unsigned char* buf, uint32_t B
     b.v[o][0] = {v.x, v.y};
     b.v[o][1] = {v.z, v.w};
   }
+}
+
+// One vector (R = 1): the 32-byte site is two chunks, orbitals (0, 1) and
+// (2, 3); under the 32-byte swizzle chunk k sits at B ^ 16 k.
+template <int R>
+__device__ __forceinline__ void tma_lds_blk(const unsigned char* buf, uint32_t B, Blk<float, 1>& b) {
+  static_assert(R == 1, "one vector per site");
+  const float4 v0 = *reinterpret_cast<const float4*>(buf + B);
+  const float4 v1 = *reinterpret_cast<const float4*>(buf + (B ^ 16u));
+  b.v[0][0] = {v0.x, v0.y};
+  b.v[1][0] = {v0.z, v0.w};
+  b.v[2][0] = {v1.x, v1.y};
+  b.v[3][0] = {v1.z, v1.w};
 }
 
 // The same four orbitals of a fixed-point block: a site of R/2 vectors of
@@ -264,6 +280,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
   static_assert(SL == 1 || R == 16, "vector slices of 16 complex64 (8 fixed-point) vectors");
   static_assert(!XM || MODEL == PVSC_TI || MODEL == PVSC_WSM, "marching along x: TI sites or Weyl cells");
   constexpr int RF = R * SL;  // vectors (complex64 layout) of the whole block
+  constexpr int VP = R == 1 ? 1 : 2;  // complex64 vectors per thread (R = 1: one per site)
   constexpr bool WSM = MODEL == 3;
   constexpr bool FX = MODEL == kModelTIFx;
   // fixed point with R/2 >= 8 vectors: a quarter-warp reads one whole 128-byte
@@ -459,9 +476,9 @@ __global__ void __launch_bounds__(32 * NW, 1)
   const int c = lane % L::CPS;
   const int q = lane / L::CPS;
   const int cg = c + sl * L::CPS;  // the chunk (complex64) or vector (fixed point) in the block
-  VecCoef<float, 2> cf;
-  if constexpr (!FX) cf = load_coef<float, 2>(p, cg);
-  DotAcc<float, 2> dacc;  // compensated fp32 sums; their fp64 part lives in shared memory
+  VecCoef<float, VP> cf;
+  if constexpr (!FX) cf = load_coef<float, VP>(p, cg);
+  DotAcc<float, VP> dacc;  // compensated fp32 sums; their fp64 part lives in shared memory
   dacc.init();
   // fixed point: exact per-unit dot sums of this thread's vector c, the
   // coefficient limbs and the fp64 value of one dot unit
@@ -495,7 +512,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
 #pragma unroll
     for (int d = 0; d < kNumDots; ++d)
 #pragma unroll
-      for (int v = 0; v < 2; ++v) {
+      for (int v = 0; v < VP; ++v) {
         double t = widen(dacc.s[d][v]) + widen(dacc.c[d][v]);
         dacc.s[d][v] = 0.f;
         dacc.c[d][v] = 0.f;
@@ -503,7 +520,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
         if (lane < L::CPS) wdots[(d * 2 + v) * L::CPS + lane] += t;
       }
   };
-  using XBlk = typename std::conditional<FX, Blk<long long, 1>, Blk<float, 2>>::type;
+  using XBlk = typename std::conditional<FX, Blk<long long, 1>, Blk<float, VP>>::type;
   XBlk xmr[IPT];
   uint32_t kx = 0, ky = 0;
   const unsigned char* ybase = base + L::NXS * L::XSTAGE;
@@ -629,7 +646,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
         } else {
           if constexpr (WSM) {
             // the Weyl cell update of the Weyl sweeps, on the cell blocks around the cell
-            Blk<float, 2> xp, ax, bx, ay, by, xc, yi, yn;
+            Blk<float, VP> xp, ax, bx, ay, by, xc, yi, yn;
             tma_lds_blk<R>(s1, Bc[i], xp);
             tma_lds_blk<R>(s0, Bxm[i], ax);
             tma_lds_blk<R>(s0, Bxp[i], bx);
@@ -646,57 +663,57 @@ __global__ void __launch_bounds__(32 * NW, 1)
             else
               wsm_cell_update(cf, V0, V1, xmr[i], xc, xp, ax, bx, ay, by, m.has_yin ? &yi : nullptr, yn);
             const int64_t sites[4] = {2 * s, 2 * s, 2 * s + 1, 2 * s + 1};
-            epilogue<float, 2, FEAT>(p, s, cg, xc, yn, dacc, sites);
+            epilogue<float, VP, FEAT>(p, s, cg, xc, yn, dacc, sites);
             xmr[i] = xc;
             continue;
           }
           // the axes in ti_axes' order (z pair, x pair, y pair), each pair loaded
           // just before it is folded in, so that few blocks are live at a time
-          Blk<float, 2> S, D, yn;
+          Blk<float, VP> S, D, yn;
           if constexpr (XM) {  // lattice z = the Y halos, x = the march, y = the X halos
             {
-              Blk<float, 2> zm, zp;
+              Blk<float, VP> zm, zp;
               tma_lds_blk<R>(s0, Bym[i], zm);
               tma_lds_blk<R>(s0, Byp[i], zp);
               axis_z_init(zm, zp, S, D);
             }
             {
-              Blk<float, 2> xp;
+              Blk<float, VP> xp;
               tma_lds_blk<R>(s1, Bc[i], xp);
               axis_x_add(xmr[i], xp, S, D);
             }
             {
-              Blk<float, 2> ay, by;
+              Blk<float, VP> ay, by;
               tma_lds_blk<R>(s0, Bxm[i], ay);
               tma_lds_blk<R>(s0, Bxp[i], by);
               axis_y_add(ay, by, S, D);
             }
           } else {
             {
-              Blk<float, 2> xp;
+              Blk<float, VP> xp;
               tma_lds_blk<R>(s1, Bc[i], xp);
               axis_z_init(xmr[i], xp, S, D);
             }
             {
-              Blk<float, 2> ax, bx;
+              Blk<float, VP> ax, bx;
               tma_lds_blk<R>(s0, Bxm[i], ax);
               tma_lds_blk<R>(s0, Bxp[i], bx);
               axis_x_add(ax, bx, S, D);
             }
             {
-              Blk<float, 2> ay, by;
+              Blk<float, VP> ay, by;
               tma_lds_blk<R>(s0, Bym[i], ay);
               tma_lds_blk<R>(s0, Byp[i], by);
               axis_y_add(ay, by, S, D);
             }
           }
-          Blk<float, 2> xc, yi;
+          Blk<float, VP> xc, yi;
           tma_lds_blk<R>(s0, Bc[i], xc);
           if (m.has_yin) tma_lds_blk<R>(sy, Bc[i], yi);
           const float Vs = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i]) : site_potential_t<float>(g, s);
           ti_combine(cf, Vs, xc, S, D, m.has_yin ? &yi : nullptr, yn, g);
           const int64_t sites[4] = {s, s, s, s};
-          epilogue<float, 2, FEAT>(p, s, cg, xc, yn, dacc, sites);
+          epilogue<float, VP, FEAT>(p, s, cg, xc, yn, dacc, sites);
           xmr[i] = xc;
         }
       }
@@ -775,19 +792,24 @@ static int encode_maps(const pvsc_lattice* lat, const Sweep& p, TmaMaps& m) {
   // fixed-point sweep's per-site (d+, d-) pair of 64-bit coefficients
   const int vf = MODEL == kModelTIFx ? 4 : vpc;
   const cuuint64_t Lx = lat->g.L[0] / vpc, Ly = lat->g.L[1], Lz = lat->g.L[2];
-  // rows of 32 floats; with SL slices a row of the block holds SL slice rows side by
-  // side (the innermost coordinate selects one) and a site SL times the slice's bytes
+  // rows of ROWB bytes (128; a whole 64- or 32-byte site for R = 2, 1); with SL
+  // slices a row of the block holds SL slice rows side by side (the innermost
+  // coordinate selects one) and a site SL times the slice's bytes
   const cuuint64_t SB = (cuuint64_t)L::SITE_B * SL;
+  const cuuint64_t RW = (cuuint64_t)L::ROWB / 4;  // floats of a row
   // the kernel's axes (X, Y, Z): (x, y, z), or (y, z, x) when marching along x
-  const cuuint64_t dims[5] = {(cuuint64_t)32 * SL, (cuuint64_t)L::ROWS, XM ? Ly : Lx, XM ? Lz : Ly, XM ? Lx : Lz};
-  const cuuint64_t strides[4] = {(cuuint64_t)128 * SL, XM ? SB * Lx : SB, XM ? SB * Lx * Ly : SB * Lx,
+  const cuuint64_t dims[5] = {RW * SL, (cuuint64_t)L::ROWS, XM ? Ly : Lx, XM ? Lz : Ly, XM ? Lx : Lz};
+  const cuuint64_t strides[4] = {(cuuint64_t)L::ROWB * SL, XM ? SB * Lx : SB, XM ? SB * Lx * Ly : SB * Lx,
                                  XM ? SB : SB * Lx * Ly};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  // the kernel's addressing: unswizzled tiles for fixed point with R/2 >= 8 vectors
-  const CUtensorMapSwizzle swz =
-      (MODEL == kModelTIFx && R >= 16) ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B;
+  // the kernel's addressing: the swizzle spanning a row (128, 64 or 32 bytes);
+  // unswizzled tiles for fixed point with R/2 >= 8 vectors
+  const CUtensorMapSwizzle swz = (MODEL == kModelTIFx && R >= 16) ? CU_TENSOR_MAP_SWIZZLE_NONE
+                                 : L::ROWB == 128                 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                 : L::ROWB == 64                  ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                                  : CU_TENSOR_MAP_SWIZZLE_32B;
   auto tile5 = [&](CUtensorMap* map, const void* ptr, cuuint32_t bx, cuuint32_t by) -> int {
-    const cuuint32_t box[5] = {32, (cuuint32_t)L::ROWS, bx, by, 1};
+    const cuuint32_t box[5] = {(cuuint32_t)RW, (cuuint32_t)L::ROWS, bx, by, 1};
     const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(ptr), dims, strides,
                            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -870,7 +892,7 @@ static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const Launc
   int occ = 0;
   PVSC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * NW, L::SMEM));
   if (occ < 1) return set_error(PVSC_ERR_CUDA, "the TMA-staged sweep does not fit an SM");
-  p.C = R / 2;
+  p.C = L::CPS;
   p.tile_x = L::TX;
   p.tile_y = L::TY;
   TmaMaps m;

@@ -21,10 +21,11 @@ static int64_t tma_fx_tiles(const Geometry& g) {
 
 bool tma_fx_possible(const pvsc_lattice* lat, int R) {
   const Geometry& g = lat->g;
-  if (!(g.model == PVSC_TI && (R == 2 || R == 4 || R == 8 || R == 16 || R == 32) && g.L[0] < 65536 &&
+  if (!(g.model == PVSC_TI && (R == 1 || R == 2 || R == 4 || R == 8 || R == 16 || R == 32) && g.L[0] < 65536 &&
         g.L[1] < 65536 && g.L[2] < 65536))
     return false;
-  const int64_t ntiles = R == 2    ? tma_fx_tiles<4>(g)
+  const int64_t ntiles = R == 1    ? tma_fx_tiles<2>(g)
+                         : R == 2  ? tma_fx_tiles<4>(g)
                          : R == 4  ? tma_fx_tiles<8>(g)
                          : R == 8  ? tma_fx_tiles<16>(g)
                          : R == 16 ? tma_fx_tiles<32>(g)
@@ -39,11 +40,15 @@ bool tma_fx_possible(const pvsc_lattice* lat, int R) {
 // (R = 16 and 32: slices of 8 vectors, each in the layout of 16).
 int launch_sweep_tma_fx(const pvsc_lattice* lat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
   if (!tma_fx_possible(lat, p.R))
-    return set_error(PVSC_ERR_UNSUPPORTED, "the TMA-staged fixed-point sweep needs a TI lattice and R = 2 .. 32");
+    return set_error(PVSC_ERR_UNSUPPORTED, "the TMA-staged fixed-point sweep needs a TI lattice and R = 1 .. 32");
   const bool deep = tma_tile_deep(2 * p.R, sh.tile_y);
   const bool wide = !deep && sh.threads == 512;
   constexpr int F = kModelTIFx;
   switch (p.R) {
+    case 1:  // the 64-byte sites of layout 2
+      return deep ? launch_tma_r<2, true, 8, F>(lat, F_DOTS, p, sh, st)
+                  : (wide ? launch_tma_r<2, false, 16, F>(lat, F_DOTS, p, sh, st)
+                          : launch_tma_r<2, false, 8, F>(lat, F_DOTS, p, sh, st));
     case 2:
       return deep ? launch_tma_r<4, true, 8, F>(lat, F_DOTS, p, sh, st)
                   : (wide ? launch_tma_r<4, false, 16, F>(lat, F_DOTS, p, sh, st)

@@ -124,7 +124,7 @@ CASES = [
 ]
 
 # the half tiles of the layout of 2R complex64 vectors (R = 16, 32: slices of 8 vectors in the layout of 16)
-DEEP_TILE = {2: (16, 8), 4: (16, 4), 8: (8, 4), 16: (8, 4), 32: (8, 4)}
+DEEP_TILE = {1: (32, 8), 2: (16, 8), 4: (16, 4), 8: (8, 4), 16: (8, 4), 32: (8, 4)}
 
 
 def _variant(R, v):
@@ -134,7 +134,7 @@ def _variant(R, v):
 
 
 @pytest.mark.parametrize("dims,per,zs", CASES)
-@pytest.mark.parametrize("R,variant", [(R, v) for R in (2, 4, 8, 16, 32) for v in ("large", "wide", "deep")])
+@pytest.mark.parametrize("R,variant", [(R, v) for R in (1, 2, 4, 8, 16, 32) for v in ("large", "wide", "deep")])
 def test_q64_tma_sweep_matches_zmarch_and_oracle(dims, per, zs, R, variant):
     n = int(np.prod(dims))
     V = W.disorder_potential(n, 2.0, 7)
@@ -172,7 +172,7 @@ def test_q64_tma_sweep_with_on_the_fly_disorder_and_generated_block():
 
 def test_q64_kernel7_tuning_is_validated():
     lat = pv.Lattice.ti((16, 8, 4), (1, 1, 0))
-    for R in (1, 64):  # no fixed-point TMA layout for these block sizes
+    for R in (64,):  # no fixed-point TMA layout for this block size
         with pytest.raises(pv.PvscError, match="kernel 7"):
             lat.set_tuning(R, pv.Q64, kernel=7)
     with pytest.raises(pv.PvscError, match="tile"):

@@ -1,5 +1,5 @@
-"""The TI sweep with TMA-staged plane tiles (tuning kernel 7, complex64, R = 4 .. 64;
-R = 32 and 64 as slices of 16 vectors).
+"""The TI sweep with TMA-staged plane tiles (tuning kernel 7, complex64, R = 1 .. 64;
+R = 1, 2 one thread per narrow site, R = 32 and 64 as slices of 16 vectors).
 
 Its stencil arithmetic is the register z-march's, in the same order, so the
 vectors it writes must equal the default sweep's bit for bit; they are also
@@ -43,7 +43,7 @@ def _lattice(dims, per, vmode, delta):
 
 
 # the half tiles with three planes in flight (R = 32, 64: slices of 16 vectors on the tiles of R = 16)
-DEEP_TILE = {4: (16, 8), 8: (16, 4), 16: (8, 4), 32: (8, 4), 64: (8, 4)}
+DEEP_TILE = {1: (32, 16), 2: (32, 8), 4: (16, 8), 8: (16, 4), 16: (8, 4), 32: (8, 4), 64: (8, 4)}
 
 
 def _variant(R, v):
@@ -55,7 +55,7 @@ def _variant(R, v):
 
 
 @pytest.mark.parametrize("dims,per,zs", CASES)
-@pytest.mark.parametrize("R,variant", [(R, v) for R in (4, 8, 16, 32, 64) for v in ("large", "wide", "deep")])
+@pytest.mark.parametrize("R,variant", [(R, v) for R in (1, 2, 4, 8, 16, 32, 64) for v in ("large", "wide", "deep")])
 def test_tma_sweep_equals_default_sweep_and_oracle(dims, per, zs, R, variant):
     lat, V = _lattice(dims, per, "stored", False)
     H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
@@ -69,7 +69,7 @@ def test_tma_sweep_equals_default_sweep_and_oracle(dims, per, zs, R, variant):
 
 
 @pytest.mark.parametrize("vmode,delta", [("stored", True), ("fly", False), ("zero", True)])
-@pytest.mark.parametrize("R,variant", [(R, v) for R in (4, 8, 16, 32, 64) for v in ("large", "wide")])
+@pytest.mark.parametrize("R,variant", [(R, v) for R in (1, 2, 4, 8, 16, 32, 64) for v in ("large", "wide")])
 def test_tma_fused_step_with_z_and_dots(vmode, delta, R, variant):
     dims, per = (24, 16, 5), (1, 0, 1)
     lat, V = _lattice(dims, per, vmode, delta)
@@ -104,7 +104,7 @@ def test_tma_fused_step_with_z_and_dots(vmode, delta, R, variant):
 
 
 @pytest.mark.parametrize("dims,per,zs", CASES[:3])
-@pytest.mark.parametrize("R,variant", [(R, v) for R in (4, 8, 16, 32, 64) for v in ("large", "wide", "deep")])
+@pytest.mark.parametrize("R,variant", [(R, v) for R in (1, 2, 4, 8, 16, 32, 64) for v in ("large", "wide", "deep")])
 def test_tma_kpm_moments_match_oracle_and_default(dims, per, zs, R, variant):
     lat, V = _lattice(dims, per, "stored", False)
     H = O.ti_hamiltonian(dims, per, 1.0, 2.0, V)
@@ -136,7 +136,7 @@ def test_tma_series_and_propagation():
 
 def test_tma_kernel_is_refused_where_it_does_not_apply():
     lat = pv.Lattice.ti((16, 8, 4), (1, 1, 0))
-    for R, prec in ((8, pv.C128), (2, pv.C64), (1, pv.C64)):
+    for R, prec in ((8, pv.C128), (2, pv.C128), (1, pv.C128)):
         with pytest.raises(pv.PvscError, match="kernel 7"):
             lat.set_tuning(R, prec, kernel=7)
     with pytest.raises(pv.PvscError, match="kernel 7"):
@@ -162,7 +162,7 @@ WSM_CASES = [((16, 5, 4), (1, 1, 0)), ((36, 2, 3), (1, 1, 1)), ((8, 1, 5), (0, 1
 
 
 @pytest.mark.parametrize("dims,per", WSM_CASES)
-@pytest.mark.parametrize("R", [4, 8, 16, 32, 64])
+@pytest.mark.parametrize("R", [1, 2, 4, 8, 16, 32, 64])
 def test_tma_weyl_cells_equal_the_cell_sweeps_and_oracle(dims, per, R):
     n = int(np.prod(dims))
     V = W.disorder_potential(n, 1.5, 6)
@@ -172,11 +172,12 @@ def test_tma_weyl_cells_equal_the_cell_sweeps_and_oracle(dims, per, R):
     y_flat = pv.apply_H(lat, x)              # default: the flat cell sweep
     lat.set_tuning(R, pv.C64, threads=128, kernel=0)
     y_march = pv.apply_H(lat, x)             # the z-marching cell sweep
-    lat.set_tuning(R, pv.C64, kernel=8)           # the cells marching along x
-    y_xm = pv.apply_H(lat, x)
+    if R >= 4:                                    # the cells marching along x (R >= 4)
+        lat.set_tuning(R, pv.C64, kernel=8)
+        assert torch.equal(pv.apply_H(lat, x), y_flat)
     lat.set_tuning(R, pv.C64, kernel=7)
     y_tma = pv.apply_H(lat, x)
-    assert torch.equal(y_tma, y_march) and torch.equal(y_tma, y_flat) and torch.equal(y_xm, y_flat)
+    assert torch.equal(y_tma, y_march) and torch.equal(y_tma, y_flat)
     ref = H @ x.cpu().numpy().astype(np.complex128)
     assert np.linalg.norm(y_tma.cpu().numpy() - ref) / np.linalg.norm(ref) < 2e-6
     # KPM moments and a fused step with z and dots
