@@ -639,13 +639,19 @@ def run_workload(args, pv, dev, rank, world):
         clk = clocks.stop()
         sites = sum(L ** 3 for L, _, _ in specs)
         lups = sites * R * (M // 2)
+        per_lattice = bool(tuning) and int(tuning.get("kernel", 0)) == 7
+        mode = ("every lattice's KPM as a chain of TMA-staged sweeps, the chains on 4 forked streams "
+                "in one CUDA graph" if per_lattice else "one persistent cooperative launch in a CUDA graph")
         line.update({"workload": "batched", "value": round(world * lups / (ms * 1e-3) / 1e9, 3),
                      "ms_per_step": round(ms, 3), "steps": args.steps, "dtype": "c64",
                      "config": {"workload": "64 periodic TI cubes, L from {24,32,48,64,96}, W~U[0,5), R=16, "
-                                            "1024 moments, one persistent cooperative launch in a CUDA graph",
+                                            "1024 moments, " + mode,
                                 "sites": sites, "mu0_min": float(mu[:, :, 0].min().item()), "launch": tuning},
-                     "roofline": _hbm_roof(96.0 + 8.0 / R, lups, ms, "kpm_batched_kernel<float,2>"),
-                     "clocks": clk, "gpu_launches": args.steps})
+                     "roofline": _hbm_roof(96.0 + 8.0 / R, lups, ms,
+                                           "ti_sweep_tma<16,F_DOTS> (per-lattice chains)" if per_lattice
+                                           else "kpm_batched_kernel<float,2>"),
+                     "clocks": clk,
+                     "gpu_launches": args.steps * (len(specs) * (2 + M // 2) if per_lattice else 1)})
     elif args.workload == "adjoint":
         cfg = W.CONFIG_GRAPHENE_ADJ
         V = cfg.potential()

@@ -399,7 +399,13 @@ size_t pvsc_propagate_adjoint_work_bytes(const pvsc_lattice* lat, int R, int eve
  * phase counter, bounded spin waits), so the lattices advance independently.
  * Launch shape (threads per block, z-slab planes, blocks per SM): the tuning
  * entry (R, prec) of lats[0] if one is set, else 256 threads, whole columns
- * (one unit per column and step) and the occupancy maximum.
+ * (one unit per column and step) and the occupancy maximum.  An entry with
+ * kernel 7 (complex64, every lattice eligible for kernel 7) runs each
+ * lattice's KPM instead as its own chain of TMA-staged sweeps (threads 256 or
+ * 512: the large tile on 8 or 16 warps), the chains on a few streams forked
+ * from `stream` inside one captured graph, the same moments as
+ * pvsc_kpm_moments with that kernel and seed; that mode does not synchronise
+ * and reports copy-wait timeouts through pvsc_device_error.
  * a, b: HOST arrays of n doubles.  Start vectors: counter hash, stream 1,
  * seed seeds[i] (HOST array of n).  mu: device [n][R][M] doubles.
  * Returns PVSC_ERR_TIMEOUT if a wait exceeded pvsc_set_wait_limit (the

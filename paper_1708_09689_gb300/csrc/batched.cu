@@ -270,6 +270,7 @@ static size_t batch_header_bytes(int n) {
 // pays a phase wait, a block reduction and a partial-row write).
 struct BatchShape {
   int threads = 256, zs = 0, bps = 0;
+  bool per_lattice = false;  // kernel 7: every lattice's KPM on the TMA-staged sweep
 };
 static BatchShape batch_shape(const pvsc_lattice* l0, int R, int prec) {
   BatchShape sh;
@@ -281,8 +282,92 @@ static BatchShape batch_shape(const pvsc_lattice* l0, int R, int prec) {
       sh.threads = t.threads;
     if (t.zslab > 0) sh.zs = t.zslab;
     sh.bps = t.blocks_per_sm;
+    if (t.kernel == kKernelTma) {
+      sh.per_lattice = true;
+      sh.threads = t.threads == 512 ? 512 : 256;
+    }
   }
   return sh;
+}
+
+// ---------------------------------------------------------------- per-lattice mode
+// Tuning kernel 7 on the batch: each lattice's KPM runs as its own chain of
+// TMA-staged sweeps (kpm_enqueue), the chains spread over a few streams that
+// fork from and join the caller's stream, all inside one captured graph; a
+// large lattice's sweeps fill the GPU while the small lattices' short sweeps
+// run beside them.  Work: per lattice the dot header and partials and its two
+// recurrence vectors.
+constexpr int kBatchStreams = 4;
+
+static bool per_lattice_possible(const pvsc_lattice* const* lats, int n, int R, int prec) {
+  for (int i = 0; i < n; ++i)
+    if (!lats[i] || !tma_sweep_possible(lats[i], R, prec)) return false;
+  return true;
+}
+
+static size_t per_lattice_bytes(const pvsc_lattice* lat, int R, int prec) {
+  return ((dots_work_bytes(lat, R) + 255) & ~size_t(255)) + 2 * vec_bytes(lat, R, prec);
+}
+
+static int kpm_per_lattice(const pvsc_lattice* const* lats, int n, int R, int prec, const uint64_t* seeds, int M,
+                           const double* a, const double* b, double* mu, void* work, size_t work_bytes,
+                           const BatchShape& bs, cudaStream_t st) {
+  std::vector<size_t> off(n);
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    off[i] = total;
+    total += (per_lattice_bytes(lats[i], R, prec) + 255) & ~size_t(255);
+  }
+  if (work_bytes < total) return set_error(PVSC_ERR_ARG, "work buffer too small: %zu < %zu", work_bytes, total);
+  static std::mutex mu_streams;
+  static cudaStream_t pool[kBatchStreams];
+  static cudaEvent_t fork_ev, join_ev[kBatchStreams];
+  static bool ready = false;
+  std::lock_guard<std::mutex> lk(mu_streams);
+  if (!ready) {
+    for (int k = 0; k < kBatchStreams; ++k) {
+      PVSC_CUDA_TRY(cudaStreamCreateWithFlags(&pool[k], cudaStreamNonBlocking));
+      PVSC_CUDA_TRY(cudaEventCreateWithFlags(&join_ev[k], cudaEventDisableTiming));
+    }
+    PVSC_CUDA_TRY(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+    ready = true;
+  }
+  // the largest lattices first, each on the stream with the least work so far
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return lats[x]->g.n_sites > lats[y]->g.n_sites; });
+  LaunchShape force;
+  force.kernel = kKernelTma;
+  force.threads = bs.threads;
+  std::vector<uint64_t> uid = {6, (uint64_t)n, (uint64_t)R, (uint64_t)prec, (uint64_t)M,
+                               (uint64_t)(uintptr_t)mu, (uint64_t)(uintptr_t)work, (uint64_t)bs.threads};
+  for (int i = 0; i < n; ++i) {
+    uint64_t ab[2];
+    std::memcpy(&ab[0], &a[i], 8);
+    std::memcpy(&ab[1], &b[i], 8);
+    uid.insert(uid.end(), {(uint64_t)(uintptr_t)lats[i], lats[i]->generation, seeds[i], ab[0], ab[1]});
+  }
+  auto body = [&](cudaStream_t cs) -> int {
+    PVSC_CUDA_TRY(cudaEventRecord(fork_ev, cs));
+    for (int k = 0; k < kBatchStreams; ++k) PVSC_CUDA_TRY(cudaStreamWaitEvent(pool[k], fork_ev, 0));
+    double load[kBatchStreams] = {0, 0, 0, 0};
+    for (int i : order) {
+      int k = 0;
+      for (int j = 1; j < kBatchStreams; ++j)
+        if (load[j] < load[k]) k = j;
+      load[k] += (double)lats[i]->g.n_sites;
+      if (int rc = kpm_enqueue(lats[i], R, prec, nullptr, seeds[i], M, a[i], b[i], mu + (size_t)i * R * M,
+                               static_cast<char*>(work) + off[i], &force, pool[k]))
+        return rc;
+    }
+    for (int k = 0; k < kBatchStreams; ++k) {
+      PVSC_CUDA_TRY(cudaEventRecord(join_ev[k], pool[k]));
+      PVSC_CUDA_TRY(cudaStreamWaitEvent(cs, join_ev[k], 0));
+    }
+    return PVSC_OK;
+  };
+  return run_graph(lats[0], uid, st, body);
 }
 
 static int batched_layout(const pvsc_lattice* const* lats, int n, int R, int prec, int M,
@@ -338,6 +423,10 @@ size_t pvsc_batched_work_bytes(const pvsc_lattice* const* lats, int n, int R, in
   size_t total = 0;
   if (!lats[0]) return 0;
   const BatchShape sh = batch_shape(lats[0], R, prec);
+  if (sh.per_lattice && per_lattice_possible(lats, n, R, prec)) {
+    for (int i = 0; i < n; ++i) total += (per_lattice_bytes(lats[i], R, prec) + 255) & ~size_t(255);
+    return total;
+  }
   if (batched_layout(lats, n, R, prec, M, L, &total, sh.threads, sh.zs) != PVSC_OK) return 0;
   return total;
 }
@@ -356,6 +445,13 @@ int pvsc_kpm_moments_batched(const pvsc_lattice* const* lats, int n, int R, int 
   if (int rc = check_ptr(work, "work")) return rc;
   if (!lats[0]) return set_error(PVSC_ERR_ARG, "lattice 0 is NULL");
   const BatchShape sh = batch_shape(lats[0], R, prec);
+  if (sh.per_lattice && per_lattice_possible(lats, n, R, prec)) {
+    for (int i = 0; i < n; ++i)
+      if (lats[i]->g.model != PVSC_TI || lats[i]->g.zhalo)
+        return set_error(PVSC_ERR_UNSUPPORTED, "batched KPM takes TI lattices without halo planes");
+    return kpm_per_lattice(lats, n, R, prec, seeds, M, a, b, mu, work, work_bytes, sh,
+                           static_cast<cudaStream_t>(stream));
+  }
   const int threads = sh.threads;
   std::vector<BatchLat> L;
   size_t total = 0;
@@ -456,6 +552,9 @@ int pvsc_autotune_batched(pvsc_lattice* const* lats, int n, int R, int prec, con
       for (int zs : {0, 16, 24, 32, 48, 64})
         if (zs == 0 || zs < Lzmax)
           for (int bps : {0, 1}) cands.push_back(pvsc_tuning{th, bps, zs, 0.f, 0, 0, 0, 0});
+  // every lattice's KPM on the TMA-staged sweep, in concurrent chains
+  if (per_lattice_possible(lats, n, R, prec))
+    for (int th : {256, 512}) cands.push_back(pvsc_tuning{th, 0, 0, 0.f, 0, 0, 0, kKernelTma});
   auto saved = l0->tuning.find({R, prec});
   const bool had = saved != l0->tuning.end();
   const pvsc_tuning old = had ? saved->second : pvsc_tuning{};

@@ -105,6 +105,11 @@ static int coef_kind(double re, double im) {
 }
 
 int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStream_t st) {
+  return launch_sweep_shape(lat, prec, feat, p, shape_for(lat, p.R, prec), st);
+}
+
+// As launch_sweep with the launch shape given instead of the lattice's tuning entry.
+int launch_sweep_shape(const pvsc_lattice* lat, int prec, int feat, Sweep& p, LaunchShape sh, cudaStream_t st) {
   p.acc_kind = coef_kind(p.cx_re, p.cx_im) | (coef_kind(p.cy_re, p.cy_im) << 2);
   const double cv[2][2] = {{p.cx_re, p.cx_im}, {p.cy_re, p.cy_im}};
   for (int t = 0; t < 2; ++t)
@@ -112,7 +117,6 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
       p.fc[t][q][0] = (float)cv[t][q];
       p.fc[t][q][1] = (float)(cv[t][q] - (double)p.fc[t][q][0]);
     }
-  LaunchShape sh = shape_for(lat, p.R, prec);
   if (sh.kernel == kKernelKpm2) sh = LaunchShape{};  // a KPM-only choice: single sweeps take the default
   if (lat->g.zhalo) {  // a slab with halo planes: the z-march over its inner planes
     const int zs = sh.zslab;
@@ -382,12 +386,6 @@ static int run_series(const pvsc_lattice* lat, int R, int prec, const void* x, v
   return PVSC_OK;
 }
 
-}  // namespace pvsc
-
-using namespace pvsc;
-
-extern "C" {
-
 // The two-step KPM sweep exists for complex64 TI lattices with R >= 2 and runs
 // when the tuning entry of (R, prec) selects it.
 static bool kpm2_possible(const pvsc_lattice* lat, int R, int prec) {
@@ -398,6 +396,91 @@ static bool kpm2_selected(const pvsc_lattice* lat, int R, int prec) {
   auto it = lat->tuning.find({R, prec});
   return it != lat->tuning.end() && it->second.kernel == kKernelKpm2;
 }
+
+// All kernels of one KPM run (the start block unless given, ceil(M/2) fused
+// sweeps with the doubling identities) enqueued on cs; force: a launch shape for
+// every sweep instead of the lattice's tuning entry (the batched runs).
+int kpm_enqueue(const pvsc_lattice* lat, int R, int prec, const void* r0, uint64_t seed, int M, double a,
+                double b, double* mu, void* work, const LaunchShape* force, cudaStream_t cs) {
+  const size_t voff = (dots_work_bytes(lat, R) + 255) & ~size_t(255);
+  void* wa = wptr(work, voff);
+  void* wb = wptr(work, voff + vec_bytes(lat, R, prec));
+  const int64_t D = lat->g.n_sites * orbitals_of(lat->g.model);
+  const LaunchShape sh = force ? *force : shape_for(lat, R, prec);
+  const bool two = !force && kpm2_selected(lat, R, prec);
+  PVSC_CUDA_TRY(cudaMemsetAsync(work, 0, kWorkHeader, cs));
+  const void* x0 = r0;
+  if (!r0) {
+    if (int rc = launch_random_phase(wa, prec, D, R, seed, cs)) return rc;
+    x0 = wa;
+  }
+  Sweep p;
+  sweep_init(p, lat, R, prec);
+  p.counter = reinterpret_cast<unsigned*>(work);
+  p.partials = reinterpret_cast<double*>(wptr(work, kWorkHeader));
+  p.mu = mu;
+  p.M = M;
+  p.dot_flags = 3;
+  for (int r = 0; r < R; ++r) {
+    p.coef[0][r] = 1.0 / a;
+    p.coef[1][r] = b;
+    p.coef[2][r] = 0.0;
+  }
+  p.x = x0;
+  p.yin = nullptr;
+  p.yout = wb;
+  p.dot_mode = 1;
+  if (int rc = launch_sweep_shape(lat, prec, F_DOTS, p, sh, cs)) return rc;
+  const void* prev = x0;
+  void* cur = wb;
+  const int nsteps = (M + 1) / 2;
+  for (int r = 0; r < R; ++r) {
+    p.coef[0][r] = 2.0 / a;
+    p.coef[2][r] = -1.0;
+  }
+  int k = 1;
+  if (two) {
+    // steps k, k+1 per sweep into two buffers distinct from both inputs
+    void* pool[4] = {wa, wb, wptr(work, voff + 2 * vec_bytes(lat, R, prec)),
+                     wptr(work, voff + 3 * vec_bytes(lat, R, prec))};
+    p.dot_mode = 3;
+    p.dot_flags = 7;
+    for (; k + 1 < nsteps; k += 2) {
+      void* o[2];
+      int no = 0;
+      for (void* q : pool)
+        if (q != prev && q != cur && no < 2) o[no++] = q;
+      p.x = cur;
+      p.yin = prev;
+      p.yout = o[0];
+      p.yout2 = o[1];
+      p.kpm_k = k;
+      if (int rc = launch_kpm2_sweep(lat, p, sh, cs)) return rc;
+      prev = o[0];
+      cur = o[1];
+    }
+    p.dot_flags = 3;
+    p.yout2 = nullptr;
+  }
+  p.dot_mode = 2;
+  for (; k < nsteps; ++k) {
+    void* out = (r0 && prev == r0) ? (cur == wa ? wb : wa) : const_cast<void*>(prev);
+    p.x = cur;
+    p.yin = prev;
+    p.yout = out;
+    p.kpm_k = k;
+    if (int rc = launch_sweep_shape(lat, prec, F_DOTS, p, sh, cs)) return rc;
+    prev = cur;
+    cur = out;
+  }
+  return PVSC_OK;
+}
+
+}  // namespace pvsc
+
+using namespace pvsc;
+
+extern "C" {
 
 size_t pvsc_work_bytes(const pvsc_lattice* lat, int op, int R, int prec, int M) {
   if (lat && valid_R(R) && prec == PVSC_Q64 && op == PVSC_OP_KPM) return fx_layout(lat, R).total;
@@ -604,81 +687,10 @@ int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, u
   const size_t need = pvsc_work_bytes(lat, PVSC_OP_KPM, R, prec, M);
   if (int rc = check_work(work, work_bytes, need)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t voff = (dots_work_bytes(lat, R) + 255) & ~size_t(255);
-  void* wa = wptr(work, voff);
-  void* wb = wptr(work, voff + vec_bytes(lat, R, prec));
-  const int64_t D = lat->g.n_sites * orbitals_of(lat->g.model);
-  const LaunchShape sh = shape_for(lat, R, prec);
-  const bool two = kpm2_selected(lat, R, prec);
   const std::vector<uint64_t> key = {1, (uint64_t)R, (uint64_t)prec, bits(r0), seed, (uint64_t)M,
                                      bits(a), bits(b), bits(mu), bits(work)};
   auto body = [&](cudaStream_t cs) -> int {
-    PVSC_CUDA_TRY(cudaMemsetAsync(work, 0, kWorkHeader, cs));
-    const void* x0 = r0;
-    if (!r0) {
-      if (int rc = launch_random_phase(wa, prec, D, R, seed, cs)) return rc;
-      x0 = wa;
-    }
-    Sweep p;
-    sweep_init(p, lat, R, prec);
-    p.counter = reinterpret_cast<unsigned*>(work);
-    p.partials = reinterpret_cast<double*>(wptr(work, kWorkHeader));
-    p.mu = mu;
-    p.M = M;
-    p.dot_flags = 3;
-    for (int r = 0; r < R; ++r) {
-      p.coef[0][r] = 1.0 / a;
-      p.coef[1][r] = b;
-      p.coef[2][r] = 0.0;
-    }
-    p.x = x0;
-    p.yin = nullptr;
-    p.yout = wb;
-    p.dot_mode = 1;
-    if (int rc = launch_sweep(lat, prec, F_DOTS, p, cs)) return rc;
-    const void* prev = x0;
-    void* cur = wb;
-    const int nsteps = (M + 1) / 2;
-    for (int r = 0; r < R; ++r) {
-      p.coef[0][r] = 2.0 / a;
-      p.coef[2][r] = -1.0;
-    }
-    int k = 1;
-    if (two) {
-      // steps k, k+1 per sweep into two buffers distinct from both inputs
-      void* pool[4] = {wa, wb, wptr(work, voff + 2 * vec_bytes(lat, R, prec)),
-                       wptr(work, voff + 3 * vec_bytes(lat, R, prec))};
-      p.dot_mode = 3;
-      p.dot_flags = 7;
-      for (; k + 1 < nsteps; k += 2) {
-        void* o[2];
-        int no = 0;
-        for (void* q : pool)
-          if (q != prev && q != cur && no < 2) o[no++] = q;
-        p.x = cur;
-        p.yin = prev;
-        p.yout = o[0];
-        p.yout2 = o[1];
-        p.kpm_k = k;
-        if (int rc = launch_kpm2_sweep(lat, p, sh, cs)) return rc;
-        prev = o[0];
-        cur = o[1];
-      }
-      p.dot_flags = 3;
-      p.yout2 = nullptr;
-    }
-    p.dot_mode = 2;
-    for (; k < nsteps; ++k) {
-      void* out = (r0 && prev == r0) ? (cur == wa ? wb : wa) : const_cast<void*>(prev);
-      p.x = cur;
-      p.yin = prev;
-      p.yout = out;
-      p.kpm_k = k;
-      if (int rc = launch_sweep(lat, prec, F_DOTS, p, cs)) return rc;
-      prev = cur;
-      cur = out;
-    }
-    return PVSC_OK;
+    return kpm_enqueue(lat, R, prec, r0, seed, M, a, b, mu, work, nullptr, cs);
   };
   return run_graph(lat, key, st, body);
 }

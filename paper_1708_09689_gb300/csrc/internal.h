@@ -171,6 +171,9 @@ void sweep_init(Sweep& p, const pvsc_lattice* lat, int R, int prec);
 // Launch one fused sweep (feat: F_* mask).  Dot features need p.partials and
 // p.counter inside a work buffer of at least dots_work_bytes(lat, R) bytes.
 int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStream_t st);
+int launch_sweep_shape(const pvsc_lattice* lat, int prec, int feat, Sweep& p, LaunchShape sh, cudaStream_t st);
+int kpm_enqueue(const pvsc_lattice* lat, int R, int prec, const void* r0, uint64_t seed, int M, double a,
+                double b, double* mu, void* work, const LaunchShape* force, cudaStream_t cs);
 size_t dots_work_bytes(const pvsc_lattice* lat, int R);
 size_t vec_bytes(const pvsc_lattice* lat, int R, int prec);  // one D x R block
 

@@ -252,3 +252,44 @@ def test_batch_autotuner_picks_a_shape_and_results_hold():
     for i, (H, (a, b)) in enumerate(zip(Hs, ab)):
         ref = O.kpm_moments(H, W.random_phase_block(H.shape[0], R, seeds[i]), M, a, b).real
         assert np.max(np.abs(mu[i] - ref)) / ref[0, 0] < 1e-4, i
+
+
+def test_per_lattice_batch_on_the_tma_sweep():
+    # tuning kernel 7 on lats[0]: every lattice's KPM runs as its own chain of
+    # TMA-staged sweeps on a few forked streams inside one graph; each chain
+    # equals the single-lattice KPM with that kernel bit for bit
+    specs = [((8, 5, 7), 1.0, 41), ((12, 6, 9), 3.0, 42), ((4, 4, 4), 0.5, 43), ((16, 9, 12), 2.0, 44),
+             ((20, 8, 3), 1.5, 45)]
+    lats, Hs, ab = _lattices(specs)
+    R, M = 8, 40
+    seeds = [200 + i for i in range(len(lats))]
+    a_, b_ = [x[0] for x in ab], [x[1] for x in ab]
+    mu_p = pv.kpm_moments_batched(lats, M, a_, b_, R=R, prec=pv.C64, seeds=seeds).cpu().numpy()
+    lats[0].set_tuning(R, pv.C64, kernel=7)
+    work = pv.work_buffer(pv.batched_work_bytes(lats, R, pv.C64, M))
+    mu_t = pv.kpm_moments_batched(lats, M, a_, b_, R=R, prec=pv.C64, seeds=seeds, work=work)
+    mu_t2 = pv.kpm_moments_batched(lats, M, a_, b_, R=R, prec=pv.C64, seeds=seeds, work=work)
+    assert torch.equal(mu_t, mu_t2)  # the replayed graph
+    assert pv.device_error() == 0
+    mu_t = mu_t.cpu().numpy()
+    assert np.max(np.abs(mu_t - mu_p)) < 1e-9  # same vectors as the persistent kernel's z-march
+    for i, lat in enumerate(lats):
+        lat.set_tuning(R, pv.C64, kernel=7)
+        mu_s = pv.kpm_moments(lat, M, a_[i], b_[i], R=R, prec=pv.C64, seed=seeds[i]).cpu().numpy()
+        assert np.array_equal(mu_t[i], mu_s), i
+        r = W.random_phase_block(Hs[i].shape[0], R, seeds[i])
+        ref = O.kpm_moments(Hs[i], r, M, a_[i], b_[i]).real
+        assert np.max(np.abs(mu_t[i] - ref)) / ref[0, 0] < 1e-4, i
+
+
+def test_per_lattice_batch_falls_back_where_the_tma_sweep_does_not_apply():
+    # Lx = 6 (not a multiple of 4) has no TMA-staged sweep: the persistent kernel runs
+    lats, Hs, ab = _lattices([((6, 4, 5), 1.0, 51), ((8, 4, 5), 2.0, 52)])
+    R, M = 4, 24
+    a_, b_ = [x[0] for x in ab], [x[1] for x in ab]
+    lats[1].set_tuning(R, pv.C64, kernel=7)
+    mu = pv.kpm_moments_batched(lats[::-1], M, a_[::-1], b_[::-1], R=R, prec=pv.C64, seeds=[3, 4]).cpu().numpy()
+    for j, i in enumerate((1, 0)):
+        r = W.random_phase_block(Hs[i].shape[0], R, [3, 4][j])
+        ref = O.kpm_moments(Hs[i], r, M, a_[i], b_[i]).real
+        assert np.max(np.abs(mu[j] - ref)) / ref[0, 0] < 1e-4
