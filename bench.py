@@ -575,6 +575,8 @@ def run_workload(args, pv, dev, rank, world):
         lat = pv.Lattice.wsm(dims, (1, 1, 0), disorder=(1.0, 11))
         emin, emax, a, b = lat.spectral_bounds()
         if args.sweeps_only:  # profiling case: one KPM call of this many sweeps, untimed
+            if args.launch:
+                lat.set_tuning(R, pv.C64, **{k: v for k, v in json.loads(args.launch).items() if k != "time_ms"})
             r0 = pv.random_vectors(lat, R, pv.C64, 13)
             mu = pv.kpm_moments(lat, 2 * args.sweeps_only, a, b, r0=r0)
             torch.cuda.synchronize()

@@ -453,7 +453,9 @@ __global__ void __launch_bounds__(32 * NW, 1)
       if (ahead_y(lu, j, L::NYS)) issue_y(lu, j, k + L::NYS);
   };
 
-  if (threadIdx.x == 0) {
+  // a block without a plane of work (more blocks than planes) issues no copy:
+  // its unit table is empty
+  if (threadIdx.x == 0 && nlu > 0) {
     prefetch_map(&m.xi);
     prefetch_map(&m.xs);
     prefetch_map(&m.ys);
@@ -915,6 +917,9 @@ static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const Launc
   m.nch = nch;
   m.nunits = ntiles * nch;  // per slice
   p.zslab = (int)((Lz + nch - 1) / nch);
+  // no more blocks than units: with fewer units than SMs, splitting columns over
+  // all SMs was measured slower (the Weyl cuboid 77.9 -> 72.2 GLUP/s: pieces at
+  // staggered depths lose the halo strips' L2 reuse)
   const int grid = (int)(SL * (m.nunits < grid_max ? m.nunits : grid_max));
   void* args[] = {&p, &m};
   PVSC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(32 * NW), args, L::SMEM, st));
