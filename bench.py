@@ -885,12 +885,17 @@ def main():
         r0_host = r0.cpu().pin_memory()
         mu_host = torch.empty((R, M), dtype=torch.float64).pin_memory()
         r0_dev = torch.empty_like(r0)
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
+
+        def e2e_step():
             r0_dev.copy_(r0_host, non_blocking=True)
             pv.kpm_moments(lat, M, a, b, r0=r0_dev, work=work, mu=mu)
             mu_host.copy_(mu, non_blocking=True)
+        for _ in range(args.warmup):  # untimed: the first call with this start block captures its graph
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
         barrier()
         te = max_over_ranks((time.perf_counter() - t0) / args.steps, dev)
         e2e = {"value": round(world * lups_per_step / te / 1e9, 3), "unit": UNIT,
