@@ -544,7 +544,7 @@ typedef struct {
                   /* 64 run as 2 and 4 slices of 16 vectors on the 8x8 tiles, one slice */
                   /* per block; tile_x x tile_y = the half tile (32x16, 32x8, 16x8, 16x4, */
                   /* 8x4, 8x4, 8x4 for R = 1 .. 64) selects rings one plane deeper on eight warps */
-                  /* (TI; Weyl cells run the large tile on eight warps); zslab = z-chunk */
+                  /* (Weyl cells run eight warps, the large or the half tile); zslab = z-chunk */
                   /* depth (0: chosen from the grid size); vpt is ignored. */
                   /* 8 (as kernel 7) the same tiles marching along x over (y, z) columns, */
                   /* for lattices whose z columns are short; eight warps, the large or */

@@ -197,10 +197,9 @@ extern "C" int pvsc_autotune_op(pvsc_lattice* lat, int R, int prec, int op, pvsc
     for (int zs : {0, 16, 32, 64})
       if (zs == 0 || zs < lat->g.L[2]) {
         cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, 0, 0, kKernelTma});
-        if (lat->g.model == PVSC_TI) {  // the Weyl cells run the large tile only
+        cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, deep_x, deep_y, kKernelTma});
+        if (lat->g.model == PVSC_TI)  // the Weyl cells run eight warps only
           cands.push_back(pvsc_tuning{512, 0, zs, 0.f, 2, 0, 0, kKernelTma});
-          cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, deep_x, deep_y, kKernelTma});
-        }
       }
     // the same tiles marching along x, where the z columns are the shorter
     if (lat->g.L[0] > lat->g.L[2] && tma_xm_possible(lat, R, prec))

@@ -5,7 +5,7 @@
 // quarter-warp reads are consecutive along x, which that swizzle spreads over
 // the 8 bank groups.  TI lattices in every launch variant (the large tile on
 // 8 or 16 warps, the half tile with deeper rings), Weyl cells on the large
-// tile.  This unit's kernels report copy-wait timeouts in its own error word.
+// and the half tile.  This unit's kernels report copy-wait timeouts in its own error word.
 #include "sweep_tma.cuh"
 
 namespace pvsc {
@@ -14,7 +14,9 @@ bool tma_tile_deep(int R, int tile_y);
 
 template <int R>
 static int launch_narrow(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
-  if (lat->g.model == PVSC_WSM) return launch_tma_r<R, false, 8, PVSC_WSM>(lat, feat, p, sh, st);
+  if (lat->g.model == PVSC_WSM)
+    return tma_tile_deep(R, sh.tile_y) ? launch_tma_r<R, true, 8, PVSC_WSM>(lat, feat, p, sh, st)
+                                       : launch_tma_r<R, false, 8, PVSC_WSM>(lat, feat, p, sh, st);
   if (tma_tile_deep(R, sh.tile_y)) return launch_tma_r<R, true, 8>(lat, feat, p, sh, st);
   if (sh.threads == 512) return launch_tma_r<R, false, 16>(lat, feat, p, sh, st);
   return launch_tma_r<R, false, 8>(lat, feat, p, sh, st);

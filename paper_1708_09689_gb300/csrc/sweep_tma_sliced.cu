@@ -3,7 +3,7 @@
 // (8 x 8 sites, or the 8 x 4 half tile with deeper rings): the 4 x 4 and 4 x 2
 // tiles that fit shared memory with whole 1 KB and 2 KB sites copy halo strips as
 // large as the tile.  TI lattices in every launch variant, Weyl-semimetal cells
-// on the large tile.  This unit's kernels report copy-wait timeouts in its own
+// on the large and the half tile.  This unit's kernels report copy-wait timeouts in its own
 // error word.
 #include "sweep_tma.cuh"
 
@@ -13,7 +13,9 @@ bool tma_tile_deep(int R, int tile_y);
 
 template <int SL>
 static int launch_sliced(const pvsc_lattice* lat, int feat, Sweep& p, const LaunchShape& sh, cudaStream_t st) {
-  if (lat->g.model == PVSC_WSM) return launch_tma_r<16, false, 8, PVSC_WSM, SL>(lat, feat, p, sh, st);
+  if (lat->g.model == PVSC_WSM)
+    return tma_tile_deep(p.R, sh.tile_y) ? launch_tma_r<16, true, 8, PVSC_WSM, SL>(lat, feat, p, sh, st)
+                                         : launch_tma_r<16, false, 8, PVSC_WSM, SL>(lat, feat, p, sh, st);
   if (tma_tile_deep(p.R, sh.tile_y)) return launch_tma_r<16, true, 8, PVSC_TI, SL>(lat, feat, p, sh, st);
   if (sh.threads == 512) return launch_tma_r<16, false, 16, PVSC_TI, SL>(lat, feat, p, sh, st);
   return launch_tma_r<16, false, 8, PVSC_TI, SL>(lat, feat, p, sh, st);

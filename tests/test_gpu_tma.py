@@ -175,6 +175,8 @@ def test_tma_weyl_cells_equal_the_cell_sweeps_and_oracle(dims, per, R):
     if R >= 4:                                    # the cells marching along x (R >= 4)
         lat.set_tuning(R, pv.C64, kernel=8)
         assert torch.equal(pv.apply_H(lat, x), y_flat)
+    lat.set_tuning(R, pv.C64, kernel=7, **_variant(R, "deep"))  # the half tile
+    assert torch.equal(pv.apply_H(lat, x), y_flat)
     lat.set_tuning(R, pv.C64, kernel=7)
     y_tma = pv.apply_H(lat, x)
     assert torch.equal(y_tma, y_march) and torch.equal(y_tma, y_flat)
