@@ -1,5 +1,7 @@
 // TI sweep with tensor-memory-accelerator (TMA) staging of z-plane tiles
-// (tuning kernel 7), complex64 storage, R = 4 .. 64.
+// (tuning kernel 7; kernel 8 marches the same tiles along x), complex64
+// storage, R = 1 .. 64; the same kernel carries the Weyl-semimetal cells and
+// the fixed-point (PVSC_Q64) KPM sweep.
 //
 // The stencil of Eq. TB_H_topi reads every x element of a plane seven times
 // (the site itself and its six neighbours).  Here a block owns a tile of
@@ -23,11 +25,14 @@
 // threads share a site, and the sites of a warp are permuted so that the 8
 // threads of every quarter-warp hit 8 distinct bank groups for the centre,
 // x+-1, y+-1 and z+1 blocks alike (conflict-free 128-bit shared loads).
+// R = 1, 2: a copied row is one 32- or 64-byte site under the 32- or 64-byte
+// swizzle and one thread owns a site; R = 32, 64: slices of 16 vectors.
 //
 // Work units are (z-chunk, tile) pairs taken in wave order (tiles fastest),
 // unit u on block u mod grid: the grid (one block per SM) works on adjacent
 // tiles at the same depth, so halo strips that another tile also reads come
-// from L2.  The arithmetic, its order and the epilogue are those of the
+// from L2; the planes of the units after the last full wave are split evenly
+// over the grid.  The arithmetic, its order and the epilogue are those of the
 // register z-march (ti_axes / ti_combine / epilogue of sweep.cuh), so the
 // vectors equal that sweep's bit for bit.
 //
