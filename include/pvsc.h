@@ -568,7 +568,7 @@ int pvsc_get_tuning(const pvsc_lattice* lat, int R, int prec, pvsc_tuning* tunin
 int pvsc_autotune(pvsc_lattice* lat, int R, int prec, pvsc_tuning* best, void* stream);
 /* pvsc_autotune timing the sweeps of one operation: PVSC_OP_KPM (what
  * pvsc_autotune times: the recurrence sweep with its dot products),
- * PVSC_OP_SERIES (the accumulating and the plain sweep of pvsc_cheb_series,
+ * PVSC_OP_SERIES (one accumulating and two plain sweeps of pvsc_cheb_series,
  * pvsc_cheb_filter, pvsc_cheb_propagate and ChebFD's filter) or PVSC_OP_APPLY
  * (the plain sweep).  The winner replaces the (R, prec) tuning entry; the
  * on-disk cache keys on the operation too. */

@@ -5,8 +5,8 @@
 // chosen by measurement instead: threads per block, resident blocks per SM
 // and z-slab depth are swept with CUDA events on the caller's stream, timing
 // the sweeps of the operation that will run (KPM: recurrence update + fp64 dot
-// products; series: the accumulating sweep and the plain one it alternates
-// with; apply: the plain sweep), and the fastest shape is stored in the
+// products; series: the accumulating sweep and the two plain ones that
+// follow it; apply: the plain sweep), and the fastest shape is stored in the
 // lattice handle.
 // With PVSC_TUNE_CACHE=<file> results are kept on disk, keyed by model,
 // dimensions, boundary conditions, R, precision and device name.
@@ -126,7 +126,7 @@ extern "C" int pvsc_autotune_op(pvsc_lattice* lat, int R, int prec, int op, pvsc
   pvsc_tuning win{256, 0, 0, 1e30f, 0, 0, 0, 0};
   // time one candidate shape: one warm sweep, then the mean of three, with the
   // sweep features of the operation: KPM (recurrence + dots), series (the
-  // accumulating sweep and the plain one it alternates with), apply (plain)
+  // accumulating sweep and the two plain ones that follow it), apply (plain)
   auto time_one = [&](const pvsc_tuning& cand, float* ms) -> int {
     lat->tuning[{R, prec}] = cand;
     Sweep p;
@@ -146,14 +146,16 @@ extern "C" int pvsc_autotune_op(pvsc_lattice* lat, int R, int prec, int op, pvsc
     p.partials = reinterpret_cast<double*>(static_cast<char*>(work) + kWorkHeader);
     p.acc = static_cast<double2*>(acc);
     p.acc_out = static_cast<double2*>(acc);
-    p.acc_mode = ACC_ADD | ACC_X;
+    p.acc_mode = ACC_ADD | ACC_X | (op == PVSC_OP_APPLY ? 0 : ACC_YIN);
     p.cx_re = 0.3;
     p.cy_im = -0.2;
+    p.cz_re = -0.1;
     PVSC_CUDA_TRY(cudaMemsetAsync(work, 0, kWorkHeader, st));
     auto one = [&]() -> int {
       if (op == PVSC_OP_KPM) return launch_sweep(lat, prec, F_DOTS, p, st);
       if (op == PVSC_OP_APPLY) return launch_sweep(lat, prec, 0, p, st);
       if (int r = launch_sweep(lat, prec, F_ACC, p, st)) return r;
+      if (int r = launch_sweep(lat, prec, 0, p, st)) return r;
       return launch_sweep(lat, prec, 0, p, st);
     };
     if (int r = one()) return r;

@@ -241,11 +241,12 @@ struct Sweep {
   double coef[4][kMaxR]; // alpha, beta, gamma, delta per vector
   // series accumulation (complex128 accumulator)
   int acc_mode;          // AccMode bits (below)
-  int acc_kind;          // set at launch: bits 0-1 kind of cx, 2-3 kind of cy (1 real, 2 imaginary, 3 zero)
+  int acc_kind;          // set at launch: bits 0-1 kind of cx, 2-3 of cy, 4-5 of cz (1 real, 2 imaginary, 3 zero)
   double2* acc;
   double2* acc_out;      // final: written here
   double cx_re, cx_im, cy_re, cy_im, ph_re, ph_im;
-  float fc[2][2][2];     // set at launch: [cx, cy][re, im][hi, lo], value = hi + lo in fp32
+  double cz_re, cz_im;   // weight of y_in (ACC_YIN)
+  float fc[3][2][2];     // set at launch: [cx, cy, cz][re, im][hi, lo], value = hi + lo in fp32
   // adjoint source and gradient
   const double2* src;    // y_new += sigma * src (complex128)
   double sg_re, sg_im;
@@ -271,10 +272,12 @@ struct Sweep {
   QDScal qds;            // graphene quantum-dot array (g.v_mode 3): range-test scalars
 };
 
-// acc_new = [INIT ? 0 : acc] + [X ? cx x : 0] + cy y_new, with x the sweep's
-// input, or under XSRC the complex128 vector src; FINAL writes ph acc_new to
-// acc_out instead of acc.
-enum AccMode { ACC_NONE = 0, ACC_INIT = 1, ACC_ADD = 2, ACC_FINAL = 4, ACC_X = 8, ACC_XSRC = 16 };
+// acc_new = [INIT ? 0 : acc] + [YIN ? cz y_in : 0] + [X ? cx x : 0] + cy y_new,
+// with x the sweep's input, or under XSRC the complex128 vector src, and y_in
+// its value before the sweep (the series writes y_new over it); FINAL writes
+// ph acc_new to acc_out instead of acc.  YIN comes with X, and with neither
+// INIT nor XSRC.
+enum AccMode { ACC_NONE = 0, ACC_INIT = 1, ACC_ADD = 2, ACC_FINAL = 4, ACC_X = 8, ACC_XSRC = 16, ACC_YIN = 32 };
 
 // ---------------------------------------------------------------- deterministic dot reduction
 // acc[d][v]: per-thread fp64 partial sums of dot d for vector rc*VPT+v.  Every

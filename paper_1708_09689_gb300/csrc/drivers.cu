@@ -110,9 +110,14 @@ int launch_sweep(const pvsc_lattice* lat, int prec, int feat, Sweep& p, cudaStre
 
 // As launch_sweep with the launch shape given instead of the lattice's tuning entry.
 int launch_sweep_shape(const pvsc_lattice* lat, int prec, int feat, Sweep& p, LaunchShape sh, cudaStream_t st) {
-  p.acc_kind = coef_kind(p.cx_re, p.cx_im) | (coef_kind(p.cy_re, p.cy_im) << 2);
-  const double cv[2][2] = {{p.cx_re, p.cx_im}, {p.cy_re, p.cy_im}};
-  for (int t = 0; t < 2; ++t)
+  if ((feat & F_ACC) && (p.acc_mode & ACC_YIN) &&
+      (!p.yin || !(p.acc_mode & ACC_X) || (p.acc_mode & (ACC_INIT | ACC_XSRC))))
+    return set_error(PVSC_ERR_ARG, "an accumulating sweep with the y_in term needs y_in and the x term, "
+                                   "and no INIT or XSRC");
+  p.acc_kind = coef_kind(p.cx_re, p.cx_im) | (coef_kind(p.cy_re, p.cy_im) << 2) |
+               (coef_kind(p.cz_re, p.cz_im) << 4);
+  const double cv[3][2] = {{p.cx_re, p.cx_im}, {p.cy_re, p.cy_im}, {p.cz_re, p.cz_im}};
+  for (int t = 0; t < 3; ++t)
     for (int q = 0; q < 2; ++q) {
       p.fc[t][q][0] = (float)cv[t][q];
       p.fc[t][q][1] = (float)(cv[t][q] - (double)p.fc[t][q][0]);
@@ -326,15 +331,18 @@ static int run_series(const pvsc_lattice* lat, int R, int prec, const void* x, v
     }
   };
   // Sweep j makes w_j from x = w_{j-1} and y_in = w_{j-2}.  The accumulator
-  // takes two terms per touch: sweep 1 starts it with cw_0 w_0 + cw_1 w_1,
-  // every odd sweep j adds cw_{j-1} w_{j-1} + cw_j w_j, even sweeps leave it
-  // alone, and the last sweep adds what is left and writes phase * acc to y.
-  auto set_acc = [&](int j, int mode, bool with_x) {
+  // takes up to three terms per touch: sweep 1 starts it with cw_0 w_0 +
+  // cw_1 w_1, sweeps j = 4, 7, 10, ... add cw_{j-2} w_{j-2} + cw_{j-1} w_{j-1}
+  // + cw_j w_j, the others leave it alone, and the last sweep adds the one to
+  // three terms left and writes phase * acc to y.
+  auto set_acc = [&](int j, int mode, int nterms) {
     p.acc = acc;
     p.acc_out = static_cast<double2*>(y);
-    p.acc_mode = mode | (with_x ? ACC_X : 0);
-    p.cx_re = with_x ? cw[j - 1].real() : 0.0;
-    p.cx_im = with_x ? cw[j - 1].imag() : 0.0;
+    p.acc_mode = mode | (nterms >= 2 ? ACC_X : 0) | (nterms == 3 ? ACC_YIN : 0);
+    p.cx_re = nterms >= 2 ? cw[j - 1].real() : 0.0;
+    p.cx_im = nterms >= 2 ? cw[j - 1].imag() : 0.0;
+    p.cz_re = nterms == 3 ? cw[j - 2].real() : 0.0;
+    p.cz_im = nterms == 3 ? cw[j - 2].imag() : 0.0;
     p.cy_re = cw[j].real();
     p.cy_im = cw[j].imag();
     p.ph_re = phase.real();
@@ -347,7 +355,7 @@ static int run_series(const pvsc_lattice* lat, int R, int prec, const void* x, v
   if (prec == PVSC_C128) {
     p.x = x;
     p.yout = wa;
-    set_acc(1, ACC_INIT, true);
+    set_acc(1, ACC_INIT, 2);
     if (int rc = launch_sweep(lat, prec, F_ACC, p, st)) return rc;
     // y may alias x: the final write is a separate pass
     if (K == 2) return launch_scale_init(acc, static_cast<double2*>(y), phase.real(), phase.imag(), n, st);
@@ -359,7 +367,7 @@ static int run_series(const pvsc_lattice* lat, int R, int prec, const void* x, v
     p.x = wb;
     p.src = static_cast<const double2*>(x);
     p.yout = (K == 2) ? nullptr : wa;
-    set_acc(1, ACC_INIT | ACC_XSRC | (K == 2 ? ACC_FINAL : 0), true);
+    set_acc(1, ACC_INIT | ACC_XSRC | (K == 2 ? ACC_FINAL : 0), 2);
     if (int rc = launch_sweep(lat, prec, F_ACC, p, st)) return rc;
     p.src = nullptr;
     if (K == 2) return PVSC_OK;
@@ -367,6 +375,7 @@ static int run_series(const pvsc_lattice* lat, int R, int prec, const void* x, v
     cur = wa;
   }
   p.yin = nullptr;
+  int done = 1;  // the accumulator holds the terms 0 .. done
   for (int j = 2; j < K; ++j) {
     const bool last = (j == K - 1);
     void* out = (prev == x) ? wb : const_cast<void*>(prev);
@@ -375,9 +384,10 @@ static int run_series(const pvsc_lattice* lat, int R, int prec, const void* x, v
     p.yin = prev;
     p.yout = last ? nullptr : out;
     int feat = 0;
-    if (j % 2 == 1 || last) {
-      set_acc(j, ACC_ADD | (last ? ACC_FINAL : 0), j % 2 == 1);
+    if (j - done == 3 || last) {
+      set_acc(j, ACC_ADD | (last ? ACC_FINAL : 0), j - done);
       feat = F_ACC;
+      done = j;
     }
     if (int rc = launch_sweep(lat, prec, feat, p, st)) return rc;
     prev = cur;

@@ -273,31 +273,57 @@ __device__ __forceinline__ void cfma_acc(double cr, double ci, int kind, double 
   }
 }
 
-// (sr, si) += c (xr + i xi) in fp32, same kinds as cfma_acc, with the
-// coefficient c = (re, im) as unevaluated fp32 sums hi + lo (c[part][0] hi,
-// c[part][1] lo): the product then carries the coefficient to about 2^-48,
-// and what remains is the rounding of the sum, which varies with the data
-// instead of repeating the same relative error on every series evaluation.
-__device__ __forceinline__ void cfma_f32(const float (&c)[2][2], int kind, float xr, float xi,
-                                         float& sr, float& si) {
-  if (kind == 1) {
-    sr = fmaf(c[0][0], xr, fmaf(c[0][1], xr, sr));
-    si = fmaf(c[0][0], xi, fmaf(c[0][1], xi, si));
-  } else if (kind == 2) {
-    sr = fmaf(-c[1][0], xi, fmaf(-c[1][1], xi, sr));
-    si = fmaf(c[1][0], xr, fmaf(c[1][1], xr, si));
-  } else if (kind == 0) {
-    sr = fmaf(c[0][0], xr, fmaf(-c[1][0], xi, fmaf(c[0][1], xr, fmaf(-c[1][1], xi, sr))));
-    si = fmaf(c[0][0], xi, fmaf(c[1][0], xr, fmaf(c[0][1], xi, fmaf(c[1][1], xr, si))));
+// A compensated fp32 sum of products: the value is S + E, where every product
+// a b = p + q exactly (q by FMA) and every addition S + p = s + e exactly
+// (Knuth's TwoSum) keep their errors in E; S + E is rounded once at the end.
+// The round-off of an uncompensated chain of partial sums is correlated with
+// the recurring series weights and the terms they multiply, which biases the
+// result; the compensated sum is rounded like the exact one.  The _rn
+// intrinsics keep the compiler from contracting these steps into FMAs.
+struct CSum {
+  float S, E;
+};
+
+__device__ __forceinline__ void csum_add(CSum& c, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float q = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(c.S, p);
+  const float bb = __fsub_rn(s, c.S);
+  const float e = __fadd_rn(__fsub_rn(c.S, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  c.S = s;
+  c.E = __fadd_rn(c.E, __fadd_rn(q, e));
+}
+
+// (sr, si) += w (xr + i xi) with the weight w = (re, im) given as fp32 pairs
+// hi + lo (w[part][0] hi, w[part][1] lo), so that the product carries the
+// weight to about 2^-48 instead of repeating one fp32 rounding of it on every
+// series evaluation: the hi products enter compensated, the lo products
+// (about 2^-24 of them) go straight into E.  kind as cfma_acc.
+__device__ __forceinline__ void csum_cfma(const float (&w)[2][2], int kind, float xr, float xi, CSum& sr,
+                                          CSum& si) {
+  if (kind == 1 || kind == 0) {
+    csum_add(sr, w[0][0], xr);
+    sr.E = __fmaf_rn(w[0][1], xr, sr.E);
+    csum_add(si, w[0][0], xi);
+    si.E = __fmaf_rn(w[0][1], xi, si.E);
+  }
+  if (kind == 2 || kind == 0) {
+    csum_add(sr, -w[1][0], xi);
+    sr.E = __fmaf_rn(-w[1][1], xi, sr.E);
+    csum_add(si, w[1][0], xr);
+    si.E = __fmaf_rn(w[1][1], xr, si.E);
   }
 }
 
 // ---------------------------------------------------------------- the shared epilogue
-// Everything a sweep does after y_new of one block is known.
+// Everything a sweep does after y_new of one block is known.  yi: the block's
+// y_in as the sweep read it (read only by an accumulating sweep that takes the
+// y_in term, which the driver runs with y_in only).
 template <typename T, int VPT, int FEAT>
 __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, const Blk<T, VPT>& xc,
                                          Blk<T, VPT>& yn, DotAcc<T, VPT>& dacc,
-                                         const int64_t* site_of /* 4 sites of the block */) {
+                                         const int64_t* site_of /* 4 sites of the block */,
+                                         const Blk<T, VPT>& yi) {
   const int R = p.R;
   if constexpr ((FEAT & F_ADJ) != 0) {
     // y_new += sigma * src (complex128 source)
@@ -325,10 +351,12 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
     store_blk<T, VPT>(static_cast<T*>(p.z), s, R, rc, zb);
   }
   if constexpr ((FEAT & F_ACC) != 0) {
-    // acc (+)= cx x + cy y_new, where x is this sweep's input (or the
-    // complex128 source) and y_new its output: with two terms per sweep the
-    // driver touches the accumulator on every other sweep only.
+    // acc (+)= cz y_in + cx x + cy y_new, where x is this sweep's input (or
+    // the complex128 source), y_in the vector y_new replaces and y_new its
+    // output: with three terms per sweep the driver touches the accumulator on
+    // every third sweep only.
     const int mode = p.acc_mode;
+    const int kx = p.acc_kind & 3, ky = (p.acc_kind >> 2) & 3, kz = (p.acc_kind >> 4) & 3;
 #pragma unroll
     for (int o = 0; o < 4; ++o)
 #pragma unroll
@@ -342,11 +370,16 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
         }
         if constexpr (sizeof(T) == 4) {
           if (!(mode & ACC_XSRC)) {
-            // complex64 vectors: the one- or two-term combination in fp32,
-            // added to the fp64 accumulator with one fp64 add per part
-            float sr = 0.f, si = 0.f;
-            if (mode & ACC_X) cfma_f32(p.fc[0], p.acc_kind & 3, xc.v[o][v].re, xc.v[o][v].im, sr, si);
-            cfma_f32(p.fc[1], p.acc_kind >> 2, yn.v[o][v].re, yn.v[o][v].im, sr, si);
+            // complex64 vectors: the one to three terms as a compensated fp32
+            // sum, rounded once and added to the fp64 accumulator with one fp64
+            // add per part.  (A plain fp32 chain of three terms is biased for the
+            // recurring weights of a propagation: the norm of the state drifts
+            // by ~1e-8 per time step.)
+            CSum cr{0.f, 0.f}, ci{0.f, 0.f};
+            if (mode & ACC_YIN) csum_cfma(p.fc[2], kz, yi.v[o][v].re, yi.v[o][v].im, cr, ci);
+            if (mode & ACC_X) csum_cfma(p.fc[0], kx, xc.v[o][v].re, xc.v[o][v].im, cr, ci);
+            csum_cfma(p.fc[1], ky, yn.v[o][v].re, yn.v[o][v].im, cr, ci);
+            const float sr = __fadd_rn(cr.S, cr.E), si = __fadd_rn(ci.S, ci.E);
             if (mode & ACC_INIT) {
               ar = widen(sr);
               ai = widen(si);
@@ -356,11 +389,11 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
             }
           } else {
             const double2 h = *acc_ptr(const_cast<double2*>(p.src), s, o, R, r);
-            cfma_acc(p.cx_re, p.cx_im, p.acc_kind & 3, h.x, h.y, ar, ai);
-            cfma_acc(p.cy_re, p.cy_im, p.acc_kind >> 2, widen(yn.v[o][v].re), widen(yn.v[o][v].im),
-                     ar, ai);
+            cfma_acc(p.cx_re, p.cx_im, kx, h.x, h.y, ar, ai);
+            cfma_acc(p.cy_re, p.cy_im, ky, widen(yn.v[o][v].re), widen(yn.v[o][v].im), ar, ai);
           }
         } else {
+          if (mode & ACC_YIN) cfma_acc(p.cz_re, p.cz_im, kz, yi.v[o][v].re, yi.v[o][v].im, ar, ai);
           if (mode & ACC_X) {
             double xr = xc.v[o][v].re, xi = xc.v[o][v].im;
             if (mode & ACC_XSRC) {
@@ -368,9 +401,9 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
               xr = h.x;
               xi = h.y;
             }
-            cfma_acc(p.cx_re, p.cx_im, p.acc_kind & 3, xr, xi, ar, ai);
+            cfma_acc(p.cx_re, p.cx_im, kx, xr, xi, ar, ai);
           }
-          cfma_acc(p.cy_re, p.cy_im, p.acc_kind >> 2, yn.v[o][v].re, yn.v[o][v].im, ar, ai);
+          cfma_acc(p.cy_re, p.cy_im, ky, yn.v[o][v].re, yn.v[o][v].im, ar, ai);
         }
         if (mode & ACC_FINAL) {
           *acc_ptr(p.acc_out, s, o, R, r) =
@@ -426,6 +459,18 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
       if (p.dot_flags & 4) dacc.add(3, v, yy);
     }
   }
+}
+
+// The epilogue for a sweep that keeps no y_in block: an accumulating sweep
+// that takes the y_in term reads it here, before y_new is stored over it.
+template <typename T, int VPT, int FEAT>
+__device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, const Blk<T, VPT>& xc,
+                                         Blk<T, VPT>& yn, DotAcc<T, VPT>& dacc, const int64_t* site_of) {
+  Blk<T, VPT> yi;
+  if constexpr ((FEAT & F_ACC) != 0) {
+    if (p.acc_mode & ACC_YIN) load_blk<T, VPT, false>(static_cast<const T*>(p.yin), s, p.R, rc, yi);
+  }
+  epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, site_of, yi);
 }
 
 // ---------------------------------------------------------------- TI sweep
@@ -856,7 +901,7 @@ __global__ void __launch_bounds__(256) ti_sweep_xmarch(const __grid_constant__ S
       ti_axes(za, zb, xm, xp, ya, yb, S, D);
       ti_combine(cf, Vs, xc, S, D, Yin != nullptr ? &yi : nullptr, yn, g);
       const int64_t sites[4] = {s, s, s, s};
-      epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
+      epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites, yi);
       xm = xc;
       xc = xp;
     }
@@ -950,7 +995,7 @@ __global__ void __launch_bounds__(256, 2) ti_sweep_flat(const __grid_constant__ 
     }
     if (p.g.has_delta) ti_add_delta(p.g, cf, xc, yn);
     const int64_t sites[4] = {s, s, s, s};
-    epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites);
+    epilogue<T, VPT, FEAT>(p, s, rc, xc, yn, dacc, sites, yi);
   }
   if constexpr (has_dots(FEAT)) {
     dacc.flush();
@@ -1181,7 +1226,7 @@ __global__ void __launch_bounds__(256, 2) wsm_sweep(const __grid_constant__ Swee
     wsm_cell_update(cf, V0, V1, n[0], xc, n[1], n[2], n[3], n[4], n[5], p.yin != nullptr ? &yi : nullptr,
                     yn);
     const int64_t sites[4] = {2 * c, 2 * c, 2 * c + 1, 2 * c + 1};
-    epilogue<T, VPT, FEAT>(p, c, rc, xc, yn, dacc, sites);
+    epilogue<T, VPT, FEAT>(p, c, rc, xc, yn, dacc, sites, yi);
   }
   if constexpr (has_dots(FEAT)) {
     dacc.flush();

@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
             else
               wsm_cell_update(cf, V0, V1, xmr[i], xc, xp, ax, bx, ay, by, m.has_yin ? &yi : nullptr, yn);
             const int64_t sites[4] = {2 * s, 2 * s, 2 * s + 1, 2 * s + 1};
-            epilogue<float, VP, FEAT>(p, s, cg, xc, yn, dacc, sites);
+            epilogue<float, VP, FEAT>(p, s, cg, xc, yn, dacc, sites, yi);
             xmr[i] = xc;
             continue;
           }
@@ -720,7 +720,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
           const float Vs = m.v_tma ? *reinterpret_cast<const float*>(sy + Vo[i]) : site_potential_t<float>(g, s);
           ti_combine(cf, Vs, xc, S, D, m.has_yin ? &yi : nullptr, yn, g);
           const int64_t sites[4] = {s, s, s, s};
-          epilogue<float, VP, FEAT>(p, s, cg, xc, yn, dacc, sites);
+          epilogue<float, VP, FEAT>(p, s, cg, xc, yn, dacc, sites, yi);
           xmr[i] = xc;
         }
       }

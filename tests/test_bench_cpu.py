@@ -17,11 +17,14 @@ def test_series_bytes_per_site_by_hand():
     # K = 3: conversion of w_0 (16 + 8), sweep 1 (x 8, w_1 8, psi 16, acc 16, V 4),
     # last sweep (x 8, y_in 8, V 4, acc 16, psi 16)
     assert bench.series_bytes_per_site(3) == 24 + 52 + 52
-    # K = 5 adds sweeps j = 2 (28) and j = 3 (28 + 32 accumulator)
-    assert bench.series_bytes_per_site(5) == 24 + 52 + 52 + 28 + 60
-    # the graphene workload's 20 terms, stored and regenerated potential
-    assert bench.series_bytes_per_site(20) == 860.0
-    assert bench.series_bytes_per_site(20, 0.0) == 860.0 - 19 * 4
+    # K = 5 adds sweeps j = 2 and 3 (28 each; the accumulator waits for the last sweep)
+    assert bench.series_bytes_per_site(5) == 24 + 52 + 52 + 28 + 28
+    # K = 6 adds sweep j = 4, which adds terms 2, 3, 4 to the accumulator (28 + 32)
+    assert bench.series_bytes_per_site(6) == 24 + 52 + 52 + 28 + 28 + 60
+    # the graphene workload's 20 terms (17 middle sweeps, five of them touch the
+    # accumulator: j = 4, 7, 10, 13, 16), stored and regenerated potential
+    assert bench.series_bytes_per_site(20) == 24 + 2 * 52 + 17 * 28 + 5 * 32 == 764.0
+    assert bench.series_bytes_per_site(20, 0.0) == 764.0 - 19 * 4
     with pytest.raises(ValueError):
         bench.series_bytes_per_site(2)
 

@@ -243,7 +243,7 @@ def test_chebyshev_filter_matches_oracle():
         assert relerr(host(y), ref) < tol
 
 
-@pytest.mark.parametrize("K", [1, 2, 3, 4, 9, 10])
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 @pytest.mark.parametrize("pattern", ["complex", "zeros"])
 def test_cheb_series_short_and_in_place(K, pattern):
     lat, H, _ = gr_pair((4, 5), (0, 0))
