@@ -147,8 +147,8 @@ extern "C" int pvsc_autotune_op(pvsc_lattice* lat, int R, int prec, int op, pvsc
     p.acc = static_cast<double2*>(acc);
     p.acc_out = static_cast<double2*>(acc);
     p.acc_mode = ACC_ADD | ACC_X | (op == PVSC_OP_APPLY ? 0 : ACC_YIN);
-    p.cx_re = 0.3;
-    p.cy_im = -0.2;
+    p.cx_re = 0.3;  // real weights, the kinds of a filter's three-term touch
+    p.cy_re = -0.2;
     p.cz_re = -0.1;
     PVSC_CUDA_TRY(cudaMemsetAsync(work, 0, kWorkHeader, st));
     auto one = [&]() -> int {

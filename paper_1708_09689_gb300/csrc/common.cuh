@@ -241,7 +241,8 @@ struct Sweep {
   double coef[4][kMaxR]; // alpha, beta, gamma, delta per vector
   // series accumulation (complex128 accumulator)
   int acc_mode;          // AccMode bits (below)
-  int acc_kind;          // set at launch: bits 0-1 kind of cx, 2-3 of cy, 4-5 of cz (1 real, 2 imaginary, 3 zero)
+  int acc_kind;          // set at launch: bits 0-1 kind of cx, 2-3 of cy, 4-5 of cz (0 general, 1 real,
+                         // 2 imaginary, 3 zero or no such term)
   double2* acc;
   double2* acc_out;      // final: written here
   double cx_re, cx_im, cy_re, cy_im, ph_re, ph_im;

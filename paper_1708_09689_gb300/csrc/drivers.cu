@@ -114,8 +114,9 @@ int launch_sweep_shape(const pvsc_lattice* lat, int prec, int feat, Sweep& p, La
       (!p.yin || !(p.acc_mode & ACC_X) || (p.acc_mode & (ACC_INIT | ACC_XSRC))))
     return set_error(PVSC_ERR_ARG, "an accumulating sweep with the y_in term needs y_in and the x term, "
                                    "and no INIT or XSRC");
-  p.acc_kind = coef_kind(p.cx_re, p.cx_im) | (coef_kind(p.cy_re, p.cy_im) << 2) |
-               (coef_kind(p.cz_re, p.cz_im) << 4);
+  // an absent x or y_in term has the kind of a zero weight (3)
+  p.acc_kind = ((p.acc_mode & ACC_X) ? coef_kind(p.cx_re, p.cx_im) : 3) | (coef_kind(p.cy_re, p.cy_im) << 2) |
+               (((p.acc_mode & ACC_YIN) ? coef_kind(p.cz_re, p.cz_im) : 3) << 4);
   const double cv[3][2] = {{p.cx_re, p.cx_im}, {p.cy_re, p.cy_im}, {p.cz_re, p.cz_im}};
   for (int t = 0; t < 3; ++t)
     for (int q = 0; q < 2; ++q) {

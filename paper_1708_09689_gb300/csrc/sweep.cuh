@@ -315,6 +315,90 @@ __device__ __forceinline__ void csum_cfma(const float (&w)[2][2], int kind, floa
   }
 }
 
+// The same with the weight's kind fixed at compile time (KIND 0, 1 or 2);
+// FIRST: the sums start with this term, exactly (S = p, E = q).
+template <int KIND, bool FIRST>
+__device__ __forceinline__ void csum_term(const float (&w)[2][2], float xr, float xi, CSum& sr, CSum& si) {
+  static_assert(KIND >= 0 && KIND <= 2, "a nonzero weight");
+  if constexpr (KIND != 2) {
+    if constexpr (FIRST) {
+      sr.S = __fmul_rn(w[0][0], xr);
+      sr.E = __fmaf_rn(w[0][0], xr, -sr.S);
+      si.S = __fmul_rn(w[0][0], xi);
+      si.E = __fmaf_rn(w[0][0], xi, -si.S);
+    } else {
+      csum_add(sr, w[0][0], xr);
+      csum_add(si, w[0][0], xi);
+    }
+    sr.E = __fmaf_rn(w[0][1], xr, sr.E);
+    si.E = __fmaf_rn(w[0][1], xi, si.E);
+  }
+  if constexpr (KIND != 1) {
+    if constexpr (FIRST && KIND == 2) {
+      sr.S = __fmul_rn(-w[1][0], xi);
+      sr.E = __fmaf_rn(-w[1][0], xi, -sr.S);
+      si.S = __fmul_rn(w[1][0], xr);
+      si.E = __fmaf_rn(w[1][0], xr, -si.S);
+    } else {
+      csum_add(sr, -w[1][0], xi);
+      csum_add(si, w[1][0], xr);
+    }
+    sr.E = __fmaf_rn(-w[1][1], xi, sr.E);
+    si.E = __fmaf_rn(w[1][1], xr, si.E);
+  }
+}
+
+// acc (+)= cz y_in + cx x + cy y_new for the complex64 values of one block:
+// the one to three terms of each value as a compensated fp32 sum (weights in
+// p.fc: [0] x, [1] y_new, [2] y_in), rounded once and added to the fp64
+// accumulator with one fp64 add per part.  KZ, KX, KY: the kinds of the y_in,
+// x and y_new weights, or -1 for all three taken at run time from p.acc_kind
+// (kind 3: no such term).
+template <int KZ, int KX, int KY, int VPT>
+__device__ __forceinline__ void acc_c64(const Sweep& p, int64_t s, int rc, const Blk<float, VPT>& yi,
+                                        const Blk<float, VPT>& xc, const Blk<float, VPT>& yn) {
+  const int R = p.R, mode = p.acc_mode;
+#pragma unroll
+  for (int o = 0; o < 4; ++o)
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int r = rc * VPT + v;
+      double ar = 0.0, ai = 0.0;
+      if (!(mode & ACC_INIT)) {
+        const double2 a = *acc_ptr(p.acc, s, o, R, r);
+        ar = a.x;
+        ai = a.y;
+      }
+      CSum cr{0.f, 0.f}, ci{0.f, 0.f};
+      if constexpr (KZ < 0) {
+        const int kx = p.acc_kind & 3, ky = (p.acc_kind >> 2) & 3, kz = (p.acc_kind >> 4) & 3;
+        csum_cfma(p.fc[2], kz, yi.v[o][v].re, yi.v[o][v].im, cr, ci);
+        csum_cfma(p.fc[0], kx, xc.v[o][v].re, xc.v[o][v].im, cr, ci);
+        csum_cfma(p.fc[1], ky, yn.v[o][v].re, yn.v[o][v].im, cr, ci);
+      } else {
+        static_assert(KZ != 3 && KX != 3 && KY != 3, "compiled for three terms");
+        csum_term<KZ, true>(p.fc[2], yi.v[o][v].re, yi.v[o][v].im, cr, ci);
+        csum_term<KX, false>(p.fc[0], xc.v[o][v].re, xc.v[o][v].im, cr, ci);
+        csum_term<KY, false>(p.fc[1], yn.v[o][v].re, yn.v[o][v].im, cr, ci);
+      }
+      const float sr = __fadd_rn(cr.S, cr.E), si = __fadd_rn(ci.S, ci.E);
+      if (mode & ACC_INIT) {
+        ar = widen(sr);
+        ai = widen(si);
+      } else {
+        ar += widen(sr);
+        ai += widen(si);
+      }
+      if (mode & ACC_FINAL) {
+        *acc_ptr(p.acc_out, s, o, R, r) = make_double2(p.ph_re * ar - p.ph_im * ai, p.ph_re * ai + p.ph_im * ar);
+      } else {
+        *acc_ptr(p.acc, s, o, R, r) = make_double2(ar, ai);
+      }
+    }
+}
+
+constexpr int acc_key(int kx, int ky, int kz) { return kx | (ky << 2) | (kz << 4); }
+
 // ---------------------------------------------------------------- the shared epilogue
 // Everything a sweep does after y_new of one block is known.  yi: the block's
 // y_in as the sweep read it (read only by an accumulating sweep that takes the
@@ -356,62 +440,63 @@ __device__ __forceinline__ void epilogue(const Sweep& p, int64_t s, int rc, cons
     // output: with three terms per sweep the driver touches the accumulator on
     // every third sweep only.
     const int mode = p.acc_mode;
-    const int kx = p.acc_kind & 3, ky = (p.acc_kind >> 2) & 3, kz = (p.acc_kind >> 4) & 3;
-#pragma unroll
-    for (int o = 0; o < 4; ++o)
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        const int r = rc * VPT + v;
-        double ar = 0.0, ai = 0.0;
-        if (!(mode & ACC_INIT)) {
-          const double2 a = *acc_ptr(p.acc, s, o, R, r);
-          ar = a.x;
-          ai = a.y;
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      // complex64 vectors (the complex128 source aside): compensated fp32 sums
+      // of the one to three terms (a plain fp32 chain of three terms is biased
+      // for the recurring weights of a propagation: the norm of the state
+      // drifts by ~1e-8 per time step), compiled for the kinds of the
+      // three-term touches of real series (filters) and of propagations
+      // (weights alternating between real and imaginary); other touches take
+      // the kinds at run time.
+      if (!(mode & ACC_XSRC)) {
+        switch (p.acc_kind) {
+          case acc_key(1, 1, 1): acc_c64<1, 1, 1, VPT>(p, s, rc, yi, xc, yn); break;
+          case acc_key(2, 1, 1): acc_c64<1, 2, 1, VPT>(p, s, rc, yi, xc, yn); break;
+          case acc_key(1, 2, 2): acc_c64<2, 1, 2, VPT>(p, s, rc, yi, xc, yn); break;
+          default: acc_c64<-1, -1, -1, VPT>(p, s, rc, yi, xc, yn);
         }
-        if constexpr (sizeof(T) == 4) {
-          if (!(mode & ACC_XSRC)) {
-            // complex64 vectors: the one to three terms as a compensated fp32
-            // sum, rounded once and added to the fp64 accumulator with one fp64
-            // add per part.  (A plain fp32 chain of three terms is biased for the
-            // recurring weights of a propagation: the norm of the state drifts
-            // by ~1e-8 per time step.)
-            CSum cr{0.f, 0.f}, ci{0.f, 0.f};
-            if (mode & ACC_YIN) csum_cfma(p.fc[2], kz, yi.v[o][v].re, yi.v[o][v].im, cr, ci);
-            if (mode & ACC_X) csum_cfma(p.fc[0], kx, xc.v[o][v].re, xc.v[o][v].im, cr, ci);
-            csum_cfma(p.fc[1], ky, yn.v[o][v].re, yn.v[o][v].im, cr, ci);
-            const float sr = __fadd_rn(cr.S, cr.E), si = __fadd_rn(ci.S, ci.E);
-            if (mode & ACC_INIT) {
-              ar = widen(sr);
-              ai = widen(si);
-            } else {
-              ar += widen(sr);
-              ai += widen(si);
-            }
-          } else {
+        done = true;
+      }
+    }
+    if (!done) {
+      const int kx = p.acc_kind & 3, ky = (p.acc_kind >> 2) & 3, kz = (p.acc_kind >> 4) & 3;
+#pragma unroll
+      for (int o = 0; o < 4; ++o)
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          const int r = rc * VPT + v;
+          double ar = 0.0, ai = 0.0;
+          if (!(mode & ACC_INIT)) {
+            const double2 a = *acc_ptr(p.acc, s, o, R, r);
+            ar = a.x;
+            ai = a.y;
+          }
+          if constexpr (sizeof(T) == 4) {  // the first touch: x exact from the complex128 source
             const double2 h = *acc_ptr(const_cast<double2*>(p.src), s, o, R, r);
             cfma_acc(p.cx_re, p.cx_im, kx, h.x, h.y, ar, ai);
             cfma_acc(p.cy_re, p.cy_im, ky, widen(yn.v[o][v].re), widen(yn.v[o][v].im), ar, ai);
-          }
-        } else {
-          if (mode & ACC_YIN) cfma_acc(p.cz_re, p.cz_im, kz, yi.v[o][v].re, yi.v[o][v].im, ar, ai);
-          if (mode & ACC_X) {
-            double xr = xc.v[o][v].re, xi = xc.v[o][v].im;
-            if (mode & ACC_XSRC) {
-              const double2 h = *acc_ptr(const_cast<double2*>(p.src), s, o, R, r);
-              xr = h.x;
-              xi = h.y;
+          } else {
+            if (mode & ACC_YIN) cfma_acc(p.cz_re, p.cz_im, kz, yi.v[o][v].re, yi.v[o][v].im, ar, ai);
+            if (mode & ACC_X) {
+              double xr = xc.v[o][v].re, xi = xc.v[o][v].im;
+              if (mode & ACC_XSRC) {
+                const double2 h = *acc_ptr(const_cast<double2*>(p.src), s, o, R, r);
+                xr = h.x;
+                xi = h.y;
+              }
+              cfma_acc(p.cx_re, p.cx_im, kx, xr, xi, ar, ai);
             }
-            cfma_acc(p.cx_re, p.cx_im, kx, xr, xi, ar, ai);
+            cfma_acc(p.cy_re, p.cy_im, ky, yn.v[o][v].re, yn.v[o][v].im, ar, ai);
           }
-          cfma_acc(p.cy_re, p.cy_im, ky, yn.v[o][v].re, yn.v[o][v].im, ar, ai);
+          if (mode & ACC_FINAL) {
+            *acc_ptr(p.acc_out, s, o, R, r) =
+                make_double2(p.ph_re * ar - p.ph_im * ai, p.ph_re * ai + p.ph_im * ar);
+          } else {
+            *acc_ptr(p.acc, s, o, R, r) = make_double2(ar, ai);
+          }
         }
-        if (mode & ACC_FINAL) {
-          *acc_ptr(p.acc_out, s, o, R, r) =
-              make_double2(p.ph_re * ar - p.ph_im * ai, p.ph_re * ai + p.ph_im * ar);
-        } else {
-          *acc_ptr(p.acc, s, o, R, r) = make_double2(ar, ai);
-        }
-      }
+    }
   }
   if constexpr ((FEAT & F_ADJ) != 0) {
     if (p.grad != nullptr) {
