@@ -550,6 +550,10 @@ typedef struct {
                   /* for lattices whose z columns are short; eight warps, the large or */
                   /* (TI) the half tile; zslab = x-chunk depth; same vectors as the */
                   /* z-march bit for bit; the fused step with z runs kernel 7. */
+                  /* Kernels 7 and 8 are launched with programmatic dependent launch: */
+                  /* the next sweep's blocks set up on free SMs and wait for the */
+                  /* previous sweep to complete before touching global memory (same */
+                  /* results; environment PVSC_NO_PDL=1 launches them plainly). */
                   /* PVSC_Q64 (KPM on TI lattices) takes kernels 0, 2, 3 (threads a */
                   /* multiple of R, one vector per thread, no tile) and 7 for R = 1 .. 32 */
                   /* (any Lx): the tiles, rings and variants of the complex64 layout */

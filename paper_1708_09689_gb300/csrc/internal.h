@@ -218,6 +218,13 @@ inline void drop_graphs(pvsc_lattice* lat) {
   lat->graphs.clear();
 }
 
+// Programmatic dependent launch of the TMA-staged sweeps (on unless
+// PVSC_NO_PDL is set to a value other than 0).
+inline bool pdl_enabled() {
+  const char* e = std::getenv("PVSC_NO_PDL");
+  return !(e && e[0] && e[0] != '0');
+}
+
 inline bool graphs_enabled() {
   const char* e = std::getenv("PVSC_NO_GRAPH");
   return !(e && e[0] && e[0] != '0');

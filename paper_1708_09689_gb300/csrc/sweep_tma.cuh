@@ -305,6 +305,11 @@ __global__ void __launch_bounds__(32 * NW, 1)
   uint64_t* full_x = reinterpret_cast<uint64_t*>(base + L::BAR_OFF);
   uint64_t* full_y = full_x + L::NXS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // Programmatic dependent launch (when the host launches with it): the next
+  // sweep on the stream may start its blocks now, on SMs this grid leaves free
+  // or frees; they set up their barriers and unit tables and then wait at
+  // griddepcontrol.wait below for this grid to complete.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (threadIdx.x == 0) {
     for (int s = 0; s < L::NXS; ++s) mbar_init(&full_x[s], 1);
     for (int s = 0; s < L::NYS; ++s) mbar_init(&full_y[s], 1);
@@ -458,6 +463,11 @@ __global__ void __launch_bounds__(32 * NW, 1)
       if (ahead_y(lu, j, L::NYS)) issue_y(lu, j, k + L::NYS);
   };
 
+  // Everything above used kernel parameters only.  Before the first access to
+  // global memory, wait for the grid this one depends on (the previous sweep,
+  // whose outputs it reads and whose inputs it may overwrite) to complete; a
+  // no-op without programmatic dependent launch.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   // a block without a plane of work (more blocks than planes) issues no copy:
   // its unit table is empty
   if (threadIdx.x == 0 && nlu > 0) {
@@ -927,7 +937,20 @@ static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const Launc
   // staggered depths lose the halo strips' L2 reuse)
   const int grid = (int)(SL * (m.nunits < grid_max ? m.nunits : grid_max));
   void* args[] = {&p, &m};
-  PVSC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(32 * NW), args, L::SMEM, st));
+  // with programmatic dependent launch: all of a sweep's blocks are resident at
+  // once (grid <= SMs x occupancy), so the next sweep's blocks, which wait for
+  // this grid to complete, only take SMs this one leaves free or has finished with
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(32 * NW);
+  cfg.dynamicSmemBytes = L::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  PVSC_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, args));
   return PVSC_OK;
 }
 

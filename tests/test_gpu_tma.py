@@ -272,3 +272,28 @@ def test_tma_x_march_is_validated():
         lat.set_tuning(8, pv.C64, kernel=9)
     lat.set_tuning(8, pv.C64, kernel=8, tile_x=16, tile_y=4)
     assert lat.get_tuning(8, pv.C64)["kernel"] == 8
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+@pytest.mark.parametrize("model,R", [("ti", 8), ("ti", 64), ("wsm", 16)])
+def test_programmatic_dependent_launch_changes_no_bit(monkeypatch, graphs, model, R):
+    # The TMA-staged sweeps start the next sweep's blocks early (they wait for the
+    # previous grid before touching global memory).  The KPM moments and a
+    # filtered block (accumulating sweeps writing over their y_in) must be the
+    # same bits with and without it, replayed from a graph or launched directly.
+    monkeypatch.setenv("PVSC_NO_GRAPH", "0" if graphs else "1")
+    dims, per = ((48, 40, 9), (1, 1, 0)) if model == "ti" else ((64, 24, 10), (1, 0, 1))
+    out = {}
+    for pdl in ("0", "1"):
+        monkeypatch.setenv("PVSC_NO_PDL", "0" if pdl == "1" else "1")
+        lat = (pv.Lattice.ti(dims, per, disorder=(2.0, 3)) if model == "ti"
+               else pv.Lattice.wsm(dims, per, disorder=(1.0, 5)))  # a fresh handle: no cached graph
+        lat.set_tuning(R, pv.C64, kernel=7)
+        _, _, a, b = lat.spectral_bounds()
+        mu = pv.kpm_moments(lat, 40, a, b, R=R, seed=6).cpu().numpy()
+        x = pv.random_vectors(lat, R, pv.C128, 8)
+        y = pv.cheb_filter(lat, x, [1.0 / (k + 1) for k in range(14)], a, b, prec=pv.C64).cpu().numpy()
+        assert pv.device_error() == 0
+        out[pdl] = (mu, y)
+    assert np.array_equal(out["0"][0], out["1"][0])
+    assert np.array_equal(out["0"][1], out["1"][1])
