@@ -86,8 +86,9 @@ def parse():
                          "eigenpairs, Weyl-semimetal KPM) and print one JSON line each")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="profiling case: one KPM call of this many complex64 sweeps (stencil, "
-                         "recurrence, dots) on the lattice (ti_slab), or this many complex64 "
-                         "propagation time steps (graphene_qd), and exit without timing")
+                         "recurrence, dots) on the lattice (ti_slab, ti_akE, wsm_kpm), this many "
+                         "complex64 propagation time steps (graphene_qd), or one complex64 filter of "
+                         "this many series terms (chebfd, R from --R), and exit without timing")
     ap.add_argument("--batched-count", type=int, default=8,
                     help="with --workload batched --sweeps-only: number of lattices of the batch")
     ap.add_argument("--q64", action="store_true",
@@ -487,6 +488,15 @@ def run_workload(args, pv, dev, rank, world):
         lat = pv.Lattice.ti(dims, (1, 1, 1), t=1.0, m=2.0)
         emin, emax, a, b = lat.spectral_bounds()
         R = 4 * nk_call
+        if args.sweeps_only:  # profiling case: one KPM call of this many sweeps on 16 k-points, untimed
+            if args.launch:
+                lat.set_tuning(R, pv.C64, **{k: v for k, v in json.loads(args.launch).items() if k != "time_ms"})
+            psi = pv.bloch_vectors(lat, [(2 * math.pi * (j - 8) / 64, 0.0, 0.0) for j in range(nk_call)], pv.C64)
+            mu = pv.kpm_moments(lat, 2 * args.sweeps_only, a, b, r0=psi)
+            torch.cuda.synchronize()
+            if rank == 0:
+                print(json.dumps({"sweeps": args.sweeps_only, "mu_0": float(mu[0, 0].item())}))
+            return 0
         if not args.no_autotune:
             lat.autotune(R, pv.C64)
         kx = [2 * math.pi * (j - 32) / 64 for j in range(64)]
@@ -533,6 +543,16 @@ def run_workload(args, pv, dev, rank, world):
         dims = (240, 240, 6)
         lat = pv.Lattice.ti(dims, (1, 1, 0), t=1.0, m=2.0, disorder=(1.0, 5))
         emin, emax, a, b = lat.spectral_bounds()
+        if args.sweeps_only:  # profiling case: one complex64 filter of this many series terms, untimed
+            Rf = args.R
+            if args.launch:
+                lat.set_tuning(Rf, pv.C64, **{k: v for k, v in json.loads(args.launch).items() if k != "time_ms"})
+            x = pv.random_vectors(lat, Rf, pv.C128, 3)
+            y = pv.cheb_filter(lat, x, [1.0 / (k + 1) for k in range(args.sweeps_only)], a, b, prec=pv.C64)
+            torch.cuda.synchronize()
+            if rank == 0:
+                print(json.dumps({"series_terms": args.sweeps_only, "R": Rf, "y_max": float(y.abs().max().item())}))
+            return 0
         t0 = time.perf_counter()
         mu = pv.kpm_moments(lat, 8192, a, b, R=32, prec=pv.C64, seed=9)
         Eg = np.linspace(-0.5, 0.5, 20001)

@@ -358,17 +358,21 @@ template <int KZ, int KX, int KY, int VPT>
 __device__ __forceinline__ void acc_c64(const Sweep& p, int64_t s, int rc, const Blk<float, VPT>& yi,
                                         const Blk<float, VPT>& xc, const Blk<float, VPT>& yn) {
   const int R = p.R, mode = p.acc_mode;
+  // all of the block's accumulator loads first: the stores below are at offsets
+  // scaled by the run-time R, which the compiler cannot tell apart from later
+  // loads, so a load after a store would wait for a full round trip each time
+  double2 av[4][VPT];
+#pragma unroll
+  for (int o = 0; o < 4; ++o)
+#pragma unroll
+    for (int v = 0; v < VPT; ++v)
+      av[o][v] = (mode & ACC_INIT) ? make_double2(0.0, 0.0) : *acc_ptr(p.acc, s, o, R, rc * VPT + v);
 #pragma unroll
   for (int o = 0; o < 4; ++o)
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
       const int r = rc * VPT + v;
-      double ar = 0.0, ai = 0.0;
-      if (!(mode & ACC_INIT)) {
-        const double2 a = *acc_ptr(p.acc, s, o, R, r);
-        ar = a.x;
-        ai = a.y;
-      }
+      double ar = av[o][v].x, ai = av[o][v].y;
       CSum cr{0.f, 0.f}, ci{0.f, 0.f};
       if constexpr (KZ < 0) {
         const int kx = p.acc_kind & 3, ky = (p.acc_kind >> 2) & 3, kz = (p.acc_kind >> 4) & 3;
