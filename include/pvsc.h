@@ -275,7 +275,11 @@ int pvsc_kpm_moments(const pvsc_lattice* lat, int R, int prec, const void* r0, u
  * sum accumulated in fp64.  x, y: device complex128 blocks (may be the same
  * buffer).  coeffs: HOST array of K complex values (re, im pairs), used as
  * given.  phase: HOST (re, im) or NULL for 1.  K >= 1.  The recurrence
- * vectors are stored in precision prec.
+ * vectors are stored in precision prec.  The accumulator is read and written
+ * on every third sweep, which adds the three terms that sweep holds (its
+ * y_in, input and output); with PVSC_C64 the three complex64 terms are summed
+ * in fp32 with exact products and compensated additions, rounded once and
+ * added in fp64 (weights carried as fp32 pairs, to about 2^-48).
  * work: pvsc_work_bytes(lat, PVSC_OP_SERIES, R, prec, K).
  */
 int pvsc_cheb_series(const pvsc_lattice* lat, int R, int prec, const void* x, void* y,
