@@ -517,7 +517,9 @@ int pvsc_debug_inject_stall(int enable);
  */
 typedef struct {
   int32_t threads;
-  int32_t blocks_per_sm;
+  int32_t blocks_per_sm; /* resident blocks per SM (0: from occupancy); kernels 7 and 8: 0 or 1, */
+                         /* 1 spreading the planes over every SM when the sweep has fewer */
+                         /* work units (tile x z-chunk) than SMs */
   int32_t zslab;
   float time_ms; /* measured time of one sweep, 0 if not measured */
   int32_t vpt;   /* vectors per thread: 1, or 2 (complex64 with R >= 2); 0 = automatic */

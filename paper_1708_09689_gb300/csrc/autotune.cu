@@ -212,13 +212,16 @@ extern "C" int pvsc_autotune_op(pvsc_lattice* lat, int R, int prec, int op, pvsc
   if (tma_sweep_possible(lat, R, prec)) {
     // the half tiles of the deeper rings (R = 32, 64: slices on the tiles of R = 16)
     const int deep_y = R == 1 ? 16 : (R == 2 || R == 4) ? 8 : 4, deep_x = R >= 16 ? 8 : (R <= 2 ? 32 : 16);
+    // blocks_per_sm 1: spread the planes over every SM when there are fewer units
+    // than SMs (the same launch otherwise)
     for (int zs : {0, 16, 32, 64})
-      if (zs == 0 || zs < lat->g.L[2]) {
-        cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, 0, 0, kKernelTma});
-        cands.push_back(pvsc_tuning{256, 0, zs, 0.f, 2, deep_x, deep_y, kKernelTma});
-        if (lat->g.model == PVSC_TI)  // the Weyl cells run eight warps only
-          cands.push_back(pvsc_tuning{512, 0, zs, 0.f, 2, 0, 0, kKernelTma});
-      }
+      if (zs == 0 || zs < lat->g.L[2])
+        for (int spread : {0, 1}) {
+          cands.push_back(pvsc_tuning{256, spread, zs, 0.f, 2, 0, 0, kKernelTma});
+          cands.push_back(pvsc_tuning{256, spread, zs, 0.f, 2, deep_x, deep_y, kKernelTma});
+          if (lat->g.model == PVSC_TI)  // the Weyl cells run eight warps only
+            cands.push_back(pvsc_tuning{512, spread, zs, 0.f, 2, 0, 0, kKernelTma});
+        }
     // the same tiles marching along x, where the z columns are the shorter
     if (lat->g.L[0] > lat->g.L[2] && tma_xm_possible(lat, R, prec))
       for (int zs : {0, 32, 64})

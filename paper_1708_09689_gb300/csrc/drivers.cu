@@ -1010,7 +1010,8 @@ static int check_q64_tuning(const pvsc_lattice* lat, int R, const pvsc_tuning* t
     if (!tma_tile_valid(2 * R, t->tile_x, t->tile_y))
       return set_error(PVSC_ERR_ARG, "PVSC_Q64 kernel 7 takes no tile other than the two of R = %d (%dx%d given)",
                        R, t->tile_x, t->tile_y);
-    if (t->blocks_per_sm < 0 || t->zslab < 0) return set_error(PVSC_ERR_ARG, "negative tuning value");
+    if (t->blocks_per_sm < 0 || t->blocks_per_sm > 1 || t->zslab < 0)
+      return set_error(PVSC_ERR_ARG, "kernel 7 takes blocks_per_sm 0 or 1 and zslab >= 0");
     return PVSC_OK;
   }
   if (t->kernel != 0 && t->kernel != 2 && t->kernel != 3)
@@ -1053,7 +1054,8 @@ int pvsc_set_tuning(pvsc_lattice* lat, int R, int prec, const pvsc_tuning* tunin
     if (!tma_tile_valid(R, tuning->tile_x, tuning->tile_y))
       return set_error(PVSC_ERR_ARG, "kernel %d takes no tile other than the two of R = %d (%dx%d given)", k, R,
                        tuning->tile_x, tuning->tile_y);
-    if (tuning->blocks_per_sm < 0 || tuning->zslab < 0) return set_error(PVSC_ERR_ARG, "negative tuning value");
+    if (tuning->blocks_per_sm < 0 || tuning->blocks_per_sm > 1 || tuning->zslab < 0)
+      return set_error(PVSC_ERR_ARG, "kernels 7 and 8 take blocks_per_sm 0 or 1 and zslab >= 0");
     lat->tuning[{R, prec}] = *tuning;
     drop_graphs(lat);
     return PVSC_OK;

@@ -932,10 +932,13 @@ static int launch_tma_r(const pvsc_lattice* lat, int feat, Sweep& p, const Launc
   m.nch = nch;
   m.nunits = ntiles * nch;  // per slice
   p.zslab = (int)((Lz + nch - 1) / nch);
-  // no more blocks than units: with fewer units than SMs, splitting columns over
-  // all SMs was measured slower (the Weyl cuboid 77.9 -> 72.2 GLUP/s: pieces at
-  // staggered depths lose the halo strips' L2 reuse)
-  const int grid = (int)(SL * (m.nunits < grid_max ? m.nunits : grid_max));
+  // no more blocks than units, unless the shape asks to spread (blocks_per_sm
+  // = 1): with fewer units than SMs, splitting the columns' planes over all SMs
+  // was measured slower on the Weyl cuboid (77.9 -> 72.2 GLUP/s: pieces at
+  // staggered depths lose the halo strips' L2 reuse) and is left to the
+  // autotuner; blocks left without a plane issue no copy
+  const bool spread = sh.blocks_per_sm == 1;
+  const int grid = (int)(SL * (m.nunits < grid_max && !spread ? m.nunits : grid_max));
   void* args[] = {&p, &m};
   // with programmatic dependent launch: all of a sweep's blocks are resident at
   // once (grid <= SMs x occupancy), so the next sweep's blocks, which wait for

@@ -179,3 +179,18 @@ def test_q64_kernel7_tuning_is_validated():
         lat.set_tuning(8, pv.Q64, kernel=7, tile_x=4, tile_y=4)
     lat.set_tuning(8, pv.Q64, kernel=7, tile_x=8, tile_y=4)
     assert lat.get_tuning(8, pv.Q64)["tile_y"] == 4
+
+
+@pytest.mark.parametrize("dims,R", [((16, 8, 3), 8), ((8, 4, 1), 2), ((16, 8, 2), 32)])
+def test_q64_tma_sweep_spread_over_all_sms_equals_default(dims, R):
+    # blocks_per_sm = 1: the planes split over every SM, most blocks without a
+    # plane; the integer vectors are unchanged, and the moments differ only in
+    # the order the blocks' fp64 conversions of the exact dot sums are added
+    lat = pv.Lattice.ti(dims, (1, 1, 0), disorder=(2.0, 3))
+    _, _, a, b = lat.spectral_bounds()
+    out = []
+    for spread in (0, 1):
+        lat.set_tuning(R, pv.Q64, kernel=7, blocks_per_sm=spread)
+        out.append(pv.kpm_moments(lat, 20, a, b, R=R, prec=pv.Q64, seed=3).cpu().numpy())
+        assert pv.device_error() == 0
+    assert np.max(np.abs(out[0] - out[1])) < 1e-14

@@ -297,3 +297,37 @@ def test_programmatic_dependent_launch_changes_no_bit(monkeypatch, graphs, model
         out[pdl] = (mu, y)
     assert np.array_equal(out["0"][0], out["1"][0])
     assert np.array_equal(out["0"][1], out["1"][1])
+
+
+@pytest.mark.parametrize("dims,per,R,kernel", [
+    ((32, 16, 12), (1, 1, 0), 8, 7),   # 8 tiles x chunks: fewer units than SMs, spread over all
+    ((8, 8, 1), (1, 1, 1), 8, 7),      # one tile, one plane: almost every block has no plane
+    ((16, 8, 3), (0, 1, 1), 64, 7),    # slices of 16 vectors, fewer planes than blocks
+    ((32, 8, 4), (1, 1, 0), 1, 7),     # narrow sites
+    ((48, 16, 8), (1, 0, 1), 16, 8),   # marching along x
+])
+def test_tma_sweep_spread_over_all_sms_equals_default(dims, per, R, kernel):
+    # blocks_per_sm = 1 splits the planes over the whole grid even when there are
+    # fewer units than SMs (blocks without a plane issue no copy); the filtered
+    # vectors must be those of the default launch bit for bit, the moments equal
+    # up to the order in which the blocks' fp64 dot partials are added.
+    lat = pv.Lattice.ti(dims, per, disorder=(2.0, 9))
+    _, _, a, b = lat.spectral_bounds()
+    out = []
+    for spread in (0, 1):
+        lat.set_tuning(R, pv.C64, kernel=kernel, blocks_per_sm=spread)
+        mu = pv.kpm_moments(lat, 24, a, b, R=R, seed=2).cpu().numpy()
+        x = pv.random_vectors(lat, R, pv.C128, 5)
+        y = pv.cheb_filter(lat, x, [0.5, -0.25, 0.125, 0.3, -0.2, 0.1, 0.05], a, b, prec=pv.C64).cpu().numpy()
+        assert pv.device_error() == 0
+        out.append((mu, y))
+    assert np.max(np.abs(out[0][0] - out[1][0])) < 1e-12
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_tma_spread_tuning_is_validated():
+    lat = pv.Lattice.ti((16, 8, 4), (1, 1, 0))
+    with pytest.raises(pv.PvscError, match="blocks_per_sm"):
+        lat.set_tuning(8, pv.C64, kernel=7, blocks_per_sm=2)
+    lat.set_tuning(8, pv.C64, kernel=7, blocks_per_sm=1)
+    assert lat.get_tuning(8, pv.C64)["blocks_per_sm"] == 1
