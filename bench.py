@@ -46,7 +46,7 @@ UNIT = "GLUP/s"
 # the captured version
 TRAFFIC = {("ti_slab", 8, "ti_sweep"): {"bytes_per_launch": 3.220e9, "source_sha256_16": "df26e831c975b98f"},
            ("ti_slab", 8, "ti_sweep_xmarch"): {"bytes_per_launch": 3.222e9, "source_sha256_16": "df26e831c975b98f"},
-           ("ti_slab", 8, "ti_sweep_tma"): {"bytes_per_launch": 3.216e9, "source_sha256_16": "88d6ced0755aa579"}}
+           ("ti_slab", 8, "ti_sweep_tma"): {"bytes_per_launch": 3.216e9, "source_sha256_16": "9c34eb70b45ba370"}}
 KERNEL_SOURCES = ("paper_1708_09689_gb300/csrc/sweep.cuh", "paper_1708_09689_gb300/csrc/common.cuh",
                   "paper_1708_09689_gb300/csrc/sweep_tma.cuh")
 
