@@ -286,6 +286,13 @@ int pvsc_cheb_series(const pvsc_lattice* lat, int R, int prec, const void* x, vo
                      const double* coeffs, int K, const double* phase, double a, double b,
                      void* work, size_t work_bytes, void* stream);
 
+/* Host-only: the accumulator schedule of a series of K terms (for tests).
+ * terms[j] (K ints, caller-owned) = the number of terms the recurrence sweep
+ * j adds to the accumulator, ending with term j: 2 at j = 1, 3 on every third
+ * sweep after it, the one to three left on the last sweep, 0 elsewhere;
+ * K = 1: terms[0] = 1 (no sweep).  PVSC_ERR_ARG if K < 1 or terms is NULL. */
+int pvsc_debug_series_plan(int K, int* terms);
+
 /*
  * Chebyshev filter (the polynomial filter of ChebFD, Sec. 4.2):
  * y = sum_{k=0}^{K-1} g_k T_k(H~) x with real HOST coefficients g (window and

@@ -103,6 +103,7 @@ _SIGNATURES = {
     "pvsc_propagate_adjoint_work_bytes": (_sz, [_vp, _i, _i, _d, _d]),
     "pvsc_debug_export_pattern": (_i, [_vp, _vp, _vp]),
     "pvsc_debug_fx_arith": (_i, [_i, _vp, ctypes.c_int64, _vp, _vp]),
+    "pvsc_debug_series_plan": (_i, [_i, _vp]),
     "pvsc_kpm_sweeps": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _d, _d, _vp, _i, _vp, _sz, _vp]),
     "pvsc_kpm_moments_batched": (_i, [ctypes.POINTER(_vp), _i, _i, _i, ctypes.POINTER(_u64), _i,
                                       _dp, _dp, _vp, _vp, _sz, _vp]),
@@ -592,6 +593,14 @@ def device_error(clear: bool = True) -> int:
     flag = ctypes.c_int(0)
     _check(_lib.pvsc_device_error(ctypes.byref(flag), int(bool(clear))))
     return int(flag.value)
+
+
+def debug_series_plan(K: int) -> list:
+    """Terms each recurrence sweep of a K-term series adds to its accumulator
+    (pvsc_debug_series_plan, host only)."""
+    out = (ctypes.c_int * max(K, 1))()
+    _check(_lib.pvsc_debug_series_plan(K, ctypes.cast(out, ctypes.c_void_p)))
+    return list(out)[:K]
 
 
 def debug_fx_arith(op: int, values, stream=None):

@@ -5,6 +5,7 @@
 #include <complex>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -308,6 +309,26 @@ static SeriesLayout series_layout(const pvsc_lattice* lat, int R, int prec) {
   return L;
 }
 
+// The accumulator touches of a series of K terms: terms[j] = the number of
+// terms sweep j adds, ending with term j (sweep 1 starts with terms 0 and 1,
+// then three terms on every third sweep, the last sweep the one to three
+// left; 0 for sweeps that leave the accumulator alone).  K = 1 has no sweep:
+// terms[0] = 1 (y = c_0 x directly).
+static void series_plan(int K, std::vector<int>& terms) {
+  terms.assign(K, 0);
+  if (K == 1) {
+    terms[0] = 1;
+    return;
+  }
+  terms[1] = 2;
+  int done = 1;  // the accumulator holds the terms 0 .. done
+  for (int j = 2; j < K; ++j)
+    if (j - done == 3 || j == K - 1) {
+      terms[j] = j - done;
+      done = j;
+    }
+}
+
 static int run_series(const pvsc_lattice* lat, int R, int prec, const void* x, void* y,
                       const std::vector<cd>& cw, cd phase, double a, double b, void* work,
                       cudaStream_t st) {
@@ -376,7 +397,8 @@ static int run_series(const pvsc_lattice* lat, int R, int prec, const void* x, v
     cur = wa;
   }
   p.yin = nullptr;
-  int done = 1;  // the accumulator holds the terms 0 .. done
+  std::vector<int> plan;
+  series_plan(K, plan);
   for (int j = 2; j < K; ++j) {
     const bool last = (j == K - 1);
     void* out = (prev == x) ? wb : const_cast<void*>(prev);
@@ -385,10 +407,9 @@ static int run_series(const pvsc_lattice* lat, int R, int prec, const void* x, v
     p.yin = prev;
     p.yout = last ? nullptr : out;
     int feat = 0;
-    if (j - done == 3 || last) {
-      set_acc(j, ACC_ADD | (last ? ACC_FINAL : 0), j - done);
+    if (plan[j] > 0) {
+      set_acc(j, ACC_ADD | (last ? ACC_FINAL : 0), plan[j]);
       feat = F_ACC;
-      done = j;
     }
     if (int rc = launch_sweep(lat, prec, feat, p, st)) return rc;
     prev = cur;
@@ -743,6 +764,14 @@ int pvsc_kpm_sweeps(const pvsc_lattice* lat, int R, int prec, int k_begin, int k
     p.kpm_k = k;
     if (int rc = launch_sweep(lat, prec, F_DOTS, p, st)) return rc;
   }
+  return PVSC_OK;
+}
+
+int pvsc_debug_series_plan(int K, int* terms) {
+  if (K < 1 || !terms) return set_error(PVSC_ERR_ARG, "need K >= 1 and an output array");
+  std::vector<int> t;
+  series_plan(K, t);
+  std::copy(t.begin(), t.end(), terms);
   return PVSC_OK;
 }
 

@@ -152,3 +152,40 @@ def test_binding_structs_match_the_c_layout(libpath, tmp_path, cname, pyname):
     assert int(out["size"]) == ctypes.sizeof(py)
     for f in fields:
         assert int(out[f]) == getattr(py, f).offset, f
+
+
+@pytest.mark.parametrize("K", list(range(1, 40)) + [202, 4000])
+def test_series_accumulator_plan_adds_every_term_once(libpath, K):
+    # The series sweeps add their terms to the fp64 accumulator in groups: the
+    # groups must tile the terms 0 .. K-1 exactly, in order, with at most three
+    # terms per group (a sweep holds only y_in, x and y_new), the last sweep
+    # always writing the result, and no sweep before it touching more often
+    # than every third sweep.
+    lib = ctypes.CDLL(libpath)
+    lib.pvsc_debug_series_plan.argtypes = [ctypes.c_int, ctypes.c_void_p]
+    terms = np.zeros(K, dtype=np.int32)
+    assert lib.pvsc_debug_series_plan(K, terms.ctypes.data) == 0
+    if K == 1:
+        assert terms.tolist() == [1]
+        return
+    assert terms[0] == 0 and terms[1] == 2 and terms[K - 1] > 0
+    covered = -1
+    touches = []
+    for j in range(1, K):
+        n = int(terms[j])
+        if n:
+            assert 1 <= n <= 3 and j - n + 1 == covered + 1  # the next terms, ending with term j
+            covered = j
+            touches.append(j)
+    assert covered == K - 1 and int(terms.sum()) == K
+    inner = [j for j in touches if 1 < j < K - 1]
+    assert all(j % 3 == 1 for j in inner)
+    assert len(touches) == 1 + len(inner) + (K - 1 > 1)
+
+
+def test_series_plan_rejects_bad_arguments(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.pvsc_debug_series_plan.argtypes = [ctypes.c_int, ctypes.c_void_p]
+    out = np.zeros(4, dtype=np.int32)
+    assert lib.pvsc_debug_series_plan(0, out.ctypes.data) != 0
+    assert lib.pvsc_debug_series_plan(3, None) != 0
